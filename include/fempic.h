@@ -1,0 +1,241 @@
+/*
+ * fempic.h -- C ABI of the GB300 (sm_103a) charge-conserving FEM-PIC library.
+ *
+ * The library implements the data-parallel step of the time-integrator-
+ * agnostic, charge-conserving finite-element particle-in-cell method of
+ * O'Connor, Crawford, Ramachandran, Luginsland and Shanker ("Time Integrator
+ * Agnostic Charge Conserving Finite Element PIC"):
+ *   - fields on a tetrahedral mesh: E on edges (Whitney-1), B on faces
+ *     (Whitney-2), Sec. II.A;
+ *   - per step: gather E, B at every particle, push (Boris or Adams-Bashforth,
+ *     Sec. III.B, Eq. adam-bashforth), walk the straight path rn -> rn+1 through
+ *     the tets (Algorithm 1, Sec. III.C), integrate Whitney-1 exactly along
+ *     every in-cell piece and accumulate the time-integrated current Gbar
+ *     (Eq. gaussredo, Eq. G), then advance the fields with the Newmark-beta
+ *     recurrence (gamma = 1/2, beta = 1/4, Sec. II.B) driven by Gbar instead of
+ *     the current (Sec. III.A), solved by preconditioned CG.
+ *
+ * Conventions (fixed by this library; the paper leaves them open):
+ *   - node ids are the caller's; edge e = (tail, head), tail < head, edges in
+ *     lexicographic order of (tail, head); face f = (a, b, c), a < b < c, in
+ *     lexicographic order, oriented by (x_b - x_a) x (x_c - x_a);
+ *   - G[e][tail] = -1, G[e][head] = +1 (so G phi is the gradient);
+ *     C[f] = +edge(a,b) + edge(b,c) - edge(a,c);
+ *     D[t][f] = +1 when face f's orientation points out of tet t;
+ *   - e_i, b_i are the circulation / flux degrees of freedom, so G, C, D are
+ *     +-1 incidence matrices with C G = 0 and D C = 0;
+ *   - SI units; rho_n = sum_p q w lambda_n(r_p) is the node charge, and the
+ *     discrete laws the library maintains are continuity
+ *       (rho + wall)^{n+1} - (rho + wall)^n = G^T dGbar   (every node)
+ *     and Gauss  G^T M e + rho + wall + rho_background = 0 (interior nodes),
+ *     where "wall" is the charge absorbed by the perfectly conducting walls.
+ *
+ * Ownership: every handle owns its host and device memory.  Pointers passed
+ * in are read (or written) only during the call.  A pointer flagged
+ * `on_device` is a device address of the current CUDA device (e.g. a torch
+ * tensor's data_ptr()); otherwise it is host memory.
+ *
+ * Errors: every call returns PIC_OK (0) or one of the PIC_ERR_* codes; the
+ * message of the last failure on the calling thread is pic_last_error().
+ * Errors raised on the device (walk cap, CG non-convergence, NaN) are latched
+ * in a status word and reported by the next call that synchronises
+ * (pic_step, pic_field_get, pic_particles_get, pic_diagnostics_get).
+ * No call aborts the process.
+ */
+#ifndef FEMPIC_H
+#define FEMPIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_OK 0
+#define PIC_ERR_INVALID_ARG 1
+#define PIC_ERR_MESH 2
+#define PIC_ERR_OOM 3
+#define PIC_ERR_PARTICLE_OUTSIDE 4
+#define PIC_ERR_WALK_CAP 5
+#define PIC_ERR_CG_NO_CONVERGENCE 6
+#define PIC_ERR_NAN 7
+#define PIC_ERR_CUDA 8
+#define PIC_ERR_OVERFLOW 9
+#define PIC_ERR_STATE 10
+
+#define PIC_FORM_WE 0        /* wave-equation form, Eq. wave_cont */
+#define PIC_FORM_MFEM 1      /* Maxwell-solver (mixed) form, Eq. maxwell_semi */
+
+#define PIC_PUSH_BORIS 0     /* 1..5: Adams-Bashforth of that order */
+
+#define PIC_PRECISION_PLAIN 0 /* everything FP64 */
+#define PIC_PRECISION_MIXED 1 /* FP32 particle state, gather and push; FP64 barycentrics, deposit, solve */
+
+#define PIC_PRECOND_JACOBI 0
+
+/* fields for pic_field_get / pic_field_set (lengths in brackets) */
+#define PIC_FIELD_E 0        /* e^n        [n_edges], 0 on wall edges */
+#define PIC_FIELD_E_PREV 1   /* e^{n-1}    [n_edges] */
+#define PIC_FIELD_B 2        /* b^n        [n_faces] */
+#define PIC_FIELD_B_PREV 3   /* b^{n-1}    [n_faces] */
+#define PIC_FIELD_G 4        /* Gbar^n     [n_edges] */
+#define PIC_FIELD_G_PREV 5   /* Gbar^{n-1} [n_edges] */
+#define PIC_FIELD_DG 6       /* Gbar^n - Gbar^{n-1} of the last step [n_edges] */
+#define PIC_FIELD_RHO 7      /* node charge of the particles [n_nodes] */
+#define PIC_FIELD_WALL 8     /* charge absorbed by the walls [n_nodes] */
+#define PIC_FIELD_RHO_BG 9   /* static background node charge [n_nodes] */
+#define PIC_FIELD_PHI 10     /* initial electrostatic potential [n_nodes] */
+
+/* ---------------------------------------------------------------------- */
+/* mesh                                                                    */
+/* ---------------------------------------------------------------------- */
+typedef struct pic_mesh pic_mesh;
+
+typedef struct {
+    int32_t n_nodes;
+    const double *xyz;        /* [3*n_nodes] node coordinates (m) */
+    int32_t n_tets;
+    const int32_t *tets;      /* [4*n_tets] node ids, any vertex order */
+    /* Optional explicit entities and incidence (all NULL/0 to let the library
+     * derive them).  When given they must equal the library's canonical ones
+     * (see the conventions above); they are validated, not trusted. */
+    int32_t n_edges;
+    const int32_t *edges;     /* [2*n_edges] (tail, head) */
+    int32_t n_faces;
+    const int32_t *faces;     /* [3*n_faces] (a, b, c) */
+    const int32_t *G_coo;     /* [3 * 2*n_edges]  rows, cols, vals */
+    const int32_t *C_coo;     /* [3 * 3*n_faces] */
+    const int32_t *D_coo;     /* [3 * 4*n_tets] */
+} pic_mesh_desc;
+
+/* Builds the mesh (Sec. II.A): validates the tets (distinct nodes, non-zero
+ * volume), derives edges, faces, incidence G/C/D (checking C G = 0 and
+ * D C = 0), tet adjacency, wall entities (faces with one tet), the Hodge
+ * matrices [*eps], [*mu^-1], the curl-curl matrix [*S] = C^T [*mu^-1] C and
+ * the node Laplacian G^T [*eps] G, and uploads everything to the current
+ * device.  Errors: PIC_ERR_INVALID_ARG (NULL or negative sizes),
+ * PIC_ERR_MESH (degenerate or non-manifold tets, incidence mismatch),
+ * PIC_ERR_OOM, PIC_ERR_CUDA. */
+int pic_mesh_create(const pic_mesh_desc *desc, pic_mesh **out);
+void pic_mesh_destroy(pic_mesh *mesh);
+
+/* counts[0..5] = n_nodes, n_edges, n_faces, n_tets, n_interior_edges,
+ * n_interior_nodes */
+int pic_mesh_info(const pic_mesh *mesh, int64_t *counts);
+
+/* Canonical entities: edges [2*n_edges], faces [3*n_faces] (host memory;
+ * either may be NULL). */
+int pic_mesh_entities(const pic_mesh *mesh, int32_t *edges, int32_t *faces);
+
+/* Incidence as COO triplets (host memory): which = 0 G (2*n_edges entries),
+ * 1 C (3*n_faces), 2 D (4*n_tets); rows/cols/vals each of that length. */
+int pic_mesh_incidence(const pic_mesh *mesh, int32_t which, int32_t *rows, int32_t *cols,
+                       int32_t *vals);
+
+/* ---------------------------------------------------------------------- */
+/* simulation                                                              */
+/* ---------------------------------------------------------------------- */
+typedef struct pic_sim pic_sim;
+
+typedef struct {
+    int32_t form;            /* PIC_FORM_WE or PIC_FORM_MFEM */
+    int32_t pusher;          /* PIC_PUSH_BORIS or 1..5 (Adams-Bashforth order) */
+    int32_t precision;       /* PIC_PRECISION_PLAIN or PIC_PRECISION_MIXED */
+    int32_t preconditioner;  /* PIC_PRECOND_JACOBI */
+    double dt;               /* time step (s), > 0 */
+    double b0[3];            /* uniform external magnetic flux density (T) */
+    double rho_background;   /* uniform static charge density (C/m^3) */
+    double cg_tol;           /* relative residual of the Newmark solve (1e-10) */
+    int32_t cg_max_iters;    /* (10000) */
+    double init_tol;         /* relative residual of the Laplacian solves (1e-14) */
+    int32_t walk_cap;        /* max tets one particle visits in one step (64) */
+    int32_t cg_check_every;  /* CG iterations between host convergence checks (16) */
+    int32_t max_species;     /* species slots (4) */
+    void *stream;            /* cudaStream_t to run on; NULL = default stream */
+} pic_config;
+
+/* Fills a config with the defaults above (form WE, Boris, PLAIN, dt = 0). */
+void pic_config_default(pic_config *cfg);
+
+/* Creates a simulation on the mesh (which must outlive it).  Assembles the
+ * Newmark matrix A = [*eps] + dt^2/4 [*S] (Sec. II.B).  Errors:
+ * PIC_ERR_INVALID_ARG (bad config), PIC_ERR_OOM, PIC_ERR_CUDA. */
+int pic_sim_create(const pic_mesh *mesh, const pic_config *cfg, pic_sim **out);
+void pic_sim_destroy(pic_sim *sim);
+
+/* Appends n particles of one species: charge q (C), mass m (kg), macro
+ * weight w; positions x [3n] and velocities v [3n] interleaved (x0,y0,z0,...)
+ * in FP64.  For Boris, v is taken as v^{n-1/2}; for Adams-Bashforth as v^n.
+ * tet_hint [n] gives each particle's tet (NULL: located by a walk from tet 0).
+ * Particles outside their tet (any barycentric below -1e-10) give
+ * PIC_ERR_PARTICLE_OUTSIDE.  Must be called before pic_sim_init.
+ * Particle ids are assigned in load order, starting at 0. */
+int pic_particles_load(pic_sim *sim, int32_t species, double q, double m, double w, int64_t n,
+                       const double *x, const double *v, const int32_t *tet_hint, int32_t on_device);
+
+/* Initial state (Sec. III.A asks only that the integrator remember the
+ * initial conditions; this is the library's start-up): b^0 = b^{-1} = flux
+ * of b0; rho^0 from the particles; (G^T M G) phi = rho^0 + rho_bg on interior
+ * nodes, e^0 = e^{-1} = -G phi; Gbar^0 = Gbar^{-1} = 0. */
+int pic_sim_init(pic_sim *sim);
+
+/* Adams-Bashforth start-up history for `levels` earlier steps (level j is j
+ * steps back), arrays [levels][n_particles][3] in load order (FP64, host).
+ * Without it the order ramps 1..k over the first steps. Call after init. */
+int pic_set_ab_history(pic_sim *sim, int32_t levels, const double *a_hist, const double *v_hist);
+
+/* Advances nsteps PIC cycles on the configured stream (Sec. II.A cycle order):
+ * sort particles by tet, stage per-tet field coefficients, gather + push +
+ * walk + exact Whitney-1 deposit, deterministic reduction to edges and nodes,
+ * Newmark right-hand side, PCG solve, Faraday update, diagnostics.  Blocks
+ * only for the CG convergence checks.  Errors: PIC_ERR_WALK_CAP,
+ * PIC_ERR_CG_NO_CONVERGENCE, PIC_ERR_NAN, PIC_ERR_OVERFLOW, PIC_ERR_CUDA. */
+int pic_step(pic_sim *sim, int32_t nsteps);
+
+/* Only the particle phase of one step with the fields frozen (gather, push,
+ * walk, deposit and reduction); updates particles, dGbar, rho and wall. */
+int pic_particle_phase(pic_sim *sim);
+
+/* Reads one PIC_FIELD_* array (canonical numbering) into out [n]; n must be
+ * the field's length.  Synchronises the stream. */
+int pic_field_get(pic_sim *sim, int32_t which, double *out, int64_t n, int32_t on_device);
+/* Overwrites one field (E, E_PREV, B, B_PREV, G, G_PREV only). */
+int pic_field_set(pic_sim *sim, int32_t which, const double *in, int64_t n, int32_t on_device);
+
+/* Number of live particles after the last step (synchronises). */
+int pic_particles_count(pic_sim *sim, int64_t *n);
+/* Copies the live particles (in the library's current order) into the
+ * caller's arrays of capacity cap: x [3*cap], v [3*cap] (FP64), tet [cap],
+ * id [cap] (any may be NULL); *n receives the count.  PIC_ERR_INVALID_ARG
+ * if cap is too small. */
+int pic_particles_get(pic_sim *sim, double *x, double *v, int32_t *tet, int32_t *id, int64_t cap,
+                      int64_t *n, int32_t on_device);
+
+typedef struct {
+    double step;            /* steps taken */
+    double continuity_abs;  /* max_n |(rho+wall)^{n+1} - (rho+wall)^n - (G^T dGbar)_n| */
+    double gauss_abs;       /* max over interior n of |(G^T M e)_n + rho_n + wall_n + rho_bg_n| */
+    double rho_max;         /* max_n |rho_n + wall_n| */
+    double divb_abs;        /* max_t |(D b)_t| */
+    double cg_iters;        /* iterations of the last Newmark solve */
+    double cg_relres;       /* its final relative residual */
+    double n_alive;         /* live particles */
+    double energy_e;        /* 1/2 e^T M e */
+    double energy_b;        /* 1/2 b^T H b */
+    double energy_k;        /* sum 1/2 m w |v|^2 */
+    double status;          /* latched device status bits */
+} pic_diag;
+
+/* Diagnostics of the last step (Sec. III.A conservation laws).  Synchronises. */
+int pic_diagnostics_get(pic_sim *sim, pic_diag *out);
+
+/* Waits for all work of the simulation. */
+int pic_sim_synchronize(pic_sim *sim);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *pic_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

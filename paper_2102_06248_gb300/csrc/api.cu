@@ -1,0 +1,622 @@
+// api.cu -- the C ABI of include/fempic.h: handles, error reporting, the
+// step sequence (Sec. II.A cycle order) and host <-> device transfers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "sim.h"
+
+namespace fp {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+int cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PIC_ERR_OOM : PIC_ERR_CUDA;
+}
+
+int upload_particles(Sim *s);
+
+namespace {
+
+__global__ void k_edges_to_canonical(int ne, const int *__restrict__ canon, const double *__restrict__ v,
+                                     double *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ne) out[canon[i]] = v[i];
+}
+__global__ void k_edges_from_canonical(int ne, int n_int, int zero_wall, const int *__restrict__ canon,
+                                       const double *__restrict__ in, double *__restrict__ v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ne) v[i] = (zero_wall && i >= n_int) ? 0.0 : in[canon[i]];
+}
+
+template <typename R>
+__global__ void k_set_history(int n, long cap, int levels, int np, const int *__restrict__ id,
+                              const double *__restrict__ ah, const double *__restrict__ vh, R *__restrict__ dah,
+                              R *__restrict__ dvh) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int p = id[i];
+    for (int l = 0; l < levels; l++)
+        for (int d = 0; d < 3; d++) {
+            dah[((size_t)l * 3 + d) * cap + i] = (R)ah[((size_t)l * np + p) * 3 + d];
+            dvh[((size_t)l * 3 + d) * cap + i] = (R)vh[((size_t)l * np + p) * 3 + d];
+        }
+}
+
+int check_status(Sim *s) {
+    const uint32_t st = s->hctl->status | s->host_status;
+    if (st & ST_WALK_CAP) {
+        set_error("a particle path crossed more tets than walk_cap in one step");
+        return PIC_ERR_WALK_CAP;
+    }
+    if (st & ST_OVERFLOW) {
+        set_error("the buffer of crossing-path records overflowed");
+        return PIC_ERR_OVERFLOW;
+    }
+    if (st & ST_CG_NO_CONV) {
+        set_error("the Newmark solve did not converge");
+        return PIC_ERR_CG_NO_CONVERGENCE;
+    }
+    if (st & ST_NAN) {
+        set_error("a particle state became NaN");
+        return PIC_ERR_NAN;
+    }
+    return PIC_OK;
+}
+
+int one_step(Sim *s, bool fields) {
+    int rc;
+    if ((rc = sort_particles(s))) return rc;
+    if ((rc = stage_coefficients(s, s->e.p, s->b.p))) return rc;
+    if ((rc = particle_push(s, 0))) return rc;
+    if ((rc = reduce_to_entities(s))) return rc;
+    if (!fields) return read_control(s);
+    if ((rc = newmark_rhs(s))) return rc;
+    if ((rc = pcg_newmark(s))) return rc;
+    if ((rc = gradient_completion(s))) return rc;
+    if ((rc = faraday_update(s))) return rc;
+    // rotate the three time levels
+    std::swap(s->e_prev, s->e);   // e_prev <- e^n
+    std::swap(s->e, s->x);        // e <- e^{n+1}, x <- e^{n-1} (overwritten next step)
+    std::swap(s->g_prev, s->g);
+    std::swap(s->g, s->g_new);
+    std::swap(s->b_prev, s->b);
+    std::swap(s->b, s->b_new);
+    if ((rc = compute_diagnostics(s))) return rc;
+    s->step++;
+    return read_control(s);
+}
+
+}  // namespace
+}  // namespace fp
+
+using namespace fp;
+
+extern "C" {
+
+const char *pic_last_error(void) { return g_err.c_str(); }
+
+int pic_mesh_create(const pic_mesh_desc *desc, pic_mesh **out) {
+    if (!out) {
+        set_error("pic_mesh_create: out is NULL");
+        return PIC_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    pic_mesh *h = new (std::nothrow) pic_mesh();
+    if (!h) {
+        set_error("pic_mesh_create: out of host memory");
+        return PIC_ERR_OOM;
+    }
+    int rc;
+    try {
+        rc = build_mesh(desc, &h->m);
+    } catch (const std::bad_alloc &) {
+        set_error("pic_mesh_create: out of host memory");
+        rc = PIC_ERR_OOM;
+    }
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return PIC_OK;
+}
+
+void pic_mesh_destroy(pic_mesh *mesh) { delete mesh; }
+
+int pic_mesh_info(const pic_mesh *mesh, int64_t *c) {
+    if (!mesh || !c) {
+        set_error("pic_mesh_info: NULL argument");
+        return PIC_ERR_INVALID_ARG;
+    }
+    const Mesh &m = mesh->m;
+    c[0] = m.n_nodes;
+    c[1] = m.n_edges;
+    c[2] = m.n_faces;
+    c[3] = m.n_tets;
+    c[4] = m.n_int_edges;
+    c[5] = m.n_int_nodes;
+    return PIC_OK;
+}
+
+int pic_mesh_entities(const pic_mesh *mesh, int32_t *edges, int32_t *faces) {
+    if (!mesh) {
+        set_error("pic_mesh_entities: NULL mesh");
+        return PIC_ERR_INVALID_ARG;
+    }
+    if (edges) std::memcpy(edges, mesh->m.h_edges.data(), sizeof(int) * mesh->m.h_edges.size());
+    if (faces) std::memcpy(faces, mesh->m.h_faces.data(), sizeof(int) * mesh->m.h_faces.size());
+    return PIC_OK;
+}
+
+int pic_mesh_incidence(const pic_mesh *mesh, int32_t which, int32_t *rows, int32_t *cols, int32_t *vals) {
+    if (!mesh || !rows || !cols || !vals || which < 0 || which > 2) {
+        set_error("pic_mesh_incidence: bad argument");
+        return PIC_ERR_INVALID_ARG;
+    }
+    return mesh_incidence_triplets(&mesh->m, which, rows, cols, vals);
+}
+
+void pic_config_default(pic_config *c) {
+    if (!c) return;
+    std::memset(c, 0, sizeof(*c));
+    c->form = PIC_FORM_WE;
+    c->pusher = PIC_PUSH_BORIS;
+    c->precision = PIC_PRECISION_PLAIN;
+    c->preconditioner = PIC_PRECOND_JACOBI;
+    c->cg_tol = 1e-10;
+    c->cg_max_iters = 10000;
+    c->init_tol = 1e-14;
+    c->walk_cap = 63;
+    c->cg_check_every = 16;
+    c->max_species = kMaxSpecies;
+}
+
+int pic_sim_create(const pic_mesh *mesh, const pic_config *cfg, pic_sim **out) {
+    if (!mesh || !cfg || !out) {
+        set_error("pic_sim_create: NULL argument");
+        return PIC_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (!(cfg->dt > 0) || (cfg->form != PIC_FORM_WE && cfg->form != PIC_FORM_MFEM) || cfg->pusher < 0 ||
+        cfg->pusher > 5 || (cfg->precision != PIC_PRECISION_PLAIN && cfg->precision != PIC_PRECISION_MIXED) ||
+        !(cfg->cg_tol > 0) || cfg->cg_max_iters <= 0 || !(cfg->init_tol > 0) || cfg->walk_cap <= 0 ||
+        cfg->walk_cap > kMaxWalk || cfg->preconditioner != PIC_PRECOND_JACOBI) {
+        set_error("pic_sim_create: invalid configuration (dt > 0, form WE/MFEM, pusher 0..5, precision, tolerances, "
+                  "walk_cap 1..63, Jacobi preconditioner)");
+        return PIC_ERR_INVALID_ARG;
+    }
+    {
+        int urc = mesh_upload(const_cast<Mesh *>(&mesh->m));
+        if (urc) return urc;
+    }
+    pic_sim *h = new (std::nothrow) pic_sim();
+    if (!h) {
+        set_error("pic_sim_create: out of host memory");
+        return PIC_ERR_OOM;
+    }
+    Sim *s = &h->s;
+    s->mesh = &mesh->m;
+    s->cfg = *cfg;
+    if (s->cfg.cg_check_every <= 0) s->cfg.cg_check_every = 16;
+    s->stream = (cudaStream_t)cfg->stream;
+    s->mixed = cfg->precision == PIC_PRECISION_MIXED;
+    s->rsize = s->mixed ? 4 : 8;
+    s->ab = cfg->pusher;
+    s->hist_levels = s->ab > 1 ? s->ab - 1 : 0;
+    int rc;
+    const Mesh *m = s->mesh;
+    Control *hc = nullptr;
+    if (cudaMallocHost((void **)&hc, sizeof(Control)) != cudaSuccess) {
+        delete h;
+        set_error("pic_sim_create: pinned allocation failed");
+        return PIC_ERR_OOM;
+    }
+    std::memset(hc, 0, sizeof(Control));
+    s->hctl = hc;
+    if ((rc = s->dctl.alloc(1)) || (rc = solver_alloc(s)) || (rc = s->coef.alloc(10 * (size_t)m->n_tets * s->rsize)) ||
+        (rc = s->tacc.alloc((size_t)kNV * m->n_tets)) || (rc = s->wacc.alloc(4 * (size_t)m->n_tets))) {
+        pic_sim_destroy(h);
+        return rc;
+    }
+    if (cudaMemset(s->dctl.p, 0, sizeof(Control)) != cudaSuccess) {
+        pic_sim_destroy(h);
+        return cuda_fail(cudaGetLastError(), "cudaMemset");
+    }
+    *out = h;
+    return PIC_OK;
+}
+
+void pic_sim_destroy(pic_sim *sim) {
+    if (!sim) return;
+    if (sim->s.stream) cudaStreamSynchronize(sim->s.stream);
+    else cudaDeviceSynchronize();
+    if (sim->s.hctl) cudaFreeHost(sim->s.hctl);
+    sim->s.hctl = nullptr;
+    delete sim;
+}
+
+int pic_particles_load(pic_sim *sim, int32_t species, double q, double mass, double w, int64_t n, const double *x,
+                       const double *v, const int32_t *tet_hint, int32_t on_device) {
+    if (!sim || n < 0 || (n > 0 && (!x || !v))) {
+        set_error("pic_particles_load: bad argument");
+        return PIC_ERR_INVALID_ARG;
+    }
+    Sim *s = &sim->s;
+    if (s->initialised) {
+        set_error("pic_particles_load: particles are loaded before pic_sim_init");
+        return PIC_ERR_STATE;
+    }
+    if (species < 0 || species >= kMaxSpecies || !(mass > 0) || !std::isfinite(q) || !std::isfinite(w)) {
+        set_error("pic_particles_load: species must be 0..3 with m > 0 and finite q, w");
+        return PIC_ERR_INVALID_ARG;
+    }
+    if ((int64_t)s->h_tet.size() + n >= (1LL << 30)) {
+        set_error("pic_particles_load: more than 2^30 particles");
+        return PIC_ERR_INVALID_ARG;
+    }
+    if (species < s->n_species) {
+        if (s->sp_q[species] != q || s->sp_m[species] != mass || s->sp_w[species] != w) {
+            set_error("pic_particles_load: species redefined with different q, m or w");
+            return PIC_ERR_INVALID_ARG;
+        }
+    } else {
+        if (species != s->n_species) {
+            set_error("pic_particles_load: species ids must be introduced in order 0, 1, ...");
+            return PIC_ERR_INVALID_ARG;
+        }
+        s->sp_q[species] = q;
+        s->sp_m[species] = mass;
+        s->sp_w[species] = w;
+        s->n_species++;
+    }
+    const size_t start = s->h_tet.size();
+    s->h_x.resize(3 * (start + n));
+    s->h_v.resize(3 * (start + n));
+    s->h_tet.resize(start + n);
+    s->h_species.resize(start + n, species);
+    if (n == 0) return PIC_OK;
+    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    FP_CUDA(cudaMemcpy(s->h_x.data() + 3 * start, x, sizeof(double) * 3 * n, kind));
+    FP_CUDA(cudaMemcpy(s->h_v.data() + 3 * start, v, sizeof(double) * 3 * n, kind));
+    if (tet_hint) {
+        FP_CUDA(cudaMemcpy(s->h_tet.data() + start, tet_hint, sizeof(int) * n, kind));
+    } else {
+        s->h_tet[start] = -2;   // marks "locate" for validate_particles
+    }
+    for (int64_t i = 0; i < 3 * n; i++)
+        if (!std::isfinite(s->h_x[3 * start + i]) || !std::isfinite(s->h_v[3 * start + i])) {
+            set_error("pic_particles_load: non-finite position or velocity");
+            s->h_x.resize(3 * start);
+            s->h_v.resize(3 * start);
+            s->h_tet.resize(start);
+            s->h_species.resize(start);
+            return PIC_ERR_INVALID_ARG;
+        }
+    int rc = validate_particles(s, (int)n, (int)start);
+    if (rc) {
+        s->h_x.resize(3 * start);
+        s->h_v.resize(3 * start);
+        s->h_tet.resize(start);
+        s->h_species.resize(start);
+    }
+    return rc;
+}
+
+int pic_sim_init(pic_sim *sim) {
+    if (!sim) {
+        set_error("pic_sim_init: NULL sim");
+        return PIC_ERR_INVALID_ARG;
+    }
+    Sim *s = &sim->s;
+    if (s->initialised) {
+        set_error("pic_sim_init: already initialised");
+        return PIC_ERR_STATE;
+    }
+    const Mesh *m = s->mesh;
+    int rc;
+    // static data: flux of the uniform B0 through every face and the background node charge
+    std::vector<double> b0(m->n_faces), bg(m->n_nodes, 0.0);
+    for (int f = 0; f < m->n_faces; f++) {
+        const double *xa = &m->h_xyz[3 * m->h_faces[3 * f]], *xb = &m->h_xyz[3 * m->h_faces[3 * f + 1]];
+        const double *xc = &m->h_xyz[3 * m->h_faces[3 * f + 2]];
+        double u[3], w[3];
+        for (int i = 0; i < 3; i++) {
+            u[i] = xb[i] - xa[i];
+            w[i] = xc[i] - xa[i];
+        }
+        const double a[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+        b0[f] = 0.5 * (s->cfg.b0[0] * a[0] + s->cfg.b0[1] * a[1] + s->cfg.b0[2] * a[2]);
+    }
+    for (int t = 0; t < m->n_tets; t++)
+        for (int k = 0; k < 4; k++) bg[m->h_tet_sorted[4 * (size_t)t + k]] += s->cfg.rho_background * m->h_vol[t] / 4.0;
+    FP_CUDA(cudaMemcpy(s->b.p, b0.data(), sizeof(double) * m->n_faces, cudaMemcpyHostToDevice));
+    FP_CUDA(cudaMemcpy(s->b_prev.p, b0.data(), sizeof(double) * m->n_faces, cudaMemcpyHostToDevice));
+    FP_CUDA(cudaMemcpy(s->rho_bg.p, bg.data(), sizeof(double) * m->n_nodes, cudaMemcpyHostToDevice));
+    if ((rc = upload_particles(s))) return rc;
+    // rho^0: charge-only pass over the sorted particles
+    if ((rc = sort_particles(s)) || (rc = stage_coefficients(s, s->e.p, s->b.p)) || (rc = particle_push(s, 1)) ||
+        (rc = reduce_to_entities(s)))
+        return rc;
+    FP_CUDA(cudaMemsetAsync(s->wall.p, 0, sizeof(double) * m->n_nodes, s->stream));
+    FP_CUDA(cudaMemsetAsync(s->wall_prev.p, 0, sizeof(double) * m->n_nodes, s->stream));
+    FP_CUDA(cudaMemcpyAsync(s->rho_prev.p, s->rho.p, sizeof(double) * m->n_nodes, cudaMemcpyDeviceToDevice, s->stream));
+    FP_CUDA(cudaMemsetAsync(s->dg.p, 0, sizeof(double) * m->n_edges, s->stream));
+    FP_CUDA(cudaMemsetAsync(s->g.p, 0, sizeof(double) * m->n_edges, s->stream));
+    FP_CUDA(cudaMemsetAsync(s->g_prev.p, 0, sizeof(double) * m->n_edges, s->stream));
+    FP_CUDA(cudaMemsetAsync(s->g_new.p, 0, sizeof(double) * m->n_edges, s->stream));
+    if ((rc = init_fields(s))) return rc;
+    FP_CUDA(cudaMemcpyAsync(s->x.p, s->e.p, sizeof(double) * m->n_edges, cudaMemcpyDeviceToDevice, s->stream));
+    FP_CUDA(cudaMemsetAsync(s->rhs.p, 0, sizeof(double) * m->n_edges, s->stream));
+    if ((rc = compute_diagnostics(s)) || (rc = read_control(s))) return rc;
+    s->initialised = 1;
+    s->nhist = 0;
+    return check_status(s);
+}
+
+int pic_set_ab_history(pic_sim *sim, int32_t levels, const double *a_hist, const double *v_hist) {
+    if (!sim || !a_hist || !v_hist) {
+        set_error("pic_set_ab_history: NULL argument");
+        return PIC_ERR_INVALID_ARG;
+    }
+    Sim *s = &sim->s;
+    if (!s->initialised || levels < 0 || levels > s->hist_levels) {
+        set_error("pic_set_ab_history: call after init with 0 <= levels <= order - 1");
+        return PIC_ERR_INVALID_ARG;
+    }
+    const int np = (int)s->h_tet.size();
+    DevBuf<double> da, dv;
+    int rc;
+    std::vector<double> ha(a_hist, a_hist + (size_t)levels * np * 3), hv(v_hist, v_hist + (size_t)levels * np * 3);
+    if ((rc = da.upload(ha)) || (rc = dv.upload(hv))) return rc;
+    PartBank &k = s->bank[s->cur];
+    const int n = s->n_total;
+    if (n > 0 && levels > 0) {
+        if (s->mixed)
+            k_set_history<float><<<(n + 255) / 256, 256, 0, s->stream>>>(n, (long)s->cap, levels, np, k.id.p, da.p,
+                                                                          dv.p, (float *)k.ah.p, (float *)k.vh.p);
+        else
+            k_set_history<double><<<(n + 255) / 256, 256, 0, s->stream>>>(n, (long)s->cap, levels, np, k.id.p, da.p,
+                                                                           dv.p, (double *)k.ah.p, (double *)k.vh.p);
+        FP_CUDA(cudaGetLastError());
+    }
+    FP_CUDA(cudaStreamSynchronize(s->stream));
+    s->nhist = levels;
+    return PIC_OK;
+}
+
+int pic_step(pic_sim *sim, int32_t nsteps) {
+    if (!sim || nsteps < 0) {
+        set_error("pic_step: bad argument");
+        return PIC_ERR_INVALID_ARG;
+    }
+    Sim *s = &sim->s;
+    if (!s->initialised) {
+        set_error("pic_step: call pic_sim_init first");
+        return PIC_ERR_STATE;
+    }
+    for (int k = 0; k < nsteps; k++) {
+        int rc = one_step(s, true);
+        if (rc) return rc;
+        if ((rc = check_status(s))) return rc;
+    }
+    return PIC_OK;
+}
+
+int pic_particle_phase(pic_sim *sim) {
+    if (!sim || !sim->s.initialised) {
+        set_error("pic_particle_phase: call pic_sim_init first");
+        return PIC_ERR_STATE;
+    }
+    int rc = one_step(&sim->s, false);
+    if (rc) return rc;
+    return check_status(&sim->s);
+}
+
+int pic_field_get(pic_sim *sim, int32_t which, double *out, int64_t n, int32_t on_device) {
+    if (!sim || !out) {
+        set_error("pic_field_get: NULL argument");
+        return PIC_ERR_INVALID_ARG;
+    }
+    Sim *s = &sim->s;
+    const Mesh *m = s->mesh;
+    const double *src = nullptr;
+    int64_t len = 0;
+    bool edge = false;
+    switch (which) {
+    case PIC_FIELD_E: src = s->e.p; len = m->n_edges; edge = true; break;
+    case PIC_FIELD_E_PREV: src = s->e_prev.p; len = m->n_edges; edge = true; break;
+    case PIC_FIELD_B: src = s->b.p; len = m->n_faces; break;
+    case PIC_FIELD_B_PREV: src = s->b_prev.p; len = m->n_faces; break;
+    case PIC_FIELD_G: src = s->g.p; len = m->n_edges; edge = true; break;
+    case PIC_FIELD_G_PREV: src = s->g_prev.p; len = m->n_edges; edge = true; break;
+    case PIC_FIELD_DG: src = s->dg.p; len = m->n_edges; edge = true; break;
+    case PIC_FIELD_RHO: src = s->rho.p; len = m->n_nodes; break;
+    case PIC_FIELD_WALL: src = s->wall.p; len = m->n_nodes; break;
+    case PIC_FIELD_RHO_BG: src = s->rho_bg.p; len = m->n_nodes; break;
+    case PIC_FIELD_PHI: src = s->phi.p; len = m->n_nodes; break;
+    default:
+        set_error("pic_field_get: unknown field");
+        return PIC_ERR_INVALID_ARG;
+    }
+    if (n != len) {
+        set_error("pic_field_get: n must equal the field length " + std::to_string(len));
+        return PIC_ERR_INVALID_ARG;
+    }
+    DevBuf<double> tmp;
+    const double *dev = src;
+    int rc;
+    if (edge) {
+        if (on_device) {
+            k_edges_to_canonical<<<(m->n_edges + 255) / 256, 256, 0, s->stream>>>(m->n_edges, m->edge_canon.p, src, out);
+            FP_CUDA(cudaGetLastError());
+            FP_CUDA(cudaStreamSynchronize(s->stream));
+            return PIC_OK;
+        }
+        if ((rc = tmp.alloc(len))) return rc;
+        k_edges_to_canonical<<<(m->n_edges + 255) / 256, 256, 0, s->stream>>>(m->n_edges, m->edge_canon.p, src, tmp.p);
+        FP_CUDA(cudaGetLastError());
+        dev = tmp.p;
+    }
+    FP_CUDA(cudaMemcpyAsync(out, dev, sizeof(double) * len, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            s->stream));
+    FP_CUDA(cudaStreamSynchronize(s->stream));
+    return PIC_OK;
+}
+
+int pic_field_set(pic_sim *sim, int32_t which, const double *in, int64_t n, int32_t on_device) {
+    if (!sim || !in) {
+        set_error("pic_field_set: NULL argument");
+        return PIC_ERR_INVALID_ARG;
+    }
+    Sim *s = &sim->s;
+    const Mesh *m = s->mesh;
+    double *dst = nullptr;
+    int64_t len = 0;
+    bool edge = false, zero_wall = false;
+    switch (which) {
+    case PIC_FIELD_E: dst = s->e.p; len = m->n_edges; edge = zero_wall = true; break;
+    case PIC_FIELD_E_PREV: dst = s->e_prev.p; len = m->n_edges; edge = zero_wall = true; break;
+    case PIC_FIELD_B: dst = s->b.p; len = m->n_faces; break;
+    case PIC_FIELD_B_PREV: dst = s->b_prev.p; len = m->n_faces; break;
+    case PIC_FIELD_G: dst = s->g.p; len = m->n_edges; edge = true; break;
+    case PIC_FIELD_G_PREV: dst = s->g_prev.p; len = m->n_edges; edge = true; break;
+    default:
+        set_error("pic_field_set: only E, E_PREV, B, B_PREV, G, G_PREV can be set");
+        return PIC_ERR_INVALID_ARG;
+    }
+    if (n != len) {
+        set_error("pic_field_set: n must equal the field length " + std::to_string(len));
+        return PIC_ERR_INVALID_ARG;
+    }
+    int rc;
+    DevBuf<double> tmp;
+    const double *dev = in;
+    if (!on_device || edge) {
+        if ((rc = tmp.alloc(len))) return rc;
+        FP_CUDA(cudaMemcpyAsync(tmp.p, in, sizeof(double) * len,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream));
+        dev = tmp.p;
+    }
+    if (edge) {
+        k_edges_from_canonical<<<(m->n_edges + 255) / 256, 256, 0, s->stream>>>(m->n_edges, m->n_int_edges, zero_wall,
+                                                                                m->edge_canon.p, dev, dst);
+        FP_CUDA(cudaGetLastError());
+    } else {
+        FP_CUDA(cudaMemcpyAsync(dst, dev, sizeof(double) * len, cudaMemcpyDeviceToDevice, s->stream));
+    }
+    FP_CUDA(cudaStreamSynchronize(s->stream));
+    return PIC_OK;
+}
+
+int pic_particles_count(pic_sim *sim, int64_t *n) {
+    if (!sim || !n) {
+        set_error("pic_particles_count: NULL argument");
+        return PIC_ERR_INVALID_ARG;
+    }
+    int rc = read_control(&sim->s);
+    if (rc) return rc;
+    *n = sim->s.hctl->n_alive;
+    return PIC_OK;
+}
+
+int pic_particles_get(pic_sim *sim, double *x, double *v, int32_t *tet, int32_t *id, int64_t cap, int64_t *n,
+                      int32_t on_device) {
+    if (!sim || !n) {
+        set_error("pic_particles_get: NULL argument");
+        return PIC_ERR_INVALID_ARG;
+    }
+    Sim *s = &sim->s;
+    int rc = read_control(s);
+    if (rc) return rc;
+    const int total = s->n_total;
+    const int live = s->hctl->n_alive;
+    *n = live;
+    if (cap < live) {
+        set_error("pic_particles_get: capacity smaller than the live count");
+        return PIC_ERR_INVALID_ARG;
+    }
+    PartBank &k = s->bank[s->cur];
+    std::vector<uint32_t> keys(total);
+    std::vector<int> ids(total);
+    std::vector<unsigned char> xs[3], vs[3];
+    if (total > 0) {
+        FP_CUDA(cudaMemcpy(keys.data(), k.key.p, sizeof(uint32_t) * total, cudaMemcpyDeviceToHost));
+        FP_CUDA(cudaMemcpy(ids.data(), k.id.p, sizeof(int) * total, cudaMemcpyDeviceToHost));
+        for (int d = 0; d < 3; d++) {
+            xs[d].resize(total * s->rsize);
+            vs[d].resize(total * s->rsize);
+            FP_CUDA(cudaMemcpy(xs[d].data(), k.x[d].p, total * s->rsize, cudaMemcpyDeviceToHost));
+            FP_CUDA(cudaMemcpy(vs[d].data(), k.v[d].p, total * s->rsize, cudaMemcpyDeviceToHost));
+        }
+    }
+    const uint32_t dead = (uint32_t)s->mesh->n_tets << 2;
+    std::vector<double> ox(3 * (size_t)live), ov(3 * (size_t)live);
+    std::vector<int> ot(live), oi(live);
+    int j = 0;
+    for (int i = 0; i < total && j < live; i++) {
+        if (keys[i] == dead) continue;
+        for (int d = 0; d < 3; d++) {
+            if (s->mixed) {
+                ox[3 * (size_t)j + d] = ((const float *)xs[d].data())[i];
+                ov[3 * (size_t)j + d] = ((const float *)vs[d].data())[i];
+            } else {
+                ox[3 * (size_t)j + d] = ((const double *)xs[d].data())[i];
+                ov[3 * (size_t)j + d] = ((const double *)vs[d].data())[i];
+            }
+        }
+        ot[j] = (int)(keys[i] >> 2);
+        oi[j] = ids[i];
+        j++;
+    }
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    if (live > 0) {
+        if (x) FP_CUDA(cudaMemcpy(x, ox.data(), sizeof(double) * 3 * live, kind));
+        if (v) FP_CUDA(cudaMemcpy(v, ov.data(), sizeof(double) * 3 * live, kind));
+        if (tet) FP_CUDA(cudaMemcpy(tet, ot.data(), sizeof(int) * live, kind));
+        if (id) FP_CUDA(cudaMemcpy(id, oi.data(), sizeof(int) * live, kind));
+    }
+    return PIC_OK;
+}
+
+int pic_diagnostics_get(pic_sim *sim, pic_diag *out) {
+    if (!sim || !out) {
+        set_error("pic_diagnostics_get: NULL argument");
+        return PIC_ERR_INVALID_ARG;
+    }
+    Sim *s = &sim->s;
+    int rc = read_control(s);
+    if (rc) return rc;
+    const Control &c = *s->hctl;
+    out->step = (double)s->step;
+    out->continuity_abs = c.diag.cont_abs;
+    out->gauss_abs = c.diag.gauss_abs;
+    out->rho_max = c.diag.rho_max;
+    out->divb_abs = c.diag.divb_abs;
+    out->cg_iters = s->step > 0 ? c.cg.iters : 0;
+    out->cg_relres = c.diag.relres;
+    out->n_alive = c.n_alive;
+    out->energy_e = c.diag.energy_e;
+    out->energy_b = c.diag.energy_b;
+    out->energy_k = c.diag.energy_k;
+    out->status = (double)(c.status | s->host_status);
+    return PIC_OK;
+}
+
+int pic_sim_synchronize(pic_sim *sim) {
+    if (!sim) {
+        set_error("pic_sim_synchronize: NULL sim");
+        return PIC_ERR_INVALID_ARG;
+    }
+    FP_CUDA(cudaStreamSynchronize(sim->s.stream));
+    return PIC_OK;
+}
+
+}  // extern "C"

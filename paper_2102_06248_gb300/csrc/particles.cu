@@ -1,0 +1,1099 @@
+// particles.cu -- the particle half of the step (Sec. III.B-C, Sec. III.A):
+//   sort particles by tet (stable LSD radix sort, deterministic),
+//   stage per-tet Whitney coefficients,
+//   fused gather -> push -> straight-path walk -> exact Whitney-1 deposit,
+//   deterministic reduction of the deposits to per-tet accumulators and then
+//   to edges (dGbar) and nodes (rho, wall charge).  No float atomics anywhere.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "sim.h"
+
+namespace fp {
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;   // keys per tile
+constexpr int kScanChunk = 4096;                       // entries per scan block (256 x 16)
+constexpr uint32_t kInvalid = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort, 8-bit digits, keys K (uint32 or uint64), uint32 payload.
+// Count n is read from the device (d_n) when given, else n_host.
+// ---------------------------------------------------------------------------
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const K *__restrict__ keys, const int *d_n, int n_host,
+                                                             int shift, uint32_t *__restrict__ hist, int tiles) {
+    __shared__ uint32_t cnt[256];
+    const int n = d_n ? min(*d_n, n_host) : n_host;
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    const long base = (long)blockIdx.x * kSortTile;
+    const long end = min((long)n, base + kSortTile);
+    for (long i = base + threadIdx.x; i < end; i += kSortThreads)
+        atomicAdd(&cnt[(unsigned)(keys[i] >> shift) & 255u], 1u);
+    __syncthreads();
+    hist[(size_t)threadIdx.x * tiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// exclusive scan, phase 1: chunk sums
+__global__ void __launch_bounds__(256) k_scan_reduce(const uint32_t *__restrict__ a, long len, uint32_t *chunk) {
+    __shared__ uint32_t red[256];
+    const long base = (long)blockIdx.x * kScanChunk;
+    uint32_t s = 0;
+    for (int k = 0; k < kScanChunk / 256; k++) {
+        long i = base + (long)k * 256 + threadIdx.x;
+        if (i < len) s += a[i];
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) chunk[blockIdx.x] = red[0];
+}
+
+// block-wide exclusive scan of 256 x 16 values held 16 per thread (in order)
+__device__ void block_scan16(uint32_t v[16], uint32_t carry_in, uint32_t *sh) {
+    uint32_t t = 0;
+    for (int k = 0; k < 16; k++) {
+        uint32_t x = v[k];
+        v[k] = t;
+        t += x;
+    }
+    sh[threadIdx.x] = t;
+    __syncthreads();
+    for (int o = 1; o < 256; o <<= 1) {
+        uint32_t y = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0;
+        __syncthreads();
+        sh[threadIdx.x] += y;
+        __syncthreads();
+    }
+    uint32_t excl = sh[threadIdx.x] - t + carry_in;
+    for (int k = 0; k < 16; k++) v[k] += excl;
+}
+
+// phase 2: single block scans the chunk sums (n_chunks <= 4096)
+__global__ void __launch_bounds__(256) k_scan_top(uint32_t *chunk, int n_chunks) {
+    __shared__ uint32_t sh[256];
+    uint32_t v[16];
+    for (int k = 0; k < 16; k++) {
+        int i = threadIdx.x * 16 + k;
+        v[k] = i < n_chunks ? chunk[i] : 0;
+    }
+    block_scan16(v, 0, sh);
+    for (int k = 0; k < 16; k++) {
+        int i = threadIdx.x * 16 + k;
+        if (i < n_chunks) chunk[i] = v[k];
+    }
+}
+
+// phase 3: scan each chunk with its offset (in place)
+__global__ void __launch_bounds__(256) k_scan_apply(uint32_t *a, long len, const uint32_t *chunk) {
+    __shared__ uint32_t sh[256];
+    const long base = (long)blockIdx.x * kScanChunk + threadIdx.x * 16;
+    uint32_t v[16];
+    for (int k = 0; k < 16; k++) v[k] = base + k < len ? a[base + k] : 0;
+    block_scan16(v, chunk[blockIdx.x], sh);
+    for (int k = 0; k < 16; k++)
+        if (base + k < len) a[base + k] = v[k];
+}
+
+// stable scatter: keys of a tile are ranked in index order per digit
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const K *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                                                K *__restrict__ kout, uint32_t *__restrict__ vout,
+                                                                const int *d_n, int n_host, int shift,
+                                                                const uint32_t *__restrict__ hist, int tiles) {
+    __shared__ uint32_t s_base[256], s_run[256];
+    __shared__ uint32_t s_wcnt[8][256];
+    __shared__ uint32_t s_woff[8][256];
+    const int n = d_n ? min(*d_n, n_host) : n_host;
+    const long base = (long)blockIdx.x * kSortTile;
+    if (base >= n) return;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    s_base[tid] = hist[(size_t)tid * tiles + blockIdx.x];
+    s_run[tid] = 0;
+    for (int w = 0; w < 8; w++) s_wcnt[w][tid] = 0;
+    __syncthreads();
+    for (int r = 0; r < kSortItems; r++) {
+        const long i = base + (long)r * kSortThreads + tid;
+        const bool valid = i < n;
+        K k = valid ? kin[i] : (K)0;
+        uint32_t v = valid ? (vin ? vin[i] : (uint32_t)i) : 0u;
+        const uint32_t d = valid ? ((unsigned)(k >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+        const uint32_t rank = __popc(peers & lanemask_lt());
+        if (valid && rank == 0) s_wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t acc = s_run[tid];
+            for (int w = 0; w < 8; w++) {
+                uint32_t c = s_wcnt[w][tid];
+                s_woff[w][tid] = acc;
+                acc += c;
+                s_wcnt[w][tid] = 0;
+            }
+            s_run[tid] = acc;
+        }
+        __syncthreads();
+        if (valid) {
+            const uint32_t pos = s_base[d] + s_woff[warp][d] + rank;
+            kout[pos] = k;
+            vout[pos] = v;
+        }
+        __syncthreads();
+    }
+    (void)lane;
+}
+
+int scan_exclusive(cudaStream_t st, uint32_t *a, long len, SortWork *w) {
+    long chunks = (len + kScanChunk - 1) / kScanChunk;
+    if (chunks > 4096) {
+        set_error("radix sort: too many tiles for the scan");
+        return PIC_ERR_INVALID_ARG;
+    }
+    k_scan_reduce<<<(unsigned)chunks, 256, 0, st>>>(a, len, w->chunk.p);
+    k_scan_top<<<1, 256, 0, st>>>(w->chunk.p, (int)chunks);
+    k_scan_apply<<<(unsigned)chunks, 256, 0, st>>>(a, len, w->chunk.p);
+    return PIC_OK;
+}
+
+int sortwork_reserve(SortWork *w, long n_cap) {
+    long tiles = std::max(1L, (n_cap + kSortTile - 1) / kSortTile);
+    if ((size_t)tiles <= w->tiles_cap) return PIC_OK;
+    int rc = w->hist.alloc(256 * (size_t)tiles);
+    if (rc) return rc;
+    rc = w->chunk.alloc(4096);
+    if (rc) return rc;
+    w->tiles_cap = tiles;
+    return PIC_OK;
+}
+
+// Sorts `bits` low bits of keys_in (identity payload) with ping-pong buffers;
+// returns where the sorted keys / payload ended up.
+template <typename K>
+int radix_sort(cudaStream_t st, const K *keys_in, K *ka, uint32_t *va, K *kb, uint32_t *vb, const int *d_n,
+               long n_cap, int bits, SortWork *w, K **out_k, uint32_t **out_v) {
+    int rc = sortwork_reserve(w, n_cap);
+    if (rc) return rc;
+    const int tiles = (int)std::max(1L, (n_cap + kSortTile - 1) / kSortTile);
+    const int passes = std::max(1, (bits + 7) / 8);
+    const K *src_k = keys_in;
+    const uint32_t *src_v = nullptr;
+    K *dk = ka;
+    uint32_t *dv = va;
+    for (int p = 0; p < passes; p++) {
+        k_radix_hist<K><<<tiles, kSortThreads, 0, st>>>(src_k, d_n, (int)n_cap, 8 * p, w->hist.p, tiles);
+        rc = scan_exclusive(st, w->hist.p, 256L * tiles, w);
+        if (rc) return rc;
+        k_radix_scatter<K><<<tiles, kSortThreads, 0, st>>>(src_k, src_v, dk, dv, d_n, (int)n_cap, 8 * p, w->hist.p,
+                                                          tiles);
+        src_k = dk;
+        src_v = dv;
+        if (dk == ka) {
+            dk = kb;
+            dv = vb;
+        } else {
+            dk = ka;
+            dv = va;
+        }
+    }
+    *out_k = const_cast<K *>(src_k);
+    *out_v = const_cast<uint32_t *>(src_v);
+    return PIC_OK;
+}
+
+int bitlen(unsigned long long x) {
+    int b = 0;
+    while (x) {
+        b++;
+        x >>= 1;
+    }
+    return b;
+}
+
+// ---------------------------------------------------------------------------
+// per-tet field coefficients (Sec. II.A): inside tet t, with d = r - x0,
+//   E(r) = E0 + Omega x d,   Omega = sum_{edges (i,j)} e_ij grad lam_i x grad lam_j,
+//   B(r) = B0 + beta d,      from W2_k = D_k (r - x_k) / (3V),
+// where E0 = e_01 g1 + e_02 g2 + e_03 g3, B0 = sum_k D_k b_k (x0 - x_k) / (3V)
+// and beta = (D b)_t / (3V) (zero up to rounding).
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) k_coefficients(int nt, const double *__restrict__ geo, const int *__restrict__ tet_edge,
+                                                      const int4 *__restrict__ tet_face, const int4 *__restrict__ tet_nodes,
+                                                      const signed char *__restrict__ tet_sign, const double *__restrict__ vol,
+                                                      const double *__restrict__ xyz, const double *__restrict__ e,
+                                                      const double *__restrict__ b, R *__restrict__ coef) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const double *gp = geo + 12 * (size_t)t;
+    double g[4][3];
+    for (int i = 0; i < 3; i++) {
+        g[1][i] = gp[3 + i];
+        g[2][i] = gp[6 + i];
+        g[3][i] = gp[9 + i];
+        g[0][i] = -(g[1][i] + g[2][i] + g[3][i]);
+    }
+    const int *te = tet_edge + 6 * (size_t)t;
+    double ev[6];
+    for (int k = 0; k < 6; k++) ev[k] = e[te[k]];
+    const int LI[6] = {0, 0, 0, 1, 1, 2}, LJ[6] = {1, 2, 3, 2, 3, 3};
+    double E0[3], Om[3] = {0, 0, 0};
+    for (int i = 0; i < 3; i++) E0[i] = ev[0] * g[1][i] + ev[1] * g[2][i] + ev[2] * g[3][i];
+    for (int k = 0; k < 6; k++) {
+        const double *a = g[LI[k]], *c = g[LJ[k]];
+        Om[0] += ev[k] * (a[1] * c[2] - a[2] * c[1]);
+        Om[1] += ev[k] * (a[2] * c[0] - a[0] * c[2]);
+        Om[2] += ev[k] * (a[0] * c[1] - a[1] * c[0]);
+    }
+    const int4 tf = tet_face[t], tn = tet_nodes[t];
+    const double bv[4] = {b[tf.x], b[tf.y], b[tf.z], b[tf.w]};
+    const int nid[4] = {tn.x, tn.y, tn.z, tn.w};
+    const double s = tet_sign[t];
+    const double inv3v = 1.0 / (3.0 * vol[t]);
+    double B0[3] = {0, 0, 0}, divb = 0.0;
+    for (int k = 0; k < 4; k++) {
+        const double Dk = (k & 1) ? -s : s;
+        divb += Dk * bv[k];
+        if (k == 0) continue;
+        for (int i = 0; i < 3; i++) B0[i] += Dk * bv[k] * (gp[i] - xyz[3 * (size_t)nid[k] + i]);
+    }
+    R *c = coef + 10 * (size_t)t;
+    for (int i = 0; i < 3; i++) {
+        c[i] = (R)E0[i];
+        c[3 + i] = (R)Om[i];
+        c[6 + i] = (R)(B0[i] * inv3v);
+    }
+    c[9] = (R)(divb * inv3v);
+}
+
+// ---------------------------------------------------------------------------
+// fused gather -> push -> walk -> deposit
+// ---------------------------------------------------------------------------
+template <typename R>
+struct PushArgs {
+    const int *d_n_alive;
+    const uint32_t *skey;
+    const uint32_t *perm;
+    const R *sx0, *sx1, *sx2, *sv0, *sv1, *sv2;
+    const int *sid;
+    const R *sah, *svh;
+    R *dx0, *dx1, *dx2, *dv0, *dv1, *dv2;
+    uint32_t *dkey;
+    int *did;
+    R *dah, *dvh;
+    long cap;
+    const double *geo;
+    const R *coef;
+    const int4 *tnodes;
+    const int4 *tnbr;
+    SpeciesParams sp;
+    double dt;
+    int ab_order, hist_levels;
+    double abw[5];
+    int walk_cap;
+    uint32_t dead_key;
+    double *tacc, *wacc;
+    double *bcar;
+    uint32_t *bcar_key;
+    unsigned long long *okey;
+    double *oval;
+    int *ocount;
+    int ocap;
+    int oshift;
+    uint32_t *status;
+    int *n_alive_next;
+    double *ke_part;
+};
+
+// barycentrics of point r in tet (affine map: lam_k = g_k . (r - x0), k=1..3)
+__device__ __forceinline__ void bary(const double *__restrict__ gp, double rx, double ry, double rz, double lam[4]) {
+    const double dx = rx - gp[0], dy = ry - gp[1], dz = rz - gp[2];
+    lam[1] = gp[3] * dx + gp[4] * dy + gp[5] * dz;
+    lam[2] = gp[6] * dx + gp[7] * dy + gp[8] * dz;
+    lam[3] = gp[9] * dx + gp[10] * dy + gp[11] * dz;
+    lam[0] = 1.0 - lam[1] - lam[2] - lam[3];
+}
+
+__device__ __forceinline__ void load_geo(const double *__restrict__ geo, int t, double gp[12]) {
+    const double2 *g2 = reinterpret_cast<const double2 *>(geo + 12 * (size_t)t);
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        double2 v = __ldg(g2 + k);
+        gp[2 * k] = v.x;
+        gp[2 * k + 1] = v.y;
+    }
+}
+
+// exact line integral of the six Whitney-1 functions along a straight piece
+// from barycentrics lS to lE: lam_i(S) lam_j(E) - lam_i(E) lam_j(S)
+__device__ __forceinline__ void segment_current(const double lS[4], const double lE[4], double qw, double out[6]) {
+    out[0] = qw * (lS[0] * lE[1] - lE[0] * lS[1]);
+    out[1] = qw * (lS[0] * lE[2] - lE[0] * lS[2]);
+    out[2] = qw * (lS[0] * lE[3] - lE[0] * lS[3]);
+    out[3] = qw * (lS[1] * lE[2] - lE[1] * lS[2]);
+    out[4] = qw * (lS[1] * lE[3] - lE[1] * lS[3]);
+    out[5] = qw * (lS[2] * lE[3] - lE[2] * lS[3]);
+}
+
+template <typename R>
+__device__ void push_record(const PushArgs<R> &a, int tet, int wall, long pidx, int seg, const double v[kNV]) {
+    const int slot = atomicAdd(a.ocount, 1);
+    if (slot >= a.ocap) {
+        atomicOr(a.status, (uint32_t)ST_OVERFLOW);
+        return;
+    }
+    const unsigned long long tw = ((unsigned long long)tet << 1) | (unsigned long long)wall;
+    a.okey[slot] = (tw << a.oshift) | ((unsigned long long)pidx << 6) | (unsigned long long)seg;
+    double *o = a.oval + (size_t)slot * kNV;
+#pragma unroll
+    for (int c = 0; c < kNV; c++) o[c] = v[c];
+}
+
+template <typename R, int MODE>   // MODE 0: Boris, 1: Adams-Bashforth, 2: charge only
+__global__ void __launch_bounds__(kPushBlock) k_push(const PushArgs<R> a) {
+    __shared__ uint32_t s_key[kPushBlock / 32][2];
+    __shared__ double s_val[kPushBlock / 32][2][kNV];
+    __shared__ double s_ke[kPushBlock / 32];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long i = (long)blockIdx.x * kPushBlock + tid;
+    const int n_alive = *a.d_n_alive;
+    const bool active = i < n_alive;
+    uint32_t rkey = kInvalid;     // reduction key: start tet
+    double vals[kNV];
+#pragma unroll
+    for (int c = 0; c < kNV; c++) vals[c] = 0.0;
+    double ke = 0.0;
+    int alive_out = 0;
+
+    if (active) {
+        const uint32_t key = a.skey[i];
+        const int tet = (int)(key >> 2), spc = (int)(key & 3u);
+        const long src = a.perm[i];
+        R P[3] = {a.sx0[src], a.sx1[src], a.sx2[src]};
+        R V[3] = {a.sv0[src], a.sv1[src], a.sv2[src]};
+        double gp[12];
+        load_geo(a.geo, tet, gp);
+        // ---- gather (Sec. II.A): E = E0 + Omega x d, B = B0 + beta d ----
+        const R *cf = a.coef + 10 * (size_t)tet;
+        R c[10];
+#pragma unroll
+        for (int k = 0; k < 10; k++) c[k] = cf[k];
+        const R d0 = (R)((double)P[0] - gp[0]), d1 = (R)((double)P[1] - gp[1]), d2 = (R)((double)P[2] - gp[2]);
+        const R E[3] = {c[0] + c[4] * d2 - c[5] * d1, c[1] + c[5] * d0 - c[3] * d2, c[2] + c[3] * d1 - c[4] * d0};
+        const R B[3] = {c[6] + c[9] * d0, c[7] + c[9] * d1, c[8] + c[9] * d2};
+        const R qm = (R)a.sp.qm[spc];
+        const R dt = (R)a.dt;
+        R Q[3], Vn[3];
+        if (MODE == 0) {
+            // ---- Boris: half kick, rotation about B, half kick (Sec. III.B) ----
+            const R h = (R)0.5 * qm * dt;
+            R vm[3], tv[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                vm[k] = V[k] + h * E[k];
+                tv[k] = h * B[k];
+            }
+            const R t2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
+            const R f = (R)2 / ((R)1 + t2);
+            const R vp[3] = {vm[0] + (vm[1] * tv[2] - vm[2] * tv[1]), vm[1] + (vm[2] * tv[0] - vm[0] * tv[2]),
+                             vm[2] + (vm[0] * tv[1] - vm[1] * tv[0])};
+            const R sv[3] = {f * tv[0], f * tv[1], f * tv[2]};
+            Vn[0] = vm[0] + (vp[1] * sv[2] - vp[2] * sv[1]) + h * E[0];
+            Vn[1] = vm[1] + (vp[2] * sv[0] - vp[0] * sv[2]) + h * E[1];
+            Vn[2] = vm[2] + (vp[0] * sv[1] - vp[1] * sv[0]) + h * E[2];
+#pragma unroll
+            for (int k = 0; k < 3; k++) Q[k] = P[k] + dt * Vn[k];
+        } else if (MODE == 1) {
+            // ---- Adams-Bashforth (Eq. adam-bashforth): a^n = q/m (E + v^n x B) ----
+            const R acc[3] = {qm * (E[0] + (V[1] * B[2] - V[2] * B[1])), qm * (E[1] + (V[2] * B[0] - V[0] * B[2])),
+                              qm * (E[2] + (V[0] * B[1] - V[1] * B[0]))};
+            R sa[3], svv[3];
+            const R w0 = (R)a.abw[0];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                sa[k] = w0 * acc[k];
+                svv[k] = w0 * V[k];
+            }
+            for (int j = 1; j < a.ab_order; j++) {
+                const R wj = (R)a.abw[j];
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    sa[k] += wj * a.sah[((size_t)(j - 1) * 3 + k) * a.cap + src];
+                    svv[k] += wj * a.svh[((size_t)(j - 1) * 3 + k) * a.cap + src];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                Vn[k] = V[k] + dt * sa[k];
+                Q[k] = P[k] + dt * svv[k];
+            }
+            // shift the history: level 0 <- current, level j <- level j-1
+            for (int j = a.hist_levels - 1; j >= 1; j--)
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    a.dah[((size_t)j * 3 + k) * a.cap + i] = a.sah[((size_t)(j - 1) * 3 + k) * a.cap + src];
+                    a.dvh[((size_t)j * 3 + k) * a.cap + i] = a.svh[((size_t)(j - 1) * 3 + k) * a.cap + src];
+                }
+            if (a.hist_levels > 0)
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    a.dah[(size_t)k * a.cap + i] = acc[k];
+                    a.dvh[(size_t)k * a.cap + i] = V[k];
+                }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                Q[k] = P[k];
+                Vn[k] = V[k];
+            }
+        }
+        // ---- walk the straight path P -> Q (Algorithm 1) with exact deposit ----
+        const double qw = a.sp.qw[spc];
+        const double Qd[3] = {(double)Q[0], (double)Q[1], (double)Q[2]};
+        double lS[4], lE[4];
+        bary(gp, (double)P[0], (double)P[1], (double)P[2], lS);
+        int T = tet;
+        int4 tn = a.tnodes[T];
+        int entry = -1;
+        int seg = 0;
+        bool done = false, absorbed = false;
+        int endT = tet;
+        for (; seg < a.walk_cap; seg++) {
+            if (seg > 0) load_geo(a.geo, T, gp);
+            bary(gp, Qd[0], Qd[1], Qd[2], lE);
+            int kmin = -1;
+            double smin = 2.0;
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (k == entry || !(lE[k] < 0.0)) continue;
+                double s = lS[k] / (lS[k] - lE[k]);
+                s = s < 0.0 ? 0.0 : s;
+                if (s < smin) {
+                    smin = s;
+                    kmin = k;
+                }
+            }
+            double rec[kNV];
+            if (kmin < 0) {
+                // path ends in T: current of the last piece + charge at the end point
+                segment_current(lS, lE, qw, rec);
+#pragma unroll
+                for (int k = 0; k < 4; k++) rec[6 + k] = qw * lE[k];
+                if (seg == 0) {
+#pragma unroll
+                    for (int c = 0; c < kNV; c++) vals[c] = rec[c];
+                } else {
+                    push_record(a, T, 0, i, seg, rec);
+                }
+                endT = T;
+                done = true;
+                break;
+            }
+            double lX[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) lX[k] = lS[k] + smin * (lE[k] - lS[k]);
+            lX[kmin] = 0.0;
+            segment_current(lS, lX, qw, rec);
+#pragma unroll
+            for (int k = 0; k < 4; k++) rec[6 + k] = 0.0;
+            if (seg == 0) {
+#pragma unroll
+                for (int c = 0; c < kNV; c++) vals[c] = rec[c];
+            } else {
+                push_record(a, T, 0, i, seg, rec);
+            }
+            const int nb = (&a.tnbr[T].x)[kmin];
+            if (nb < 0) {
+                // absorbed by the wall at the exit point: its charge stays there
+                double wrec[kNV];
+#pragma unroll
+                for (int k = 0; k < 6; k++) wrec[k] = 0.0;
+#pragma unroll
+                for (int k = 0; k < 4; k++) wrec[6 + k] = qw * lX[k];
+                push_record(a, T, 1, i, kMaxWalk, wrec);
+                absorbed = true;
+                done = true;
+                break;
+            }
+            // carry the three shared barycentrics into the neighbour exactly
+            const int4 nn = a.tnodes[nb];
+            const int tv[4] = {tn.x, tn.y, tn.z, tn.w};
+            const int nv[4] = {nn.x, nn.y, nn.z, nn.w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                double l = 0.0;
+                bool shared = false;
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if (nv[j] == tv[k]) {
+                        l = lX[k];
+                        shared = true;
+                    }
+                lS[j] = l;
+                if (!shared) entry = j;
+            }
+            T = nb;
+            tn = nn;
+        }
+        if (!done) {
+            atomicOr(a.status, (uint32_t)ST_WALK_CAP);
+            absorbed = true;   // the particle is dropped; the step reports the error
+        }
+        // ---- write the particle back in sorted order ----
+        a.dx0[i] = Q[0];
+        a.dx1[i] = Q[1];
+        a.dx2[i] = Q[2];
+        a.dv0[i] = Vn[0];
+        a.dv1[i] = Vn[1];
+        a.dv2[i] = Vn[2];
+        a.did[i] = a.sid[src];
+        a.dkey[i] = absorbed ? a.dead_key : (((uint32_t)endT << 2) | (uint32_t)spc);
+        if (!absorbed) {
+            alive_out = 1;
+            ke = 0.5 * a.sp.mw[spc] * ((double)Vn[0] * Vn[0] + (double)Vn[1] * Vn[1] + (double)Vn[2] * Vn[2]);
+            if (!(ke == ke) || !(Qd[0] == Qd[0])) atomicOr(a.status, (uint32_t)ST_NAN);
+        }
+        rkey = (uint32_t)tet;
+    }
+
+    // ---- live count and kinetic energy (block partial, fixed order) ----
+    {
+        const unsigned ball = __ballot_sync(0xFFFFFFFFu, alive_out);
+        if (lane == 0 && ball) atomicAdd(a.n_alive_next, __popc(ball));
+        double k2 = ke;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) k2 += __shfl_down_sync(0xFFFFFFFFu, k2, o);
+        if (lane == 0) s_ke[warp] = k2;
+    }
+
+    // ---- warp-segmented inclusive scan of the first-piece deposits by start tet ----
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t ko = __shfl_up_sync(0xFFFFFFFFu, rkey, off);
+#pragma unroll
+        for (int c = 0; c < kNV; c++) {
+            const double vo = __shfl_up_sync(0xFFFFFFFFu, vals[c], off);
+            if (lane >= off && ko == rkey) vals[c] += vo;
+        }
+    }
+    const uint32_t knext = __shfl_down_sync(0xFFFFFFFFu, rkey, 1);
+    const bool tail = (lane == 31) || (knext != rkey);
+    const uint32_t kfirst = __shfl_sync(0xFFFFFFFFu, rkey, 0);
+    if (lane == 0) {
+        s_key[warp][0] = kInvalid;
+        s_key[warp][1] = kInvalid;
+    }
+    __syncwarp();
+    if (tail && rkey != kInvalid) {
+        const bool first = (rkey == kfirst);
+        const bool last = (lane == 31);
+        if (!first && !last) {
+            // a run that starts and ends inside this warp: sole writer
+            double *dst = a.tacc + (size_t)rkey * kNV;
+#pragma unroll
+            for (int c = 0; c < kNV; c++) dst[c] = vals[c];
+        } else {
+            const int slot = first ? 0 : 1;
+            s_key[warp][slot] = rkey;
+#pragma unroll
+            for (int c = 0; c < kNV; c++) s_val[warp][slot][c] = vals[c];
+        }
+    }
+    __syncthreads();
+
+    // ---- block level: merge the warp boundary pieces in warp order ----
+    if (tid == 0) {
+        double kes = 0.0;
+        for (int w = 0; w < kPushBlock / 32; w++) kes += s_ke[w];
+        a.ke_part[blockIdx.x] = kes;
+    }
+    const long blk0 = (long)blockIdx.x * kPushBlock;
+    if (tid < kNV || tid == 32) {
+        // thread c < kNV handles value c; thread 32 writes the keys
+        const int c = tid < kNV ? tid : 0;
+        const bool writer_keys = (tid == 32);
+        const uint32_t prevk = (blk0 > 0 && blk0 - 1 < n_alive) ? (a.skey[blk0 - 1] >> 2) : kInvalid;
+        const long blk_end = min(blk0 + kPushBlock, (long)n_alive);
+        const uint32_t nextk = (blk_end < n_alive) ? (a.skey[blk_end] >> 2) : kInvalid;
+        uint32_t run_key = kInvalid;
+        double run_val = 0.0;
+        bool run_is_first = true;
+        int n_runs = 0;
+        uint32_t out_key[2] = {kInvalid, kInvalid};
+        double out_val[2] = {0.0, 0.0};
+        // flush a finished run: complete -> direct store, partial -> block carry slot
+        auto flush = [&](bool is_last_run) {
+            if (run_key == kInvalid) return;
+            const bool touches_prev = run_is_first && prevk == run_key;
+            const bool touches_next = is_last_run && nextk == run_key;
+            if (touches_prev || touches_next) {
+                const int slot = (run_is_first) ? 0 : 1;
+                out_key[slot] = run_key;
+                out_val[slot] = run_val;
+            } else if (!writer_keys) {
+                a.tacc[(size_t)run_key * kNV + c] = run_val;
+            }
+        };
+        for (int w = 0; w < kPushBlock / 32; w++)
+            for (int sl = 0; sl < 2; sl++) {
+                const uint32_t k = s_key[w][sl];
+                if (k == kInvalid) continue;
+                const double v = s_val[w][sl][c];
+                if (k == run_key) {
+                    run_val += v;
+                } else {
+                    if (run_key != kInvalid) {
+                        flush(false);
+                        run_is_first = false;
+                    }
+                    run_key = k;
+                    run_val = v;
+                    n_runs++;
+                }
+            }
+        flush(true);
+        if (writer_keys) {
+            a.bcar_key[2 * blockIdx.x] = out_key[0];
+            a.bcar_key[2 * blockIdx.x + 1] = out_key[1];
+        } else {
+            a.bcar[(2 * (size_t)blockIdx.x) * kNV + c] = out_val[0];
+            a.bcar[(2 * (size_t)blockIdx.x + 1) * kNV + c] = out_val[1];
+        }
+        (void)n_runs;
+    }
+}
+
+// spanning runs: a head piece (the last run of a block, or a block's first run
+// that does not continue from the previous block) adds the following blocks'
+// first-run pieces of the same tet in block order
+__global__ void __launch_bounds__(256) k_fixup(int n_blocks, const uint32_t *__restrict__ skey, const int *d_n_alive,
+                                               const uint32_t *__restrict__ bkey, const double *__restrict__ bval,
+                                               double *__restrict__ tacc) {
+    const long j = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= 2L * n_blocks) return;
+    const uint32_t k = bkey[j];
+    if (k == kInvalid) return;
+    const long blk = j >> 1;
+    const int slot = (int)(j & 1);
+    if (slot == 0) {
+        const long p = blk * kPushBlock - 1;
+        const int n_alive = *d_n_alive;
+        if (blk > 0 && p < n_alive && (skey[p] >> 2) == k) return;   // continues a run from before
+    }
+    double sum[kNV];
+    for (int c = 0; c < kNV; c++) sum[c] = bval[j * kNV + c];
+    for (long b = blk + 1; b < n_blocks && bkey[2 * b] == k; b++)
+        for (int c = 0; c < kNV; c++) sum[c] += bval[2 * b * kNV + c];
+    for (int c = 0; c < kNV; c++) tacc[(size_t)k * kNV + c] = sum[c];
+}
+
+// overflow records (later pieces of crossing paths, wall hits), sorted by
+// (tet, wall, particle, piece): each (tet, wall) run is summed in that order
+__global__ void __launch_bounds__(256) k_overflow_reduce(const int *d_count, int cap, const unsigned long long *__restrict__ okey,
+                                                         const uint32_t *__restrict__ oidx, const double *__restrict__ oval,
+                                                         int oshift, double *__restrict__ tacc, double *__restrict__ wacc) {
+    const int n = min(*d_count, cap);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const unsigned long long tw = okey[j] >> oshift;
+    if (j > 0 && (okey[j - 1] >> oshift) == tw) return;
+    double sum[kNV];
+    for (int c = 0; c < kNV; c++) sum[c] = 0.0;
+    for (int r = j; r < n && (okey[r] >> oshift) == tw; r++) {
+        const double *v = oval + (size_t)oidx[r] * kNV;
+        for (int c = 0; c < kNV; c++) sum[c] += v[c];
+    }
+    const long tet = (long)(tw >> 1);
+    if (tw & 1ull) {
+        for (int c = 0; c < 4; c++) wacc[tet * 4 + c] += sum[6 + c];
+    } else {
+        for (int c = 0; c < kNV; c++) tacc[tet * kNV + c] += sum[c];
+    }
+}
+
+// per-tet accumulators -> edges and nodes, in the fixed order of the maps
+__global__ void __launch_bounds__(256) k_gather_edges(int ne, const int *__restrict__ ptr, const int *__restrict__ idx,
+                                                      const double *__restrict__ tacc, const double *__restrict__ g,
+                                                      double *__restrict__ dg, double *__restrict__ g_new) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    double s = 0.0;
+    for (int k = ptr[e]; k < ptr[e + 1]; k++) {
+        const int ref = idx[k];
+        s += tacc[(size_t)(ref / 6) * kNV + ref % 6];
+    }
+    dg[e] = s;
+    g_new[e] = g[e] + s;
+}
+
+__global__ void __launch_bounds__(256) k_gather_nodes(int nn, const int *__restrict__ ptr, const int *__restrict__ idx,
+                                                      const double *__restrict__ tacc, const double *__restrict__ wacc,
+                                                      const double *__restrict__ wall_old, double *__restrict__ rho,
+                                                      double *__restrict__ wall) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    double r = 0.0, w = 0.0;
+    for (int k = ptr[n]; k < ptr[n + 1]; k++) {
+        const int ref = idx[k];
+        r += tacc[(size_t)(ref / 4) * kNV + 6 + ref % 4];
+        w += wacc[(size_t)(ref / 4) * 4 + ref % 4];
+    }
+    rho[n] = r;
+    wall[n] = wall_old[n] + w;
+}
+
+// load-time check (and location): every particle inside its tet.  Without a
+// hint the particle is located by a straight walk in physical space from the
+// centroid of tet 0 (exits through a wall mean the point is outside the mesh).
+__global__ void k_validate(int n, int start, const double *__restrict__ x, const int *__restrict__ tet, int nt,
+                           const double *__restrict__ geo, const int4 *__restrict__ tnbr, const int4 *__restrict__ tnodes,
+                           const double *__restrict__ xyz, int *__restrict__ tet_out, int *bad) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const double Q[3] = {x[3 * (size_t)p], x[3 * (size_t)p + 1], x[3 * (size_t)p + 2]};
+    int t = tet ? tet[p] : 0;
+    if (t < 0 || t >= nt) {
+        atomicAdd(bad, 1);
+        tet_out[start + p] = -1;
+        return;
+    }
+    double gp[12], lq[4];
+    load_geo(geo, t, gp);
+    if (!tet) {
+        const int4 tn = tnodes[t];
+        const int ids[4] = {tn.x, tn.y, tn.z, tn.w};
+        double S[3] = {0, 0, 0};
+        for (int k = 0; k < 4; k++)
+            for (int d = 0; d < 3; d++) S[d] += 0.25 * xyz[3 * (size_t)ids[k] + d];
+        int entry = -1;
+        for (int it = 0; it < (1 << 22); it++) {
+            double ls[4];
+            bary(gp, S[0], S[1], S[2], ls);
+            bary(gp, Q[0], Q[1], Q[2], lq);
+            int kmin = -1;
+            double smin = 2.0;
+            for (int k = 0; k < 4; k++) {
+                if (k == entry || !(lq[k] < 0.0)) continue;
+                double sk = ls[k] / (ls[k] - lq[k]);
+                sk = sk < 0.0 ? 0.0 : sk;
+                if (sk < smin) {
+                    smin = sk;
+                    kmin = k;
+                }
+            }
+            if (kmin < 0) break;
+            const int nb = (&tnbr[t].x)[kmin];
+            if (nb < 0) {
+                atomicAdd(bad, 1);
+                tet_out[start + p] = -1;
+                return;
+            }
+            for (int d = 0; d < 3; d++) S[d] = S[d] + smin * (Q[d] - S[d]);
+            // entry face of nb: the one shared with t
+            for (int k = 0; k < 4; k++)
+                if ((&tnbr[nb].x)[k] == t) entry = k;
+            t = nb;
+            load_geo(geo, t, gp);
+        }
+    }
+    bary(gp, Q[0], Q[1], Q[2], lq);
+    if (lq[0] < -1e-10 || lq[1] < -1e-10 || lq[2] < -1e-10 || lq[3] < -1e-10) {
+        atomicAdd(bad, 1);
+        tet_out[start + p] = -1;
+        return;
+    }
+    tet_out[start + p] = t;
+}
+
+template <typename R>
+__global__ void k_load_particles(int n, int start, const double *__restrict__ x, const double *__restrict__ v,
+                                 const int *__restrict__ tet, int species, int id0, R *x0, R *x1, R *x2, R *v0, R *v1,
+                                 R *v2, uint32_t *key, int *id) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const long q = start + p;
+    x0[q] = (R)x[3 * (size_t)p];
+    x1[q] = (R)x[3 * (size_t)p + 1];
+    x2[q] = (R)x[3 * (size_t)p + 2];
+    v0[q] = (R)v[3 * (size_t)p];
+    v1[q] = (R)v[3 * (size_t)p + 1];
+    v2[q] = (R)v[3 * (size_t)p + 2];
+    key[q] = ((uint32_t)tet[start + p] << 2) | (uint32_t)species;
+    id[q] = id0 + p;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+int particles_alloc(Sim *s, size_t cap) {
+    int rc;
+    const size_t rs = s->rsize;
+    for (int b = 0; b < 2; b++) {
+        PartBank &k = s->bank[b];
+        for (int d = 0; d < 3; d++) {
+            if ((rc = k.x[d].alloc(cap * rs)) || (rc = k.v[d].alloc(cap * rs))) return rc;
+        }
+        if ((rc = k.key.alloc(cap)) || (rc = k.id.alloc(cap))) return rc;
+        if (s->hist_levels > 0) {
+            if ((rc = k.ah.alloc(cap * rs * 3 * s->hist_levels)) || (rc = k.vh.alloc(cap * rs * 3 * s->hist_levels)))
+                return rc;
+        }
+    }
+    if ((rc = s->skey.alloc(cap)) || (rc = s->sval.alloc(cap)) || (rc = s->tkey.alloc(cap)) ||
+        (rc = s->tval.alloc(cap)))
+        return rc;
+    s->ocap = (int)std::min<size_t>(std::max<size_t>(cap, 4096), (size_t)1 << 30);
+    if ((rc = s->okey.alloc(s->ocap)) || (rc = s->okey2.alloc(s->ocap)) || (rc = s->oidx.alloc(s->ocap)) ||
+        (rc = s->oidx2.alloc(s->ocap)) || (rc = s->oval.alloc((size_t)s->ocap * kNV)))
+        return rc;
+    const size_t blocks = std::max<size_t>(1, (cap + kPushBlock - 1) / kPushBlock);
+    if ((rc = s->bcar.alloc(2 * blocks * kNV)) || (rc = s->bcar_key.alloc(2 * blocks)) ||
+        (rc = s->ke_part.alloc(blocks)))
+        return rc;
+    s->push_blocks_cap = blocks;
+    s->cap = cap;
+    return PIC_OK;
+}
+
+int validate_particles(Sim *s, int n, int start) {
+    // positions / hints are staged on the host (s->h_x, s->h_tet) -- upload, check on the device
+    DevBuf<double> dx;
+    DevBuf<int> dt_in, dt_out, dbad;
+    int rc;
+    std::vector<double> xs(s->h_x.begin() + 3 * (size_t)start, s->h_x.begin() + 3 * (size_t)(start + n));
+    if ((rc = dx.upload(xs))) return rc;
+    const bool have_hint = s->h_tet[start] != -2;
+    if (have_hint) {
+        std::vector<int> ts(s->h_tet.begin() + start, s->h_tet.begin() + start + n);
+        if ((rc = dt_in.upload(ts))) return rc;
+    }
+    if ((rc = dt_out.alloc((size_t)start + n)) || (rc = dbad.alloc(1))) return rc;
+    FP_CUDA(cudaMemset(dbad.p, 0, sizeof(int)));
+    const Mesh *m = s->mesh;
+    if (n > 0)
+        k_validate<<<(n + 127) / 128, 128>>>(n, start, dx.p, have_hint ? dt_in.p : nullptr, m->n_tets, m->geo.p,
+                                             m->tet_nbr.p, m->tet_nodes.p, m->xyz.p, dt_out.p, dbad.p);
+    FP_CUDA(cudaGetLastError());
+    int bad = 0;
+    FP_CUDA(cudaMemcpy(&bad, dbad.p, sizeof(int), cudaMemcpyDeviceToHost));
+    std::vector<int> out((size_t)start + n);
+    FP_CUDA(cudaMemcpy(out.data(), dt_out.p, sizeof(int) * ((size_t)start + n), cudaMemcpyDeviceToHost));
+    for (int p = 0; p < n; p++) s->h_tet[start + p] = out[start + p];
+    if (bad) {
+        set_error("pic_particles_load: " + std::to_string(bad) + " particle(s) outside their tet or the mesh");
+        return PIC_ERR_PARTICLE_OUTSIDE;
+    }
+    return PIC_OK;
+}
+
+// uploads the staged particles into bank 0 (called by init)
+int upload_particles(Sim *s) {
+    const int n = (int)s->h_tet.size();
+    int rc = particles_alloc(s, std::max<size_t>((size_t)n, 1));
+    if (rc) return rc;
+    DevBuf<double> dx, dv;
+    DevBuf<int> dt;
+    if ((rc = dx.upload(s->h_x)) || (rc = dv.upload(s->h_v)) || (rc = dt.upload(s->h_tet))) return rc;
+    PartBank &k = s->bank[0];
+    int start = 0;
+    while (start < n) {
+        int sp = s->h_species[start];
+        int end = start;
+        while (end < n && s->h_species[end] == sp) end++;
+        const int cnt = end - start;
+        const int blocks = (cnt + 255) / 256;
+        if (s->mixed)
+            k_load_particles<float><<<blocks, 256, 0, s->stream>>>(
+                cnt, start, dx.p + 3 * (size_t)start, dv.p + 3 * (size_t)start, dt.p, sp, start, (float *)k.x[0].p,
+                (float *)k.x[1].p, (float *)k.x[2].p, (float *)k.v[0].p, (float *)k.v[1].p, (float *)k.v[2].p, k.key.p,
+                k.id.p);
+        else
+            k_load_particles<double><<<blocks, 256, 0, s->stream>>>(
+                cnt, start, dx.p + 3 * (size_t)start, dv.p + 3 * (size_t)start, dt.p, sp, start, (double *)k.x[0].p,
+                (double *)k.x[1].p, (double *)k.x[2].p, (double *)k.v[0].p, (double *)k.v[1].p, (double *)k.v[2].p,
+                k.key.p, k.id.p);
+        start = end;
+    }
+    FP_CUDA(cudaGetLastError());
+    FP_CUDA(cudaStreamSynchronize(s->stream));
+    s->n_total = n;
+    s->cur = 0;
+    s->hctl->n_alive = n;
+    FP_CUDA(cudaMemcpyAsync(&s->dctl.p->n_alive, &n, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    FP_CUDA(cudaStreamSynchronize(s->stream));
+    return PIC_OK;
+}
+
+int sort_particles(Sim *s) {
+    if (s->n_total == 0) return PIC_OK;
+    const int bits = bitlen(((unsigned long long)s->mesh->n_tets << 2));
+    uint32_t *ok, *ov;
+    int rc = radix_sort<uint32_t>(s->stream, s->bank[s->cur].key.p, s->skey.p, s->sval.p, s->tkey.p, s->tval.p,
+                                  nullptr, s->n_total, bits, &s->sortw, &ok, &ov);
+    if (rc) return rc;
+    if (ok != s->skey.p) {
+        std::swap(s->skey, s->tkey);
+        std::swap(s->sval, s->tval);
+    }
+    FP_CUDA(cudaGetLastError());
+    return PIC_OK;
+}
+
+int stage_coefficients(Sim *s, const double *e, const double *b) {
+    const Mesh *m = s->mesh;
+    const int nt = m->n_tets;
+    if (s->mixed)
+        k_coefficients<float><<<(nt + 255) / 256, 256, 0, s->stream>>>(
+            nt, m->geo.p, m->tet_edge.p, m->tet_face.p, m->tet_nodes.p, m->tet_sign.p, m->tet_vol.p, m->xyz.p, e, b,
+            (float *)s->coef.p);
+    else
+        k_coefficients<double><<<(nt + 255) / 256, 256, 0, s->stream>>>(
+            nt, m->geo.p, m->tet_edge.p, m->tet_face.p, m->tet_nodes.p, m->tet_sign.p, m->tet_vol.p, m->xyz.p, e, b,
+            (double *)s->coef.p);
+    FP_CUDA(cudaGetLastError());
+    return PIC_OK;
+}
+
+template <typename R>
+static int launch_push(Sim *s, int mode) {
+    const Mesh *m = s->mesh;
+    PartBank &src = s->bank[s->cur], &dst = s->bank[1 - s->cur];
+    PushArgs<R> a;
+    Control *dc = s->dctl.p;
+    a.d_n_alive = &dc->n_alive;
+    a.skey = s->skey.p;
+    a.perm = s->sval.p;
+    a.sx0 = (const R *)src.x[0].p;
+    a.sx1 = (const R *)src.x[1].p;
+    a.sx2 = (const R *)src.x[2].p;
+    a.sv0 = (const R *)src.v[0].p;
+    a.sv1 = (const R *)src.v[1].p;
+    a.sv2 = (const R *)src.v[2].p;
+    a.sid = src.id.p;
+    a.sah = (const R *)src.ah.p;
+    a.svh = (const R *)src.vh.p;
+    a.dx0 = (R *)dst.x[0].p;
+    a.dx1 = (R *)dst.x[1].p;
+    a.dx2 = (R *)dst.x[2].p;
+    a.dv0 = (R *)dst.v[0].p;
+    a.dv1 = (R *)dst.v[1].p;
+    a.dv2 = (R *)dst.v[2].p;
+    a.dkey = dst.key.p;
+    a.did = dst.id.p;
+    a.dah = (R *)dst.ah.p;
+    a.dvh = (R *)dst.vh.p;
+    a.cap = (long)s->cap;
+    a.geo = m->geo.p;
+    a.coef = (const R *)s->coef.p;
+    a.tnodes = m->tet_nodes.p;
+    a.tnbr = m->tet_nbr.p;
+    for (int k = 0; k < kMaxSpecies; k++) {
+        a.sp.qm[k] = k < s->n_species ? s->sp_q[k] / s->sp_m[k] : 0.0;
+        a.sp.qw[k] = k < s->n_species ? s->sp_q[k] * s->sp_w[k] : 0.0;
+        a.sp.mw[k] = k < s->n_species ? s->sp_m[k] * s->sp_w[k] : 0.0;
+    }
+    a.dt = s->cfg.dt;
+    // Adams-Bashforth weights (newest first); the order ramps 1..k at start-up
+    static const double W[5][5] = {{1.0, 0, 0, 0, 0},
+                                   {1.5, -0.5, 0, 0, 0},
+                                   {23.0 / 12.0, -16.0 / 12.0, 5.0 / 12.0, 0, 0},
+                                   {55.0 / 24.0, -59.0 / 24.0, 37.0 / 24.0, -9.0 / 24.0, 0},
+                                   {1901.0 / 720.0, -2774.0 / 720.0, 2616.0 / 720.0, -1274.0 / 720.0, 251.0 / 720.0}};
+    a.ab_order = s->ab ? std::min(s->nhist + 1, s->ab) : 1;
+    a.hist_levels = s->hist_levels;
+    for (int k = 0; k < 5; k++) a.abw[k] = W[a.ab_order - 1][k];
+    a.walk_cap = std::min(s->cfg.walk_cap, kMaxWalk);
+    a.dead_key = (uint32_t)m->n_tets << 2;
+    a.tacc = s->tacc.p;
+    a.wacc = s->wacc.p;
+    a.bcar = s->bcar.p;
+    a.bcar_key = s->bcar_key.p;
+    a.okey = s->okey.p;
+    a.oval = s->oval.p;
+    a.ocount = &dc->n_over;
+    a.ocap = s->ocap;
+    a.oshift = 6 + std::max(1, bitlen((unsigned long long)s->n_total));
+    a.status = &dc->status;
+    a.n_alive_next = &dc->n_alive;   // rewritten below through a scratch counter
+    a.ke_part = s->ke_part.p;
+    // the live count of this step is read at kernel start; the next count is
+    // accumulated into a separate counter and copied over afterwards
+    a.n_alive_next = reinterpret_cast<int *>(&dc->pad);
+    // the live particles of this step are the first hctl->n_alive sorted entries
+    const int live = s->hctl->n_alive;
+    const int blocks = std::max(1, (live + kPushBlock - 1) / kPushBlock);
+    s->last_push_blocks = blocks;
+    FP_CUDA(cudaMemsetAsync(&dc->pad, 0, sizeof(int), s->stream));
+    if (mode == 2)
+        k_push<R, 2><<<blocks, kPushBlock, 0, s->stream>>>(a);
+    else if (mode == 1)
+        k_push<R, 1><<<blocks, kPushBlock, 0, s->stream>>>(a);
+    else
+        k_push<R, 0><<<blocks, kPushBlock, 0, s->stream>>>(a);
+    FP_CUDA(cudaGetLastError());
+    k_fixup<<<(2 * blocks + 255) / 256, 256, 0, s->stream>>>(blocks, s->skey.p, &dc->n_alive, s->bcar_key.p, s->bcar.p,
+                                                             s->tacc.p);
+    FP_CUDA(cudaGetLastError());
+    return PIC_OK;
+}
+
+int particle_push(Sim *s, int charge_only) {
+    const Mesh *m = s->mesh;
+    FP_CUDA(cudaMemsetAsync(s->tacc.p, 0, sizeof(double) * kNV * (size_t)m->n_tets, s->stream));
+    FP_CUDA(cudaMemsetAsync(s->wacc.p, 0, sizeof(double) * 4 * (size_t)m->n_tets, s->stream));
+    FP_CUDA(cudaMemsetAsync(&s->dctl.p->n_over, 0, sizeof(int), s->stream));
+    if (s->n_total > 0) {
+        const int mode = charge_only ? 2 : (s->ab ? 1 : 0);
+        int rc = s->mixed ? launch_push<float>(s, mode) : launch_push<double>(s, mode);
+        if (rc) return rc;
+        // overflow records: sort by (tet, wall, particle, piece) and add in that order
+        const int oshift = 6 + std::max(1, bitlen((unsigned long long)s->n_total));
+        const int bits = oshift + bitlen(((unsigned long long)m->n_tets << 1) | 1ull);
+        unsigned long long *ok;
+        uint32_t *ov;
+        // clamp the device count to the capacity before sorting
+        rc = radix_sort<unsigned long long>(s->stream, s->okey.p, s->okey2.p, s->oidx.p, s->okey.p, s->oidx2.p,
+                                            &s->dctl.p->n_over, s->ocap, bits, &s->osortw, &ok, &ov);
+        if (rc) return rc;
+        k_overflow_reduce<<<(s->ocap + 255) / 256, 256, 0, s->stream>>>(&s->dctl.p->n_over, s->ocap, ok, ov, s->oval.p,
+                                                                        oshift, s->tacc.p, s->wacc.p);
+        FP_CUDA(cudaGetLastError());
+        // the next step's live count; the new bank holds the first `live` entries
+        FP_CUDA(cudaMemcpyAsync(&s->dctl.p->n_alive, &s->dctl.p->pad, sizeof(int), cudaMemcpyDeviceToDevice, s->stream));
+        s->cur = 1 - s->cur;
+        s->n_total = s->hctl->n_alive;
+        if (!charge_only && s->ab && s->nhist < s->hist_levels) s->nhist++;
+    }
+    return PIC_OK;
+}
+
+int reduce_to_entities(Sim *s) {
+    const Mesh *m = s->mesh;
+    std::swap(s->rho_prev, s->rho);
+    std::swap(s->wall_prev, s->wall);
+    k_gather_edges<<<(m->n_edges + 255) / 256, 256, 0, s->stream>>>(m->n_edges, m->e2t.rowptr.p, m->e2t.col.p,
+                                                                    s->tacc.p, s->g.p, s->dg.p, s->g_new.p);
+    k_gather_nodes<<<(m->n_nodes + 255) / 256, 256, 0, s->stream>>>(m->n_nodes, m->n2t.rowptr.p, m->n2t.col.p,
+                                                                    s->tacc.p, s->wacc.p, s->wall_prev.p, s->rho.p,
+                                                                    s->wall.p);
+    FP_CUDA(cudaGetLastError());
+    return PIC_OK;
+}
+
+}  // namespace fp

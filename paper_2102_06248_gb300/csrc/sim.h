@@ -1,0 +1,161 @@
+// sim.h -- simulation state and kernel launchers of the GB300 FEM-PIC library.
+#pragma once
+
+#include "internal.h"
+
+namespace fp {
+
+constexpr int kMaxSpecies = 4;
+constexpr int kPushBlock = 256;     // threads (= particles) per block of the push kernel
+constexpr int kNV = 10;             // per-tet accumulator: 6 edge currents + 4 node charges
+constexpr int kMaxWalk = 63;        // walk cap limit (segment index fits 6 bits)
+
+// CG scalars and counters kept on the device (one struct per solver)
+struct CgState {
+    double rz;        // r.z of the current iterate
+    double rr;        // r.r
+    double bb;        // b.b
+    double tol2;      // tol^2
+    double alpha, beta;
+    int iters;
+    int done;
+    int max_iters;
+    int failed;
+    unsigned int count_a, count_b;   // arrival counters of the last-block reductions
+};
+
+// Diagnostics record on the device (mirrors pic_diag)
+struct DiagDev {
+    double cont_abs, gauss_abs, rho_max, divb_abs;
+    double energy_e, energy_b, energy_k;
+    double relres;
+    unsigned int count;   // arrival counter
+    int pad;
+};
+
+// Host-visible control block (pinned), refreshed at every synchronising point
+struct Control {
+    CgState cg;
+    CgState lap;
+    DiagDev diag;
+    uint32_t status;
+    int n_alive;
+    int n_over;
+    int pad;
+};
+
+struct SpeciesParams {
+    double qm[kMaxSpecies];   // q/m
+    double qw[kMaxSpecies];   // q * weight
+    double mw[kMaxSpecies];   // m * weight (kinetic energy)
+};
+
+// A bank of particle arrays (SoA).  Element type of x/v/history is double
+// (PLAIN) or float (MIXED).
+struct PartBank {
+    DevBuf<unsigned char> x[3], v[3];
+    DevBuf<uint32_t> key;
+    DevBuf<int> id;
+    DevBuf<unsigned char> ah, vh;   // AB history, levels*3 component arrays of cap entries
+};
+
+// Reusable radix-sort workspace
+struct SortWork {
+    DevBuf<uint32_t> hist;        // 256 * tiles
+    DevBuf<uint32_t> chunk;       // partial sums of the scan
+    size_t tiles_cap = 0;
+};
+
+struct Sim {
+    const Mesh *mesh = nullptr;
+    pic_config cfg{};
+    cudaStream_t stream = nullptr;
+    int mixed = 0;
+    int ab = 0;               // Adams-Bashforth order (0 = Boris)
+    int hist_levels = 0;      // ab - 1
+    int nhist = 0;            // history levels filled (order ramp)
+    int initialised = 0;
+    long step = 0;
+    size_t rsize = 8;         // bytes of one particle real
+
+    // species
+    int n_species = 0;
+    double sp_q[kMaxSpecies], sp_m[kMaxSpecies], sp_w[kMaxSpecies];
+
+    // particles
+    size_t cap = 0;           // allocated particles
+    int n_total = 0;          // particles in the arrays (live first after a sort, then dead)
+    int cur = 0;              // current bank
+    PartBank bank[2];
+    int next_id = 0;
+    // host staging of loads before init
+    std::vector<double> h_x, h_v;
+    std::vector<int> h_tet, h_species;
+
+    // sort
+    DevBuf<uint32_t> skey, sval, tkey, tval;
+    SortWork sortw;
+    // overflow records
+    int ocap = 0;
+    DevBuf<unsigned long long> okey, okey2;
+    DevBuf<uint32_t> oidx, oidx2;
+    DevBuf<double> oval;
+    SortWork osortw;
+
+    // per tet
+    DevBuf<unsigned char> coef;     // 10 reals per tet
+    DevBuf<double> tacc;            // kNV per tet
+    DevBuf<double> wacc;            // 4 per tet
+    DevBuf<double> bcar;            // 2 * kNV per push block
+    DevBuf<uint32_t> bcar_key;      // 2 per push block
+    DevBuf<double> ke_part;         // kinetic energy per push block
+    size_t push_blocks_cap = 0;
+
+    // fields, internal edge numbering (length n_edges; wall entries stay 0)
+    DevBuf<double> e, e_prev, x;    // x = e^{n+1} being solved
+    DevBuf<double> g, g_prev, g_new, dg;
+    DevBuf<double> b, b_prev, b_new;
+    DevBuf<double> rho, rho_prev, wall, wall_prev, rho_bg, phi;
+    DevBuf<double> rhs;
+    // solver work
+    DevBuf<double> A_val, Dinv;
+    DevBuf<double> cg_r, cg_z, cg_p0, cg_p1, cg_q, cg_part;
+    DevBuf<double> hb;              // face vector H (b + b_prev)
+    DevBuf<double> w_edge;          // gradient completion: M t - d2 Gbar on interior edges
+    DevBuf<double> me;              // M x on interior edges
+    // Laplacian solver (interior nodes)
+    DevBuf<double> L_Dinv, l_x, l_b, l_r, l_z, l_p0, l_p1, l_q, l_part;
+    // device control and pinned host mirror
+    DevBuf<Control> dctl;
+    Control *hctl = nullptr;
+    DevBuf<double> diag_part;       // per-block partials of the diagnostic reductions
+    int last_cg_iters = 0;          // previous solves' iteration counts (first chunk size)
+    int last_lap_iters = 0;
+    int last_push_blocks = 0;       // grid of the last push (kinetic-energy partials)
+    uint32_t host_status = 0;       // latched errors seen on the host
+};
+
+// ---- launchers (particles.cu) ----
+int particles_alloc(Sim *s, size_t cap);
+int sort_particles(Sim *s);
+int stage_coefficients(Sim *s, const double *e, const double *b);
+int particle_push(Sim *s, int charge_only);
+int reduce_to_entities(Sim *s);          // per-tet accumulators -> dG, rho, wall
+int validate_particles(Sim *s, int n_new, int start);
+
+// ---- launchers (solver.cu) ----
+int solver_alloc(Sim *s);
+int newmark_rhs(Sim *s);
+int pcg_newmark(Sim *s);
+int gradient_completion(Sim *s);
+int laplacian_solve(Sim *s, const double *rhs_nodes, double *x_nodes, double tol);
+int faraday_update(Sim *s);
+int compute_diagnostics(Sim *s);
+int init_fields(Sim *s);
+int read_control(Sim *s);
+
+}  // namespace fp
+
+struct pic_sim {
+    fp::Sim s;
+};

@@ -1,0 +1,309 @@
+"""Python binding of the GB300 FEM-PIC C ABI (include/fempic.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``_build/libfempic_gb300.so``.  The functions below carry the C names; the
+``Mesh`` and ``Sim`` classes wrap the handles.  PyTorch is used only for device
+buffers (``on_device`` transfers) and streams.  There is no CPU fallback: if
+the library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+PIC_OK = 0
+ERRORS = {1: "INVALID_ARG", 2: "MESH", 3: "OOM", 4: "PARTICLE_OUTSIDE", 5: "WALK_CAP",
+          6: "CG_NO_CONVERGENCE", 7: "NAN", 8: "CUDA", 9: "OVERFLOW", 10: "STATE"}
+FORMS = {"we": 0, "mfem": 1}
+PRECISIONS = {"plain": 0, "mixed": 1}
+FIELDS = {"E": 0, "E_PREV": 1, "B": 2, "B_PREV": 3, "G": 4, "G_PREV": 5, "DG": 6, "RHO": 7,
+          "WALL": 8, "RHO_BG": 9, "PHI": 10}
+
+
+class PicError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: PIC_ERR_{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class pic_mesh_desc(C.Structure):
+    _fields_ = [("n_nodes", C.c_int32), ("xyz", C.POINTER(C.c_double)), ("n_tets", C.c_int32),
+                ("tets", C.POINTER(C.c_int32)), ("n_edges", C.c_int32), ("edges", C.POINTER(C.c_int32)),
+                ("n_faces", C.c_int32), ("faces", C.POINTER(C.c_int32)), ("G_coo", C.POINTER(C.c_int32)),
+                ("C_coo", C.POINTER(C.c_int32)), ("D_coo", C.POINTER(C.c_int32))]
+
+
+class pic_config(C.Structure):
+    _fields_ = [("form", C.c_int32), ("pusher", C.c_int32), ("precision", C.c_int32),
+                ("preconditioner", C.c_int32), ("dt", C.c_double), ("b0", C.c_double * 3),
+                ("rho_background", C.c_double), ("cg_tol", C.c_double), ("cg_max_iters", C.c_int32),
+                ("init_tol", C.c_double), ("walk_cap", C.c_int32), ("cg_check_every", C.c_int32),
+                ("max_species", C.c_int32), ("stream", C.c_void_p)]
+
+
+class pic_diag(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "step", "continuity_abs", "gauss_abs", "rho_max", "divb_abs", "cg_iters", "cg_relres", "n_alive",
+        "energy_e", "energy_b", "energy_k", "status")]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Loads the CUDA library (building it first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise ImportError(f"GB300 library not built: {_build.LIB}")
+        _build.build()
+    lib = C.CDLL(_build.LIB)
+    P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    dp, ip, lp = C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+    sig = {
+        "pic_mesh_create": ([C.POINTER(pic_mesh_desc), C.POINTER(P)], I32),
+        "pic_mesh_destroy": ([P], None),
+        "pic_mesh_info": ([P, lp], I32),
+        "pic_mesh_entities": ([P, ip, ip], I32),
+        "pic_mesh_incidence": ([P, I32, ip, ip, ip], I32),
+        "pic_config_default": ([C.POINTER(pic_config)], None),
+        "pic_sim_create": ([P, C.POINTER(pic_config), C.POINTER(P)], I32),
+        "pic_sim_destroy": ([P], None),
+        "pic_particles_load": ([P, I32, D, D, D, I64, C.c_void_p, C.c_void_p, C.c_void_p, I32], I32),
+        "pic_sim_init": ([P], I32),
+        "pic_set_ab_history": ([P, I32, dp, dp], I32),
+        "pic_step": ([P, I32], I32),
+        "pic_particle_phase": ([P], I32),
+        "pic_field_get": ([P, I32, C.c_void_p, I64, I32], I32),
+        "pic_field_set": ([P, I32, C.c_void_p, I64, I32], I32),
+        "pic_particles_count": ([P, lp], I32),
+        "pic_particles_get": ([P, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, I64, lp, I32], I32),
+        "pic_diagnostics_get": ([P, C.POINTER(pic_diag)], I32),
+        "pic_sim_synchronize": ([P], I32),
+        "pic_last_error": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str):
+    if rc != PIC_OK:
+        raise PicError(rc, where, (_lib.pic_last_error() or b"").decode())
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+class Mesh:
+    """pic_mesh_create on node coordinates and tets (host arrays)."""
+
+    def __init__(self, xyz: np.ndarray, tets: np.ndarray, edges: Optional[np.ndarray] = None,
+                 faces: Optional[np.ndarray] = None, incidence: Optional[Dict[str, np.ndarray]] = None):
+        lib = load()
+        self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        self._tets = np.ascontiguousarray(tets, dtype=np.int32)
+        d = pic_mesh_desc()
+        d.n_nodes = self._xyz.shape[0]
+        d.xyz = _ptr(self._xyz, C.c_double)
+        d.n_tets = self._tets.shape[0]
+        d.tets = _ptr(self._tets, C.c_int32)
+        keep = []
+        if edges is not None:
+            e = np.ascontiguousarray(edges, dtype=np.int32)
+            keep.append(e)
+            d.n_edges = e.shape[0]
+            d.edges = _ptr(e, C.c_int32)
+        if faces is not None:
+            f = np.ascontiguousarray(faces, dtype=np.int32)
+            keep.append(f)
+            d.n_faces = f.shape[0]
+            d.faces = _ptr(f, C.c_int32)
+        for key, field in (("G", "G_coo"), ("C", "C_coo"), ("D", "D_coo")):
+            if incidence and key in incidence:
+                a = np.ascontiguousarray(incidence[key], dtype=np.int32)
+                keep.append(a)
+                setattr(d, field, _ptr(a, C.c_int32))
+        h = C.c_void_p()
+        _check(lib.pic_mesh_create(C.byref(d), C.byref(h)), "pic_mesh_create")
+        self._h = h
+        c = np.zeros(6, dtype=np.int64)
+        _check(lib.pic_mesh_info(h, _ptr(c, C.c_int64)), "pic_mesh_info")
+        (self.n_nodes, self.n_edges, self.n_faces, self.n_tets,
+         self.n_int_edges, self.n_int_nodes) = (int(x) for x in c)
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.pic_mesh_destroy(self._h)
+            self._h = None
+
+    def entities(self):
+        e = np.zeros((self.n_edges, 2), dtype=np.int32)
+        f = np.zeros((self.n_faces, 3), dtype=np.int32)
+        _check(_lib.pic_mesh_entities(self._h, _ptr(e, C.c_int32), _ptr(f, C.c_int32)), "pic_mesh_entities")
+        return e, f
+
+    def incidence(self, which: str):
+        n = {"G": 2 * self.n_edges, "C": 3 * self.n_faces, "D": 4 * self.n_tets}[which]
+        r, c, v = (np.zeros(n, dtype=np.int32) for _ in range(3))
+        _check(_lib.pic_mesh_incidence(self._h, "GCD".index(which), _ptr(r, C.c_int32), _ptr(c, C.c_int32),
+                                       _ptr(v, C.c_int32)), "pic_mesh_incidence")
+        return r, c, v
+
+
+def default_config() -> pic_config:
+    load()
+    c = pic_config()
+    _lib.pic_config_default(C.byref(c))
+    return c
+
+
+class Sim:
+    """pic_sim_create / pic_particles_load / pic_sim_init / pic_step ... on one mesh."""
+
+    def __init__(self, mesh: Mesh, dt: float, form: str = "we", pusher: str = "boris",
+                 precision: str = "plain", b0: Sequence[float] = (0.0, 0.0, 0.0), rho_background: float = 0.0,
+                 cg_tol: float = 1e-10, init_tol: float = 1e-14, cg_max_iters: int = 10000,
+                 walk_cap: int = 63, stream=None):
+        lib = load()
+        self.mesh = mesh
+        c = default_config()
+        c.form = FORMS[form]
+        c.pusher = 0 if pusher == "boris" else int(pusher[2:])
+        c.precision = PRECISIONS[precision]
+        c.dt = dt
+        for i in range(3):
+            c.b0[i] = b0[i]
+        c.rho_background = rho_background
+        c.cg_tol = cg_tol
+        c.init_tol = init_tol
+        c.cg_max_iters = cg_max_iters
+        c.walk_cap = walk_cap
+        if stream is not None:
+            c.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        self.config = c
+        h = C.c_void_p()
+        _check(lib.pic_sim_create(mesh._h, C.byref(c), C.byref(h)), "pic_sim_create")
+        self._h = h
+        self.n_loaded = 0
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.pic_sim_destroy(self._h)
+            self._h = None
+
+    def particles_load(self, species: int, q: float, m: float, w: float, x, v, tet=None):
+        """Host numpy arrays, or CUDA torch tensors (x, v float64 [n,3]; tet int32 [n])."""
+        on_dev = hasattr(x, "is_cuda") and x.is_cuda
+        if on_dev:
+            n = x.shape[0]
+            xp, vp = C.c_void_p(x.data_ptr()), C.c_void_p(v.data_ptr())
+            tp = C.c_void_p(tet.data_ptr()) if tet is not None else None
+        else:
+            x = np.ascontiguousarray(x, dtype=np.float64)
+            v = np.ascontiguousarray(v, dtype=np.float64)
+            n = x.shape[0]
+            xp, vp = C.c_void_p(x.ctypes.data), C.c_void_p(v.ctypes.data)
+            if tet is not None:
+                tet = np.ascontiguousarray(tet, dtype=np.int32)
+                tp = C.c_void_p(tet.ctypes.data)
+            else:
+                tp = None
+        _check(_lib.pic_particles_load(self._h, species, q, m, w, n, xp, vp, tp, int(on_dev)),
+               "pic_particles_load")
+        self.n_loaded += n
+
+    def init(self):
+        _check(_lib.pic_sim_init(self._h), "pic_sim_init")
+
+    def set_ab_history(self, a_hist: np.ndarray, v_hist: np.ndarray):
+        a = np.ascontiguousarray(a_hist, dtype=np.float64)
+        v = np.ascontiguousarray(v_hist, dtype=np.float64)
+        _check(_lib.pic_set_ab_history(self._h, a.shape[0], _ptr(a, C.c_double), _ptr(v, C.c_double)),
+               "pic_set_ab_history")
+
+    def step(self, n: int = 1):
+        _check(_lib.pic_step(self._h, n), "pic_step")
+
+    def particle_phase(self):
+        _check(_lib.pic_particle_phase(self._h), "pic_particle_phase")
+
+    def field_len(self, which: str) -> int:
+        m = self.mesh
+        if which in ("E", "E_PREV", "G", "G_PREV", "DG"):
+            return m.n_edges
+        if which in ("B", "B_PREV"):
+            return m.n_faces
+        return m.n_nodes
+
+    def field(self, which: str, out=None):
+        n = self.field_len(which)
+        if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+            _check(_lib.pic_field_get(self._h, FIELDS[which], C.c_void_p(out.data_ptr()), n, 1), "pic_field_get")
+            return out
+        a = np.zeros(n)
+        _check(_lib.pic_field_get(self._h, FIELDS[which], C.c_void_p(a.ctypes.data), n, 0), "pic_field_get")
+        return a
+
+    def set_field(self, which: str, values):
+        n = self.field_len(which)
+        if hasattr(values, "is_cuda") and values.is_cuda:
+            _check(_lib.pic_field_set(self._h, FIELDS[which], C.c_void_p(values.data_ptr()), n, 1), "pic_field_set")
+            return
+        a = np.ascontiguousarray(values, dtype=np.float64)
+        _check(_lib.pic_field_set(self._h, FIELDS[which], C.c_void_p(a.ctypes.data), n, 0), "pic_field_set")
+
+    def count(self) -> int:
+        n = C.c_int64()
+        _check(_lib.pic_particles_count(self._h, C.byref(n)), "pic_particles_count")
+        return n.value
+
+    def particles(self):
+        """(x [n,3], v [n,3], tet [n], id [n]) of the live particles, sorted by id."""
+        cap = max(self.n_loaded, 1)
+        x = np.zeros((cap, 3))
+        v = np.zeros((cap, 3))
+        t = np.zeros(cap, dtype=np.int32)
+        i = np.zeros(cap, dtype=np.int32)
+        n = C.c_int64()
+        _check(_lib.pic_particles_get(self._h, C.c_void_p(x.ctypes.data), C.c_void_p(v.ctypes.data),
+                                      C.c_void_p(t.ctypes.data), C.c_void_p(i.ctypes.data), cap, C.byref(n), 0),
+               "pic_particles_get")
+        k = n.value
+        order = np.argsort(i[:k], kind="stable")
+        return x[:k][order], v[:k][order], t[:k][order], i[:k][order]
+
+    def diag(self) -> Dict[str, float]:
+        d = pic_diag()
+        _check(_lib.pic_diagnostics_get(self._h, C.byref(d)), "pic_diagnostics_get")
+        return {n: getattr(d, n) for n, _ in pic_diag._fields_}
+
+    def synchronize(self):
+        _check(_lib.pic_sim_synchronize(self._h), "pic_sim_synchronize")
+
+
+def sim_from_workload(wl, dt: float, precision: str = "plain", cg_tol: float = 1e-10,
+                      init_tol: float = 1e-14, mesh: Optional[Mesh] = None, stream=None) -> Sim:
+    """Builds and initialises a simulation of a ``workloads.Workload``."""
+    mesh = mesh or Mesh(wl.mesh.xyz, wl.mesh.tets)
+    sim = Sim(mesh, dt, form=wl.form, pusher=wl.pusher, precision=precision, b0=wl.b0,
+              rho_background=wl.rho_background, cg_tol=cg_tol, init_tol=init_tol, stream=stream)
+    for k, sp in enumerate(wl.species):
+        sim.particles_load(k, sp.q, sp.m, sp.w, sp.x, sp.v, sp.tet)
+    sim.init()
+    return sim

@@ -1,0 +1,231 @@
+"""GPU path vs the FP64 oracle, element by element, on the same seeded inputs.
+
+Tolerances: FP64 path <= 1e-10 relative (to the field's max magnitude, or the
+box size for positions) on fields and particles over the first 10 steps;
+conservation (continuity and Gauss) <= 1e-12 relative every step.  The
+Newmark solves run at cg_tol 1e-13 in the parity cases, so that the
+comparison measures the two implementations and not two CG stopping points.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2102_06248_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DT_CFL_6 = 1.3017565848335032e-10   # tests/golden/dt_cfl.json, thermal_plasma_cube_6^3
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2102_06248_gb300 import fempic
+    fempic.load()
+    return fempic
+
+
+def rel_err(a, b):
+    scale = max(np.abs(b).max(), 1e-300)
+    return np.abs(a - b).max() / scale
+
+
+def compare_particles(gpu, orc, box_scale, tol=1e-10):
+    gx, gv, gt, gid = gpu
+    ox, ov, ot, alive = orc
+    ids = np.where(alive)[0]
+    assert np.array_equal(gid, ids), (len(gid), len(ids))
+    assert np.array_equal(gt, ot[ids])
+    assert np.abs(gx - ox[ids]).max() <= tol * box_scale
+    assert np.abs(gv - ov[ids]).max() <= tol * max(np.abs(ov).max(), 1e-300)
+
+
+def frozen_field_case(F, oracle_lib, precision="plain", pusher="boris", seed=3, n=4000, cells=4, speed=0.3):
+    """Random fields and fast particles so that many paths cross several tets
+    and some reach the walls."""
+    box = W.kuhn_box((cells,) * 3, (1.0,) * 3, jitter=0.15, seed=seed)
+    om = oracle_lib.OracleMesh(box.xyz, box.tets)
+    rng = np.random.default_rng(seed)
+    ref = rng.uniform(0.0, 1.0, (n, 3))
+    x, tet = W.place_in_box(box, ref)
+    dt = 1e-9
+    v = rng.normal(size=(n, 3)) * speed * (1.0 / cells) / dt      # ~speed cells per step
+    e = rng.normal(size=om.n_edges) * 1e-3
+    eb, _, _ = om.flags()
+    e[eb == 1] = 0.0
+    b = rng.normal(size=om.n_faces) * 1e-12
+    q, m, w = W.Q_E, W.M_E, 1e3
+    cfg = oracle_lib.OracleConfig(dt=dt, pusher=pusher)
+    osim = oracle_lib.OracleSim(om, cfg)
+    osim.add_species(q, m, w, x, v, tet)
+    osim.init()
+    osim.set_field("E", e)
+    osim.set_field("B", b)
+    pm = F.Mesh(box.xyz, box.tets)
+    gsim = F.Sim(pm, dt, pusher=pusher, precision=precision)
+    gsim.particles_load(0, q, m, w, x, v, tet)
+    gsim.init()
+    gsim.set_field("E", e)
+    gsim.set_field("B", b)
+    return box, om, osim, gsim
+
+
+def test_particle_phase_frozen_fields(F, oracle_lib):
+    box, om, osim, gsim = frozen_field_case(F, oracle_lib)
+    for it in range(3):
+        osim.particle_phase()
+        gsim.particle_phase()
+        compare_particles(gsim.particles(), osim.particles(), 1.0)
+        assert rel_err(gsim.field("DG"), osim.field("DG")) <= 1e-12
+        assert rel_err(gsim.field("RHO"), osim.field("RHO")) <= 1e-12
+        assert rel_err(gsim.field("WALL"), osim.field("WALL")) <= 1e-12
+    _, _, _, alive = osim.particles()
+    assert alive.sum() < alive.size          # some particles were absorbed
+
+
+def test_particle_phase_many_crossings(F, oracle_lib):
+    """Paths of up to several cells per step: exercises the overflow records."""
+    box, om, osim, gsim = frozen_field_case(F, oracle_lib, speed=2.5, n=2000, seed=8)
+    osim.particle_phase()
+    gsim.particle_phase()
+    compare_particles(gsim.particles(), osim.particles(), 1.0)
+    assert rel_err(gsim.field("DG"), osim.field("DG")) <= 1e-12
+    assert rel_err(gsim.field("RHO"), osim.field("RHO")) <= 1e-12
+    assert rel_err(gsim.field("WALL"), osim.field("WALL")) <= 1e-12
+
+
+@pytest.mark.parametrize("pusher", ["ab2", "ab4"])
+def test_particle_phase_adams_bashforth(F, oracle_lib, pusher):
+    box, om, osim, gsim = frozen_field_case(F, oracle_lib, pusher=pusher, n=1500, seed=4)
+    for it in range(5):       # covers the order ramp and the full order
+        osim.particle_phase()
+        gsim.particle_phase()
+        compare_particles(gsim.particles(), osim.particles(), 1.0)
+        assert rel_err(gsim.field("DG"), osim.field("DG")) <= 1e-12
+
+
+def run_pair(F, oracle_lib, wl, dt, steps, cg_tol=1e-13):
+    from oracle.oracle import from_workload
+    osim = from_workload(wl, dt, cg_tol=cg_tol)
+    gsim = F.sim_from_workload(wl, dt, cg_tol=cg_tol)
+    return osim, gsim
+
+
+@pytest.mark.parametrize("form", ["we", "mfem"])
+def test_full_step_parity_10_steps(F, oracle_lib, form):
+    """Thermal plasma cube (6^3, 10,000 electrons, B0 = 0.1 T, 2 x CFL):
+    fields and particles within 1e-10 of the oracle for 10 steps."""
+    wl = W.thermal_plasma_cube()
+    wl.form = form
+    osim, gsim = run_pair(F, oracle_lib, wl, 2 * DT_CFL_6, 10)
+    for name in ("E", "B", "RHO", "PHI"):
+        assert rel_err(gsim.field(name), osim.field(name)) <= 1e-12, name
+    for step in range(10):
+        osim.step()
+        gsim.step()
+        for name in ("E", "E_PREV", "B", "G", "DG", "RHO", "WALL"):
+            assert rel_err(gsim.field(name), osim.field(name)) <= 1e-10, (step, name)
+        compare_particles(gsim.particles(), osim.particles(), 1.0)
+        gd, od = gsim.diag(), osim.diag()
+        assert gd["n_alive"] == od["n_alive"]
+        assert abs(gd["cg_iters"] - od["cg_iters"]) <= 1
+
+
+def test_larmor_mfem_parity(F, oracle_lib):
+    """Single electron, Maxwell-solver form, dt = T_c/64 on a small box."""
+    wl = W.larmor_orbit_box(n_cells=8, steps=40)
+    osim, gsim = run_pair(F, oracle_lib, wl, wl.dt, 40)
+    for step in range(40):
+        osim.step()
+        gsim.step()
+    for name in ("E", "B", "G", "RHO"):
+        assert rel_err(gsim.field(name), osim.field(name)) <= 1e-10, name
+    compare_particles(gsim.particles(), osim.particles(), wl.mesh.size[0])
+
+
+def test_conservation_100_steps(F):
+    """Sec. III.A on the GPU: continuity and Gauss at round-off for 100 steps
+    of the thermal cube at the production tolerance (cg_tol 1e-10)."""
+    wl = W.thermal_plasma_cube()
+    gsim = F.sim_from_workload(wl, 2 * DT_CFL_6)
+    d0 = gsim.diag()
+    assert d0["gauss_abs"] <= 1e-13 * d0["rho_max"]
+    worst_c = worst_g = 0.0
+    for _ in range(100):
+        gsim.step()
+        d = gsim.diag()
+        worst_c = max(worst_c, d["continuity_abs"] / d["rho_max"])
+        worst_g = max(worst_g, d["gauss_abs"] / d["rho_max"])
+        assert d["cg_relres"] <= 2e-10
+    assert worst_c <= 1e-12 and worst_g <= 1e-12, (worst_c, worst_g)
+    assert d["divb_abs"] <= 1e-12 * np.abs(gsim.field("B")).max()
+
+
+def test_deterministic(F):
+    wl = W.thermal_plasma_cube(n_cells=4, n_particles=5000, seed=21)
+    outs = []
+    for _ in range(2):
+        s = F.sim_from_workload(wl, 3e-10)
+        s.step(5)
+        outs.append((s.field("E"), s.field("G"), s.particles()[0]))
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+
+
+def test_no_particles_vacuum_mode(F, oracle_lib):
+    """Empty particle set: the field update alone (a curl eigenmode keeps its
+    amplitude and advances by 2 atan(w dt/2) per step)."""
+    import scipy.linalg as sl
+    box = W.kuhn_box((3, 3, 3), (1.0, 1.0, 1.0))
+    om = oracle_lib.OracleMesh(box.xyz, box.tets)
+    eb, _, _ = om.flags()
+    ii = np.where(eb == 0)[0]
+    M, K = om.matrix_dense("M"), om.matrix_dense("K")
+    w2, U = sl.eigh(K[np.ix_(ii, ii)], M[np.ix_(ii, ii)])
+    k = int(np.argmax(w2 > 1e-6 * w2.max())) + 5
+    omega = math.sqrt(w2[k])
+    dt = 2.0 * 2.0 / math.sqrt(w2.max())
+    phi = 2 * math.atan(omega * dt / 2)
+    u = np.zeros(om.n_edges)
+    u[ii] = U[:, k] / np.abs(U[:, k]).max()
+    pm = F.Mesh(box.xyz, box.tets)
+    s = F.Sim(pm, dt, cg_tol=1e-13)
+    s.init()
+    s.set_field("E", u)
+    s.set_field("E_PREV", math.cos(phi) * u)
+    s.step(20)
+    assert np.allclose(s.field("E"), math.cos(20 * phi) * u, atol=1e-9)
+
+
+def test_error_paths(F):
+    box = W.kuhn_box((3, 3, 3), (1.0, 1.0, 1.0))
+    pm = F.Mesh(box.xyz, box.tets)
+    with pytest.raises(F.PicError) as ei:
+        F.Sim(pm, -1.0)
+    assert ei.value.code == 1
+    s = F.Sim(pm, 1e-9)
+    x = np.array([[0.5, 0.5, 0.5]])
+    with pytest.raises(F.PicError) as ei:            # wrong tet hint
+        s.particles_load(0, W.Q_E, W.M_E, 1.0, x, np.zeros((1, 3)), np.array([0], dtype=np.int32))
+    assert ei.value.code == 4
+    with pytest.raises(F.PicError) as ei:            # outside the mesh, located by a walk
+        s.particles_load(0, W.Q_E, W.M_E, 1.0, np.array([[1.5, 0.5, 0.5]]), np.zeros((1, 3)))
+    assert ei.value.code == 4
+    s.particles_load(0, W.Q_E, W.M_E, 1.0, x, np.zeros((1, 3)))   # located by a walk
+    with pytest.raises(F.PicError) as ei:
+        s.step()                                     # before init
+    assert ei.value.code == 10
+    s.init()
+    _, _, t, _ = s.particles()
+    assert 0 <= t[0] < pm.n_tets
+    # walk cap: a particle crossing many cells in one step with walk_cap = 1
+    s2 = F.Sim(pm, 1e-9, walk_cap=1)
+    xx, tt = W.place_in_box(box, np.array([[0.1, 0.5, 0.5]]))
+    s2.particles_load(0, W.Q_E, W.M_E, 1.0, xx, np.array([[5e8, 0.0, 0.0]]), tt)
+    s2.init()
+    with pytest.raises(F.PicError) as ei:
+        s2.step()
+    assert ei.value.code == 5
