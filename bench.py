@@ -1,0 +1,406 @@
+"""Benchmark of the GB300 charge-conserving FEM-PIC step.
+
+One step = one full PIC cycle of the library (sort by tet, per-tet
+coefficients, gather + push + walk + exact deposit, reduction to edges and
+nodes, Newmark RHS, PCG to 1e-10, gradient completion, Faraday update,
+diagnostics) over every particle of the workload.  The metric is
+particle-steps/s over whole steps; the plain-FP64 GPU path is timed in the
+same run for the comparison the metric names.
+
+Default workload: the neutral plasma ball of 64^3 Kuhn cells (1,572,864 tets,
+interior vertices jittered by up to 20% of h), 16M electrons + 16M protons
+(mass ratio 1836) in a Gaussian sphere, Te = 10 eV, Ti = 0.1 eV, Debye length
+2h at the peak density, PEC walls, wave-equation Newmark, Boris push,
+dt = 4 x the explicit limit, Jacobi-PCG to 1e-10.  Synthetic seeded inputs.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+        [--workload plasma_ball|thermal_cube] [--cells C] [--particles P]
+Under torchrun (N > 1) each rank runs an independent replica (the method's
+field solve couples the whole mesh, so there is nothing to shard): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2102_06248_gb300 import workloads as W  # noqa: E402
+
+METRIC = "particle-steps/s (gather+push+deposit) and step time vs plain FP64 GPU path"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def dt_table():
+    with open(os.path.join(ROOT, "tests", "golden", "dt_cfl.json")) as f:
+        return json.load(f)
+
+
+def make_workload(name: str, cells: int, per_species: int):
+    tab = dt_table()
+    if name == "plasma_ball":
+        wl = W.plasma_ball(n_cells=cells, n_per_species=per_species)
+        kappa = tab["kuhn_lattice_16^3_jitter0.2"]["kappa"]
+        dt = wl.dt_cfl_multiple * kappa * wl.mesh.h / W.C0
+        desc = (f"plasma_ball {cells}^3 Kuhn cells ({6 * cells ** 3} tets, 20% jitter), "
+                f"{per_species} e- + {per_species} p+ Gaussian sphere, Te=10 eV, Ti=0.1 eV, "
+                f"WE Newmark, Boris, dt=4xCFL, Jacobi-PCG 1e-10, PEC walls")
+    elif name == "thermal_cube":
+        wl = W.thermal_plasma_cube(n_cells=cells, n_particles=per_species)
+        dt = 2.0 * tab["thermal_plasma_cube_6^3"]["dt_cfl_s"] * (6.0 / cells)
+        desc = (f"thermal_cube {cells}^3 Kuhn cells, {per_species} e- Maxwellian 0.01c, "
+                f"B0=0.1 T, WE Newmark, Boris, dt=2xCFL, Jacobi-PCG 1e-10")
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return wl, dt, desc
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                d = json.load(f)
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "of measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "of fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus: int):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local, dist
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(dist, value: float, device) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(dist, value: float, device) -> float:
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def push_bytes(n_particles: int, n_tets: int, precision: str) -> float:
+    """Algorithmic bytes of one launch of the fused push kernel: every live
+    particle's state read (through the sort permutation) and written once,
+    plus the per-tet geometry, coefficients and accumulators once."""
+    r = 4 if precision == "mixed" else 8
+    per_particle = 2 * (6 * r + 4 + 4) + 4 + 4      # x,v,key,id in and out; perm; sorted key
+    per_tet = 96 + 10 * r + 80                      # geometry, coefficients, accumulator write
+    return n_particles * per_particle + n_tets * per_tet
+
+
+def spmv_bytes(n_rows: int, nnz: int) -> float:
+    """Algorithmic bytes of one fused PCG SpMV launch (q = A p, p = z + beta p):
+    values + columns (12 B/nnz), row pointers, z and p_old read, p_new and q written."""
+    return 12.0 * nnz + 4.0 * (n_rows + 1) + 32.0 * n_rows
+
+
+def time_gpu(F, wl, dt, precision, steps, warmup, stream, dist, device, torch, profile=True):
+    sim = F.sim_from_workload(wl, dt, precision=precision, stream=stream, profile=profile)
+    for _ in range(warmup):
+        sim.step()
+    sim.profile_reset()
+    barrier(dist, device)
+    torch.cuda.synchronize()
+    l0 = F.launch_count()
+    start = torch.cuda.Event(enable_timing=True)
+    stop = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(steps):
+        sim.step()
+    stop.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist, device)
+    ms = start.elapsed_time(stop)
+    launches = F.launch_count() - l0
+    prof = sim.profile()
+    diag = sim.diag()
+    return sim, ms, launches, prof, diag
+
+
+def gpu_arm(args):
+    import torch
+    from paper_2102_06248_gb300 import fempic as F
+
+    rank, world, local, dist = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    F.load()
+    wl, dt, desc = make_workload(args.workload, args.cells, args.particles)
+    n_part = wl.n_particles
+
+    # ---- mixed precision (headline) with clocks sampled during the timed region ----
+    clocks = ClockSampler(local)
+    sim_m = F.sim_from_workload(wl, dt, precision="mixed", stream=stream, profile=True)
+    mesh = sim_m.mesh
+    for _ in range(args.warmup):
+        sim_m.step()
+    sim_m.profile_reset()
+    barrier(dist, local if world > 1 else None)
+    torch.cuda.synchronize()
+    l0 = F.launch_count()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        sim_m.step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(dist, local if world > 1 else None)
+    ms_mixed = ev0.elapsed_time(ev1)
+    launches = F.launch_count() - l0
+    prof_m = sim_m.profile()
+    diag_m = sim_m.diag()
+    alive_m = diag_m["n_alive"]
+    ms_max = max_over_ranks(dist, ms_mixed, device)
+    total_ps = sum_over_ranks(dist, float(n_part) * args.steps, device)
+    value = total_ps / (ms_max / 1e3)
+    del sim_m
+
+    # ---- plain FP64 GPU path, same workload ----
+    sim_p, ms_plain, _, prof_p, diag_p = time_gpu(F, wl, dt, "plain", args.steps, args.warmup, stream, dist,
+                                                   local if world > 1 else None, torch)
+    del sim_p
+    ms_plain_max = max_over_ranks(dist, ms_plain, device)
+    value_plain = total_ps / (ms_plain_max / 1e3)
+
+    # ---- end to end through the public API from host arrays ----
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim_e = F.Sim(F.Mesh(wl.mesh.xyz, wl.mesh.tets), dt, form=wl.form, pusher=wl.pusher, precision="mixed",
+                  b0=wl.b0, rho_background=wl.rho_background, stream=stream)
+    t_mesh = time.perf_counter()
+    for k, sp in enumerate(wl.species):
+        sim_e.particles_load(k, sp.q, sp.m, sp.w, sp.x, sp.v, sp.tet)
+    sim_e.init()
+    sim_e.step(args.steps)
+    e_out = sim_e.field("E")
+    xo, vo, to, io = sim_e.particles()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    e2e_s = t1 - t_mesh
+    h2d = sum(sp.x.nbytes + sp.v.nbytes + sp.tet.nbytes for sp in wl.species)
+    d2h = e_out.nbytes + xo.nbytes + vo.nbytes + to.nbytes + io.nbytes
+    del sim_e
+    e2e_s_max = max_over_ranks(dist, e2e_s, device)
+
+    # ---- roofline of the dominant kernel (live CUDA-event times) ----
+    peak, peak_src = measured_peak()
+    push_ms, push_n = prof_m["push"]
+    spmv_ms, spmv_n = prof_m["spmv"]
+    push_avg = push_ms / max(push_n, 1)
+    spmv_avg = spmv_ms / max(spmv_n, 1)
+    nnz_A = int(getattr(mesh, "nnz_A", 0))
+    if push_ms >= spmv_ms:
+        kernel = "k_push (fused gather/push/walk/deposit, mixed)"
+        alg = push_bytes(int(alive_m), mesh.n_tets, "mixed")
+        avg_ms = push_avg
+    else:
+        kernel = "k_cg_a (fused PCG SpMV)"
+        alg = spmv_bytes(mesh.n_int_edges, nnz_A)
+        avg_ms = spmv_avg
+    achieved = alg / (avg_ms / 1e3) / 1e9
+    roofline = {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
+                "traffic": None, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": round(avg_ms, 5)}
+
+    # ---- CPU baseline: the oracle on a bounded, proportionally scaled sample ----
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, seconds=args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 push + f64 deposit/solve", "data": "synthetic",
+            "config": {"workload": desc, "particles_per_gpu": n_part, "tets": mesh.n_tets,
+                       "edges": mesh.n_edges, "interior_edges": mesh.n_int_edges, "dt_s": dt,
+                       "precision": "mixed", "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (particle state > 1 GB per GPU)"},
+            "plain_fp64": {"value": value_plain, "ms_per_step": ms_plain_max / args.steps,
+                           "speedup_mixed_over_plain": value / value_plain},
+            "phases_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof_m.items() if k != "spmv"},
+            "phases_ms_per_step_plain": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof_p.items()
+                                         if k != "spmv"},
+            "cg_iters_last": diag_m["cg_iters"],
+            "conservation_last": {"continuity_rel": diag_m["continuity_abs"] / max(diag_m["rho_max"], 1e-300),
+                                  "gauss_rel": diag_m["gauss_abs"] / max(diag_m["rho_max"], 1e-300)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": total_ps / e2e_s_max, "unit": "particle-steps/s",
+                    "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                    "seconds": e2e_s_max,
+                    "what": "particles_load from host arrays + init + K steps + E field and particles read back"},
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(args, seconds: float = 20.0):
+    """The FP64 oracle, as it stands, on the host cores: a proportionally
+    scaled copy of the workload (cells / 4 per axis, particles / 64, same
+    density and dt recipe), stepped until about `seconds` of CPU work."""
+    from oracle.oracle import from_workload
+    cells = max(4, args.cells // 4)
+    per = max(1000, args.particles // 64)
+    wl, dt, _ = make_workload(args.workload, cells, per)
+    sim = from_workload(wl, dt)
+    n = wl.n_particles
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        sim.step()
+        steps += 1
+        if time.perf_counter() - t0 > seconds or steps >= 200:
+            break
+    el = time.perf_counter() - t0
+    return {"value": n * steps / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{args.workload} scaled to {cells}^3 cells and {n} particles (same density and dt recipe), "
+                      f"{steps} full steps in {el:.1f} s, single thread"}
+
+
+def reference_arm(args):
+    """The oracle as the reference arm: K timed steps (after W warm-up steps)
+    of the bounded scaled sample of the same workload, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle.oracle import from_workload
+    cells = max(4, args.cells // 4)
+    per = max(1000, args.particles // 64)
+    wl, dt, desc = make_workload(args.workload, cells, per)
+    sim = from_workload(wl, dt)
+    for _ in range(args.warmup):
+        sim.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.step()
+    el = time.perf_counter() - t0
+    n = wl.n_particles
+    value = n * args.steps / el
+    sample = f"{desc}; scaled copy of the GPU workload ({cells}^3 cells, {n} particles), single thread"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": sample},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="plasma_ball", choices=["plasma_ball", "thermal_cube"])
+    ap.add_argument("--cells", type=int, default=64)
+    ap.add_argument("--particles", type=int, default=16 * 1024 * 1024, help="particles per species")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gb300":
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

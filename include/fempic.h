@@ -76,7 +76,8 @@ extern "C" {
 /* fields for pic_field_get / pic_field_set (lengths in brackets) */
 #define PIC_FIELD_E 0        /* e^n        [n_edges], 0 on wall edges */
 #define PIC_FIELD_E_PREV 1   /* e^{n-1}    [n_edges] */
-#define PIC_FIELD_B 2        /* b^n        [n_faces] */
+#define PIC_FIELD_B 2        /* b^n        [n_faces], self-consistent part: the uniform
+                                external b0 of the config is added at the particles */
 #define PIC_FIELD_B_PREV 3   /* b^{n-1}    [n_faces] */
 #define PIC_FIELD_G 4        /* Gbar^n     [n_edges] */
 #define PIC_FIELD_G_PREV 5   /* Gbar^{n-1} [n_edges] */
@@ -112,15 +113,16 @@ typedef struct {
  * volume), derives edges, faces, incidence G/C/D (checking C G = 0 and
  * D C = 0), tet adjacency, wall entities (faces with one tet), the Hodge
  * matrices [*eps], [*mu^-1], the curl-curl matrix [*S] = C^T [*mu^-1] C and
- * the node Laplacian G^T [*eps] G, and uploads everything to the current
- * device.  Errors: PIC_ERR_INVALID_ARG (NULL or negative sizes),
+ * the node Laplacian G^T [*eps] G.  Host work only: the device copy is made
+ * by the first pic_sim_create on the mesh (on the current device).  Errors: PIC_ERR_INVALID_ARG (NULL or negative sizes),
  * PIC_ERR_MESH (degenerate or non-manifold tets, incidence mismatch),
  * PIC_ERR_OOM, PIC_ERR_CUDA. */
 int pic_mesh_create(const pic_mesh_desc *desc, pic_mesh **out);
 void pic_mesh_destroy(pic_mesh *mesh);
 
-/* counts[0..5] = n_nodes, n_edges, n_faces, n_tets, n_interior_edges,
- * n_interior_nodes */
+/* counts[0..7] = n_nodes, n_edges, n_faces, n_tets, n_interior_edges,
+ * n_interior_nodes, nonzeros of the Newmark matrix on interior edges,
+ * nonzeros of the node Laplacian on interior nodes */
 int pic_mesh_info(const pic_mesh *mesh, int64_t *counts);
 
 /* Canonical entities: edges [2*n_edges], faces [3*n_faces] (host memory;
@@ -147,10 +149,13 @@ typedef struct {
     double rho_background;   /* uniform static charge density (C/m^3) */
     double cg_tol;           /* relative residual of the Newmark solve (1e-10) */
     int32_t cg_max_iters;    /* (10000) */
-    double init_tol;         /* relative residual of the Laplacian solves (1e-14) */
+    double init_tol;         /* relative residual of the initial electrostatic solve (1e-14) */
+    double completion_tol;   /* the gradient-subspace completion of each Newmark solve stops
+                                when its defect is <= completion_tol * max|rho + wall| (1e-16) */
     int32_t walk_cap;        /* max tets one particle visits in one step (64) */
     int32_t cg_check_every;  /* CG iterations between host convergence checks (16) */
     int32_t max_species;     /* species slots (4) */
+    int32_t profile;         /* 1: time the phases of every step with CUDA events (0) */
     void *stream;            /* cudaStream_t to run on; NULL = default stream */
 } pic_config;
 
@@ -174,8 +179,9 @@ int pic_particles_load(pic_sim *sim, int32_t species, double q, double m, double
                        const double *x, const double *v, const int32_t *tet_hint, int32_t on_device);
 
 /* Initial state (Sec. III.A asks only that the integrator remember the
- * initial conditions; this is the library's start-up): b^0 = b^{-1} = flux
- * of b0; rho^0 from the particles; (G^T M G) phi = rho^0 + rho_bg on interior
+ * initial conditions; this is the library's start-up): b^0 = b^{-1} = 0
+ * (the uniform b0 is a static solution and is added at the particles);
+ * rho^0 from the particles; (G^T M G) phi = rho^0 + rho_bg on interior
  * nodes, e^0 = e^{-1} = -G phi; Gbar^0 = Gbar^{-1} = 0. */
 int pic_sim_init(pic_sim *sim);
 
@@ -228,6 +234,27 @@ typedef struct {
 
 /* Diagnostics of the last step (Sec. III.A conservation laws).  Synchronises. */
 int pic_diagnostics_get(pic_sim *sim, pic_diag *out);
+
+/* Phases of a step timed when pic_config.profile is set (device time from
+ * CUDA events on the simulation's stream). */
+#define PIC_PHASE_SORT 0        /* radix sort of the particles by tet */
+#define PIC_PHASE_COEF 1        /* per-tet Whitney coefficients */
+#define PIC_PHASE_PUSH 2        /* the fused gather/push/walk/deposit kernel */
+#define PIC_PHASE_DEPOSIT 3     /* spanning runs, crossing records, edge/node reduction */
+#define PIC_PHASE_RHS 4         /* Newmark right-hand side */
+#define PIC_PHASE_CG 5          /* PCG on the Newmark system */
+#define PIC_PHASE_COMPLETION 6  /* gradient-subspace completion (Laplacian PCG) */
+#define PIC_PHASE_FIELD_OTHER 7 /* Faraday update and diagnostics */
+#define PIC_PHASE_SPMV 8        /* each SpMV kernel of the Newmark PCG (per launch) */
+#define PIC_PHASE_COUNT 9
+
+/* Accumulated milliseconds and sample counts per phase, arrays of
+ * PIC_PHASE_COUNT (host memory). */
+int pic_profile_get(pic_sim *sim, double *ms, int64_t *count);
+int pic_profile_reset(pic_sim *sim);
+
+/* Number of kernels the library has launched in this process. */
+int64_t pic_launch_count(void);
 
 /* Waits for all work of the simulation. */
 int pic_sim_synchronize(pic_sim *sim);

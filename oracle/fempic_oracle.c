@@ -596,6 +596,7 @@ struct orc_sim {
     double *diagA;                  /* diag of A = M + dt^2/4 K */
     csr A;
     int step;
+    int last_completion_iters;
     orc_diag diag;
     char err[256];
 };
@@ -692,10 +693,11 @@ static double vdot(const double *a, const double *b, int n) {
     return s;
 }
 
-/* Jacobi-preconditioned CG on the interior DOFs; stops when
- * ||b - A x||_2 <= tol ||b||_2 (checked before every iteration) */
+/* Jacobi-preconditioned CG on the interior DOFs; stops (checked before every
+ * iteration) when ||b - A x||_2 <= tol ||b||_2, or, if abs_inf > 0, when
+ * max_i |b - A x|_i <= abs_inf */
 static int pcg(const csr *A, const double *dA, const int *bnd, const double *b, double *x, int n,
-               double tol, int max_iters, int *iters, double *relres) {
+               double tol, int max_iters, int *iters, double *relres, double abs_inf) {
     double *r = calloc(n, 8), *z = calloc(n, 8), *p = calloc(n, 8), *q = calloc(n, 8), *tmp = calloc(n, 8);
     double *bm = calloc(n, 8);
     for (int i = 0; i < n; i++) { bm[i] = bnd[i] ? 0.0 : b[i]; if (bnd[i]) x[i] = 0.0; }
@@ -711,7 +713,13 @@ static int pcg(const csr *A, const double *dA, const int *bnd, const double *b, 
     for (int i = 0; i < n; i++) { r[i] = bm[i] - q[i]; z[i] = bnd[i] ? 0.0 : r[i] / dA[i]; p[i] = z[i]; }
     double rz = vdot(r, z, n);
     double rnorm = sqrt(vdot(r, r, n));
-    while (rnorm > tol * bnorm) {
+    for (;;) {
+        if (abs_inf > 0.0) {
+            double rmax = 0.0;
+            for (int i = 0; i < n; i++) if (fabs(r[i]) > rmax) rmax = fabs(r[i]);
+            if (rmax <= abs_inf) break;
+        }
+        if (rnorm <= tol * bnorm) break;
         if (it >= max_iters) { rc = ORC_ERR_CG; break; }
         masked_matvec(A, bnd, p, q, tmp, n);
         double alpha = rz / vdot(p, q, n);
@@ -730,7 +738,6 @@ static int pcg(const csr *A, const double *dA, const int *bnd, const double *b, 
 }
 
 static void compute_diag(orc_sim *s, int cg_iters, double cg_relres);
-
 /* Completion of the Newmark solve on the gradient subspace.  The part of the
  * residual that the divergence sees is d = G_int^T (b - A x).  Because
  * G^T K = 0 and G^T C^T = 0 it equals, for the wave-equation form,
@@ -741,8 +748,9 @@ static void compute_diag(orc_sim *s, int cg_iters, double cg_relres);
  * A CG stopped at a relative residual leaves d at the tolerance, and the
  * Gauss residual then drifts by d every step (Sec. III.A: errors of the
  * linear solve).  Solving (G^T M G) psi = d on interior nodes and adding
- * G psi removes it, since A G psi = M G psi.  Only the solve's own residual
- * enters; the charge does not. */
+ * G psi removes it, since A G psi = M G psi.  The correction uses only the
+ * solve's own defect; the node charge sets just the stopping threshold of
+ * this small solve (max|d - L psi| <= completion_tol * max|rho + wall|). */
 static int gradient_completion(orc_sim *s, const double *b, const double *gn1, double *x, double *relres) {
     orc_mesh *m = s->m;
     int ne = m->n_edges, nn = m->n_nodes;
@@ -764,7 +772,17 @@ static int gradient_completion(orc_sim *s, const double *b, const double *gn1, d
         for (int k = m->L.rowptr[q]; k < m->L.rowptr[q + 1]; k++)
             if (m->L.col[k] == q) dL[q] = m->L.val[k];
     int it; double rr;
-    int rc = pcg(&m->L, dL, m->node_bnd, d, psi, nn, s->cfg.init_tol, 100000, &it, &rr);
+    /* stop when the defect left is below completion_tol * max|rho + wall| */
+    double qmax = 0.0;
+    for (int q = 0; q < nn; q++) {
+        double v = fabs(s->rho[q] + s->wall[q]);
+        if (v > qmax) qmax = v;
+    }
+    /* (without any charge the threshold falls back to the relative init_tol) */
+    const int absolute = s->cfg.completion_tol > 0 && qmax > 0;
+    int rc = pcg(&m->L, dL, m->node_bnd, d, psi, nn, absolute ? 0.0 : s->cfg.init_tol, 100000, &it, &rr,
+                 absolute ? s->cfg.completion_tol * qmax : 0.0);
+    s->last_completion_iters = it;
     if (rc) snprintf(s->err, sizeof s->err, "gradient completion did not converge");
     for (int e = 0; e < ne; e++)
         if (!m->edge_bnd[e]) x[e] += psi[m->edge[2 * e + 1]] - psi[m->edge[2 * e]];
@@ -783,21 +801,17 @@ static int gradient_completion(orc_sim *s, const double *b, const double *gn1, d
 
 /* Initial state (the paper leaves start-up open; Sec. III.A only asks that the
  * integrator remember the initial conditions):
- *   b^0 = b^{-1} = flux of the uniform B0 through every face;
+ *   b^0 = b^{-1} = 0: the face DOFs carry the self-consistent field only; the
+ *   uniform external B0 is a static solution of both Newmark forms and is
+ *   added to B at the particle (kept out of the DOFs, where C^T H b0 = 0
+ *   would only appear as cancellation noise in the Maxwell-solver update);
  *   rho^0 from the particles, then the electrostatic solve
  *   (G^T M G) phi = rho^0 + rho_bg on interior nodes, e^0 = e^{-1} = -G phi;
  *   Gbar^0 = Gbar^{-1} = 0. */
 int orc_init(orc_sim *s) {
     orc_mesh *m = s->m;
     int nn = m->n_nodes, ne = m->n_edges;
-    for (int f = 0; f < m->n_faces; f++) {
-        const double *xa = m->xyz + 3 * m->face[3 * f], *xb = m->xyz + 3 * m->face[3 * f + 1];
-        const double *xc = m->xyz + 3 * m->face[3 * f + 2];
-        double u[3], w[3], a[3];
-        sub3(xb, xa, u); sub3(xc, xa, w); cross3(u, w, a);
-        s->b[f] = 0.5 * dot3(s->cfg.b0, a);
-        s->b_prev[f] = s->b[f];
-    }
+    for (int f = 0; f < m->n_faces; f++) s->b[f] = s->b_prev[f] = 0.0;
     /* rho_bg,n = int lam_n rho_background = rho_background * sum_{T ni n} V_T / 4 */
     memset(s->rho_bg, 0, sizeof(double) * nn);
     for (int t = 0; t < m->n_tets; t++)
@@ -813,7 +827,7 @@ int orc_init(orc_sim *s) {
             if (m->L.col[k] == r) dL[r] = m->L.val[k];
     memset(s->phi, 0, sizeof(double) * nn);
     int it; double rr;
-    int rc = pcg(&m->L, dL, m->node_bnd, rhs, s->phi, nn, s->cfg.init_tol, 100000, &it, &rr);
+    int rc = pcg(&m->L, dL, m->node_bnd, rhs, s->phi, nn, s->cfg.init_tol, 100000, &it, &rr, 0.0);
     free(rhs); free(dL);
     if (rc) { snprintf(s->err, sizeof s->err, "initial electrostatic solve did not converge"); return rc; }
     for (int e = 0; e < ne; e++) {
@@ -850,6 +864,7 @@ static int move_particle(orc_sim *s, int p) {
     double *r = s->x + 3 * p, *v = s->v + 3 * p;
     double E[3], B[3];
     orc_gather(m, t, r, s->e, s->b, E, B);
+    for (int d = 0; d < 3; d++) B[d] += s->cfg.b0[d];   /* uniform external field */
     double qm = s->q[p] / s->mass[p], dt = s->cfg.dt;
     double Q[3];
     if (s->cfg.pusher == ORC_PUSH_BORIS) {
@@ -965,9 +980,21 @@ int orc_step(orc_sim *s) {
     /* initial guess 2 e^n - e^{n-1} */
     for (int i = 0; i < ne; i++) x[i] = 2.0 * s->e[i] - s->e_prev[i];
     int it; double rr;
-    rc = pcg(&s->A, s->diagA, m->edge_bnd, rhs, x, ne, s->cfg.cg_tol, s->cfg.cg_max_iters, &it, &rr);
+    rc = pcg(&s->A, s->diagA, m->edge_bnd, rhs, x, ne, s->cfg.cg_tol, s->cfg.cg_max_iters, &it, &rr, 0.0);
     if (rc) snprintf(s->err, sizeof s->err, "Newmark solve did not converge");
-    else rc = gradient_completion(s, rhs, gn1, x, &rr);
+    else if (s->cfg.gradient_completion) rc = gradient_completion(s, rhs, gn1, x, &rr);
+    else {
+        /* report the true relative residual */
+        double *ax = calloc(ne, 8), *tmp2 = calloc(ne, 8), bn = 0.0, rn = 0.0;
+        masked_matvec(&s->A, m->edge_bnd, x, ax, tmp2, ne);
+        for (int e = 0; e < ne; e++) {
+            if (m->edge_bnd[e]) continue;
+            bn += rhs[e] * rhs[e];
+            rn += (rhs[e] - ax[e]) * (rhs[e] - ax[e]);
+        }
+        rr = bn > 0 ? sqrt(rn / bn) : 0.0;
+        free(ax); free(tmp2);
+    }
     /* magnetic update */
     int *cr = malloc(sizeof(int) * 3 * nf), *cc = malloc(sizeof(int) * 3 * nf), *cv = malloc(sizeof(int) * 3 * nf);
     orc_mesh_C(m, cr, cc, cv);

@@ -56,6 +56,8 @@ typedef struct {
     double init_tol;     /* relative residual for the initial electrostatic solve */
     double rho_background; /* uniform static charge density (C/m^3) */
     int walk_cap;        /* max tets visited by one particle in one step */
+    int gradient_completion; /* 1: complete the solve on the gradient subspace */
+    double completion_tol;   /* completion stops when max|defect| <= this * max|rho+wall| (0: relative init_tol) */
 } orc_config;
 
 /* diagnostics record, all FP64 */

@@ -50,7 +50,8 @@ class _Diag(C.Structure):
 class _Config(C.Structure):
     _fields_ = [("form", C.c_int), ("pusher", C.c_int), ("dt", C.c_double), ("b0", C.c_double * 3),
                 ("cg_tol", C.c_double), ("cg_max_iters", C.c_int), ("init_tol", C.c_double),
-                ("rho_background", C.c_double), ("walk_cap", C.c_int)]
+                ("rho_background", C.c_double), ("walk_cap", C.c_int),
+                ("gradient_completion", C.c_int), ("completion_tol", C.c_double)]
 
 
 def _load():
@@ -259,6 +260,8 @@ class OracleConfig:
     init_tol: float = 1e-14
     rho_background: float = 0.0
     walk_cap: int = 64
+    gradient_completion: bool = True
+    completion_tol: float = 1e-16
 
     def to_c(self) -> _Config:
         c = _Config()
@@ -272,6 +275,8 @@ class OracleConfig:
         c.init_tol = self.init_tol
         c.rho_background = self.rho_background
         c.walk_cap = self.walk_cap
+        c.gradient_completion = int(self.gradient_completion)
+        c.completion_tol = self.completion_tol
         return c
 
 
@@ -340,11 +345,13 @@ class OracleSim:
 
 
 def from_workload(wl, dt: float, cg_tol: float = 1e-10, init_tol: float = 1e-14,
-                  mesh: Optional[OracleMesh] = None) -> OracleSim:
+                  mesh: Optional[OracleMesh] = None, gradient_completion: bool = True,
+                  completion_tol: float = 1e-16) -> OracleSim:
     """Oracle simulation of a ``workloads.Workload`` with the given dt."""
     mesh = mesh or OracleMesh(wl.mesh.xyz, wl.mesh.tets)
     cfg = OracleConfig(dt=dt, form=wl.form, pusher=wl.pusher, b0=wl.b0, cg_tol=cg_tol,
-                       init_tol=init_tol, rho_background=wl.rho_background)
+                       init_tol=init_tol, rho_background=wl.rho_background,
+                       gradient_completion=gradient_completion, completion_tol=completion_tol)
     sim = OracleSim(mesh, cfg)
     for sp in wl.species:
         sim.add_species(sp.q, sp.m, sp.w, sp.x, sp.v, sp.tet)

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -13,8 +14,36 @@
 namespace fp {
 
 static thread_local std::string g_err;
+static std::atomic<long long> g_launches{0};
 
 void set_error(const std::string &msg) { g_err = msg; }
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void prof_begin(Sim *s, int ph) {
+    if (!s->profile) return;
+    if (!s->ev0[ph]) {
+        cudaEventCreate(&s->ev0[ph]);
+        cudaEventCreate(&s->ev1[ph]);
+    }
+    cudaEventRecord(s->ev0[ph], s->stream);
+}
+void prof_end(Sim *s, int ph) {
+    if (!s->profile) return;
+    cudaEventRecord(s->ev1[ph], s->stream);
+    s->ev_used[ph] = true;
+}
+void prof_collect(Sim *s) {
+    if (!s->profile) return;
+    for (int ph = 0; ph < PH_COUNT; ph++) {
+        if (!s->ev_used[ph]) continue;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, s->ev0[ph], s->ev1[ph]) == cudaSuccess) {
+            s->prof_ms[ph] += ms;
+            s->prof_n[ph] += 1;
+        }
+        s->ev_used[ph] = false;
+    }
+}
 
 int cuda_fail(cudaError_t e, const char *what) {
     g_err = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
@@ -73,14 +102,30 @@ int check_status(Sim *s) {
 
 int one_step(Sim *s, bool fields) {
     int rc;
+    prof_begin(s, PH_SORT);
     if ((rc = sort_particles(s))) return rc;
+    prof_end(s, PH_SORT);
+    prof_begin(s, PH_COEF);
     if ((rc = stage_coefficients(s, s->e.p, s->b.p))) return rc;
-    if ((rc = particle_push(s, 0))) return rc;
+    prof_end(s, PH_COEF);
+    if ((rc = particle_push(s, 0))) return rc;        // records PH_PUSH and opens PH_DEPOSIT
     if ((rc = reduce_to_entities(s))) return rc;
-    if (!fields) return read_control(s);
+    prof_end(s, PH_DEPOSIT);
+    if (!fields) {
+        rc = read_control(s);
+        prof_collect(s);
+        return rc;
+    }
+    prof_begin(s, PH_RHS);
     if ((rc = newmark_rhs(s))) return rc;
+    prof_end(s, PH_RHS);
+    prof_begin(s, PH_CG);
     if ((rc = pcg_newmark(s))) return rc;
+    prof_end(s, PH_CG);
+    prof_begin(s, PH_COMPLETION);
     if ((rc = gradient_completion(s))) return rc;
+    prof_end(s, PH_COMPLETION);
+    prof_begin(s, PH_FIELD_OTHER);
     if ((rc = faraday_update(s))) return rc;
     // rotate the three time levels
     std::swap(s->e_prev, s->e);   // e_prev <- e^n
@@ -90,8 +135,11 @@ int one_step(Sim *s, bool fields) {
     std::swap(s->b_prev, s->b);
     std::swap(s->b, s->b_new);
     if ((rc = compute_diagnostics(s))) return rc;
+    prof_end(s, PH_FIELD_OTHER);
     s->step++;
-    return read_control(s);
+    rc = read_control(s);
+    prof_collect(s);
+    return rc;
 }
 
 }  // namespace
@@ -143,6 +191,8 @@ int pic_mesh_info(const pic_mesh *mesh, int64_t *c) {
     c[3] = m.n_tets;
     c[4] = m.n_int_edges;
     c[5] = m.n_int_nodes;
+    c[6] = m.nnz_A;
+    c[7] = m.nnz_L;
     return PIC_OK;
 }
 
@@ -174,6 +224,7 @@ void pic_config_default(pic_config *c) {
     c->cg_tol = 1e-10;
     c->cg_max_iters = 10000;
     c->init_tol = 1e-14;
+    c->completion_tol = 1e-16;
     c->walk_cap = 63;
     c->cg_check_every = 16;
     c->max_species = kMaxSpecies;
@@ -187,7 +238,8 @@ int pic_sim_create(const pic_mesh *mesh, const pic_config *cfg, pic_sim **out) {
     *out = nullptr;
     if (!(cfg->dt > 0) || (cfg->form != PIC_FORM_WE && cfg->form != PIC_FORM_MFEM) || cfg->pusher < 0 ||
         cfg->pusher > 5 || (cfg->precision != PIC_PRECISION_PLAIN && cfg->precision != PIC_PRECISION_MIXED) ||
-        !(cfg->cg_tol > 0) || cfg->cg_max_iters <= 0 || !(cfg->init_tol > 0) || cfg->walk_cap <= 0 ||
+        !(cfg->cg_tol > 0) || cfg->cg_max_iters <= 0 || !(cfg->init_tol > 0) || !(cfg->completion_tol > 0) ||
+        cfg->walk_cap <= 0 ||
         cfg->walk_cap > kMaxWalk || cfg->preconditioner != PIC_PRECOND_JACOBI) {
         set_error("pic_sim_create: invalid configuration (dt > 0, form WE/MFEM, pusher 0..5, precision, tolerances, "
                   "walk_cap 1..63, Jacobi preconditioner)");
@@ -211,6 +263,7 @@ int pic_sim_create(const pic_mesh *mesh, const pic_config *cfg, pic_sim **out) {
     s->rsize = s->mixed ? 4 : 8;
     s->ab = cfg->pusher;
     s->hist_levels = s->ab > 1 ? s->ab - 1 : 0;
+    s->profile = cfg->profile != 0;
     int rc;
     const Mesh *m = s->mesh;
     Control *hc = nullptr;
@@ -238,6 +291,11 @@ void pic_sim_destroy(pic_sim *sim) {
     if (!sim) return;
     if (sim->s.stream) cudaStreamSynchronize(sim->s.stream);
     else cudaDeviceSynchronize();
+    for (int ph = 0; ph < PH_COUNT; ph++) {
+        if (sim->s.ev0[ph]) cudaEventDestroy(sim->s.ev0[ph]);
+        if (sim->s.ev1[ph]) cudaEventDestroy(sim->s.ev1[ph]);
+    }
+    for (cudaEvent_t ev : sim->s.spmv_ev) cudaEventDestroy(ev);
     if (sim->s.hctl) cudaFreeHost(sim->s.hctl);
     sim->s.hctl = nullptr;
     delete sim;
@@ -322,23 +380,14 @@ int pic_sim_init(pic_sim *sim) {
     }
     const Mesh *m = s->mesh;
     int rc;
-    // static data: flux of the uniform B0 through every face and the background node charge
-    std::vector<double> b0(m->n_faces), bg(m->n_nodes, 0.0);
-    for (int f = 0; f < m->n_faces; f++) {
-        const double *xa = &m->h_xyz[3 * m->h_faces[3 * f]], *xb = &m->h_xyz[3 * m->h_faces[3 * f + 1]];
-        const double *xc = &m->h_xyz[3 * m->h_faces[3 * f + 2]];
-        double u[3], w[3];
-        for (int i = 0; i < 3; i++) {
-            u[i] = xb[i] - xa[i];
-            w[i] = xc[i] - xa[i];
-        }
-        const double a[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
-        b0[f] = 0.5 * (s->cfg.b0[0] * a[0] + s->cfg.b0[1] * a[1] + s->cfg.b0[2] * a[2]);
-    }
+    // static data: the background node charge int lam_n rho_bg.  The face DOFs
+    // start at zero: they carry the self-consistent field, and the uniform
+    // external b0 is added to B in the coefficient staging.
+    std::vector<double> bg(m->n_nodes, 0.0);
     for (int t = 0; t < m->n_tets; t++)
         for (int k = 0; k < 4; k++) bg[m->h_tet_sorted[4 * (size_t)t + k]] += s->cfg.rho_background * m->h_vol[t] / 4.0;
-    FP_CUDA(cudaMemcpy(s->b.p, b0.data(), sizeof(double) * m->n_faces, cudaMemcpyHostToDevice));
-    FP_CUDA(cudaMemcpy(s->b_prev.p, b0.data(), sizeof(double) * m->n_faces, cudaMemcpyHostToDevice));
+    FP_CUDA(cudaMemset(s->b.p, 0, sizeof(double) * m->n_faces));
+    FP_CUDA(cudaMemset(s->b_prev.p, 0, sizeof(double) * m->n_faces));
     FP_CUDA(cudaMemcpy(s->rho_bg.p, bg.data(), sizeof(double) * m->n_nodes, cudaMemcpyHostToDevice));
     if ((rc = upload_particles(s))) return rc;
     // rho^0: charge-only pass over the sorted particles
@@ -380,11 +429,11 @@ int pic_set_ab_history(pic_sim *sim, int32_t levels, const double *a_hist, const
     const int n = s->n_total;
     if (n > 0 && levels > 0) {
         if (s->mixed)
-            k_set_history<float><<<(n + 255) / 256, 256, 0, s->stream>>>(n, (long)s->cap, levels, np, k.id.p, da.p,
-                                                                          dv.p, (float *)k.ah.p, (float *)k.vh.p);
+            { k_set_history<float><<<(n + 255) / 256, 256, 0, s->stream>>>(n, (long)s->cap, levels, np, k.id.p, da.p,
+                                                                          dv.p, (float *)k.ah.p, (float *)k.vh.p); note_launch(); }
         else
-            k_set_history<double><<<(n + 255) / 256, 256, 0, s->stream>>>(n, (long)s->cap, levels, np, k.id.p, da.p,
-                                                                           dv.p, (double *)k.ah.p, (double *)k.vh.p);
+            { k_set_history<double><<<(n + 255) / 256, 256, 0, s->stream>>>(n, (long)s->cap, levels, np, k.id.p, da.p,
+                                                                           dv.p, (double *)k.ah.p, (double *)k.vh.p); note_launch(); }
         FP_CUDA(cudaGetLastError());
     }
     FP_CUDA(cudaStreamSynchronize(s->stream));
@@ -455,13 +504,13 @@ int pic_field_get(pic_sim *sim, int32_t which, double *out, int64_t n, int32_t o
     int rc;
     if (edge) {
         if (on_device) {
-            k_edges_to_canonical<<<(m->n_edges + 255) / 256, 256, 0, s->stream>>>(m->n_edges, m->edge_canon.p, src, out);
+            { k_edges_to_canonical<<<(m->n_edges + 255) / 256, 256, 0, s->stream>>>(m->n_edges, m->edge_canon.p, src, out); note_launch(); }
             FP_CUDA(cudaGetLastError());
             FP_CUDA(cudaStreamSynchronize(s->stream));
             return PIC_OK;
         }
         if ((rc = tmp.alloc(len))) return rc;
-        k_edges_to_canonical<<<(m->n_edges + 255) / 256, 256, 0, s->stream>>>(m->n_edges, m->edge_canon.p, src, tmp.p);
+        { k_edges_to_canonical<<<(m->n_edges + 255) / 256, 256, 0, s->stream>>>(m->n_edges, m->edge_canon.p, src, tmp.p); note_launch(); }
         FP_CUDA(cudaGetLastError());
         dev = tmp.p;
     }
@@ -506,8 +555,8 @@ int pic_field_set(pic_sim *sim, int32_t which, const double *in, int64_t n, int3
         dev = tmp.p;
     }
     if (edge) {
-        k_edges_from_canonical<<<(m->n_edges + 255) / 256, 256, 0, s->stream>>>(m->n_edges, m->n_int_edges, zero_wall,
-                                                                                m->edge_canon.p, dev, dst);
+        { k_edges_from_canonical<<<(m->n_edges + 255) / 256, 256, 0, s->stream>>>(m->n_edges, m->n_int_edges, zero_wall,
+                                                                                m->edge_canon.p, dev, dst); note_launch(); }
         FP_CUDA(cudaGetLastError());
     } else {
         FP_CUDA(cudaMemcpyAsync(dst, dev, sizeof(double) * len, cudaMemcpyDeviceToDevice, s->stream));
@@ -607,6 +656,32 @@ int pic_diagnostics_get(pic_sim *sim, pic_diag *out) {
     out->energy_b = c.diag.energy_b;
     out->energy_k = c.diag.energy_k;
     out->status = (double)(c.status | s->host_status);
+    return PIC_OK;
+}
+
+int64_t pic_launch_count(void) { return (int64_t)g_launches.load(); }
+
+int pic_profile_get(pic_sim *sim, double *ms, int64_t *count) {
+    if (!sim || !ms || !count) {
+        set_error("pic_profile_get: NULL argument");
+        return PIC_ERR_INVALID_ARG;
+    }
+    for (int ph = 0; ph < PH_COUNT; ph++) {
+        ms[ph] = sim->s.prof_ms[ph];
+        count[ph] = sim->s.prof_n[ph];
+    }
+    return PIC_OK;
+}
+
+int pic_profile_reset(pic_sim *sim) {
+    if (!sim) {
+        set_error("pic_profile_reset: NULL sim");
+        return PIC_ERR_INVALID_ARG;
+    }
+    for (int ph = 0; ph < PH_COUNT; ph++) {
+        sim->s.prof_ms[ph] = 0.0;
+        sim->s.prof_n[ph] = 0;
+    }
     return PIC_OK;
 }
 

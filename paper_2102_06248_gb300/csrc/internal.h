@@ -28,6 +28,7 @@ enum : uint32_t {
 };
 
 void set_error(const std::string &msg);
+void note_launch();   // counts the library's kernel launches (pic_launch_count)
 int cuda_fail(cudaError_t e, const char *what);
 
 #define FP_CUDA(call)                                     \
@@ -36,10 +37,29 @@ int cuda_fail(cudaError_t e, const char *what);
         if (e_ != cudaSuccess) return fp::cuda_fail(e_, #call); \
     } while (0)
 
+// Owning device buffer.  Move-only: std::swap exchanges ownership (the
+// time levels of the fields rotate this way), copies are not allowed.
 template <typename T>
 struct DevBuf {
     T *p = nullptr;
     size_t n = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    DevBuf(DevBuf &&o) noexcept : p(o.p), n(o.n) {
+        o.p = nullptr;
+        o.n = 0;
+    }
+    DevBuf &operator=(DevBuf &&o) noexcept {
+        if (this != &o) {
+            free();
+            p = o.p;
+            n = o.n;
+            o.p = nullptr;
+            o.n = 0;
+        }
+        return *this;
+    }
     int alloc(size_t count) {
         free();
         n = count;
@@ -94,6 +114,7 @@ struct HostStage {
 // orientation, so no sign tables are needed.
 struct Mesh {
     int n_nodes = 0, n_edges = 0, n_faces = 0, n_tets = 0, n_int_edges = 0, n_int_nodes = 0;
+    long long nnz_A = 0, nnz_L = 0;   // nonzeros of the Newmark matrix and of the node Laplacian
     // host copies needed by the API
     std::vector<int> h_edges;        // canonical (tail, head)
     std::vector<int> h_faces;        // canonical (a, b, c)
@@ -108,6 +129,7 @@ struct Mesh {
 
     // per tet
     DevBuf<double> geo;        // 12 per tet: x0, grad lam_1, grad lam_2, grad lam_3
+    DevBuf<float> geo32;       // the same maps rounded to FP32 (MIXED precision)
     DevBuf<int4> tet_nodes;    // sorted node ids
     DevBuf<int4> tet_nbr;      // tet across the face opposite local vertex k, -1 on the wall
     DevBuf<int> tet_edge;      // 6 per tet: internal edge id of local edge k

@@ -437,6 +437,8 @@ int build_mesh(const pic_mesh_desc *d, Mesh *m) {
     }
     H.geo = std::move(geo);
     H.tet_edge = std::move(tet_edge);
+    m->nnz_A = (long long)pa.col.size();
+    m->nnz_L = (long long)pl.col.size();
     H.A = {std::move(pa.rowptr), std::move(pa.col)};
     H.M_val = std::move(Mv);
     H.K_val = std::move(Kv);
@@ -463,7 +465,9 @@ int mesh_upload(Mesh *m) {
         return d->col.upload(h.col);
     };
     int rc;
-    if ((rc = m->geo.upload(H.geo)) || (rc = m->tet_nodes.upload(H.tet_nodes)) || (rc = m->tet_nbr.upload(H.tet_nbr)) ||
+    std::vector<float> g32(H.geo.begin(), H.geo.end());
+    if ((rc = m->geo.upload(H.geo)) || (rc = m->geo32.upload(g32)) || (rc = m->tet_nodes.upload(H.tet_nodes)) ||
+        (rc = m->tet_nbr.upload(H.tet_nbr)) ||
         (rc = m->tet_edge.upload(H.tet_edge)) || (rc = m->tet_face.upload(H.tet_face)) ||
         (rc = m->tet_sign.upload(m->h_tet_sign)) || (rc = m->tet_vol.upload(m->h_vol)) || (rc = m->xyz.upload(m->h_xyz)))
         return rc;

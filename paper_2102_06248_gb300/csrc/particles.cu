@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <type_traits>
 
 #include "sim.h"
 
@@ -164,9 +165,9 @@ int scan_exclusive(cudaStream_t st, uint32_t *a, long len, SortWork *w) {
         set_error("radix sort: too many tiles for the scan");
         return PIC_ERR_INVALID_ARG;
     }
-    k_scan_reduce<<<(unsigned)chunks, 256, 0, st>>>(a, len, w->chunk.p);
-    k_scan_top<<<1, 256, 0, st>>>(w->chunk.p, (int)chunks);
-    k_scan_apply<<<(unsigned)chunks, 256, 0, st>>>(a, len, w->chunk.p);
+    { k_scan_reduce<<<(unsigned)chunks, 256, 0, st>>>(a, len, w->chunk.p); note_launch(); }
+    { k_scan_top<<<1, 256, 0, st>>>(w->chunk.p, (int)chunks); note_launch(); }
+    { k_scan_apply<<<(unsigned)chunks, 256, 0, st>>>(a, len, w->chunk.p); note_launch(); }
     return PIC_OK;
 }
 
@@ -195,11 +196,11 @@ int radix_sort(cudaStream_t st, const K *keys_in, K *ka, uint32_t *va, K *kb, ui
     K *dk = ka;
     uint32_t *dv = va;
     for (int p = 0; p < passes; p++) {
-        k_radix_hist<K><<<tiles, kSortThreads, 0, st>>>(src_k, d_n, (int)n_cap, 8 * p, w->hist.p, tiles);
+        { k_radix_hist<K><<<tiles, kSortThreads, 0, st>>>(src_k, d_n, (int)n_cap, 8 * p, w->hist.p, tiles); note_launch(); }
         rc = scan_exclusive(st, w->hist.p, 256L * tiles, w);
         if (rc) return rc;
-        k_radix_scatter<K><<<tiles, kSortThreads, 0, st>>>(src_k, src_v, dk, dv, d_n, (int)n_cap, 8 * p, w->hist.p,
-                                                          tiles);
+        { k_radix_scatter<K><<<tiles, kSortThreads, 0, st>>>(src_k, src_v, dk, dv, d_n, (int)n_cap, 8 * p, w->hist.p,
+                                                          tiles); note_launch(); }
         src_k = dk;
         src_v = dv;
         if (dk == ka) {
@@ -229,14 +230,15 @@ int bitlen(unsigned long long x) {
 //   E(r) = E0 + Omega x d,   Omega = sum_{edges (i,j)} e_ij grad lam_i x grad lam_j,
 //   B(r) = B0 + beta d,      from W2_k = D_k (r - x_k) / (3V),
 // where E0 = e_01 g1 + e_02 g2 + e_03 g3, B0 = sum_k D_k b_k (x0 - x_k) / (3V)
-// and beta = (D b)_t / (3V) (zero up to rounding).
+// and beta = (D b)_t / (3V) (zero up to rounding).  The uniform external field
+// b0 is added to B0 here; the face DOFs hold the self-consistent part only.
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(256) k_coefficients(int nt, const double *__restrict__ geo, const int *__restrict__ tet_edge,
                                                       const int4 *__restrict__ tet_face, const int4 *__restrict__ tet_nodes,
                                                       const signed char *__restrict__ tet_sign, const double *__restrict__ vol,
                                                       const double *__restrict__ xyz, const double *__restrict__ e,
-                                                      const double *__restrict__ b, R *__restrict__ coef) {
+                                                      const double *__restrict__ b, double3 b_ext, R *__restrict__ coef) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
     const double *gp = geo + 12 * (size_t)t;
@@ -272,10 +274,11 @@ __global__ void __launch_bounds__(256) k_coefficients(int nt, const double *__re
         for (int i = 0; i < 3; i++) B0[i] += Dk * bv[k] * (gp[i] - xyz[3 * (size_t)nid[k] + i]);
     }
     R *c = coef + 10 * (size_t)t;
+    const double bx[3] = {b_ext.x, b_ext.y, b_ext.z};
     for (int i = 0; i < 3; i++) {
         c[i] = (R)E0[i];
         c[3 + i] = (R)Om[i];
-        c[6 + i] = (R)(B0[i] * inv3v);
+        c[6 + i] = (R)(B0[i] * inv3v + bx[i]);
     }
     c[9] = (R)(divb * inv3v);
 }
@@ -283,7 +286,16 @@ __global__ void __launch_bounds__(256) k_coefficients(int nt, const double *__re
 // ---------------------------------------------------------------------------
 // fused gather -> push -> walk -> deposit
 // ---------------------------------------------------------------------------
-template <typename R>
+// Deposit values: FP64 (PLAIN) or fixed point in int64 (MIXED).  In MIXED the
+// barycentrics of every path end point are 24-bit fixed point that sum to
+// exactly 2^24, so the exact Whitney-1 integral lam_i(S) lam_j(E) -
+// lam_i(E) lam_j(S) is an exact int64 (scale 2^48) and the node charge an exact
+// integer (scale 2^24): discrete continuity then holds exactly in integers.
+constexpr int kFixOne = 1 << 24;
+constexpr double kFixNode = 1.0 / 16777216.0;                  // 2^-24
+constexpr double kFixEdge = 1.0 / 281474976710656.0;           // 2^-48
+
+template <typename R, typename V>
 struct PushArgs {
     const int *d_n_alive;
     const uint32_t *skey;
@@ -296,7 +308,8 @@ struct PushArgs {
     int *did;
     R *dah, *dvh;
     long cap;
-    const double *geo;
+    const double *geo;      // FP64 barycentric maps (PLAIN)
+    const float *geo32;     // FP32 barycentric maps (MIXED)
     const R *coef;
     const int4 *tnodes;
     const int4 *tnbr;
@@ -306,11 +319,12 @@ struct PushArgs {
     double abw[5];
     int walk_cap;
     uint32_t dead_key;
-    double *tacc, *wacc;
-    double *bcar;
+    int nsp;                // species slots per tet in the accumulators (MIXED), 1 for PLAIN
+    V *tacc, *wacc;
+    V *bcar;
     uint32_t *bcar_key;
     unsigned long long *okey;
-    double *oval;
+    V *oval;
     int *ocount;
     int ocap;
     int oshift;
@@ -318,6 +332,12 @@ struct PushArgs {
     int *n_alive_next;
     double *ke_part;
 };
+
+// accumulator index of a sorted key: tet (PLAIN) or tet * nsp + species (MIXED)
+template <typename V>
+__device__ __forceinline__ uint32_t acc_index(uint32_t key, int nsp) {
+    return std::is_same<V, double>::value ? (key >> 2) : (key >> 2) * (uint32_t)nsp + (key & 3u);
+}
 
 // barycentrics of point r in tet (affine map: lam_k = g_k . (r - x0), k=1..3)
 __device__ __forceinline__ void bary(const double *__restrict__ gp, double rx, double ry, double rz, double lam[4]) {
@@ -328,6 +348,17 @@ __device__ __forceinline__ void bary(const double *__restrict__ gp, double rx, d
     lam[0] = 1.0 - lam[1] - lam[2] - lam[3];
 }
 
+// FP32 barycentrics with a fixed sequence of correctly rounded operations, so
+// that the end point of one step and the start point of the next (the same
+// stored position) give bit-identical values wherever the code is inlined
+__device__ __forceinline__ void bary32(const float *__restrict__ gp, float rx, float ry, float rz, float lam[4]) {
+    const float dx = __fsub_rn(rx, gp[0]), dy = __fsub_rn(ry, gp[1]), dz = __fsub_rn(rz, gp[2]);
+    lam[1] = __fmaf_rn(gp[3], dx, __fmaf_rn(gp[4], dy, __fmul_rn(gp[5], dz)));
+    lam[2] = __fmaf_rn(gp[6], dx, __fmaf_rn(gp[7], dy, __fmul_rn(gp[8], dz)));
+    lam[3] = __fmaf_rn(gp[9], dx, __fmaf_rn(gp[10], dy, __fmul_rn(gp[11], dz)));
+    lam[0] = __fsub_rn(__fsub_rn(__fsub_rn(1.0f, lam[1]), lam[2]), lam[3]);
+}
+
 __device__ __forceinline__ void load_geo(const double *__restrict__ geo, int t, double gp[12]) {
     const double2 *g2 = reinterpret_cast<const double2 *>(geo + 12 * (size_t)t);
 #pragma unroll
@@ -336,6 +367,36 @@ __device__ __forceinline__ void load_geo(const double *__restrict__ geo, int t, 
         gp[2 * k] = v.x;
         gp[2 * k + 1] = v.y;
     }
+}
+
+__device__ __forceinline__ void load_geo32(const float *__restrict__ geo, int t, float gp[12]) {
+    const float4 *g4 = reinterpret_cast<const float4 *>(geo + 12 * (size_t)t);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        float4 v = __ldg(g4 + k);
+        gp[4 * k] = v.x;
+        gp[4 * k + 1] = v.y;
+        gp[4 * k + 2] = v.z;
+        gp[4 * k + 3] = v.w;
+    }
+}
+
+// fixed-point barycentrics: rounded, non-negative, summing to 2^24 exactly
+// (the rounding surplus or deficit goes to the largest component); `skip`
+// (if >= 0) is forced to 0
+__device__ __forceinline__ void quantize(const float lam[4], int skip, int L[4]) {
+    int sum = 0, big = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        int v = __float2int_rn(lam[k] * 16777216.0f);
+        v = (v < 0 || k == skip) ? 0 : v;
+        L[k] = v;
+        sum += v;
+    }
+#pragma unroll
+    for (int k = 1; k < 4; k++)
+        if (L[k] > L[big]) big = k;
+    L[big] += kFixOne - sum;
 }
 
 // exact line integral of the six Whitney-1 functions along a straight piece
@@ -349,132 +410,257 @@ __device__ __forceinline__ void segment_current(const double lS[4], const double
     out[5] = qw * (lS[2] * lE[3] - lE[2] * lS[3]);
 }
 
-template <typename R>
-__device__ void push_record(const PushArgs<R> &a, int tet, int wall, long pidx, int seg, const double v[kNV]) {
+// the same integral in fixed point (exact int64, scale 2^48 per unit charge)
+__device__ __forceinline__ void segment_current_fix(const int S[4], const int E[4], long long out[6]) {
+    out[0] = (long long)S[0] * E[1] - (long long)E[0] * S[1];
+    out[1] = (long long)S[0] * E[2] - (long long)E[0] * S[2];
+    out[2] = (long long)S[0] * E[3] - (long long)E[0] * S[3];
+    out[3] = (long long)S[1] * E[2] - (long long)E[1] * S[2];
+    out[4] = (long long)S[1] * E[3] - (long long)E[1] * S[3];
+    out[5] = (long long)S[2] * E[3] - (long long)E[2] * S[3];
+}
+
+template <typename R, typename V>
+__device__ void push_record(const PushArgs<R, V> &a, uint32_t aidx, int wall, long pidx, int seg, const V v[kNV]) {
     const int slot = atomicAdd(a.ocount, 1);
     if (slot >= a.ocap) {
         atomicOr(a.status, (uint32_t)ST_OVERFLOW);
         return;
     }
-    const unsigned long long tw = ((unsigned long long)tet << 1) | (unsigned long long)wall;
+    const unsigned long long tw = ((unsigned long long)aidx << 1) | (unsigned long long)wall;
     a.okey[slot] = (tw << a.oshift) | ((unsigned long long)pidx << 6) | (unsigned long long)seg;
-    double *o = a.oval + (size_t)slot * kNV;
+    V *o = a.oval + (size_t)slot * kNV;
 #pragma unroll
     for (int c = 0; c < kNV; c++) o[c] = v[c];
 }
 
-template <typename R, int MODE>   // MODE 0: Boris, 1: Adams-Bashforth, 2: charge only
-__global__ void __launch_bounds__(kPushBlock) k_push(const PushArgs<R> a) {
+__device__ __forceinline__ double shfl_up_v(double v, int off) { return __shfl_up_sync(0xFFFFFFFFu, v, off); }
+__device__ __forceinline__ long long shfl_up_v(long long v, int off) { return __shfl_up_sync(0xFFFFFFFFu, v, off); }
+
+// Deterministic reduction of the first-piece deposits of a block of sorted
+// particles into the per-tet accumulators: a warp-segmented inclusive scan by
+// key, runs inside a warp stored directly (sole writer), the warps' boundary
+// pieces merged in warp order, and the block's own boundary runs handed to
+// k_fixup through the carry slots.
+template <typename R, typename V>
+__device__ __forceinline__ void reduce_block(const PushArgs<R, V> &a, uint32_t rkey, V vals[kNV], double ke,
+                                             int alive_out, int n_alive) {
     __shared__ uint32_t s_key[kPushBlock / 32][2];
-    __shared__ double s_val[kPushBlock / 32][2][kNV];
+    __shared__ V s_val[kPushBlock / 32][2][kNV];
     __shared__ double s_ke[kPushBlock / 32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const long i = (long)blockIdx.x * kPushBlock + tid;
+    {
+        const unsigned ball = __ballot_sync(0xFFFFFFFFu, alive_out);
+        if (lane == 0 && ball) atomicAdd(a.n_alive_next, __popc(ball));
+        double k2 = ke;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) k2 += __shfl_down_sync(0xFFFFFFFFu, k2, o);
+        if (lane == 0) s_ke[warp] = k2;
+    }
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t ko = __shfl_up_sync(0xFFFFFFFFu, rkey, off);
+#pragma unroll
+        for (int c = 0; c < kNV; c++) {
+            const V vo = shfl_up_v(vals[c], off);
+            if (lane >= off && ko == rkey) vals[c] += vo;
+        }
+    }
+    const uint32_t knext = __shfl_down_sync(0xFFFFFFFFu, rkey, 1);
+    const bool tail = (lane == 31) || (knext != rkey);
+    const uint32_t kfirst = __shfl_sync(0xFFFFFFFFu, rkey, 0);
+    if (lane == 0) {
+        s_key[warp][0] = kInvalid;
+        s_key[warp][1] = kInvalid;
+    }
+    __syncwarp();
+    if (tail && rkey != kInvalid) {
+        const bool first = (rkey == kfirst);
+        const bool last = (lane == 31);
+        if (!first && !last) {
+            V *dst = a.tacc + (size_t)rkey * kNV;
+#pragma unroll
+            for (int c = 0; c < kNV; c++) dst[c] = vals[c];
+        } else {
+            const int slot = first ? 0 : 1;
+            s_key[warp][slot] = rkey;
+#pragma unroll
+            for (int c = 0; c < kNV; c++) s_val[warp][slot][c] = vals[c];
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double kes = 0.0;
+        for (int w = 0; w < kPushBlock / 32; w++) kes += s_ke[w];
+        a.ke_part[blockIdx.x] = kes;
+    }
+    const long blk0 = (long)blockIdx.x * kPushBlock;
+    if (tid < kNV || tid == 32) {
+        // thread c < kNV merges value c; thread 32 writes the carry keys
+        const int c = tid < kNV ? tid : 0;
+        const bool writer_keys = (tid == 32);
+        const uint32_t prevk = (blk0 > 0 && blk0 - 1 < n_alive) ? acc_index<V>(a.skey[blk0 - 1], a.nsp) : kInvalid;
+        const long blk_end = min(blk0 + kPushBlock, (long)n_alive);
+        const uint32_t nextk = (blk_end < n_alive) ? acc_index<V>(a.skey[blk_end], a.nsp) : kInvalid;
+        uint32_t run_key = kInvalid;
+        V run_val = 0;
+        bool run_is_first = true;
+        uint32_t out_key[2] = {kInvalid, kInvalid};
+        V out_val[2] = {0, 0};
+        auto flush = [&](bool is_last_run) {
+            if (run_key == kInvalid) return;
+            const bool touches_prev = run_is_first && prevk == run_key;
+            const bool touches_next = is_last_run && nextk == run_key;
+            if (touches_prev || touches_next) {
+                const int slot = run_is_first ? 0 : 1;
+                out_key[slot] = run_key;
+                out_val[slot] = run_val;
+            } else if (!writer_keys) {
+                a.tacc[(size_t)run_key * kNV + c] = run_val;
+            }
+        };
+        for (int w = 0; w < kPushBlock / 32; w++)
+            for (int sl = 0; sl < 2; sl++) {
+                const uint32_t k = s_key[w][sl];
+                if (k == kInvalid) continue;
+                const V v = s_val[w][sl][c];
+                if (k == run_key) {
+                    run_val += v;
+                } else {
+                    if (run_key != kInvalid) {
+                        flush(false);
+                        run_is_first = false;
+                    }
+                    run_key = k;
+                    run_val = v;
+                }
+            }
+        flush(true);
+        if (writer_keys) {
+            a.bcar_key[2 * blockIdx.x] = out_key[0];
+            a.bcar_key[2 * blockIdx.x + 1] = out_key[1];
+        } else {
+            a.bcar[(2 * (size_t)blockIdx.x) * kNV + c] = out_val[0];
+            a.bcar[(2 * (size_t)blockIdx.x + 1) * kNV + c] = out_val[1];
+        }
+    }
+}
+
+// gather + push shared by both precisions; returns the new position and velocity
+template <typename R, int MODE>
+__device__ __forceinline__ void gather_push(const PushArgs<R, typename std::conditional<std::is_same<R, double>::value, double, long long>::type> &a,
+                                            const R *cf, const R P[3], const R V[3], R d0, R d1, R d2, int spc,
+                                            long src, long i, R Q[3], R Vn[3]) {
+    R c[10];
+#pragma unroll
+    for (int k = 0; k < 10; k++) c[k] = cf[k];
+    // Whitney fields in the tet (Sec. II.A): E = E0 + Omega x d, B = B0 + beta d
+    const R E[3] = {c[0] + c[4] * d2 - c[5] * d1, c[1] + c[5] * d0 - c[3] * d2, c[2] + c[3] * d1 - c[4] * d0};
+    const R B[3] = {c[6] + c[9] * d0, c[7] + c[9] * d1, c[8] + c[9] * d2};
+    const R qm = (R)a.sp.qm[spc];
+    const R dt = (R)a.dt;
+    if (MODE == 0) {
+        // Boris: half kick, rotation about B, half kick (Sec. III.B)
+        const R h = (R)0.5 * qm * dt;
+        R vm[3], tv[3];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            vm[k] = V[k] + h * E[k];
+            tv[k] = h * B[k];
+        }
+        const R t2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
+        const R f = (R)2 / ((R)1 + t2);
+        const R vp[3] = {vm[0] + (vm[1] * tv[2] - vm[2] * tv[1]), vm[1] + (vm[2] * tv[0] - vm[0] * tv[2]),
+                         vm[2] + (vm[0] * tv[1] - vm[1] * tv[0])};
+        const R sv[3] = {f * tv[0], f * tv[1], f * tv[2]};
+        Vn[0] = vm[0] + (vp[1] * sv[2] - vp[2] * sv[1]) + h * E[0];
+        Vn[1] = vm[1] + (vp[2] * sv[0] - vp[0] * sv[2]) + h * E[1];
+        Vn[2] = vm[2] + (vp[0] * sv[1] - vp[1] * sv[0]) + h * E[2];
+#pragma unroll
+        for (int k = 0; k < 3; k++) Q[k] = P[k] + dt * Vn[k];
+    } else if (MODE == 1) {
+        // Adams-Bashforth (Eq. adam-bashforth): a^n = q/m (E + v^n x B)
+        const R acc[3] = {qm * (E[0] + (V[1] * B[2] - V[2] * B[1])), qm * (E[1] + (V[2] * B[0] - V[0] * B[2])),
+                          qm * (E[2] + (V[0] * B[1] - V[1] * B[0]))};
+        R sa[3], svv[3];
+        const R w0 = (R)a.abw[0];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            sa[k] = w0 * acc[k];
+            svv[k] = w0 * V[k];
+        }
+        for (int j = 1; j < a.ab_order; j++) {
+            const R wj = (R)a.abw[j];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                sa[k] += wj * a.sah[((size_t)(j - 1) * 3 + k) * a.cap + src];
+                svv[k] += wj * a.svh[((size_t)(j - 1) * 3 + k) * a.cap + src];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            Vn[k] = V[k] + dt * sa[k];
+            Q[k] = P[k] + dt * svv[k];
+        }
+        // history: level 0 <- current, level j <- level j-1
+        for (int j = a.hist_levels - 1; j >= 1; j--)
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                a.dah[((size_t)j * 3 + k) * a.cap + i] = a.sah[((size_t)(j - 1) * 3 + k) * a.cap + src];
+                a.dvh[((size_t)j * 3 + k) * a.cap + i] = a.svh[((size_t)(j - 1) * 3 + k) * a.cap + src];
+            }
+        if (a.hist_levels > 0)
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                a.dah[(size_t)k * a.cap + i] = acc[k];
+                a.dvh[(size_t)k * a.cap + i] = V[k];
+            }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            Q[k] = P[k];
+            Vn[k] = V[k];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// PLAIN: FP64 state, FP64 barycentrics, FP64 deposit
+// ---------------------------------------------------------------------------
+template <int MODE>   // 0: Boris, 1: Adams-Bashforth, 2: charge only
+__global__ void __launch_bounds__(kPushBlock) k_push_plain(const PushArgs<double, double> a) {
+    const long i = (long)blockIdx.x * kPushBlock + threadIdx.x;
     const int n_alive = *a.d_n_alive;
     const bool active = i < n_alive;
-    uint32_t rkey = kInvalid;     // reduction key: start tet
+    uint32_t rkey = kInvalid;
     double vals[kNV];
 #pragma unroll
     for (int c = 0; c < kNV; c++) vals[c] = 0.0;
     double ke = 0.0;
     int alive_out = 0;
-
     if (active) {
         const uint32_t key = a.skey[i];
         const int tet = (int)(key >> 2), spc = (int)(key & 3u);
         const long src = a.perm[i];
-        R P[3] = {a.sx0[src], a.sx1[src], a.sx2[src]};
-        R V[3] = {a.sv0[src], a.sv1[src], a.sv2[src]};
+        const double P[3] = {a.sx0[src], a.sx1[src], a.sx2[src]};
+        const double V[3] = {a.sv0[src], a.sv1[src], a.sv2[src]};
         double gp[12];
         load_geo(a.geo, tet, gp);
-        // ---- gather (Sec. II.A): E = E0 + Omega x d, B = B0 + beta d ----
-        const R *cf = a.coef + 10 * (size_t)tet;
-        R c[10];
-#pragma unroll
-        for (int k = 0; k < 10; k++) c[k] = cf[k];
-        const R d0 = (R)((double)P[0] - gp[0]), d1 = (R)((double)P[1] - gp[1]), d2 = (R)((double)P[2] - gp[2]);
-        const R E[3] = {c[0] + c[4] * d2 - c[5] * d1, c[1] + c[5] * d0 - c[3] * d2, c[2] + c[3] * d1 - c[4] * d0};
-        const R B[3] = {c[6] + c[9] * d0, c[7] + c[9] * d1, c[8] + c[9] * d2};
-        const R qm = (R)a.sp.qm[spc];
-        const R dt = (R)a.dt;
-        R Q[3], Vn[3];
-        if (MODE == 0) {
-            // ---- Boris: half kick, rotation about B, half kick (Sec. III.B) ----
-            const R h = (R)0.5 * qm * dt;
-            R vm[3], tv[3];
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                vm[k] = V[k] + h * E[k];
-                tv[k] = h * B[k];
-            }
-            const R t2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
-            const R f = (R)2 / ((R)1 + t2);
-            const R vp[3] = {vm[0] + (vm[1] * tv[2] - vm[2] * tv[1]), vm[1] + (vm[2] * tv[0] - vm[0] * tv[2]),
-                             vm[2] + (vm[0] * tv[1] - vm[1] * tv[0])};
-            const R sv[3] = {f * tv[0], f * tv[1], f * tv[2]};
-            Vn[0] = vm[0] + (vp[1] * sv[2] - vp[2] * sv[1]) + h * E[0];
-            Vn[1] = vm[1] + (vp[2] * sv[0] - vp[0] * sv[2]) + h * E[1];
-            Vn[2] = vm[2] + (vp[0] * sv[1] - vp[1] * sv[0]) + h * E[2];
-#pragma unroll
-            for (int k = 0; k < 3; k++) Q[k] = P[k] + dt * Vn[k];
-        } else if (MODE == 1) {
-            // ---- Adams-Bashforth (Eq. adam-bashforth): a^n = q/m (E + v^n x B) ----
-            const R acc[3] = {qm * (E[0] + (V[1] * B[2] - V[2] * B[1])), qm * (E[1] + (V[2] * B[0] - V[0] * B[2])),
-                              qm * (E[2] + (V[0] * B[1] - V[1] * B[0]))};
-            R sa[3], svv[3];
-            const R w0 = (R)a.abw[0];
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                sa[k] = w0 * acc[k];
-                svv[k] = w0 * V[k];
-            }
-            for (int j = 1; j < a.ab_order; j++) {
-                const R wj = (R)a.abw[j];
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    sa[k] += wj * a.sah[((size_t)(j - 1) * 3 + k) * a.cap + src];
-                    svv[k] += wj * a.svh[((size_t)(j - 1) * 3 + k) * a.cap + src];
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                Vn[k] = V[k] + dt * sa[k];
-                Q[k] = P[k] + dt * svv[k];
-            }
-            // shift the history: level 0 <- current, level j <- level j-1
-            for (int j = a.hist_levels - 1; j >= 1; j--)
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    a.dah[((size_t)j * 3 + k) * a.cap + i] = a.sah[((size_t)(j - 1) * 3 + k) * a.cap + src];
-                    a.dvh[((size_t)j * 3 + k) * a.cap + i] = a.svh[((size_t)(j - 1) * 3 + k) * a.cap + src];
-                }
-            if (a.hist_levels > 0)
-#pragma unroll
-                for (int k = 0; k < 3; k++) {
-                    a.dah[(size_t)k * a.cap + i] = acc[k];
-                    a.dvh[(size_t)k * a.cap + i] = V[k];
-                }
-        } else {
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                Q[k] = P[k];
-                Vn[k] = V[k];
-            }
-        }
-        // ---- walk the straight path P -> Q (Algorithm 1) with exact deposit ----
+        double Q[3], Vn[3];
+        gather_push<double, MODE>(a, a.coef + 10 * (size_t)tet, P, V, P[0] - gp[0], P[1] - gp[1], P[2] - gp[2], spc,
+                                  src, i, Q, Vn);
+        // walk the straight path P -> Q (Algorithm 1) with the exact deposit
         const double qw = a.sp.qw[spc];
-        const double Qd[3] = {(double)Q[0], (double)Q[1], (double)Q[2]};
         double lS[4], lE[4];
-        bary(gp, (double)P[0], (double)P[1], (double)P[2], lS);
+        bary(gp, P[0], P[1], P[2], lS);
         int T = tet;
         int4 tn = a.tnodes[T];
         int entry = -1;
-        int seg = 0;
         bool done = false, absorbed = false;
         int endT = tet;
-        for (; seg < a.walk_cap; seg++) {
+        for (int seg = 0; seg < a.walk_cap; seg++) {
             if (seg > 0) load_geo(a.geo, T, gp);
-            bary(gp, Qd[0], Qd[1], Qd[2], lE);
+            bary(gp, Q[0], Q[1], Q[2], lE);
             int kmin = -1;
             double smin = 2.0;
 #pragma unroll
@@ -489,7 +675,6 @@ __global__ void __launch_bounds__(kPushBlock) k_push(const PushArgs<R> a) {
             }
             double rec[kNV];
             if (kmin < 0) {
-                // path ends in T: current of the last piece + charge at the end point
                 segment_current(lS, lE, qw, rec);
 #pragma unroll
                 for (int k = 0; k < 4; k++) rec[6 + k] = qw * lE[k];
@@ -497,7 +682,7 @@ __global__ void __launch_bounds__(kPushBlock) k_push(const PushArgs<R> a) {
 #pragma unroll
                     for (int c = 0; c < kNV; c++) vals[c] = rec[c];
                 } else {
-                    push_record(a, T, 0, i, seg, rec);
+                    push_record(a, (uint32_t)T, 0, i, seg, rec);
                 }
                 endT = T;
                 done = true;
@@ -514,17 +699,16 @@ __global__ void __launch_bounds__(kPushBlock) k_push(const PushArgs<R> a) {
 #pragma unroll
                 for (int c = 0; c < kNV; c++) vals[c] = rec[c];
             } else {
-                push_record(a, T, 0, i, seg, rec);
+                push_record(a, (uint32_t)T, 0, i, seg, rec);
             }
             const int nb = (&a.tnbr[T].x)[kmin];
             if (nb < 0) {
-                // absorbed by the wall at the exit point: its charge stays there
                 double wrec[kNV];
 #pragma unroll
                 for (int k = 0; k < 6; k++) wrec[k] = 0.0;
 #pragma unroll
                 for (int k = 0; k < 4; k++) wrec[6 + k] = qw * lX[k];
-                push_record(a, T, 1, i, kMaxWalk, wrec);
+                push_record(a, (uint32_t)T, 1, i, kMaxWalk, wrec);
                 absorbed = true;
                 done = true;
                 break;
@@ -551,9 +735,145 @@ __global__ void __launch_bounds__(kPushBlock) k_push(const PushArgs<R> a) {
         }
         if (!done) {
             atomicOr(a.status, (uint32_t)ST_WALK_CAP);
-            absorbed = true;   // the particle is dropped; the step reports the error
+            absorbed = true;
         }
-        // ---- write the particle back in sorted order ----
+        a.dx0[i] = Q[0];
+        a.dx1[i] = Q[1];
+        a.dx2[i] = Q[2];
+        a.dv0[i] = Vn[0];
+        a.dv1[i] = Vn[1];
+        a.dv2[i] = Vn[2];
+        a.did[i] = a.sid[src];
+        a.dkey[i] = absorbed ? a.dead_key : (((uint32_t)endT << 2) | (uint32_t)spc);
+        if (!absorbed) {
+            alive_out = 1;
+            ke = 0.5 * a.sp.mw[spc] * (Vn[0] * Vn[0] + Vn[1] * Vn[1] + Vn[2] * Vn[2]);
+            if (!(ke == ke) || !(Q[0] == Q[0])) atomicOr(a.status, (uint32_t)ST_NAN);
+        }
+        rkey = (uint32_t)tet;
+    }
+    reduce_block<double, double>(a, rkey, vals, ke, alive_out, n_alive);
+}
+
+// ---------------------------------------------------------------------------
+// MIXED: FP32 state, gather, push and walk; fixed-point barycentrics and an
+// integer deposit (exact), accumulators per (tet, species)
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void __launch_bounds__(kPushBlock) k_push_mixed(const PushArgs<float, long long> a) {
+    const long i = (long)blockIdx.x * kPushBlock + threadIdx.x;
+    const int n_alive = *a.d_n_alive;
+    const bool active = i < n_alive;
+    uint32_t rkey = kInvalid;
+    long long vals[kNV];
+#pragma unroll
+    for (int c = 0; c < kNV; c++) vals[c] = 0;
+    double ke = 0.0;
+    int alive_out = 0;
+    if (active) {
+        const uint32_t key = a.skey[i];
+        const int tet = (int)(key >> 2), spc = (int)(key & 3u);
+        const long src = a.perm[i];
+        const float P[3] = {a.sx0[src], a.sx1[src], a.sx2[src]};
+        const float V[3] = {a.sv0[src], a.sv1[src], a.sv2[src]};
+        float gp[12];
+        load_geo32(a.geo32, tet, gp);
+        float Q[3], Vn[3];
+        gather_push<float, MODE>(a, a.coef + 10 * (size_t)tet, P, V, P[0] - gp[0], P[1] - gp[1], P[2] - gp[2], spc,
+                                 src, i, Q, Vn);
+        float lf[4];
+        int LS[4], LE[4];
+        bary32(gp, P[0], P[1], P[2], lf);
+        quantize(lf, -1, LS);
+        int T = tet;
+        int4 tn = a.tnodes[T];
+        int entry = -1;
+        bool done = false, absorbed = false;
+        int endT = tet;
+        for (int seg = 0; seg < a.walk_cap; seg++) {
+            if (seg > 0) load_geo32(a.geo32, T, gp);
+            float le[4];
+            bary32(gp, Q[0], Q[1], Q[2], le);
+            int kmin = -1;
+            float smin = 2.0f;
+            float ls[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) ls[k] = (float)LS[k] * (1.0f / 16777216.0f);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (k == entry || !(le[k] < 0.0f)) continue;
+                float s = ls[k] / (ls[k] - le[k]);
+                s = s < 0.0f ? 0.0f : s;
+                if (s < smin) {
+                    smin = s;
+                    kmin = k;
+                }
+            }
+            long long rec[kNV];
+            if (kmin < 0) {
+                quantize(le, -1, LE);
+                segment_current_fix(LS, LE, rec);
+#pragma unroll
+                for (int k = 0; k < 4; k++) rec[6 + k] = LE[k];
+                if (seg == 0) {
+#pragma unroll
+                    for (int c = 0; c < kNV; c++) vals[c] = rec[c];
+                } else {
+                    push_record(a, (uint32_t)(T * a.nsp + spc), 0, i, seg, rec);
+                }
+                endT = T;
+                done = true;
+                break;
+            }
+            float lx[4];
+            int LX[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) lx[k] = ls[k] + smin * (le[k] - ls[k]);
+            quantize(lx, kmin, LX);
+            segment_current_fix(LS, LX, rec);
+#pragma unroll
+            for (int k = 0; k < 4; k++) rec[6 + k] = 0;
+            if (seg == 0) {
+#pragma unroll
+                for (int c = 0; c < kNV; c++) vals[c] = rec[c];
+            } else {
+                push_record(a, (uint32_t)(T * a.nsp + spc), 0, i, seg, rec);
+            }
+            const int nb = (&a.tnbr[T].x)[kmin];
+            if (nb < 0) {
+                long long wrec[kNV];
+#pragma unroll
+                for (int k = 0; k < 6; k++) wrec[k] = 0;
+#pragma unroll
+                for (int k = 0; k < 4; k++) wrec[6 + k] = LX[k];
+                push_record(a, (uint32_t)(T * a.nsp + spc), 1, i, kMaxWalk, wrec);
+                absorbed = true;
+                done = true;
+                break;
+            }
+            const int4 nn = a.tnodes[nb];
+            const int tv[4] = {tn.x, tn.y, tn.z, tn.w};
+            const int nv[4] = {nn.x, nn.y, nn.z, nn.w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                int l = 0;
+                bool shared = false;
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if (nv[j] == tv[k]) {
+                        l = LX[k];
+                        shared = true;
+                    }
+                LS[j] = l;
+                if (!shared) entry = j;
+            }
+            T = nb;
+            tn = nn;
+        }
+        if (!done) {
+            atomicOr(a.status, (uint32_t)ST_WALK_CAP);
+            absorbed = true;
+        }
         a.dx0[i] = Q[0];
         a.dx1[i] = Q[1];
         a.dx2[i] = Q[2];
@@ -565,124 +885,20 @@ __global__ void __launch_bounds__(kPushBlock) k_push(const PushArgs<R> a) {
         if (!absorbed) {
             alive_out = 1;
             ke = 0.5 * a.sp.mw[spc] * ((double)Vn[0] * Vn[0] + (double)Vn[1] * Vn[1] + (double)Vn[2] * Vn[2]);
-            if (!(ke == ke) || !(Qd[0] == Qd[0])) atomicOr(a.status, (uint32_t)ST_NAN);
+            if (!(ke == ke) || !(Q[0] == Q[0])) atomicOr(a.status, (uint32_t)ST_NAN);
         }
-        rkey = (uint32_t)tet;
+        rkey = (uint32_t)(tet * a.nsp + spc);
     }
-
-    // ---- live count and kinetic energy (block partial, fixed order) ----
-    {
-        const unsigned ball = __ballot_sync(0xFFFFFFFFu, alive_out);
-        if (lane == 0 && ball) atomicAdd(a.n_alive_next, __popc(ball));
-        double k2 = ke;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) k2 += __shfl_down_sync(0xFFFFFFFFu, k2, o);
-        if (lane == 0) s_ke[warp] = k2;
-    }
-
-    // ---- warp-segmented inclusive scan of the first-piece deposits by start tet ----
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t ko = __shfl_up_sync(0xFFFFFFFFu, rkey, off);
-#pragma unroll
-        for (int c = 0; c < kNV; c++) {
-            const double vo = __shfl_up_sync(0xFFFFFFFFu, vals[c], off);
-            if (lane >= off && ko == rkey) vals[c] += vo;
-        }
-    }
-    const uint32_t knext = __shfl_down_sync(0xFFFFFFFFu, rkey, 1);
-    const bool tail = (lane == 31) || (knext != rkey);
-    const uint32_t kfirst = __shfl_sync(0xFFFFFFFFu, rkey, 0);
-    if (lane == 0) {
-        s_key[warp][0] = kInvalid;
-        s_key[warp][1] = kInvalid;
-    }
-    __syncwarp();
-    if (tail && rkey != kInvalid) {
-        const bool first = (rkey == kfirst);
-        const bool last = (lane == 31);
-        if (!first && !last) {
-            // a run that starts and ends inside this warp: sole writer
-            double *dst = a.tacc + (size_t)rkey * kNV;
-#pragma unroll
-            for (int c = 0; c < kNV; c++) dst[c] = vals[c];
-        } else {
-            const int slot = first ? 0 : 1;
-            s_key[warp][slot] = rkey;
-#pragma unroll
-            for (int c = 0; c < kNV; c++) s_val[warp][slot][c] = vals[c];
-        }
-    }
-    __syncthreads();
-
-    // ---- block level: merge the warp boundary pieces in warp order ----
-    if (tid == 0) {
-        double kes = 0.0;
-        for (int w = 0; w < kPushBlock / 32; w++) kes += s_ke[w];
-        a.ke_part[blockIdx.x] = kes;
-    }
-    const long blk0 = (long)blockIdx.x * kPushBlock;
-    if (tid < kNV || tid == 32) {
-        // thread c < kNV handles value c; thread 32 writes the keys
-        const int c = tid < kNV ? tid : 0;
-        const bool writer_keys = (tid == 32);
-        const uint32_t prevk = (blk0 > 0 && blk0 - 1 < n_alive) ? (a.skey[blk0 - 1] >> 2) : kInvalid;
-        const long blk_end = min(blk0 + kPushBlock, (long)n_alive);
-        const uint32_t nextk = (blk_end < n_alive) ? (a.skey[blk_end] >> 2) : kInvalid;
-        uint32_t run_key = kInvalid;
-        double run_val = 0.0;
-        bool run_is_first = true;
-        int n_runs = 0;
-        uint32_t out_key[2] = {kInvalid, kInvalid};
-        double out_val[2] = {0.0, 0.0};
-        // flush a finished run: complete -> direct store, partial -> block carry slot
-        auto flush = [&](bool is_last_run) {
-            if (run_key == kInvalid) return;
-            const bool touches_prev = run_is_first && prevk == run_key;
-            const bool touches_next = is_last_run && nextk == run_key;
-            if (touches_prev || touches_next) {
-                const int slot = (run_is_first) ? 0 : 1;
-                out_key[slot] = run_key;
-                out_val[slot] = run_val;
-            } else if (!writer_keys) {
-                a.tacc[(size_t)run_key * kNV + c] = run_val;
-            }
-        };
-        for (int w = 0; w < kPushBlock / 32; w++)
-            for (int sl = 0; sl < 2; sl++) {
-                const uint32_t k = s_key[w][sl];
-                if (k == kInvalid) continue;
-                const double v = s_val[w][sl][c];
-                if (k == run_key) {
-                    run_val += v;
-                } else {
-                    if (run_key != kInvalid) {
-                        flush(false);
-                        run_is_first = false;
-                    }
-                    run_key = k;
-                    run_val = v;
-                    n_runs++;
-                }
-            }
-        flush(true);
-        if (writer_keys) {
-            a.bcar_key[2 * blockIdx.x] = out_key[0];
-            a.bcar_key[2 * blockIdx.x + 1] = out_key[1];
-        } else {
-            a.bcar[(2 * (size_t)blockIdx.x) * kNV + c] = out_val[0];
-            a.bcar[(2 * (size_t)blockIdx.x + 1) * kNV + c] = out_val[1];
-        }
-        (void)n_runs;
-    }
+    reduce_block<float, long long>(a, rkey, vals, ke, alive_out, n_alive);
 }
 
 // spanning runs: a head piece (the last run of a block, or a block's first run
 // that does not continue from the previous block) adds the following blocks'
-// first-run pieces of the same tet in block order
-__global__ void __launch_bounds__(256) k_fixup(int n_blocks, const uint32_t *__restrict__ skey, const int *d_n_alive,
-                                               const uint32_t *__restrict__ bkey, const double *__restrict__ bval,
-                                               double *__restrict__ tacc) {
+// first-run pieces of the same key in block order
+template <typename V>
+__global__ void __launch_bounds__(256) k_fixup(int n_blocks, int nsp, const uint32_t *__restrict__ skey,
+                                               const int *d_n_alive, const uint32_t *__restrict__ bkey,
+                                               const V *__restrict__ bval, V *__restrict__ tacc) {
     const long j = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= 2L * n_blocks) return;
     const uint32_t k = bkey[j];
@@ -692,65 +908,86 @@ __global__ void __launch_bounds__(256) k_fixup(int n_blocks, const uint32_t *__r
     if (slot == 0) {
         const long p = blk * kPushBlock - 1;
         const int n_alive = *d_n_alive;
-        if (blk > 0 && p < n_alive && (skey[p] >> 2) == k) return;   // continues a run from before
+        if (blk > 0 && p < n_alive && acc_index<V>(skey[p], nsp) == k) return;
     }
-    double sum[kNV];
+    V sum[kNV];
     for (int c = 0; c < kNV; c++) sum[c] = bval[j * kNV + c];
     for (long b = blk + 1; b < n_blocks && bkey[2 * b] == k; b++)
         for (int c = 0; c < kNV; c++) sum[c] += bval[2 * b * kNV + c];
     for (int c = 0; c < kNV; c++) tacc[(size_t)k * kNV + c] = sum[c];
 }
 
-// overflow records (later pieces of crossing paths, wall hits), sorted by
-// (tet, wall, particle, piece): each (tet, wall) run is summed in that order
+// crossing records sorted by (accumulator, wall, particle, piece): each
+// (accumulator, wall) run is summed in that order and added
+template <typename V>
 __global__ void __launch_bounds__(256) k_overflow_reduce(const int *d_count, int cap, const unsigned long long *__restrict__ okey,
-                                                         const uint32_t *__restrict__ oidx, const double *__restrict__ oval,
-                                                         int oshift, double *__restrict__ tacc, double *__restrict__ wacc) {
+                                                         const uint32_t *__restrict__ oidx, const V *__restrict__ oval,
+                                                         int oshift, V *__restrict__ tacc, V *__restrict__ wacc) {
     const int n = min(*d_count, cap);
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const unsigned long long tw = okey[j] >> oshift;
     if (j > 0 && (okey[j - 1] >> oshift) == tw) return;
-    double sum[kNV];
-    for (int c = 0; c < kNV; c++) sum[c] = 0.0;
+    V sum[kNV];
+    for (int c = 0; c < kNV; c++) sum[c] = 0;
     for (int r = j; r < n && (okey[r] >> oshift) == tw; r++) {
-        const double *v = oval + (size_t)oidx[r] * kNV;
+        const V *v = oval + (size_t)oidx[r] * kNV;
         for (int c = 0; c < kNV; c++) sum[c] += v[c];
     }
-    const long tet = (long)(tw >> 1);
+    const long idx = (long)(tw >> 1);
     if (tw & 1ull) {
-        for (int c = 0; c < 4; c++) wacc[tet * 4 + c] += sum[6 + c];
+        for (int c = 0; c < 4; c++) wacc[idx * 4 + c] += sum[6 + c];
     } else {
-        for (int c = 0; c < kNV; c++) tacc[tet * kNV + c] += sum[c];
+        for (int c = 0; c < kNV; c++) tacc[idx * kNV + c] += sum[c];
     }
 }
 
-// per-tet accumulators -> edges and nodes, in the fixed order of the maps
+// per-tet accumulators -> edges and nodes, in the fixed order of the maps.
+// PLAIN accumulators hold charge already; MIXED ones hold fixed-point sums per
+// species, converted here with the species' q w.
+template <typename V>
 __global__ void __launch_bounds__(256) k_gather_edges(int ne, const int *__restrict__ ptr, const int *__restrict__ idx,
-                                                      const double *__restrict__ tacc, const double *__restrict__ g,
-                                                      double *__restrict__ dg, double *__restrict__ g_new) {
+                                                      const V *__restrict__ tacc, int nsp, SpeciesParams sp,
+                                                      const double *__restrict__ g, double *__restrict__ dg,
+                                                      double *__restrict__ g_new) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ne) return;
     double s = 0.0;
     for (int k = ptr[e]; k < ptr[e + 1]; k++) {
         const int ref = idx[k];
-        s += tacc[(size_t)(ref / 6) * kNV + ref % 6];
+        const size_t t = (size_t)(ref / 6);
+        const int l = ref % 6;
+        if (std::is_same<V, double>::value) {
+            s += (double)tacc[t * kNV + l];
+        } else {
+            for (int q = 0; q < nsp; q++) s += (double)tacc[(t * nsp + q) * kNV + l] * (sp.qw[q] * kFixEdge);
+        }
     }
     dg[e] = s;
     g_new[e] = g[e] + s;
 }
 
+template <typename V>
 __global__ void __launch_bounds__(256) k_gather_nodes(int nn, const int *__restrict__ ptr, const int *__restrict__ idx,
-                                                      const double *__restrict__ tacc, const double *__restrict__ wacc,
-                                                      const double *__restrict__ wall_old, double *__restrict__ rho,
-                                                      double *__restrict__ wall) {
+                                                      const V *__restrict__ tacc, const V *__restrict__ wacc, int nsp,
+                                                      SpeciesParams sp, const double *__restrict__ wall_old,
+                                                      double *__restrict__ rho, double *__restrict__ wall) {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nn) return;
     double r = 0.0, w = 0.0;
     for (int k = ptr[n]; k < ptr[n + 1]; k++) {
         const int ref = idx[k];
-        r += tacc[(size_t)(ref / 4) * kNV + 6 + ref % 4];
-        w += wacc[(size_t)(ref / 4) * 4 + ref % 4];
+        const size_t t = (size_t)(ref / 4);
+        const int l = ref % 4;
+        if (std::is_same<V, double>::value) {
+            r += (double)tacc[t * kNV + 6 + l];
+            w += (double)wacc[t * 4 + l];
+        } else {
+            for (int q = 0; q < nsp; q++) {
+                r += (double)tacc[(t * nsp + q) * kNV + 6 + l] * (sp.qw[q] * kFixNode);
+                w += (double)wacc[(t * nsp + q) * 4 + l] * (sp.qw[q] * kFixNode);
+            }
+        }
     }
     rho[n] = r;
     wall[n] = wall_old[n] + w;
@@ -841,6 +1078,26 @@ __global__ void k_load_particles(int n, int start, const double *__restrict__ x,
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
+SpeciesParams species_params(const Sim *s) {
+    SpeciesParams sp;
+    for (int k = 0; k < kMaxSpecies; k++) {
+        sp.qm[k] = k < s->n_species ? s->sp_q[k] / s->sp_m[k] : 0.0;
+        sp.qw[k] = k < s->n_species ? s->sp_q[k] * s->sp_w[k] : 0.0;
+        sp.mw[k] = k < s->n_species ? s->sp_m[k] * s->sp_w[k] : 0.0;
+    }
+    return sp;
+}
+
+// records of the later pieces of crossing paths (and wall hits); grown on demand
+static int overflow_alloc(Sim *s, int cap) {
+    int rc;
+    if ((rc = s->okey.alloc(cap)) || (rc = s->okey2.alloc(cap)) || (rc = s->oidx.alloc(cap)) ||
+        (rc = s->oidx2.alloc(cap)) || (rc = s->oval.alloc((size_t)cap * kNV)))
+        return rc;
+    s->ocap = cap;
+    return PIC_OK;
+}
+
 int particles_alloc(Sim *s, size_t cap) {
     int rc;
     const size_t rs = s->rsize;
@@ -858,9 +1115,7 @@ int particles_alloc(Sim *s, size_t cap) {
     if ((rc = s->skey.alloc(cap)) || (rc = s->sval.alloc(cap)) || (rc = s->tkey.alloc(cap)) ||
         (rc = s->tval.alloc(cap)))
         return rc;
-    s->ocap = (int)std::min<size_t>(std::max<size_t>(cap, 4096), (size_t)1 << 30);
-    if ((rc = s->okey.alloc(s->ocap)) || (rc = s->okey2.alloc(s->ocap)) || (rc = s->oidx.alloc(s->ocap)) ||
-        (rc = s->oidx2.alloc(s->ocap)) || (rc = s->oval.alloc((size_t)s->ocap * kNV)))
+    if ((rc = overflow_alloc(s, (int)std::min<size_t>(std::max<size_t>(cap / 8, 65536), (size_t)1 << 30))))
         return rc;
     const size_t blocks = std::max<size_t>(1, (cap + kPushBlock - 1) / kPushBlock);
     if ((rc = s->bcar.alloc(2 * blocks * kNV)) || (rc = s->bcar_key.alloc(2 * blocks)) ||
@@ -887,8 +1142,8 @@ int validate_particles(Sim *s, int n, int start) {
     FP_CUDA(cudaMemset(dbad.p, 0, sizeof(int)));
     const Mesh *m = s->mesh;
     if (n > 0)
-        k_validate<<<(n + 127) / 128, 128>>>(n, start, dx.p, have_hint ? dt_in.p : nullptr, m->n_tets, m->geo.p,
-                                             m->tet_nbr.p, m->tet_nodes.p, m->xyz.p, dt_out.p, dbad.p);
+        { k_validate<<<(n + 127) / 128, 128>>>(n, start, dx.p, have_hint ? dt_in.p : nullptr, m->n_tets, m->geo.p,
+                                             m->tet_nbr.p, m->tet_nodes.p, m->xyz.p, dt_out.p, dbad.p); note_launch(); }
     FP_CUDA(cudaGetLastError());
     int bad = 0;
     FP_CUDA(cudaMemcpy(&bad, dbad.p, sizeof(int), cudaMemcpyDeviceToHost));
@@ -907,6 +1162,11 @@ int upload_particles(Sim *s) {
     const int n = (int)s->h_tet.size();
     int rc = particles_alloc(s, std::max<size_t>((size_t)n, 1));
     if (rc) return rc;
+    // per-tet accumulators: one set per species in MIXED (fixed point is per unit charge)
+    s->nsp = s->mixed ? std::max(1, s->n_species) : 1;
+    if ((rc = s->tacc.alloc((size_t)kNV * s->mesh->n_tets * s->nsp)) ||
+        (rc = s->wacc.alloc((size_t)4 * s->mesh->n_tets * s->nsp)))
+        return rc;
     DevBuf<double> dx, dv;
     DevBuf<int> dt;
     if ((rc = dx.upload(s->h_x)) || (rc = dv.upload(s->h_v)) || (rc = dt.upload(s->h_tet))) return rc;
@@ -919,15 +1179,15 @@ int upload_particles(Sim *s) {
         const int cnt = end - start;
         const int blocks = (cnt + 255) / 256;
         if (s->mixed)
-            k_load_particles<float><<<blocks, 256, 0, s->stream>>>(
+            { k_load_particles<float><<<blocks, 256, 0, s->stream>>>(
                 cnt, start, dx.p + 3 * (size_t)start, dv.p + 3 * (size_t)start, dt.p, sp, start, (float *)k.x[0].p,
                 (float *)k.x[1].p, (float *)k.x[2].p, (float *)k.v[0].p, (float *)k.v[1].p, (float *)k.v[2].p, k.key.p,
-                k.id.p);
+                k.id.p); note_launch(); }
         else
-            k_load_particles<double><<<blocks, 256, 0, s->stream>>>(
+            { k_load_particles<double><<<blocks, 256, 0, s->stream>>>(
                 cnt, start, dx.p + 3 * (size_t)start, dv.p + 3 * (size_t)start, dt.p, sp, start, (double *)k.x[0].p,
                 (double *)k.x[1].p, (double *)k.x[2].p, (double *)k.v[0].p, (double *)k.v[1].p, (double *)k.v[2].p,
-                k.key.p, k.id.p);
+                k.key.p, k.id.p); note_launch(); }
         start = end;
     }
     FP_CUDA(cudaGetLastError());
@@ -959,22 +1219,21 @@ int stage_coefficients(Sim *s, const double *e, const double *b) {
     const Mesh *m = s->mesh;
     const int nt = m->n_tets;
     if (s->mixed)
-        k_coefficients<float><<<(nt + 255) / 256, 256, 0, s->stream>>>(
+        { k_coefficients<float><<<(nt + 255) / 256, 256, 0, s->stream>>>(
             nt, m->geo.p, m->tet_edge.p, m->tet_face.p, m->tet_nodes.p, m->tet_sign.p, m->tet_vol.p, m->xyz.p, e, b,
-            (float *)s->coef.p);
+            make_double3(s->cfg.b0[0], s->cfg.b0[1], s->cfg.b0[2]), (float *)s->coef.p); note_launch(); }
     else
-        k_coefficients<double><<<(nt + 255) / 256, 256, 0, s->stream>>>(
+        { k_coefficients<double><<<(nt + 255) / 256, 256, 0, s->stream>>>(
             nt, m->geo.p, m->tet_edge.p, m->tet_face.p, m->tet_nodes.p, m->tet_sign.p, m->tet_vol.p, m->xyz.p, e, b,
-            (double *)s->coef.p);
+            make_double3(s->cfg.b0[0], s->cfg.b0[1], s->cfg.b0[2]), (double *)s->coef.p); note_launch(); }
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
 }
 
-template <typename R>
-static int launch_push(Sim *s, int mode) {
+template <typename R, typename V>
+static void fill_push_args(Sim *s, PushArgs<R, V> &a) {
     const Mesh *m = s->mesh;
     PartBank &src = s->bank[s->cur], &dst = s->bank[1 - s->cur];
-    PushArgs<R> a;
     Control *dc = s->dctl.p;
     a.d_n_alive = &dc->n_alive;
     a.skey = s->skey.p;
@@ -1000,14 +1259,11 @@ static int launch_push(Sim *s, int mode) {
     a.dvh = (R *)dst.vh.p;
     a.cap = (long)s->cap;
     a.geo = m->geo.p;
+    a.geo32 = m->geo32.p;
     a.coef = (const R *)s->coef.p;
     a.tnodes = m->tet_nodes.p;
     a.tnbr = m->tet_nbr.p;
-    for (int k = 0; k < kMaxSpecies; k++) {
-        a.sp.qm[k] = k < s->n_species ? s->sp_q[k] / s->sp_m[k] : 0.0;
-        a.sp.qw[k] = k < s->n_species ? s->sp_q[k] * s->sp_w[k] : 0.0;
-        a.sp.mw[k] = k < s->n_species ? s->sp_m[k] * s->sp_w[k] : 0.0;
-    }
+    a.sp = species_params(s);
     a.dt = s->cfg.dt;
     // Adams-Bashforth weights (newest first); the order ramps 1..k at start-up
     static const double W[5][5] = {{1.0, 0, 0, 0, 0},
@@ -1020,60 +1276,98 @@ static int launch_push(Sim *s, int mode) {
     for (int k = 0; k < 5; k++) a.abw[k] = W[a.ab_order - 1][k];
     a.walk_cap = std::min(s->cfg.walk_cap, kMaxWalk);
     a.dead_key = (uint32_t)m->n_tets << 2;
-    a.tacc = s->tacc.p;
-    a.wacc = s->wacc.p;
-    a.bcar = s->bcar.p;
+    a.nsp = s->nsp;
+    a.tacc = (V *)s->tacc.p;
+    a.wacc = (V *)s->wacc.p;
+    a.bcar = (V *)s->bcar.p;
     a.bcar_key = s->bcar_key.p;
     a.okey = s->okey.p;
-    a.oval = s->oval.p;
+    a.oval = (V *)s->oval.p;
     a.ocount = &dc->n_over;
     a.ocap = s->ocap;
     a.oshift = 6 + std::max(1, bitlen((unsigned long long)s->n_total));
     a.status = &dc->status;
-    a.n_alive_next = &dc->n_alive;   // rewritten below through a scratch counter
-    a.ke_part = s->ke_part.p;
     // the live count of this step is read at kernel start; the next count is
-    // accumulated into a separate counter and copied over afterwards
+    // accumulated in a separate counter and copied over after the step
     a.n_alive_next = reinterpret_cast<int *>(&dc->pad);
+    a.ke_part = s->ke_part.p;
+}
+
+template <typename R, typename V>
+static int launch_push(Sim *s, int mode) {
+    PushArgs<R, V> a;
+    fill_push_args(s, a);
+    Control *dc = s->dctl.p;
     // the live particles of this step are the first hctl->n_alive sorted entries
     const int live = s->hctl->n_alive;
     const int blocks = std::max(1, (live + kPushBlock - 1) / kPushBlock);
     s->last_push_blocks = blocks;
     FP_CUDA(cudaMemsetAsync(&dc->pad, 0, sizeof(int), s->stream));
-    if (mode == 2)
-        k_push<R, 2><<<blocks, kPushBlock, 0, s->stream>>>(a);
-    else if (mode == 1)
-        k_push<R, 1><<<blocks, kPushBlock, 0, s->stream>>>(a);
-    else
-        k_push<R, 0><<<blocks, kPushBlock, 0, s->stream>>>(a);
+    prof_begin(s, PH_PUSH);
+    if (std::is_same<R, float>::value) {
+        const PushArgs<float, long long> &am = reinterpret_cast<const PushArgs<float, long long> &>(a);
+        if (mode == 2) { k_push_mixed<2><<<blocks, kPushBlock, 0, s->stream>>>(am); note_launch(); }
+        else if (mode == 1) { k_push_mixed<1><<<blocks, kPushBlock, 0, s->stream>>>(am); note_launch(); }
+        else { k_push_mixed<0><<<blocks, kPushBlock, 0, s->stream>>>(am); note_launch(); }
+    } else {
+        const PushArgs<double, double> &ap = reinterpret_cast<const PushArgs<double, double> &>(a);
+        if (mode == 2) { k_push_plain<2><<<blocks, kPushBlock, 0, s->stream>>>(ap); note_launch(); }
+        else if (mode == 1) { k_push_plain<1><<<blocks, kPushBlock, 0, s->stream>>>(ap); note_launch(); }
+        else { k_push_plain<0><<<blocks, kPushBlock, 0, s->stream>>>(ap); note_launch(); }
+    }
+    prof_end(s, PH_PUSH);
+    prof_begin(s, PH_DEPOSIT);
     FP_CUDA(cudaGetLastError());
-    k_fixup<<<(2 * blocks + 255) / 256, 256, 0, s->stream>>>(blocks, s->skey.p, &dc->n_alive, s->bcar_key.p, s->bcar.p,
-                                                             s->tacc.p);
+    { k_fixup<V><<<(2 * blocks + 255) / 256, 256, 0, s->stream>>>(blocks, s->nsp, s->skey.p, &dc->n_alive, s->bcar_key.p, (const V *)s->bcar.p, (V *)s->tacc.p); note_launch(); }
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
 }
 
 int particle_push(Sim *s, int charge_only) {
     const Mesh *m = s->mesh;
-    FP_CUDA(cudaMemsetAsync(s->tacc.p, 0, sizeof(double) * kNV * (size_t)m->n_tets, s->stream));
-    FP_CUDA(cudaMemsetAsync(s->wacc.p, 0, sizeof(double) * 4 * (size_t)m->n_tets, s->stream));
-    FP_CUDA(cudaMemsetAsync(&s->dctl.p->n_over, 0, sizeof(int), s->stream));
-    if (s->n_total > 0) {
+    const size_t vsz = 8;   // double or int64 accumulators
+    for (int attempt = 0;; attempt++) {
+        FP_CUDA(cudaMemsetAsync(s->tacc.p, 0, vsz * kNV * (size_t)m->n_tets * s->nsp, s->stream));
+        FP_CUDA(cudaMemsetAsync(s->wacc.p, 0, vsz * 4 * (size_t)m->n_tets * s->nsp, s->stream));
+        FP_CUDA(cudaMemsetAsync(&s->dctl.p->n_over, 0, sizeof(int), s->stream));
+        if (s->n_total == 0) break;
         const int mode = charge_only ? 2 : (s->ab ? 1 : 0);
-        int rc = s->mixed ? launch_push<float>(s, mode) : launch_push<double>(s, mode);
+        int rc = s->mixed ? launch_push<float, long long>(s, mode) : launch_push<double, double>(s, mode);
         if (rc) return rc;
-        // overflow records: sort by (tet, wall, particle, piece) and add in that order
+        // the push reads the current bank and writes the other one, so a push
+        // whose record buffer overflowed is simply run again with more room
+        FP_CUDA(cudaMemcpyAsync(&s->hctl->n_over, &s->dctl.p->n_over, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+        FP_CUDA(cudaStreamSynchronize(s->stream));
+        const int need = s->hctl->n_over;
+        if (need <= s->ocap) break;
+        if (attempt >= 2 || need >= (1 << 30)) {
+            s->host_status |= ST_OVERFLOW;
+            set_error("crossing-path records exceed the buffer");
+            return PIC_ERR_OVERFLOW;
+        }
+        if ((rc = overflow_alloc(s, std::min(need + need / 2 + 1024, (1 << 30) - 1)))) return rc;
+        // clear the latched overflow bit of this attempt
+        uint32_t st = 0;
+        FP_CUDA(cudaMemcpy(&st, &s->dctl.p->status, sizeof(uint32_t), cudaMemcpyDeviceToHost));
+        st &= ~(uint32_t)ST_OVERFLOW;
+        FP_CUDA(cudaMemcpy(&s->dctl.p->status, &st, sizeof(uint32_t), cudaMemcpyHostToDevice));
+    }
+    if (s->n_total > 0) {
+        int rc;
+        // crossing records: sort by (accumulator, wall, particle, piece) and add in that order
         const int oshift = 6 + std::max(1, bitlen((unsigned long long)s->n_total));
-        const int bits = oshift + bitlen(((unsigned long long)m->n_tets << 1) | 1ull);
-        unsigned long long *ok;
-        uint32_t *ov;
-        // clamp the device count to the capacity before sorting
-        rc = radix_sort<unsigned long long>(s->stream, s->okey.p, s->okey2.p, s->oidx.p, s->okey.p, s->oidx2.p,
-                                            &s->dctl.p->n_over, s->ocap, bits, &s->osortw, &ok, &ov);
-        if (rc) return rc;
-        k_overflow_reduce<<<(s->ocap + 255) / 256, 256, 0, s->stream>>>(&s->dctl.p->n_over, s->ocap, ok, ov, s->oval.p,
-                                                                        oshift, s->tacc.p, s->wacc.p);
-        FP_CUDA(cudaGetLastError());
+        const int bits = oshift + bitlen(((unsigned long long)m->n_tets * s->nsp << 1) | 1ull);
+        const int nover = s->hctl->n_over;   // known on the host since the push
+        if (nover > 0) {
+            unsigned long long *ok;
+            uint32_t *ov;
+            rc = radix_sort<unsigned long long>(s->stream, s->okey.p, s->okey2.p, s->oidx.p, s->okey.p, s->oidx2.p,
+                                                nullptr, nover, bits, &s->osortw, &ok, &ov);
+            if (rc) return rc;
+            if (s->mixed) { k_overflow_reduce<long long><<<(nover + 255) / 256, 256, 0, s->stream>>>(&s->dctl.p->n_over, nover, ok, ov, (const long long *)s->oval.p, oshift, (long long *)s->tacc.p, (long long *)s->wacc.p); note_launch(); }
+            else { k_overflow_reduce<double><<<(nover + 255) / 256, 256, 0, s->stream>>>(&s->dctl.p->n_over, nover, ok, ov, (const double *)s->oval.p, oshift, (double *)s->tacc.p, (double *)s->wacc.p); note_launch(); }
+            FP_CUDA(cudaGetLastError());
+        }
         // the next step's live count; the new bank holds the first `live` entries
         FP_CUDA(cudaMemcpyAsync(&s->dctl.p->n_alive, &s->dctl.p->pad, sizeof(int), cudaMemcpyDeviceToDevice, s->stream));
         s->cur = 1 - s->cur;
@@ -1087,11 +1381,14 @@ int reduce_to_entities(Sim *s) {
     const Mesh *m = s->mesh;
     std::swap(s->rho_prev, s->rho);
     std::swap(s->wall_prev, s->wall);
-    k_gather_edges<<<(m->n_edges + 255) / 256, 256, 0, s->stream>>>(m->n_edges, m->e2t.rowptr.p, m->e2t.col.p,
-                                                                    s->tacc.p, s->g.p, s->dg.p, s->g_new.p);
-    k_gather_nodes<<<(m->n_nodes + 255) / 256, 256, 0, s->stream>>>(m->n_nodes, m->n2t.rowptr.p, m->n2t.col.p,
-                                                                    s->tacc.p, s->wacc.p, s->wall_prev.p, s->rho.p,
-                                                                    s->wall.p);
+    const SpeciesParams sp = species_params(s);
+    if (s->mixed) {
+        { k_gather_edges<long long><<<(m->n_edges + 255) / 256, 256, 0, s->stream>>>(m->n_edges, m->e2t.rowptr.p, m->e2t.col.p, (const long long *)s->tacc.p, s->nsp, sp, s->g.p, s->dg.p, s->g_new.p); note_launch(); }
+        { k_gather_nodes<long long><<<(m->n_nodes + 255) / 256, 256, 0, s->stream>>>(m->n_nodes, m->n2t.rowptr.p, m->n2t.col.p, (const long long *)s->tacc.p, (const long long *)s->wacc.p, s->nsp, sp, s->wall_prev.p, s->rho.p, s->wall.p); note_launch(); }
+    } else {
+        { k_gather_edges<double><<<(m->n_edges + 255) / 256, 256, 0, s->stream>>>(m->n_edges, m->e2t.rowptr.p, m->e2t.col.p, (const double *)s->tacc.p, 1, sp, s->g.p, s->dg.p, s->g_new.p); note_launch(); }
+        { k_gather_nodes<double><<<(m->n_nodes + 255) / 256, 256, 0, s->stream>>>(m->n_nodes, m->n2t.rowptr.p, m->n2t.col.p, (const double *)s->tacc.p, (const double *)s->wacc.p, 1, sp, s->wall_prev.p, s->rho.p, s->wall.p); note_launch(); }
+    }
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
 }

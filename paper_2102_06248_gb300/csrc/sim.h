@@ -17,6 +17,8 @@ struct CgState {
     double bb;        // b.b
     double tol2;      // tol^2
     double alpha, beta;
+    double abs_inf;   // stop also when max|r| <= abs_inf (negative: off)
+    double fallback_tol2;
     int iters;
     int done;
     int max_iters;
@@ -38,6 +40,7 @@ struct Control {
     CgState cg;
     CgState lap;
     DiagDev diag;
+    double qmax;      // max |rho + wall| of the current step (completion threshold)
     uint32_t status;
     int n_alive;
     int n_over;
@@ -66,6 +69,9 @@ struct SortWork {
     size_t tiles_cap = 0;
 };
 
+// device-time phases of a step (CUDA events on the sim's stream)
+enum Phase { PH_SORT = 0, PH_COEF, PH_PUSH, PH_DEPOSIT, PH_RHS, PH_CG, PH_COMPLETION, PH_FIELD_OTHER, PH_SPMV, PH_COUNT };
+
 struct Sim {
     const Mesh *mesh = nullptr;
     pic_config cfg{};
@@ -80,6 +86,7 @@ struct Sim {
 
     // species
     int n_species = 0;
+    int nsp = 1;              // species slots per tet in the accumulators (MIXED: n_species)
     double sp_q[kMaxSpecies], sp_m[kMaxSpecies], sp_w[kMaxSpecies];
 
     // particles
@@ -133,9 +140,22 @@ struct Sim {
     int last_lap_iters = 0;
     int last_push_blocks = 0;       // grid of the last push (kinetic-energy partials)
     uint32_t host_status = 0;       // latched errors seen on the host
+    // optional phase profiler
+    int profile = 0;
+    cudaEvent_t ev0[PH_COUNT] = {}, ev1[PH_COUNT] = {};
+    bool ev_used[PH_COUNT] = {};
+    double prof_ms[PH_COUNT] = {};
+    long long prof_n[PH_COUNT] = {};
+    std::vector<cudaEvent_t> spmv_ev;   // pairs around each Newmark SpMV launch
+    int spmv_used = 0;
 };
 
+void prof_begin(Sim *s, int ph);
+void prof_end(Sim *s, int ph);
+void prof_collect(Sim *s);   // after a stream synchronisation
+
 // ---- launchers (particles.cu) ----
+SpeciesParams species_params(const Sim *s);
 int particles_alloc(Sim *s, size_t cap);
 int sort_particles(Sim *s);
 int stage_coefficients(Sim *s, const double *e, const double *b);
@@ -148,7 +168,8 @@ int solver_alloc(Sim *s);
 int newmark_rhs(Sim *s);
 int pcg_newmark(Sim *s);
 int gradient_completion(Sim *s);
-int laplacian_solve(Sim *s, const double *rhs_nodes, double *x_nodes, double tol);
+int laplacian_solve(Sim *s, const double *rhs_nodes, double *x_nodes, double tol, const double *abs_src,
+                    double abs_factor);
 int faraday_update(Sim *s);
 int compute_diagnostics(Sim *s);
 int init_fields(Sim *s);

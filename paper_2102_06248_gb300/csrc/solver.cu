@@ -16,9 +16,10 @@ namespace fp {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kLanes = 16;                       // lanes per CSR row
+constexpr int kLanes = 4;                        // lanes per CSR row (~16 nonzeros: 4 each)
+constexpr int kRowsPerWarp = 32 / kLanes;
 constexpr int kRowsPerBlock = kThreads / kLanes;
-constexpr int kMaxBlocks = 152 * 8;
+constexpr int kMaxBlocks = 152 * 16;             // 16 blocks of 256 threads per SM
 
 // ---- deterministic block / grid reductions ----
 template <int N>
@@ -117,12 +118,12 @@ __global__ void __launch_bounds__(kThreads) k_rhs_we(int n, const int *__restric
                                                      const double *__restrict__ gp, double *__restrict__ rhs,
                                                      double *__restrict__ x) {
     const int lane = threadIdx.x % kLanes;
-    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~1; r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
-        const int r = r0_ + ((threadIdx.x / kLanes) & 1);
+    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
+        const int r = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
         const bool rv = r < n;
         const int kb = rv ? rp[r] : 0, kend = rv ? rp[r + 1] : 0;
         double sm = 0.0, sk = 0.0;
-        for (int k = kb + lane; k < kend; k += kLanes) {
+        _Pragma("unroll 4") for (int k = kb + lane; k < kend; k += kLanes) {
             const int j = col[k];
             const double ej = e[j], epj = ep[j];
             sm += Mv[k] * (2.0 * ej - epj);
@@ -142,12 +143,12 @@ __global__ void __launch_bounds__(kThreads) k_face_hb(int n, const int *__restri
                                                       const double *__restrict__ Hv, const double *__restrict__ b,
                                                       const double *__restrict__ bp, double *__restrict__ hb) {
     const int lane = threadIdx.x % kLanes;
-    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~1; r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
-        const int r = r0_ + ((threadIdx.x / kLanes) & 1);
+    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
+        const int r = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
         const bool rv = r < n;
         const int kb = rv ? rp[r] : 0, kend = rv ? rp[r + 1] : 0;
         double s = 0.0;
-        for (int k = kb + lane; k < kend; k += kLanes) {
+        _Pragma("unroll 4") for (int k = kb + lane; k < kend; k += kLanes) {
             const int j = col[k];
             s += Hv[k] * (b[j] + bp[j]);
         }
@@ -167,12 +168,12 @@ __global__ void __launch_bounds__(kThreads) k_rhs_mfem(int n, const int *__restr
                                                        const double *__restrict__ hb, double *__restrict__ rhs,
                                                        double *__restrict__ x) {
     const int lane = threadIdx.x % kLanes;
-    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~1; r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
-        const int r = r0_ + ((threadIdx.x / kLanes) & 1);
+    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
+        const int r = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
         const bool rv = r < n;
         const int kb = rv ? rp[r] : 0, kend = rv ? rp[r + 1] : 0;
         double sm = 0.0, sk = 0.0, sc = 0.0;
-        for (int k = kb + lane; k < kend; k += kLanes) {
+        _Pragma("unroll 4") for (int k = kb + lane; k < kend; k += kLanes) {
             const int j = col[k];
             const double ej = e[j], epj = ep[j];
             sm += Mv[k] * epj;
@@ -197,16 +198,18 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(int n, const int *__restri
                                                       const double *__restrict__ Av, const double *__restrict__ Dinv,
                                                       const double *__restrict__ b, const double *__restrict__ x,
                                                       double *__restrict__ r, double *__restrict__ z,
-                                                      double *__restrict__ p, double *part, CgState *st) {
-    __shared__ double sh[3 * kThreads / 32];
+                                                      double *__restrict__ p, double *part, CgState *st,
+                                                      const double *abs_src, double abs_factor) {
+    __shared__ double sh[4 * kThreads / 32];
     const int lane = threadIdx.x % kLanes;
     double acc[3] = {0.0, 0.0, 0.0};
-    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~1; r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
-        const int i = r0_ + ((threadIdx.x / kLanes) & 1);
+    double amax[1] = {0.0};
+    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
+        const int i = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
         const bool rv = i < n;
         const int kb = rv ? rp[i] : 0, kend = rv ? rp[i + 1] : 0;
         double s = 0.0;
-        for (int k = kb + lane; k < kend; k += kLanes) s += Av[k] * x[col[k]];
+        _Pragma("unroll 4") for (int k = kb + lane; k < kend; k += kLanes) s += Av[k] * x[col[k]];
         s = row_reduce(s);
         if (rv && lane == 0) {
             const double ri = b[i] - s, zi = Dinv[i] * ri;
@@ -216,20 +219,30 @@ __global__ void __launch_bounds__(kThreads) k_cg_init(int n, const int *__restri
             acc[0] += ri * zi;
             acc[1] += ri * ri;
             acc[2] += b[i] * b[i];
+            amax[0] = fmax(amax[0], fabs(ri));
         }
     }
     block_sum<3>(acc, sh);
-    if (arrive<3>(acc, part, &st->count_a)) {
-        double tot[3];
+    block_max<1>(amax, sh + 3 * kThreads / 32);
+    double both[4] = {acc[0], acc[1], acc[2], amax[0]};
+    if (arrive<4>(both, part, &st->count_a)) {
+        double tot[3], mx[1];
         grid_combine<3, false>(tot, part, sh);
+        grid_combine<1, true>(mx, part + 3 * gridDim.x, sh + 3 * kThreads / 32);
         if (threadIdx.x == 0) {
+            if (abs_src) {
+                // absolute threshold from a device scalar; without charge, the relative fallback
+                const double q = *abs_src;
+                if (q > 0.0) st->abs_inf = abs_factor * q;
+                else st->tol2 = st->fallback_tol2;
+            }
             st->rz = tot[0];
             st->rr = tot[1];
             st->bb = tot[2];
             st->iters = 0;
             st->failed = 0;
             st->beta = 0.0;
-            st->done = (tot[2] == 0.0) || (tot[1] <= st->tol2 * tot[2]);
+            st->done = (tot[2] == 0.0) || (tot[1] <= st->tol2 * tot[2]) || (mx[0] <= st->abs_inf);
             st->count_a = 0;
         }
     }
@@ -252,12 +265,12 @@ __global__ void __launch_bounds__(kThreads) k_cg_a(int n, const int *__restrict_
     const double beta = st->beta;
     const int lane = threadIdx.x % kLanes;
     double acc[1] = {0.0};
-    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~1; r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
-        const int i = r0_ + ((threadIdx.x / kLanes) & 1);
+    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
+        const int i = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
         const bool rv = i < n;
         const int kb = rv ? rp[i] : 0, kend = rv ? rp[i + 1] : 0;
         double s = 0.0;
-        for (int k = kb + lane; k < kend; k += kLanes) {
+        _Pragma("unroll 4") for (int k = kb + lane; k < kend; k += kLanes) {
             const int j = col[k];
             const double pj = first ? z[j] : z[j] + beta * pold[j];
             s += Av[k] * pj;
@@ -286,10 +299,11 @@ __global__ void __launch_bounds__(kThreads) k_cg_b(int n, const double *__restri
                                                    double *__restrict__ r, double *__restrict__ z,
                                                    const double *__restrict__ p, const double *__restrict__ q,
                                                    double *part, CgState *st) {
-    __shared__ double sh[2 * kThreads / 32];
+    __shared__ double sh[3 * kThreads / 32];
     if (st->done) return;
     const double alpha = st->alpha;
     double acc[2] = {0.0, 0.0};
+    double amax[1] = {0.0};
     for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) {
         x[i] += alpha * p[i];
         const double ri = r[i] - alpha * q[i];
@@ -298,17 +312,21 @@ __global__ void __launch_bounds__(kThreads) k_cg_b(int n, const double *__restri
         z[i] = zi;
         acc[0] += ri * zi;
         acc[1] += ri * ri;
+        amax[0] = fmax(amax[0], fabs(ri));
     }
     block_sum<2>(acc, sh);
-    if (arrive<2>(acc, part, &st->count_b)) {
-        double tot[2];
+    block_max<1>(amax, sh + 2 * kThreads / 32);
+    double both[3] = {acc[0], acc[1], amax[0]};
+    if (arrive<3>(both, part, &st->count_b)) {
+        double tot[2], mx[1];
         grid_combine<2, false>(tot, part, sh);
+        grid_combine<1, true>(mx, part + 2 * gridDim.x, sh + 2 * kThreads / 32);
         if (threadIdx.x == 0) {
             st->beta = tot[0] / st->rz;
             st->rz = tot[0];
             st->rr = tot[1];
             st->iters += 1;
-            if (tot[1] <= st->tol2 * st->bb) st->done = 1;
+            if (tot[1] <= st->tol2 * st->bb || mx[0] <= st->abs_inf) st->done = 1;
             else if (st->iters >= st->max_iters) {
                 st->done = 1;
                 st->failed = 1;
@@ -327,12 +345,12 @@ __global__ void __launch_bounds__(kThreads) k_gc_w(int n, const int *__restrict_
                                                    const double *__restrict__ gn, const double *__restrict__ g,
                                                    const double *__restrict__ gp, double *__restrict__ w) {
     const int lane = threadIdx.x % kLanes;
-    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~1; r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
-        const int r = r0_ + ((threadIdx.x / kLanes) & 1);
+    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
+        const int r = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
         const bool rv = r < n;
         const int kb = rv ? rp[r] : 0, kend = rv ? rp[r + 1] : 0;
         double s = 0.0;
-        for (int k = kb + lane; k < kend; k += kLanes) {
+        _Pragma("unroll 4") for (int k = kb + lane; k < kend; k += kLanes) {
             const int j = col[k];
             const double t = form == PIC_FORM_WE ? 2.0 * e[j] - ep[j] - x[j] : ep[j] - x[j];
             s += Mv[k] * t;
@@ -402,12 +420,12 @@ __global__ void __launch_bounds__(kThreads) k_resid(int n, const int *__restrict
     __shared__ double sh[3 * kThreads / 32];
     const int lane = threadIdx.x % kLanes;
     double acc[3] = {0.0, 0.0, 0.0};
-    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~1; r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
-        const int r = r0_ + ((threadIdx.x / kLanes) & 1);
+    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
+        const int r = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
         const bool rv = r < n;
         const int kb = rv ? rp[r] : 0, kend = rv ? rp[r + 1] : 0;
         double sm = 0.0, sk = 0.0;
-        for (int k = kb + lane; k < kend; k += kLanes) {
+        _Pragma("unroll 4") for (int k = kb + lane; k < kend; k += kLanes) {
             const double xj = x[col[k]];
             sm += Mv[k] * xj;
             sk += Kv[k] * xj;
@@ -518,12 +536,12 @@ __global__ void __launch_bounds__(kThreads) k_diag_energy_b(int nf, const int *_
     __shared__ double sh[kThreads / 32];
     const int lane = threadIdx.x % kLanes;
     double acc[1] = {0.0};
-    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~1; r0_ < nf; r0_ += gridDim.x * kRowsPerBlock) {
-        const int r = r0_ + ((threadIdx.x / kLanes) & 1);
+    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < nf; r0_ += gridDim.x * kRowsPerBlock) {
+        const int r = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
         const bool rv = r < nf;
         const int kb = rv ? rp[r] : 0, kend = rv ? rp[r + 1] : 0;
         double s = 0.0;
-        for (int k = kb + lane; k < kend; k += kLanes) s += Hv[k] * b[col[k]];
+        _Pragma("unroll 4") for (int k = kb + lane; k < kend; k += kLanes) s += Hv[k] * b[col[k]];
         s = row_reduce(s);
         if (rv && lane == 0) acc[0] += b[r] * s;
     }
@@ -545,6 +563,24 @@ __global__ void __launch_bounds__(kThreads) k_sum_ke(int nb, const double *__res
     for (int b = threadIdx.x; b < nb; b += kThreads) acc[0] += kp[b];
     block_sum<1>(acc, sh);
     if (threadIdx.x == 0) dg->energy_k = acc[0];
+}
+
+// max_n |a_n + b_n| (deterministic; max is order-free)
+__global__ void __launch_bounds__(kThreads) k_max_abs_sum(int n, const double *__restrict__ a, const double *__restrict__ b,
+                                                          double *part, unsigned *counter, double *out) {
+    __shared__ double sh[kThreads / 32];
+    double acc[1] = {0.0};
+    for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads)
+        acc[0] = fmax(acc[0], fabs(a[i] + b[i]));
+    block_max<1>(acc, sh);
+    if (arrive<1>(acc, part, counter)) {
+        double tot[1];
+        grid_combine<1, true>(tot, part, sh);
+        if (threadIdx.x == 0) {
+            *out = tot[0];
+            *counter = 0;
+        }
+    }
 }
 
 int grid_for_rows(int n) { return std::max(1, std::min(kMaxBlocks, (n + kRowsPerBlock - 1) / kRowsPerBlock)); }
@@ -575,7 +611,10 @@ struct CgProblem {
     double *x, *r, *z, *p0, *p1, *q, *part;
     CgState *st;        // device
     CgState *hst;       // host mirror inside the pinned control block
-    size_t st_off;      // byte offset of st inside Control
+    bool timed = false; // time each SpMV launch (profiler)
+    const double *abs_src = nullptr;  // device scalar: stop also when max|r| <= abs_factor * (*abs_src)
+    double abs_factor = 0.0;
+    double fallback_tol = 0.0;        // relative tolerance used when *abs_src is 0
 };
 
 int run_pcg(Sim *s, CgProblem &P, double tol, int max_iters, int *last_iters) {
@@ -583,24 +622,51 @@ int run_pcg(Sim *s, CgProblem &P, double tol, int max_iters, int *last_iters) {
     CgState init{};
     init.tol2 = tol * tol;
     init.max_iters = max_iters;
+    init.abs_inf = -1.0;
+    init.fallback_tol2 = P.fallback_tol * P.fallback_tol;
     FP_CUDA(cudaMemcpyAsync(P.st, &init, sizeof(CgState), cudaMemcpyHostToDevice, st));
     const int gr = grid_for_rows(P.n), ge = grid_for_elems(P.n);
-    k_cg_init<<<gr, kThreads, 0, st>>>(P.n, P.rp, P.col, P.Av, P.Dinv, P.b, P.x, P.r, P.z, P.p0, P.part, P.st);
-    k_cg_zero_if_trivial<<<ge, kThreads, 0, st>>>(P.n, P.x, P.st);
+    { k_cg_init<<<gr, kThreads, 0, st>>>(P.n, P.rp, P.col, P.Av, P.Dinv, P.b, P.x, P.r, P.z, P.p0, P.part, P.st, P.abs_src, P.abs_factor); note_launch(); }
+    { k_cg_zero_if_trivial<<<ge, kThreads, 0, st>>>(P.n, P.x, P.st); note_launch(); }
     FP_CUDA(cudaGetLastError());
     int launched = 0;
     int chunk = std::max(1, *last_iters - 1);
     double *pold = P.p0, *pnew = P.p1;
     for (;;) {
         for (int c = 0; c < chunk; c++) {
-            k_cg_a<<<gr, kThreads, 0, st>>>(P.n, P.rp, P.col, P.Av, P.z, pold, pnew, P.q, P.part, P.st);
-            k_cg_b<<<ge, kThreads, 0, st>>>(P.n, P.Dinv, P.x, P.r, P.z, pnew, P.q, P.part + 3 * kMaxBlocks, P.st);
+            const bool timed = P.timed && s->profile;
+            if (timed) {
+                if ((size_t)(2 * s->spmv_used + 2) > s->spmv_ev.size()) {
+                    cudaEvent_t a, b;
+                    cudaEventCreate(&a);
+                    cudaEventCreate(&b);
+                    s->spmv_ev.push_back(a);
+                    s->spmv_ev.push_back(b);
+                }
+                cudaEventRecord(s->spmv_ev[2 * s->spmv_used], st);
+            }
+            { k_cg_a<<<gr, kThreads, 0, st>>>(P.n, P.rp, P.col, P.Av, P.z, pold, pnew, P.q, P.part, P.st); note_launch(); }
+            if (timed) cudaEventRecord(s->spmv_ev[2 * s->spmv_used++ + 1], st);
+            { k_cg_b<<<ge, kThreads, 0, st>>>(P.n, P.Dinv, P.x, P.r, P.z, pnew, P.q, P.part + 3 * kMaxBlocks, P.st); note_launch(); }
             std::swap(pold, pnew);
             launched++;
         }
         FP_CUDA(cudaGetLastError());
         FP_CUDA(cudaMemcpyAsync(P.hst, P.st, sizeof(CgState), cudaMemcpyDeviceToHost, st));
         FP_CUDA(cudaStreamSynchronize(st));
+        if (s->spmv_used) {
+            // SpMV launches that ran past convergence return at once; only the
+            // iterations the solve performed are counted
+            const int ran = std::min(s->spmv_used, std::max(0, P.hst->iters - (launched - s->spmv_used)));
+            for (int k = 0; k < ran; k++) {
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, s->spmv_ev[2 * k], s->spmv_ev[2 * k + 1]) == cudaSuccess) {
+                    s->prof_ms[PH_SPMV] += ms;
+                    s->prof_n[PH_SPMV] += 1;
+                }
+            }
+            s->spmv_used = 0;
+        }
         if (P.hst->done) break;
         chunk = std::max(2, std::min(s->cfg.cg_check_every, P.hst->iters / 8 + 2));
         if (launched > max_iters + 64) break;
@@ -651,10 +717,10 @@ int solver_alloc(Sim *s) {
     const double c4 = 0.25 * s->cfg.dt * s->cfg.dt;
     if ((rc = s->A_val.alloc(std::max(m->A.nnz, 1)))) return rc;
     if (m->A.nnz > 0) {
-        k_axpby<<<(m->A.nnz + 255) / 256, 256>>>(m->A.nnz, 1.0, m->M_val.p, c4, m->K_val.p, s->A_val.p);
-        k_recip_diag<<<(ni + 255) / 256, 256>>>(ni, m->A.rowptr.p, m->A.col.p, s->A_val.p, s->Dinv.p);
+        { k_axpby<<<(m->A.nnz + 255) / 256, 256>>>(m->A.nnz, 1.0, m->M_val.p, c4, m->K_val.p, s->A_val.p); note_launch(); }
+        { k_recip_diag<<<(ni + 255) / 256, 256>>>(ni, m->A.rowptr.p, m->A.col.p, s->A_val.p, s->Dinv.p); note_launch(); }
     }
-    if (nin > 0) k_recip_diag<<<(nin + 255) / 256, 256>>>(nin, m->L.rowptr.p, m->L.col.p, m->L_val.p, s->L_Dinv.p);
+    if (nin > 0) { k_recip_diag<<<(nin + 255) / 256, 256>>>(nin, m->L.rowptr.p, m->L.col.p, m->L_val.p, s->L_Dinv.p); note_launch(); }
     FP_CUDA(cudaGetLastError());
     FP_CUDA(cudaDeviceSynchronize());
     return PIC_OK;
@@ -666,15 +732,15 @@ int newmark_rhs(Sim *s) {
     if (ni == 0) return PIC_OK;
     const double dt = s->cfg.dt, c4 = 0.25 * dt * dt;
     if (s->cfg.form == PIC_FORM_WE) {
-        k_rhs_we<<<grid_for_rows(ni), kThreads, 0, s->stream>>>(ni, m->A.rowptr.p, m->A.col.p, m->M_val.p, m->K_val.p, c4,
+        { k_rhs_we<<<grid_for_rows(ni), kThreads, 0, s->stream>>>(ni, m->A.rowptr.p, m->A.col.p, m->M_val.p, m->K_val.p, c4,
                                                                 s->e.p, s->e_prev.p, s->g_new.p, s->g.p, s->g_prev.p,
-                                                                s->rhs.p, s->x.p);
+                                                                s->rhs.p, s->x.p); note_launch(); }
     } else {
-        k_face_hb<<<grid_for_rows(m->n_faces), kThreads, 0, s->stream>>>(m->n_faces, m->H.rowptr.p, m->H.col.p,
-                                                                         m->H_val.p, s->b.p, s->b_prev.p, s->hb.p);
-        k_rhs_mfem<<<grid_for_rows(ni), kThreads, 0, s->stream>>>(
+        { k_face_hb<<<grid_for_rows(m->n_faces), kThreads, 0, s->stream>>>(m->n_faces, m->H.rowptr.p, m->H.col.p,
+                                                                         m->H_val.p, s->b.p, s->b_prev.p, s->hb.p); note_launch(); }
+        { k_rhs_mfem<<<grid_for_rows(ni), kThreads, 0, s->stream>>>(
             ni, m->A.rowptr.p, m->A.col.p, m->M_val.p, m->K_val.p, c4, dt, s->e.p, s->e_prev.p, s->g_new.p, s->g_prev.p,
-            m->e2f.rowptr.p, m->e2f.col.p, m->e2f_sgn.p, s->hb.p, s->rhs.p, s->x.p);
+            m->e2f.rowptr.p, m->e2f.col.p, m->e2f_sgn.p, s->hb.p, s->rhs.p, s->x.p); note_launch(); }
     }
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
@@ -699,12 +765,14 @@ int pcg_newmark(Sim *s) {
     P.part = s->cg_part.p;
     P.st = &s->dctl.p->cg;
     P.hst = &s->hctl->cg;
+    P.timed = true;
     int rc = run_pcg(s, P, s->cfg.cg_tol, s->cfg.cg_max_iters, &s->last_cg_iters);
     if (rc) s->host_status |= ST_CG_NO_CONV;
     return rc;
 }
 
-int laplacian_solve(Sim *s, const double *rhs_int, double *x_int, double tol) {
+int laplacian_solve(Sim *s, const double *rhs_int, double *x_int, double tol, const double *abs_src,
+                    double abs_factor) {
     const Mesh *m = s->mesh;
     if (m->n_int_nodes == 0) return PIC_OK;
     CgProblem P;
@@ -723,6 +791,9 @@ int laplacian_solve(Sim *s, const double *rhs_int, double *x_int, double tol) {
     P.part = s->l_part.p;
     P.st = &s->dctl.p->lap;
     P.hst = &s->hctl->lap;
+    P.abs_src = abs_src;
+    P.abs_factor = abs_factor;
+    P.fallback_tol = s->cfg.init_tol;
     return run_pcg(s, P, tol, 20000, &s->last_lap_iters);
 }
 
@@ -737,24 +808,26 @@ int gradient_completion(Sim *s) {
     const Mesh *m = s->mesh;
     const int ni = m->n_int_edges, nin = m->n_int_nodes;
     if (ni == 0 || nin == 0) return PIC_OK;
-    k_gc_w<<<grid_for_rows(ni), kThreads, 0, s->stream>>>(ni, m->A.rowptr.p, m->A.col.p, m->M_val.p, s->cfg.form,
+    { k_gc_w<<<grid_for_rows(ni), kThreads, 0, s->stream>>>(ni, m->A.rowptr.p, m->A.col.p, m->M_val.p, s->cfg.form,
                                                           s->e.p, s->e_prev.p, s->x.p, s->g_new.p, s->g.p, s->g_prev.p,
-                                                          s->w_edge.p);
-    k_gc_d<<<(nin + 255) / 256, 256, 0, s->stream>>>(nin, m->int_node.p, m->n2e.rowptr.p, m->n2e.col.p, m->n2e_sgn.p,
-                                                     ni, s->w_edge.p, s->l_b.p);
+                                                          s->w_edge.p); note_launch(); }
+    { k_gc_d<<<(nin + 255) / 256, 256, 0, s->stream>>>(nin, m->int_node.p, m->n2e.rowptr.p, m->n2e.col.p, m->n2e_sgn.p,
+                                                     ni, s->w_edge.p, s->l_b.p); note_launch(); }
     FP_CUDA(cudaMemsetAsync(s->l_x.p, 0, sizeof(double) * nin, s->stream));
+    // stopping threshold: completion_tol * max_n |rho_n + wall_n| (charge at t^{n+1})
+    { k_max_abs_sum<<<grid_for_elems(m->n_nodes), kThreads, 0, s->stream>>>(m->n_nodes, s->rho.p, s->wall.p, s->diag_part.p, &s->dctl.p->diag.count, &s->dctl.p->qmax); note_launch(); }
     FP_CUDA(cudaGetLastError());
-    int rc = laplacian_solve(s, s->l_b.p, s->l_x.p, s->cfg.init_tol);
+    int rc = laplacian_solve(s, s->l_b.p, s->l_x.p, 0.0, &s->dctl.p->qmax, s->cfg.completion_tol);
     if (rc) return rc;
-    k_gc_apply<<<(ni + 255) / 256, 256, 0, s->stream>>>(ni, m->edge_nodes.p, m->node_int.p, s->l_x.p, s->x.p);
+    { k_gc_apply<<<(ni + 255) / 256, 256, 0, s->stream>>>(ni, m->edge_nodes.p, m->node_int.p, s->l_x.p, s->x.p); note_launch(); }
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
 }
 
 int faraday_update(Sim *s) {
     const Mesh *m = s->mesh;
-    k_faraday<<<(m->n_faces + 255) / 256, 256, 0, s->stream>>>(m->n_faces, m->f2e.p, s->cfg.form, s->cfg.dt, s->x.p,
-                                                                s->e.p, s->e_prev.p, s->b.p, s->b_prev.p, s->b_new.p);
+    { k_faraday<<<(m->n_faces + 255) / 256, 256, 0, s->stream>>>(m->n_faces, m->f2e.p, s->cfg.form, s->cfg.dt, s->x.p,
+                                                                s->e.p, s->e_prev.p, s->b.p, s->b_prev.p, s->b_new.p); note_launch(); }
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
 }
@@ -765,17 +838,17 @@ int compute_diagnostics(Sim *s) {
     DiagDev *dg = &s->dctl.p->diag;
     const int ni = m->n_int_edges;
     if (ni > 0)
-        k_resid<<<grid_for_rows(ni), kThreads, 0, s->stream>>>(ni, m->A.rowptr.p, m->A.col.p, m->M_val.p, m->K_val.p,
+        { k_resid<<<grid_for_rows(ni), kThreads, 0, s->stream>>>(ni, m->A.rowptr.p, m->A.col.p, m->M_val.p, m->K_val.p,
                                                                0.25 * s->cfg.dt * s->cfg.dt, s->e.p, s->rhs.p, s->me.p,
-                                                               s->diag_part.p, dg);
-    k_diag_nodes<<<grid_for_elems(m->n_nodes), kThreads, 0, s->stream>>>(
+                                                               s->diag_part.p, dg); note_launch(); }
+    { k_diag_nodes<<<grid_for_elems(m->n_nodes), kThreads, 0, s->stream>>>(
         m->n_nodes, m->n2e.rowptr.p, m->n2e.col.p, m->n2e_sgn.p, ni, s->dg.p, s->me.p, s->rho.p, s->rho_prev.p,
-        s->wall.p, s->wall_prev.p, s->rho_bg.p, m->node_bnd.p, s->diag_part.p, dg);
-    k_diag_divb<<<grid_for_elems(m->n_tets), kThreads, 0, s->stream>>>(m->n_tets, m->tet_face.p, m->tet_sign.p, s->b.p,
-                                                                       s->diag_part.p, dg);
-    k_diag_energy_b<<<grid_for_rows(m->n_faces), kThreads, 0, s->stream>>>(m->n_faces, m->H.rowptr.p, m->H.col.p,
-                                                                           m->H_val.p, s->b.p, s->diag_part.p, dg);
-    k_sum_ke<<<1, kThreads, 0, s->stream>>>(s->last_push_blocks, s->ke_part.p, dg);
+        s->wall.p, s->wall_prev.p, s->rho_bg.p, m->node_bnd.p, s->diag_part.p, dg); note_launch(); }
+    { k_diag_divb<<<grid_for_elems(m->n_tets), kThreads, 0, s->stream>>>(m->n_tets, m->tet_face.p, m->tet_sign.p, s->b.p,
+                                                                       s->diag_part.p, dg); note_launch(); }
+    { k_diag_energy_b<<<grid_for_rows(m->n_faces), kThreads, 0, s->stream>>>(m->n_faces, m->H.rowptr.p, m->H.col.p,
+                                                                           m->H_val.p, s->b.p, s->diag_part.p, dg); note_launch(); }
+    { k_sum_ke<<<1, kThreads, 0, s->stream>>>(s->last_push_blocks, s->ke_part.p, dg); note_launch(); }
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
 }
@@ -785,15 +858,15 @@ int init_fields(Sim *s) {
     const Mesh *m = s->mesh;
     const int nin = m->n_int_nodes, ni = m->n_int_edges;
     if (nin > 0) {
-        k_node_to_int<<<(nin + 255) / 256, 256, 0, s->stream>>>(nin, m->int_node.p, s->rho.p, s->rho_bg.p, s->l_b.p);
+        { k_node_to_int<<<(nin + 255) / 256, 256, 0, s->stream>>>(nin, m->int_node.p, s->rho.p, s->rho_bg.p, s->l_b.p); note_launch(); }
         FP_CUDA(cudaMemsetAsync(s->l_x.p, 0, sizeof(double) * nin, s->stream));
-        int rc = laplacian_solve(s, s->l_b.p, s->l_x.p, s->cfg.init_tol);
+        int rc = laplacian_solve(s, s->l_b.p, s->l_x.p, s->cfg.init_tol, nullptr, 0.0);
         if (rc) return rc;
         FP_CUDA(cudaMemsetAsync(s->phi.p, 0, sizeof(double) * m->n_nodes, s->stream));
-        k_int_to_node<<<(nin + 255) / 256, 256, 0, s->stream>>>(nin, m->int_node.p, s->l_x.p, s->phi.p);
+        { k_int_to_node<<<(nin + 255) / 256, 256, 0, s->stream>>>(nin, m->int_node.p, s->l_x.p, s->phi.p); note_launch(); }
         if (ni > 0)
-            k_minus_grad<<<(ni + 255) / 256, 256, 0, s->stream>>>(ni, m->edge_nodes.p, m->node_int.p, s->l_x.p, s->e.p,
-                                                                  s->e_prev.p);
+            { k_minus_grad<<<(ni + 255) / 256, 256, 0, s->stream>>>(ni, m->edge_nodes.p, m->node_int.p, s->l_x.p, s->e.p,
+                                                                  s->e_prev.p); note_launch(); }
         FP_CUDA(cudaGetLastError());
     }
     return PIC_OK;

@@ -42,8 +42,9 @@ class pic_config(C.Structure):
     _fields_ = [("form", C.c_int32), ("pusher", C.c_int32), ("precision", C.c_int32),
                 ("preconditioner", C.c_int32), ("dt", C.c_double), ("b0", C.c_double * 3),
                 ("rho_background", C.c_double), ("cg_tol", C.c_double), ("cg_max_iters", C.c_int32),
-                ("init_tol", C.c_double), ("walk_cap", C.c_int32), ("cg_check_every", C.c_int32),
-                ("max_species", C.c_int32), ("stream", C.c_void_p)]
+                ("init_tol", C.c_double), ("completion_tol", C.c_double), ("walk_cap", C.c_int32),
+                ("cg_check_every", C.c_int32),
+                ("max_species", C.c_int32), ("profile", C.c_int32), ("stream", C.c_void_p)]
 
 
 class pic_diag(C.Structure):
@@ -91,6 +92,9 @@ def load(build_if_missing: bool = True):
         "pic_particles_get": ([P, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, I64, lp, I32], I32),
         "pic_diagnostics_get": ([P, C.POINTER(pic_diag)], I32),
         "pic_sim_synchronize": ([P], I32),
+        "pic_profile_get": ([P, dp, lp], I32),
+        "pic_profile_reset": ([P], I32),
+        "pic_launch_count": ([], I64),
         "pic_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -142,10 +146,10 @@ class Mesh:
         h = C.c_void_p()
         _check(lib.pic_mesh_create(C.byref(d), C.byref(h)), "pic_mesh_create")
         self._h = h
-        c = np.zeros(6, dtype=np.int64)
+        c = np.zeros(8, dtype=np.int64)
         _check(lib.pic_mesh_info(h, _ptr(c, C.c_int64)), "pic_mesh_info")
         (self.n_nodes, self.n_edges, self.n_faces, self.n_tets,
-         self.n_int_edges, self.n_int_nodes) = (int(x) for x in c)
+         self.n_int_edges, self.n_int_nodes, self.nnz_A, self.nnz_L) = (int(x) for x in c)
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -179,7 +183,7 @@ class Sim:
     def __init__(self, mesh: Mesh, dt: float, form: str = "we", pusher: str = "boris",
                  precision: str = "plain", b0: Sequence[float] = (0.0, 0.0, 0.0), rho_background: float = 0.0,
                  cg_tol: float = 1e-10, init_tol: float = 1e-14, cg_max_iters: int = 10000,
-                 walk_cap: int = 63, stream=None):
+                 walk_cap: int = 63, stream=None, profile: bool = False):
         lib = load()
         self.mesh = mesh
         c = default_config()
@@ -194,6 +198,7 @@ class Sim:
         c.init_tol = init_tol
         c.cg_max_iters = cg_max_iters
         c.walk_cap = walk_cap
+        c.profile = int(profile)
         if stream is not None:
             c.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
         self.config = c
@@ -293,16 +298,33 @@ class Sim:
         _check(_lib.pic_diagnostics_get(self._h, C.byref(d)), "pic_diagnostics_get")
         return {n: getattr(d, n) for n, _ in pic_diag._fields_}
 
+    PHASES = ("sort", "coef", "push", "deposit", "rhs", "cg", "completion", "field_other", "spmv")
+
+    def profile(self) -> Dict[str, tuple]:
+        ms = np.zeros(len(self.PHASES))
+        cnt = np.zeros(len(self.PHASES), dtype=np.int64)
+        _check(_lib.pic_profile_get(self._h, _ptr(ms, C.c_double), _ptr(cnt, C.c_int64)), "pic_profile_get")
+        return {p: (float(ms[i]), int(cnt[i])) for i, p in enumerate(self.PHASES)}
+
+    def profile_reset(self):
+        _check(_lib.pic_profile_reset(self._h), "pic_profile_reset")
+
     def synchronize(self):
         _check(_lib.pic_sim_synchronize(self._h), "pic_sim_synchronize")
 
 
+def launch_count() -> int:
+    return int(load().pic_launch_count())
+
+
 def sim_from_workload(wl, dt: float, precision: str = "plain", cg_tol: float = 1e-10,
-                      init_tol: float = 1e-14, mesh: Optional[Mesh] = None, stream=None) -> Sim:
+                      init_tol: float = 1e-14, mesh: Optional[Mesh] = None, stream=None,
+                      profile: bool = False) -> Sim:
     """Builds and initialises a simulation of a ``workloads.Workload``."""
     mesh = mesh or Mesh(wl.mesh.xyz, wl.mesh.tets)
     sim = Sim(mesh, dt, form=wl.form, pusher=wl.pusher, precision=precision, b0=wl.b0,
-              rho_background=wl.rho_background, cg_tol=cg_tol, init_tol=init_tol, stream=stream)
+              rho_background=wl.rho_background, cg_tol=cg_tol, init_tol=init_tol, stream=stream,
+              profile=profile)
     for k, sp in enumerate(wl.species):
         sim.particles_load(k, sp.q, sp.m, sp.w, sp.x, sp.v, sp.tet)
     sim.init()

@@ -239,8 +239,11 @@ def larmor_orbit_box(n_cells: int = 20, b0z: float = 0.05, vperp_over_c: float =
     mesh = kuhn_box((n_cells,) * 3, (side,) * 3)
     centre = np.array([0.5 * side, 0.5 * side, 0.5 * side])
     # Electron (q < 0) in B0 z gyrates counter-clockwise seen from +z; starting
-    # at centre + r_L x with velocity +vperp y keeps the guiding centre at centre.
-    ref = (centre + np.array([r_l, 0.0, 0.0]))[None, :] + 1e-7 * side
+    # at centre + r_L x with velocity +vperp y keeps the guiding centre near the
+    # centre.  The start is shifted by (0, 0.137, 0.291) h so that the orbit
+    # plane and the start point stay clear of mesh faces and edges.
+    h = side / n_cells
+    ref = (centre + np.array([r_l, 0.137 * h, 0.291 * h]))[None, :]
     x, tet = place_in_box(mesh, ref)
     v = np.array([[0.0, vperp, 0.0]])
     sp = Species(q=Q_E, m=M_E, w=1.0, x=x, v=v, tet=tet)
