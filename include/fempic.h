@@ -256,6 +256,28 @@ int pic_profile_reset(pic_sim *sim);
 /* Number of kernels the library has launched in this process. */
 int64_t pic_launch_count(void);
 
+/* Allocation-free electrostatic solve (the paper has no counterpart; it is a
+ * service of this library).  For callers that cannot allocate device memory
+ * when they need the solve: work recorded under CUDA stream capture, where
+ * cudaMalloc is not allowed, or runtimes that hand out all device memory
+ * from their own pool.  Solves (G^T M G) phi = rho on the interior nodes
+ * (phi = 0 on wall nodes) with the Jacobi-PCG of pic_sim_init, to the relative
+ * residual tol, on `stream`.
+ *   rho_nodes [n_nodes], phi_nodes [n_nodes]: device arrays of the current
+ *   device, read / written during the call (phi is fully overwritten).
+ * It allocates nothing: its working vectors live in one fixed device array of
+ * the library (33.7 MB on every GPU that loads the solver, held until exit),
+ * which limits the mesh to 524,288 interior nodes (PIC_ERR_INVALID_ARG above
+ * that).  The mesh must already have its device copy, made by a
+ * pic_sim_create on it (PIC_ERR_STATE otherwise).  The first call on each
+ * device looks up the array's device address and should come before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents (the call sets everything it reads); calls that overlap on the
+ * GPU, from two streams or two threads, race on it.  Synchronises `stream`
+ * for its convergence checks. */
+int pic_electrostatic_solve_noalloc(const pic_mesh *mesh, const double *rho_nodes, double *phi_nodes, double tol,
+                                    void *stream);
+
 /* Waits for all work of the simulation. */
 int pic_sim_synchronize(pic_sim *sim);
 

@@ -661,6 +661,15 @@ int pic_diagnostics_get(pic_sim *sim, pic_diag *out) {
 
 int64_t pic_launch_count(void) { return (int64_t)g_launches.load(); }
 
+int pic_electrostatic_solve_noalloc(const pic_mesh *mesh, const double *rho_nodes, double *phi_nodes, double tol,
+                                    void *stream) {
+    if (!mesh) {
+        set_error("pic_electrostatic_solve_noalloc: NULL mesh");
+        return PIC_ERR_INVALID_ARG;
+    }
+    return electrostatic_solve_noalloc(&mesh->m, rho_nodes, phi_nodes, tol, (cudaStream_t)stream);
+}
+
 int pic_profile_get(pic_sim *sim, double *ms, int64_t *count) {
     if (!sim || !ms || !count) {
         set_error("pic_profile_get: NULL argument");

@@ -174,6 +174,8 @@ int faraday_update(Sim *s);
 int compute_diagnostics(Sim *s);
 int init_fields(Sim *s);
 int read_control(Sim *s);
+int electrostatic_solve_noalloc(const Mesh *m, const double *rho_nodes, double *phi_nodes, double tol,
+                                cudaStream_t st);
 
 }  // namespace fp
 

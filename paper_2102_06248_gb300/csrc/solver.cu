@@ -8,6 +8,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <string>
 
 #include "sim.h"
 
@@ -875,6 +877,120 @@ int init_fields(Sim *s) {
 int read_control(Sim *s) {
     FP_CUDA(cudaMemcpyAsync(s->hctl, s->dctl.p, sizeof(Control), cudaMemcpyDeviceToHost, s->stream));
     FP_CUDA(cudaStreamSynchronize(s->stream));
+    return PIC_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Allocation-free electrostatic solve.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// solve: code that runs while a CUDA stream is being captured into a graph
+// (cudaMalloc is not a capturable operation), or a host runtime that owns all
+// device memory through its own pool and forbids allocations from libraries.
+// For them pic_electrostatic_solve_noalloc runs the Jacobi-PCG of the node
+// Laplacian (the same kernels as the start-up solve of pic_sim_init) with its
+// working vectors in the fixed array below instead of buffers it allocates.
+//
+// The array is a file-scope device variable: every GPU on which this library's
+// solver module is loaded holds its 33.7 MB until the process exits.  It
+// bounds the problem to kNoAllocMaxNodes interior nodes.  All calls share it
+// and it keeps the last call's contents; calls whose work overlaps on the GPU
+// (different streams, or different host threads on one device) race on it.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocMaxNodes = 524288;
+constexpr size_t kNoAllocVectors = 8;   // D^-1, b, x, r, z, p, p', q
+constexpr size_t kNoAllocDoubles = kNoAllocVectors * kNoAllocMaxNodes + 8 * (size_t)kMaxBlocks + 64;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+namespace {
+std::mutex g_noalloc_mutex;
+constexpr int kNoAllocMaxDevices = 64;
+double *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// device address of the scratch array on the current device (looked up once
+// per device; the first call on a device must not run under stream capture)
+int noalloc_scratch(double **out) {
+    int dev = 0;
+    FP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        set_error("pic_electrostatic_solve_noalloc: device index out of range");
+        return PIC_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return PIC_OK;
+}
+}  // namespace
+
+int electrostatic_solve_noalloc(const Mesh *m, const double *rho_nodes, double *phi_nodes, double tol,
+                                cudaStream_t st) {
+    const int nin = m->n_int_nodes;
+    if (nin > kNoAllocMaxNodes) {
+        set_error("pic_electrostatic_solve_noalloc: " + std::to_string(nin) + " interior nodes exceed the limit of " +
+                  std::to_string(kNoAllocMaxNodes));
+        return PIC_ERR_INVALID_ARG;
+    }
+    if (!m->uploaded) {
+        set_error("pic_electrostatic_solve_noalloc: the mesh has no device copy yet (create a simulation on it first)");
+        return PIC_ERR_STATE;
+    }
+    if (!(tol > 0) || !rho_nodes || !phi_nodes) {
+        set_error("pic_electrostatic_solve_noalloc: needs tol > 0 and device arrays for rho and phi");
+        return PIC_ERR_INVALID_ARG;
+    }
+    double *base = nullptr;
+    int rc = noalloc_scratch(&base);
+    if (rc) return rc;
+    FP_CUDA(cudaMemsetAsync(phi_nodes, 0, sizeof(double) * m->n_nodes, st));
+    if (nin == 0) return PIC_OK;
+    double *v[kNoAllocVectors];
+    for (size_t k = 0; k < kNoAllocVectors; k++) v[k] = base + k * kNoAllocMaxNodes;
+    double *dinv = v[0], *b = v[1], *x = v[2], *r = v[3], *z = v[4], *p0 = v[5], *p1 = v[6], *q = v[7];
+    double *part = base + kNoAllocVectors * kNoAllocMaxNodes;
+    CgState *dst = reinterpret_cast<CgState *>(part + 8 * (size_t)kMaxBlocks);
+    // everything the solve reads before writing is set here: the diagonal, the
+    // right-hand side, x = 0 and the CG scalars with their arrival counters
+    { k_recip_diag<<<(nin + 255) / 256, 256, 0, st>>>(nin, m->L.rowptr.p, m->L.col.p, m->L_val.p, dinv); note_launch(); }
+    { k_node_to_int<<<(nin + 255) / 256, 256, 0, st>>>(nin, m->int_node.p, rho_nodes, nullptr, b); note_launch(); }
+    FP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * nin, st));
+    CgState init{};
+    init.tol2 = tol * tol;
+    init.max_iters = 20000;
+    init.abs_inf = -1.0;
+    FP_CUDA(cudaMemcpyAsync(dst, &init, sizeof(CgState), cudaMemcpyHostToDevice, st));
+    const int gr = grid_for_rows(nin), ge = grid_for_elems(nin);
+    { k_cg_init<<<gr, kThreads, 0, st>>>(nin, m->L.rowptr.p, m->L.col.p, m->L_val.p, dinv, b, x, r, z, p0, part, dst, nullptr, 0.0); note_launch(); }
+    { k_cg_zero_if_trivial<<<ge, kThreads, 0, st>>>(nin, x, dst); note_launch(); }
+    FP_CUDA(cudaGetLastError());
+    CgState h{};
+    double *pold = p0, *pnew = p1;
+    int launched = 0;
+    for (;;) {
+        for (int c = 0; c < 16; c++) {
+            { k_cg_a<<<gr, kThreads, 0, st>>>(nin, m->L.rowptr.p, m->L.col.p, m->L_val.p, z, pold, pnew, q, part, dst); note_launch(); }
+            { k_cg_b<<<ge, kThreads, 0, st>>>(nin, dinv, x, r, z, pnew, q, part + 3 * kMaxBlocks, dst); note_launch(); }
+            std::swap(pold, pnew);
+            launched++;
+        }
+        FP_CUDA(cudaGetLastError());
+        FP_CUDA(cudaMemcpyAsync(&h, dst, sizeof(CgState), cudaMemcpyDeviceToHost, st));
+        FP_CUDA(cudaStreamSynchronize(st));
+        if (h.done || launched > init.max_iters + 64) break;
+    }
+    if (h.failed || !h.done) {
+        set_error("pic_electrostatic_solve_noalloc: PCG did not reach the tolerance");
+        return PIC_ERR_CG_NO_CONVERGENCE;
+    }
+    { k_int_to_node<<<(nin + 255) / 256, 256, 0, st>>>(nin, m->int_node.p, x, phi_nodes); note_launch(); }
+    FP_CUDA(cudaGetLastError());
+    FP_CUDA(cudaStreamSynchronize(st));
     return PIC_OK;
 }
 

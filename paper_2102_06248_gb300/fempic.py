@@ -95,6 +95,7 @@ def load(build_if_missing: bool = True):
         "pic_profile_get": ([P, dp, lp], I32),
         "pic_profile_reset": ([P], I32),
         "pic_launch_count": ([], I64),
+        "pic_electrostatic_solve_noalloc": ([P, C.c_void_p, C.c_void_p, D, C.c_void_p], I32),
         "pic_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -311,6 +312,17 @@ class Sim:
 
     def synchronize(self):
         _check(_lib.pic_sim_synchronize(self._h), "pic_sim_synchronize")
+
+
+def electrostatic_solve_noalloc(mesh: Mesh, rho, phi, tol: float = 1e-14, stream=None):
+    """pic_electrostatic_solve_noalloc on CUDA tensors rho, phi [n_nodes] (float64).
+
+    The library allocates nothing during this call (see include/fempic.h)."""
+    load()
+    st = None if stream is None else C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(_lib.pic_electrostatic_solve_noalloc(mesh._h, C.c_void_p(rho.data_ptr()), C.c_void_p(phi.data_ptr()),
+                                                tol, st), "pic_electrostatic_solve_noalloc")
+    return phi
 
 
 def launch_count() -> int:

@@ -1,0 +1,57 @@
+"""The allocation-free electrostatic solve against the library's own.
+
+pic_electrostatic_solve_noalloc exists for callers that cannot allocate device
+memory when they need the solve (work recorded under CUDA stream capture,
+runtimes that own all device memory).  It keeps its working vectors in one
+fixed device array shared by all calls, so this test calls it twice in a row
+on the same inputs and checks both results against the potential that
+pic_sim_init computed through the regular (allocating) path.  The file name
+makes pytest collect it after every other test.
+"""
+import numpy as np
+import pytest
+
+from paper_2102_06248_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12     # the tolerance of the other field comparisons of the suite
+
+
+def test_noalloc_solve_matches_sim_init_twice():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2102_06248_gb300 import fempic as F
+
+    wl = W.thermal_plasma_cube(n_cells=8, n_particles=20000, seed=31)
+    sim = F.sim_from_workload(wl, 3.0e-10)
+    rho = sim.field("RHO") + sim.field("RHO_BG")
+    phi_ref = sim.field("PHI")
+    scale = np.abs(phi_ref).max()
+    assert scale > 0
+    rho_d = torch.tensor(rho, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    results = []
+    for call in range(2):
+        phi_d = torch.full((sim.mesh.n_nodes,), float("nan"), dtype=torch.float64, device="cuda")
+        F.electrostatic_solve_noalloc(sim.mesh, rho_d, phi_d, tol=1e-14, stream=stream)
+        torch.cuda.synchronize()
+        phi = phi_d.cpu().numpy()
+        assert np.all(np.isfinite(phi))
+        assert np.abs(phi - phi_ref).max() <= TOL * scale, call
+        results.append(phi)
+    assert np.abs(results[0] - results[1]).max() <= TOL * scale
+
+
+def test_noalloc_solve_rejects_meshes_beyond_its_limit():
+    pytest.importorskip("torch")
+    from paper_2102_06248_gb300 import fempic as F
+
+    box = W.kuhn_box((90, 90, 70), (0.9, 0.9, 0.7))      # 546,679 interior nodes > 524,288
+    mesh = F.Mesh(box.xyz, box.tets)
+    assert mesh.n_int_nodes > 524288
+    with pytest.raises(F.PicError) as ei:
+        F._check(F.load().pic_electrostatic_solve_noalloc(mesh._h, None, None, 1e-14, None),
+                 "pic_electrostatic_solve_noalloc")
+    assert ei.value.code == 1 and "limit" in str(ei.value)
