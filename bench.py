@@ -164,13 +164,14 @@ def sum_over_ranks(dist, value: float, device) -> float:
     return float(t.item())
 
 
-def push_bytes(n_particles: int, n_tets: int, precision: str) -> float:
+def push_bytes(n_particles: int, n_tets: int, precision: str, n_species: int = 1) -> float:
     """Algorithmic bytes of one launch of the fused push kernel: every live
     particle's state read (through the sort permutation) and written once,
     plus the per-tet geometry, coefficients and accumulators once."""
     r = 4 if precision == "mixed" else 8
     per_particle = 2 * (6 * r + 4 + 4) + 4 + 4      # x,v,key,id in and out; perm; sorted key
-    per_tet = 96 + 10 * r + 80                      # geometry, coefficients, accumulator write
+    acc = 80 * (n_species if precision == "mixed" else 1)
+    per_tet = 12 * r + 10 * r + acc                 # barycentric map, coefficients, accumulator write
     return n_particles * per_particle + n_tets * per_tet
 
 
@@ -246,31 +247,36 @@ def gpu_arm(args):
     del sim_m
 
     # ---- plain FP64 GPU path, same workload ----
-    sim_p, ms_plain, _, prof_p, diag_p = time_gpu(F, wl, dt, "plain", args.steps, args.warmup, stream, dist,
-                                                   local if world > 1 else None, torch)
-    del sim_p
+    if args.skip_plain:
+        ms_plain, prof_p = float("nan"), {}
+    else:
+        sim_p, ms_plain, _, prof_p, diag_p = time_gpu(F, wl, dt, "plain", args.steps, args.warmup, stream, dist,
+                                                       local if world > 1 else None, torch)
+        del sim_p
     ms_plain_max = max_over_ranks(dist, ms_plain, device)
     value_plain = total_ps / (ms_plain_max / 1e3)
 
     # ---- end to end through the public API from host arrays ----
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sim_e = F.Sim(F.Mesh(wl.mesh.xyz, wl.mesh.tets), dt, form=wl.form, pusher=wl.pusher, precision="mixed",
-                  b0=wl.b0, rho_background=wl.rho_background, stream=stream)
-    t_mesh = time.perf_counter()
-    for k, sp in enumerate(wl.species):
-        sim_e.particles_load(k, sp.q, sp.m, sp.w, sp.x, sp.v, sp.tet)
-    sim_e.init()
-    sim_e.step(args.steps)
-    e_out = sim_e.field("E")
-    xo, vo, to, io = sim_e.particles()
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    e2e_s = t1 - t_mesh
-    h2d = sum(sp.x.nbytes + sp.v.nbytes + sp.tet.nbytes for sp in wl.species)
-    d2h = e_out.nbytes + xo.nbytes + vo.nbytes + to.nbytes + io.nbytes
-    del sim_e
-    e2e_s_max = max_over_ranks(dist, e2e_s, device)
+    if args.skip_e2e:
+        e2e_s_max, h2d, d2h = float("nan"), 0, 0
+    else:
+        torch.cuda.synchronize()
+        sim_e = F.Sim(F.Mesh(wl.mesh.xyz, wl.mesh.tets), dt, form=wl.form, pusher=wl.pusher, precision="mixed",
+                      b0=wl.b0, rho_background=wl.rho_background, stream=stream)
+        t_mesh = time.perf_counter()
+        for k, sp in enumerate(wl.species):
+            sim_e.particles_load(k, sp.q, sp.m, sp.w, sp.x, sp.v, sp.tet)
+        sim_e.init()
+        sim_e.step(args.steps)
+        e_out = sim_e.field("E")
+        xo, vo, to, io = sim_e.particles()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        e2e_s = t1 - t_mesh
+        h2d = sum(sp.x.nbytes + sp.v.nbytes + sp.tet.nbytes for sp in wl.species)
+        d2h = e_out.nbytes + xo.nbytes + vo.nbytes + to.nbytes + io.nbytes
+        del sim_e
+        e2e_s_max = max_over_ranks(dist, e2e_s, device)
 
     # ---- roofline of the dominant kernel (live CUDA-event times) ----
     peak, peak_src = measured_peak()
@@ -281,10 +287,10 @@ def gpu_arm(args):
     nnz_A = int(getattr(mesh, "nnz_A", 0))
     if push_ms >= spmv_ms:
         kernel = "k_push (fused gather/push/walk/deposit, mixed)"
-        alg = push_bytes(int(alive_m), mesh.n_tets, "mixed")
+        alg = push_bytes(int(alive_m), mesh.n_tets, "mixed", len(wl.species))
         avg_ms = push_avg
     else:
-        kernel = "k_cg_a (fused PCG SpMV)"
+        kernel = "k_cg_a<0> (fused PCG SpMV of the Newmark solve)"
         alg = spmv_bytes(mesh.n_int_edges, nnz_A)
         avg_ms = spmv_avg
     achieved = alg / (avg_ms / 1e3) / 1e9
@@ -307,8 +313,9 @@ def gpu_arm(args):
                        "edges": mesh.n_edges, "interior_edges": mesh.n_int_edges, "dt_s": dt,
                        "precision": "mixed", "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (particle state > 1 GB per GPU)"},
-            "plain_fp64": {"value": value_plain, "ms_per_step": ms_plain_max / args.steps,
-                           "speedup_mixed_over_plain": value / value_plain},
+            "plain_fp64": None if args.skip_plain else {
+                "value": value_plain, "ms_per_step": ms_plain_max / args.steps,
+                "speedup_mixed_over_plain": value / value_plain},
             "phases_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof_m.items() if k != "spmv"},
             "phases_ms_per_step_plain": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof_p.items()
                                          if k != "spmv"},
@@ -317,7 +324,7 @@ def gpu_arm(args):
                                   "gauss_rel": diag_m["gauss_abs"] / max(diag_m["rho_max"], 1e-300)},
             "roofline": roofline,
             "cpu_baseline": cpu,
-            "e2e": {"value": total_ps / e2e_s_max, "unit": "particle-steps/s",
+            "e2e": None if args.skip_e2e else {"value": total_ps / e2e_s_max, "unit": "particle-steps/s",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                     "seconds": e2e_s_max,
                     "what": "particles_load from host arrays + init + K steps + E field and particles read back"},
@@ -393,6 +400,8 @@ def main():
     ap.add_argument("--particles", type=int, default=16 * 1024 * 1024, help="particles per species")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-plain", action="store_true", help="do not time the plain-FP64 path (profiling runs)")
+    ap.add_argument("--skip-e2e", action="store_true", help="do not run the end-to-end leg (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
