@@ -290,7 +290,7 @@ def gpu_arm(args):
         alg = push_bytes(int(alive_m), mesh.n_tets, "mixed", len(wl.species))
         avg_ms = push_avg
     else:
-        kernel = "k_cg_a<0> (fused PCG SpMV of the Newmark solve)"
+        kernel = "k_cg_a_sell (fused PCG SpMV of the Newmark solve, SELL-32)"
         alg = spmv_bytes(mesh.n_int_edges, nnz_A)
         avg_ms = spmv_avg
     achieved = alg / (avg_ms / 1e3) / 1e9

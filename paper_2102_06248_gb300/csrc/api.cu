@@ -90,12 +90,16 @@ int check_status(Sim *s) {
         return PIC_ERR_OVERFLOW;
     }
     if (st & ST_CG_NO_CONV) {
-        set_error("the Newmark solve did not converge");
+        set_error("a PCG solve (Newmark or gradient completion) did not converge");
         return PIC_ERR_CG_NO_CONVERGENCE;
     }
     if (st & ST_NAN) {
         set_error("a particle state became NaN");
         return PIC_ERR_NAN;
+    }
+    if (st & ST_BARRIER) {
+        set_error("a persistent solver kernel timed out at a grid barrier");
+        return PIC_ERR_CUDA;
     }
     return PIC_OK;
 }

@@ -25,6 +25,7 @@ enum : uint32_t {
     ST_NAN = 4u,
     ST_OVERFLOW = 8u,
     ST_OUTSIDE = 16u,
+    ST_BARRIER = 32u,   // a persistent kernel's grid barrier timed out
 };
 
 void set_error(const std::string &msg);
@@ -92,6 +93,15 @@ struct DevCsr {
     DevBuf<int> rowptr, col;
 };
 
+// Sparse matrix pattern in SELL-32 (device): slice s = rows 32s..32s+31,
+// entry j of lane l at ptr[s] + 32 j + l, width[s] entries per row (padded
+// with the row's own column and a zero value)
+struct DevSell {
+    int n_rows = 0, n_slices = 0;
+    long long n_elems = 0;
+    DevBuf<int> ptr, width, col;
+};
+
 // Host-side staging of the device arrays (kept until the first upload)
 struct HostCsrStage {
     std::vector<int> rowptr, col;
@@ -101,8 +111,10 @@ struct HostStage {
     std::vector<int4> tet_nodes, tet_nbr, tet_face, f2e;
     std::vector<int> tet_edge, node_int, int_node;
     std::vector<int2> edge_nodes;
-    HostCsrStage e2t, n2t, A, H, L, e2f, n2e;
-    std::vector<double> M_val, K_val, H_val, L_val;
+    HostCsrStage e2t, n2t, H, L, e2f, n2e;
+    std::vector<double> H_val, L_val;
+    std::vector<int> sell_ptr, sell_w, sell_col;
+    std::vector<double> sell_M, sell_K, M_diag, K_diag;
     std::vector<signed char> e2f_sgn, n2e_sgn;
 };
 
@@ -140,9 +152,10 @@ struct Mesh {
     // reductions from per-tet accumulators to entities (fixed order)
     DevCsr e2t;                // internal edge -> tet*6 + local edge
     DevCsr n2t;                // node -> tet*4 + local vertex
-    // Newmark system on interior edges: shared pattern of M, K (and A)
-    DevCsr A;
-    DevBuf<double> M_val, K_val;
+    // Newmark system on interior edges: shared SELL-32 pattern of M, K (and A)
+    DevSell As;
+    DevBuf<double> M_val, K_val;     // in the SELL layout
+    DevBuf<double> M_diag, K_diag;   // diagonals (interior rows)
     // face mass [*mu^-1] on all faces
     DevCsr H;
     DevBuf<double> H_val;

@@ -221,12 +221,27 @@ int build_mesh(const pic_mesh_desc *d, Mesh *m) {
         edge_bnd[edge_id((uint64_t)b * nn + c)] = 1;
         edge_bnd[edge_id((uint64_t)a * nn + c)] = 1;
     }
-    // internal numbering: interior edges first
+    // internal numbering: interior edges first, ordered by the length of
+    // their row in the Newmark matrix (edges sharing a tet) and canonically
+    // within a length, so that 32 consecutive rows (one SELL slice) have
+    // nearly equal lengths; boundary edges follow in canonical order
     m->h_edge_internal.assign(ne, -1);
     m->h_edge_canonical.assign(ne, -1);
     int ni = 0;
-    for (int e = 0; e < ne; e++)
-        if (!edge_bnd[e]) m->h_edge_internal[e] = ni++;
+    {
+        HostCsr pc = pattern_from_groups(ne, nt, 6, ne, ne, [&](int t, int *out) {
+            for (int k = 0; k < 6; k++) {
+                const int e = tet_edge_c[6 * (size_t)t + k];
+                out[k] = edge_bnd[e] ? -1 : e;
+            }
+        });
+        std::vector<std::pair<int, int>> order;
+        order.reserve(ne);
+        for (int e = 0; e < ne; e++)
+            if (!edge_bnd[e]) order.push_back({pc.rowptr[e + 1] - pc.rowptr[e], e});
+        std::sort(order.begin(), order.end());
+        for (auto &pr : order) m->h_edge_internal[pr.second] = ni++;
+    }
     m->n_int_edges = ni;
     int nb_ = ni;
     for (int e = 0; e < ne; e++)
@@ -437,11 +452,51 @@ int build_mesh(const pic_mesh_desc *d, Mesh *m) {
     }
     H.geo = std::move(geo);
     H.tet_edge = std::move(tet_edge);
-    m->nnz_A = (long long)pa.col.size();
     m->nnz_L = (long long)pl.col.size();
-    H.A = {std::move(pa.rowptr), std::move(pa.col)};
-    H.M_val = std::move(Mv);
-    H.K_val = std::move(Kv);
+    // SELL-32 layout of the Newmark pattern: slice s holds rows 32s..32s+31,
+    // entry j of lane l at sell_ptr[s] + 32 j + l; padding points at the row
+    // itself with value 0
+    {
+        const int nsl = (nie + 31) / 32;
+        H.sell_ptr.assign(nsl + 1, 0);
+        H.sell_w.assign(nsl, 0);
+        for (int sl = 0; sl < nsl; sl++) {
+            int w = 0;
+            for (int l = 0; l < 32; l++) {
+                const int r = 32 * sl + l;
+                if (r < nie) w = std::max(w, pa.rowptr[r + 1] - pa.rowptr[r]);
+            }
+            H.sell_w[sl] = w;
+            H.sell_ptr[sl + 1] = H.sell_ptr[sl] + 32 * w;
+        }
+        const size_t nel = (size_t)H.sell_ptr[nsl];
+        H.sell_col.assign(nel, 0);
+        H.sell_M.assign(nel, 0.0);
+        H.sell_K.assign(nel, 0.0);
+        H.M_diag.assign(nie, 0.0);
+        H.K_diag.assign(nie, 0.0);
+        for (int sl = 0; sl < nsl; sl++)
+            for (int l = 0; l < 32; l++) {
+                const int r = 32 * sl + l;
+                const int rr = r < nie ? r : nie - 1;
+                for (int j = 0; j < H.sell_w[sl]; j++) {
+                    const size_t q = (size_t)H.sell_ptr[sl] + 32 * (size_t)j + l;
+                    const int k = pa.rowptr[rr] + j;
+                    if (r < nie && k < pa.rowptr[r + 1]) {
+                        H.sell_col[q] = pa.col[k];
+                        H.sell_M[q] = Mv[k];
+                        H.sell_K[q] = Kv[k];
+                        if (pa.col[k] == r) {
+                            H.M_diag[r] = Mv[k];
+                            H.K_diag[r] = Kv[k];
+                        }
+                    } else {
+                        H.sell_col[q] = rr;
+                    }
+                }
+            }
+        m->nnz_A = (long long)pa.col.size();
+    }
     H.H = {std::move(ph.rowptr), std::move(ph.col)};
     H.H_val = std::move(Hv);
     H.L = {std::move(pl.rowptr), std::move(pl.col)};
@@ -472,7 +527,13 @@ int mesh_upload(Mesh *m) {
         (rc = m->tet_sign.upload(m->h_tet_sign)) || (rc = m->tet_vol.upload(m->h_vol)) || (rc = m->xyz.upload(m->h_xyz)))
         return rc;
     if ((rc = csr(H.e2t, &m->e2t)) || (rc = csr(H.n2t, &m->n2t))) return rc;
-    if ((rc = csr(H.A, &m->A)) || (rc = m->M_val.upload(H.M_val)) || (rc = m->K_val.upload(H.K_val))) return rc;
+    m->As.n_rows = m->n_int_edges;
+    m->As.n_slices = (int)H.sell_w.size();
+    m->As.n_elems = H.sell_ptr.empty() ? 0 : H.sell_ptr.back();
+    if ((rc = m->As.ptr.upload(H.sell_ptr)) || (rc = m->As.width.upload(H.sell_w)) || (rc = m->As.col.upload(H.sell_col)) ||
+        (rc = m->M_val.upload(H.sell_M)) || (rc = m->K_val.upload(H.sell_K)) || (rc = m->M_diag.upload(H.M_diag)) ||
+        (rc = m->K_diag.upload(H.K_diag)))
+        return rc;
     if ((rc = csr(H.H, &m->H)) || (rc = m->H_val.upload(H.H_val))) return rc;
     if ((rc = csr(H.L, &m->L)) || (rc = m->L_val.upload(H.L_val))) return rc;
     if ((rc = m->node_int.upload(H.node_int)) || (rc = m->int_node.upload(H.int_node))) return rc;

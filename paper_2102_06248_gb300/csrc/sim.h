@@ -35,8 +35,17 @@ struct DiagDev {
     int pad;
 };
 
+// state of the bounded grid barrier of the persistent kernels
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+    int timeout;
+    int pad;
+};
+
 // Host-visible control block (pinned), refreshed at every synchronising point
 struct Control {
+    GridBarrier gbar;
     CgState cg;
     CgState lap;
     DiagDev diag;
@@ -139,6 +148,7 @@ struct Sim {
     int last_cg_iters = 0;          // previous solves' iteration counts (first chunk size)
     int last_lap_iters = 0;
     int last_push_blocks = 0;       // grid of the last push (kinetic-energy partials)
+    int coop_blocks = -1;           // co-resident blocks of the persistent PCG (0: unavailable)
     uint32_t host_status = 0;       // latched errors seen on the host
     // optional phase profiler
     int profile = 0;

@@ -106,39 +106,6 @@ __device__ __forceinline__ double row_reduce(double s) {
     return s;
 }
 
-// ---------------------------------------------------------------------------
-// Newmark right-hand sides (Sec. II.B with Gbar in place of the current)
-// ---------------------------------------------------------------------------
-// wave equation:
-//   rhs = M (2 e - e') - c4 K (2 e + e') - (Gbar^{n+1} - 2 Gbar^n + Gbar^{n-1}),
-// i.e. (2M - dt^2/2 K) e^n - (M + dt^2/4 K) e^{n-1} - second difference of Gbar;
-// initial guess x = 2 e - e'.
-__global__ void __launch_bounds__(kThreads) k_rhs_we(int n, const int *__restrict__ rp, const int *__restrict__ col,
-                                                     const double *__restrict__ Mv, const double *__restrict__ Kv,
-                                                     double c4, const double *__restrict__ e, const double *__restrict__ ep,
-                                                     const double *__restrict__ gn, const double *__restrict__ g,
-                                                     const double *__restrict__ gp, double *__restrict__ rhs,
-                                                     double *__restrict__ x) {
-    const int lane = threadIdx.x % kLanes;
-    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
-        const int r = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
-        const bool rv = r < n;
-        const int kb = rv ? rp[r] : 0, kend = rv ? rp[r + 1] : 0;
-        double sm = 0.0, sk = 0.0;
-        _Pragma("unroll 4") for (int k = kb + lane; k < kend; k += kLanes) {
-            const int j = col[k];
-            const double ej = e[j], epj = ep[j];
-            sm += Mv[k] * (2.0 * ej - epj);
-            sk += Kv[k] * (2.0 * ej + epj);
-        }
-        sm = row_reduce(sm);
-        sk = row_reduce(sk);
-        if (rv && lane == 0) {
-            rhs[r] = sm - c4 * sk - (gn[r] - 2.0 * g[r] + gp[r]);
-            x[r] = 2.0 * e[r] - ep[r];
-        }
-    }
-}
 
 // face vector hb = H (b + b')
 __global__ void __launch_bounds__(kThreads) k_face_hb(int n, const int *__restrict__ rp, const int *__restrict__ col,
@@ -159,37 +126,234 @@ __global__ void __launch_bounds__(kThreads) k_face_hb(int n, const int *__restri
     }
 }
 
-// Maxwell-solver form, Faraday row eliminated:
-//   rhs = M e' - c4 K (2 e + e') + dt C^T H (b + b') - (Gbar^{n+1} - Gbar^{n-1})
-__global__ void __launch_bounds__(kThreads) k_rhs_mfem(int n, const int *__restrict__ rp, const int *__restrict__ col,
-                                                       const double *__restrict__ Mv, const double *__restrict__ Kv,
-                                                       double c4, double dt, const double *__restrict__ e,
-                                                       const double *__restrict__ ep, const double *__restrict__ gn,
-                                                       const double *__restrict__ gp, const int *__restrict__ efp,
-                                                       const int *__restrict__ efc, const signed char *__restrict__ efs,
-                                                       const double *__restrict__ hb, double *__restrict__ rhs,
-                                                       double *__restrict__ x) {
-    const int lane = threadIdx.x % kLanes;
-    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
-        const int r = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
-        const bool rv = r < n;
-        const int kb = rv ? rp[r] : 0, kend = rv ? rp[r + 1] : 0;
+
+// ---------------------------------------------------------------------------
+// SELL-32 kernels on the Newmark pattern (thread per row, warp per slice):
+// the 32 rows of a slice read their j-th entries as one coalesced 128-byte
+// (columns) and 256-byte (values) access.
+// ---------------------------------------------------------------------------
+constexpr int kSlicesPerBlock = kThreads / 32;
+
+#define SELL_LOOP(n_slices, n)                                                                         \
+    const int lane = threadIdx.x & 31;                                                                 \
+    for (int sl = blockIdx.x * kSlicesPerBlock + (threadIdx.x >> 5); sl < (n_slices);                 \
+         sl += gridDim.x * kSlicesPerBlock) {                                                          \
+        const int r = sl * 32 + lane;                                                                  \
+        const bool rv = r < (n);                                                                       \
+        const int kb = sp[sl] + lane, kw = sw[sl];
+
+__global__ void __launch_bounds__(kThreads) k_rhs_we_sell(int n, int n_slices, const int *__restrict__ sp,
+                                                          const int *__restrict__ sw, const int *__restrict__ col,
+                                                          const double *__restrict__ Mv, const double *__restrict__ Kv,
+                                                          double c4, const double *__restrict__ e,
+                                                          const double *__restrict__ ep, const double *__restrict__ gn,
+                                                          const double *__restrict__ g, const double *__restrict__ gp,
+                                                          double *__restrict__ rhs, double *__restrict__ x) {
+    SELL_LOOP(n_slices, n)
+        double sm = 0.0, sk = 0.0;
+#pragma unroll 4
+        for (int j = 0; j < kw; j++) {
+            const int k = kb + 32 * j;
+            const int c = col[k];
+            const double ej = e[c], epj = ep[c];
+            sm += Mv[k] * (2.0 * ej - epj);
+            sk += Kv[k] * (2.0 * ej + epj);
+        }
+        if (rv) {
+            rhs[r] = sm - c4 * sk - (gn[r] - 2.0 * g[r] + gp[r]);
+            x[r] = 2.0 * e[r] - ep[r];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_rhs_mfem_sell(int n, int n_slices, const int *__restrict__ sp,
+                                                            const int *__restrict__ sw, const int *__restrict__ col,
+                                                            const double *__restrict__ Mv, const double *__restrict__ Kv,
+                                                            double c4, double dt, const double *__restrict__ e,
+                                                            const double *__restrict__ ep, const double *__restrict__ gn,
+                                                            const double *__restrict__ gp, const int *__restrict__ efp,
+                                                            const int *__restrict__ efc,
+                                                            const signed char *__restrict__ efs,
+                                                            const double *__restrict__ hb, double *__restrict__ rhs,
+                                                            double *__restrict__ x) {
+    SELL_LOOP(n_slices, n)
         double sm = 0.0, sk = 0.0, sc = 0.0;
-        _Pragma("unroll 4") for (int k = kb + lane; k < kend; k += kLanes) {
-            const int j = col[k];
-            const double ej = e[j], epj = ep[j];
+#pragma unroll 4
+        for (int j = 0; j < kw; j++) {
+            const int k = kb + 32 * j;
+            const int c = col[k];
+            const double ej = e[c], epj = ep[c];
             sm += Mv[k] * epj;
             sk += Kv[k] * (2.0 * ej + epj);
         }
-        if (rv) for (int k = efp[r] + lane; k < efp[r + 1]; k += kLanes) sc += (double)efs[k] * hb[efc[k]];
-        sm = row_reduce(sm);
-        sk = row_reduce(sk);
-        sc = row_reduce(sc);
-        if (rv && lane == 0) {
+        if (rv) {
+            for (int k = efp[r]; k < efp[r + 1]; k++) sc += (double)efs[k] * hb[efc[k]];
             rhs[r] = sm - c4 * sk + dt * sc - (gn[r] - gp[r]);
             x[r] = 2.0 * e[r] - ep[r];
         }
     }
+}
+
+__global__ void __launch_bounds__(kThreads) k_gc_w_sell(int n, int n_slices, const int *__restrict__ sp,
+                                                        const int *__restrict__ sw, const int *__restrict__ col,
+                                                        const double *__restrict__ Mv, int form,
+                                                        const double *__restrict__ e, const double *__restrict__ ep,
+                                                        const double *__restrict__ x, const double *__restrict__ gn,
+                                                        const double *__restrict__ g, const double *__restrict__ gp,
+                                                        double *__restrict__ w) {
+    SELL_LOOP(n_slices, n)
+        double s = 0.0;
+#pragma unroll 4
+        for (int j = 0; j < kw; j++) {
+            const int k = kb + 32 * j;
+            const int c = col[k];
+            const double t = form == PIC_FORM_WE ? 2.0 * e[c] - ep[c] - x[c] : ep[c] - x[c];
+            s += Mv[k] * t;
+        }
+        if (rv) w[r] = s - (form == PIC_FORM_WE ? gn[r] - 2.0 * g[r] + gp[r] : gn[r] - gp[r]);
+    }
+}
+
+// r = b - A x, z = D^-1 r, p = z; rz, rr, bb, max|r|
+__global__ void __launch_bounds__(kThreads) k_cg_init_sell(int n, int n_slices, const int *__restrict__ sp,
+                                                           const int *__restrict__ sw, const int *__restrict__ col,
+                                                           const double *__restrict__ Av, const double *__restrict__ Dinv,
+                                                           const double *__restrict__ b, const double *__restrict__ x,
+                                                           double *__restrict__ r_, double *__restrict__ z,
+                                                           double *__restrict__ p, double *part, CgState *st) {
+    __shared__ double sh[4 * kThreads / 32];
+    double acc[3] = {0.0, 0.0, 0.0};
+    double amax[1] = {0.0};
+    SELL_LOOP(n_slices, n)
+        double s = 0.0;
+#pragma unroll 4
+        for (int j = 0; j < kw; j++) {
+            const int k = kb + 32 * j;
+            s += Av[k] * x[col[k]];
+        }
+        if (rv) {
+            const double ri = b[r] - s, zi = Dinv[r] * ri;
+            r_[r] = ri;
+            z[r] = zi;
+            p[r] = zi;
+            acc[0] += ri * zi;
+            acc[1] += ri * ri;
+            acc[2] += b[r] * b[r];
+            amax[0] = fmax(amax[0], fabs(ri));
+        }
+    }
+    block_sum<3>(acc, sh);
+    block_max<1>(amax, sh + 3 * kThreads / 32);
+    double both[4] = {acc[0], acc[1], acc[2], amax[0]};
+    if (arrive<4>(both, part, &st->count_a)) {
+        double tot[3], mx[1];
+        grid_combine<3, false>(tot, part, sh);
+        grid_combine<1, true>(mx, part + 3 * gridDim.x, sh + 3 * kThreads / 32);
+        if (threadIdx.x == 0) {
+            st->rz = tot[0];
+            st->rr = tot[1];
+            st->bb = tot[2];
+            st->iters = 0;
+            st->failed = 0;
+            st->beta = 0.0;
+            st->done = (tot[2] == 0.0) || (tot[1] <= st->tol2 * tot[2]) || (mx[0] <= st->abs_inf);
+            st->count_a = 0;
+        }
+    }
+}
+
+// p = z + beta p_old (on the fly for the neighbours), q = A p, pq: the SpMV
+// of the Newmark PCG
+__global__ void __launch_bounds__(kThreads) k_cg_a_sell(int n, int n_slices, const int *__restrict__ sp,
+                                                        const int *__restrict__ sw, const int *__restrict__ col,
+                                                        const double *__restrict__ Av, const double *__restrict__ z,
+                                                        const double *__restrict__ pold, double *__restrict__ pnew,
+                                                        double *__restrict__ q, double *part, CgState *st) {
+    __shared__ double sh[kThreads / 32];
+    if (st->done) return;
+    const bool first = st->iters == 0;
+    const double beta = st->beta;
+    double acc[1] = {0.0};
+    SELL_LOOP(n_slices, n)
+        double s = 0.0;
+        if (first) {
+#pragma unroll 4
+            for (int j = 0; j < kw; j++) {
+                const int k = kb + 32 * j;
+                s += Av[k] * z[col[k]];
+            }
+        } else {
+#pragma unroll 4
+            for (int j = 0; j < kw; j++) {
+                const int k = kb + 32 * j;
+                const int c = col[k];
+                s += Av[k] * (z[c] + beta * pold[c]);
+            }
+        }
+        if (rv) {
+            const double pi = first ? z[r] : z[r] + beta * pold[r];
+            pnew[r] = pi;
+            q[r] = s;
+            acc[0] += pi * s;
+        }
+    }
+    block_sum<1>(acc, sh);
+    if (arrive<1>(acc, part, &st->count_a)) {
+        double tot[1];
+        grid_combine<1, false>(tot, part, sh);
+        if (threadIdx.x == 0) {
+            st->alpha = st->rz / tot[0];
+            st->count_a = 0;
+        }
+    }
+}
+
+// true residual and M x on the Newmark pattern: relres, energy_e
+__global__ void __launch_bounds__(kThreads) k_resid_sell(int n, int n_slices, const int *__restrict__ sp,
+                                                         const int *__restrict__ sw, const int *__restrict__ col,
+                                                         const double *__restrict__ Mv, const double *__restrict__ Kv,
+                                                         double c4, const double *__restrict__ x,
+                                                         const double *__restrict__ rhs, double *__restrict__ me,
+                                                         double *part, DiagDev *dg) {
+    __shared__ double sh[3 * kThreads / 32];
+    double acc[3] = {0.0, 0.0, 0.0};
+    SELL_LOOP(n_slices, n)
+        double sm = 0.0, sk = 0.0;
+#pragma unroll 4
+        for (int j = 0; j < kw; j++) {
+            const int k = kb + 32 * j;
+            const double xj = x[col[k]];
+            sm += Mv[k] * xj;
+            sk += Kv[k] * xj;
+        }
+        if (rv) {
+            me[r] = sm;
+            const double res = rhs[r] - (sm + c4 * sk);
+            acc[0] += res * res;
+            acc[1] += rhs[r] * rhs[r];
+            acc[2] += x[r] * sm;
+        }
+    }
+    block_sum<3>(acc, sh);
+    if (arrive<3>(acc, part, &dg->count)) {
+        double tot[3];
+        grid_combine<3, false>(tot, part, sh);
+        if (threadIdx.x == 0) {
+            dg->relres = tot[1] > 0.0 ? sqrt(tot[0] / tot[1]) : 0.0;
+            dg->energy_e = 0.5 * tot[2];
+            dg->count = 0;
+        }
+    }
+}
+
+__global__ void k_recip_diag_mk(int n, const double *__restrict__ md, const double *__restrict__ kd, double c4,
+                                double *__restrict__ dinv) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dinv[i] = 1.0 / (md[i] + c4 * kd[i]);
+}
+
+int grid_for_slices(int n_slices) {
+    return std::max(1, std::min(kMaxBlocks, (n_slices + kSlicesPerBlock - 1) / kSlicesPerBlock));
 }
 
 // ---------------------------------------------------------------------------
@@ -256,11 +420,9 @@ __global__ void k_cg_zero_if_trivial(int n, double *x, const CgState *st) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = 0.0;
 }
 
-// p = z + beta p_old (on the fly for the neighbours), q = A p, pq.
-// TAG only names the instance: 0 for the Newmark solve, 1 for the node
-// Laplacian, so that profilers can tell the two apart.
-template <int TAG>
-__global__ void __launch_bounds__(kThreads) k_cg_a(int n, const int *__restrict__ rp, const int *__restrict__ col,
+// p = z + beta p_old (on the fly for the neighbours), q = A p, pq: the SpMV
+// of the CSR solves (node Laplacian)
+__global__ void __launch_bounds__(kThreads) k_cg_a_csr(int n, const int *__restrict__ rp, const int *__restrict__ col,
                                                    const double *__restrict__ Av, const double *__restrict__ z,
                                                    const double *__restrict__ pold, double *__restrict__ pnew,
                                                    double *__restrict__ q, double *part, CgState *st) {
@@ -341,29 +503,6 @@ __global__ void __launch_bounds__(kThreads) k_cg_b(int n, const double *__restri
     }
 }
 
-// ---------------------------------------------------------------------------
-// completion on the gradient subspace (see gradient_completion below)
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_gc_w(int n, const int *__restrict__ rp, const int *__restrict__ col,
-                                                   const double *__restrict__ Mv, int form, const double *__restrict__ e,
-                                                   const double *__restrict__ ep, const double *__restrict__ x,
-                                                   const double *__restrict__ gn, const double *__restrict__ g,
-                                                   const double *__restrict__ gp, double *__restrict__ w) {
-    const int lane = threadIdx.x % kLanes;
-    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
-        const int r = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
-        const bool rv = r < n;
-        const int kb = rv ? rp[r] : 0, kend = rv ? rp[r + 1] : 0;
-        double s = 0.0;
-        _Pragma("unroll 4") for (int k = kb + lane; k < kend; k += kLanes) {
-            const int j = col[k];
-            const double t = form == PIC_FORM_WE ? 2.0 * e[j] - ep[j] - x[j] : ep[j] - x[j];
-            s += Mv[k] * t;
-        }
-        s = row_reduce(s);
-        if (rv && lane == 0) w[r] = s - (form == PIC_FORM_WE ? gn[r] - 2.0 * g[r] + gp[r] : gn[r] - gp[r]);
-    }
-}
 
 // d_k = (G_int^T w)_k for interior node k
 __global__ void k_gc_d(int nin, const int *__restrict__ int_node, const int *__restrict__ ptr,
@@ -417,45 +556,6 @@ __global__ void k_int_to_node(int nin, const int *__restrict__ int_node, const d
     out[int_node[k]] = v[k];
 }
 
-// true residual and M x: relres = ||rhs - A x|| / ||rhs||, energy_e = x.Mx / 2
-__global__ void __launch_bounds__(kThreads) k_resid(int n, const int *__restrict__ rp, const int *__restrict__ col,
-                                                    const double *__restrict__ Mv, const double *__restrict__ Kv,
-                                                    double c4, const double *__restrict__ x, const double *__restrict__ rhs,
-                                                    double *__restrict__ me, double *part, DiagDev *dg) {
-    __shared__ double sh[3 * kThreads / 32];
-    const int lane = threadIdx.x % kLanes;
-    double acc[3] = {0.0, 0.0, 0.0};
-    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
-        const int r = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
-        const bool rv = r < n;
-        const int kb = rv ? rp[r] : 0, kend = rv ? rp[r + 1] : 0;
-        double sm = 0.0, sk = 0.0;
-        _Pragma("unroll 4") for (int k = kb + lane; k < kend; k += kLanes) {
-            const double xj = x[col[k]];
-            sm += Mv[k] * xj;
-            sk += Kv[k] * xj;
-        }
-        sm = row_reduce(sm);
-        sk = row_reduce(sk);
-        if (rv && lane == 0) {
-            me[r] = sm;
-            const double res = rhs[r] - (sm + c4 * sk);
-            acc[0] += res * res;
-            acc[1] += rhs[r] * rhs[r];
-            acc[2] += x[r] * sm;
-        }
-    }
-    block_sum<3>(acc, sh);
-    if (arrive<3>(acc, part, &dg->count)) {
-        double tot[3];
-        grid_combine<3, false>(tot, part, sh);
-        if (threadIdx.x == 0) {
-            dg->relres = tot[1] > 0.0 ? sqrt(tot[0] / tot[1]) : 0.0;
-            dg->energy_e = 0.5 * tot[2];
-            dg->count = 0;
-        }
-    }
-}
 
 // Faraday: wave equation b^{n+1} = b^n - dt/2 C (e^{n+1} + e^n);
 // Maxwell-solver row b^{n+1} = b^{n-1} - 2 dt C (e^{n+1}/4 + e^n/2 + e^{n-1}/4)
@@ -588,6 +688,212 @@ __global__ void __launch_bounds__(kThreads) k_max_abs_sum(int n, const double *_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent Jacobi-PCG for the small CSR systems (the node Laplacian of the
+// gradient completion and of the start-up solve): one cooperative launch runs
+// every iteration with two grid barriers per iteration.  Every block reduces
+// the per-block partials in the same fixed order, so all blocks take the same
+// decisions and the result is deterministic.  Vectors written by other blocks
+// inside the launch are read through L2 (__ldcg).  The barrier spins with a
+// bound: past it the kernel records a timeout and every block leaves.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool grid_barrier(GridBarrier *gb) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *vgen = &gb->gen;
+        volatile int *vto = &gb->timeout;
+        int good = (*vto == 0);
+        if (good) {
+            const unsigned int g = *vgen;
+            __threadfence();
+            if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
+                gb->count = 0;
+                __threadfence();
+                atomicAdd(&gb->gen, 1u);
+            } else {
+                long spins = 0;
+                while (*vgen == g) {
+                    if (++spins > (1L << 24) || *vto != 0) {
+                        atomicExch(&gb->timeout, 1);
+                        good = 0;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            __threadfence();
+        }
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// fixed-order sum / max over the blocks' partials, broadcast to the block
+template <bool MAX>
+__device__ __forceinline__ double all_blocks_combine(const double *part, double *sh, double *bcast) {
+    double v[1] = {0.0};
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += kThreads) {
+        const double x = __ldcg(part + b);
+        v[0] = MAX ? fmax(v[0], x) : v[0] + x;
+    }
+    if (MAX) block_max<1>(v, sh);
+    else block_sum<1>(v, sh);
+    if (threadIdx.x == 0) *bcast = v[0];
+    __syncthreads();
+    const double out = *bcast;
+    __syncthreads();
+    return out;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_pcg_persistent(int n, const int *__restrict__ rp,
+                                                             const int *__restrict__ col, const double *__restrict__ Av,
+                                                             const double *__restrict__ Dinv, const double *__restrict__ b,
+                                                             double *x, double *r, double *z, double *p0, double *p1,
+                                                             double *q, double *part, CgState *st, GridBarrier *gb,
+                                                             const double *abs_src, double abs_factor, uint32_t *status) {
+    __shared__ double sh[3 * kThreads / 32];
+    __shared__ double bc;
+    const int lane = threadIdx.x % kLanes;
+    const int G = gridDim.x;
+    double *pp0 = part, *pp1 = part + G, *pp2 = part + 2 * G, *pp3 = part + 3 * G;
+    const double tol2_cfg = st->tol2, fallback2 = st->fallback_tol2;
+    const int max_iters = st->max_iters;
+    double abs_inf = st->abs_inf;
+    double tol2 = tol2_cfg;
+    if (abs_src) {
+        const double qv = *abs_src;
+        if (qv > 0.0) abs_inf = abs_factor * qv;
+        else tol2 = fallback2;
+    }
+    // ---- r = b - A x, z = D^-1 r, p = z ----
+    {
+        double v3[3] = {0.0, 0.0, 0.0}, vm[1] = {0.0};
+        for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < n;
+             r0_ += G * kRowsPerBlock) {
+            const int i = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
+            const bool rv = i < n;
+            const int kb = rv ? rp[i] : 0, kend = rv ? rp[i + 1] : 0;
+            double sacc = 0.0;
+            for (int k = kb + lane; k < kend; k += kLanes) sacc += Av[k] * x[col[k]];
+            sacc = row_reduce(sacc);
+            if (rv && lane == 0) {
+                const double ri = b[i] - sacc, zi = Dinv[i] * ri;
+                r[i] = ri;
+                z[i] = zi;
+                v3[0] += ri * zi;
+                v3[1] += ri * ri;
+                v3[2] += b[i] * b[i];
+                vm[0] = fmax(vm[0], fabs(ri));
+            }
+        }
+        block_sum<3>(v3, sh);
+        block_max<1>(vm, sh);
+        if (threadIdx.x == 0) {
+            pp0[blockIdx.x] = v3[0];
+            pp1[blockIdx.x] = v3[1];
+            pp2[blockIdx.x] = v3[2];
+            pp3[blockIdx.x] = vm[0];
+        }
+    }
+    if (!grid_barrier(gb)) goto timeout;
+    {
+        double rz = all_blocks_combine<false>(pp0, sh, &bc);
+        double rr = all_blocks_combine<false>(pp1, sh, &bc);
+        const double bb = all_blocks_combine<false>(pp2, sh, &bc);
+        const double mx0 = all_blocks_combine<true>(pp3, sh, &bc);
+        bool done = (bb == 0.0) || (rr <= tol2 * bb) || (mx0 <= abs_inf);
+        if (bb == 0.0)
+            for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += G * kThreads) x[i] = 0.0;
+        int iters = 0;
+        bool failed = false;
+        double beta = 0.0;
+        double *pold = p0, *pnew = p1;
+        // the partials of the previous combine must be read by every block
+        // before they are overwritten: barrier
+        if (!grid_barrier(gb)) goto timeout;
+        while (!done) {
+            if (iters >= max_iters) {
+                failed = true;
+                break;
+            }
+            const bool first = iters == 0;
+            // ---- q = A p with p = z + beta p_old formed on the fly ----
+            double vpq[1] = {0.0};
+            for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < n;
+                 r0_ += G * kRowsPerBlock) {
+                const int i = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
+                const bool rv = i < n;
+                const int kb = rv ? rp[i] : 0, kend = rv ? rp[i + 1] : 0;
+                double sacc = 0.0;
+                for (int k = kb + lane; k < kend; k += kLanes) {
+                    const int j = col[k];
+                    const double pj = first ? __ldcg(z + j) : __ldcg(z + j) + beta * __ldcg(pold + j);
+                    sacc += Av[k] * pj;
+                }
+                sacc = row_reduce(sacc);
+                if (rv && lane == 0) {
+                    const double pi = first ? __ldcg(z + i) : __ldcg(z + i) + beta * __ldcg(pold + i);
+                    pnew[i] = pi;
+                    q[i] = sacc;
+                    vpq[0] += pi * sacc;
+                }
+            }
+            block_sum<1>(vpq, sh);
+            if (threadIdx.x == 0) pp0[blockIdx.x] = vpq[0];
+            if (!grid_barrier(gb)) goto timeout;
+            const double alpha = rz / all_blocks_combine<false>(pp0, sh, &bc);
+            // ---- x += alpha p, r -= alpha q, z = D^-1 r ----
+            double v2[2] = {0.0, 0.0}, vm[1] = {0.0};
+            for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += G * kThreads) {
+                x[i] = __ldcg(x + i) + alpha * __ldcg(pnew + i);
+                const double ri = __ldcg(r + i) - alpha * __ldcg(q + i);
+                r[i] = ri;
+                const double zi = Dinv[i] * ri;
+                z[i] = zi;
+                v2[0] += ri * zi;
+                v2[1] += ri * ri;
+                vm[0] = fmax(vm[0], fabs(ri));
+            }
+            block_sum<2>(v2, sh);
+            block_max<1>(vm, sh);
+            if (threadIdx.x == 0) {
+                pp1[blockIdx.x] = v2[0];
+                pp2[blockIdx.x] = v2[1];
+                pp3[blockIdx.x] = vm[0];
+            }
+            if (!grid_barrier(gb)) goto timeout;
+            const double rz_new = all_blocks_combine<false>(pp1, sh, &bc);
+            rr = all_blocks_combine<false>(pp2, sh, &bc);
+            const double mx = all_blocks_combine<true>(pp3, sh, &bc);
+            beta = rz_new / rz;
+            rz = rz_new;
+            iters++;
+            double *t = pold;
+            pold = pnew;
+            pnew = t;
+            done = (rr <= tol2 * bb) || (mx <= abs_inf);
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            st->iters = iters;
+            st->rr = rr;
+            st->rz = rz;
+            st->bb = bb;
+            st->done = 1;
+            st->failed = failed ? 1 : 0;
+            if (failed) atomicOr(status, (uint32_t)ST_CG_NO_CONV);
+        }
+        return;
+    }
+timeout:
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->done = 1;
+        st->failed = 1;
+        atomicOr(status, (uint32_t)ST_BARRIER);
+    }
+}
+
 int grid_for_rows(int n) { return std::max(1, std::min(kMaxBlocks, (n + kRowsPerBlock - 1) / kRowsPerBlock)); }
 int grid_for_elems(int n) { return std::max(1, std::min(kMaxBlocks, (n + kThreads - 1) / kThreads)); }
 
@@ -620,6 +926,8 @@ struct CgProblem {
     const double *abs_src = nullptr;  // device scalar: stop also when max|r| <= abs_factor * (*abs_src)
     double abs_factor = 0.0;
     double fallback_tol = 0.0;        // relative tolerance used when *abs_src is 0
+    const int *sp = nullptr, *sw = nullptr;   // SELL-32 slices (Newmark matrix) instead of CSR
+    int n_slices = 0;
 };
 
 int run_pcg(Sim *s, CgProblem &P, double tol, int max_iters, int *last_iters) {
@@ -630,8 +938,9 @@ int run_pcg(Sim *s, CgProblem &P, double tol, int max_iters, int *last_iters) {
     init.abs_inf = -1.0;
     init.fallback_tol2 = P.fallback_tol * P.fallback_tol;
     FP_CUDA(cudaMemcpyAsync(P.st, &init, sizeof(CgState), cudaMemcpyHostToDevice, st));
-    const int gr = grid_for_rows(P.n), ge = grid_for_elems(P.n);
-    { k_cg_init<<<gr, kThreads, 0, st>>>(P.n, P.rp, P.col, P.Av, P.Dinv, P.b, P.x, P.r, P.z, P.p0, P.part, P.st, P.abs_src, P.abs_factor); note_launch(); }
+    const int gr = P.sp ? grid_for_slices(P.n_slices) : grid_for_rows(P.n), ge = grid_for_elems(P.n);
+    if (P.sp) { k_cg_init_sell<<<gr, kThreads, 0, st>>>(P.n, P.n_slices, P.sp, P.sw, P.col, P.Av, P.Dinv, P.b, P.x, P.r, P.z, P.p0, P.part, P.st); note_launch(); }
+    else { k_cg_init<<<gr, kThreads, 0, st>>>(P.n, P.rp, P.col, P.Av, P.Dinv, P.b, P.x, P.r, P.z, P.p0, P.part, P.st, P.abs_src, P.abs_factor); note_launch(); }
     { k_cg_zero_if_trivial<<<ge, kThreads, 0, st>>>(P.n, P.x, P.st); note_launch(); }
     FP_CUDA(cudaGetLastError());
     int launched = 0;
@@ -650,8 +959,8 @@ int run_pcg(Sim *s, CgProblem &P, double tol, int max_iters, int *last_iters) {
                 }
                 cudaEventRecord(s->spmv_ev[2 * s->spmv_used], st);
             }
-            if (P.timed) { k_cg_a<0><<<gr, kThreads, 0, st>>>(P.n, P.rp, P.col, P.Av, P.z, pold, pnew, P.q, P.part, P.st); note_launch(); }
-            else { k_cg_a<1><<<gr, kThreads, 0, st>>>(P.n, P.rp, P.col, P.Av, P.z, pold, pnew, P.q, P.part, P.st); note_launch(); }
+            if (P.sp) { k_cg_a_sell<<<gr, kThreads, 0, st>>>(P.n, P.n_slices, P.sp, P.sw, P.col, P.Av, P.z, pold, pnew, P.q, P.part, P.st); note_launch(); }
+            else { k_cg_a_csr<<<gr, kThreads, 0, st>>>(P.n, P.rp, P.col, P.Av, P.z, pold, pnew, P.q, P.part, P.st); note_launch(); }
             if (timed) cudaEventRecord(s->spmv_ev[2 * s->spmv_used++ + 1], st);
             { k_cg_b<<<ge, kThreads, 0, st>>>(P.n, P.Dinv, P.x, P.r, P.z, pnew, P.q, P.part + 3 * kMaxBlocks, P.st); note_launch(); }
             std::swap(pold, pnew);
@@ -721,10 +1030,11 @@ int solver_alloc(Sim *s) {
         return rc;
     // A = M + dt^2/4 K and the Jacobi preconditioners
     const double c4 = 0.25 * s->cfg.dt * s->cfg.dt;
-    if ((rc = s->A_val.alloc(std::max(m->A.nnz, 1)))) return rc;
-    if (m->A.nnz > 0) {
-        { k_axpby<<<(m->A.nnz + 255) / 256, 256>>>(m->A.nnz, 1.0, m->M_val.p, c4, m->K_val.p, s->A_val.p); note_launch(); }
-        { k_recip_diag<<<(ni + 255) / 256, 256>>>(ni, m->A.rowptr.p, m->A.col.p, s->A_val.p, s->Dinv.p); note_launch(); }
+    const long long nel = m->As.n_elems;
+    if ((rc = s->A_val.alloc(std::max(nel, 1LL)))) return rc;
+    if (nel > 0) {
+        { k_axpby<<<(unsigned)((nel + 255) / 256), 256>>>((int)nel, 1.0, m->M_val.p, c4, m->K_val.p, s->A_val.p); note_launch(); }
+        { k_recip_diag_mk<<<(ni + 255) / 256, 256>>>(ni, m->M_diag.p, m->K_diag.p, c4, s->Dinv.p); note_launch(); }
     }
     if (nin > 0) { k_recip_diag<<<(nin + 255) / 256, 256>>>(nin, m->L.rowptr.p, m->L.col.p, m->L_val.p, s->L_Dinv.p); note_launch(); }
     FP_CUDA(cudaGetLastError());
@@ -737,16 +1047,14 @@ int newmark_rhs(Sim *s) {
     const int ni = m->n_int_edges;
     if (ni == 0) return PIC_OK;
     const double dt = s->cfg.dt, c4 = 0.25 * dt * dt;
+    const DevSell &A = m->As;
+    const int gs = grid_for_slices(A.n_slices);
     if (s->cfg.form == PIC_FORM_WE) {
-        { k_rhs_we<<<grid_for_rows(ni), kThreads, 0, s->stream>>>(ni, m->A.rowptr.p, m->A.col.p, m->M_val.p, m->K_val.p, c4,
-                                                                s->e.p, s->e_prev.p, s->g_new.p, s->g.p, s->g_prev.p,
-                                                                s->rhs.p, s->x.p); note_launch(); }
+        { k_rhs_we_sell<<<gs, kThreads, 0, s->stream>>>(ni, A.n_slices, A.ptr.p, A.width.p, A.col.p, m->M_val.p, m->K_val.p, c4, s->e.p, s->e_prev.p, s->g_new.p, s->g.p, s->g_prev.p, s->rhs.p, s->x.p); note_launch(); }
     } else {
         { k_face_hb<<<grid_for_rows(m->n_faces), kThreads, 0, s->stream>>>(m->n_faces, m->H.rowptr.p, m->H.col.p,
                                                                          m->H_val.p, s->b.p, s->b_prev.p, s->hb.p); note_launch(); }
-        { k_rhs_mfem<<<grid_for_rows(ni), kThreads, 0, s->stream>>>(
-            ni, m->A.rowptr.p, m->A.col.p, m->M_val.p, m->K_val.p, c4, dt, s->e.p, s->e_prev.p, s->g_new.p, s->g_prev.p,
-            m->e2f.rowptr.p, m->e2f.col.p, m->e2f_sgn.p, s->hb.p, s->rhs.p, s->x.p); note_launch(); }
+        { k_rhs_mfem_sell<<<gs, kThreads, 0, s->stream>>>(ni, A.n_slices, A.ptr.p, A.width.p, A.col.p, m->M_val.p, m->K_val.p, c4, dt, s->e.p, s->e_prev.p, s->g_new.p, s->g_prev.p, m->e2f.rowptr.p, m->e2f.col.p, m->e2f_sgn.p, s->hb.p, s->rhs.p, s->x.p); note_launch(); }
     }
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
@@ -757,8 +1065,11 @@ int pcg_newmark(Sim *s) {
     if (m->n_int_edges == 0) return PIC_OK;
     CgProblem P;
     P.n = m->n_int_edges;
-    P.rp = m->A.rowptr.p;
-    P.col = m->A.col.p;
+    P.rp = nullptr;
+    P.col = m->As.col.p;
+    P.sp = m->As.ptr.p;
+    P.sw = m->As.width.p;
+    P.n_slices = m->As.n_slices;
     P.Av = s->A_val.p;
     P.Dinv = s->Dinv.p;
     P.b = s->rhs.p;
@@ -777,10 +1088,48 @@ int pcg_newmark(Sim *s) {
     return rc;
 }
 
+// co-resident blocks of the persistent PCG on the current device (0: no
+// cooperative launch)
+static int coop_capacity() {
+    int dev = 0, sms = 0, coop = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent, kThreads, 0) != cudaSuccess) return 0;
+    return per_sm * sms;
+}
+
 int laplacian_solve(Sim *s, const double *rhs_int, double *x_int, double tol, const double *abs_src,
                     double abs_factor) {
     const Mesh *m = s->mesh;
     if (m->n_int_nodes == 0) return PIC_OK;
+    if (s->coop_blocks < 0) s->coop_blocks = coop_capacity();
+    if (s->coop_blocks > 0) {
+        // one cooperative launch for the whole solve; failures surface through
+        // the status word at the step's next synchronisation
+        int n = m->n_int_nodes;
+        const int G = std::max(1, std::min(std::min(s->coop_blocks, kMaxBlocks), (n + kRowsPerBlock - 1) / kRowsPerBlock));
+        CgState init{};
+        init.tol2 = tol * tol;
+        init.fallback_tol2 = s->cfg.init_tol * s->cfg.init_tol;
+        init.max_iters = 20000;
+        init.abs_inf = -1.0;
+        Control *dc = s->dctl.p;
+        FP_CUDA(cudaMemcpyAsync(&dc->lap, &init, sizeof(CgState), cudaMemcpyHostToDevice, s->stream));
+        FP_CUDA(cudaMemsetAsync(&dc->gbar, 0, sizeof(GridBarrier), s->stream));
+        const int *rp = m->L.rowptr.p, *col = m->L.col.p;
+        const double *Av = m->L_val.p, *Dinv = s->L_Dinv.p, *b = rhs_int;
+        double *x = x_int, *r = s->l_r.p, *z = s->l_z.p, *p0 = s->l_p0.p, *p1 = s->l_p1.p, *q = s->l_q.p;
+        double *part = s->l_part.p;
+        CgState *st = &dc->lap;
+        GridBarrier *gb = &dc->gbar;
+        uint32_t *status = &dc->status;
+        void *args[] = {&n, &rp, &col, &Av, &Dinv, &b, &x, &r, &z, &p0, &p1, &q, &part, &st, &gb,
+                        (void *)&abs_src, &abs_factor, &status};
+        FP_CUDA(cudaLaunchCooperativeKernel((const void *)k_pcg_persistent, G, kThreads, args, 0, s->stream));
+        note_launch();
+        return PIC_OK;
+    }
     CgProblem P;
     P.n = m->n_int_nodes;
     P.rp = m->L.rowptr.p;
@@ -814,9 +1163,7 @@ int gradient_completion(Sim *s) {
     const Mesh *m = s->mesh;
     const int ni = m->n_int_edges, nin = m->n_int_nodes;
     if (ni == 0 || nin == 0) return PIC_OK;
-    { k_gc_w<<<grid_for_rows(ni), kThreads, 0, s->stream>>>(ni, m->A.rowptr.p, m->A.col.p, m->M_val.p, s->cfg.form,
-                                                          s->e.p, s->e_prev.p, s->x.p, s->g_new.p, s->g.p, s->g_prev.p,
-                                                          s->w_edge.p); note_launch(); }
+    { k_gc_w_sell<<<grid_for_slices(m->As.n_slices), kThreads, 0, s->stream>>>(ni, m->As.n_slices, m->As.ptr.p, m->As.width.p, m->As.col.p, m->M_val.p, s->cfg.form, s->e.p, s->e_prev.p, s->x.p, s->g_new.p, s->g.p, s->g_prev.p, s->w_edge.p); note_launch(); }
     { k_gc_d<<<(nin + 255) / 256, 256, 0, s->stream>>>(nin, m->int_node.p, m->n2e.rowptr.p, m->n2e.col.p, m->n2e_sgn.p,
                                                      ni, s->w_edge.p, s->l_b.p); note_launch(); }
     FP_CUDA(cudaMemsetAsync(s->l_x.p, 0, sizeof(double) * nin, s->stream));
@@ -844,9 +1191,7 @@ int compute_diagnostics(Sim *s) {
     DiagDev *dg = &s->dctl.p->diag;
     const int ni = m->n_int_edges;
     if (ni > 0)
-        { k_resid<<<grid_for_rows(ni), kThreads, 0, s->stream>>>(ni, m->A.rowptr.p, m->A.col.p, m->M_val.p, m->K_val.p,
-                                                               0.25 * s->cfg.dt * s->cfg.dt, s->e.p, s->rhs.p, s->me.p,
-                                                               s->diag_part.p, dg); note_launch(); }
+        { k_resid_sell<<<grid_for_slices(m->As.n_slices), kThreads, 0, s->stream>>>(ni, m->As.n_slices, m->As.ptr.p, m->As.width.p, m->As.col.p, m->M_val.p, m->K_val.p, 0.25 * s->cfg.dt * s->cfg.dt, s->e.p, s->rhs.p, s->me.p, s->diag_part.p, dg); note_launch(); }
     { k_diag_nodes<<<grid_for_elems(m->n_nodes), kThreads, 0, s->stream>>>(
         m->n_nodes, m->n2e.rowptr.p, m->n2e.col.p, m->n2e_sgn.p, ni, s->dg.p, s->me.p, s->rho.p, s->rho_prev.p,
         s->wall.p, s->wall_prev.p, s->rho_bg.p, m->node_bnd.p, s->diag_part.p, dg); note_launch(); }
@@ -978,7 +1323,7 @@ int electrostatic_solve_noalloc(const Mesh *m, const double *rho_nodes, double *
     int launched = 0;
     for (;;) {
         for (int c = 0; c < 16; c++) {
-            { k_cg_a<1><<<gr, kThreads, 0, st>>>(nin, m->L.rowptr.p, m->L.col.p, m->L_val.p, z, pold, pnew, q, part, dst); note_launch(); }
+            { k_cg_a_csr<<<gr, kThreads, 0, st>>>(nin, m->L.rowptr.p, m->L.col.p, m->L_val.p, z, pold, pnew, q, part, dst); note_launch(); }
             { k_cg_b<<<ge, kThreads, 0, st>>>(nin, dinv, x, r, z, pnew, q, part + 3 * kMaxBlocks, dst); note_launch(); }
             std::swap(pold, pnew);
             launched++;
