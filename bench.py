@@ -320,6 +320,7 @@ def gpu_arm(args):
             "phases_ms_per_step_plain": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof_p.items()
                                          if k != "spmv"},
             "cg_iters_last": diag_m["cg_iters"],
+            "completion_iters_last": diag_m["completion_iters"],
             "conservation_last": {"continuity_rel": diag_m["continuity_abs"] / max(diag_m["rho_max"], 1e-300),
                                   "gauss_rel": diag_m["gauss_abs"] / max(diag_m["rho_max"], 1e-300)},
             "roofline": roofline,

@@ -230,6 +230,7 @@ typedef struct {
     double energy_b;        /* 1/2 b^T H b */
     double energy_k;        /* sum 1/2 m w |v|^2 */
     double status;          /* latched device status bits */
+    double completion_iters; /* iterations of the last gradient-subspace completion */
 } pic_diag;
 
 /* Diagnostics of the last step (Sec. III.A conservation laws).  Synchronises. */

@@ -660,6 +660,7 @@ int pic_diagnostics_get(pic_sim *sim, pic_diag *out) {
     out->energy_b = c.diag.energy_b;
     out->energy_k = c.diag.energy_k;
     out->status = (double)(c.status | s->host_status);
+    out->completion_iters = s->step > 0 ? c.lap.iters : 0;
     return PIC_OK;
 }
 

@@ -113,8 +113,8 @@ struct HostStage {
     std::vector<int2> edge_nodes;
     HostCsrStage e2t, n2t, H, L, e2f, n2e;
     std::vector<double> H_val, L_val;
-    std::vector<int> sell_ptr, sell_w, sell_col;
-    std::vector<double> sell_M, sell_K, M_diag, K_diag;
+    std::vector<int> sell_ptr, sell_w, sell_col, lsell_ptr, lsell_w, lsell_col;
+    std::vector<double> sell_M, sell_K, M_diag, K_diag, lsell_L, L_diag;
     std::vector<signed char> e2f_sgn, n2e_sgn;
 };
 
@@ -159,9 +159,12 @@ struct Mesh {
     // face mass [*mu^-1] on all faces
     DevCsr H;
     DevBuf<double> H_val;
-    // node Laplacian G^T M G on interior nodes (compact numbering)
+    // node Laplacian G^T M G on interior nodes (compact numbering, ordered by
+    // row length): CSR and SELL-32 copies
     DevCsr L;
     DevBuf<double> L_val;
+    DevSell Ls;
+    DevBuf<double> Ls_val, L_diag;
     DevBuf<int> node_int;      // node -> interior index or -1
     DevBuf<int> int_node;      // interior index -> node
     // incidence gathers

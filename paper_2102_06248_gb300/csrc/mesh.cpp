@@ -83,6 +83,49 @@ inline int find_col(const HostCsr &a, int row, int col) {
 }
 
 
+// SELL-32 layout of a CSR pattern: slice s holds rows 32s..32s+31, entry j of
+// lane l at ptr[s] + 32 j + l; padding points at the row itself with value 0.
+// vals: CSR value arrays to lay out; diag receives each row's diagonal.
+void build_sell(const HostCsr &pa, const std::vector<const std::vector<double> *> &vals, std::vector<int> &ptr,
+                std::vector<int> &w, std::vector<int> &col, std::vector<std::vector<double>> &out,
+                std::vector<std::vector<double>> &diag) {
+    const int n = (int)pa.rowptr.size() - 1;
+    const int nsl = (n + 31) / 32;
+    ptr.assign(nsl + 1, 0);
+    w.assign(nsl, 0);
+    for (int sl = 0; sl < nsl; sl++) {
+        int ww = 0;
+        for (int l = 0; l < 32; l++) {
+            const int r = 32 * sl + l;
+            if (r < n) ww = std::max(ww, pa.rowptr[r + 1] - pa.rowptr[r]);
+        }
+        w[sl] = ww;
+        ptr[sl + 1] = ptr[sl] + 32 * ww;
+    }
+    const size_t nel = (size_t)ptr[nsl];
+    col.assign(nel, 0);
+    out.assign(vals.size(), std::vector<double>(nel, 0.0));
+    diag.assign(vals.size(), std::vector<double>(n, 0.0));
+    for (int sl = 0; sl < nsl; sl++)
+        for (int l = 0; l < 32; l++) {
+            const int r = 32 * sl + l;
+            const int rr = r < n ? r : n - 1;
+            for (int j = 0; j < w[sl]; j++) {
+                const size_t q = (size_t)ptr[sl] + 32 * (size_t)j + l;
+                const int k = pa.rowptr[rr] + j;
+                if (r < n && k < pa.rowptr[r + 1]) {
+                    col[q] = pa.col[k];
+                    for (size_t v = 0; v < vals.size(); v++) {
+                        out[v][q] = (*vals[v])[k];
+                        if (pa.col[k] == r) diag[v][r] = (*vals[v])[k];
+                    }
+                } else {
+                    col[q] = rr;
+                }
+            }
+        }
+}
+
 }  // namespace
 
 int build_mesh(const pic_mesh_desc *d, Mesh *m) {
@@ -247,12 +290,25 @@ int build_mesh(const pic_mesh_desc *d, Mesh *m) {
     for (int e = 0; e < ne; e++)
         if (edge_bnd[e]) m->h_edge_internal[e] = nb_++;
     for (int e = 0; e < ne; e++) m->h_edge_canonical[m->h_edge_internal[e]] = e;
+    // interior nodes, ordered by the length of their Laplacian row (node ids
+    // within a length) for the SELL-32 layout of the node Laplacian
     std::vector<int> node_int(nn, -1), int_node;
-    for (int n = 0; n < nn; n++)
-        if (!m->h_node_bnd[n]) {
-            node_int[n] = (int)int_node.size();
-            int_node.push_back(n);
+    {
+        HostCsr pn = pattern_from_groups(nn, nt, 4, nn, nn, [&](int t, int *out) {
+            for (int k = 0; k < 4; k++) {
+                const int v = TS[4 * t + k];
+                out[k] = m->h_node_bnd[v] ? -1 : v;
+            }
+        });
+        std::vector<std::pair<int, int>> order;
+        for (int n = 0; n < nn; n++)
+            if (!m->h_node_bnd[n]) order.push_back({pn.rowptr[n + 1] - pn.rowptr[n], n});
+        std::sort(order.begin(), order.end());
+        for (auto &pr : order) {
+            node_int[pr.second] = (int)int_node.size();
+            int_node.push_back(pr.second);
         }
+    }
     m->n_int_nodes = (int)int_node.size();
 
     // ---- optional caller-supplied entities / incidence must match ----
@@ -453,49 +509,18 @@ int build_mesh(const pic_mesh_desc *d, Mesh *m) {
     H.geo = std::move(geo);
     H.tet_edge = std::move(tet_edge);
     m->nnz_L = (long long)pl.col.size();
-    // SELL-32 layout of the Newmark pattern: slice s holds rows 32s..32s+31,
-    // entry j of lane l at sell_ptr[s] + 32 j + l; padding points at the row
-    // itself with value 0
+    // SELL-32 layout of the Newmark pattern (M and K values) and of the node Laplacian
     {
-        const int nsl = (nie + 31) / 32;
-        H.sell_ptr.assign(nsl + 1, 0);
-        H.sell_w.assign(nsl, 0);
-        for (int sl = 0; sl < nsl; sl++) {
-            int w = 0;
-            for (int l = 0; l < 32; l++) {
-                const int r = 32 * sl + l;
-                if (r < nie) w = std::max(w, pa.rowptr[r + 1] - pa.rowptr[r]);
-            }
-            H.sell_w[sl] = w;
-            H.sell_ptr[sl + 1] = H.sell_ptr[sl] + 32 * w;
-        }
-        const size_t nel = (size_t)H.sell_ptr[nsl];
-        H.sell_col.assign(nel, 0);
-        H.sell_M.assign(nel, 0.0);
-        H.sell_K.assign(nel, 0.0);
-        H.M_diag.assign(nie, 0.0);
-        H.K_diag.assign(nie, 0.0);
-        for (int sl = 0; sl < nsl; sl++)
-            for (int l = 0; l < 32; l++) {
-                const int r = 32 * sl + l;
-                const int rr = r < nie ? r : nie - 1;
-                for (int j = 0; j < H.sell_w[sl]; j++) {
-                    const size_t q = (size_t)H.sell_ptr[sl] + 32 * (size_t)j + l;
-                    const int k = pa.rowptr[rr] + j;
-                    if (r < nie && k < pa.rowptr[r + 1]) {
-                        H.sell_col[q] = pa.col[k];
-                        H.sell_M[q] = Mv[k];
-                        H.sell_K[q] = Kv[k];
-                        if (pa.col[k] == r) {
-                            H.M_diag[r] = Mv[k];
-                            H.K_diag[r] = Kv[k];
-                        }
-                    } else {
-                        H.sell_col[q] = rr;
-                    }
-                }
-            }
+        std::vector<std::vector<double>> out, dg;
+        build_sell(pa, {&Mv, &Kv}, H.sell_ptr, H.sell_w, H.sell_col, out, dg);
+        H.sell_M = std::move(out[0]);
+        H.sell_K = std::move(out[1]);
+        H.M_diag = std::move(dg[0]);
+        H.K_diag = std::move(dg[1]);
         m->nnz_A = (long long)pa.col.size();
+        build_sell(pl, {&Lv}, H.lsell_ptr, H.lsell_w, H.lsell_col, out, dg);
+        H.lsell_L = std::move(out[0]);
+        H.L_diag = std::move(dg[0]);
     }
     H.H = {std::move(ph.rowptr), std::move(ph.col)};
     H.H_val = std::move(Hv);
@@ -536,6 +561,12 @@ int mesh_upload(Mesh *m) {
         return rc;
     if ((rc = csr(H.H, &m->H)) || (rc = m->H_val.upload(H.H_val))) return rc;
     if ((rc = csr(H.L, &m->L)) || (rc = m->L_val.upload(H.L_val))) return rc;
+    m->Ls.n_rows = m->n_int_nodes;
+    m->Ls.n_slices = (int)H.lsell_w.size();
+    m->Ls.n_elems = H.lsell_ptr.empty() ? 0 : H.lsell_ptr.back();
+    if ((rc = m->Ls.ptr.upload(H.lsell_ptr)) || (rc = m->Ls.width.upload(H.lsell_w)) ||
+        (rc = m->Ls.col.upload(H.lsell_col)) || (rc = m->Ls_val.upload(H.lsell_L)) || (rc = m->L_diag.upload(H.L_diag)))
+        return rc;
     if ((rc = m->node_int.upload(H.node_int)) || (rc = m->int_node.upload(H.int_node))) return rc;
     if ((rc = csr(H.e2f, &m->e2f)) || (rc = m->e2f_sgn.upload(H.e2f_sgn))) return rc;
     if ((rc = csr(H.n2e, &m->n2e)) || (rc = m->n2e_sgn.upload(H.n2e_sgn))) return rc;

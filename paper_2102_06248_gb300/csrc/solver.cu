@@ -714,12 +714,11 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier *gb) {
             } else {
                 long spins = 0;
                 while (*vgen == g) {
-                    if (++spins > (1L << 24) || *vto != 0) {
+                    if (++spins > (1L << 26) || *vto != 0) {
                         atomicExch(&gb->timeout, 1);
                         good = 0;
                         break;
                     }
-                    __nanosleep(32);
                 }
             }
             __threadfence();
@@ -730,120 +729,148 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier *gb) {
     return ok != 0;
 }
 
-// fixed-order sum / max over the blocks' partials, broadcast to the block
-template <bool MAX>
-__device__ __forceinline__ double all_blocks_combine(const double *part, double *sh, double *bcast) {
-    double v[1] = {0.0};
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += kThreads) {
-        const double x = __ldcg(part + b);
-        v[0] = MAX ? fmax(v[0], x) : v[0] + x;
+// fixed-order combination over the blocks' partials, broadcast to the block:
+// NS sums (arrays part + c*G, c < NS) and NM maxima (the next NM arrays)
+template <int NS, int NM>
+__device__ __forceinline__ void all_blocks_combine(const double *part, double *sh, double *bcast, double out[NS + NM]) {
+    const int G = gridDim.x;
+    double vs[NS > 0 ? NS : 1], vm[NM > 0 ? NM : 1];
+#pragma unroll
+    for (int c = 0; c < NS; c++) vs[c] = 0.0;
+#pragma unroll
+    for (int c = 0; c < NM; c++) vm[c] = 0.0;
+    for (int b = threadIdx.x; b < G; b += kThreads) {
+#pragma unroll
+        for (int c = 0; c < NS; c++) vs[c] += __ldcg(part + c * G + b);
+#pragma unroll
+        for (int c = 0; c < NM; c++) vm[c] = fmax(vm[c], __ldcg(part + (NS + c) * G + b));
     }
-    if (MAX) block_max<1>(v, sh);
-    else block_sum<1>(v, sh);
-    if (threadIdx.x == 0) *bcast = v[0];
+    if constexpr (NS > 0) block_sum<NS>(vs, sh);
+    if constexpr (NM > 0) block_max<NM>(vm, sh);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int c = 0; c < NS; c++) bcast[c] = vs[c];
+#pragma unroll
+        for (int c = 0; c < NM; c++) bcast[NS + c] = vm[c];
+    }
     __syncthreads();
-    const double out = *bcast;
+#pragma unroll
+    for (int c = 0; c < NS + NM; c++) out[c] = bcast[c];
     __syncthreads();
-    return out;
 }
 
-__global__ void __launch_bounds__(kThreads, 2) k_pcg_persistent(int n, const int *__restrict__ rp,
-                                                             const int *__restrict__ col, const double *__restrict__ Av,
-                                                             const double *__restrict__ Dinv, const double *__restrict__ b,
-                                                             double *x, double *r, double *z, double *p0, double *p1,
-                                                             double *q, double *part, CgState *st, GridBarrier *gb,
-                                                             const double *abs_src, double abs_factor, uint32_t *status) {
+// SELL-32 row of the node Laplacian: sum_j L_rj v_j (v read through L2)
+__device__ __forceinline__ double sell_row_dot(int kb, int kw, const int *__restrict__ col,
+                                               const double *__restrict__ val, const double *v) {
+    double s = 0.0;
+#pragma unroll 4
+    for (int j = 0; j < kw; j++) {
+        const int k = kb + 32 * j;
+        s += val[k] * __ldcg(v + col[k]);
+    }
+    return s;
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(int n, int n_slices, const int *__restrict__ sp,
+                                                                const int *__restrict__ sw, const int *__restrict__ col,
+                                                                const double *__restrict__ Av,
+                                                                const double *__restrict__ Dinv,
+                                                                const double *__restrict__ b, double *x, double *r,
+                                                                double *z, double *p0, double *p1, double *q,
+                                                                double *part, CgState *st, GridBarrier *gb,
+                                                                const double *abs_src, double abs_factor,
+                                                                uint32_t *status) {
     __shared__ double sh[3 * kThreads / 32];
-    __shared__ double bc;
-    const int lane = threadIdx.x % kLanes;
+    __shared__ double bc[4];
     const int G = gridDim.x;
-    double *pp0 = part, *pp1 = part + G, *pp2 = part + 2 * G, *pp3 = part + 3 * G;
-    const double tol2_cfg = st->tol2, fallback2 = st->fallback_tol2;
+    const int lane = threadIdx.x & 31;
     const int max_iters = st->max_iters;
     double abs_inf = st->abs_inf;
-    double tol2 = tol2_cfg;
+    double tol2 = st->tol2;
     if (abs_src) {
         const double qv = *abs_src;
         if (qv > 0.0) abs_inf = abs_factor * qv;
-        else tol2 = fallback2;
+        else tol2 = st->fallback_tol2;
     }
-    // ---- r = b - A x, z = D^-1 r, p = z ----
+    // ---- r = b - A x, z = D^-1 r ----
     {
-        double v3[3] = {0.0, 0.0, 0.0}, vm[1] = {0.0};
-        for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < n;
-             r0_ += G * kRowsPerBlock) {
-            const int i = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
-            const bool rv = i < n;
-            const int kb = rv ? rp[i] : 0, kend = rv ? rp[i + 1] : 0;
-            double sacc = 0.0;
-            for (int k = kb + lane; k < kend; k += kLanes) sacc += Av[k] * x[col[k]];
-            sacc = row_reduce(sacc);
-            if (rv && lane == 0) {
-                const double ri = b[i] - sacc, zi = Dinv[i] * ri;
+        double v[3] = {0.0, 0.0, 0.0}, vm[1] = {0.0};
+        for (int sl = blockIdx.x * kSlicesPerBlock + (threadIdx.x >> 5); sl < n_slices; sl += G * kSlicesPerBlock) {
+            const int i = sl * 32 + lane;
+            const double s = sell_row_dot(sp[sl] + lane, sw[sl], col, Av, x);
+            if (i < n) {
+                const double ri = b[i] - s, zi = Dinv[i] * ri;
                 r[i] = ri;
                 z[i] = zi;
-                v3[0] += ri * zi;
-                v3[1] += ri * ri;
-                v3[2] += b[i] * b[i];
+                v[0] += ri * zi;
+                v[1] += ri * ri;
+                v[2] += b[i] * b[i];
                 vm[0] = fmax(vm[0], fabs(ri));
             }
         }
-        block_sum<3>(v3, sh);
+        block_sum<3>(v, sh);
         block_max<1>(vm, sh);
         if (threadIdx.x == 0) {
-            pp0[blockIdx.x] = v3[0];
-            pp1[blockIdx.x] = v3[1];
-            pp2[blockIdx.x] = v3[2];
-            pp3[blockIdx.x] = vm[0];
+            part[blockIdx.x] = v[0];
+            part[G + blockIdx.x] = v[1];
+            part[2 * G + blockIdx.x] = v[2];
+            part[3 * G + blockIdx.x] = vm[0];
         }
     }
     if (!grid_barrier(gb)) goto timeout;
     {
-        double rz = all_blocks_combine<false>(pp0, sh, &bc);
-        double rr = all_blocks_combine<false>(pp1, sh, &bc);
-        const double bb = all_blocks_combine<false>(pp2, sh, &bc);
-        const double mx0 = all_blocks_combine<true>(pp3, sh, &bc);
-        bool done = (bb == 0.0) || (rr <= tol2 * bb) || (mx0 <= abs_inf);
+        double t[4];
+        all_blocks_combine<3, 1>(part, sh, bc, t);
+        double rz = t[0], rr = t[1];
+        const double bb = t[2];
+        bool done = (bb == 0.0) || (rr <= tol2 * bb) || (t[3] <= abs_inf);
         if (bb == 0.0)
             for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += G * kThreads) x[i] = 0.0;
         int iters = 0;
         bool failed = false;
         double beta = 0.0;
         double *pold = p0, *pnew = p1;
-        // the partials of the previous combine must be read by every block
-        // before they are overwritten: barrier
-        if (!grid_barrier(gb)) goto timeout;
+        double *pp = part + 4 * G;   // partials of p.q (the others use part)
         while (!done) {
             if (iters >= max_iters) {
                 failed = true;
                 break;
             }
             const bool first = iters == 0;
-            // ---- q = A p with p = z + beta p_old formed on the fly ----
+            // ---- p = z + beta p_old, q = A p (p of the neighbours formed on the fly) ----
             double vpq[1] = {0.0};
-            for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < n;
-                 r0_ += G * kRowsPerBlock) {
-                const int i = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
-                const bool rv = i < n;
-                const int kb = rv ? rp[i] : 0, kend = rv ? rp[i + 1] : 0;
-                double sacc = 0.0;
-                for (int k = kb + lane; k < kend; k += kLanes) {
-                    const int j = col[k];
-                    const double pj = first ? __ldcg(z + j) : __ldcg(z + j) + beta * __ldcg(pold + j);
-                    sacc += Av[k] * pj;
+            for (int sl = blockIdx.x * kSlicesPerBlock + (threadIdx.x >> 5); sl < n_slices;
+                 sl += G * kSlicesPerBlock) {
+                const int i = sl * 32 + lane;
+                const int kb = sp[sl] + lane, kw = sw[sl];
+                double s = 0.0;
+                if (first) {
+#pragma unroll 4
+                    for (int j = 0; j < kw; j++) {
+                        const int k = kb + 32 * j;
+                        s += Av[k] * __ldcg(z + col[k]);
+                    }
+                } else {
+#pragma unroll 4
+                    for (int j = 0; j < kw; j++) {
+                        const int k = kb + 32 * j;
+                        const int c = col[k];
+                        s += Av[k] * (__ldcg(z + c) + beta * __ldcg(pold + c));
+                    }
                 }
-                sacc = row_reduce(sacc);
-                if (rv && lane == 0) {
+                if (i < n) {
                     const double pi = first ? __ldcg(z + i) : __ldcg(z + i) + beta * __ldcg(pold + i);
                     pnew[i] = pi;
-                    q[i] = sacc;
-                    vpq[0] += pi * sacc;
+                    q[i] = s;
+                    vpq[0] += pi * s;
                 }
             }
             block_sum<1>(vpq, sh);
-            if (threadIdx.x == 0) pp0[blockIdx.x] = vpq[0];
+            if (threadIdx.x == 0) pp[blockIdx.x] = vpq[0];
             if (!grid_barrier(gb)) goto timeout;
-            const double alpha = rz / all_blocks_combine<false>(pp0, sh, &bc);
+            double tpq[1];
+            all_blocks_combine<1, 0>(pp, sh, bc, tpq);
+            const double alpha = rz / tpq[0];
             // ---- x += alpha p, r -= alpha q, z = D^-1 r ----
             double v2[2] = {0.0, 0.0}, vm[1] = {0.0};
             for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += G * kThreads) {
@@ -859,21 +886,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_pcg_persistent(int n, const int
             block_sum<2>(v2, sh);
             block_max<1>(vm, sh);
             if (threadIdx.x == 0) {
-                pp1[blockIdx.x] = v2[0];
-                pp2[blockIdx.x] = v2[1];
-                pp3[blockIdx.x] = vm[0];
+                part[blockIdx.x] = v2[0];
+                part[G + blockIdx.x] = v2[1];
+                part[2 * G + blockIdx.x] = vm[0];
             }
             if (!grid_barrier(gb)) goto timeout;
-            const double rz_new = all_blocks_combine<false>(pp1, sh, &bc);
-            rr = all_blocks_combine<false>(pp2, sh, &bc);
-            const double mx = all_blocks_combine<true>(pp3, sh, &bc);
-            beta = rz_new / rz;
-            rz = rz_new;
+            double t3[3];
+            all_blocks_combine<2, 1>(part, sh, bc, t3);
+            beta = t3[0] / rz;
+            rz = t3[0];
+            rr = t3[1];
             iters++;
-            double *t = pold;
+            double *tmp = pold;
             pold = pnew;
-            pnew = t;
-            done = (rr <= tol2 * bb) || (mx <= abs_inf);
+            pnew = tmp;
+            done = (rr <= tol2 * bb) || (t3[2] <= abs_inf);
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             st->iters = iters;
@@ -1108,7 +1135,8 @@ int laplacian_solve(Sim *s, const double *rhs_int, double *x_int, double tol, co
         // one cooperative launch for the whole solve; failures surface through
         // the status word at the step's next synchronisation
         int n = m->n_int_nodes;
-        const int G = std::max(1, std::min(std::min(s->coop_blocks, kMaxBlocks), (n + kRowsPerBlock - 1) / kRowsPerBlock));
+        const int G = std::max(1, std::min(std::min(s->coop_blocks, kMaxBlocks / 2),
+                                           (m->Ls.n_slices + kSlicesPerBlock - 1) / kSlicesPerBlock));
         CgState init{};
         init.tol2 = tol * tol;
         init.fallback_tol2 = s->cfg.init_tol * s->cfg.init_tol;
@@ -1117,14 +1145,15 @@ int laplacian_solve(Sim *s, const double *rhs_int, double *x_int, double tol, co
         Control *dc = s->dctl.p;
         FP_CUDA(cudaMemcpyAsync(&dc->lap, &init, sizeof(CgState), cudaMemcpyHostToDevice, s->stream));
         FP_CUDA(cudaMemsetAsync(&dc->gbar, 0, sizeof(GridBarrier), s->stream));
-        const int *rp = m->L.rowptr.p, *col = m->L.col.p;
-        const double *Av = m->L_val.p, *Dinv = s->L_Dinv.p, *b = rhs_int;
+        int nsl = m->Ls.n_slices;
+        const int *sp = m->Ls.ptr.p, *sw = m->Ls.width.p, *col = m->Ls.col.p;
+        const double *Av = m->Ls_val.p, *Dinv = s->L_Dinv.p, *b = rhs_int;
         double *x = x_int, *r = s->l_r.p, *z = s->l_z.p, *p0 = s->l_p0.p, *p1 = s->l_p1.p, *q = s->l_q.p;
         double *part = s->l_part.p;
         CgState *st = &dc->lap;
         GridBarrier *gb = &dc->gbar;
         uint32_t *status = &dc->status;
-        void *args[] = {&n, &rp, &col, &Av, &Dinv, &b, &x, &r, &z, &p0, &p1, &q, &part, &st, &gb,
+        void *args[] = {&n, &nsl, &sp, &sw, &col, &Av, &Dinv, &b, &x, &r, &z, &p0, &p1, &q, &part, &st, &gb,
                         (void *)&abs_src, &abs_factor, &status};
         FP_CUDA(cudaLaunchCooperativeKernel((const void *)k_pcg_persistent, G, kThreads, args, 0, s->stream));
         note_launch();

@@ -50,7 +50,7 @@ class pic_config(C.Structure):
 class pic_diag(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "step", "continuity_abs", "gauss_abs", "rho_max", "divb_abs", "cg_iters", "cg_relres", "n_alive",
-        "energy_e", "energy_b", "energy_k", "status")]
+        "energy_e", "energy_b", "energy_k", "status", "completion_iters")]
 
 
 _lib = None
