@@ -38,6 +38,7 @@ from paper_2102_06248_gb300 import workloads as W  # noqa: E402
 
 METRIC = "particle-steps/s (gather+push+deposit) and step time vs plain FP64 GPU path"
 FALLBACK_HBM_GBS = 6800.0
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (non-tensor) nominal rate
 
 
 def dt_table():
@@ -175,10 +176,18 @@ def push_bytes(n_particles: int, n_tets: int, precision: str, n_species: int = 1
     return n_particles * per_particle + n_tets * per_tet
 
 
-def spmv_bytes(n_rows: int, nnz: int) -> float:
-    """Algorithmic bytes of one fused PCG SpMV launch (q = A p, p = z + beta p):
-    values + columns (12 B/nnz), row pointers, z and p_old read, p_new and q written."""
-    return 12.0 * nnz + 4.0 * (n_rows + 1) + 32.0 * n_rows
+def pcg_iter_bytes(n_rows: int, nnz: int) -> float:
+    """Algorithmic bytes of one iteration of the persistent Chronopoulos-Gear
+    PCG on SELL-32: values + columns once (12 B/nnz) and two slice headers per
+    32 rows; the SpMV reads u once and writes w; the vector phase reads u, w,
+    p, s, x, r, D^-1 and writes p, s, x, r, u (14 vector passes of 8 B)."""
+    return 12.0 * nnz + 8.0 * (n_rows + 31) / 32 + 8.0 * 14 * n_rows
+
+
+def pcg_iter_flops(n_rows: int, nnz: int) -> float:
+    """FP64 flops of one such iteration: a multiply-add per stored entry and
+    per row the seven of the vector phase plus the one of (w, u)."""
+    return 2.0 * nnz + 2.0 * 8 * n_rows
 
 
 def time_gpu(F, wl, dt, precision, steps, warmup, stream, dist, device, torch, profile=True):
@@ -223,6 +232,7 @@ def gpu_arm(args):
     for _ in range(args.warmup):
         sim_m.step()
     sim_m.profile_reset()
+    d0 = sim_m.diag()
     barrier(dist, local if world > 1 else None)
     torch.cuda.synchronize()
     l0 = F.launch_count()
@@ -241,6 +251,7 @@ def gpu_arm(args):
     prof_m = sim_m.profile()
     diag_m = sim_m.diag()
     alive_m = diag_m["n_alive"]
+    cg_iters_timed = diag_m["cg_iters_sum"] - d0["cg_iters_sum"]
     ms_max = max_over_ranks(dist, ms_mixed, device)
     total_ps = sum_over_ranks(dist, float(n_part) * args.steps, device)
     value = total_ps / (ms_max / 1e3)
@@ -281,22 +292,32 @@ def gpu_arm(args):
     # ---- roofline of the dominant kernel (live CUDA-event times) ----
     peak, peak_src = measured_peak()
     push_ms, push_n = prof_m["push"]
-    spmv_ms, spmv_n = prof_m["spmv"]
+    cg_ms, cg_n = prof_m["cg"]
     push_avg = push_ms / max(push_n, 1)
-    spmv_avg = spmv_ms / max(spmv_n, 1)
+    cg_avg = cg_ms / max(cg_n, 1)
     nnz_A = int(getattr(mesh, "nnz_A", 0))
-    if push_ms >= spmv_ms:
-        kernel = "k_push (fused gather/push/walk/deposit, mixed)"
+    fp64 = None
+    if push_ms >= cg_ms:
+        kernel = "k_push_mixed (fused gather/push/walk/deposit)"
         alg = push_bytes(int(alive_m), mesh.n_tets, "mixed", len(wl.species))
         avg_ms = push_avg
     else:
-        kernel = "k_cg_a_sell (fused PCG SpMV of the Newmark solve, SELL-32)"
-        alg = spmv_bytes(mesh.n_int_edges, nnz_A)
-        avg_ms = spmv_avg
+        # one launch runs the whole Newmark solve: its algorithmic bytes are
+        # the iterations it ran times the bytes of one iteration
+        kernel = "k_pcg_persistent (Newmark PCG, Chronopoulos-Gear, SELL-32)"
+        iters_per_launch = cg_iters_timed / max(cg_n, 1)
+        alg = iters_per_launch * pcg_iter_bytes(mesh.n_int_edges, nnz_A)
+        avg_ms = cg_avg
+        flops = iters_per_launch * pcg_iter_flops(mesh.n_int_edges, nnz_A)
+        fp64_tf = flops / (avg_ms / 1e3) / 1e12
+        fp64 = {"achieved_tflops": round(fp64_tf, 4), "peak_tflops": FP64_NOMINAL_TFLOPS,
+                "frac": round(fp64_tf / FP64_NOMINAL_TFLOPS, 4), "peak_source": "nominal",
+                "iters_per_launch": iters_per_launch}
     achieved = alg / (avg_ms / 1e3) / 1e9
     roofline = {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
-                "traffic": None, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": round(avg_ms, 5)}
+                "traffic": None, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": round(avg_ms, 5),
+                "fp64": fp64}
 
     # ---- CPU baseline: the oracle on a bounded, proportionally scaled sample ----
     cpu = None
@@ -316,9 +337,8 @@ def gpu_arm(args):
             "plain_fp64": None if args.skip_plain else {
                 "value": value_plain, "ms_per_step": ms_plain_max / args.steps,
                 "speedup_mixed_over_plain": value / value_plain},
-            "phases_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof_m.items() if k != "spmv"},
-            "phases_ms_per_step_plain": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof_p.items()
-                                         if k != "spmv"},
+            "phases_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof_m.items()},
+            "phases_ms_per_step_plain": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof_p.items()},
             "cg_iters_last": diag_m["cg_iters"],
             "completion_iters_last": diag_m["completion_iters"],
             "conservation_last": {"continuity_rel": diag_m["continuity_abs"] / max(diag_m["rho_max"], 1e-300),

@@ -231,6 +231,8 @@ typedef struct {
     double energy_k;        /* sum 1/2 m w |v|^2 */
     double status;          /* latched device status bits */
     double completion_iters; /* iterations of the last gradient-subspace completion */
+    double cg_iters_sum;    /* Newmark PCG iterations summed over all steps taken */
+    double completion_iters_sum; /* completion PCG iterations summed over all steps */
 } pic_diag;
 
 /* Diagnostics of the last step (Sec. III.A conservation laws).  Synchronises. */
@@ -243,11 +245,10 @@ int pic_diagnostics_get(pic_sim *sim, pic_diag *out);
 #define PIC_PHASE_PUSH 2        /* the fused gather/push/walk/deposit kernel */
 #define PIC_PHASE_DEPOSIT 3     /* spanning runs, crossing records, edge/node reduction */
 #define PIC_PHASE_RHS 4         /* Newmark right-hand side */
-#define PIC_PHASE_CG 5          /* PCG on the Newmark system */
+#define PIC_PHASE_CG 5          /* PCG on the Newmark system (one persistent kernel) */
 #define PIC_PHASE_COMPLETION 6  /* gradient-subspace completion (Laplacian PCG) */
 #define PIC_PHASE_FIELD_OTHER 7 /* Faraday update and diagnostics */
-#define PIC_PHASE_SPMV 8        /* each SpMV kernel of the Newmark PCG (per launch) */
-#define PIC_PHASE_COUNT 9
+#define PIC_PHASE_COUNT 8
 
 /* Accumulated milliseconds and sample counts per phase, arrays of
  * PIC_PHASE_COUNT (host memory). */

@@ -299,7 +299,6 @@ void pic_sim_destroy(pic_sim *sim) {
         if (sim->s.ev0[ph]) cudaEventDestroy(sim->s.ev0[ph]);
         if (sim->s.ev1[ph]) cudaEventDestroy(sim->s.ev1[ph]);
     }
-    for (cudaEvent_t ev : sim->s.spmv_ev) cudaEventDestroy(ev);
     if (sim->s.hctl) cudaFreeHost(sim->s.hctl);
     sim->s.hctl = nullptr;
     delete sim;
@@ -459,6 +458,8 @@ int pic_step(pic_sim *sim, int32_t nsteps) {
         int rc = one_step(s, true);
         if (rc) return rc;
         if ((rc = check_status(s))) return rc;
+        s->cg_iters_sum += s->hctl->cg.iters;
+        s->lap_iters_sum += s->hctl->lap.iters;
     }
     return PIC_OK;
 }
@@ -661,6 +662,8 @@ int pic_diagnostics_get(pic_sim *sim, pic_diag *out) {
     out->energy_k = c.diag.energy_k;
     out->status = (double)(c.status | s->host_status);
     out->completion_iters = s->step > 0 ? c.lap.iters : 0;
+    out->cg_iters_sum = (double)s->cg_iters_sum;
+    out->completion_iters_sum = (double)s->lap_iters_sum;
     return PIC_OK;
 }
 

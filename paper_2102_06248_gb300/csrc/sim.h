@@ -41,6 +41,7 @@ struct GridBarrier {
     unsigned int gen;
     int timeout;
     int pad;
+    double val[6];    // results the last arriving block publishes
 };
 
 // Host-visible control block (pinned), refreshed at every synchronising point
@@ -79,7 +80,7 @@ struct SortWork {
 };
 
 // device-time phases of a step (CUDA events on the sim's stream)
-enum Phase { PH_SORT = 0, PH_COEF, PH_PUSH, PH_DEPOSIT, PH_RHS, PH_CG, PH_COMPLETION, PH_FIELD_OTHER, PH_SPMV, PH_COUNT };
+enum Phase { PH_SORT = 0, PH_COEF, PH_PUSH, PH_DEPOSIT, PH_RHS, PH_CG, PH_COMPLETION, PH_FIELD_OTHER, PH_COUNT };
 
 struct Sim {
     const Mesh *mesh = nullptr;
@@ -145,9 +146,9 @@ struct Sim {
     DevBuf<Control> dctl;
     Control *hctl = nullptr;
     DevBuf<double> diag_part;       // per-block partials of the diagnostic reductions
-    int last_cg_iters = 0;          // previous solves' iteration counts (first chunk size)
-    int last_lap_iters = 0;
     int last_push_blocks = 0;       // grid of the last push (kinetic-energy partials)
+    long long cg_iters_sum = 0;     // PCG iterations over all steps (Newmark, completion)
+    long long lap_iters_sum = 0;
     int coop_blocks = -1;           // co-resident blocks of the persistent PCG (0: unavailable)
     uint32_t host_status = 0;       // latched errors seen on the host
     // optional phase profiler
@@ -156,8 +157,6 @@ struct Sim {
     bool ev_used[PH_COUNT] = {};
     double prof_ms[PH_COUNT] = {};
     long long prof_n[PH_COUNT] = {};
-    std::vector<cudaEvent_t> spmv_ev;   // pairs around each Newmark SpMV launch
-    int spmv_used = 0;
 };
 
 void prof_begin(Sim *s, int ph);

@@ -215,99 +215,8 @@ __global__ void __launch_bounds__(kThreads) k_gc_w_sell(int n, int n_slices, con
 }
 
 // r = b - A x, z = D^-1 r, p = z; rz, rr, bb, max|r|
-__global__ void __launch_bounds__(kThreads) k_cg_init_sell(int n, int n_slices, const int *__restrict__ sp,
-                                                           const int *__restrict__ sw, const int *__restrict__ col,
-                                                           const double *__restrict__ Av, const double *__restrict__ Dinv,
-                                                           const double *__restrict__ b, const double *__restrict__ x,
-                                                           double *__restrict__ r_, double *__restrict__ z,
-                                                           double *__restrict__ p, double *part, CgState *st) {
-    __shared__ double sh[4 * kThreads / 32];
-    double acc[3] = {0.0, 0.0, 0.0};
-    double amax[1] = {0.0};
-    SELL_LOOP(n_slices, n)
-        double s = 0.0;
-#pragma unroll 4
-        for (int j = 0; j < kw; j++) {
-            const int k = kb + 32 * j;
-            s += Av[k] * x[col[k]];
-        }
-        if (rv) {
-            const double ri = b[r] - s, zi = Dinv[r] * ri;
-            r_[r] = ri;
-            z[r] = zi;
-            p[r] = zi;
-            acc[0] += ri * zi;
-            acc[1] += ri * ri;
-            acc[2] += b[r] * b[r];
-            amax[0] = fmax(amax[0], fabs(ri));
-        }
-    }
-    block_sum<3>(acc, sh);
-    block_max<1>(amax, sh + 3 * kThreads / 32);
-    double both[4] = {acc[0], acc[1], acc[2], amax[0]};
-    if (arrive<4>(both, part, &st->count_a)) {
-        double tot[3], mx[1];
-        grid_combine<3, false>(tot, part, sh);
-        grid_combine<1, true>(mx, part + 3 * gridDim.x, sh + 3 * kThreads / 32);
-        if (threadIdx.x == 0) {
-            st->rz = tot[0];
-            st->rr = tot[1];
-            st->bb = tot[2];
-            st->iters = 0;
-            st->failed = 0;
-            st->beta = 0.0;
-            st->done = (tot[2] == 0.0) || (tot[1] <= st->tol2 * tot[2]) || (mx[0] <= st->abs_inf);
-            st->count_a = 0;
-        }
-    }
-}
-
 // p = z + beta p_old (on the fly for the neighbours), q = A p, pq: the SpMV
 // of the Newmark PCG
-__global__ void __launch_bounds__(kThreads) k_cg_a_sell(int n, int n_slices, const int *__restrict__ sp,
-                                                        const int *__restrict__ sw, const int *__restrict__ col,
-                                                        const double *__restrict__ Av, const double *__restrict__ z,
-                                                        const double *__restrict__ pold, double *__restrict__ pnew,
-                                                        double *__restrict__ q, double *part, CgState *st) {
-    __shared__ double sh[kThreads / 32];
-    if (st->done) return;
-    const bool first = st->iters == 0;
-    const double beta = st->beta;
-    double acc[1] = {0.0};
-    SELL_LOOP(n_slices, n)
-        double s = 0.0;
-        if (first) {
-#pragma unroll 4
-            for (int j = 0; j < kw; j++) {
-                const int k = kb + 32 * j;
-                s += Av[k] * z[col[k]];
-            }
-        } else {
-#pragma unroll 4
-            for (int j = 0; j < kw; j++) {
-                const int k = kb + 32 * j;
-                const int c = col[k];
-                s += Av[k] * (z[c] + beta * pold[c]);
-            }
-        }
-        if (rv) {
-            const double pi = first ? z[r] : z[r] + beta * pold[r];
-            pnew[r] = pi;
-            q[r] = s;
-            acc[0] += pi * s;
-        }
-    }
-    block_sum<1>(acc, sh);
-    if (arrive<1>(acc, part, &st->count_a)) {
-        double tot[1];
-        grid_combine<1, false>(tot, part, sh);
-        if (threadIdx.x == 0) {
-            st->alpha = st->rz / tot[0];
-            st->count_a = 0;
-        }
-    }
-}
-
 // true residual and M x on the Newmark pattern: relres, energy_e
 __global__ void __launch_bounds__(kThreads) k_resid_sell(int n, int n_slices, const int *__restrict__ sp,
                                                          const int *__restrict__ sw, const int *__restrict__ col,
@@ -689,13 +598,30 @@ __global__ void __launch_bounds__(kThreads) k_max_abs_sum(int n, const double *_
 }
 
 // ---------------------------------------------------------------------------
-// Persistent Jacobi-PCG for the small CSR systems (the node Laplacian of the
-// gradient completion and of the start-up solve): one cooperative launch runs
-// every iteration with two grid barriers per iteration.  Every block reduces
-// the per-block partials in the same fixed order, so all blocks take the same
-// decisions and the result is deterministic.  Vectors written by other blocks
-// inside the launch are read through L2 (__ldcg).  The barrier spins with a
-// bound: past it the kernel records a timeout and every block leaves.
+// Persistent Jacobi-PCG on a SELL-32 matrix (the Newmark operator A = M +
+// dt^2/4 K on interior edges, and the node Laplacian G^T M G of the gradient
+// completion and of the start-up solve).  One cooperative launch runs the whole
+// solve.
+//
+// Sec. III leaves the linear solver open; this one is shaped by the FP64 rate
+// of the part it runs on, which is far below its memory and FP32 rates, so the
+// iteration is arranged to issue as few FP64 instructions as possible:
+//  * the Chronopoulos-Gear recurrence of PCG: the SpMV acts on the
+//    preconditioned residual u = D^-1 r alone (w = A u, one multiply-add per
+//    stored entry), and the search direction's image s = A p follows from
+//    s = w + beta s, so one global reduction per iteration yields
+//    gamma = (r,u), delta = (w,u) and (r,r), from which
+//    beta = gamma'/gamma and alpha = gamma'/(delta - beta gamma'/alpha);
+//  * each block reduces its threads' values through shared memory (one warp
+//    per quantity) and only the last block to arrive at the grid barrier
+//    combines the blocks' partials, in a fixed order, and publishes the
+//    result; max|r| travels as the bit pattern of a nonnegative double, whose
+//    integer order is its numeric order, so it costs no FP64 instruction.
+// Every thread owns the same rows (row 32*slice + lane of its warp's slices)
+// in the vector phase and in the SpMV, so a thread reads back only what it
+// wrote itself, except the gathered u, which is read through L2 (__ldcg).
+// Every grid barrier spins with a bound: past it the kernel records a timeout
+// and every block leaves.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool grid_barrier(GridBarrier *gb) {
     __shared__ int ok;
@@ -729,187 +655,249 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier *gb) {
     return ok != 0;
 }
 
-// fixed-order combination over the blocks' partials, broadcast to the block:
-// NS sums (arrays part + c*G, c < NS) and NM maxima (the next NM arrays)
-template <int NS, int NM>
-__device__ __forceinline__ void all_blocks_combine(const double *part, double *sh, double *bcast, double out[NS + NM]) {
-    const int G = gridDim.x;
-    double vs[NS > 0 ? NS : 1], vm[NM > 0 ? NM : 1];
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// Block reduction of NS sums and one maximum (as bits) into this block's
+// partials: part[c*G + block] for c < NS, the maximum at part[NS*G + block].
+template <int NS>
+__device__ __forceinline__ void block_partials(const double v[NS], unsigned long long mx, double *shv,
+                                               unsigned long long *shm, double *part) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, G = gridDim.x;
 #pragma unroll
-    for (int c = 0; c < NS; c++) vs[c] = 0.0;
+    for (int c = 0; c < NS; c++) shv[c * kThreads + threadIdx.x] = v[c];
+    shm[threadIdx.x] = mx;
+    __syncthreads();
+    if (warp < NS) {
+        double s = shv[warp * kThreads + lane];
 #pragma unroll
-    for (int c = 0; c < NM; c++) vm[c] = 0.0;
-    for (int b = threadIdx.x; b < G; b += kThreads) {
+        for (int k = 1; k < kThreads / 32; k++) s += shv[warp * kThreads + lane + 32 * k];
 #pragma unroll
-        for (int c = 0; c < NS; c++) vs[c] += __ldcg(part + c * G + b);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+        if (lane == 0) part[warp * G + blockIdx.x] = s;
+    } else if (warp == NS) {
+        unsigned long long m = shm[lane];
 #pragma unroll
-        for (int c = 0; c < NM; c++) vm[c] = fmax(vm[c], __ldcg(part + (NS + c) * G + b));
+        for (int k = 1; k < kThreads / 32; k++) m = max(m, shm[lane + 32 * k]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xFFFFFFFFu, m, o));
+        if (lane == 0) reinterpret_cast<unsigned long long *>(part)[NS * G + blockIdx.x] = m;
     }
-    if constexpr (NS > 0) block_sum<NS>(vs, sh);
-    if constexpr (NM > 0) block_max<NM>(vm, sh);
+}
+
+// Grid barrier whose last arriving block combines the partials written by
+// block_partials<NS> (sums in block order, then a shuffle tree: the same
+// order whichever block is last) and publishes them in gb->val before it
+// opens the barrier.  out[0..NS) are the sums, out[NS] the maximum.
+template <int NS>
+__device__ __forceinline__ bool grid_reduce(GridBarrier *gb, const double *part, double out[NS + 1]) {
+    __shared__ int role;   // 1: last block, 0: waits, -1: timed out
+    __shared__ double res[NS + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, G = gridDim.x;
+    unsigned int g = 0;
+    __syncthreads();
     if (threadIdx.x == 0) {
-#pragma unroll
-        for (int c = 0; c < NS; c++) bcast[c] = vs[c];
-#pragma unroll
-        for (int c = 0; c < NM; c++) bcast[NS + c] = vm[c];
+        volatile unsigned int *vgen = &gb->gen;
+        volatile int *vto = &gb->timeout;
+        role = -1;
+        if (*vto == 0) {
+            g = *vgen;
+            __threadfence();
+            role = atomicAdd(&gb->count, 1u) == (unsigned)G - 1 ? 1 : 0;
+        }
     }
     __syncthreads();
+    if (role == 1) {
+        __threadfence();
+        if (warp < NS) {
+            double s = 0.0;
+            for (int b = lane; b < G; b += 32) s += __ldcg(part + warp * G + b);
 #pragma unroll
-    for (int c = 0; c < NS + NM; c++) out[c] = bcast[c];
-    __syncthreads();
-}
-
-// SELL-32 row of the node Laplacian: sum_j L_rj v_j (v read through L2)
-__device__ __forceinline__ double sell_row_dot(int kb, int kw, const int *__restrict__ col,
-                                               const double *__restrict__ val, const double *v) {
-    double s = 0.0;
-#pragma unroll 4
-    for (int j = 0; j < kw; j++) {
-        const int k = kb + 32 * j;
-        s += val[k] * __ldcg(v + col[k]);
-    }
-    return s;
-}
-
-__global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(int n, int n_slices, const int *__restrict__ sp,
-                                                                const int *__restrict__ sw, const int *__restrict__ col,
-                                                                const double *__restrict__ Av,
-                                                                const double *__restrict__ Dinv,
-                                                                const double *__restrict__ b, double *x, double *r,
-                                                                double *z, double *p0, double *p1, double *q,
-                                                                double *part, CgState *st, GridBarrier *gb,
-                                                                const double *abs_src, double abs_factor,
-                                                                uint32_t *status) {
-    __shared__ double sh[3 * kThreads / 32];
-    __shared__ double bc[4];
-    const int G = gridDim.x;
-    const int lane = threadIdx.x & 31;
-    const int max_iters = st->max_iters;
-    double abs_inf = st->abs_inf;
-    double tol2 = st->tol2;
-    if (abs_src) {
-        const double qv = *abs_src;
-        if (qv > 0.0) abs_inf = abs_factor * qv;
-        else tol2 = st->fallback_tol2;
-    }
-    // ---- r = b - A x, z = D^-1 r ----
-    {
-        double v[3] = {0.0, 0.0, 0.0}, vm[1] = {0.0};
-        for (int sl = blockIdx.x * kSlicesPerBlock + (threadIdx.x >> 5); sl < n_slices; sl += G * kSlicesPerBlock) {
-            const int i = sl * 32 + lane;
-            const double s = sell_row_dot(sp[sl] + lane, sw[sl], col, Av, x);
-            if (i < n) {
-                const double ri = b[i] - s, zi = Dinv[i] * ri;
-                r[i] = ri;
-                z[i] = zi;
-                v[0] += ri * zi;
-                v[1] += ri * ri;
-                v[2] += b[i] * b[i];
-                vm[0] = fmax(vm[0], fabs(ri));
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+            if (lane == 0) {
+                res[warp] = s;
+                gb->val[warp] = s;
+            }
+        } else if (warp == NS) {
+            const unsigned long long *pm = reinterpret_cast<const unsigned long long *>(part) + NS * G;
+            unsigned long long m = 0;
+            for (int b = lane; b < G; b += 32) m = max(m, __ldcg(pm + b));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xFFFFFFFFu, m, o));
+            if (lane == 0) {
+                res[NS] = __longlong_as_double((long long)m);
+                gb->val[NS] = res[NS];
             }
         }
-        block_sum<3>(v, sh);
-        block_max<1>(vm, sh);
+        __syncthreads();
         if (threadIdx.x == 0) {
-            part[blockIdx.x] = v[0];
-            part[G + blockIdx.x] = v[1];
-            part[2 * G + blockIdx.x] = v[2];
-            part[3 * G + blockIdx.x] = vm[0];
+            gb->count = 0;
+            __threadfence();
+            atomicAdd(&gb->gen, 1u);
+        }
+    } else if (role == 0 && threadIdx.x == 0) {
+        volatile unsigned int *vgen = &gb->gen;
+        volatile int *vto = &gb->timeout;
+        long spins = 0;
+        while (*vgen == g) {
+            if (++spins > (1L << 26) || *vto != 0) {
+                atomicExch(&gb->timeout, 1);
+                role = -1;
+                break;
+            }
+        }
+        if (role == 0) {
+            __threadfence();
+#pragma unroll
+            for (int c = 0; c <= NS; c++) res[c] = __ldcg(&gb->val[c]);
         }
     }
-    if (!grid_barrier(gb)) goto timeout;
+    __syncthreads();
+    if (role < 0) return false;
+#pragma unroll
+    for (int c = 0; c <= NS; c++) out[c] = res[c];
+    return true;
+}
+
+struct PcgArgs {
+    int n, n_slices;
+    const int *sp, *sw, *col;     // SELL-32: slice offsets, widths, column indices
+    const double *Av, *Dinv, *b;
+    double *x, *r, *u, *w, *p, *s;
+    double *part;                 // >= 5 * gridDim.x partials
+    CgState *st;
+    GridBarrier *gb;
+    const double *abs_src;        // device scalar, or NULL (see CgState::abs_inf)
+    double abs_factor;
+    uint32_t *status;
+    int x_zero;                   // the initial guess is 0 (x is written, not read)
+};
+
+__global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(const PcgArgs a) {
+    __shared__ double shv[4 * kThreads];
+    __shared__ unsigned long long shm[kThreads];
+    const int n = a.n, lane = threadIdx.x & 31;
+    const int sl0 = blockIdx.x * kSlicesPerBlock + (threadIdx.x >> 5), sls = gridDim.x * kSlicesPerBlock;
+    const int *__restrict__ sp = a.sp;
+    const int *__restrict__ sw = a.sw;
+    const int *__restrict__ col = a.col;
+    const double *__restrict__ Av = a.Av;
+    const double *__restrict__ Dinv = a.Dinv;
+    double *x = a.x, *r = a.r, *u = a.u, *w = a.w, *p = a.p, *s = a.s;
+    CgState *st = a.st;
+    const int max_iters = st->max_iters;
+    double abs_inf = st->abs_inf, tol2 = st->tol2;
+    if (a.abs_src) {
+        const double qv = *a.abs_src;
+        if (qv > 0.0) abs_inf = a.abs_factor * qv;
+        else tol2 = st->fallback_tol2;
+    }
+    double t[5];
+    // ---- r = b - A x, u = D^-1 r; then w = A u ----
     {
-        double t[4];
-        all_blocks_combine<3, 1>(part, sh, bc, t);
-        double rz = t[0], rr = t[1];
-        const double bb = t[2];
-        bool done = (bb == 0.0) || (rr <= tol2 * bb) || (t[3] <= abs_inf);
+        double v[4] = {0.0, 0.0, 0.0, 0.0};   // gamma, rr, delta, bb
+        unsigned long long mx = 0;
+        for (int sl = sl0; sl < a.n_slices; sl += sls) {
+            const int i = sl * 32 + lane;
+            double ax = 0.0;
+            if (!a.x_zero) {
+                const int kb = sp[sl] + lane, kw = sw[sl];
+#pragma unroll 4
+                for (int j = 0; j < kw; j++) ax = fma(Av[kb + 32 * j], x[col[kb + 32 * j]], ax);
+            }
+            if (i < n) {
+                const double bi = a.b[i], ri = bi - ax, ui = Dinv[i] * ri;
+                if (a.x_zero) x[i] = 0.0;
+                r[i] = ri;
+                u[i] = ui;
+                v[0] = fma(ri, ui, v[0]);
+                v[1] = fma(ri, ri, v[1]);
+                v[3] = fma(bi, bi, v[3]);
+                mx = max(mx, abs_bits(ri));
+            }
+        }
+        if (!grid_barrier(a.gb)) goto timeout;
+        for (int sl = sl0; sl < a.n_slices; sl += sls) {
+            const int i = sl * 32 + lane, kb = sp[sl] + lane, kw = sw[sl];
+            double au = 0.0;
+#pragma unroll 4
+            for (int j = 0; j < kw; j++) au = fma(Av[kb + 32 * j], __ldcg(u + col[kb + 32 * j]), au);
+            if (i < n) {
+                w[i] = au;
+                v[2] = fma(au, u[i], v[2]);
+            }
+        }
+        block_partials<4>(v, mx, shv, shm, a.part);
+        if (!grid_reduce<4>(a.gb, a.part, t)) goto timeout;
+    }
+    {
+        double gamma = t[0], rr = t[1];
+        const double bb = t[3];
+        double alpha = t[0] / t[2], beta = 0.0;
+        bool done = (bb == 0.0) || (rr <= tol2 * bb) || (t[4] <= abs_inf);
         if (bb == 0.0)
-            for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += G * kThreads) x[i] = 0.0;
+            for (int sl = sl0; sl < a.n_slices; sl += sls)
+                if (sl * 32 + lane < n) x[sl * 32 + lane] = 0.0;
         int iters = 0;
         bool failed = false;
-        double beta = 0.0;
-        double *pold = p0, *pnew = p1;
-        double *pp = part + 4 * G;   // partials of p.q (the others use part)
         while (!done) {
             if (iters >= max_iters) {
                 failed = true;
                 break;
             }
             const bool first = iters == 0;
-            // ---- p = z + beta p_old, q = A p (p of the neighbours formed on the fly) ----
-            double vpq[1] = {0.0};
-            for (int sl = blockIdx.x * kSlicesPerBlock + (threadIdx.x >> 5); sl < n_slices;
-                 sl += G * kSlicesPerBlock) {
+            // ---- p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r ----
+            double v[3] = {0.0, 0.0, 0.0};   // gamma, rr, delta
+            unsigned long long mx = 0;
+            for (int sl = sl0; sl < a.n_slices; sl += sls) {
                 const int i = sl * 32 + lane;
-                const int kb = sp[sl] + lane, kw = sw[sl];
-                double s = 0.0;
-                if (first) {
-#pragma unroll 4
-                    for (int j = 0; j < kw; j++) {
-                        const int k = kb + 32 * j;
-                        s += Av[k] * __ldcg(z + col[k]);
-                    }
-                } else {
-#pragma unroll 4
-                    for (int j = 0; j < kw; j++) {
-                        const int k = kb + 32 * j;
-                        const int c = col[k];
-                        s += Av[k] * (__ldcg(z + c) + beta * __ldcg(pold + c));
-                    }
-                }
                 if (i < n) {
-                    const double pi = first ? __ldcg(z + i) : __ldcg(z + i) + beta * __ldcg(pold + i);
-                    pnew[i] = pi;
-                    q[i] = s;
-                    vpq[0] += pi * s;
+                    const double ui = u[i], wi = w[i];
+                    const double pi = first ? ui : fma(beta, p[i], ui);
+                    const double si = first ? wi : fma(beta, s[i], wi);
+                    p[i] = pi;
+                    s[i] = si;
+                    x[i] = fma(alpha, pi, x[i]);
+                    const double ri = fma(-alpha, si, r[i]);
+                    const double un = Dinv[i] * ri;
+                    r[i] = ri;
+                    u[i] = un;
+                    v[0] = fma(ri, un, v[0]);
+                    v[1] = fma(ri, ri, v[1]);
+                    mx = max(mx, abs_bits(ri));
                 }
             }
-            block_sum<1>(vpq, sh);
-            if (threadIdx.x == 0) pp[blockIdx.x] = vpq[0];
-            if (!grid_barrier(gb)) goto timeout;
-            double tpq[1];
-            all_blocks_combine<1, 0>(pp, sh, bc, tpq);
-            const double alpha = rz / tpq[0];
-            // ---- x += alpha p, r -= alpha q, z = D^-1 r ----
-            double v2[2] = {0.0, 0.0}, vm[1] = {0.0};
-            for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += G * kThreads) {
-                x[i] = __ldcg(x + i) + alpha * __ldcg(pnew + i);
-                const double ri = __ldcg(r + i) - alpha * __ldcg(q + i);
-                r[i] = ri;
-                const double zi = Dinv[i] * ri;
-                z[i] = zi;
-                v2[0] += ri * zi;
-                v2[1] += ri * ri;
-                vm[0] = fmax(vm[0], fabs(ri));
+            if (!grid_barrier(a.gb)) goto timeout;
+            // ---- w = A u ----
+            for (int sl = sl0; sl < a.n_slices; sl += sls) {
+                const int i = sl * 32 + lane, kb = sp[sl] + lane, kw = sw[sl];
+                double au = 0.0;
+#pragma unroll 4
+                for (int j = 0; j < kw; j++) au = fma(Av[kb + 32 * j], __ldcg(u + col[kb + 32 * j]), au);
+                if (i < n) {
+                    w[i] = au;
+                    v[2] = fma(au, u[i], v[2]);
+                }
             }
-            block_sum<2>(v2, sh);
-            block_max<1>(vm, sh);
-            if (threadIdx.x == 0) {
-                part[blockIdx.x] = v2[0];
-                part[G + blockIdx.x] = v2[1];
-                part[2 * G + blockIdx.x] = vm[0];
-            }
-            if (!grid_barrier(gb)) goto timeout;
-            double t3[3];
-            all_blocks_combine<2, 1>(part, sh, bc, t3);
-            beta = t3[0] / rz;
-            rz = t3[0];
-            rr = t3[1];
+            block_partials<3>(v, mx, shv, shm, a.part);
+            if (!grid_reduce<3>(a.gb, a.part, t)) goto timeout;
             iters++;
-            double *tmp = pold;
-            pold = pnew;
-            pnew = tmp;
-            done = (rr <= tol2 * bb) || (t3[2] <= abs_inf);
+            rr = t[1];
+            done = (rr <= tol2 * bb) || (t[3] <= abs_inf);
+            const double gnew = t[0];
+            beta = gnew / gamma;
+            alpha = gnew / (t[2] - beta * gnew / alpha);
+            gamma = gnew;
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             st->iters = iters;
             st->rr = rr;
-            st->rz = rz;
+            st->rz = gamma;
             st->bb = bb;
             st->done = 1;
             st->failed = failed ? 1 : 0;
-            if (failed) atomicOr(status, (uint32_t)ST_CG_NO_CONV);
+            if (failed) atomicOr(a.status, (uint32_t)ST_CG_NO_CONV);
         }
         return;
     }
@@ -917,7 +905,7 @@ timeout:
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         st->done = 1;
         st->failed = 1;
-        atomicOr(status, (uint32_t)ST_BARRIER);
+        atomicOr(a.status, (uint32_t)ST_BARRIER);
     }
 }
 
@@ -938,87 +926,6 @@ __global__ void k_axpby(int n, double a, const double *__restrict__ x, double b,
                         double *__restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = a * x[i] + b * y[i];
-}
-
-// Generic PCG driver: the host checks the device flag after each chunk.
-struct CgProblem {
-    int n;
-    const int *rp, *col;
-    const double *Av, *Dinv;
-    const double *b;
-    double *x, *r, *z, *p0, *p1, *q, *part;
-    CgState *st;        // device
-    CgState *hst;       // host mirror inside the pinned control block
-    bool timed = false; // time each SpMV launch (profiler)
-    const double *abs_src = nullptr;  // device scalar: stop also when max|r| <= abs_factor * (*abs_src)
-    double abs_factor = 0.0;
-    double fallback_tol = 0.0;        // relative tolerance used when *abs_src is 0
-    const int *sp = nullptr, *sw = nullptr;   // SELL-32 slices (Newmark matrix) instead of CSR
-    int n_slices = 0;
-};
-
-int run_pcg(Sim *s, CgProblem &P, double tol, int max_iters, int *last_iters) {
-    cudaStream_t st = s->stream;
-    CgState init{};
-    init.tol2 = tol * tol;
-    init.max_iters = max_iters;
-    init.abs_inf = -1.0;
-    init.fallback_tol2 = P.fallback_tol * P.fallback_tol;
-    FP_CUDA(cudaMemcpyAsync(P.st, &init, sizeof(CgState), cudaMemcpyHostToDevice, st));
-    const int gr = P.sp ? grid_for_slices(P.n_slices) : grid_for_rows(P.n), ge = grid_for_elems(P.n);
-    if (P.sp) { k_cg_init_sell<<<gr, kThreads, 0, st>>>(P.n, P.n_slices, P.sp, P.sw, P.col, P.Av, P.Dinv, P.b, P.x, P.r, P.z, P.p0, P.part, P.st); note_launch(); }
-    else { k_cg_init<<<gr, kThreads, 0, st>>>(P.n, P.rp, P.col, P.Av, P.Dinv, P.b, P.x, P.r, P.z, P.p0, P.part, P.st, P.abs_src, P.abs_factor); note_launch(); }
-    { k_cg_zero_if_trivial<<<ge, kThreads, 0, st>>>(P.n, P.x, P.st); note_launch(); }
-    FP_CUDA(cudaGetLastError());
-    int launched = 0;
-    int chunk = std::max(1, *last_iters - 1);
-    double *pold = P.p0, *pnew = P.p1;
-    for (;;) {
-        for (int c = 0; c < chunk; c++) {
-            const bool timed = P.timed && s->profile;
-            if (timed) {
-                if ((size_t)(2 * s->spmv_used + 2) > s->spmv_ev.size()) {
-                    cudaEvent_t a, b;
-                    cudaEventCreate(&a);
-                    cudaEventCreate(&b);
-                    s->spmv_ev.push_back(a);
-                    s->spmv_ev.push_back(b);
-                }
-                cudaEventRecord(s->spmv_ev[2 * s->spmv_used], st);
-            }
-            if (P.sp) { k_cg_a_sell<<<gr, kThreads, 0, st>>>(P.n, P.n_slices, P.sp, P.sw, P.col, P.Av, P.z, pold, pnew, P.q, P.part, P.st); note_launch(); }
-            else { k_cg_a_csr<<<gr, kThreads, 0, st>>>(P.n, P.rp, P.col, P.Av, P.z, pold, pnew, P.q, P.part, P.st); note_launch(); }
-            if (timed) cudaEventRecord(s->spmv_ev[2 * s->spmv_used++ + 1], st);
-            { k_cg_b<<<ge, kThreads, 0, st>>>(P.n, P.Dinv, P.x, P.r, P.z, pnew, P.q, P.part + 3 * kMaxBlocks, P.st); note_launch(); }
-            std::swap(pold, pnew);
-            launched++;
-        }
-        FP_CUDA(cudaGetLastError());
-        FP_CUDA(cudaMemcpyAsync(P.hst, P.st, sizeof(CgState), cudaMemcpyDeviceToHost, st));
-        FP_CUDA(cudaStreamSynchronize(st));
-        if (s->spmv_used) {
-            // SpMV launches that ran past convergence return at once; only the
-            // iterations the solve performed are counted
-            const int ran = std::min(s->spmv_used, std::max(0, P.hst->iters - (launched - s->spmv_used)));
-            for (int k = 0; k < ran; k++) {
-                float ms = 0.f;
-                if (cudaEventElapsedTime(&ms, s->spmv_ev[2 * k], s->spmv_ev[2 * k + 1]) == cudaSuccess) {
-                    s->prof_ms[PH_SPMV] += ms;
-                    s->prof_n[PH_SPMV] += 1;
-                }
-            }
-            s->spmv_used = 0;
-        }
-        if (P.hst->done) break;
-        chunk = std::max(2, std::min(s->cfg.cg_check_every, P.hst->iters / 8 + 2));
-        if (launched > max_iters + 64) break;
-    }
-    *last_iters = P.hst->iters;
-    if (P.hst->failed || !P.hst->done) {
-        set_error("PCG did not reach the tolerance within " + std::to_string(max_iters) + " iterations");
-        return PIC_ERR_CG_NO_CONVERGENCE;
-    }
-    return PIC_OK;
 }
 
 }  // namespace
@@ -1087,34 +994,6 @@ int newmark_rhs(Sim *s) {
     return PIC_OK;
 }
 
-int pcg_newmark(Sim *s) {
-    const Mesh *m = s->mesh;
-    if (m->n_int_edges == 0) return PIC_OK;
-    CgProblem P;
-    P.n = m->n_int_edges;
-    P.rp = nullptr;
-    P.col = m->As.col.p;
-    P.sp = m->As.ptr.p;
-    P.sw = m->As.width.p;
-    P.n_slices = m->As.n_slices;
-    P.Av = s->A_val.p;
-    P.Dinv = s->Dinv.p;
-    P.b = s->rhs.p;
-    P.x = s->x.p;
-    P.r = s->cg_r.p;
-    P.z = s->cg_z.p;
-    P.p0 = s->cg_p0.p;
-    P.p1 = s->cg_p1.p;
-    P.q = s->cg_q.p;
-    P.part = s->cg_part.p;
-    P.st = &s->dctl.p->cg;
-    P.hst = &s->hctl->cg;
-    P.timed = true;
-    int rc = run_pcg(s, P, s->cfg.cg_tol, s->cfg.cg_max_iters, &s->last_cg_iters);
-    if (rc) s->host_status |= ST_CG_NO_CONV;
-    return rc;
-}
-
 // co-resident blocks of the persistent PCG on the current device (0: no
 // cooperative launch)
 static int coop_capacity() {
@@ -1126,59 +1005,78 @@ static int coop_capacity() {
     return per_sm * sms;
 }
 
+// One cooperative launch of the persistent PCG on a SELL-32 system; its
+// iteration count and failures reach the host through the control block at
+// the step's next synchronisation.  st must hold tol2, fallback_tol2,
+// max_iters and abs_inf; the rest of it is written by the kernel.
+static int launch_pcg(Sim *s, const DevSell &A, const double *Av, const double *Dinv, const double *b, double *x,
+                      double *r, double *u, double *w, double *p, double *sv, double *part, CgState *st,
+                      const CgState &init, const double *abs_src, double abs_factor, bool x_zero) {
+    if (s->coop_blocks < 0) s->coop_blocks = coop_capacity();
+    if (s->coop_blocks <= 0) {
+        set_error("the persistent PCG needs a device with cooperative launch");
+        return PIC_ERR_CUDA;
+    }
+    Control *dc = s->dctl.p;
+    PcgArgs a;
+    a.n = A.n_rows;
+    a.n_slices = A.n_slices;
+    a.sp = A.ptr.p;
+    a.sw = A.width.p;
+    a.col = A.col.p;
+    a.Av = Av;
+    a.Dinv = Dinv;
+    a.b = b;
+    a.x = x;
+    a.r = r;
+    a.u = u;
+    a.w = w;
+    a.p = p;
+    a.s = sv;
+    a.part = part;
+    a.st = st;
+    a.gb = &dc->gbar;
+    a.abs_src = abs_src;
+    a.abs_factor = abs_factor;
+    a.status = &dc->status;
+    a.x_zero = x_zero ? 1 : 0;
+    // blocks: all co-resident, at most one slice per warp, and partials for
+    // five quantities per block fit in the 8 * kMaxBlocks buffer
+    const int G = std::max(1, std::min(std::min(s->coop_blocks, kMaxBlocks),
+                                       (A.n_slices + kSlicesPerBlock - 1) / kSlicesPerBlock));
+    FP_CUDA(cudaMemcpyAsync(st, &init, sizeof(CgState), cudaMemcpyHostToDevice, s->stream));
+    FP_CUDA(cudaMemsetAsync(&dc->gbar, 0, sizeof(GridBarrier), s->stream));
+    void *args[] = {&a};
+    FP_CUDA(cudaLaunchCooperativeKernel((const void *)k_pcg_persistent, G, kThreads, args, 0, s->stream));
+    note_launch();
+    return PIC_OK;
+}
+
+int pcg_newmark(Sim *s) {
+    const Mesh *m = s->mesh;
+    if (m->n_int_edges == 0) return PIC_OK;
+    CgState init{};
+    init.tol2 = s->cfg.cg_tol * s->cfg.cg_tol;
+    init.max_iters = s->cfg.cg_max_iters;
+    init.abs_inf = -1.0;
+    return launch_pcg(s, m->As, s->A_val.p, s->Dinv.p, s->rhs.p, s->x.p, s->cg_r.p, s->cg_z.p, s->cg_q.p,
+                      s->cg_p0.p, s->cg_p1.p, s->cg_part.p, &s->dctl.p->cg, init, nullptr, 0.0, false);
+}
+
+// Node-Laplacian solve on interior nodes from x = 0.  Stops at
+// ||r|| <= tol ||b||, or, with abs_src, at max|r| <= abs_factor * (*abs_src)
+// (relative init_tol instead when *abs_src is 0).
 int laplacian_solve(Sim *s, const double *rhs_int, double *x_int, double tol, const double *abs_src,
                     double abs_factor) {
     const Mesh *m = s->mesh;
     if (m->n_int_nodes == 0) return PIC_OK;
-    if (s->coop_blocks < 0) s->coop_blocks = coop_capacity();
-    if (s->coop_blocks > 0) {
-        // one cooperative launch for the whole solve; failures surface through
-        // the status word at the step's next synchronisation
-        int n = m->n_int_nodes;
-        const int G = std::max(1, std::min(std::min(s->coop_blocks, kMaxBlocks / 2),
-                                           (m->Ls.n_slices + kSlicesPerBlock - 1) / kSlicesPerBlock));
-        CgState init{};
-        init.tol2 = tol * tol;
-        init.fallback_tol2 = s->cfg.init_tol * s->cfg.init_tol;
-        init.max_iters = 20000;
-        init.abs_inf = -1.0;
-        Control *dc = s->dctl.p;
-        FP_CUDA(cudaMemcpyAsync(&dc->lap, &init, sizeof(CgState), cudaMemcpyHostToDevice, s->stream));
-        FP_CUDA(cudaMemsetAsync(&dc->gbar, 0, sizeof(GridBarrier), s->stream));
-        int nsl = m->Ls.n_slices;
-        const int *sp = m->Ls.ptr.p, *sw = m->Ls.width.p, *col = m->Ls.col.p;
-        const double *Av = m->Ls_val.p, *Dinv = s->L_Dinv.p, *b = rhs_int;
-        double *x = x_int, *r = s->l_r.p, *z = s->l_z.p, *p0 = s->l_p0.p, *p1 = s->l_p1.p, *q = s->l_q.p;
-        double *part = s->l_part.p;
-        CgState *st = &dc->lap;
-        GridBarrier *gb = &dc->gbar;
-        uint32_t *status = &dc->status;
-        void *args[] = {&n, &nsl, &sp, &sw, &col, &Av, &Dinv, &b, &x, &r, &z, &p0, &p1, &q, &part, &st, &gb,
-                        (void *)&abs_src, &abs_factor, &status};
-        FP_CUDA(cudaLaunchCooperativeKernel((const void *)k_pcg_persistent, G, kThreads, args, 0, s->stream));
-        note_launch();
-        return PIC_OK;
-    }
-    CgProblem P;
-    P.n = m->n_int_nodes;
-    P.rp = m->L.rowptr.p;
-    P.col = m->L.col.p;
-    P.Av = m->L_val.p;
-    P.Dinv = s->L_Dinv.p;
-    P.b = rhs_int;
-    P.x = x_int;
-    P.r = s->l_r.p;
-    P.z = s->l_z.p;
-    P.p0 = s->l_p0.p;
-    P.p1 = s->l_p1.p;
-    P.q = s->l_q.p;
-    P.part = s->l_part.p;
-    P.st = &s->dctl.p->lap;
-    P.hst = &s->hctl->lap;
-    P.abs_src = abs_src;
-    P.abs_factor = abs_factor;
-    P.fallback_tol = s->cfg.init_tol;
-    return run_pcg(s, P, tol, 20000, &s->last_lap_iters);
+    CgState init{};
+    init.tol2 = tol * tol;
+    init.fallback_tol2 = s->cfg.init_tol * s->cfg.init_tol;
+    init.max_iters = 20000;
+    init.abs_inf = -1.0;
+    return launch_pcg(s, m->Ls, m->Ls_val.p, s->L_Dinv.p, rhs_int, x_int, s->l_r.p, s->l_z.p, s->l_q.p, s->l_p0.p,
+                      s->l_p1.p, s->l_part.p, &s->dctl.p->lap, init, abs_src, abs_factor, true);
 }
 
 // Completion of the Newmark solve on the gradient subspace: the part of the
@@ -1195,7 +1093,6 @@ int gradient_completion(Sim *s) {
     { k_gc_w_sell<<<grid_for_slices(m->As.n_slices), kThreads, 0, s->stream>>>(ni, m->As.n_slices, m->As.ptr.p, m->As.width.p, m->As.col.p, m->M_val.p, s->cfg.form, s->e.p, s->e_prev.p, s->x.p, s->g_new.p, s->g.p, s->g_prev.p, s->w_edge.p); note_launch(); }
     { k_gc_d<<<(nin + 255) / 256, 256, 0, s->stream>>>(nin, m->int_node.p, m->n2e.rowptr.p, m->n2e.col.p, m->n2e_sgn.p,
                                                      ni, s->w_edge.p, s->l_b.p); note_launch(); }
-    FP_CUDA(cudaMemsetAsync(s->l_x.p, 0, sizeof(double) * nin, s->stream));
     // stopping threshold: completion_tol * max_n |rho_n + wall_n| (charge at t^{n+1})
     { k_max_abs_sum<<<grid_for_elems(m->n_nodes), kThreads, 0, s->stream>>>(m->n_nodes, s->rho.p, s->wall.p, s->diag_part.p, &s->dctl.p->diag.count, &s->dctl.p->qmax); note_launch(); }
     FP_CUDA(cudaGetLastError());
@@ -1239,8 +1136,7 @@ int init_fields(Sim *s) {
     const int nin = m->n_int_nodes, ni = m->n_int_edges;
     if (nin > 0) {
         { k_node_to_int<<<(nin + 255) / 256, 256, 0, s->stream>>>(nin, m->int_node.p, s->rho.p, s->rho_bg.p, s->l_b.p); note_launch(); }
-        FP_CUDA(cudaMemsetAsync(s->l_x.p, 0, sizeof(double) * nin, s->stream));
-        int rc = laplacian_solve(s, s->l_b.p, s->l_x.p, s->cfg.init_tol, nullptr, 0.0);
+            int rc = laplacian_solve(s, s->l_b.p, s->l_x.p, s->cfg.init_tol, nullptr, 0.0);
         if (rc) return rc;
         FP_CUDA(cudaMemsetAsync(s->phi.p, 0, sizeof(double) * m->n_nodes, s->stream));
         { k_int_to_node<<<(nin + 255) / 256, 256, 0, s->stream>>>(nin, m->int_node.p, s->l_x.p, s->phi.p); note_launch(); }

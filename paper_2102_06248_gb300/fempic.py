@@ -50,7 +50,8 @@ class pic_config(C.Structure):
 class pic_diag(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "step", "continuity_abs", "gauss_abs", "rho_max", "divb_abs", "cg_iters", "cg_relres", "n_alive",
-        "energy_e", "energy_b", "energy_k", "status", "completion_iters")]
+        "energy_e", "energy_b", "energy_k", "status", "completion_iters", "cg_iters_sum",
+        "completion_iters_sum")]
 
 
 _lib = None
@@ -299,7 +300,7 @@ class Sim:
         _check(_lib.pic_diagnostics_get(self._h, C.byref(d)), "pic_diagnostics_get")
         return {n: getattr(d, n) for n, _ in pic_diag._fields_}
 
-    PHASES = ("sort", "coef", "push", "deposit", "rhs", "cg", "completion", "field_other", "spmv")
+    PHASES = ("sort", "coef", "push", "deposit", "rhs", "cg", "completion", "field_other")
 
     def profile(self) -> Dict[str, tuple]:
         ms = np.zeros(len(self.PHASES))
@@ -331,12 +332,12 @@ def launch_count() -> int:
 
 def sim_from_workload(wl, dt: float, precision: str = "plain", cg_tol: float = 1e-10,
                       init_tol: float = 1e-14, mesh: Optional[Mesh] = None, stream=None,
-                      profile: bool = False) -> Sim:
+                      profile: bool = False, cg_max_iters: int = 10000) -> Sim:
     """Builds and initialises a simulation of a ``workloads.Workload``."""
     mesh = mesh or Mesh(wl.mesh.xyz, wl.mesh.tets)
     sim = Sim(mesh, dt, form=wl.form, pusher=wl.pusher, precision=precision, b0=wl.b0,
               rho_background=wl.rho_background, cg_tol=cg_tol, init_tol=init_tol, stream=stream,
-              profile=profile)
+              profile=profile, cg_max_iters=cg_max_iters)
     for k, sp in enumerate(wl.species):
         sim.particles_load(k, sp.q, sp.m, sp.w, sp.x, sp.v, sp.tet)
     sim.init()

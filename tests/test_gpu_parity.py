@@ -245,6 +245,17 @@ def test_error_paths(F):
     with pytest.raises(F.PicError) as ei:
         s2.step()
     assert ei.value.code == 5
+    # a Newmark PCG capped at one iteration reports non-convergence, and the
+    # device stays usable for the next simulation
+    wl = W.thermal_plasma_cube(n_particles=2000, seed=5)
+    m3 = F.Mesh(wl.mesh.xyz, wl.mesh.tets)
+    s3 = F.sim_from_workload(wl, DT_CFL_6, mesh=m3, cg_tol=1e-15, cg_max_iters=1)
+    with pytest.raises(F.PicError) as ei:
+        s3.step()
+    assert ei.value.code == 6
+    s4 = F.sim_from_workload(wl, DT_CFL_6, mesh=m3)
+    s4.step()
+    assert s4.diag()["cg_iters"] > 1
 
 
 # ---------------------------------------------------------------------------
