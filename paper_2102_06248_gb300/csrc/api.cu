@@ -230,7 +230,7 @@ void pic_config_default(pic_config *c) {
     c->init_tol = 1e-14;
     c->completion_tol = 1e-16;
     c->walk_cap = 63;
-    c->cg_check_every = 16;
+    c->solver_blocks_per_sm = 0;
     c->max_species = kMaxSpecies;
 }
 
@@ -243,8 +243,8 @@ int pic_sim_create(const pic_mesh *mesh, const pic_config *cfg, pic_sim **out) {
     if (!(cfg->dt > 0) || (cfg->form != PIC_FORM_WE && cfg->form != PIC_FORM_MFEM) || cfg->pusher < 0 ||
         cfg->pusher > 5 || (cfg->precision != PIC_PRECISION_PLAIN && cfg->precision != PIC_PRECISION_MIXED) ||
         !(cfg->cg_tol > 0) || cfg->cg_max_iters <= 0 || !(cfg->init_tol > 0) || !(cfg->completion_tol > 0) ||
-        cfg->walk_cap <= 0 ||
-        cfg->walk_cap > kMaxWalk || cfg->preconditioner != PIC_PRECOND_JACOBI) {
+        cfg->walk_cap <= 0 || cfg->walk_cap > kMaxWalk || cfg->solver_blocks_per_sm < 0 ||
+        cfg->preconditioner != PIC_PRECOND_JACOBI) {
         set_error("pic_sim_create: invalid configuration (dt > 0, form WE/MFEM, pusher 0..5, precision, tolerances, "
                   "walk_cap 1..63, Jacobi preconditioner)");
         return PIC_ERR_INVALID_ARG;
@@ -261,7 +261,6 @@ int pic_sim_create(const pic_mesh *mesh, const pic_config *cfg, pic_sim **out) {
     Sim *s = &h->s;
     s->mesh = &mesh->m;
     s->cfg = *cfg;
-    if (s->cfg.cg_check_every <= 0) s->cfg.cg_check_every = 16;
     s->stream = (cudaStream_t)cfg->stream;
     s->mixed = cfg->precision == PIC_PRECISION_MIXED;
     s->rsize = s->mixed ? 4 : 8;

@@ -37,11 +37,11 @@ struct DiagDev {
 
 // state of the bounded grid barrier of the persistent kernels
 struct GridBarrier {
-    unsigned int count;
-    unsigned int gen;
+    unsigned int count;   // arrivals since the launch (epoch k completes at k * blocks)
+    unsigned int flag;    // last epoch whose reduction results are published
     int timeout;
     int pad;
-    double val[6];    // results the last arriving block publishes
+    double val[6];        // results the last arriving block publishes
 };
 
 // Host-visible control block (pinned), refreshed at every synchronising point

@@ -620,36 +620,57 @@ __global__ void __launch_bounds__(kThreads) k_max_abs_sum(int n, const double *_
 // Every thread owns the same rows (row 32*slice + lane of its warp's slices)
 // in the vector phase and in the SpMV, so a thread reads back only what it
 // wrote itself, except the gathered u, which is read through L2 (__ldcg).
-// Every grid barrier spins with a bound: past it the kernel records a timeout
-// and every block leaves.
+// The rest is latency work: the slice headers of a block's slices sit in
+// shared memory for the whole solve (the next one is read while the current
+// slice is summed), and the grid barriers are one release-add on a counter
+// that only grows plus acquire-loads.  (An L2 bulk prefetch of the next
+// slice's values and columns made the solve slower: it delays the slowest
+// blocks at the barrier.)  Every barrier spins with a bound: past it the kernel
+// records a timeout and every block leaves.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool grid_barrier(GridBarrier *gb) {
+constexpr int kMaxPcgBlocks = 4 * kThreads;    // largest grid of the persistent PCG
+constexpr int kSmemSlices = 512;               // slice headers a block keeps in shared memory
+constexpr long kSpinLimit = 1L << 22;         // about a second of polling
+
+__device__ __forceinline__ void red_release_add(unsigned int *p, unsigned int v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned int atom_acq_rel_add(unsigned int *p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned int *p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Spins (thread 0) until *p >= target; false when the bound or another
+// block's timeout ends the wait.
+__device__ __forceinline__ bool spin_until(GridBarrier *gb, const unsigned int *p, unsigned int target) {
+    volatile int *vto = &gb->timeout;
+    long spins = 0;
+    while (ld_acquire(p) < target) {
+        if (++spins > kSpinLimit || ((spins & 255) == 0 && *vto != 0)) {
+            atomicExch(&gb->timeout, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Grid barrier number `epoch` (1, 2, ... in every block): the counter reaches
+// epoch * G once every block has arrived.
+__device__ __forceinline__ bool grid_barrier(GridBarrier *gb, unsigned int epoch) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int *vgen = &gb->gen;
-        volatile int *vto = &gb->timeout;
-        int good = (*vto == 0);
-        if (good) {
-            const unsigned int g = *vgen;
-            __threadfence();
-            if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
-                gb->count = 0;
-                __threadfence();
-                atomicAdd(&gb->gen, 1u);
-            } else {
-                long spins = 0;
-                while (*vgen == g) {
-                    if (++spins > (1L << 26) || *vto != 0) {
-                        atomicExch(&gb->timeout, 1);
-                        good = 0;
-                        break;
-                    }
-                }
-            }
-            __threadfence();
-        }
-        ok = good;
+        red_release_add(&gb->count, 1u);
+        ok = spin_until(gb, &gb->count, epoch * gridDim.x);
     }
     __syncthreads();
     return ok != 0;
@@ -659,12 +680,14 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
     return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
 }
 
-// Block reduction of NS sums and one maximum (as bits) into this block's
-// partials: part[c*G + block] for c < NS, the maximum at part[NS*G + block].
-template <int NS>
-__device__ __forceinline__ void block_partials(const double v[NS], unsigned long long mx, double *shv,
-                                               unsigned long long *shm, double *part) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, G = gridDim.x;
+// Block reduction of NS sums and one maximum (kept as bits) in a fixed order:
+// per quantity one warp adds the threads' values in thread order, then a
+// shuffle tree.  out(c, value) runs on lane 0 of warps 0..NS; the caller
+// synchronises before the shared arrays are reused.
+template <int NS, typename Out>
+__device__ __forceinline__ void block_reduce(const double v[NS], unsigned long long mx, double *shv,
+                                             unsigned long long *shm, Out out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int c = 0; c < NS; c++) shv[c * kThreads + threadIdx.x] = v[c];
     shm[threadIdx.x] = mx;
@@ -675,82 +698,64 @@ __device__ __forceinline__ void block_partials(const double v[NS], unsigned long
         for (int k = 1; k < kThreads / 32; k++) s += shv[warp * kThreads + lane + 32 * k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
-        if (lane == 0) part[warp * G + blockIdx.x] = s;
+        if (lane == 0) out(warp, s);
     } else if (warp == NS) {
         unsigned long long m = shm[lane];
 #pragma unroll
         for (int k = 1; k < kThreads / 32; k++) m = max(m, shm[lane + 32 * k]);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xFFFFFFFFu, m, o));
-        if (lane == 0) reinterpret_cast<unsigned long long *>(part)[NS * G + blockIdx.x] = m;
+        if (lane == 0) out(NS, __longlong_as_double((long long)m));
     }
 }
 
-// Grid barrier whose last arriving block combines the partials written by
-// block_partials<NS> (sums in block order, then a shuffle tree: the same
-// order whichever block is last) and publishes them in gb->val before it
-// opens the barrier.  out[0..NS) are the sums, out[NS] the maximum.
+// Grid-wide reduction at barrier number `epoch`: every block leaves its
+// partials (sums in part[c*G + block], c < NS; the maximum's bits in
+// part[NS*G + block]); the last block to arrive combines them in a fixed
+// order (thread t adds blocks t, t + kThreads, ..., all loads issued first,
+// then block_reduce), publishes the results in gb->val and raises gb->flag to
+// epoch.  out[0..NS) are the sums, out[NS] the maximum.
 template <int NS>
-__device__ __forceinline__ bool grid_reduce(GridBarrier *gb, const double *part, double out[NS + 1]) {
+__device__ __forceinline__ bool grid_reduce(GridBarrier *gb, double *part, const double v[NS],
+                                            unsigned long long mx, double *shv, unsigned long long *shm,
+                                            unsigned int epoch, double out[NS + 1]) {
     __shared__ int role;   // 1: last block, 0: waits, -1: timed out
     __shared__ double res[NS + 1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, G = gridDim.x;
-    unsigned int g = 0;
+    const int G = gridDim.x;
+    block_reduce<NS>(v, mx, shv, shm, [&](int c, double val) { part[c * G + blockIdx.x] = val; });
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned int *vgen = &gb->gen;
-        volatile int *vto = &gb->timeout;
-        role = -1;
-        if (*vto == 0) {
-            g = *vgen;
-            __threadfence();
-            role = atomicAdd(&gb->count, 1u) == (unsigned)G - 1 ? 1 : 0;
-        }
+        const unsigned int old = atom_acq_rel_add(&gb->count, 1u);
+        role = (old + 1u == epoch * (unsigned)G) ? 1 : 0;
     }
     __syncthreads();
     if (role == 1) {
-        __threadfence();
-        if (warp < NS) {
-            double s = 0.0;
-            for (int b = lane; b < G; b += 32) s += __ldcg(part + warp * G + b);
+        double w[NS];
+        unsigned long long m = 0;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
-            if (lane == 0) {
-                res[warp] = s;
-                gb->val[warp] = s;
-            }
-        } else if (warp == NS) {
-            const unsigned long long *pm = reinterpret_cast<const unsigned long long *>(part) + NS * G;
-            unsigned long long m = 0;
-            for (int b = lane; b < G; b += 32) m = max(m, __ldcg(pm + b));
+        for (int c = 0; c < NS; c++) w[c] = 0.0;
+        const unsigned long long *pm = reinterpret_cast<const unsigned long long *>(part) + NS * G;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(0xFFFFFFFFu, m, o));
-            if (lane == 0) {
-                res[NS] = __longlong_as_double((long long)m);
-                gb->val[NS] = res[NS];
+        for (int k = 0; k < kMaxPcgBlocks / kThreads; k++) {
+            const int b = threadIdx.x + k * kThreads;
+            if (b < G) {
+#pragma unroll
+                for (int c = 0; c < NS; c++) w[c] += __ldcg(part + c * G + b);
+                m = max(m, __ldcg(pm + b));
             }
         }
+        block_reduce<NS>(w, m, shv, shm, [&](int c, double val) {
+            res[c] = val;
+            gb->val[c] = val;
+        });
         __syncthreads();
-        if (threadIdx.x == 0) {
-            gb->count = 0;
-            __threadfence();
-            atomicAdd(&gb->gen, 1u);
-        }
+        if (threadIdx.x == 0) st_release(&gb->flag, epoch);
     } else if (role == 0 && threadIdx.x == 0) {
-        volatile unsigned int *vgen = &gb->gen;
-        volatile int *vto = &gb->timeout;
-        long spins = 0;
-        while (*vgen == g) {
-            if (++spins > (1L << 26) || *vto != 0) {
-                atomicExch(&gb->timeout, 1);
-                role = -1;
-                break;
-            }
-        }
-        if (role == 0) {
-            __threadfence();
+        if (spin_until(gb, &gb->flag, epoch)) {
 #pragma unroll
             for (int c = 0; c <= NS; c++) res[c] = __ldcg(&gb->val[c]);
+        } else {
+            role = -1;
         }
     }
     __syncthreads();
@@ -758,6 +763,15 @@ __device__ __forceinline__ bool grid_reduce(GridBarrier *gb, const double *part,
 #pragma unroll
     for (int c = 0; c <= NS; c++) out[c] = res[c];
     return true;
+}
+
+// one SELL-32 row: sum_j A_rj v_j, v read through L2
+__device__ __forceinline__ double sell_row(const double *__restrict__ Av, const int *__restrict__ col,
+                                           const double *v, int kb, int kw) {
+    double acc = 0.0;
+#pragma unroll 8
+    for (int j = 0; j < kw; j++) acc = fma(Av[kb + 32 * j], __ldcg(v + col[kb + 32 * j]), acc);
+    return acc;
 }
 
 struct PcgArgs {
@@ -777,15 +791,46 @@ struct PcgArgs {
 __global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(const PcgArgs a) {
     __shared__ double shv[4 * kThreads];
     __shared__ unsigned long long shm[kThreads];
-    const int n = a.n, lane = threadIdx.x & 31;
-    const int sl0 = blockIdx.x * kSlicesPerBlock + (threadIdx.x >> 5), sls = gridDim.x * kSlicesPerBlock;
-    const int *__restrict__ sp = a.sp;
-    const int *__restrict__ sw = a.sw;
-    const int *__restrict__ col = a.col;
+    __shared__ int s_sp[kSmemSlices], s_sw[kSmemSlices];
+    const int n = a.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sl0 = blockIdx.x * kSlicesPerBlock + warp, sls = gridDim.x * kSlicesPerBlock;
     const double *__restrict__ Av = a.Av;
+    const int *__restrict__ col = a.col;
     const double *__restrict__ Dinv = a.Dinv;
     double *x = a.x, *r = a.r, *u = a.u, *w = a.w, *p = a.p, *s = a.s;
     CgState *st = a.st;
+    // the block's slice headers, k-th slice of warp `warp` at k * 8 + warp
+    const bool cached = (long)((a.n_slices + sls - 1) / sls) * kSlicesPerBlock <= kSmemSlices;
+    if (cached)
+        for (int k = 0, sl = sl0; sl < a.n_slices; k++, sl += sls)
+            if (lane == 0) {
+                s_sp[k * kSlicesPerBlock + warp] = a.sp[sl];
+                s_sw[k * kSlicesPerBlock + warp] = a.sw[sl];
+            }
+    __syncwarp();
+    auto slice = [&](int k, int sl, int &off, int &wid) {
+        if (cached) {
+            off = s_sp[k * kSlicesPerBlock + warp];
+            wid = s_sw[k * kSlicesPerBlock + warp];
+        } else {
+            off = a.sp[sl];
+            wid = a.sw[sl];
+        }
+    };
+    // SpMV phase over the warp's slices: out_i = sum_j A_ij v_j, then f(i, out_i)
+    auto spmv = [&](const double *v, auto f) {
+        int off, wid;
+        if (sl0 < a.n_slices) slice(0, sl0, off, wid);
+        for (int k = 0, sl = sl0; sl < a.n_slices; k++, sl += sls) {
+            int noff = 0, nwid = 0;
+            if (sl + sls < a.n_slices) slice(k + 1, sl + sls, noff, nwid);
+            const double acc = sell_row(Av, col, v, off + lane, wid);
+            const int i = sl * 32 + lane;
+            if (i < n) f(i, acc);
+            off = noff;
+            wid = nwid;
+        }
+    };
     const int max_iters = st->max_iters;
     double abs_inf = st->abs_inf, tol2 = st->tol2;
     if (a.abs_src) {
@@ -793,43 +838,34 @@ __global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(const PcgArgs a)
         if (qv > 0.0) abs_inf = a.abs_factor * qv;
         else tol2 = st->fallback_tol2;
     }
+    unsigned int epoch = 0;
     double t[5];
     // ---- r = b - A x, u = D^-1 r; then w = A u ----
     {
         double v[4] = {0.0, 0.0, 0.0, 0.0};   // gamma, rr, delta, bb
         unsigned long long mx = 0;
-        for (int sl = sl0; sl < a.n_slices; sl += sls) {
-            const int i = sl * 32 + lane;
-            double ax = 0.0;
-            if (!a.x_zero) {
-                const int kb = sp[sl] + lane, kw = sw[sl];
-#pragma unroll 4
-                for (int j = 0; j < kw; j++) ax = fma(Av[kb + 32 * j], x[col[kb + 32 * j]], ax);
-            }
-            if (i < n) {
-                const double bi = a.b[i], ri = bi - ax, ui = Dinv[i] * ri;
-                if (a.x_zero) x[i] = 0.0;
-                r[i] = ri;
-                u[i] = ui;
-                v[0] = fma(ri, ui, v[0]);
-                v[1] = fma(ri, ri, v[1]);
-                v[3] = fma(bi, bi, v[3]);
-                mx = max(mx, abs_bits(ri));
-            }
+        auto init_row = [&](int i, double ax) {
+            const double bi = a.b[i], ri = bi - ax, ui = Dinv[i] * ri;
+            if (a.x_zero) x[i] = 0.0;
+            r[i] = ri;
+            u[i] = ui;
+            v[0] = fma(ri, ui, v[0]);
+            v[1] = fma(ri, ri, v[1]);
+            v[3] = fma(bi, bi, v[3]);
+            mx = max(mx, abs_bits(ri));
+        };
+        if (a.x_zero) {
+            for (int sl = sl0; sl < a.n_slices; sl += sls)
+                if (sl * 32 + lane < n) init_row(sl * 32 + lane, 0.0);
+        } else {
+            spmv(x, init_row);
         }
-        if (!grid_barrier(a.gb)) goto timeout;
-        for (int sl = sl0; sl < a.n_slices; sl += sls) {
-            const int i = sl * 32 + lane, kb = sp[sl] + lane, kw = sw[sl];
-            double au = 0.0;
-#pragma unroll 4
-            for (int j = 0; j < kw; j++) au = fma(Av[kb + 32 * j], __ldcg(u + col[kb + 32 * j]), au);
-            if (i < n) {
-                w[i] = au;
-                v[2] = fma(au, u[i], v[2]);
-            }
-        }
-        block_partials<4>(v, mx, shv, shm, a.part);
-        if (!grid_reduce<4>(a.gb, a.part, t)) goto timeout;
+        if (!grid_barrier(a.gb, ++epoch)) goto timeout;
+        spmv(u, [&](int i, double au) {
+            w[i] = au;
+            v[2] = fma(au, u[i], v[2]);
+        });
+        if (!grid_reduce<4>(a.gb, a.part, v, mx, shv, shm, ++epoch, t)) goto timeout;
     }
     {
         double gamma = t[0], rr = t[1];
@@ -868,20 +904,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(const PcgArgs a)
                     mx = max(mx, abs_bits(ri));
                 }
             }
-            if (!grid_barrier(a.gb)) goto timeout;
+            if (!grid_barrier(a.gb, ++epoch)) goto timeout;
             // ---- w = A u ----
-            for (int sl = sl0; sl < a.n_slices; sl += sls) {
-                const int i = sl * 32 + lane, kb = sp[sl] + lane, kw = sw[sl];
-                double au = 0.0;
-#pragma unroll 4
-                for (int j = 0; j < kw; j++) au = fma(Av[kb + 32 * j], __ldcg(u + col[kb + 32 * j]), au);
-                if (i < n) {
-                    w[i] = au;
-                    v[2] = fma(au, u[i], v[2]);
-                }
-            }
-            block_partials<3>(v, mx, shv, shm, a.part);
-            if (!grid_reduce<3>(a.gb, a.part, t)) goto timeout;
+            spmv(u, [&](int i, double au) {
+                w[i] = au;
+                v[2] = fma(au, u[i], v[2]);
+            });
+            if (!grid_reduce<3>(a.gb, a.part, v, mx, shv, shm, ++epoch, t)) goto timeout;
             iters++;
             rr = t[1];
             done = (rr <= tol2 * bb) || (t[3] <= abs_inf);
@@ -996,12 +1025,13 @@ int newmark_rhs(Sim *s) {
 
 // co-resident blocks of the persistent PCG on the current device (0: no
 // cooperative launch)
-static int coop_capacity() {
+static int coop_capacity(int want_per_sm) {
     int dev = 0, sms = 0, coop = 0, per_sm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent, kThreads, 0) != cudaSuccess) return 0;
+    if (want_per_sm > 0) per_sm = std::min(per_sm, want_per_sm);
     return per_sm * sms;
 }
 
@@ -1012,7 +1042,7 @@ static int coop_capacity() {
 static int launch_pcg(Sim *s, const DevSell &A, const double *Av, const double *Dinv, const double *b, double *x,
                       double *r, double *u, double *w, double *p, double *sv, double *part, CgState *st,
                       const CgState &init, const double *abs_src, double abs_factor, bool x_zero) {
-    if (s->coop_blocks < 0) s->coop_blocks = coop_capacity();
+    if (s->coop_blocks < 0) s->coop_blocks = coop_capacity(s->cfg.solver_blocks_per_sm);
     if (s->coop_blocks <= 0) {
         set_error("the persistent PCG needs a device with cooperative launch");
         return PIC_ERR_CUDA;
@@ -1042,7 +1072,7 @@ static int launch_pcg(Sim *s, const DevSell &A, const double *Av, const double *
     a.x_zero = x_zero ? 1 : 0;
     // blocks: all co-resident, at most one slice per warp, and partials for
     // five quantities per block fit in the 8 * kMaxBlocks buffer
-    const int G = std::max(1, std::min(std::min(s->coop_blocks, kMaxBlocks),
+    const int G = std::max(1, std::min(std::min(s->coop_blocks, kMaxPcgBlocks),
                                        (A.n_slices + kSlicesPerBlock - 1) / kSlicesPerBlock));
     FP_CUDA(cudaMemcpyAsync(st, &init, sizeof(CgState), cudaMemcpyHostToDevice, s->stream));
     FP_CUDA(cudaMemsetAsync(&dc->gbar, 0, sizeof(GridBarrier), s->stream));

@@ -43,7 +43,7 @@ class pic_config(C.Structure):
                 ("preconditioner", C.c_int32), ("dt", C.c_double), ("b0", C.c_double * 3),
                 ("rho_background", C.c_double), ("cg_tol", C.c_double), ("cg_max_iters", C.c_int32),
                 ("init_tol", C.c_double), ("completion_tol", C.c_double), ("walk_cap", C.c_int32),
-                ("cg_check_every", C.c_int32),
+                ("solver_blocks_per_sm", C.c_int32),
                 ("max_species", C.c_int32), ("profile", C.c_int32), ("stream", C.c_void_p)]
 
 
@@ -185,7 +185,7 @@ class Sim:
     def __init__(self, mesh: Mesh, dt: float, form: str = "we", pusher: str = "boris",
                  precision: str = "plain", b0: Sequence[float] = (0.0, 0.0, 0.0), rho_background: float = 0.0,
                  cg_tol: float = 1e-10, init_tol: float = 1e-14, cg_max_iters: int = 10000,
-                 walk_cap: int = 63, stream=None, profile: bool = False):
+                 walk_cap: int = 63, stream=None, profile: bool = False, solver_blocks_per_sm: int = 0):
         lib = load()
         self.mesh = mesh
         c = default_config()
@@ -200,6 +200,7 @@ class Sim:
         c.init_tol = init_tol
         c.cg_max_iters = cg_max_iters
         c.walk_cap = walk_cap
+        c.solver_blocks_per_sm = solver_blocks_per_sm
         c.profile = int(profile)
         if stream is not None:
             c.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
@@ -332,12 +333,12 @@ def launch_count() -> int:
 
 def sim_from_workload(wl, dt: float, precision: str = "plain", cg_tol: float = 1e-10,
                       init_tol: float = 1e-14, mesh: Optional[Mesh] = None, stream=None,
-                      profile: bool = False, cg_max_iters: int = 10000) -> Sim:
+                      profile: bool = False, cg_max_iters: int = 10000, solver_blocks_per_sm: int = 0) -> Sim:
     """Builds and initialises a simulation of a ``workloads.Workload``."""
     mesh = mesh or Mesh(wl.mesh.xyz, wl.mesh.tets)
     sim = Sim(mesh, dt, form=wl.form, pusher=wl.pusher, precision=precision, b0=wl.b0,
               rho_background=wl.rho_background, cg_tol=cg_tol, init_tol=init_tol, stream=stream,
-              profile=profile, cg_max_iters=cg_max_iters)
+              profile=profile, cg_max_iters=cg_max_iters, solver_blocks_per_sm=solver_blocks_per_sm)
     for k, sp in enumerate(wl.species):
         sim.particles_load(k, sp.q, sp.m, sp.w, sp.x, sp.v, sp.tet)
     sim.init()
