@@ -72,6 +72,8 @@ extern "C" {
 #define PIC_PRECISION_MIXED 1 /* FP32 particle state, gather and push; FP64 barycentrics, deposit, solve */
 
 #define PIC_PRECOND_JACOBI 0
+#define PIC_PRECOND_GNN 1      /* learned edge preconditioner in a flexible PCG once it has weights
+                                  (pic_gnn_train / pic_gnn_set_weights); Jacobi-PCG before that */
 
 /* fields for pic_field_get / pic_field_set (lengths in brackets) */
 #define PIC_FIELD_E 0        /* e^n        [n_edges], 0 on wall edges */
@@ -143,7 +145,7 @@ typedef struct {
     int32_t form;            /* PIC_FORM_WE or PIC_FORM_MFEM */
     int32_t pusher;          /* PIC_PUSH_BORIS or 1..5 (Adams-Bashforth order) */
     int32_t precision;       /* PIC_PRECISION_PLAIN or PIC_PRECISION_MIXED */
-    int32_t preconditioner;  /* PIC_PRECOND_JACOBI */
+    int32_t preconditioner;  /* PIC_PRECOND_JACOBI or PIC_PRECOND_GNN */
     double dt;               /* time step (s), > 0 */
     double b0[3];            /* uniform external magnetic flux density (T) */
     double rho_background;   /* uniform static charge density (C/m^3) */
@@ -254,6 +256,43 @@ int pic_diagnostics_get(pic_sim *sim, pic_diag *out);
  * PIC_PHASE_COUNT (host memory). */
 int pic_profile_get(pic_sim *sim, double *ms, int64_t *count);
 int pic_profile_reset(pic_sim *sim);
+
+/* ---------------------------------------------------------------------------
+ * Learned preconditioner of the Newmark solve.  The paper has no learned
+ * component: this is a project addition to the CG of the field update
+ * (Sec. III).  A 3-layer message-passing network on the graph of the
+ * interior-edge system A (hidden width 32, bfloat16 weights, FP32 activations)
+ * maps a residual r to z = D^-1 r + rho D^-1/2 y(r), D = diag(A); it is
+ * used by a flexible PCG (Polak-Ribiere) that falls back to Jacobi-PCG when
+ * the network's direction is not a descent direction or progress stalls.
+ * The solve still stops at the same relative residual, and the gradient-
+ * subspace completion follows it, so conservation is unchanged.
+ * ------------------------------------------------------------------------- */
+#define PIC_GNN_PARAMS 6369    /* float32 parameters (layout in the design notes) */
+
+typedef struct {
+    int32_t steps;          /* Adam steps (e.g. 300) */
+    double lr;              /* Adam learning rate (e.g. 1e-3) */
+    int32_t samples;        /* residual samples, 1..16: the residuals of Jacobi-PCG on the last
+                               Newmark system after 0, 1, 2, 4, ... iterations */
+} pic_gnn_train_cfg;
+
+/* Trains the network on residuals of the simulation's last Newmark system
+ * (call after at least one pic_step) with the library's own forward,
+ * backward and Adam kernels.  *final_loss (may be NULL) receives the mean
+ * training loss (z^T A z - 2 z^T r) / (r^T D^-1 r) over the samples.
+ * Synchronises. */
+int pic_gnn_train(pic_sim *sim, const pic_gnn_train_cfg *cfg, double *final_loss);
+/* Current FP32 master weights (host array of PIC_GNN_PARAMS floats). */
+int pic_gnn_get_weights(pic_sim *sim, float *w, int64_t n);
+/* Sets the weights (host array of PIC_GNN_PARAMS floats); marks the network usable. */
+int pic_gnn_set_weights(pic_sim *sim, const float *w, int64_t n);
+/* Applies the network to a residual: r_edges, z_edges are host arrays of
+ * n_edges doubles in canonical edge order (wall edges are ignored / set to 0). */
+int pic_gnn_apply(pic_sim *sim, const double *r_edges, double *z_edges);
+/* Training loss and its gradient for one residual (host arrays; grad holds
+ * PIC_GNN_PARAMS doubles, d loss / d weight at the bfloat16 weights). */
+int pic_gnn_loss_grad(pic_sim *sim, const double *r_edges, double *loss, double *grad);
 
 /* Number of kernels the library has launched in this process. */
 int64_t pic_launch_count(void);

@@ -244,9 +244,9 @@ int pic_sim_create(const pic_mesh *mesh, const pic_config *cfg, pic_sim **out) {
         cfg->pusher > 5 || (cfg->precision != PIC_PRECISION_PLAIN && cfg->precision != PIC_PRECISION_MIXED) ||
         !(cfg->cg_tol > 0) || cfg->cg_max_iters <= 0 || !(cfg->init_tol > 0) || !(cfg->completion_tol > 0) ||
         cfg->walk_cap <= 0 || cfg->walk_cap > kMaxWalk || cfg->solver_blocks_per_sm < 0 ||
-        cfg->preconditioner != PIC_PRECOND_JACOBI) {
+        (cfg->preconditioner != PIC_PRECOND_JACOBI && cfg->preconditioner != PIC_PRECOND_GNN)) {
         set_error("pic_sim_create: invalid configuration (dt > 0, form WE/MFEM, pusher 0..5, precision, tolerances, "
-                  "walk_cap 1..63, Jacobi preconditioner)");
+                  "walk_cap 1..63, Jacobi or GNN preconditioner)");
         return PIC_ERR_INVALID_ARG;
     }
     {
@@ -667,6 +667,105 @@ int pic_diagnostics_get(pic_sim *sim, pic_diag *out) {
 }
 
 int64_t pic_launch_count(void) { return (int64_t)g_launches.load(); }
+
+namespace {
+// interior-edge vector (internal order, device) from a canonical host array, and back
+int gnn_in(Sim *s, const double *r_edges, DevBuf<double> &d) {
+    const Mesh *m = s->mesh;
+    const int n = m->n_int_edges;
+    std::vector<double> h((size_t)std::max(n, 1), 0.0);
+    for (int c = 0; c < m->n_edges; c++) {
+        const int i = m->h_edge_internal[c];
+        if (i < n) h[i] = r_edges[c];
+    }
+    int rc = d.alloc(h.size());
+    if (rc) return rc;
+    FP_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, s->stream));
+    FP_CUDA(cudaStreamSynchronize(s->stream));
+    return PIC_OK;
+}
+int gnn_ready(pic_sim *sim, const char *where) {
+    if (!sim) {
+        set_error(std::string(where) + ": NULL sim");
+        return PIC_ERR_INVALID_ARG;
+    }
+    return gnn_prepare(&sim->s);
+}
+}  // namespace
+
+int pic_gnn_train(pic_sim *sim, const pic_gnn_train_cfg *cfg, double *final_loss) {
+    int rc = gnn_ready(sim, "pic_gnn_train");
+    if (rc) return rc;
+    if (!cfg || cfg->steps < 0 || !(cfg->lr > 0) || cfg->samples < 1 || cfg->samples > 16) {
+        set_error("pic_gnn_train: needs steps >= 0, lr > 0 and 1..16 samples");
+        return PIC_ERR_INVALID_ARG;
+    }
+    if (sim->s.step < 1) {
+        set_error("pic_gnn_train: take at least one step first (the samples come from its Newmark system)");
+        return PIC_ERR_STATE;
+    }
+    rc = gnn_train(&sim->s, cfg, final_loss);
+    if (rc) return rc;
+    FP_CUDA(cudaStreamSynchronize(sim->s.stream));
+    return check_status(&sim->s);
+}
+
+int pic_gnn_get_weights(pic_sim *sim, float *w, int64_t n) {
+    int rc = gnn_ready(sim, "pic_gnn_get_weights");
+    if (rc) return rc;
+    if (!w) {
+        set_error("pic_gnn_get_weights: NULL array");
+        return PIC_ERR_INVALID_ARG;
+    }
+    return gnn_get_weights(&sim->s, w, n);
+}
+
+int pic_gnn_set_weights(pic_sim *sim, const float *w, int64_t n) {
+    int rc = gnn_ready(sim, "pic_gnn_set_weights");
+    if (rc) return rc;
+    if (!w) {
+        set_error("pic_gnn_set_weights: NULL array");
+        return PIC_ERR_INVALID_ARG;
+    }
+    if ((rc = gnn_set_weights(&sim->s, w, n))) return rc;
+    sim->s.gnn.trained = 1;
+    return PIC_OK;
+}
+
+int pic_gnn_apply(pic_sim *sim, const double *r_edges, double *z_edges) {
+    int rc = gnn_ready(sim, "pic_gnn_apply");
+    if (rc) return rc;
+    if (!r_edges || !z_edges) {
+        set_error("pic_gnn_apply: NULL array");
+        return PIC_ERR_INVALID_ARG;
+    }
+    Sim *s = &sim->s;
+    const Mesh *m = s->mesh;
+    const int n = m->n_int_edges;
+    DevBuf<double> dr, dz;
+    if ((rc = gnn_in(s, r_edges, dr)) || (rc = dz.alloc((size_t)std::max(n, 1)))) return rc;
+    if ((rc = gnn_forward(s, dr.p, dz.p))) return rc;
+    std::vector<double> h((size_t)std::max(n, 1));
+    FP_CUDA(cudaMemcpyAsync(h.data(), dz.p, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+    FP_CUDA(cudaStreamSynchronize(s->stream));
+    for (int c = 0; c < m->n_edges; c++) {
+        const int i = m->h_edge_internal[c];
+        z_edges[c] = i < n ? h[i] : 0.0;
+    }
+    return PIC_OK;
+}
+
+int pic_gnn_loss_grad(pic_sim *sim, const double *r_edges, double *loss, double *grad) {
+    int rc = gnn_ready(sim, "pic_gnn_loss_grad");
+    if (rc) return rc;
+    if (!r_edges) {
+        set_error("pic_gnn_loss_grad: NULL residual");
+        return PIC_ERR_INVALID_ARG;
+    }
+    DevBuf<double> dr;
+    if ((rc = gnn_in(&sim->s, r_edges, dr))) return rc;
+    return gnn_loss_grad(&sim->s, dr.p, loss, grad);
+}
 
 int pic_electrostatic_solve_noalloc(const pic_mesh *mesh, const double *rho_nodes, double *phi_nodes, double tol,
                                     void *stream) {

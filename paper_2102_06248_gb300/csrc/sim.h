@@ -57,6 +57,28 @@ struct Control {
     int pad;
 };
 
+// Learned edge preconditioner of the Newmark solve (weights, activations and
+// the vectors of its flexible PCG); allocated on first use
+constexpr int kGnnParams = 6369;
+struct GnnState {
+    int ready = 0;              // buffers allocated, static inputs computed
+    int trained = 0;            // weights trained or set by the caller
+    int fell_back = 0;          // a flexible PCG switched to Jacobi
+    long long adam_t = 0;
+    DevBuf<float> theta, adam_m, adam_v;    // FP32 master weights and Adam moments
+    DevBuf<unsigned short> theta_bf;        // bfloat16 copies used by the kernels
+    DevBuf<double> grad;                    // dL/dtheta
+    DevBuf<float> ahat, feat_a, xin;        // D^-1/2 A D^-1/2 (SELL layout), log d - mean, x
+    DevBuf<double> isd, logd, gy;
+    DevBuf<float> h[4], pre[4], g[4];       // activations, 32 per row
+    DevBuf<float> dh, dh2, tq;              // backward buffers, 32 per row
+    DevBuf<double> part, sc;                // reduction partials and scalars
+    DevBuf<float> wpart;                    // per-block weight-gradient partials
+    DevBuf<int> dst;                        // parameter index of each partial
+    DevBuf<double> samples;                 // training residuals
+    DevBuf<double> r, z, zold, p, q;        // flexible PCG
+};
+
 struct SpeciesParams {
     double qm[kMaxSpecies];   // q/m
     double qw[kMaxSpecies];   // q * weight
@@ -149,6 +171,8 @@ struct Sim {
     int last_push_blocks = 0;       // grid of the last push (kinetic-energy partials)
     long long cg_iters_sum = 0;     // PCG iterations over all steps (Newmark, completion)
     long long lap_iters_sum = 0;
+    GnnState gnn;
+    int gnn_iters = 0;              // iterations of the last flexible PCG (host copy source)
     int coop_blocks = -1;           // co-resident blocks of the persistent PCG (0: unavailable)
     uint32_t host_status = 0;       // latched errors seen on the host
     // optional phase profiler
@@ -183,6 +207,15 @@ int faraday_update(Sim *s);
 int compute_diagnostics(Sim *s);
 int init_fields(Sim *s);
 int read_control(Sim *s);
+int newmark_truncated_residual(Sim *s, int iters, double *r_out);
+// learned preconditioner (gnn.cu)
+int gnn_prepare(Sim *s);
+int gnn_set_weights(Sim *s, const float *w, long long np);
+int gnn_get_weights(Sim *s, float *w, long long np);
+int gnn_forward(Sim *s, const double *r, double *z);
+int gnn_loss_grad(Sim *s, const double *r, double *loss, double *grad_host);
+int gnn_train(Sim *s, const pic_gnn_train_cfg *cfg, double *loss_out);
+int fpcg_newmark(Sim *s, int *iters_out);
 int electrostatic_solve_noalloc(const Mesh *m, const double *rho_nodes, double *phi_nodes, double tol,
                                 cudaStream_t st);
 

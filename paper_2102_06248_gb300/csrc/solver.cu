@@ -786,6 +786,7 @@ struct PcgArgs {
     double abs_factor;
     uint32_t *status;
     int x_zero;                   // the initial guess is 0 (x is written, not read)
+    int quiet;                    // reaching max_iters ends the solve without an error
 };
 
 __global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(const PcgArgs a) {
@@ -926,7 +927,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(const PcgArgs a)
             st->bb = bb;
             st->done = 1;
             st->failed = failed ? 1 : 0;
-            if (failed) atomicOr(a.status, (uint32_t)ST_CG_NO_CONV);
+            if (failed && !a.quiet) atomicOr(a.status, (uint32_t)ST_CG_NO_CONV);
         }
         return;
     }
@@ -1041,7 +1042,8 @@ static int coop_capacity(int want_per_sm) {
 // max_iters and abs_inf; the rest of it is written by the kernel.
 static int launch_pcg(Sim *s, const DevSell &A, const double *Av, const double *Dinv, const double *b, double *x,
                       double *r, double *u, double *w, double *p, double *sv, double *part, CgState *st,
-                      const CgState &init, const double *abs_src, double abs_factor, bool x_zero) {
+                      const CgState &init, const double *abs_src, double abs_factor, bool x_zero,
+                      bool quiet = false) {
     if (s->coop_blocks < 0) s->coop_blocks = coop_capacity(s->cfg.solver_blocks_per_sm);
     if (s->coop_blocks <= 0) {
         set_error("the persistent PCG needs a device with cooperative launch");
@@ -1070,6 +1072,7 @@ static int launch_pcg(Sim *s, const DevSell &A, const double *Av, const double *
     a.abs_factor = abs_factor;
     a.status = &dc->status;
     a.x_zero = x_zero ? 1 : 0;
+    a.quiet = quiet ? 1 : 0;
     // blocks: all co-resident, at most one slice per warp, and partials for
     // five quantities per block fit in the 8 * kMaxBlocks buffer
     const int G = std::max(1, std::min(std::min(s->coop_blocks, kMaxPcgBlocks),
@@ -1085,12 +1088,40 @@ static int launch_pcg(Sim *s, const DevSell &A, const double *Av, const double *
 int pcg_newmark(Sim *s) {
     const Mesh *m = s->mesh;
     if (m->n_int_edges == 0) return PIC_OK;
+    // the learned preconditioner takes over once it has weights; until then
+    // (the steps whose systems it trains on) Jacobi-PCG runs
+    if (s->cfg.preconditioner == PIC_PRECOND_GNN && s->gnn.trained) {
+        int iters = 0, rc = fpcg_newmark(s, &iters);
+        if (rc) return rc;
+        s->gnn_iters = iters;
+        FP_CUDA(cudaMemcpyAsync(&s->dctl.p->cg.iters, &s->gnn_iters, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+        return PIC_OK;
+    }
     CgState init{};
     init.tol2 = s->cfg.cg_tol * s->cfg.cg_tol;
     init.max_iters = s->cfg.cg_max_iters;
     init.abs_inf = -1.0;
     return launch_pcg(s, m->As, s->A_val.p, s->Dinv.p, s->rhs.p, s->x.p, s->cg_r.p, s->cg_z.p, s->cg_q.p,
                       s->cg_p0.p, s->cg_p1.p, s->cg_part.p, &s->dctl.p->cg, init, nullptr, 0.0, false);
+}
+
+// Residual of Jacobi-PCG on the last Newmark system (b = rhs) from x = 0
+// after `iters` iterations, into r_out (device, interior edges); training
+// samples of the learned preconditioner.  Overwrites the solver's scratch
+// vectors and x (which holds no state between steps).
+int newmark_truncated_residual(Sim *s, int iters, double *r_out) {
+    const Mesh *m = s->mesh;
+    const int n = m->n_int_edges;
+    if (n == 0) return PIC_OK;
+    CgState init{};
+    init.tol2 = 0.0;
+    init.max_iters = iters;
+    init.abs_inf = -1.0;
+    int rc = launch_pcg(s, m->As, s->A_val.p, s->Dinv.p, s->rhs.p, s->x.p, s->cg_r.p, s->cg_z.p, s->cg_q.p,
+                        s->cg_p0.p, s->cg_p1.p, s->cg_part.p, &s->dctl.p->cg, init, nullptr, 0.0, true, true);
+    if (rc) return rc;
+    FP_CUDA(cudaMemcpyAsync(r_out, s->cg_r.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
+    return PIC_OK;
 }
 
 // Node-Laplacian solve on interior nodes from x = 0.  Stops at

@@ -47,6 +47,14 @@ class pic_config(C.Structure):
                 ("max_species", C.c_int32), ("profile", C.c_int32), ("stream", C.c_void_p)]
 
 
+class pic_gnn_train_cfg(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("lr", C.c_double), ("samples", C.c_int32)]
+
+
+GNN_PARAMS = 6369
+PRECONDITIONERS = {"jacobi": 0, "gnn": 1}
+
+
 class pic_diag(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "step", "continuity_abs", "gauss_abs", "rho_max", "divb_abs", "cg_iters", "cg_relres", "n_alive",
@@ -97,6 +105,11 @@ def load(build_if_missing: bool = True):
         "pic_profile_reset": ([P], I32),
         "pic_launch_count": ([], I64),
         "pic_electrostatic_solve_noalloc": ([P, C.c_void_p, C.c_void_p, D, C.c_void_p], I32),
+        "pic_gnn_train": ([P, C.POINTER(pic_gnn_train_cfg), dp], I32),
+        "pic_gnn_get_weights": ([P, C.POINTER(C.c_float), I64], I32),
+        "pic_gnn_set_weights": ([P, C.POINTER(C.c_float), I64], I32),
+        "pic_gnn_apply": ([P, dp, dp], I32),
+        "pic_gnn_loss_grad": ([P, dp, dp, dp], I32),
         "pic_last_error": ([], C.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -185,7 +198,8 @@ class Sim:
     def __init__(self, mesh: Mesh, dt: float, form: str = "we", pusher: str = "boris",
                  precision: str = "plain", b0: Sequence[float] = (0.0, 0.0, 0.0), rho_background: float = 0.0,
                  cg_tol: float = 1e-10, init_tol: float = 1e-14, cg_max_iters: int = 10000,
-                 walk_cap: int = 63, stream=None, profile: bool = False, solver_blocks_per_sm: int = 0):
+                 walk_cap: int = 63, stream=None, profile: bool = False, solver_blocks_per_sm: int = 0,
+                 preconditioner: str = "jacobi"):
         lib = load()
         self.mesh = mesh
         c = default_config()
@@ -201,6 +215,7 @@ class Sim:
         c.cg_max_iters = cg_max_iters
         c.walk_cap = walk_cap
         c.solver_blocks_per_sm = solver_blocks_per_sm
+        c.preconditioner = PRECONDITIONERS[preconditioner]
         c.profile = int(profile)
         if stream is not None:
             c.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
@@ -315,6 +330,36 @@ class Sim:
     def synchronize(self):
         _check(_lib.pic_sim_synchronize(self._h), "pic_sim_synchronize")
 
+    # ---- learned preconditioner ----
+    def gnn_train(self, steps: int = 300, lr: float = 1e-3, samples: int = 8) -> float:
+        cfg = pic_gnn_train_cfg(int(steps), float(lr), int(samples))
+        loss = C.c_double(0.0)
+        _check(_lib.pic_gnn_train(self._h, C.byref(cfg), C.byref(loss)), "pic_gnn_train")
+        return float(loss.value)
+
+    def gnn_weights(self) -> np.ndarray:
+        w = np.zeros(GNN_PARAMS, dtype=np.float32)
+        _check(_lib.pic_gnn_get_weights(self._h, _ptr(w, C.c_float), GNN_PARAMS), "pic_gnn_get_weights")
+        return w
+
+    def gnn_set_weights(self, w: np.ndarray):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        _check(_lib.pic_gnn_set_weights(self._h, _ptr(w, C.c_float), w.size), "pic_gnn_set_weights")
+
+    def gnn_apply(self, r_edges: np.ndarray) -> np.ndarray:
+        r = np.ascontiguousarray(r_edges, dtype=np.float64)
+        z = np.zeros_like(r)
+        _check(_lib.pic_gnn_apply(self._h, _ptr(r, C.c_double), _ptr(z, C.c_double)), "pic_gnn_apply")
+        return z
+
+    def gnn_loss_grad(self, r_edges: np.ndarray):
+        r = np.ascontiguousarray(r_edges, dtype=np.float64)
+        loss = C.c_double(0.0)
+        g = np.zeros(GNN_PARAMS)
+        _check(_lib.pic_gnn_loss_grad(self._h, _ptr(r, C.c_double), C.byref(loss), _ptr(g, C.c_double)),
+               "pic_gnn_loss_grad")
+        return float(loss.value), g
+
 
 def electrostatic_solve_noalloc(mesh: Mesh, rho, phi, tol: float = 1e-14, stream=None):
     """pic_electrostatic_solve_noalloc on CUDA tensors rho, phi [n_nodes] (float64).
@@ -333,12 +378,14 @@ def launch_count() -> int:
 
 def sim_from_workload(wl, dt: float, precision: str = "plain", cg_tol: float = 1e-10,
                       init_tol: float = 1e-14, mesh: Optional[Mesh] = None, stream=None,
-                      profile: bool = False, cg_max_iters: int = 10000, solver_blocks_per_sm: int = 0) -> Sim:
+                      profile: bool = False, cg_max_iters: int = 10000, solver_blocks_per_sm: int = 0,
+                      preconditioner: str = "jacobi") -> Sim:
     """Builds and initialises a simulation of a ``workloads.Workload``."""
     mesh = mesh or Mesh(wl.mesh.xyz, wl.mesh.tets)
     sim = Sim(mesh, dt, form=wl.form, pusher=wl.pusher, precision=precision, b0=wl.b0,
               rho_background=wl.rho_background, cg_tol=cg_tol, init_tol=init_tol, stream=stream,
-              profile=profile, cg_max_iters=cg_max_iters, solver_blocks_per_sm=solver_blocks_per_sm)
+              profile=profile, cg_max_iters=cg_max_iters, solver_blocks_per_sm=solver_blocks_per_sm,
+              preconditioner=preconditioner)
     for k, sp in enumerate(wl.species):
         sim.particles_load(k, sp.q, sp.m, sp.w, sp.x, sp.v, sp.tet)
     sim.init()
