@@ -190,6 +190,47 @@ def pcg_iter_flops(n_rows: int, nnz: int) -> float:
     return 2.0 * nnz + 2.0 * 8 * n_rows
 
 
+def batched_leg(F, torch, args):
+    """64 independent thermal runs (cells 8^3..32^3, 1e4..1e6 electrons, log-
+    uniform from a seed), MIXED, stepped as one batch (one stream per run, one
+    persistent launch per solve over all runs, six-step CUDA graphs) and, for
+    comparison, one after another with pic_step.  Host wall clock around
+    calls that synchronise at their end, after a device synchronise."""
+    runs = W.batched_runs(n_runs=args.batch_runs)
+    dt6 = dt_table()["thermal_plasma_cube_6^3"]["dt_cfl_s"]
+    sims = []
+    for wl in runs:
+        cells = round(len(wl.mesh.tets) / 6) ** (1.0 / 3.0)
+        sims.append(F.sim_from_workload(wl, 2.0 * dt6 * 6.0 / round(cells), precision="mixed"))
+    n_part = sum(wl.n_particles for wl in runs)
+    batch = F.Batch(sims)
+    batch.step(7)                      # warm-up: one eager step, tuning, capture, one graph launch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    batch.step(args.batch_steps)
+    t1 = time.perf_counter()
+    info = batch.info()
+    # the same runs one by one (fewer steps: every pic_step synchronises)
+    seq_steps = max(1, args.batch_steps // 5)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    for s in sims:
+        s.step(seq_steps)
+    t3 = time.perf_counter()
+    ps_b = n_part * args.batch_steps / (t1 - t0)
+    ps_s = n_part * seq_steps / (t3 - t2)
+    ok = all(s.diag()["continuity_abs"] <= 1e-12 * max(s.diag()["rho_max"], 1e-300) for s in sims)
+    del batch
+    return {"workload": f"{len(runs)} thermal runs, cells 8^3..32^3, 1e4..1e6 electrons (log-uniform, seed 1005), "
+                        f"MIXED, WE Newmark, Boris, dt = 2xCFL, Jacobi-PCG 1e-10",
+            "particles": n_part, "steps": args.batch_steps, "ms_per_step": 1e3 * (t1 - t0) / args.batch_steps,
+            "value": ps_b, "unit": "particle-steps/s",
+            "one_by_one": {"steps": seq_steps, "ms_per_step": 1e3 * (t3 - t2) / seq_steps, "value": ps_s},
+            "speedup_batched": ps_b / ps_s, "continuity_ok": ok, "timing": "host clock around synchronising calls",
+            "graph": info["graph"], "graph_steps": info["graph_steps"], "graph_launches": info["graph_launches"],
+            "solver_blocks_per_sm": info["solver_blocks_per_sm"], "tune_ms_2_3_4": info["tune_ms"]}
+
+
 def time_gpu(F, wl, dt, precision, steps, warmup, stream, dist, device, torch, profile=True):
     sim = F.sim_from_workload(wl, dt, precision=precision, stream=stream, profile=profile)
     for _ in range(warmup):
@@ -319,6 +360,11 @@ def gpu_arm(args):
                 "traffic": None, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": round(avg_ms, 5),
                 "fp64": fp64}
 
+    # ---- batched runs: 64 uneven thermal runs stepped together vs one by one ----
+    batched = None
+    if not args.skip_batched:
+        batched = batched_leg(F, torch, args)
+
     # ---- CPU baseline: the oracle on a bounded, proportionally scaled sample ----
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -351,6 +397,7 @@ def gpu_arm(args):
                     "what": "particles_load from host arrays + init + K steps + E field and particles read back"},
             "gpu_launches": launches,
             "clocks": clk,
+            "batched": batched,
         }
         print(json.dumps(line))
     if dist is not None:
@@ -423,6 +470,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-plain", action="store_true", help="do not time the plain-FP64 path (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true", help="do not run the end-to-end leg (profiling runs)")
+    ap.add_argument("--skip-batched", action="store_true", help="do not run the batched-runs leg")
+    ap.add_argument("--batch-runs", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=60)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3

@@ -294,6 +294,41 @@ int pic_gnn_apply(pic_sim *sim, const double *r_edges, double *z_edges);
  * PIC_GNN_PARAMS doubles, d loss / d weight at the bfloat16 weights). */
 int pic_gnn_loss_grad(pic_sim *sim, const double *r_edges, double *loss, double *grad);
 
+/* ---------------------------------------------------------------------------
+ * Batches: many independent simulations stepped together (the paper runs
+ * one at a time; this is a throughput service of the library).  Each step
+ * runs the members' particle and field kernels on one stream per member and
+ * each of the step's two solves (Newmark PCG, gradient-subspace completion)
+ * for all members in ONE persistent launch; six consecutive steps (the
+ * period of the buffer rotations) are captured once as a CUDA graph and
+ * replayed.  The solver's blocks per SM are picked by timing candidates on
+ * the batch's own systems (kept per batch shape).  Results are those of
+ * pic_step on each member: bitwise when every member's solve gets the
+ * blocks it would get alone (then the kernels and reduction orders are the
+ * same), otherwise equal to the solve tolerance.
+ * Members: 1..64 initialised simulations on the current device, Jacobi
+ * preconditioner; the mesh and particle arrays stay owned by each member.
+ * ------------------------------------------------------------------------- */
+typedef struct pic_batch pic_batch;
+
+typedef struct {
+    int32_t n_sims;
+    int32_t graph;                /* 1: steps replay a captured graph, 0: not yet, -1: unavailable */
+    int32_t graph_steps;          /* steps per graph launch (6) */
+    int32_t solver_blocks_per_sm; /* chosen by the tuner (0: not tuned yet) */
+    int64_t graph_launches;
+    int64_t eager_steps;          /* steps issued one by one (warm-up, remainders) */
+    double tune_ms[3];            /* tuning solve time at 2, 3, 4 blocks per SM */
+} pic_batch_info_t;
+
+/* Creates a batch over sims[0..n) (the simulations must outlive it). */
+int pic_batch_create(pic_sim *const *sims, int32_t n, pic_batch **out);
+/* Advances every member by nsteps.  Synchronises at the end; device errors
+ * of any member (walk cap, record overflow, solver) are returned then. */
+int pic_batch_step(pic_batch *b, int32_t nsteps);
+int pic_batch_info(const pic_batch *b, pic_batch_info_t *out);
+void pic_batch_destroy(pic_batch *b);
+
 /* Number of kernels the library has launched in this process. */
 int64_t pic_launch_count(void);
 

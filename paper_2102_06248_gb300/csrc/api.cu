@@ -79,6 +79,9 @@ __global__ void k_set_history(int n, long cap, int levels, int np, const int *__
         }
 }
 
+
+}  // namespace
+
 int check_status(Sim *s) {
     const uint32_t st = s->hctl->status | s->host_status;
     if (st & ST_WALK_CAP) {
@@ -104,7 +107,12 @@ int check_status(Sim *s) {
     return PIC_OK;
 }
 
-int one_step(Sim *s, bool fields) {
+// The step in the cycle order of Sec. II.A, in three parts around the two
+// solves so that a batch of simulations can run each solve for all of them
+// in one launch.  Part 1: sort, Whitney coefficients, the fused
+// gather/push/walk/deposit, the deposit's reduction to edges and nodes, and
+// (fields) the Newmark right-hand side.
+int step_particles(Sim *s, bool fields) {
     int rc;
     prof_begin(s, PH_SORT);
     if ((rc = sort_particles(s))) return rc;
@@ -115,23 +123,21 @@ int one_step(Sim *s, bool fields) {
     if ((rc = particle_push(s, 0))) return rc;        // records PH_PUSH and opens PH_DEPOSIT
     if ((rc = reduce_to_entities(s))) return rc;
     prof_end(s, PH_DEPOSIT);
-    if (!fields) {
-        rc = read_control(s);
-        prof_collect(s);
-        return rc;
-    }
+    if (!fields) return PIC_OK;
     prof_begin(s, PH_RHS);
     if ((rc = newmark_rhs(s))) return rc;
     prof_end(s, PH_RHS);
-    prof_begin(s, PH_CG);
-    if ((rc = pcg_newmark(s))) return rc;
-    prof_end(s, PH_CG);
-    prof_begin(s, PH_COMPLETION);
-    if ((rc = gradient_completion(s))) return rc;
+    return PIC_OK;
+}
+
+// Part 3, after the completion's solve: apply the completion, Faraday,
+// rotate the three time levels, diagnostics.
+int step_fields_end(Sim *s) {
+    int rc;
+    if ((rc = gc_finish(s))) return rc;
     prof_end(s, PH_COMPLETION);
     prof_begin(s, PH_FIELD_OTHER);
     if ((rc = faraday_update(s))) return rc;
-    // rotate the three time levels
     std::swap(s->e_prev, s->e);   // e_prev <- e^n
     std::swap(s->e, s->x);        // e <- e^{n+1}, x <- e^{n-1} (overwritten next step)
     std::swap(s->g_prev, s->g);
@@ -141,6 +147,29 @@ int one_step(Sim *s, bool fields) {
     if ((rc = compute_diagnostics(s))) return rc;
     prof_end(s, PH_FIELD_OTHER);
     s->step++;
+    return PIC_OK;
+}
+
+namespace {
+
+int one_step(Sim *s, bool fields) {
+    int rc;
+    if ((rc = step_particles(s, fields))) return rc;
+    if (!fields) {
+        rc = read_control(s);
+        prof_collect(s);
+        return rc;
+    }
+    prof_begin(s, PH_CG);
+    if ((rc = pcg_newmark(s))) return rc;
+    prof_end(s, PH_CG);
+    prof_begin(s, PH_COMPLETION);
+    if ((rc = gc_prepare(s))) return rc;
+    {
+        PcgArgs a = pcg_args_completion(s);
+        if ((rc = launch_pcg_runs(&a, 1, s->cfg.solver_blocks_per_sm, s->stream))) return rc;
+    }
+    if ((rc = step_fields_end(s))) return rc;
     rc = read_control(s);
     prof_collect(s);
     return rc;

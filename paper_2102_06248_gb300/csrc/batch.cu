@@ -1,0 +1,403 @@
+// batch.cu -- many independent simulations stepped together.
+//
+// The paper runs one simulation at a time; small meshes and particle counts
+// leave most of a GB300 idle, and a step of one small run is dozens of short
+// launches.  A batch steps its simulations in lock step:
+//   * the per-simulation kernels of a step (sort, coefficients, push,
+//     deposit reduction, Newmark right-hand side, completion set-up, Faraday,
+//     diagnostics) run on one stream per simulation, forked from and joined
+//     to the batch's stream, so independent runs overlap on the SMs;
+//   * each of the two solves of the step (the Newmark PCG, the gradient-
+//     subspace completion) runs for all simulations in ONE persistent
+//     cooperative launch, the co-resident blocks split between the runs in
+//     proportion to their slices, each run with its own grid barrier;
+//   * nothing in a batched step waits on the host (counts stay on the
+//     device), so six consecutive steps -- the period of the buffer rotations
+//     (three time levels, two particle banks) -- are captured once as a CUDA
+//     graph and replayed;
+//   * the solver's blocks per SM are picked by timing the candidates on the
+//     batch's own systems, and the choice is kept per batch shape.
+#include <map>
+#include <mutex>
+#include <utility>
+#include <vector>
+
+#include "sim.h"
+
+struct pic_batch {
+    std::vector<pic_sim *> sims;
+    cudaStream_t ms = nullptr;                 // the batch's stream
+    std::vector<cudaStream_t> st;              // one per simulation
+    std::vector<void *> saved_stream;
+    std::vector<int> saved_profile;
+    cudaEvent_t fork = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_state = 0;                       // 0 not captured, 1 ready, -1 unavailable
+    int phase = 0;                             // steps since the captured pointer state, mod 6
+    std::vector<long long> step_at;            // each sim's step counter the batch expects
+    std::vector<int> n_total_at;               // particle counts the graph was captured with
+    int blocks_per_sm = 0;
+    double tune_ms[5] = {0, 0, 0, 0, 0};       // time of the tuning solve per blocks/SM (index 2..4)
+    long long graph_launches = 0, eager_steps = 0;
+};
+
+namespace fp {
+namespace {
+
+constexpr int kGraphSteps = 6;   // lcm of the rotation periods (3 field levels, 2 banks)
+
+std::mutex g_tune_mutex;
+std::map<std::pair<int, long long>, int> g_tuned;   // (runs, total rows) -> blocks per SM
+
+int fork_all(pic_batch *b) {
+    FP_CUDA(cudaEventRecord(b->fork, b->ms));
+    for (auto s : b->st) FP_CUDA(cudaStreamWaitEvent(s, b->fork, 0));
+    return PIC_OK;
+}
+
+int join_all(pic_batch *b) {
+    for (size_t k = 0; k < b->st.size(); k++) {
+        FP_CUDA(cudaEventRecord(b->join[k], b->st[k]));
+        FP_CUDA(cudaStreamWaitEvent(b->ms, b->join[k], 0));
+    }
+    return PIC_OK;
+}
+
+// one step of every simulation, nothing waiting on the host
+int batch_step_once(pic_batch *b) {
+    const int n = (int)b->sims.size();
+    std::vector<PcgArgs> runs;
+    int rc;
+    if ((rc = fork_all(b))) return rc;
+    for (auto *ps : b->sims)
+        if ((rc = step_particles(&ps->s, true))) return rc;
+    if ((rc = join_all(b))) return rc;
+    runs.clear();
+    for (auto *ps : b->sims)
+        if (ps->s.mesh->n_int_edges > 0) runs.push_back(pcg_args_newmark(&ps->s));
+    if ((rc = launch_pcg_runs(runs.data(), (int)runs.size(), b->blocks_per_sm, b->ms))) return rc;
+    if ((rc = fork_all(b))) return rc;
+    for (auto *ps : b->sims)
+        if ((rc = gc_prepare(&ps->s))) return rc;
+    if ((rc = join_all(b))) return rc;
+    runs.clear();
+    for (auto *ps : b->sims)
+        if (ps->s.mesh->n_int_edges > 0 && ps->s.mesh->n_int_nodes > 0) runs.push_back(pcg_args_completion(&ps->s));
+    if ((rc = launch_pcg_runs(runs.data(), (int)runs.size(), b->blocks_per_sm, b->ms))) return rc;
+    if ((rc = fork_all(b))) return rc;
+    for (auto *ps : b->sims)
+        if ((rc = step_fields_end(&ps->s))) return rc;
+    if ((rc = join_all(b))) return rc;
+    (void)n;
+    return PIC_OK;
+}
+
+// The solver's blocks per SM for this batch: a fixed-length solve of every
+// run's last Newmark system in one launch, timed for 2, 3 and 4 blocks per
+// SM; the fastest is kept for batches of the same shape.
+int autotune(pic_batch *b) {
+    long long rows = 0;
+    for (auto *ps : b->sims) rows += ps->s.mesh->n_int_edges;
+    const std::pair<int, long long> key((int)b->sims.size(), rows);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            b->blocks_per_sm = it->second;
+            return PIC_OK;
+        }
+    }
+    cudaEvent_t e0, e1;
+    FP_CUDA(cudaEventCreate(&e0));
+    FP_CUDA(cudaEventCreate(&e1));
+    int best = 4;
+    float best_ms = 1e30f;
+    for (int bps = 4; bps >= 2; bps--) {
+        std::vector<PcgArgs> runs;
+        for (auto *ps : b->sims)
+            if (ps->s.mesh->n_int_edges > 0) runs.push_back(pcg_args_truncated(&ps->s, 40));
+        int rc = launch_pcg_runs(runs.data(), (int)runs.size(), bps, b->ms);   // warm-up
+        if (rc) return rc;
+        FP_CUDA(cudaEventRecord(e0, b->ms));
+        if ((rc = launch_pcg_runs(runs.data(), (int)runs.size(), bps, b->ms))) return rc;
+        FP_CUDA(cudaEventRecord(e1, b->ms));
+        FP_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        FP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        b->tune_ms[bps] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = bps;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->blocks_per_sm = best;
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tuned[key] = best;
+    return PIC_OK;
+}
+
+// The buffers a step rotates, to undo a capture that failed part-way (the
+// host-side rotations ran without the kernels).
+struct Rotation {
+    std::vector<std::vector<double *>> f;   // per sim: field buffers in fixed slots
+    std::vector<std::vector<uint32_t *>> k;
+    std::vector<int> cur;
+    std::vector<long long> step;
+};
+
+std::vector<DevBuf<double> *> field_slots(Sim *s) {
+    return {&s->e, &s->e_prev, &s->x, &s->g, &s->g_prev, &s->g_new, &s->b, &s->b_prev, &s->b_new,
+            &s->rho, &s->rho_prev, &s->wall, &s->wall_prev};
+}
+std::vector<DevBuf<uint32_t> *> key_slots(Sim *s) { return {&s->skey, &s->tkey, &s->sval, &s->tval}; }
+
+Rotation snapshot(pic_batch *b) {
+    Rotation r;
+    for (auto *ps : b->sims) {
+        Sim *s = &ps->s;
+        std::vector<double *> f;
+        for (auto *d : field_slots(s)) f.push_back(d->p);
+        std::vector<uint32_t *> k;
+        for (auto *d : key_slots(s)) k.push_back(d->p);
+        r.f.push_back(f);
+        r.k.push_back(k);
+        r.cur.push_back(s->cur);
+        r.step.push_back(s->step);
+    }
+    return r;
+}
+
+template <typename T>
+void restore_slots(std::vector<DevBuf<T> *> slots, const std::vector<T *> &want) {
+    for (size_t i = 0; i < slots.size(); i++)
+        for (size_t j = i; j < slots.size(); j++)
+            if (slots[j]->p == want[i]) {
+                if (j != i) std::swap(*slots[i], *slots[j]);
+                break;
+            }
+}
+
+void restore(pic_batch *b, const Rotation &r) {
+    for (size_t q = 0; q < b->sims.size(); q++) {
+        Sim *s = &b->sims[q]->s;
+        restore_slots(field_slots(s), r.f[q]);
+        restore_slots(key_slots(s), r.k[q]);
+        s->cur = r.cur[q];
+        s->step = r.step[q];
+    }
+}
+
+// Captures kGraphSteps batched steps as one graph (nothing runs); on any
+// failure the host state is put back and the batch keeps stepping eagerly.
+int capture(pic_batch *b) {
+    Rotation before = snapshot(b);
+    cudaError_t e = cudaStreamBeginCapture(b->ms, cudaStreamCaptureModeThreadLocal);
+    int rc = e == cudaSuccess ? PIC_OK : PIC_ERR_CUDA;
+    for (int k = 0; k < kGraphSteps && rc == PIC_OK; k++) rc = batch_step_once(b);
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) {
+        cudaError_t e2 = cudaStreamEndCapture(b->ms, &g);
+        if (e2 != cudaSuccess) rc = PIC_ERR_CUDA;
+    }
+    cudaGetLastError();
+    Rotation after = snapshot(b);
+    restore(b, before);   // the captured steps have not run yet
+    if (rc == PIC_OK && g) {
+        bool same = true;   // the rotations must have come back to where they started
+        for (size_t q = 0; q < b->sims.size(); q++)
+            if (after.f[q] != before.f[q] || after.k[q] != before.k[q] || after.cur[q] != before.cur[q]) same = false;
+        cudaGraphExec_t ex = nullptr;
+        if (same && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+            b->graph = g;
+            b->exec = ex;
+            b->graph_state = 1;
+            b->phase = 0;
+            b->n_total_at.clear();
+            for (auto *ps : b->sims) b->n_total_at.push_back(ps->s.n_total);
+            return PIC_OK;
+        }
+        cudaGetLastError();
+    }
+    if (g) cudaGraphDestroy(g);
+    b->graph_state = -1;
+    return PIC_OK;
+}
+
+void drop_graph(pic_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    if (b->graph_state == 1) b->graph_state = 0;
+}
+
+void leave(pic_batch *b) {
+    for (size_t q = 0; q < b->sims.size(); q++) {
+        Sim *s = &b->sims[q]->s;
+        s->stream = static_cast<cudaStream_t>(b->saved_stream[q]);
+        s->profile = b->saved_profile[q];
+        s->batch_mode = 0;
+    }
+}
+
+}  // namespace
+}  // namespace fp
+
+using namespace fp;
+
+extern "C" {
+
+int pic_batch_create(pic_sim *const *sims, int32_t n, pic_batch **out) {
+    if (!out || !sims || n < 1 || n > kMaxBatchRuns) {
+        set_error("pic_batch_create: needs 1.." + std::to_string(kMaxBatchRuns) + " simulations and an out pointer");
+        return PIC_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    for (int i = 0; i < n; i++) {
+        if (!sims[i] || !sims[i]->s.initialised) {
+            set_error("pic_batch_create: every simulation must exist and be initialised");
+            return PIC_ERR_STATE;
+        }
+        if (sims[i]->s.cfg.preconditioner != PIC_PRECOND_JACOBI) {
+            set_error("pic_batch_create: batched solves use the Jacobi preconditioner");
+            return PIC_ERR_INVALID_ARG;
+        }
+        for (int j = 0; j < i; j++)
+            if (sims[j] == sims[i]) {
+                set_error("pic_batch_create: a simulation appears twice");
+                return PIC_ERR_INVALID_ARG;
+            }
+    }
+    pic_batch *b = new (std::nothrow) pic_batch();
+    if (!b) {
+        set_error("pic_batch_create: out of host memory");
+        return PIC_ERR_OOM;
+    }
+    b->sims.assign(sims, sims + n);
+    cudaError_t e = cudaStreamCreateWithFlags(&b->ms, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    for (int i = 0; i < n && e == cudaSuccess; i++) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        b->st.push_back(s);
+        b->join.push_back(ev);
+    }
+    if (e != cudaSuccess) {
+        pic_batch_destroy(b);
+        return cuda_fail(e, "pic_batch_create");
+    }
+    for (int i = 0; i < n; i++) b->step_at.push_back(sims[i]->s.step);
+    *out = b;
+    return PIC_OK;
+}
+
+void pic_batch_destroy(pic_batch *b) {
+    if (!b) return;
+    if (b->ms) cudaStreamSynchronize(b->ms);
+    drop_graph(b);
+    for (auto s : b->st)
+        if (s) cudaStreamDestroy(s);
+    for (auto ev : b->join)
+        if (ev) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->ms) cudaStreamDestroy(b->ms);
+    delete b;
+}
+
+int pic_batch_step(pic_batch *b, int32_t nsteps) {
+    if (!b || nsteps < 0) {
+        set_error("pic_batch_step: NULL batch or negative step count");
+        return PIC_ERR_INVALID_ARG;
+    }
+    const int n = (int)b->sims.size();
+    // the graph holds pointers and sizes of the state it was captured in:
+    // stepping a member outside the batch, or a changed particle count,
+    // makes it stale
+    for (int q = 0; q < n; q++)
+        if (b->sims[q]->s.step != b->step_at[q]) {
+            drop_graph(b);
+            b->phase = 0;
+        }
+    if (b->graph_state == 1)
+        for (int q = 0; q < n; q++)
+            if (b->sims[q]->s.n_total != b->n_total_at[q]) {
+                drop_graph(b);
+                b->phase = 0;
+            }
+    // enter batch mode: every member on its batch stream, no per-step syncs
+    FP_CUDA(cudaDeviceSynchronize());
+    b->saved_stream.clear();
+    b->saved_profile.clear();
+    for (int q = 0; q < n; q++) {
+        Sim *s = &b->sims[q]->s;
+        b->saved_stream.push_back(s->stream);
+        b->saved_profile.push_back(s->profile);
+        s->stream = b->st[q];
+        s->profile = 0;
+        s->batch_mode = 1;
+    }
+    int rc = PIC_OK;
+    for (int q = 0; q < n && rc == PIC_OK; q++) rc = particles_batch_prepare(&b->sims[q]->s);
+    bool ramp_done = true;
+    for (auto *ps : b->sims)
+        if (ps->s.ab && ps->s.nhist < ps->s.hist_levels) ramp_done = false;
+    int left = nsteps;
+    while (rc == PIC_OK && left > 0) {
+        if (b->graph_state == 1 && b->phase == 0 && left >= kGraphSteps) {
+            cudaError_t e = cudaGraphLaunch(b->exec, b->ms);
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "cudaGraphLaunch");
+                break;
+            }
+            for (auto *ps : b->sims) ps->s.step += kGraphSteps;
+            b->graph_launches++;
+            left -= kGraphSteps;
+            continue;
+        }
+        if (b->graph_state == 0 && left >= kGraphSteps && ramp_done && b->eager_steps > 0) {
+            if (b->blocks_per_sm == 0 && (rc = autotune(b))) break;
+            if ((rc = capture(b))) break;
+            continue;
+        }
+        rc = batch_step_once(b);
+        if (rc) break;
+        b->eager_steps++;
+        b->phase = (b->phase + 1) % kGraphSteps;
+        left--;
+    }
+    cudaError_t e = cudaStreamSynchronize(b->ms);
+    if (rc == PIC_OK && e != cudaSuccess) rc = cuda_fail(e, "pic_batch_step");
+    for (int q = 0; q < n && rc == PIC_OK; q++) {
+        Sim *s = &b->sims[q]->s;
+        if ((rc = read_control(s))) break;
+        // the step on its own sorts exactly the entries the last push wrote
+        s->n_total = s->hctl->n_sorted;
+        rc = check_status(s);
+        b->step_at[q] = s->step;
+    }
+    leave(b);
+    return rc;
+}
+
+int pic_batch_info(const pic_batch *b, pic_batch_info_t *out) {
+    if (!b || !out) {
+        set_error("pic_batch_info: NULL argument");
+        return PIC_ERR_INVALID_ARG;
+    }
+    out->n_sims = (int32_t)b->sims.size();
+    out->graph = b->graph_state;
+    out->graph_steps = kGraphSteps;
+    out->solver_blocks_per_sm = b->blocks_per_sm;
+    out->graph_launches = b->graph_launches;
+    out->eager_steps = b->eager_steps;
+    for (int i = 0; i < 3; i++) out->tune_ms[i] = b->tune_ms[i + 2];
+    return PIC_OK;
+}
+
+}  // extern "C"

@@ -1196,6 +1196,7 @@ int upload_particles(Sim *s) {
     s->cur = 0;
     s->hctl->n_alive = n;
     FP_CUDA(cudaMemcpyAsync(&s->dctl.p->n_alive, &n, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    FP_CUDA(cudaMemcpyAsync(&s->dctl.p->n_sorted, &n, sizeof(int), cudaMemcpyHostToDevice, s->stream));
     FP_CUDA(cudaStreamSynchronize(s->stream));
     return PIC_OK;
 }
@@ -1204,8 +1205,11 @@ int sort_particles(Sim *s) {
     if (s->n_total == 0) return PIC_OK;
     const int bits = bitlen(((unsigned long long)s->mesh->n_tets << 2));
     uint32_t *ok, *ov;
+    // the last push wrote n_total entries (live, then absorbed ones with the
+    // dead key); in a batch that count is known on the device only
+    const int *d_n = s->batch_mode ? &s->dctl.p->n_sorted : nullptr;
     int rc = radix_sort<uint32_t>(s->stream, s->bank[s->cur].key.p, s->skey.p, s->sval.p, s->tkey.p, s->tval.p,
-                                  nullptr, s->n_total, bits, &s->sortw, &ok, &ov);
+                                  d_n, s->n_total, bits, &s->sortw, &ok, &ov);
     if (rc) return rc;
     if (ok != s->skey.p) {
         std::swap(s->skey, s->tkey);
@@ -1298,8 +1302,9 @@ static int launch_push(Sim *s, int mode) {
     PushArgs<R, V> a;
     fill_push_args(s, a);
     Control *dc = s->dctl.p;
-    // the live particles of this step are the first hctl->n_alive sorted entries
-    const int live = s->hctl->n_alive;
+    // the live particles of this step are the first n_alive sorted entries
+    // (in a batch the grid covers all n_total and the kernel reads n_alive)
+    const int live = s->batch_mode ? s->n_total : s->hctl->n_alive;
     const int blocks = std::max(1, (live + kPushBlock - 1) / kPushBlock);
     s->last_push_blocks = blocks;
     FP_CUDA(cudaMemsetAsync(&dc->pad, 0, sizeof(int), s->stream));
@@ -1334,6 +1339,7 @@ int particle_push(Sim *s, int charge_only) {
         const int mode = charge_only ? 2 : (s->ab ? 1 : 0);
         int rc = s->mixed ? launch_push<float, long long>(s, mode) : launch_push<double, double>(s, mode);
         if (rc) return rc;
+        if (s->batch_mode) break;   // no retry: an overflow latches its status bit
         // the push reads the current bank and writes the other one, so a push
         // whose record buffer overflowed is simply run again with more room
         FP_CUDA(cudaMemcpyAsync(&s->hctl->n_over, &s->dctl.p->n_over, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
@@ -1357,23 +1363,36 @@ int particle_push(Sim *s, int charge_only) {
         // crossing records: sort by (accumulator, wall, particle, piece) and add in that order
         const int oshift = 6 + std::max(1, bitlen((unsigned long long)s->n_total));
         const int bits = oshift + bitlen(((unsigned long long)m->n_tets * s->nsp << 1) | 1ull);
-        const int nover = s->hctl->n_over;   // known on the host since the push
+        // known on the host since the push, or (batch) a device count bounded by the buffer
+        const int nover = s->batch_mode ? s->ocap : s->hctl->n_over;
         if (nover > 0) {
             unsigned long long *ok;
             uint32_t *ov;
             rc = radix_sort<unsigned long long>(s->stream, s->okey.p, s->okey2.p, s->oidx.p, s->okey.p, s->oidx2.p,
-                                                nullptr, nover, bits, &s->osortw, &ok, &ov);
+                                                s->batch_mode ? &s->dctl.p->n_over : nullptr, nover, bits,
+                                                &s->osortw, &ok, &ov);
             if (rc) return rc;
             if (s->mixed) { k_overflow_reduce<long long><<<(nover + 255) / 256, 256, 0, s->stream>>>(&s->dctl.p->n_over, nover, ok, ov, (const long long *)s->oval.p, oshift, (long long *)s->tacc.p, (long long *)s->wacc.p); note_launch(); }
             else { k_overflow_reduce<double><<<(nover + 255) / 256, 256, 0, s->stream>>>(&s->dctl.p->n_over, nover, ok, ov, (const double *)s->oval.p, oshift, (double *)s->tacc.p, (double *)s->wacc.p); note_launch(); }
             FP_CUDA(cudaGetLastError());
         }
         // the next step's live count; the new bank holds the first `live` entries
+        FP_CUDA(cudaMemcpyAsync(&s->dctl.p->n_sorted, &s->dctl.p->n_alive, sizeof(int), cudaMemcpyDeviceToDevice, s->stream));
         FP_CUDA(cudaMemcpyAsync(&s->dctl.p->n_alive, &s->dctl.p->pad, sizeof(int), cudaMemcpyDeviceToDevice, s->stream));
         s->cur = 1 - s->cur;
-        s->n_total = s->hctl->n_alive;
+        if (!s->batch_mode) s->n_total = s->hctl->n_alive;
         if (!charge_only && s->ab && s->nhist < s->hist_levels) s->nhist++;
     }
+    return PIC_OK;
+}
+
+// Before batched stepping: crossing-record room for every particle (a batch
+// step cannot grow the buffer), reserved sort workspaces.
+int particles_batch_prepare(Sim *s) {
+    if (s->n_total == 0) return PIC_OK;
+    const int want = std::min(std::max(s->n_total + 1024, s->ocap), (1 << 30) - 1);
+    int rc;
+    if (want > s->ocap && (rc = overflow_alloc(s, want))) return rc;
     return PIC_OK;
 }
 

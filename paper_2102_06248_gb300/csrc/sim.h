@@ -46,7 +46,8 @@ struct GridBarrier {
 
 // Host-visible control block (pinned), refreshed at every synchronising point
 struct Control {
-    GridBarrier gbar;
+    GridBarrier gbar;     // barrier of the Newmark solve
+    GridBarrier gbar2;    // barrier of the node-Laplacian solves
     CgState cg;
     CgState lap;
     DiagDev diag;
@@ -54,8 +55,32 @@ struct Control {
     uint32_t status;
     int n_alive;
     int n_over;
-    int pad;
+    int pad;          // live count after the push (copied to n_alive after it)
+    int n_sorted;     // entries the last push wrote (live and absorbed): the next sort's length
 };
+
+// One solve of the persistent Jacobi-PCG (solver.cu): the SELL-32 system,
+// its vectors, the stopping rule and the blocks of the launch it owns
+struct PcgArgs {
+    int n, n_slices;
+    const int *sp, *sw, *col;     // SELL-32: slice offsets, widths, column indices
+    const double *Av, *Dinv, *b;
+    double *x, *r, *u, *w, *p, *s;
+    double *part;                 // >= 5 * blocks partials
+    CgState *st;                  // results (iterations, residual, failure)
+    GridBarrier *gb;              // this solve's barrier (zeroed before the launch)
+    const double *abs_src;        // device scalar, or NULL
+    double abs_factor;            // stop at max|r| <= abs_factor * (*abs_src) (rel. fallback_tol2 if it is 0)
+    double tol2;                  // stop at r.r <= tol2 * b.b
+    double fallback_tol2;
+    double abs_inf;               // stop at max|r| <= abs_inf (negative: off)
+    uint32_t *status;
+    int max_iters;
+    int x_zero;                   // the initial guess is 0 (x is written, not read)
+    int quiet;                    // reaching max_iters ends the solve without an error
+    int block0, blocks;           // blocks of the launch that run this solve
+};
+constexpr int kMaxBatchRuns = 64;
 
 // Learned edge preconditioner of the Newmark solve (weights, activations and
 // the vectors of its flexible PCG); allocated on first use
@@ -173,10 +198,10 @@ struct Sim {
     long long lap_iters_sum = 0;
     GnnState gnn;
     int gnn_iters = 0;              // iterations of the last flexible PCG (host copy source)
-    int coop_blocks = -1;           // co-resident blocks of the persistent PCG (0: unavailable)
     uint32_t host_status = 0;       // latched errors seen on the host
     // optional phase profiler
     int profile = 0;
+    int batch_mode = 0;             // inside a batch: no host synchronisation in a step (counts stay on the device)
     cudaEvent_t ev0[PH_COUNT] = {}, ev1[PH_COUNT] = {};
     bool ev_used[PH_COUNT] = {};
     double prof_ms[PH_COUNT] = {};
@@ -208,6 +233,19 @@ int compute_diagnostics(Sim *s);
 int init_fields(Sim *s);
 int read_control(Sim *s);
 int newmark_truncated_residual(Sim *s, int iters, double *r_out);
+// batched solves: the argument blocks of one sim's two systems, and one
+// persistent launch over many of them (blocks_per_sm 0: as many as fit)
+PcgArgs pcg_args_newmark(Sim *s);
+PcgArgs pcg_args_truncated(Sim *s, int iters);
+PcgArgs pcg_args_completion(Sim *s);
+int launch_pcg_runs(PcgArgs *runs, int n_runs, int blocks_per_sm, cudaStream_t st);
+int gc_prepare(Sim *s);
+int gc_finish(Sim *s);
+// the step in parts (api.cu) and the batch-mode particle set-up (particles.cu)
+int step_particles(Sim *s, bool fields);
+int step_fields_end(Sim *s);
+int check_status(Sim *s);
+int particles_batch_prepare(Sim *s);
 // learned preconditioner (gnn.cu)
 int gnn_prepare(Sim *s);
 int gnn_set_weights(Sim *s, const float *w, long long np);

@@ -663,14 +663,14 @@ __device__ __forceinline__ bool spin_until(GridBarrier *gb, const unsigned int *
     return true;
 }
 
-// Grid barrier number `epoch` (1, 2, ... in every block): the counter reaches
-// epoch * G once every block has arrived.
-__device__ __forceinline__ bool grid_barrier(GridBarrier *gb, unsigned int epoch) {
+// Barrier number `epoch` (1, 2, ... in every block) among the nb blocks of
+// one solve: the counter reaches epoch * nb once every block has arrived.
+__device__ __forceinline__ bool grid_barrier(GridBarrier *gb, unsigned int epoch, int nb) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         red_release_add(&gb->count, 1u);
-        ok = spin_until(gb, &gb->count, epoch * gridDim.x);
+        ok = spin_until(gb, &gb->count, epoch * (unsigned)nb);
     }
     __syncthreads();
     return ok != 0;
@@ -709,7 +709,8 @@ __device__ __forceinline__ void block_reduce(const double v[NS], unsigned long l
     }
 }
 
-// Grid-wide reduction at barrier number `epoch`: every block leaves its
+// Reduction over the nb blocks of one solve at barrier number `epoch` (this
+// block is number bid): every block leaves its
 // partials (sums in part[c*G + block], c < NS; the maximum's bits in
 // part[NS*G + block]); the last block to arrive combines them in a fixed
 // order (thread t adds blocks t, t + kThreads, ..., all loads issued first,
@@ -718,11 +719,11 @@ __device__ __forceinline__ void block_reduce(const double v[NS], unsigned long l
 template <int NS>
 __device__ __forceinline__ bool grid_reduce(GridBarrier *gb, double *part, const double v[NS],
                                             unsigned long long mx, double *shv, unsigned long long *shm,
-                                            unsigned int epoch, double out[NS + 1]) {
+                                            unsigned int epoch, double out[NS + 1], int nb, int bid) {
     __shared__ int role;   // 1: last block, 0: waits, -1: timed out
     __shared__ double res[NS + 1];
-    const int G = gridDim.x;
-    block_reduce<NS>(v, mx, shv, shm, [&](int c, double val) { part[c * G + blockIdx.x] = val; });
+    const int G = nb;
+    block_reduce<NS>(v, mx, shv, shm, [&](int c, double val) { part[c * G + bid] = val; });
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned int old = atom_acq_rel_add(&gb->count, 1u);
@@ -774,27 +775,22 @@ __device__ __forceinline__ double sell_row(const double *__restrict__ Av, const 
     return acc;
 }
 
-struct PcgArgs {
-    int n, n_slices;
-    const int *sp, *sw, *col;     // SELL-32: slice offsets, widths, column indices
-    const double *Av, *Dinv, *b;
-    double *x, *r, *u, *w, *p, *s;
-    double *part;                 // >= 5 * gridDim.x partials
-    CgState *st;
-    GridBarrier *gb;
-    const double *abs_src;        // device scalar, or NULL (see CgState::abs_inf)
-    double abs_factor;
-    uint32_t *status;
-    int x_zero;                   // the initial guess is 0 (x is written, not read)
-    int quiet;                    // reaching max_iters ends the solve without an error
+
+// Several independent solves share one launch: run r owns the blocks
+// [block0, block0 + blocks) and synchronises them with its own barrier.
+template <int MAXR>
+struct PcgBatch {
+    int n_runs;
+    PcgArgs run[MAXR];
 };
 
-__global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(const PcgArgs a) {
+// the whole solve, run by block `bid` of the nb blocks that own it
+__device__ __forceinline__ void pcg_body(const PcgArgs &a, const int nb, const int bid) {
     __shared__ double shv[4 * kThreads];
     __shared__ unsigned long long shm[kThreads];
     __shared__ int s_sp[kSmemSlices], s_sw[kSmemSlices];
     const int n = a.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int sl0 = blockIdx.x * kSlicesPerBlock + warp, sls = gridDim.x * kSlicesPerBlock;
+    const int sl0 = bid * kSlicesPerBlock + warp, sls = nb * kSlicesPerBlock;
     const double *__restrict__ Av = a.Av;
     const int *__restrict__ col = a.col;
     const double *__restrict__ Dinv = a.Dinv;
@@ -832,12 +828,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(const PcgArgs a)
             wid = nwid;
         }
     };
-    const int max_iters = st->max_iters;
-    double abs_inf = st->abs_inf, tol2 = st->tol2;
+    const int max_iters = a.max_iters;
+    double abs_inf = a.abs_inf, tol2 = a.tol2;
     if (a.abs_src) {
         const double qv = *a.abs_src;
         if (qv > 0.0) abs_inf = a.abs_factor * qv;
-        else tol2 = st->fallback_tol2;
+        else tol2 = a.fallback_tol2;
     }
     unsigned int epoch = 0;
     double t[5];
@@ -861,12 +857,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(const PcgArgs a)
         } else {
             spmv(x, init_row);
         }
-        if (!grid_barrier(a.gb, ++epoch)) goto timeout;
+        if (!grid_barrier(a.gb, ++epoch, nb)) goto timeout;
         spmv(u, [&](int i, double au) {
             w[i] = au;
             v[2] = fma(au, u[i], v[2]);
         });
-        if (!grid_reduce<4>(a.gb, a.part, v, mx, shv, shm, ++epoch, t)) goto timeout;
+        if (!grid_reduce<4>(a.gb, a.part, v, mx, shv, shm, ++epoch, t, nb, bid)) goto timeout;
     }
     {
         double gamma = t[0], rr = t[1];
@@ -905,13 +901,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(const PcgArgs a)
                     mx = max(mx, abs_bits(ri));
                 }
             }
-            if (!grid_barrier(a.gb, ++epoch)) goto timeout;
+            if (!grid_barrier(a.gb, ++epoch, nb)) goto timeout;
             // ---- w = A u ----
             spmv(u, [&](int i, double au) {
                 w[i] = au;
                 v[2] = fma(au, u[i], v[2]);
             });
-            if (!grid_reduce<3>(a.gb, a.part, v, mx, shv, shm, ++epoch, t)) goto timeout;
+            if (!grid_reduce<3>(a.gb, a.part, v, mx, shv, shm, ++epoch, t, nb, bid)) goto timeout;
             iters++;
             rr = t[1];
             done = (rr <= tol2 * bb) || (t[3] <= abs_inf);
@@ -920,7 +916,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(const PcgArgs a)
             alpha = gnew / (t[2] - beta * gnew / alpha);
             gamma = gnew;
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (bid == 0 && threadIdx.x == 0) {
             st->iters = iters;
             st->rr = rr;
             st->rz = gamma;
@@ -932,11 +928,28 @@ __global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(const PcgArgs a)
         return;
     }
 timeout:
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (bid == 0 && threadIdx.x == 0) {
         st->done = 1;
         st->failed = 1;
         atomicOr(a.status, (uint32_t)ST_BARRIER);
     }
+}
+
+// one solve per launch (its arguments passed by value)
+__global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(const PcgArgs a) { pcg_body(a, gridDim.x, blockIdx.x); }
+
+// several solves per launch: run r owns blocks [block0, block0 + blocks)
+__global__ void __launch_bounds__(kThreads, 4) k_pcg_batched(const __grid_constant__ PcgBatch<kMaxBatchRuns> B) {
+    // the block's run, copied to shared memory: read through a dynamic index
+    // in parameter space, the arguments made the solve half as fast again
+    __shared__ PcgArgs sa;
+    if (threadIdx.x == 0) {
+        int ri = 0;
+        while (ri + 1 < B.n_runs && (int)blockIdx.x >= B.run[ri + 1].block0) ri++;
+        sa = B.run[ri];
+    }
+    __syncthreads();
+    pcg_body(sa, sa.blocks, (int)blockIdx.x - sa.block0);
 }
 
 int grid_for_rows(int n) { return std::max(1, std::min(kMaxBlocks, (n + kRowsPerBlock - 1) / kRowsPerBlock)); }
@@ -1024,33 +1037,125 @@ int newmark_rhs(Sim *s) {
     return PIC_OK;
 }
 
-// co-resident blocks of the persistent PCG on the current device (0: no
-// cooperative launch)
-static int coop_capacity(int want_per_sm) {
-    int dev = 0, sms = 0, coop = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+// co-resident blocks per SM of the persistent PCG for up to MAXR runs (0:
+// no cooperative launch on this device)
+// (queried once per device and kept: no runtime queries while a stream is
+// being captured)
+constexpr int kMaxDevices = 64;
+template <bool BATCHED>
+static int coop_per_sm() {
+    static int cache[kMaxDevices];   // 0: not queried, -1: unavailable
+    int dev = 0, coop = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+    if (cache[dev]) return std::max(cache[dev], 0);
+    cache[dev] = -1;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent, kThreads, 0) != cudaSuccess) return 0;
-    if (want_per_sm > 0) per_sm = std::min(per_sm, want_per_sm);
-    return per_sm * sms;
+    cudaError_t e = BATCHED ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_batched, kThreads, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent, kThreads, 0);
+    if (e != cudaSuccess) return 0;
+    cache[dev] = per_sm > 0 ? per_sm : -1;
+    return std::max(per_sm, 0);
 }
 
-// One cooperative launch of the persistent PCG on a SELL-32 system; its
-// iteration count and failures reach the host through the control block at
-// the step's next synchronisation.  st must hold tol2, fallback_tol2,
-// max_iters and abs_inf; the rest of it is written by the kernel.
-static int launch_pcg(Sim *s, const DevSell &A, const double *Av, const double *Dinv, const double *b, double *x,
-                      double *r, double *u, double *w, double *p, double *sv, double *part, CgState *st,
-                      const CgState &init, const double *abs_src, double abs_factor, bool x_zero,
-                      bool quiet = false) {
-    if (s->coop_blocks < 0) s->coop_blocks = coop_capacity(s->cfg.solver_blocks_per_sm);
-    if (s->coop_blocks <= 0) {
+static int sm_count() {
+    static int cache[kMaxDevices];
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+    if (cache[dev]) return cache[dev];
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    cache[dev] = sms;
+    return sms;
+}
+
+__global__ void k_reset_barriers(PcgBatch<kMaxBatchRuns> B) {
+    const int r = threadIdx.x;
+    if (r < B.n_runs) {
+        GridBarrier *gb = B.run[r].gb;
+        gb->count = 0;
+        gb->flag = 0;
+        gb->timeout = 0;
+    }
+}
+
+// Splits a budget of co-resident blocks between the runs: each wants one
+// warp per slice at most; when they want more than the budget, blocks go in
+// proportion to the slices (at least one each).
+static int assign_blocks(PcgArgs *runs, int n_runs, int budget) {
+    if (n_runs > budget) {
+        set_error("more batched solves than co-resident blocks");
+        return PIC_ERR_INVALID_ARG;
+    }
+    long want_total = 0, slices = 0;
+    std::vector<int> want(n_runs);
+    for (int r = 0; r < n_runs; r++) {
+        want[r] = std::max(1, std::min(kMaxPcgBlocks, (runs[r].n_slices + kSlicesPerBlock - 1) / kSlicesPerBlock));
+        want_total += want[r];
+        slices += std::max(runs[r].n_slices, 1);
+    }
+    std::vector<int> got(n_runs);
+    long total = 0;
+    for (int r = 0; r < n_runs; r++) {
+        got[r] = want_total <= budget ? want[r]
+                                      : std::max(1, std::min(want[r], (int)((double)budget * std::max(runs[r].n_slices, 1) / slices)));
+        total += got[r];
+    }
+    while (total > budget) {
+        int big = 0;
+        for (int r = 1; r < n_runs; r++)
+            if (got[r] > got[big]) big = r;
+        got[big]--;
+        total--;
+    }
+    int b0 = 0;
+    for (int r = 0; r < n_runs; r++) {
+        runs[r].block0 = b0;
+        runs[r].blocks = got[r];
+        b0 += got[r];
+    }
+    return PIC_OK;
+}
+
+// One cooperative launch of the persistent PCG over n_runs solves on stream
+// st.  Results and failures reach the host through each run's CgState and
+// status word at the next synchronisation.
+int launch_pcg_runs(PcgArgs *runs, int n_runs, int blocks_per_sm, cudaStream_t st) {
+    if (n_runs <= 0) return PIC_OK;
+    if (n_runs > kMaxBatchRuns) {
+        set_error("at most " + std::to_string(kMaxBatchRuns) + " solves per persistent launch");
+        return PIC_ERR_INVALID_ARG;
+    }
+    const bool one = n_runs == 1;
+    int per_sm = one ? coop_per_sm<false>() : coop_per_sm<true>();
+    if (per_sm <= 0) {
         set_error("the persistent PCG needs a device with cooperative launch");
         return PIC_ERR_CUDA;
     }
+    if (blocks_per_sm > 0) per_sm = std::min(per_sm, blocks_per_sm);
+    int rc = assign_blocks(runs, n_runs, per_sm * sm_count());
+    if (rc) return rc;
+    const int G = runs[n_runs - 1].block0 + runs[n_runs - 1].blocks;
+    PcgBatch<kMaxBatchRuns> all;
+    all.n_runs = n_runs;
+    for (int r = 0; r < n_runs; r++) all.run[r] = runs[r];
+    { k_reset_barriers<<<1, kMaxBatchRuns, 0, st>>>(all); note_launch(); }
+    if (one) {
+        PcgArgs a1 = all.run[0];
+        void *args[] = {&a1};
+        FP_CUDA(cudaLaunchCooperativeKernel((const void *)k_pcg_persistent, G, kThreads, args, 0, st));
+    } else {
+        void *args[] = {&all};
+        FP_CUDA(cudaLaunchCooperativeKernel((const void *)k_pcg_batched, G, kThreads, args, 0, st));
+    }
+    note_launch();
+    return PIC_OK;
+}
+
+static PcgArgs make_args(Sim *s, const DevSell &A, const double *Av, const double *Dinv, const double *b, double *x,
+                         double *r, double *u, double *w, double *p, double *sv, double *part, CgState *st,
+                         double tol, double fallback_tol, int max_iters, const double *abs_src, double abs_factor,
+                         bool x_zero, bool quiet) {
     Control *dc = s->dctl.p;
-    PcgArgs a;
+    PcgArgs a{};
     a.n = A.n_rows;
     a.n_slices = A.n_slices;
     a.sp = A.ptr.p;
@@ -1067,22 +1172,41 @@ static int launch_pcg(Sim *s, const DevSell &A, const double *Av, const double *
     a.s = sv;
     a.part = part;
     a.st = st;
-    a.gb = &dc->gbar;
+    a.gb = st == &dc->cg ? &dc->gbar : &dc->gbar2;
     a.abs_src = abs_src;
     a.abs_factor = abs_factor;
+    a.tol2 = tol * tol;
+    a.fallback_tol2 = fallback_tol * fallback_tol;
+    a.abs_inf = -1.0;
     a.status = &dc->status;
+    a.max_iters = max_iters;
     a.x_zero = x_zero ? 1 : 0;
     a.quiet = quiet ? 1 : 0;
-    // blocks: all co-resident, at most one slice per warp, and partials for
-    // five quantities per block fit in the 8 * kMaxBlocks buffer
-    const int G = std::max(1, std::min(std::min(s->coop_blocks, kMaxPcgBlocks),
-                                       (A.n_slices + kSlicesPerBlock - 1) / kSlicesPerBlock));
-    FP_CUDA(cudaMemcpyAsync(st, &init, sizeof(CgState), cudaMemcpyHostToDevice, s->stream));
-    FP_CUDA(cudaMemsetAsync(&dc->gbar, 0, sizeof(GridBarrier), s->stream));
-    void *args[] = {&a};
-    FP_CUDA(cudaLaunchCooperativeKernel((const void *)k_pcg_persistent, G, kThreads, args, 0, s->stream));
-    note_launch();
-    return PIC_OK;
+    return a;
+}
+
+// Jacobi-PCG on the last Newmark system from x = 0, stopped after `iters`
+// iterations without an error (training samples, solver timing)
+PcgArgs pcg_args_truncated(Sim *s, int iters) {
+    const Mesh *m = s->mesh;
+    return make_args(s, m->As, s->A_val.p, s->Dinv.p, s->rhs.p, s->x.p, s->cg_r.p, s->cg_z.p, s->cg_q.p, s->cg_p0.p,
+                     s->cg_p1.p, s->cg_part.p, &s->dctl.p->cg, 0.0, 0.0, iters, nullptr, 0.0, true, true);
+}
+
+PcgArgs pcg_args_newmark(Sim *s) {
+    const Mesh *m = s->mesh;
+    return make_args(s, m->As, s->A_val.p, s->Dinv.p, s->rhs.p, s->x.p, s->cg_r.p, s->cg_z.p, s->cg_q.p, s->cg_p0.p,
+                     s->cg_p1.p, s->cg_part.p, &s->dctl.p->cg, s->cfg.cg_tol, 0.0, s->cfg.cg_max_iters, nullptr, 0.0,
+                     false, false);
+}
+
+// the completion: defect in l_b, solution in l_x, stopping at
+// max|d - L psi| <= completion_tol * max|rho + wall| (qmax, computed on the device)
+PcgArgs pcg_args_completion(Sim *s) {
+    const Mesh *m = s->mesh;
+    return make_args(s, m->Ls, m->Ls_val.p, s->L_Dinv.p, s->l_b.p, s->l_x.p, s->l_r.p, s->l_z.p, s->l_q.p, s->l_p0.p,
+                     s->l_p1.p, s->l_part.p, &s->dctl.p->lap, 0.0, s->cfg.init_tol, 20000, &s->dctl.p->qmax,
+                     s->cfg.completion_tol, true, false);
 }
 
 int pcg_newmark(Sim *s) {
@@ -1097,12 +1221,8 @@ int pcg_newmark(Sim *s) {
         FP_CUDA(cudaMemcpyAsync(&s->dctl.p->cg.iters, &s->gnn_iters, sizeof(int), cudaMemcpyHostToDevice, s->stream));
         return PIC_OK;
     }
-    CgState init{};
-    init.tol2 = s->cfg.cg_tol * s->cfg.cg_tol;
-    init.max_iters = s->cfg.cg_max_iters;
-    init.abs_inf = -1.0;
-    return launch_pcg(s, m->As, s->A_val.p, s->Dinv.p, s->rhs.p, s->x.p, s->cg_r.p, s->cg_z.p, s->cg_q.p,
-                      s->cg_p0.p, s->cg_p1.p, s->cg_part.p, &s->dctl.p->cg, init, nullptr, 0.0, false);
+    PcgArgs a = pcg_args_newmark(s);
+    return launch_pcg_runs(&a, 1, s->cfg.solver_blocks_per_sm, s->stream);
 }
 
 // Residual of Jacobi-PCG on the last Newmark system (b = rhs) from x = 0
@@ -1113,12 +1233,8 @@ int newmark_truncated_residual(Sim *s, int iters, double *r_out) {
     const Mesh *m = s->mesh;
     const int n = m->n_int_edges;
     if (n == 0) return PIC_OK;
-    CgState init{};
-    init.tol2 = 0.0;
-    init.max_iters = iters;
-    init.abs_inf = -1.0;
-    int rc = launch_pcg(s, m->As, s->A_val.p, s->Dinv.p, s->rhs.p, s->x.p, s->cg_r.p, s->cg_z.p, s->cg_q.p,
-                        s->cg_p0.p, s->cg_p1.p, s->cg_part.p, &s->dctl.p->cg, init, nullptr, 0.0, true, true);
+    PcgArgs a = pcg_args_truncated(s, iters);
+    int rc = launch_pcg_runs(&a, 1, s->cfg.solver_blocks_per_sm, s->stream);
     if (rc) return rc;
     FP_CUDA(cudaMemcpyAsync(r_out, s->cg_r.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s->stream));
     return PIC_OK;
@@ -1131,13 +1247,10 @@ int laplacian_solve(Sim *s, const double *rhs_int, double *x_int, double tol, co
                     double abs_factor) {
     const Mesh *m = s->mesh;
     if (m->n_int_nodes == 0) return PIC_OK;
-    CgState init{};
-    init.tol2 = tol * tol;
-    init.fallback_tol2 = s->cfg.init_tol * s->cfg.init_tol;
-    init.max_iters = 20000;
-    init.abs_inf = -1.0;
-    return launch_pcg(s, m->Ls, m->Ls_val.p, s->L_Dinv.p, rhs_int, x_int, s->l_r.p, s->l_z.p, s->l_q.p, s->l_p0.p,
-                      s->l_p1.p, s->l_part.p, &s->dctl.p->lap, init, abs_src, abs_factor, true);
+    PcgArgs a = make_args(s, m->Ls, m->Ls_val.p, s->L_Dinv.p, rhs_int, x_int, s->l_r.p, s->l_z.p, s->l_q.p,
+                          s->l_p0.p, s->l_p1.p, s->l_part.p, &s->dctl.p->lap, tol, s->cfg.init_tol, 20000, abs_src,
+                          abs_factor, true, false);
+    return launch_pcg_runs(&a, 1, s->cfg.solver_blocks_per_sm, s->stream);
 }
 
 // Completion of the Newmark solve on the gradient subspace: the part of the
@@ -1147,7 +1260,7 @@ int laplacian_solve(Sim *s, const double *rhs_int, double *x_int, double tol, co
 // form.  Solving (G^T M G) psi = d and adding G psi removes it (A G = M G), so
 // the Gauss residual does not drift with the CG tolerance (Sec. III.A notes
 // that the linear solve is the only source of error).  The charge is not used.
-int gradient_completion(Sim *s) {
+int gc_prepare(Sim *s) {
     const Mesh *m = s->mesh;
     const int ni = m->n_int_edges, nin = m->n_int_nodes;
     if (ni == 0 || nin == 0) return PIC_OK;
@@ -1157,11 +1270,26 @@ int gradient_completion(Sim *s) {
     // stopping threshold: completion_tol * max_n |rho_n + wall_n| (charge at t^{n+1})
     { k_max_abs_sum<<<grid_for_elems(m->n_nodes), kThreads, 0, s->stream>>>(m->n_nodes, s->rho.p, s->wall.p, s->diag_part.p, &s->dctl.p->diag.count, &s->dctl.p->qmax); note_launch(); }
     FP_CUDA(cudaGetLastError());
-    int rc = laplacian_solve(s, s->l_b.p, s->l_x.p, 0.0, &s->dctl.p->qmax, s->cfg.completion_tol);
-    if (rc) return rc;
+    return PIC_OK;
+}
+
+int gc_finish(Sim *s) {
+    const Mesh *m = s->mesh;
+    const int ni = m->n_int_edges, nin = m->n_int_nodes;
+    if (ni == 0 || nin == 0) return PIC_OK;
     { k_gc_apply<<<(ni + 255) / 256, 256, 0, s->stream>>>(ni, m->edge_nodes.p, m->node_int.p, s->l_x.p, s->x.p); note_launch(); }
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
+}
+
+int gradient_completion(Sim *s) {
+    const Mesh *m = s->mesh;
+    if (m->n_int_edges == 0 || m->n_int_nodes == 0) return PIC_OK;
+    int rc;
+    if ((rc = gc_prepare(s))) return rc;
+    PcgArgs a = pcg_args_completion(s);
+    if ((rc = launch_pcg_runs(&a, 1, s->cfg.solver_blocks_per_sm, s->stream))) return rc;
+    return gc_finish(s);
 }
 
 int faraday_update(Sim *s) {

@@ -55,6 +55,12 @@ GNN_PARAMS = 6369
 PRECONDITIONERS = {"jacobi": 0, "gnn": 1}
 
 
+class pic_batch_info_t(C.Structure):
+    _fields_ = [("n_sims", C.c_int32), ("graph", C.c_int32), ("graph_steps", C.c_int32),
+                ("solver_blocks_per_sm", C.c_int32), ("graph_launches", C.c_int64), ("eager_steps", C.c_int64),
+                ("tune_ms", C.c_double * 3)]
+
+
 class pic_diag(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "step", "continuity_abs", "gauss_abs", "rho_max", "divb_abs", "cg_iters", "cg_relres", "n_alive",
@@ -106,6 +112,10 @@ def load(build_if_missing: bool = True):
         "pic_launch_count": ([], I64),
         "pic_electrostatic_solve_noalloc": ([P, C.c_void_p, C.c_void_p, D, C.c_void_p], I32),
         "pic_gnn_train": ([P, C.POINTER(pic_gnn_train_cfg), dp], I32),
+        "pic_batch_create": ([C.POINTER(P), I32, C.POINTER(P)], I32),
+        "pic_batch_step": ([P, I32], I32),
+        "pic_batch_info": ([P, C.POINTER(pic_batch_info_t)], I32),
+        "pic_batch_destroy": ([P], None),
         "pic_gnn_get_weights": ([P, C.POINTER(C.c_float), I64], I32),
         "pic_gnn_set_weights": ([P, C.POINTER(C.c_float), I64], I32),
         "pic_gnn_apply": ([P, dp, dp], I32),
@@ -359,6 +369,33 @@ class Sim:
         _check(_lib.pic_gnn_loss_grad(self._h, _ptr(r, C.c_double), C.byref(loss), _ptr(g, C.c_double)),
                "pic_gnn_loss_grad")
         return float(loss.value), g
+
+
+class Batch:
+    """pic_batch_create / pic_batch_step over simulations on one device."""
+
+    def __init__(self, sims: Sequence["Sim"]):
+        lib = load()
+        self.sims = list(sims)              # keep the members alive
+        arr = (C.c_void_p * len(self.sims))(*[s._h for s in self.sims])
+        h = C.c_void_p()
+        _check(lib.pic_batch_create(arr, len(self.sims), C.byref(h)), "pic_batch_create")
+        self._h = h
+
+    def step(self, n: int = 1):
+        _check(_lib.pic_batch_step(self._h, int(n)), "pic_batch_step")
+
+    def info(self) -> Dict[str, object]:
+        d = pic_batch_info_t()
+        _check(_lib.pic_batch_info(self._h, C.byref(d)), "pic_batch_info")
+        return {"n_sims": d.n_sims, "graph": d.graph, "graph_steps": d.graph_steps,
+                "solver_blocks_per_sm": d.solver_blocks_per_sm, "graph_launches": d.graph_launches,
+                "eager_steps": d.eager_steps, "tune_ms": list(d.tune_ms)}
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.pic_batch_destroy(self._h)
+            self._h = None
 
 
 def electrostatic_solve_noalloc(mesh: Mesh, rho, phi, tol: float = 1e-14, stream=None):

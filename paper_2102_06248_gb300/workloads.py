@@ -225,6 +225,33 @@ def thermal_plasma_cube(n_cells: int = 6, n_particles: int = 10_000, seed: int =
                     dt=None, steps=steps, rho_background=rho_bg)
 
 
+def batched_runs(n_runs: int = 64, seed: int = 1005, cells: Tuple[int, int] = (8, 32),
+                 particles: Tuple[float, float] = (1.0e4, 1.0e6), vth_over_c: float = 0.01,
+                 b0z: float = 0.1) -> List[Workload]:
+    """Independent thermal-electron runs of uneven size for batched stepping.
+
+    Run k: a unit PEC cube of c_k^3 Kuhn cells with N_k Maxwellian electrons
+    (v_th = 0.01c), c_k and N_k log-uniform in the given ranges (counter-based
+    draws from `seed`).  The density scales as (c_k/6)^2 x 1e11 m^-3, so the
+    Debye length stays about one cell and the plasma period resolves the same
+    way at dt = 2 x CFL on every mesh; weight = density / N_k.
+    """
+    lo_c, hi_c = math.log(cells[0]), math.log(cells[1] + 0.999)
+    lo_n, hi_n = math.log(particles[0]), math.log(particles[1])
+    uc = uniform(seed, 0, n_runs)
+    un = uniform(seed, 1, n_runs)
+    out = []
+    for k in range(n_runs):
+        c = int(math.exp(lo_c + (hi_c - lo_c) * uc[k]))
+        n = int(round(math.exp(lo_n + (hi_n - lo_n) * un[k])))
+        density = 1.0e11 * (c / 6.0) ** 2
+        wl = thermal_plasma_cube(n_cells=c, n_particles=n, seed=seed * 1000 + k, vth_over_c=vth_over_c,
+                                 weight=density / n, b0z=b0z)
+        wl.name = f"batched_run_{k}_{c}^3_{n}"
+        out.append(wl)
+    return out
+
+
 def larmor_orbit_box(n_cells: int = 20, b0z: float = 0.05, vperp_over_c: float = 0.05,
                      steps: int = 10_000, form: str = "mfem", pusher: str = "boris") -> Workload:
     """One electron gyrating in uniform B0 inside a PEC box (Sec. IV.A analogue).

@@ -1,0 +1,75 @@
+"""Batched stepping: several independent runs of uneven size stepped together
+(one stream per run, one persistent launch per solve over all runs, six-step
+CUDA graphs) give exactly what stepping each run alone gives, and each run
+still conserves charge.
+"""
+import numpy as np
+import pytest
+
+from paper_2102_06248_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DT_CFL_6 = 1.3017565848335032e-10   # tests/golden/dt_cfl.json, thermal_plasma_cube_6^3
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2102_06248_gb300 import fempic
+    fempic.load()
+    return fempic
+
+
+def runs(F, precision):
+    out = []
+    for k, (cells, n) in enumerate([(4, 3000), (6, 8000), (8, 20000)]):
+        wl = W.thermal_plasma_cube(n_cells=cells, n_particles=n, seed=40 + k)
+        dt = 2 * DT_CFL_6 * 6 / cells
+        out.append((wl, dt))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["mixed", "plain"])
+def test_batch_equals_individual_steps(F, precision):
+    cases = runs(F, precision)
+    solo = [F.sim_from_workload(wl, dt, precision=precision) for wl, dt in cases]
+    memb = [F.sim_from_workload(wl, dt, precision=precision) for wl, dt in cases]
+    batch = F.Batch(memb)
+    steps = 13            # one eager step, then two six-step graph launches
+    batch.step(steps)
+    for s in solo:
+        s.step(steps)
+    info = batch.info()
+    assert info["graph"] == 1 and info["graph_launches"] == 2, info
+    for a, b in zip(solo, memb):
+        for f in ("E", "B", "RHO", "G"):
+            np.testing.assert_array_equal(a.field(f), b.field(f))
+        xa, va, ta, ia = a.particles()
+        xb, vb, tb, ib = b.particles()
+        np.testing.assert_array_equal(ia, ib)
+        np.testing.assert_array_equal(xa, xb)
+        np.testing.assert_array_equal(va, vb)
+        d = b.diag()
+        assert d["step"] == steps
+        assert d["continuity_abs"] <= 1e-12 * d["rho_max"]
+        assert d["gauss_abs"] <= 1e-12 * d["rho_max"]
+    # a member stepped on its own afterwards continues from the batched state
+    memb[1].step(1)
+    solo[1].step(1)
+    np.testing.assert_array_equal(solo[1].field("E"), memb[1].field("E"))
+    batch.step(7)         # graph dropped (a member moved), recaptured
+    assert batch.info()["graph"] == 1
+
+
+def test_batch_rejects_bad_members(F):
+    wl = W.thermal_plasma_cube(n_cells=4, n_particles=100, seed=3)
+    s = F.sim_from_workload(wl, 2 * DT_CFL_6 * 1.5)
+    with pytest.raises(F.PicError) as ei:
+        F.Batch([s, s])
+    assert ei.value.code == 1
+    g = F.sim_from_workload(wl, 2 * DT_CFL_6 * 1.5, preconditioner="gnn")
+    with pytest.raises(F.PicError):
+        F.Batch([g])
