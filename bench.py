@@ -190,6 +190,41 @@ def pcg_iter_flops(n_rows: int, nnz: int) -> float:
     return 2.0 * nnz + 2.0 * 8 * n_rows
 
 
+def gnn_leg(F, torch, wl, dt, stream, args):
+    """The headline workload (MIXED) with the learned preconditioner: three
+    Jacobi steps, training on residuals of the last Newmark system with the
+    library's own kernels, then steps whose Newmark solve is the flexible PCG
+    with the network (CUDA events on the simulation's stream)."""
+    sim = F.sim_from_workload(wl, dt, precision="mixed", stream=stream, profile=True, preconditioner="gnn")
+    for _ in range(3):
+        sim.step()
+    jac_iters = sim.diag()["cg_iters"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = sim.gnn_train(steps=args.gnn_train_steps, lr=1e-3, samples=8)
+    t1 = time.perf_counter()
+    sim.profile_reset()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    iters = []
+    for _ in range(args.gnn_steps):
+        sim.step()
+        iters.append(sim.diag()["cg_iters"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    pr = sim.profile()
+    d = sim.diag()
+    out = {"train_steps": args.gnn_train_steps, "train_s": t1 - t0, "train_loss": loss,
+           "ms_per_step": ev0.elapsed_time(ev1) / args.gnn_steps,
+           "cg_ms_per_step": pr["cg"][0] / args.gnn_steps, "cg_iters": iters, "jacobi_cg_iters_before": jac_iters,
+           "continuity_rel": d["continuity_abs"] / max(d["rho_max"], 1e-300),
+           "gauss_rel": d["gauss_abs"] / max(d["rho_max"], 1e-300),
+           "solve": "flexible PCG (Polak-Ribiere) with the network, 3 message-passing layers, hidden 32, bf16 weights"}
+    del sim
+    return out
+
+
 def batched_leg(F, torch, args):
     """64 independent thermal runs (cells 8^3..32^3, 1e4..1e6 electrons, log-
     uniform from a seed), MIXED, stepped as one batch (one stream per run, one
@@ -360,6 +395,11 @@ def gpu_arm(args):
                 "traffic": None, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": round(avg_ms, 5),
                 "fp64": fp64}
 
+    # ---- learned preconditioner on the same workload ----
+    gnn = None
+    if not args.skip_gnn:
+        gnn = gnn_leg(F, torch, wl, dt, stream, args)
+
     # ---- batched runs: 64 uneven thermal runs stepped together vs one by one ----
     batched = None
     if not args.skip_batched:
@@ -397,6 +437,7 @@ def gpu_arm(args):
                     "what": "particles_load from host arrays + init + K steps + E field and particles read back"},
             "gpu_launches": launches,
             "clocks": clk,
+            "gnn": gnn,
             "batched": batched,
         }
         print(json.dumps(line))
@@ -471,6 +512,9 @@ def main():
     ap.add_argument("--skip-plain", action="store_true", help="do not time the plain-FP64 path (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true", help="do not run the end-to-end leg (profiling runs)")
     ap.add_argument("--skip-batched", action="store_true", help="do not run the batched-runs leg")
+    ap.add_argument("--skip-gnn", action="store_true", help="do not run the learned-preconditioner leg")
+    ap.add_argument("--gnn-train-steps", type=int, default=300)
+    ap.add_argument("--gnn-steps", type=int, default=3)
     ap.add_argument("--batch-runs", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=60)
     args = ap.parse_args()
