@@ -315,6 +315,7 @@ struct PushArgs {
     const int4 *tnbr;
     SpeciesParams sp;
     double dt;
+    float qm32[kMaxSpecies], mw32[kMaxSpecies], dt32;   // FP32 copies (MIXED: no FP64 per particle)
     int ab_order, hist_levels;
     double abw[5];
     int walk_cap;
@@ -442,8 +443,8 @@ __device__ __forceinline__ long long shfl_up_v(long long v, int off) { return __
 // key, runs inside a warp stored directly (sole writer), the warps' boundary
 // pieces merged in warp order, and the block's own boundary runs handed to
 // k_fixup through the carry slots.
-template <typename R, typename V>
-__device__ __forceinline__ void reduce_block(const PushArgs<R, V> &a, uint32_t rkey, V vals[kNV], double ke,
+template <typename R, typename V, typename KE>
+__device__ __forceinline__ void reduce_block(const PushArgs<R, V> &a, uint32_t rkey, V vals[kNV], KE ke,
                                              int alive_out, int n_alive) {
     __shared__ uint32_t s_key[kPushBlock / 32][2];
     __shared__ V s_val[kPushBlock / 32][2][kNV];
@@ -452,10 +453,10 @@ __device__ __forceinline__ void reduce_block(const PushArgs<R, V> &a, uint32_t r
     {
         const unsigned ball = __ballot_sync(0xFFFFFFFFu, alive_out);
         if (lane == 0 && ball) atomicAdd(a.n_alive_next, __popc(ball));
-        double k2 = ke;
+        KE k2 = ke;   // kinetic energy: FP32 per warp in MIXED, FP64 across warps
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) k2 += __shfl_down_sync(0xFFFFFFFFu, k2, o);
-        if (lane == 0) s_ke[warp] = k2;
+        if (lane == 0) s_ke[warp] = (double)k2;
     }
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -557,8 +558,14 @@ __device__ __forceinline__ void gather_push(const PushArgs<R, typename std::cond
     // Whitney fields in the tet (Sec. II.A): E = E0 + Omega x d, B = B0 + beta d
     const R E[3] = {c[0] + c[4] * d2 - c[5] * d1, c[1] + c[5] * d0 - c[3] * d2, c[2] + c[3] * d1 - c[4] * d0};
     const R B[3] = {c[6] + c[9] * d0, c[7] + c[9] * d1, c[8] + c[9] * d2};
-    const R qm = (R)a.sp.qm[spc];
-    const R dt = (R)a.dt;
+    R qm, dt;
+    if constexpr (std::is_same<R, float>::value) {
+        qm = a.qm32[spc];
+        dt = a.dt32;
+    } else {
+        qm = a.sp.qm[spc];
+        dt = a.dt;
+    }
     if (MODE == 0) {
         // Boris: half kick, rotation about B, half kick (Sec. III.B)
         const R h = (R)0.5 * qm * dt;
@@ -752,7 +759,7 @@ __global__ void __launch_bounds__(kPushBlock) k_push_plain(const PushArgs<double
         }
         rkey = (uint32_t)tet;
     }
-    reduce_block<double, double>(a, rkey, vals, ke, alive_out, n_alive);
+    reduce_block<double, double, double>(a, rkey, vals, ke, alive_out, n_alive);
 }
 
 // ---------------------------------------------------------------------------
@@ -768,7 +775,7 @@ __global__ void __launch_bounds__(kPushBlock) k_push_mixed(const PushArgs<float,
     long long vals[kNV];
 #pragma unroll
     for (int c = 0; c < kNV; c++) vals[c] = 0;
-    double ke = 0.0;
+    float ke = 0.0f;
     int alive_out = 0;
     if (active) {
         const uint32_t key = a.skey[i];
@@ -884,12 +891,12 @@ __global__ void __launch_bounds__(kPushBlock) k_push_mixed(const PushArgs<float,
         a.dkey[i] = absorbed ? a.dead_key : (((uint32_t)endT << 2) | (uint32_t)spc);
         if (!absorbed) {
             alive_out = 1;
-            ke = 0.5 * a.sp.mw[spc] * ((double)Vn[0] * Vn[0] + (double)Vn[1] * Vn[1] + (double)Vn[2] * Vn[2]);
+            ke = 0.5f * a.mw32[spc] * (Vn[0] * Vn[0] + Vn[1] * Vn[1] + Vn[2] * Vn[2]);
             if (!(ke == ke) || !(Q[0] == Q[0])) atomicOr(a.status, (uint32_t)ST_NAN);
         }
         rkey = (uint32_t)(tet * a.nsp + spc);
     }
-    reduce_block<float, long long>(a, rkey, vals, ke, alive_out, n_alive);
+    reduce_block<float, long long, float>(a, rkey, vals, ke, alive_out, n_alive);
 }
 
 // spanning runs: a head piece (the last run of a block, or a block's first run
@@ -1269,6 +1276,11 @@ static void fill_push_args(Sim *s, PushArgs<R, V> &a) {
     a.tnbr = m->tet_nbr.p;
     a.sp = species_params(s);
     a.dt = s->cfg.dt;
+    for (int k = 0; k < kMaxSpecies; k++) {
+        a.qm32[k] = (float)a.sp.qm[k];
+        a.mw32[k] = (float)a.sp.mw[k];
+    }
+    a.dt32 = (float)a.dt;
     // Adams-Bashforth weights (newest first); the order ramps 1..k at start-up
     static const double W[5][5] = {{1.0, 0, 0, 0, 0},
                                    {1.5, -0.5, 0, 0, 0},
