@@ -190,6 +190,61 @@ def pcg_iter_flops(n_rows: int, nnz: int) -> float:
     return 2.0 * nnz + 2.0 * 8 * n_rows
 
 
+def refine_bytes(n_rows: int, nnz: int, inner_iters: float, outer: float) -> float:
+    """Algorithmic bytes of one MIXED Newmark solve (FP64 refinement with FP32
+    correction solves): per FP32 iteration 8 B per nonzero (FP32 value +
+    column) + 14 vector passes of 4 B per row; per refinement step one FP64
+    residual (12 B per nonzero, b read, x gathered, r in FP32 written: 20 B per
+    row) and the update x += d (20 B per row); plus the final residual check."""
+    inner = inner_iters * (8.0 * nnz + 4.0 * 14 * n_rows)
+    return inner + (outer + 1) * (12.0 * nnz + 20.0 * n_rows) + outer * 20.0 * n_rows
+
+
+def beam_leg(F, torch, stream, args):
+    """The non-neutral electron beam (MIXED): 32x32x128 Kuhn cells of 1.25 mm,
+    2M electrons in flight, the steady-state injection at z = 0 before every
+    step (pic_particles_inject with host arrays, generated before the timed
+    region), dt = 4 x CFL.  Host wall clock around inject + step (both
+    synchronise)."""
+    tab = dt_table()
+    wl = W.electron_beam(n_inflight=args.beam_particles)
+    h = 1.25e-3
+    dt = 4.0 * tab["kuhn_lattice_16^3"]["kappa"] * h / W.C0
+    n_inj = W.inject_per_step(wl, dt)
+    total = args.warmup + args.beam_steps
+    inj = [W.beam_injection(wl, k, n_inj, dt) for k in range(total)]
+    sim = F.sim_from_workload(wl, dt, precision="mixed", stream=stream, profile=True)
+    for k in range(args.warmup):
+        sim.particles_inject(0, *inj[k])
+        sim.step()
+    sim.profile_reset()
+    torch.cuda.synchronize()
+    alive0 = sim.diag()["n_alive"]
+    t_inj = 0.0
+    t0 = time.perf_counter()
+    for k in range(args.warmup, total):
+        a = time.perf_counter()
+        sim.particles_inject(0, *inj[k])
+        t_inj += time.perf_counter() - a
+        sim.step()
+    t1 = time.perf_counter()
+    d = sim.diag()
+    pr = sim.profile()
+    ms = 1e3 * (t1 - t0) / args.beam_steps
+    out = {"workload": "electron beam 32x32x128 Kuhn cells (786,432 tets), h = 1.25 mm, PEC; "
+                       f"{args.beam_particles} electrons in flight, radial Gaussian sigma = 0.1 width, vz = 0.1c, "
+                       f"1% spread, {n_inj} injected per step, 0.25 A, dt = 4xCFL, MIXED, Jacobi-PCG 1e-10",
+           "steps": args.beam_steps, "ms_per_step": ms, "inject_ms_per_step": 1e3 * t_inj / args.beam_steps,
+           "particles_alive": [alive0, d["n_alive"]],
+           "value": 0.5 * (alive0 + d["n_alive"]) / (ms / 1e3), "unit": "particle-steps/s",
+           "phases_ms_per_step": {k: round(v[0] / args.beam_steps, 4) for k, v in pr.items()},
+           "continuity_rel": d["continuity_abs"] / max(d["rho_max"], 1e-300),
+           "gauss_rel": d["gauss_abs"] / max(d["rho_max"], 1e-300),
+           "timing": "host clock around synchronising calls"}
+    del sim
+    return out
+
+
 def gnn_leg(F, torch, wl, dt, stream, args):
     """The headline workload (MIXED) with the learned preconditioner: three
     Jacobi steps, training on residuals of the last Newmark system with the
@@ -380,15 +435,24 @@ def gpu_arm(args):
     else:
         # one launch runs the whole Newmark solve: its algorithmic bytes are
         # the iterations it ran times the bytes of one iteration
-        kernel = "k_pcg_persistent (Newmark PCG, Chronopoulos-Gear, SELL-32)"
         iters_per_launch = cg_iters_timed / max(cg_n, 1)
-        alg = iters_per_launch * pcg_iter_bytes(mesh.n_int_edges, nnz_A)
         avg_ms = cg_avg
-        flops = iters_per_launch * pcg_iter_flops(mesh.n_int_edges, nnz_A)
-        fp64_tf = flops / (avg_ms / 1e3) / 1e12
-        fp64 = {"achieved_tflops": round(fp64_tf, 4), "peak_tflops": FP64_NOMINAL_TFLOPS,
-                "frac": round(fp64_tf / FP64_NOMINAL_TFLOPS, 4), "peak_source": "nominal",
-                "iters_per_launch": iters_per_launch}
+        outer = diag_m.get("cg_outer", 0.0)
+        if outer > 0:
+            # MIXED: FP64 refinement steps (the last solve's count) around FP32 correction iterations
+            kernel = ("k_pcg_persistent (Newmark: FP64 refinement, FP32 Chronopoulos-Gear corrections, "
+                      "SELL-32)")
+            alg = refine_bytes(mesh.n_int_edges, nnz_A, iters_per_launch, outer)
+            fp64 = {"note": "the FP32 correction iterations issue no FP64 arithmetic", "outer_steps": outer,
+                    "fp32_iters_per_launch": iters_per_launch}
+        else:
+            kernel = "k_pcg_persistent (Newmark PCG, Chronopoulos-Gear, SELL-32)"
+            alg = iters_per_launch * pcg_iter_bytes(mesh.n_int_edges, nnz_A)
+            flops = iters_per_launch * pcg_iter_flops(mesh.n_int_edges, nnz_A)
+            fp64_tf = flops / (avg_ms / 1e3) / 1e12
+            fp64 = {"achieved_tflops": round(fp64_tf, 4), "peak_tflops": FP64_NOMINAL_TFLOPS,
+                    "frac": round(fp64_tf / FP64_NOMINAL_TFLOPS, 4), "peak_source": "nominal",
+                    "iters_per_launch": iters_per_launch}
     achieved = alg / (avg_ms / 1e3) / 1e9
     roofline = {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
@@ -399,6 +463,11 @@ def gpu_arm(args):
     gnn = None
     if not args.skip_gnn:
         gnn = gnn_leg(F, torch, wl, dt, stream, args)
+
+    # ---- electron beam with injection (32x32x128 cells, 2M electrons in flight) ----
+    beam = None
+    if not args.skip_beam:
+        beam = beam_leg(F, torch, stream, args)
 
     # ---- batched runs: 64 uneven thermal runs stepped together vs one by one ----
     batched = None
@@ -426,6 +495,7 @@ def gpu_arm(args):
             "phases_ms_per_step": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof_m.items()},
             "phases_ms_per_step_plain": {k: round(v[0] / max(args.steps, 1), 4) for k, v in prof_p.items()},
             "cg_iters_last": diag_m["cg_iters"],
+            "cg_outer_last": diag_m.get("cg_outer", 0.0),
             "completion_iters_last": diag_m["completion_iters"],
             "conservation_last": {"continuity_rel": diag_m["continuity_abs"] / max(diag_m["rho_max"], 1e-300),
                                   "gauss_rel": diag_m["gauss_abs"] / max(diag_m["rho_max"], 1e-300)},
@@ -438,6 +508,7 @@ def gpu_arm(args):
             "gpu_launches": launches,
             "clocks": clk,
             "gnn": gnn,
+            "beam": beam,
             "batched": batched,
         }
         print(json.dumps(line))
@@ -513,6 +584,9 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true", help="do not run the end-to-end leg (profiling runs)")
     ap.add_argument("--skip-batched", action="store_true", help="do not run the batched-runs leg")
     ap.add_argument("--skip-gnn", action="store_true", help="do not run the learned-preconditioner leg")
+    ap.add_argument("--skip-beam", action="store_true", help="do not run the electron-beam leg")
+    ap.add_argument("--beam-particles", type=int, default=2_000_000)
+    ap.add_argument("--beam-steps", type=int, default=20)
     ap.add_argument("--gnn-train-steps", type=int, default=300)
     ap.add_argument("--gnn-steps", type=int, default=3)
     ap.add_argument("--batch-runs", type=int, default=64)

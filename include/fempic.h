@@ -187,6 +187,21 @@ int pic_particles_load(pic_sim *sim, int32_t species, double q, double m, double
  * nodes, e^0 = e^{-1} = -G phi; Gbar^0 = Gbar^{-1} = 0. */
 int pic_sim_init(pic_sim *sim);
 
+/* Particles entering between steps, e.g. from a beam source (the injected beam
+ * of Sec. IV.B): n particles of an already loaded species (its q, m, w) at host
+ * positions x [3n] and host velocities v [3n] (interleaved FP64; v^{n-1/2}
+ * for Boris), tet_hint [n] optional (NULL: located by a walk).  Call after
+ * pic_sim_init, between pic_step calls; the arrays grow as needed.  The
+ * particles' charge q w lambda(x) joins rho and leaves the node wall
+ * reservoir (where absorbed charge goes), so the Gauss residual of the current
+ * state is unchanged and the continuity of the next step holds.  Boris pusher
+ * only (PIC_ERR_STATE for Adams-Bashforth, whose history the new particles
+ * lack).  Errors:
+ * PIC_ERR_PARTICLE_OUTSIDE, PIC_ERR_INVALID_ARG, PIC_ERR_STATE, PIC_ERR_OOM.
+ * Synchronises. */
+int pic_particles_inject(pic_sim *sim, int32_t species, int64_t n, const double *x, const double *v,
+                         const int32_t *tet_hint);
+
 /* Adams-Bashforth start-up history for `levels` earlier steps (level j is j
  * steps back), arrays [levels][n_particles][3] in load order (FP64, host).
  * Without it the order ramps 1..k over the first steps. Call after init. */
@@ -235,6 +250,8 @@ typedef struct {
     double completion_iters; /* iterations of the last gradient-subspace completion */
     double cg_iters_sum;    /* Newmark PCG iterations summed over all steps taken */
     double completion_iters_sum; /* completion PCG iterations summed over all steps */
+    double cg_outer;        /* MIXED: FP64 refinement steps of the last Newmark solve (cg_iters counts
+                               the FP32 correction iterations); 0 in PLAIN */
 } pic_diag;
 
 /* Diagnostics of the last step (Sec. III.A conservation laws).  Synchronises. */

@@ -669,6 +669,22 @@ int orc_add_species(orc_sim *s, double q, double mass, double w, int n, const do
     return ORC_OK;
 }
 
+int orc_inject(orc_sim *s, double q, double mass, double w, int n, const double *x, const double *v, const int *tet) {
+    int p0 = s->np;
+    int rc = orc_add_species(s, q, mass, w, n, x, v, tet);
+    if (rc) return rc;
+    for (int p = p0; p < s->np; p++) {
+        double lam[4];
+        orc_lambda(s->m, s->tet[p], s->x + 3 * p, lam);
+        for (int k = 0; k < 4; k++) {
+            int nd = s->m->tet[4 * s->tet[p] + k];
+            s->rho[nd] += q * w * lam[k];
+            s->wall[nd] -= q * w * lam[k];
+        }
+    }
+    return ORC_OK;
+}
+
 /* node charge rho_n = sum_p q w lam_n(r_p) over live particles (Eq. chargeDef
  * with delta-shaped particles, Sec. II.A) */
 static void deposit_charge(orc_sim *s, double *rho) {

@@ -114,6 +114,11 @@ void orc_sim_free(orc_sim *s);
 int orc_add_species(orc_sim *s, double q, double mass, double w, int n,
                     const double *x, const double *v, const int *tet);
 int orc_init(orc_sim *s);
+/* particles entering between steps (a beam source, Sec. IV.B), after orc_init:
+ * appended like orc_add_species; their charge q w lambda(x) is added to rho^n
+ * and taken from the node wall reservoir, so rho + wall (and the Gauss
+ * residual) is unchanged and the next step's continuity holds */
+int orc_inject(orc_sim *s, double q, double mass, double w, int n, const double *x, const double *v, const int *tet);
 /* Adams-Bashforth history of the previous `levels` steps (level j = j steps
  * back, j = 1..levels), arrays [levels][n_particles][3]; call after orc_init */
 int orc_set_ab_history(orc_sim *s, int levels, const double *a_hist, const double *v_hist);

@@ -86,6 +86,8 @@ def _load():
     lib.orc_sim_new.argtypes = [P, C.POINTER(_Config)]
     lib.orc_sim_free.argtypes = [P]
     lib.orc_add_species.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_int, dp, dp, ip]
+    lib.orc_inject.argtypes = [P, C.c_double, C.c_double, C.c_double, C.c_int, dp, dp, ip]
+    lib.orc_inject.restype = C.c_int
     for name in ("orc_init", "orc_step", "orc_particle_phase", "orc_add_species"):
         getattr(lib, name).restype = C.c_int
     lib.orc_init.argtypes = [P]
@@ -301,6 +303,12 @@ class OracleSim:
         v = np.ascontiguousarray(v, dtype=np.float64)
         tet = np.ascontiguousarray(tet, dtype=np.int32)
         self._check(_lib.orc_add_species(self._h, q, m, w, x.shape[0], _dp(x), _dp(v), _ip(tet)), "add_species")
+
+    def inject(self, q: float, m: float, w: float, x: np.ndarray, v: np.ndarray, tet: np.ndarray):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        v = np.ascontiguousarray(v, dtype=np.float64)
+        tet = np.ascontiguousarray(tet, dtype=np.int32)
+        self._check(_lib.orc_inject(self._h, q, m, w, x.shape[0], _dp(x), _dp(v), _ip(tet)), "inject")
 
     def init(self):
         self._check(_lib.orc_init(self._h), "init")

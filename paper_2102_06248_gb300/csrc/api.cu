@@ -441,6 +441,30 @@ int pic_sim_init(pic_sim *sim) {
     return check_status(s);
 }
 
+int pic_particles_inject(pic_sim *sim, int32_t species, int64_t n, const double *x, const double *v,
+                         const int32_t *tet_hint) {
+    if (!sim || n < 0 || (n > 0 && (!x || !v))) {
+        set_error("pic_particles_inject: bad argument");
+        return PIC_ERR_INVALID_ARG;
+    }
+    Sim *s = &sim->s;
+    if (!s->initialised || s->ab) {
+        set_error("pic_particles_inject: needs an initialised simulation with the Boris pusher");
+        return PIC_ERR_STATE;
+    }
+    if (species < 0 || species >= s->n_species) {
+        set_error("pic_particles_inject: unknown species (load it with pic_particles_load first)");
+        return PIC_ERR_INVALID_ARG;
+    }
+    if ((int64_t)s->next_id + n >= (1LL << 30)) {
+        set_error("pic_particles_inject: more than 2^30 particles in total");
+        return PIC_ERR_INVALID_ARG;
+    }
+    int rc = particles_inject(s, species, (int)n, x, v, tet_hint);
+    if (rc) return rc;
+    return check_status(s);
+}
+
 int pic_set_ab_history(pic_sim *sim, int32_t levels, const double *a_hist, const double *v_hist) {
     if (!sim || !a_hist || !v_hist) {
         set_error("pic_set_ab_history: NULL argument");
@@ -692,6 +716,7 @@ int pic_diagnostics_get(pic_sim *sim, pic_diag *out) {
     out->completion_iters = s->step > 0 ? c.lap.iters : 0;
     out->cg_iters_sum = (double)s->cg_iters_sum;
     out->completion_iters_sum = (double)s->lap_iters_sum;
+    out->cg_outer = s->step > 0 ? c.cg.outer : 0;
     return PIC_OK;
 }
 

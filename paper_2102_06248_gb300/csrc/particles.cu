@@ -1080,6 +1080,68 @@ __global__ void k_load_particles(int n, int start, const double *__restrict__ x,
     id[q] = id0 + p;
 }
 
+// Injected particles appended to the current bank at [start, start + n)
+template <typename R>
+__global__ void k_inject_particles(int n, long start, const double *__restrict__ x, const double *__restrict__ v,
+                                   const int *__restrict__ tet, int species, int id0, R *x0, R *x1, R *x2, R *v0,
+                                   R *v1, R *v2, uint32_t *key, int *id) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const long q = start + p;
+    x0[q] = (R)x[3 * (size_t)p];
+    x1[q] = (R)x[3 * (size_t)p + 1];
+    x2[q] = (R)x[3 * (size_t)p + 2];
+    v0[q] = (R)v[3 * (size_t)p];
+    v1[q] = (R)v[3 * (size_t)p + 1];
+    v2[q] = (R)v[3 * (size_t)p + 2];
+    key[q] = ((uint32_t)tet[p] << 2) | (uint32_t)species;
+    id[q] = id0 + p;
+}
+
+// The node charges of injected particles in fixed point (integer sums do not
+// depend on the order of the atomics): MIXED uses exactly the 24-bit
+// barycentrics the next push starts from (bary32 + quantize of the stored FP32
+// position), PLAIN the FP64 barycentrics at scale 2^40.
+template <typename R>
+__global__ void k_inject_charge(int n, long start, const R *__restrict__ x0, const R *__restrict__ x1,
+                                const R *__restrict__ x2, const int *__restrict__ tet, const double *__restrict__ geo,
+                                const float *__restrict__ geo32, const int4 *__restrict__ tnodes,
+                                unsigned long long *__restrict__ acc) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const long q = start + p;
+    const int t = tet[p];
+    const int4 tn = tnodes[t];
+    const int nodes[4] = {tn.x, tn.y, tn.z, tn.w};
+    long long L[4];
+    if constexpr (std::is_same<R, float>::value) {
+        float gp[12], lf[4];
+        int Li[4];
+        load_geo32(geo32, t, gp);
+        bary32(gp, x0[q], x1[q], x2[q], lf);
+        quantize(lf, -1, Li);
+        for (int k = 0; k < 4; k++) L[k] = Li[k];
+    } else {
+        double gp[12], lam[4];
+        load_geo(geo, t, gp);
+        bary(gp, x0[q], x1[q], x2[q], lam);
+        for (int k = 0; k < 4; k++) L[k] = llrint(lam[k] * 1099511627776.0);   // 2^40
+    }
+    for (int k = 0; k < 4; k++) atomicAdd(acc + nodes[k], (unsigned long long)L[k]);
+}
+
+// rho += c, wall -= c with c = qw * acc / scale (the charge leaves the wall reservoir)
+__global__ void k_inject_apply(int nn, const unsigned long long *__restrict__ acc, double factor,
+                               double *__restrict__ rho, double *__restrict__ wall) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    const long long a = (long long)acc[i];
+    if (a == 0) return;
+    const double c = factor * (double)a;
+    rho[i] += c;
+    wall[i] -= c;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1200,6 +1262,7 @@ int upload_particles(Sim *s) {
     FP_CUDA(cudaGetLastError());
     FP_CUDA(cudaStreamSynchronize(s->stream));
     s->n_total = n;
+    s->next_id = n;
     s->cur = 0;
     s->hctl->n_alive = n;
     FP_CUDA(cudaMemcpyAsync(&s->dctl.p->n_alive, &n, sizeof(int), cudaMemcpyHostToDevice, s->stream));
@@ -1405,6 +1468,117 @@ int particles_batch_prepare(Sim *s) {
     const int want = std::min(std::max(s->n_total + 1024, s->ocap), (1 << 30) - 1);
     int rc;
     if (want > s->ocap && (rc = overflow_alloc(s, want))) return rc;
+    return PIC_OK;
+}
+
+// Grows the particle arrays to `cap`, keeping the current bank's first
+// `keep` entries (the other bank and the sort buffers hold no state between
+// steps).
+static int particles_grow(Sim *s, size_t cap, size_t keep) {
+    const size_t rs = s->rsize;
+    PartBank &k = s->bank[s->cur];
+    int rc;
+    auto grow = [&](DevBuf<unsigned char> &b, size_t bytes, size_t keep_bytes) -> int {
+        DevBuf<unsigned char> nb;
+        int r = nb.alloc(bytes);
+        if (r) return r;
+        if (keep_bytes) FP_CUDA(cudaMemcpy(nb.p, b.p, keep_bytes, cudaMemcpyDeviceToDevice));
+        b = std::move(nb);
+        return PIC_OK;
+    };
+    for (int d = 0; d < 3; d++)
+        if ((rc = grow(k.x[d], cap * rs, keep * rs)) || (rc = grow(k.v[d], cap * rs, keep * rs))) return rc;
+    {
+        DevBuf<uint32_t> nk;
+        DevBuf<int> ni;
+        if ((rc = nk.alloc(cap)) || (rc = ni.alloc(cap))) return rc;
+        if (keep) {
+            FP_CUDA(cudaMemcpy(nk.p, k.key.p, sizeof(uint32_t) * keep, cudaMemcpyDeviceToDevice));
+            FP_CUDA(cudaMemcpy(ni.p, k.id.p, sizeof(int) * keep, cudaMemcpyDeviceToDevice));
+        }
+        k.key = std::move(nk);
+        k.id = std::move(ni);
+    }
+    PartBank &o = s->bank[1 - s->cur];
+    for (int d = 0; d < 3; d++)
+        if ((rc = o.x[d].alloc(cap * rs)) || (rc = o.v[d].alloc(cap * rs))) return rc;
+    if ((rc = o.key.alloc(cap)) || (rc = o.id.alloc(cap))) return rc;
+    if ((rc = s->skey.alloc(cap)) || (rc = s->sval.alloc(cap)) || (rc = s->tkey.alloc(cap)) ||
+        (rc = s->tval.alloc(cap)))
+        return rc;
+    const size_t blocks = std::max<size_t>(1, (cap + kPushBlock - 1) / kPushBlock);
+    if ((rc = s->bcar.alloc(2 * blocks * kNV)) || (rc = s->bcar_key.alloc(2 * blocks)) ||
+        (rc = s->ke_part.alloc(blocks)))
+        return rc;
+    s->push_blocks_cap = blocks;
+    s->cap = cap;
+    return PIC_OK;
+}
+
+// Particles entering between steps (a beam source, Sec. IV.B): n particles of
+// a loaded species at host positions x [3n] (inside the mesh) with host
+// velocities v [3n] (v^{n-1/2} for Boris), appended to the current bank.
+// Their charge q w lam(x) is added to rho^n and taken from the wall
+// reservoir, so (rho + wall)^n, and with it the Gauss residual, is unchanged
+// and the next step's continuity holds as for every other particle.
+int particles_inject(Sim *s, int species, int n, const double *hx, const double *hv, const int *htet) {
+    if (n == 0) return PIC_OK;
+    int rc;
+    if ((rc = read_control(s))) return rc;
+    const Mesh *m = s->mesh;
+    // where the particles are: the hint checked, or a walk from tet 0
+    DevBuf<double> dx, dv;
+    DevBuf<int> dt_in, dt, dbad;
+    std::vector<double> xs(hx, hx + 3 * (size_t)n), vs(hv, hv + 3 * (size_t)n);
+    if ((rc = dx.upload(xs)) || (rc = dv.upload(vs)) || (rc = dt.alloc(n)) || (rc = dbad.alloc(1))) return rc;
+    if (htet) {
+        std::vector<int> ts(htet, htet + n);
+        if ((rc = dt_in.upload(ts))) return rc;
+    }
+    FP_CUDA(cudaMemsetAsync(dbad.p, 0, sizeof(int), s->stream));
+    { k_validate<<<(n + 127) / 128, 128, 0, s->stream>>>(n, 0, dx.p, htet ? dt_in.p : nullptr, m->n_tets, m->geo.p,
+                                                       m->tet_nbr.p, m->tet_nodes.p, m->xyz.p, dt.p, dbad.p); note_launch(); }
+    FP_CUDA(cudaGetLastError());
+    int bad = 0;
+    FP_CUDA(cudaMemcpyAsync(&bad, dbad.p, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    FP_CUDA(cudaStreamSynchronize(s->stream));
+    if (bad) {
+        set_error("pic_particles_inject: " + std::to_string(bad) + " particle(s) outside their tet or the mesh");
+        return PIC_ERR_PARTICLE_OUTSIDE;
+    }
+    // the entries the last push wrote stay where they are; the new ones follow
+    const long start = s->hctl->n_sorted;
+    if ((size_t)start + n > s->cap &&
+        (rc = particles_grow(s, std::max<size_t>(2 * s->cap, (size_t)start + n), (size_t)start)))
+        return rc;
+    if ((size_t)start + n > (size_t)s->ocap / 2 &&
+        (rc = overflow_alloc(s, (int)std::min<size_t>(2 * ((size_t)start + n), (size_t)1 << 30))))
+        return rc;
+    PartBank &k = s->bank[s->cur];
+    DevBuf<unsigned long long> acc;
+    if ((rc = acc.alloc(m->n_nodes))) return rc;
+    FP_CUDA(cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long) * m->n_nodes, s->stream));
+    const int blocks = (n + 255) / 256;
+    if (s->mixed) {
+        { k_inject_particles<float><<<blocks, 256, 0, s->stream>>>(n, start, dx.p, dv.p, dt.p, species, s->next_id, (float *)k.x[0].p, (float *)k.x[1].p, (float *)k.x[2].p, (float *)k.v[0].p, (float *)k.v[1].p, (float *)k.v[2].p, k.key.p, k.id.p); note_launch(); }
+        { k_inject_charge<float><<<blocks, 256, 0, s->stream>>>(n, start, (const float *)k.x[0].p, (const float *)k.x[1].p, (const float *)k.x[2].p, dt.p, m->geo.p, m->geo32.p, m->tet_nodes.p, acc.p); note_launch(); }
+    } else {
+        { k_inject_particles<double><<<blocks, 256, 0, s->stream>>>(n, start, dx.p, dv.p, dt.p, species, s->next_id, (double *)k.x[0].p, (double *)k.x[1].p, (double *)k.x[2].p, (double *)k.v[0].p, (double *)k.v[1].p, (double *)k.v[2].p, k.key.p, k.id.p); note_launch(); }
+        { k_inject_charge<double><<<blocks, 256, 0, s->stream>>>(n, start, (const double *)k.x[0].p, (const double *)k.x[1].p, (const double *)k.x[2].p, dt.p, m->geo.p, m->geo32.p, m->tet_nodes.p, acc.p); note_launch(); }
+    }
+    const double qw = s->sp_q[species] * s->sp_w[species];
+    const double factor = qw / (s->mixed ? 16777216.0 : 1099511627776.0);
+    { k_inject_apply<<<(m->n_nodes + 255) / 256, 256, 0, s->stream>>>(m->n_nodes, acc.p, factor, s->rho.p, s->wall.p); note_launch(); }
+    FP_CUDA(cudaGetLastError());
+    // counts: the bank now holds start + n entries, n more of them live
+    const int sorted = (int)(start + n), alive = s->hctl->n_alive + n;
+    s->hctl->n_sorted = sorted;
+    s->hctl->n_alive = alive;
+    FP_CUDA(cudaMemcpyAsync(&s->dctl.p->n_sorted, &s->hctl->n_sorted, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    FP_CUDA(cudaMemcpyAsync(&s->dctl.p->n_alive, &s->hctl->n_alive, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    FP_CUDA(cudaStreamSynchronize(s->stream));
+    s->n_total = sorted;
+    s->next_id += n;
     return PIC_OK;
 }
 

@@ -24,6 +24,8 @@ struct CgState {
     int max_iters;
     int failed;
     unsigned int count_a, count_b;   // arrival counters of the last-block reductions
+    int outer;                       // refinement steps of a mixed-precision solve
+    int pad_;
 };
 
 // Diagnostics record on the device (mirrors pic_diag)
@@ -79,6 +81,11 @@ struct PcgArgs {
     int x_zero;                   // the initial guess is 0 (x is written, not read)
     int quiet;                    // reaching max_iters ends the solve without an error
     int block0, blocks;           // blocks of the launch that run this solve
+    // mixed-precision refinement (refine = 1): FP64 residuals, FP32 corrections
+    int refine;
+    double inner_tol2;            // relative residual^2 of each FP32 correction solve
+    const float *Av32, *Dinv32;   // FP32 copies of the values and of D^-1
+    float *b32, *d32, *r32, *u32, *w32, *p32, *s32;
 };
 constexpr int kMaxBatchRuns = 64;
 
@@ -183,6 +190,7 @@ struct Sim {
     DevBuf<double> rhs;
     // solver work
     DevBuf<double> A_val, Dinv;
+    DevBuf<float> A32, Dinv32, cg32;  // MIXED: FP32 values, D^-1 and seven correction vectors
     DevBuf<double> cg_r, cg_z, cg_p0, cg_p1, cg_q, cg_part;
     DevBuf<double> hb;              // face vector H (b + b_prev)
     DevBuf<double> w_edge;          // gradient completion: M t - d2 Gbar on interior edges
@@ -246,6 +254,7 @@ int step_particles(Sim *s, bool fields);
 int step_fields_end(Sim *s);
 int check_status(Sim *s);
 int particles_batch_prepare(Sim *s);
+int particles_inject(Sim *s, int species, int n, const double *hx, const double *hv, const int *htet);
 // learned preconditioner (gnn.cu)
 int gnn_prepare(Sim *s);
 int gnn_set_weights(Sim *s, const float *w, long long np);

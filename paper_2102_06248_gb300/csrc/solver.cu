@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 
 #include "sim.h"
 
@@ -630,7 +631,9 @@ __global__ void __launch_bounds__(kThreads) k_max_abs_sum(int n, const double *_
 // ---------------------------------------------------------------------------
 constexpr int kMaxPcgBlocks = 4 * kThreads;    // largest grid of the persistent PCG
 constexpr int kSmemSlices = 512;               // slice headers a block keeps in shared memory
-constexpr long kSpinLimit = 1L << 22;         // about a second of polling
+constexpr long kSpinLimit = 1L << 22;
+constexpr int kMaxOuter = 12;                 // refinement steps of a mixed-precision solve
+constexpr int kMaxInner = 400;                // FP32 iterations per refinement step         // about a second of polling
 
 __device__ __forceinline__ void red_release_add(unsigned int *p, unsigned int v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -766,16 +769,6 @@ __device__ __forceinline__ bool grid_reduce(GridBarrier *gb, double *part, const
     return true;
 }
 
-// one SELL-32 row: sum_j A_rj v_j, v read through L2
-__device__ __forceinline__ double sell_row(const double *__restrict__ Av, const int *__restrict__ col,
-                                           const double *v, int kb, int kw) {
-    double acc = 0.0;
-#pragma unroll 8
-    for (int j = 0; j < kw; j++) acc = fma(Av[kb + 32 * j], __ldcg(v + col[kb + 32 * j]), acc);
-    return acc;
-}
-
-
 // Several independent solves share one launch: run r owns the blocks
 // [block0, block0 + blocks) and synchronises them with its own barrier.
 template <int MAXR>
@@ -784,149 +777,260 @@ struct PcgBatch {
     PcgArgs run[MAXR];
 };
 
-// the whole solve, run by block `bid` of the nb blocks that own it
-__device__ __forceinline__ void pcg_body(const PcgArgs &a, const int nb, const int bid) {
-    __shared__ double shv[4 * kThreads];
-    __shared__ unsigned long long shm[kThreads];
-    __shared__ int s_sp[kSmemSlices], s_sw[kSmemSlices];
-    const int n = a.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int sl0 = bid * kSlicesPerBlock + warp, sls = nb * kSlicesPerBlock;
-    const double *__restrict__ Av = a.Av;
-    const int *__restrict__ col = a.col;
-    const double *__restrict__ Dinv = a.Dinv;
-    double *x = a.x, *r = a.r, *u = a.u, *w = a.w, *p = a.p, *s = a.s;
-    CgState *st = a.st;
-    // the block's slice headers, k-th slice of warp `warp` at k * 8 + warp
-    const bool cached = (long)((a.n_slices + sls - 1) / sls) * kSlicesPerBlock <= kSmemSlices;
-    if (cached)
-        for (int k = 0, sl = sl0; sl < a.n_slices; k++, sl += sls)
-            if (lane == 0) {
-                s_sp[k * kSlicesPerBlock + warp] = a.sp[sl];
-                s_sw[k * kSlicesPerBlock + warp] = a.sw[sl];
-            }
-    __syncwarp();
-    auto slice = [&](int k, int sl, int &off, int &wid) {
+// Per-block context of one solve: the block's place in its run, the slice
+// headers it caches, the barrier epoch and the shared reduction buffers.
+struct SolveCtx {
+    const PcgArgs *a;
+    int nb, bid, lane, warp, sl0, sls;
+    bool cached;
+    int *s_sp, *s_sw;
+    double *shv;
+    unsigned long long *shm;
+    unsigned int epoch;
+    __device__ void slice(int k, int sl, int &off, int &wid) const {
         if (cached) {
             off = s_sp[k * kSlicesPerBlock + warp];
             wid = s_sw[k * kSlicesPerBlock + warp];
         } else {
-            off = a.sp[sl];
-            wid = a.sw[sl];
+            off = a->sp[sl];
+            wid = a->sw[sl];
         }
-    };
-    // SpMV phase over the warp's slices: out_i = sum_j A_ij v_j, then f(i, out_i)
-    auto spmv = [&](const double *v, auto f) {
-        int off, wid;
-        if (sl0 < a.n_slices) slice(0, sl0, off, wid);
-        for (int k = 0, sl = sl0; sl < a.n_slices; k++, sl += sls) {
+    }
+    // SpMV over the warp's slices with values Av: f(i, sum_j A_ij v_j)
+    template <typename T, typename F>
+    __device__ __forceinline__ void spmv(const T *__restrict__ Av, const T *v, F f) const {
+        const int *__restrict__ col = a->col;
+        const int n = a->n, ns = a->n_slices;
+        int off = 0, wid = 0;
+        if (sl0 < ns) slice(0, sl0, off, wid);
+        for (int k = 0, sl = sl0; sl < ns; k++, sl += sls) {
             int noff = 0, nwid = 0;
-            if (sl + sls < a.n_slices) slice(k + 1, sl + sls, noff, nwid);
-            const double acc = sell_row(Av, col, v, off + lane, wid);
+            if (sl + sls < ns) slice(k + 1, sl + sls, noff, nwid);
+            T acc = 0;
+            const int kb = off + lane;
+#pragma unroll 8
+            for (int j = 0; j < wid; j++) acc = fma(Av[kb + 32 * j], __ldcg(v + col[kb + 32 * j]), acc);
             const int i = sl * 32 + lane;
             if (i < n) f(i, acc);
             off = noff;
             wid = nwid;
         }
-    };
-    const int max_iters = a.max_iters;
+    }
+};
+
+struct CgOut {
+    int iters;
+    bool failed;
+    double rr, gamma, bb;
+};
+
+// Chronopoulos-Gear Jacobi-PCG on the context's matrix with values Av in
+// precision T: x, r, u = D^-1 r, w = A u, p, s = A p.  Per-thread sums are
+// kept in T and the block and grid reductions in FP64 (in FP32 the per-thread
+// sums cover about a dozen rows).  max|r| is tracked in FP64 only.  Returns
+// false if a barrier timed out.
+template <typename T>
+__device__ __forceinline__ bool cg_core(SolveCtx &c, const T *__restrict__ Av, const T *__restrict__ Dinv,
+                                        const T *b, T *x, T *r, T *u, T *w, T *p, T *s, bool x_zero, double tol2,
+                                        double abs_inf, int max_iters, CgOut &o) {
+    constexpr bool kMax = std::is_same<T, double>::value;
+    const PcgArgs &a = *c.a;
+    const int n = a.n, lane = c.lane;
+    double t[5];
+    {
+        T v[4] = {0, 0, 0, 0};   // gamma, rr, delta, bb
+        unsigned long long mx = 0;
+        auto init_row = [&](int i, T ax) {
+            const T bi = b[i], ri = bi - ax, ui = Dinv[i] * ri;
+            if (x_zero) x[i] = 0;
+            r[i] = ri;
+            u[i] = ui;
+            v[0] = fma(ri, ui, v[0]);
+            v[1] = fma(ri, ri, v[1]);
+            v[3] = fma(bi, bi, v[3]);
+            if constexpr (kMax) mx = max(mx, abs_bits(ri));
+        };
+        if (x_zero) {
+            for (int sl = c.sl0; sl < a.n_slices; sl += c.sls)
+                if (sl * 32 + lane < n) init_row(sl * 32 + lane, (T)0);
+        } else {
+            c.spmv(Av, x, init_row);
+        }
+        if (!grid_barrier(a.gb, ++c.epoch, c.nb)) return false;
+        c.spmv(Av, u, [&](int i, T au) {
+            w[i] = au;
+            v[2] = fma(au, u[i], v[2]);
+        });
+        const double vd[4] = {(double)v[0], (double)v[1], (double)v[2], (double)v[3]};
+        if (!grid_reduce<4>(a.gb, a.part, vd, mx, c.shv, c.shm, ++c.epoch, t, c.nb, c.bid)) return false;
+    }
+    double gamma = t[0], rr = t[1];
+    const double bb = t[3];
+    double alpha = t[0] / t[2], beta = 0.0;
+    bool done = (bb == 0.0) || (rr <= tol2 * bb) || (t[4] <= abs_inf);
+    if (bb == 0.0)
+        for (int sl = c.sl0; sl < a.n_slices; sl += c.sls)
+            if (sl * 32 + lane < n) x[sl * 32 + lane] = 0;
+    int iters = 0;
+    bool failed = false;
+    while (!done) {
+        if (iters >= max_iters) {
+            failed = true;
+            break;
+        }
+        const bool first = iters == 0;
+        const T al = (T)alpha, be = (T)beta;
+        // ---- p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r ----
+        T v[3] = {0, 0, 0};   // gamma, rr, delta
+        unsigned long long mx = 0;
+        for (int sl = c.sl0; sl < a.n_slices; sl += c.sls) {
+            const int i = sl * 32 + lane;
+            if (i < n) {
+                const T ui = u[i], wi = w[i];
+                const T pi = first ? ui : fma(be, p[i], ui);
+                const T si = first ? wi : fma(be, s[i], wi);
+                p[i] = pi;
+                s[i] = si;
+                x[i] = fma(al, pi, x[i]);
+                const T ri = fma(-al, si, r[i]);
+                const T un = Dinv[i] * ri;
+                r[i] = ri;
+                u[i] = un;
+                v[0] = fma(ri, un, v[0]);
+                v[1] = fma(ri, ri, v[1]);
+                if constexpr (kMax) mx = max(mx, abs_bits(ri));
+            }
+        }
+        if (!grid_barrier(a.gb, ++c.epoch, c.nb)) return false;
+        // ---- w = A u ----
+        c.spmv(Av, u, [&](int i, T au) {
+            w[i] = au;
+            v[2] = fma(au, u[i], v[2]);
+        });
+        const double vd[3] = {(double)v[0], (double)v[1], (double)v[2]};
+        if (!grid_reduce<3>(a.gb, a.part, vd, mx, c.shv, c.shm, ++c.epoch, t, c.nb, c.bid)) return false;
+        iters++;
+        rr = t[1];
+        done = (rr <= tol2 * bb) || (t[3] <= abs_inf);
+        const double gnew = t[0];
+        beta = gnew / gamma;
+        alpha = gnew / (t[2] - beta * gnew / alpha);
+        gamma = gnew;
+    }
+    o.iters = iters;
+    o.failed = failed;
+    o.rr = rr;
+    o.gamma = gamma;
+    o.bb = bb;
+    return true;
+}
+
+// the whole solve, run by block `bid` of the nb blocks that own it
+__device__ __forceinline__ void pcg_body(const PcgArgs &a, const int nb, const int bid) {
+    __shared__ double shv[4 * kThreads];
+    __shared__ unsigned long long shm[kThreads];
+    __shared__ int s_sp[kSmemSlices], s_sw[kSmemSlices];
+    SolveCtx c;
+    c.a = &a;
+    c.nb = nb;
+    c.bid = bid;
+    c.lane = threadIdx.x & 31;
+    c.warp = threadIdx.x >> 5;
+    c.sl0 = bid * kSlicesPerBlock + c.warp;
+    c.sls = nb * kSlicesPerBlock;
+    c.s_sp = s_sp;
+    c.s_sw = s_sw;
+    c.shv = shv;
+    c.shm = shm;
+    c.epoch = 0;
+    // the block's slice headers, k-th slice of warp `warp` at k * 8 + warp
+    c.cached = (long)((a.n_slices + c.sls - 1) / c.sls) * kSlicesPerBlock <= kSmemSlices;
+    if (c.cached)
+        for (int k = 0, sl = c.sl0; sl < a.n_slices; k++, sl += c.sls)
+            if (c.lane == 0) {
+                s_sp[k * kSlicesPerBlock + c.warp] = a.sp[sl];
+                s_sw[k * kSlicesPerBlock + c.warp] = a.sw[sl];
+            }
+    __syncwarp();
+    CgState *st = a.st;
     double abs_inf = a.abs_inf, tol2 = a.tol2;
     if (a.abs_src) {
         const double qv = *a.abs_src;
         if (qv > 0.0) abs_inf = a.abs_factor * qv;
         else tol2 = a.fallback_tol2;
     }
-    unsigned int epoch = 0;
-    double t[5];
-    // ---- r = b - A x, u = D^-1 r; then w = A u ----
-    {
-        double v[4] = {0.0, 0.0, 0.0, 0.0};   // gamma, rr, delta, bb
-        unsigned long long mx = 0;
-        auto init_row = [&](int i, double ax) {
-            const double bi = a.b[i], ri = bi - ax, ui = Dinv[i] * ri;
-            if (a.x_zero) x[i] = 0.0;
-            r[i] = ri;
-            u[i] = ui;
-            v[0] = fma(ri, ui, v[0]);
-            v[1] = fma(ri, ri, v[1]);
-            v[3] = fma(bi, bi, v[3]);
-            mx = max(mx, abs_bits(ri));
-        };
-        if (a.x_zero) {
-            for (int sl = sl0; sl < a.n_slices; sl += sls)
-                if (sl * 32 + lane < n) init_row(sl * 32 + lane, 0.0);
-        } else {
-            spmv(x, init_row);
-        }
-        if (!grid_barrier(a.gb, ++epoch, nb)) goto timeout;
-        spmv(u, [&](int i, double au) {
-            w[i] = au;
-            v[2] = fma(au, u[i], v[2]);
-        });
-        if (!grid_reduce<4>(a.gb, a.part, v, mx, shv, shm, ++epoch, t, nb, bid)) goto timeout;
-    }
-    {
-        double gamma = t[0], rr = t[1];
-        const double bb = t[3];
-        double alpha = t[0] / t[2], beta = 0.0;
-        bool done = (bb == 0.0) || (rr <= tol2 * bb) || (t[4] <= abs_inf);
-        if (bb == 0.0)
-            for (int sl = sl0; sl < a.n_slices; sl += sls)
-                if (sl * 32 + lane < n) x[sl * 32 + lane] = 0.0;
-        int iters = 0;
+    CgOut o{0, false, 0.0, 0.0, 0.0};
+    int outer = 0;
+    if (!a.refine) {
+        if (!cg_core<double>(c, a.Av, a.Dinv, a.b, a.x, a.r, a.u, a.w, a.p, a.s, a.x_zero != 0, tol2, abs_inf,
+                             a.max_iters, o))
+            goto timeout;
+    } else {
+        // Iterative refinement: the FP64 residual b - A x is the judge; each
+        // correction A d = r / sigma is solved in FP32 (values and vectors) to
+        // a relative residual of inner_tol, and x += sigma d in FP64.  sigma,
+        // the RMS of the residual, keeps the FP32 vectors near 1: in SI units
+        // the residuals are far below 1 and their squares would reach the
+        // FP32 subnormal range.
+        const int n = a.n;
+        int total = 0;
         bool failed = false;
-        while (!done) {
-            if (iters >= max_iters) {
+        double rr = 0.0, bb = 0.0;
+        while (true) {
+            if (outer > 0 && !grid_barrier(a.gb, ++c.epoch, nb)) goto timeout;   // x complete
+            double t[3];
+            {
+                double v2[2] = {0.0, 0.0};
+                c.spmv(a.Av, a.x, [&](int i, double ax) {
+                    const double bi = a.b[i], ri = bi - ax;
+                    a.r[i] = ri;
+                    v2[0] = fma(ri, ri, v2[0]);
+                    v2[1] = fma(bi, bi, v2[1]);
+                });
+                if (!grid_reduce<2>(a.gb, a.part, v2, 0ull, shv, shm, ++c.epoch, t, nb, bid)) goto timeout;
+            }
+            rr = t[0];
+            bb = t[1];
+            if (bb == 0.0 || rr <= tol2 * bb) break;
+            if (total >= a.max_iters || outer >= kMaxOuter) {
                 failed = true;
                 break;
             }
-            const bool first = iters == 0;
-            // ---- p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r ----
-            double v[3] = {0.0, 0.0, 0.0};   // gamma, rr, delta
-            unsigned long long mx = 0;
-            for (int sl = sl0; sl < a.n_slices; sl += sls) {
-                const int i = sl * 32 + lane;
-                if (i < n) {
-                    const double ui = u[i], wi = w[i];
-                    const double pi = first ? ui : fma(beta, p[i], ui);
-                    const double si = first ? wi : fma(beta, s[i], wi);
-                    p[i] = pi;
-                    s[i] = si;
-                    x[i] = fma(alpha, pi, x[i]);
-                    const double ri = fma(-alpha, si, r[i]);
-                    const double un = Dinv[i] * ri;
-                    r[i] = ri;
-                    u[i] = un;
-                    v[0] = fma(ri, un, v[0]);
-                    v[1] = fma(ri, ri, v[1]);
-                    mx = max(mx, abs_bits(ri));
-                }
+            const double sigma = sqrt(rr / n), inv = 1.0 / sigma;
+            for (int sl = c.sl0; sl < a.n_slices; sl += c.sls) {
+                const int i = sl * 32 + c.lane;
+                if (i < n) a.b32[i] = (float)(a.r[i] * inv);
             }
-            if (!grid_barrier(a.gb, ++epoch, nb)) goto timeout;
-            // ---- w = A u ----
-            spmv(u, [&](int i, double au) {
-                w[i] = au;
-                v[2] = fma(au, u[i], v[2]);
-            });
-            if (!grid_reduce<3>(a.gb, a.part, v, mx, shv, shm, ++epoch, t, nb, bid)) goto timeout;
-            iters++;
-            rr = t[1];
-            done = (rr <= tol2 * bb) || (t[3] <= abs_inf);
-            const double gnew = t[0];
-            beta = gnew / gamma;
-            alpha = gnew / (t[2] - beta * gnew / alpha);
-            gamma = gnew;
+            CgOut oi{0, false, 0.0, 0.0, 0.0};
+            if (!cg_core<float>(c, a.Av32, a.Dinv32, a.b32, a.d32, a.r32, a.u32, a.w32, a.p32, a.s32, true,
+                                a.inner_tol2, -1.0, min(kMaxInner, a.max_iters - total), oi))
+                goto timeout;
+            total += oi.iters;
+            outer++;
+            for (int sl = c.sl0; sl < a.n_slices; sl += c.sls) {
+                const int i = sl * 32 + c.lane;
+                if (i < n) a.x[i] = fma(sigma, (double)a.d32[i], a.x[i]);
+            }
         }
-        if (bid == 0 && threadIdx.x == 0) {
-            st->iters = iters;
-            st->rr = rr;
-            st->rz = gamma;
-            st->bb = bb;
-            st->done = 1;
-            st->failed = failed ? 1 : 0;
-            if (failed && !a.quiet) atomicOr(a.status, (uint32_t)ST_CG_NO_CONV);
-        }
-        return;
+        if (bb == 0.0)
+            for (int sl = c.sl0; sl < a.n_slices; sl += c.sls)
+                if (sl * 32 + c.lane < n) a.x[sl * 32 + c.lane] = 0.0;
+        o.iters = total;
+        o.failed = failed;
+        o.rr = rr;
+        o.bb = bb;
     }
+    if (bid == 0 && threadIdx.x == 0) {
+        st->iters = o.iters;
+        st->outer = outer;
+        st->rr = o.rr;
+        st->rz = o.gamma;
+        st->bb = o.bb;
+        st->done = 1;
+        st->failed = o.failed ? 1 : 0;
+        if (o.failed && !a.quiet) atomicOr(a.status, (uint32_t)ST_CG_NO_CONV);
+    }
+    return;
 timeout:
     if (bid == 0 && threadIdx.x == 0) {
         st->done = 1;
@@ -969,6 +1073,11 @@ __global__ void k_axpby(int n, double a, const double *__restrict__ x, double b,
                         double *__restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = a * x[i] + b * y[i];
+}
+
+__global__ void k_to_f32(long long n, const double *__restrict__ x, float *__restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)x[i];
 }
 
 }  // namespace
@@ -1014,6 +1123,12 @@ int solver_alloc(Sim *s) {
         { k_recip_diag_mk<<<(ni + 255) / 256, 256>>>(ni, m->M_diag.p, m->K_diag.p, c4, s->Dinv.p); note_launch(); }
     }
     if (nin > 0) { k_recip_diag<<<(nin + 255) / 256, 256>>>(nin, m->L.rowptr.p, m->L.col.p, m->L_val.p, s->L_Dinv.p); note_launch(); }
+    // MIXED: FP32 copies for the correction solves of the Newmark refinement
+    if (s->mixed && nel > 0) {
+        if ((rc = s->A32.alloc(nel)) || (rc = s->Dinv32.alloc(ni)) || (rc = s->cg32.alloc(7 * (size_t)ni))) return rc;
+        { k_to_f32<<<(unsigned)((nel + 255) / 256), 256>>>(nel, s->A_val.p, s->A32.p); note_launch(); }
+        { k_to_f32<<<(unsigned)((ni + 255) / 256), 256>>>(ni, s->Dinv.p, s->Dinv32.p); note_launch(); }
+    }
     FP_CUDA(cudaGetLastError());
     FP_CUDA(cudaDeviceSynchronize());
     return PIC_OK;
@@ -1193,11 +1308,30 @@ PcgArgs pcg_args_truncated(Sim *s, int iters) {
                      s->cg_p1.p, s->cg_part.p, &s->dctl.p->cg, 0.0, 0.0, iters, nullptr, 0.0, true, true);
 }
 
+// The Newmark solve.  MIXED refines in FP64 with FP32 correction solves
+// (each to 1e-5 relative); the FP64 residual ||b - A x|| <= cg_tol ||b|| is
+// the stopping rule in both precisions.
 PcgArgs pcg_args_newmark(Sim *s) {
     const Mesh *m = s->mesh;
-    return make_args(s, m->As, s->A_val.p, s->Dinv.p, s->rhs.p, s->x.p, s->cg_r.p, s->cg_z.p, s->cg_q.p, s->cg_p0.p,
-                     s->cg_p1.p, s->cg_part.p, &s->dctl.p->cg, s->cfg.cg_tol, 0.0, s->cfg.cg_max_iters, nullptr, 0.0,
-                     false, false);
+    PcgArgs a = make_args(s, m->As, s->A_val.p, s->Dinv.p, s->rhs.p, s->x.p, s->cg_r.p, s->cg_z.p, s->cg_q.p,
+                          s->cg_p0.p, s->cg_p1.p, s->cg_part.p, &s->dctl.p->cg, s->cfg.cg_tol, 0.0,
+                          s->cfg.cg_max_iters, nullptr, 0.0, false, false);
+    if (s->mixed && s->A32.p) {
+        const size_t ni = (size_t)m->n_int_edges;
+        float *v = s->cg32.p;
+        a.refine = 1;
+        a.inner_tol2 = 1e-10;
+        a.Av32 = s->A32.p;
+        a.Dinv32 = s->Dinv32.p;
+        a.b32 = v;
+        a.d32 = v + ni;
+        a.r32 = v + 2 * ni;
+        a.u32 = v + 3 * ni;
+        a.w32 = v + 4 * ni;
+        a.p32 = v + 5 * ni;
+        a.s32 = v + 6 * ni;
+    }
+    return a;
 }
 
 // the completion: defect in l_b, solution in l_x, stopping at

@@ -65,7 +65,7 @@ class pic_diag(C.Structure):
     _fields_ = [(n, C.c_double) for n in (
         "step", "continuity_abs", "gauss_abs", "rho_max", "divb_abs", "cg_iters", "cg_relres", "n_alive",
         "energy_e", "energy_b", "energy_k", "status", "completion_iters", "cg_iters_sum",
-        "completion_iters_sum")]
+        "completion_iters_sum", "cg_outer")]
 
 
 _lib = None
@@ -112,6 +112,7 @@ def load(build_if_missing: bool = True):
         "pic_launch_count": ([], I64),
         "pic_electrostatic_solve_noalloc": ([P, C.c_void_p, C.c_void_p, D, C.c_void_p], I32),
         "pic_gnn_train": ([P, C.POINTER(pic_gnn_train_cfg), dp], I32),
+        "pic_particles_inject": ([P, I32, I64, dp, dp, ip], I32),
         "pic_batch_create": ([C.POINTER(P), I32, C.POINTER(P)], I32),
         "pic_batch_step": ([P, I32], I32),
         "pic_batch_info": ([P, C.POINTER(pic_batch_info_t)], I32),
@@ -305,6 +306,18 @@ class Sim:
         n = C.c_int64()
         _check(_lib.pic_particles_count(self._h, C.byref(n)), "pic_particles_count")
         return n.value
+
+    def particles_inject(self, species: int, x, v, tet=None):
+        """pic_particles_inject with host numpy arrays x, v [n,3] (float64), tet [n] (int32) or None."""
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1, 3)
+        tp = None
+        if tet is not None:
+            tet = np.ascontiguousarray(tet, dtype=np.int32)
+            tp = _ptr(tet, C.c_int32)
+        _check(_lib.pic_particles_inject(self._h, int(species), x.shape[0], _ptr(x, C.c_double), _ptr(v, C.c_double),
+                                         tp), "pic_particles_inject")
+        self.n_loaded += x.shape[0]
 
     def particles(self):
         """(x [n,3], v [n,3], tet [n], id [n]) of the live particles, sorted by id."""

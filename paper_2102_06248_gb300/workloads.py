@@ -252,6 +252,71 @@ def batched_runs(n_runs: int = 64, seed: int = 1005, cells: Tuple[int, int] = (8
     return out
 
 
+def _beam_particles(seed: int, stream: int, n: int, side_xy: float, z0: float, z1: float, sigma: float,
+                    vz: float, vth: float) -> Tuple[np.ndarray, np.ndarray]:
+    """n beam electrons: radial Gaussian (sigma) about the box axis, cut at
+    0.45 of the width, z uniform in (z0, z1); v = (0, 0, vz) + vth N(0, 1)."""
+    c = 0.5 * side_xy
+    r = np.stack([normal(seed, stream, n), normal(seed, stream + 1, n)], axis=1) * sigma
+    lim = 0.45 * side_xy
+    r = np.clip(r, -lim, lim)
+    z = z0 + (z1 - z0) * uniform(seed, stream + 2, n)
+    x = np.stack([c + r[:, 0], c + r[:, 1], z], axis=1)
+    v = np.stack([vth * normal(seed, stream + 3 + a, n) for a in range(3)], axis=1)
+    v[:, 2] += vz
+    return x, v
+
+
+def electron_beam(cells: Tuple[int, int, int] = (32, 32, 128), h: float = 1.25e-3, n_inflight: int = 2_000_000,
+                  seed: int = 1003, sigma_frac: float = 0.1, vz_over_c: float = 0.1, spread: float = 0.01,
+                  current: float = 0.25, steps: int = 2000, dt_cfl_multiple: float = 4.0) -> Workload:
+    """Non-neutral electron beam with space charge (Sec. IV.B analogue).
+
+    A PEC box of cells[0] x cells[1] x cells[2] Kuhn cells of side h; electrons
+    enter at z = 0 with a radial Gaussian profile (sigma = sigma_frac * width),
+    axial speed vz_over_c * c and a thermal spread of `spread` of it per
+    component.  The beam starts in its steady state: n_inflight electrons
+    spread uniformly along the box (the in-flight population the injection
+    keeps), with the macro weight that carries `current` amperes.  Each step
+    then injects `inject_per_step(dt)` electrons (see beam_injection); they
+    leave through the far wall.
+    """
+    size = (cells[0] * h, cells[1] * h, cells[2] * h)
+    mesh = kuhn_box(cells, size)
+    vz = vz_over_c * C0
+    x, v = _beam_particles(seed, 0, n_inflight, size[0], 0.0, size[2], sigma_frac * size[0], vz, spread * vz)
+    x, tet = place_in_box(mesh, x)
+    w = current * size[2] / (vz * abs(Q_E) * n_inflight)
+    sp = Species(q=Q_E, m=M_E, w=w, x=x, v=v, tet=tet)
+    return Workload(name=f"electron_beam_{cells[0]}x{cells[1]}x{cells[2]}", mesh=mesh, species=[sp],
+                    b0=(0.0, 0.0, 0.0), form="we", pusher="boris", dt_cfl_multiple=dt_cfl_multiple, dt=None,
+                    steps=steps, rho_background=0.0,
+                    notes=f"h={h} m, sigma={sigma_frac * size[0]:.4e} m, vz={vz:.4e} m/s, weight={w:.6e}, "
+                          f"I={current} A, seed={seed}")
+
+
+def inject_per_step(wl: Workload, dt: float) -> int:
+    """Electrons entering per step so that the in-flight population stays
+    constant: N * vz * dt / Lz."""
+    sp = wl.species[0]
+    lz = float(wl.mesh.xyz[:, 2].max())
+    vz = float(np.mean(sp.v[:, 2]))
+    return max(1, int(round(sp.x.shape[0] * vz * dt / lz)))
+
+
+def beam_injection(wl: Workload, step: int, n: int, dt: float, seed: int = 1003,
+                   sigma_frac: float = 0.1, vz_over_c: float = 0.1, spread: float = 0.01):
+    """The electrons injected before step `step`: the beam profile at
+    z in (0, vz dt) (the slab that entered during one step); (x [n,3], v [n,3], tet [n])."""
+    side = float(wl.mesh.xyz[:, 0].max())
+    vz = vz_over_c * C0
+    zmax = min(vz * dt, 0.5 * float(wl.mesh.xyz[:, 2].max()))
+    x, v = _beam_particles(seed, 100 + 8 * step, n, side, 0.0, zmax, sigma_frac * side, vz, spread * vz)
+    x[:, 2] = np.maximum(x[:, 2], 1e-9 * zmax)
+    x, tet = place_in_box(wl.mesh, x)
+    return x, v, tet
+
+
 def larmor_orbit_box(n_cells: int = 20, b0z: float = 0.05, vperp_over_c: float = 0.05,
                      steps: int = 10_000, form: str = "mfem", pusher: str = "boris") -> Workload:
     """One electron gyrating in uniform B0 inside a PEC box (Sec. IV.A analogue).

@@ -331,3 +331,53 @@ def test_mixed_conservation_100_steps(F):
         worst_c = max(worst_c, d["continuity_abs"] / d["rho_max"])
         worst_g = max(worst_g, d["gauss_abs"] / d["rho_max"])
     assert worst_c <= 1e-13 and worst_g <= 1e-12, (worst_c, worst_g)
+
+
+# ---------------------------------------------------------------------------
+# Injection between steps (the beam source of Sec. IV.B)
+# ---------------------------------------------------------------------------
+BEAM_H = 1.0e-3
+BEAM_DT = 4.0 * 0.2305 * BEAM_H / W.C0   # 4 x CFL, kappa of the Kuhn lattice (tests/golden/dt_cfl.json)
+
+
+def test_injection_parity(F, oracle_lib):
+    """A small beam: electrons injected at z = 0 before every step into both
+    the oracle and the GPU path (PLAIN).  Fields and particles agree to 1e-10,
+    conservation holds every step."""
+    wl = W.electron_beam(cells=(4, 4, 8), h=BEAM_H, n_inflight=300, seed=13)
+    osim = oracle_lib.from_workload(wl, BEAM_DT, cg_tol=1e-13)
+    gsim = F.sim_from_workload(wl, BEAM_DT, cg_tol=1e-13)
+    sp = wl.species[0]
+    box = float(wl.mesh.xyz.max())
+    for step in range(6):
+        x, v, tet = W.beam_injection(wl, step, W.inject_per_step(wl, BEAM_DT) + 5, BEAM_DT, seed=13)
+        osim.inject(sp.q, sp.m, sp.w, x, v, tet)
+        gsim.particles_inject(0, x, v, tet)
+        osim.step()
+        gsim.step()
+        for f in ("E", "RHO", "WALL"):
+            assert rel_err(gsim.field(f), osim.field(f)) <= 1e-10, f
+        assert rel_err(gsim.field("B"), osim.field("B"), b_scale(osim.field("E"), BEAM_H)) <= 1e-10
+        compare_particles(gsim.particles(), osim.particles(), box)
+        d = gsim.diag()
+        assert d["continuity_abs"] <= 1e-12 * d["rho_max"]
+        assert d["gauss_abs"] <= 1e-12 * d["rho_max"]
+
+
+def test_injection_mixed_growth(F):
+    """MIXED: injecting more particles than were loaded grows the arrays; the
+    exact integer deposit keeps continuity at round-off and Gauss holds."""
+    wl = W.electron_beam(cells=(4, 4, 8), h=BEAM_H, n_inflight=200, seed=17)
+    sim = F.sim_from_workload(wl, BEAM_DT, precision="mixed")
+    for step in range(8):
+        x, v, tet = W.beam_injection(wl, step, 150, BEAM_DT, seed=17)
+        sim.particles_inject(0, x, v, None if step % 2 else tet)   # odd steps: located by a walk
+        sim.step()
+        d = sim.diag()
+        assert d["continuity_abs"] <= 1e-12 * d["rho_max"]
+        assert d["gauss_abs"] <= 1e-12 * d["rho_max"]
+    xs, vs, ts, ids = sim.particles()
+    assert len(ids) == len(np.unique(ids)) and ids.max() < 200 + 8 * 150
+    with pytest.raises(F.PicError) as ei:            # outside the mesh
+        sim.particles_inject(0, np.array([[0.5, 0.5, -1.0]]), np.zeros((1, 3)))
+    assert ei.value.code == 4
