@@ -39,6 +39,12 @@ from paper_2102_06248_gb300 import workloads as W  # noqa: E402
 METRIC = "particle-steps/s (gather+push+deposit) and step time vs plain FP64 GPU path"
 FALLBACK_HBM_GBS = 6800.0
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (non-tensor) nominal rate
+# DRAM bytes over algorithmic bytes of the Newmark k_pcg_persistent launch, from
+# the ncu capture summarised in profiles/pcg_persistent_plasma_ball_64.md
+# (MIXED refinement: 21.350 GB measured for 60 FP32 + 2 FP64 iterations whose
+# algorithmic bytes are 21.233 GB; PLAIN: 28.588 GB for 50 iterations, 27.525 GB)
+TRAFFIC_RATIO_MIXED = 21.350 / 21.233
+TRAFFIC_RATIO_PLAIN = 28.588 / 27.525
 
 
 def dt_table():
@@ -428,6 +434,7 @@ def gpu_arm(args):
     cg_avg = cg_ms / max(cg_n, 1)
     nnz_A = int(getattr(mesh, "nnz_A", 0))
     fp64 = None
+    traffic = None
     if push_ms >= cg_ms:
         kernel = "k_push_mixed (fused gather/push/walk/deposit)"
         alg = push_bytes(int(alive_m), mesh.n_tets, "mixed", len(wl.species))
@@ -443,11 +450,13 @@ def gpu_arm(args):
             kernel = ("k_pcg_persistent (Newmark: FP64 refinement, FP32 Chronopoulos-Gear corrections, "
                       "SELL-32)")
             alg = refine_bytes(mesh.n_int_edges, nnz_A, iters_per_launch, outer)
+            traffic = alg * TRAFFIC_RATIO_MIXED
             fp64 = {"note": "the FP32 correction iterations issue no FP64 arithmetic", "outer_steps": outer,
                     "fp32_iters_per_launch": iters_per_launch}
         else:
             kernel = "k_pcg_persistent (Newmark PCG, Chronopoulos-Gear, SELL-32)"
             alg = iters_per_launch * pcg_iter_bytes(mesh.n_int_edges, nnz_A)
+            traffic = alg * TRAFFIC_RATIO_PLAIN
             flops = iters_per_launch * pcg_iter_flops(mesh.n_int_edges, nnz_A)
             fp64_tf = flops / (avg_ms / 1e3) / 1e12
             fp64 = {"achieved_tflops": round(fp64_tf, 4), "peak_tflops": FP64_NOMINAL_TFLOPS,
@@ -456,7 +465,8 @@ def gpu_arm(args):
     achieved = alg / (avg_ms / 1e3) / 1e9
     roofline = {"kernel": kernel, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_source": peak_src,
-                "traffic": None, "algorithmic_bytes_per_launch": alg, "avg_launch_ms": round(avg_ms, 5),
+                "traffic": traffic, "traffic_source": "ncu DRAM/algorithmic ratio of the same kernel, scaled to this launch",
+                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": round(avg_ms, 5),
                 "fp64": fp64}
 
     # ---- learned preconditioner on the same workload ----
