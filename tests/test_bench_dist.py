@@ -1,0 +1,62 @@
+"""The benchmark's multi-rank host logic on CPU: two gloo ranks (the layout
+torchrun gives `bench.py --gpus 2`, one replica per GPU).  Each rank times its
+own replica; the job's time is the maximum over ranks and the work the sum, so
+the reported throughput is total work / slowest rank.  No data-path collective
+exists: the replicas share nothing but these scalars."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out):
+    os.environ.update({"RANK": str(rank), "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    sys.path.insert(0, ROOT)
+    import bench
+    r, w, local, dist = bench.dist_setup(world)
+    assert (r, w, local) == (rank, world, rank) and dist is not None
+    bench.barrier(dist)
+    t = bench.max_over_ranks(dist, 10.0 + rank, "cpu")       # per-rank times 10 ms and 11 ms
+    n = bench.sum_over_ranks(dist, 1000.0 * (rank + 1), "cpu")  # per-rank work 1000 and 2000 units
+    out.put((rank, t, n))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_max_time_sum_work():
+    torch = pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res == [(0, 11.0, 3000.0), (1, 11.0, 3000.0)]
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
+    import importlib
+    sys.path.insert(0, ROOT)
+    bench = importlib.import_module("bench")
+    monkeypatch.setenv("RANK", "1")
+    called = []
+    monkeypatch.setattr("oracle.oracle.from_workload", lambda *a, **k: called.append(1), raising=False)
+
+    class Args:
+        cells, particles, workload, steps, warmup = 16, 1000, "plasma_ball", 1, 3
+    assert bench.reference_arm(Args()) is None
+    assert not called
