@@ -394,10 +394,16 @@ __device__ __forceinline__ void quantize(const float lam[4], int skip, int L[4])
         L[k] = v;
         sum += v;
     }
+    int lbig = L[0];
 #pragma unroll
     for (int k = 1; k < 4; k++)
-        if (L[k] > L[big]) big = k;
-    L[big] += kFixOne - sum;
+        if (L[k] > lbig) {
+            big = k;
+            lbig = L[k];
+        }
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        if (k == big) L[k] += kFixOne - sum;   // unrolled select: no local-memory indexing
 }
 
 // exact line integral of the six Whitney-1 functions along a straight piece
@@ -422,7 +428,7 @@ __device__ __forceinline__ void segment_current_fix(const int S[4], const int E[
 }
 
 template <typename R, typename V>
-__device__ void push_record(const PushArgs<R, V> &a, uint32_t aidx, int wall, long pidx, int seg, const V v[kNV]) {
+__device__ __forceinline__ void push_record(const PushArgs<R, V> &a, uint32_t aidx, int wall, long pidx, int seg, const V v[kNV]) {
     const int slot = atomicAdd(a.ocount, 1);
     if (slot >= a.ocap) {
         atomicOr(a.status, (uint32_t)ST_OVERFLOW);
@@ -458,13 +464,39 @@ __device__ __forceinline__ void reduce_block(const PushArgs<R, V> &a, uint32_t r
         for (int o = 16; o > 0; o >>= 1) k2 += __shfl_down_sync(0xFFFFFFFFu, k2, o);
         if (lane == 0) s_ke[warp] = (double)k2;
     }
+    if constexpr (std::is_same<V, long long>::value) {
+        // MIXED: the four node charges are integers in [0, 2^24]; a warp's run
+        // sums at most 32 of them (< 2^29), so two share one 64-bit lane of
+        // the scan without carries: 8 scanned channels instead of 10
+        long long w[8];
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t ko = __shfl_up_sync(0xFFFFFFFFu, rkey, off);
+        for (int c = 0; c < 6; c++) w[c] = vals[c];
+        w[6] = vals[6] | (vals[7] << 32);
+        w[7] = vals[8] | (vals[9] << 32);
 #pragma unroll
-        for (int c = 0; c < kNV; c++) {
-            const V vo = shfl_up_v(vals[c], off);
-            if (lane >= off && ko == rkey) vals[c] += vo;
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t ko = __shfl_up_sync(0xFFFFFFFFu, rkey, off);
+#pragma unroll
+            for (int c = 0; c < 8; c++) {
+                const long long vo = shfl_up_v(w[c], off);
+                if (lane >= off && ko == rkey) w[c] += vo;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 6; c++) vals[c] = w[c];
+        vals[6] = w[6] & 0xFFFFFFFFll;
+        vals[7] = (long long)((unsigned long long)w[6] >> 32);
+        vals[8] = w[7] & 0xFFFFFFFFll;
+        vals[9] = (long long)((unsigned long long)w[7] >> 32);
+    } else {
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t ko = __shfl_up_sync(0xFFFFFFFFu, rkey, off);
+#pragma unroll
+            for (int c = 0; c < kNV; c++) {
+                const V vo = shfl_up_v(vals[c], off);
+                if (lane >= off && ko == rkey) vals[c] += vo;
+            }
         }
     }
     const uint32_t knext = __shfl_down_sync(0xFFFFFFFFu, rkey, 1);
@@ -767,7 +799,7 @@ __global__ void __launch_bounds__(kPushBlock) k_push_plain(const PushArgs<double
 // integer deposit (exact), accumulators per (tet, species)
 // ---------------------------------------------------------------------------
 template <int MODE>
-__global__ void __launch_bounds__(kPushBlock) k_push_mixed(const PushArgs<float, long long> a) {
+__global__ void __launch_bounds__(kPushBlock, 4) k_push_mixed(const PushArgs<float, long long> a) {
     const long i = (long)blockIdx.x * kPushBlock + threadIdx.x;
     const int n_alive = *a.d_n_alive;
     const bool active = i < n_alive;
