@@ -1014,18 +1014,28 @@ __global__ void __launch_bounds__(256) k_gather_nodes(int nn, const int *__restr
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= nn) return;
     double r = 0.0, w = 0.0;
-    for (int k = ptr[n]; k < ptr[n + 1]; k++) {
-        const int ref = idx[k];
-        const size_t t = (size_t)(ref / 4);
-        const int l = ref % 4;
-        if (std::is_same<V, double>::value) {
+    if constexpr (std::is_same<V, double>::value) {
+        for (int k = ptr[n]; k < ptr[n + 1]; k++) {
+            const int ref = idx[k];
+            const size_t t = (size_t)(ref / 4);
+            const int l = ref % 4;
             r += (double)tacc[t * kNV + 6 + l];
             w += (double)wacc[t * 4 + l];
-        } else {
-            for (int q = 0; q < nsp; q++) {
-                r += (double)tacc[(t * nsp + q) * kNV + 6 + l] * (sp.qw[q] * kFixNode);
-                w += (double)wacc[(t * nsp + q) * 4 + l] * (sp.qw[q] * kFixNode);
+        }
+    } else {
+        // MIXED: exact integer sums per species (24-bit charges, far from
+        // overflow), one conversion each
+        for (int q = 0; q < nsp; q++) {
+            long long ri = 0, wi = 0;
+            for (int k = ptr[n]; k < ptr[n + 1]; k++) {
+                const int ref = idx[k];
+                const size_t t = (size_t)(ref / 4);
+                const int l = ref % 4;
+                ri += tacc[(t * nsp + q) * kNV + 6 + l];
+                wi += wacc[(t * nsp + q) * 4 + l];
             }
+            r += (double)ri * (sp.qw[q] * kFixNode);
+            w += (double)wi * (sp.qw[q] * kFixNode);
         }
     }
     rho[n] = r;
