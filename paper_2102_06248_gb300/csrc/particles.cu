@@ -1122,6 +1122,53 @@ __global__ void k_load_particles(int n, int start, const double *__restrict__ x,
     id[q] = id0 + p;
 }
 
+// MIXED node charges, tet by tet: each (tet, species) reads its four node
+// charges and four wall charges once (contiguous) and adds them to per-(node,
+// species) integer sums.  Integer additions commute, so the sums do not depend
+// on the order of the atomics; a node gather would read one 8-byte value from
+// a different tet record per reference instead (7x the bytes, measured).
+__global__ void __launch_bounds__(256) k_scatter_node_charge(int nt, int nsp, const int4 *__restrict__ tnodes,
+                                                             const long long *__restrict__ tacc,
+                                                             const long long *__restrict__ wacc,
+                                                             unsigned long long *__restrict__ nacc) {
+    const int tq = blockIdx.x * blockDim.x + threadIdx.x;
+    if (tq >= nt * nsp) return;
+    const int t = tq / nsp, q = tq - t * nsp;
+    const longlong2 *a2 = reinterpret_cast<const longlong2 *>(tacc + (size_t)tq * kNV + 6);
+    const longlong2 *w2 = reinterpret_cast<const longlong2 *>(wacc + (size_t)tq * 4);
+    const longlong2 a01 = a2[0], a23 = a2[1], w01 = w2[0], w23 = w2[1];
+    const long long ca[4] = {a01.x, a01.y, a23.x, a23.y}, cw[4] = {w01.x, w01.y, w23.x, w23.y};
+    if ((ca[0] | ca[1] | ca[2] | ca[3] | cw[0] | cw[1] | cw[2] | cw[3]) == 0) return;
+    const int4 tn = tnodes[t];
+    const int nd[4] = {tn.x, tn.y, tn.z, tn.w};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        unsigned long long *o = nacc + 2 * ((size_t)nd[k] * nsp + q);
+        if (ca[k]) atomicAdd(o, (unsigned long long)ca[k]);
+        if (cw[k]) atomicAdd(o + 1, (unsigned long long)cw[k]);
+    }
+}
+
+// rho = sum_q qw_q 2^-24 charge_q, wall = wall_old + the same for wall hits;
+// the sums are cleared for the next step
+__global__ void __launch_bounds__(256) k_node_charge_convert(int nn, int nsp, SpeciesParams sp,
+                                                             unsigned long long *__restrict__ nacc,
+                                                             const double *__restrict__ wall_old,
+                                                             double *__restrict__ rho, double *__restrict__ wall) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= nn) return;
+    double r = 0.0, w = 0.0;
+    for (int q = 0; q < nsp; q++) {
+        unsigned long long *o = nacc + 2 * ((size_t)n * nsp + q);
+        r += (double)(long long)o[0] * (sp.qw[q] * kFixNode);
+        w += (double)(long long)o[1] * (sp.qw[q] * kFixNode);
+        o[0] = 0;
+        o[1] = 0;
+    }
+    rho[n] = r;
+    wall[n] = wall_old[n] + w;
+}
+
 // Injected particles appended to the current bank at [start, start + n)
 template <typename R>
 __global__ void k_inject_particles(int n, long start, const double *__restrict__ x, const double *__restrict__ v,
@@ -1631,7 +1678,14 @@ int reduce_to_entities(Sim *s) {
     const SpeciesParams sp = species_params(s);
     if (s->mixed) {
         { k_gather_edges<long long><<<(m->n_edges + 255) / 256, 256, 0, s->stream>>>(m->n_edges, m->e2t.rowptr.p, m->e2t.col.p, (const long long *)s->tacc.p, s->nsp, sp, s->g.p, s->dg.p, s->g_new.p); note_launch(); }
-        { k_gather_nodes<long long><<<(m->n_nodes + 255) / 256, 256, 0, s->stream>>>(m->n_nodes, m->n2t.rowptr.p, m->n2t.col.p, (const long long *)s->tacc.p, (const long long *)s->wacc.p, s->nsp, sp, s->wall_prev.p, s->rho.p, s->wall.p); note_launch(); }
+        if (!s->nacc.p) {
+            int rc = s->nacc.alloc(2 * (size_t)m->n_nodes * s->nsp);
+            if (rc) return rc;
+            FP_CUDA(cudaMemsetAsync(s->nacc.p, 0, sizeof(unsigned long long) * s->nacc.n, s->stream));
+        }
+        const int ntq = m->n_tets * s->nsp;
+        { k_scatter_node_charge<<<(ntq + 255) / 256, 256, 0, s->stream>>>(m->n_tets, s->nsp, m->tet_nodes.p, (const long long *)s->tacc.p, (const long long *)s->wacc.p, s->nacc.p); note_launch(); }
+        { k_node_charge_convert<<<(m->n_nodes + 255) / 256, 256, 0, s->stream>>>(m->n_nodes, s->nsp, sp, s->nacc.p, s->wall_prev.p, s->rho.p, s->wall.p); note_launch(); }
     } else {
         { k_gather_edges<double><<<(m->n_edges + 255) / 256, 256, 0, s->stream>>>(m->n_edges, m->e2t.rowptr.p, m->e2t.col.p, (const double *)s->tacc.p, 1, sp, s->g.p, s->dg.p, s->g_new.p); note_launch(); }
         { k_gather_nodes<double><<<(m->n_nodes + 255) / 256, 256, 0, s->stream>>>(m->n_nodes, m->n2t.rowptr.p, m->n2t.col.p, (const double *)s->tacc.p, (const double *)s->wacc.p, 1, sp, s->wall_prev.p, s->rho.p, s->wall.p); note_launch(); }

@@ -177,6 +177,7 @@ struct Sim {
     DevBuf<unsigned char> coef;     // 10 reals per tet
     DevBuf<double> tacc;            // kNV per tet
     DevBuf<double> wacc;            // 4 per tet
+    DevBuf<unsigned long long> nacc;   // MIXED: per (node, species) charge and wall sums, zero between steps
     DevBuf<double> bcar;            // 2 * kNV per push block
     DevBuf<uint32_t> bcar_key;      // 2 per push block
     DevBuf<double> ke_part;         // kinetic energy per push block
