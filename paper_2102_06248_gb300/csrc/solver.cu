@@ -631,9 +631,9 @@ __global__ void __launch_bounds__(kThreads) k_max_abs_sum(int n, const double *_
 // ---------------------------------------------------------------------------
 constexpr int kMaxPcgBlocks = 4 * kThreads;    // largest grid of the persistent PCG
 constexpr int kSmemSlices = 512;               // slice headers a block keeps in shared memory
-constexpr long kSpinLimit = 1L << 22;
-constexpr int kMaxOuter = 12;                 // refinement steps of a mixed-precision solve
-constexpr int kMaxInner = 400;                // FP32 iterations per refinement step         // about a second of polling
+constexpr long kSpinLimit = 1L << 22;          // about a second of polling
+constexpr int kMaxOuter = 12;                  // refinement steps of a mixed-precision solve
+constexpr int kMaxInner = 400;                 // FP32 iterations per refinement step
 
 __device__ __forceinline__ void red_release_add(unsigned int *p, unsigned int v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -966,12 +966,15 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int nb, const i
                              a.max_iters, o))
             goto timeout;
     } else {
-        // Iterative refinement: the FP64 residual b - A x is the judge; each
-        // correction A d = r / sigma is solved in FP32 (values and vectors) to
-        // a relative residual of inner_tol, and x += sigma d in FP64.  sigma,
-        // the RMS of the residual, keeps the FP32 vectors near 1: in SI units
-        // the residuals are far below 1 and their squares would reach the
-        // FP32 subnormal range.
+        // Iterative refinement: the FP64 residual b - A x is the judge (the
+        // same stopping rules as the FP64 solve: ||r|| <= tol ||b|| or
+        // max|r| <= abs_inf); each correction A d = r / sigma is solved in
+        // FP32 (values and vectors) and x += sigma d in FP64.  sigma, the RMS
+        // of the residual, keeps the FP32 vectors near 1: in SI units the
+        // residuals are far below 1 and their squares would reach the FP32
+        // subnormal range.  A correction solve reduces its residual by what
+        // the stopping rule still asks, with a factor 2 to spare (max|r| <=
+        // ||r||), but by at least inner_tol: no further than FP32 carries.
         const int n = a.n;
         int total = 0;
         bool failed = false;
@@ -981,29 +984,34 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int nb, const i
             double t[3];
             {
                 double v2[2] = {0.0, 0.0};
-                c.spmv(a.Av, a.x, [&](int i, double ax) {
+                unsigned long long mx = 0;
+                auto res_row = [&](int i, double ax) {
                     const double bi = a.b[i], ri = bi - ax;
                     a.r[i] = ri;
                     v2[0] = fma(ri, ri, v2[0]);
                     v2[1] = fma(bi, bi, v2[1]);
-                });
-                if (!grid_reduce<2>(a.gb, a.part, v2, 0ull, shv, shm, ++c.epoch, t, nb, bid)) goto timeout;
+                    mx = max(mx, abs_bits(ri));
+                };
+                c.spmv(a.Av, a.x, res_row);
+                if (!grid_reduce<2>(a.gb, a.part, v2, mx, shv, shm, ++c.epoch, t, nb, bid)) goto timeout;
             }
             rr = t[0];
             bb = t[1];
-            if (bb == 0.0 || rr <= tol2 * bb) break;
+            if (bb == 0.0 || rr <= tol2 * bb || t[2] <= abs_inf) break;
             if (total >= a.max_iters || outer >= kMaxOuter) {
                 failed = true;
                 break;
             }
+            const double need2 = max(tol2 * bb, abs_inf > 0.0 ? abs_inf * abs_inf : 0.0);
+            const double inner2 = max(a.inner_tol2, 0.25 * need2 / rr);
             const double sigma = sqrt(rr / n), inv = 1.0 / sigma;
             for (int sl = c.sl0; sl < a.n_slices; sl += c.sls) {
                 const int i = sl * 32 + c.lane;
                 if (i < n) a.b32[i] = (float)(a.r[i] * inv);
             }
             CgOut oi{0, false, 0.0, 0.0, 0.0};
-            if (!cg_core<float>(c, a.Av32, a.Dinv32, a.b32, a.d32, a.r32, a.u32, a.w32, a.p32, a.s32, true,
-                                a.inner_tol2, -1.0, min(kMaxInner, a.max_iters - total), oi))
+            if (!cg_core<float>(c, a.Av32, a.Dinv32, a.b32, a.d32, a.r32, a.u32, a.w32, a.p32, a.s32, true, inner2,
+                                -1.0, min(kMaxInner, a.max_iters - total), oi))
                 goto timeout;
             total += oi.iters;
             outer++;
@@ -1309,8 +1317,9 @@ PcgArgs pcg_args_truncated(Sim *s, int iters) {
 }
 
 // The Newmark solve.  MIXED refines in FP64 with FP32 correction solves
-// (each to 1e-5 relative); the FP64 residual ||b - A x|| <= cg_tol ||b|| is
-// the stopping rule in both precisions.
+// (each to what the stopping rule still asks, 1e-5 relative at most); the
+// FP64 residual ||b - A x|| <= cg_tol ||b|| is the stopping rule in both
+// precisions.
 PcgArgs pcg_args_newmark(Sim *s) {
     const Mesh *m = s->mesh;
     PcgArgs a = make_args(s, m->As, s->A_val.p, s->Dinv.p, s->rhs.p, s->x.p, s->cg_r.p, s->cg_z.p, s->cg_q.p,
@@ -1338,9 +1347,11 @@ PcgArgs pcg_args_newmark(Sim *s) {
 // max|d - L psi| <= completion_tol * max|rho + wall| (qmax, computed on the device)
 PcgArgs pcg_args_completion(Sim *s) {
     const Mesh *m = s->mesh;
-    return make_args(s, m->Ls, m->Ls_val.p, s->L_Dinv.p, s->l_b.p, s->l_x.p, s->l_r.p, s->l_z.p, s->l_q.p, s->l_p0.p,
-                     s->l_p1.p, s->l_part.p, &s->dctl.p->lap, 0.0, s->cfg.init_tol, 20000, &s->dctl.p->qmax,
-                     s->cfg.completion_tol, true, false);
+    // (in both precisions FP64: the completion is bound by the latency of its
+    // iterations, not by their arithmetic, and FP32 corrections took more)
+    return make_args(s, m->Ls, m->Ls_val.p, s->L_Dinv.p, s->l_b.p, s->l_x.p, s->l_r.p, s->l_z.p, s->l_q.p,
+                     s->l_p0.p, s->l_p1.p, s->l_part.p, &s->dctl.p->lap, 0.0, s->cfg.init_tol, 20000,
+                     &s->dctl.p->qmax, s->cfg.completion_tol, true, false);
 }
 
 int pcg_newmark(Sim *s) {
