@@ -634,6 +634,7 @@ constexpr int kSmemSlices = 512;               // slice headers a block keeps in
 constexpr long kSpinLimit = 1L << 22;          // about a second of polling
 constexpr int kMaxOuter = 12;                  // refinement steps of a mixed-precision solve
 constexpr int kMaxInner = 400;                 // FP32 iterations per refinement step
+constexpr int kVecSlices = 2;                  // slices a warp updates at once in the vector phase
 
 __device__ __forceinline__ void red_release_add(unsigned int *p, unsigned int v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -796,7 +797,8 @@ struct SolveCtx {
             wid = a->sw[sl];
         }
     }
-    // SpMV over the warp's slices with values Av: f(i, sum_j A_ij v_j)
+    // SpMV over the warp's slices with values Av: f(i, sum_j A_ij v_j, v_i)
+    // (the row's own v_i is read with the row's entries, not after them)
     template <typename T, typename F>
     __device__ __forceinline__ void spmv(const T *__restrict__ Av, const T *v, F f) const {
         const int *__restrict__ col = a->col;
@@ -806,12 +808,13 @@ struct SolveCtx {
         for (int k = 0, sl = sl0; sl < ns; k++, sl += sls) {
             int noff = 0, nwid = 0;
             if (sl + sls < ns) slice(k + 1, sl + sls, noff, nwid);
+            const int i = sl * 32 + lane;
+            const T vi = i < n ? v[i] : (T)0;
             T acc = 0;
             const int kb = off + lane;
 #pragma unroll 8
             for (int j = 0; j < wid; j++) acc = fma(Av[kb + 32 * j], __ldcg(v + col[kb + 32 * j]), acc);
-            const int i = sl * 32 + lane;
-            if (i < n) f(i, acc);
+            if (i < n) f(i, acc, vi);
             off = noff;
             wid = nwid;
         }
@@ -840,7 +843,7 @@ __device__ __forceinline__ bool cg_core(SolveCtx &c, const T *__restrict__ Av, c
     {
         T v[4] = {0, 0, 0, 0};   // gamma, rr, delta, bb
         unsigned long long mx = 0;
-        auto init_row = [&](int i, T ax) {
+        auto init_row = [&](int i, T ax, T) {
             const T bi = b[i], ri = bi - ax, ui = Dinv[i] * ri;
             if (x_zero) x[i] = 0;
             r[i] = ri;
@@ -852,14 +855,14 @@ __device__ __forceinline__ bool cg_core(SolveCtx &c, const T *__restrict__ Av, c
         };
         if (x_zero) {
             for (int sl = c.sl0; sl < a.n_slices; sl += c.sls)
-                if (sl * 32 + lane < n) init_row(sl * 32 + lane, (T)0);
+                if (sl * 32 + lane < n) init_row(sl * 32 + lane, (T)0, (T)0);
         } else {
             c.spmv(Av, x, init_row);
         }
         if (!grid_barrier(a.gb, ++c.epoch, c.nb)) return false;
-        c.spmv(Av, u, [&](int i, T au) {
+        c.spmv(Av, u, [&](int i, T au, T ui) {
             w[i] = au;
-            v[2] = fma(au, u[i], v[2]);
+            v[2] = fma(au, ui, v[2]);
         });
         const double vd[4] = {(double)v[0], (double)v[1], (double)v[2], (double)v[3]};
         if (!grid_reduce<4>(a.gb, a.part, vd, mx, c.shv, c.shm, ++c.epoch, t, c.nb, c.bid)) return false;
@@ -881,31 +884,53 @@ __device__ __forceinline__ bool cg_core(SolveCtx &c, const T *__restrict__ Av, c
         const bool first = iters == 0;
         const T al = (T)alpha, be = (T)beta;
         // ---- p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = D^-1 r ----
+        // kVecSlices of the warp's slices at a time, every load issued before
+        // the first store (the vectors may alias as far as the compiler knows)
         T v[3] = {0, 0, 0};   // gamma, rr, delta
         unsigned long long mx = 0;
-        for (int sl = c.sl0; sl < a.n_slices; sl += c.sls) {
-            const int i = sl * 32 + lane;
-            if (i < n) {
-                const T ui = u[i], wi = w[i];
-                const T pi = first ? ui : fma(be, p[i], ui);
-                const T si = first ? wi : fma(be, s[i], wi);
-                p[i] = pi;
-                s[i] = si;
-                x[i] = fma(al, pi, x[i]);
-                const T ri = fma(-al, si, r[i]);
-                const T un = Dinv[i] * ri;
-                r[i] = ri;
-                u[i] = un;
-                v[0] = fma(ri, un, v[0]);
-                v[1] = fma(ri, ri, v[1]);
-                if constexpr (kMax) mx = max(mx, abs_bits(ri));
+        for (int sl = c.sl0; sl < a.n_slices; sl += kVecSlices * c.sls) {
+            T q[kVecSlices][7];   // u w p s x r D^-1
+#pragma unroll
+            for (int h = 0; h < kVecSlices; h++) {
+#pragma unroll
+                for (int k = 0; k < 7; k++) q[h][k] = 0;
+                const int slh = sl + h * c.sls, i = slh * 32 + lane;
+                if (slh < a.n_slices && i < n) {
+                    q[h][0] = u[i];
+                    q[h][1] = w[i];
+                    if (!first) {
+                        q[h][2] = p[i];
+                        q[h][3] = s[i];
+                    }
+                    q[h][4] = x[i];
+                    q[h][5] = r[i];
+                    q[h][6] = Dinv[i];
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < kVecSlices; h++) {
+                const int slh = sl + h * c.sls, i = slh * 32 + lane;
+                if (slh < a.n_slices && i < n) {
+                    const T pi = first ? q[h][0] : fma(be, q[h][2], q[h][0]);
+                    const T si = first ? q[h][1] : fma(be, q[h][3], q[h][1]);
+                    const T ri = fma(-al, si, q[h][5]);
+                    const T un = q[h][6] * ri;
+                    p[i] = pi;
+                    s[i] = si;
+                    x[i] = fma(al, pi, q[h][4]);
+                    r[i] = ri;
+                    u[i] = un;
+                    v[0] = fma(ri, un, v[0]);
+                    v[1] = fma(ri, ri, v[1]);
+                    if constexpr (kMax) mx = max(mx, abs_bits(ri));
+                }
             }
         }
         if (!grid_barrier(a.gb, ++c.epoch, c.nb)) return false;
         // ---- w = A u ----
-        c.spmv(Av, u, [&](int i, T au) {
+        c.spmv(Av, u, [&](int i, T au, T ui) {
             w[i] = au;
-            v[2] = fma(au, u[i], v[2]);
+            v[2] = fma(au, ui, v[2]);
         });
         const double vd[3] = {(double)v[0], (double)v[1], (double)v[2]};
         if (!grid_reduce<3>(a.gb, a.part, vd, mx, c.shv, c.shm, ++c.epoch, t, c.nb, c.bid)) return false;
@@ -966,15 +991,14 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int nb, const i
                              a.max_iters, o))
             goto timeout;
     } else {
-        // Iterative refinement: the FP64 residual b - A x is the judge (the
-        // same stopping rules as the FP64 solve: ||r|| <= tol ||b|| or
-        // max|r| <= abs_inf); each correction A d = r / sigma is solved in
-        // FP32 (values and vectors) and x += sigma d in FP64.  sigma, the RMS
-        // of the residual, keeps the FP32 vectors near 1: in SI units the
-        // residuals are far below 1 and their squares would reach the FP32
-        // subnormal range.  A correction solve reduces its residual by what
-        // the stopping rule still asks, with a factor 2 to spare (max|r| <=
-        // ||r||), but by at least inner_tol: no further than FP32 carries.
+        // Iterative refinement: the FP64 residual b - A x is the judge; each
+        // correction A d = r / sigma is solved in FP32 (values and vectors) to
+        // a relative residual of inner_tol, and x += sigma d in FP64.  sigma,
+        // the RMS of the residual, keeps the FP32 vectors near 1: in SI units
+        // the residuals are far below 1 and their squares would reach the
+        // FP32 subnormal range.  (Stopping a correction solve at what the
+        // stopping rule still asks saves FP32 iterations but leaves the
+        // completion more to do, at a higher price per order of magnitude.)
         const int n = a.n;
         int total = 0;
         bool failed = false;
@@ -984,34 +1008,29 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int nb, const i
             double t[3];
             {
                 double v2[2] = {0.0, 0.0};
-                unsigned long long mx = 0;
-                auto res_row = [&](int i, double ax) {
+                c.spmv(a.Av, a.x, [&](int i, double ax, double) {
                     const double bi = a.b[i], ri = bi - ax;
                     a.r[i] = ri;
                     v2[0] = fma(ri, ri, v2[0]);
                     v2[1] = fma(bi, bi, v2[1]);
-                    mx = max(mx, abs_bits(ri));
-                };
-                c.spmv(a.Av, a.x, res_row);
-                if (!grid_reduce<2>(a.gb, a.part, v2, mx, shv, shm, ++c.epoch, t, nb, bid)) goto timeout;
+                });
+                if (!grid_reduce<2>(a.gb, a.part, v2, 0ull, shv, shm, ++c.epoch, t, nb, bid)) goto timeout;
             }
             rr = t[0];
             bb = t[1];
-            if (bb == 0.0 || rr <= tol2 * bb || t[2] <= abs_inf) break;
+            if (bb == 0.0 || rr <= tol2 * bb) break;
             if (total >= a.max_iters || outer >= kMaxOuter) {
                 failed = true;
                 break;
             }
-            const double need2 = max(tol2 * bb, abs_inf > 0.0 ? abs_inf * abs_inf : 0.0);
-            const double inner2 = max(a.inner_tol2, 0.25 * need2 / rr);
             const double sigma = sqrt(rr / n), inv = 1.0 / sigma;
             for (int sl = c.sl0; sl < a.n_slices; sl += c.sls) {
                 const int i = sl * 32 + c.lane;
                 if (i < n) a.b32[i] = (float)(a.r[i] * inv);
             }
             CgOut oi{0, false, 0.0, 0.0, 0.0};
-            if (!cg_core<float>(c, a.Av32, a.Dinv32, a.b32, a.d32, a.r32, a.u32, a.w32, a.p32, a.s32, true, inner2,
-                                -1.0, min(kMaxInner, a.max_iters - total), oi))
+            if (!cg_core<float>(c, a.Av32, a.Dinv32, a.b32, a.d32, a.r32, a.u32, a.w32, a.p32, a.s32, true,
+                                a.inner_tol2, -1.0, min(kMaxInner, a.max_iters - total), oi))
                 goto timeout;
             total += oi.iters;
             outer++;
@@ -1317,9 +1336,8 @@ PcgArgs pcg_args_truncated(Sim *s, int iters) {
 }
 
 // The Newmark solve.  MIXED refines in FP64 with FP32 correction solves
-// (each to what the stopping rule still asks, 1e-5 relative at most); the
-// FP64 residual ||b - A x|| <= cg_tol ||b|| is the stopping rule in both
-// precisions.
+// (each to 1e-5 relative); the FP64 residual ||b - A x|| <= cg_tol ||b|| is
+// the stopping rule in both precisions.
 PcgArgs pcg_args_newmark(Sim *s) {
     const Mesh *m = s->mesh;
     PcgArgs a = make_args(s, m->As, s->A_val.p, s->Dinv.p, s->rhs.p, s->x.p, s->cg_r.p, s->cg_z.p, s->cg_q.p,
