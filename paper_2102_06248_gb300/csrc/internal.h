@@ -111,10 +111,10 @@ struct HostStage {
     std::vector<int4> tet_nodes, tet_nbr, tet_face, f2e;
     std::vector<int> tet_edge, node_int, int_node;
     std::vector<int2> edge_nodes;
-    HostCsrStage e2t, n2t, H, L, e2f, n2e;
-    std::vector<double> H_val, L_val;
-    std::vector<int> sell_ptr, sell_w, sell_col, lsell_ptr, lsell_w, lsell_col;
-    std::vector<double> sell_M, sell_K, M_diag, K_diag, lsell_L, L_diag;
+    HostCsrStage e2t, n2t, L, e2f, n2e;
+    std::vector<double> L_val;
+    std::vector<int> sell_ptr, sell_w, sell_col, lsell_ptr, lsell_w, lsell_col, hsell_ptr, hsell_w, hsell_col;
+    std::vector<double> sell_M, sell_K, M_diag, K_diag, lsell_L, L_diag, hsell_H;
     std::vector<signed char> e2f_sgn, n2e_sgn;
 };
 
@@ -156,9 +156,9 @@ struct Mesh {
     DevSell As;
     DevBuf<double> M_val, K_val;     // in the SELL layout
     DevBuf<double> M_diag, K_diag;   // diagonals (interior rows)
-    // face mass [*mu^-1] on all faces
-    DevCsr H;
-    DevBuf<double> H_val;
+    // face mass [*mu^-1] on all faces (SELL-32, natural face order)
+    DevSell Hs;
+    DevBuf<double> Hs_val;
     // node Laplacian G^T M G on interior nodes (compact numbering, ordered by
     // row length): CSR and SELL-32 copies
     DevCsr L;

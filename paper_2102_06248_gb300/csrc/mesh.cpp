@@ -521,9 +521,10 @@ int build_mesh(const pic_mesh_desc *d, Mesh *m) {
         build_sell(pl, {&Lv}, H.lsell_ptr, H.lsell_w, H.lsell_col, out, dg);
         H.lsell_L = std::move(out[0]);
         H.L_diag = std::move(dg[0]);
+        // the face mass in natural face order (rows of 4 or 7 entries)
+        build_sell(ph, {&Hv}, H.hsell_ptr, H.hsell_w, H.hsell_col, out, dg);
+        H.hsell_H = std::move(out[0]);
     }
-    H.H = {std::move(ph.rowptr), std::move(ph.col)};
-    H.H_val = std::move(Hv);
     H.L = {std::move(pl.rowptr), std::move(pl.col)};
     H.L_val = std::move(Lv);
     H.node_int = std::move(node_int);
@@ -559,7 +560,12 @@ int mesh_upload(Mesh *m) {
         (rc = m->M_val.upload(H.sell_M)) || (rc = m->K_val.upload(H.sell_K)) || (rc = m->M_diag.upload(H.M_diag)) ||
         (rc = m->K_diag.upload(H.K_diag)))
         return rc;
-    if ((rc = csr(H.H, &m->H)) || (rc = m->H_val.upload(H.H_val))) return rc;
+    m->Hs.n_rows = m->n_faces;
+    m->Hs.n_slices = (int)H.hsell_w.size();
+    m->Hs.n_elems = H.hsell_ptr.empty() ? 0 : H.hsell_ptr.back();
+    if ((rc = m->Hs.ptr.upload(H.hsell_ptr)) || (rc = m->Hs.width.upload(H.hsell_w)) ||
+        (rc = m->Hs.col.upload(H.hsell_col)) || (rc = m->Hs_val.upload(H.hsell_H)))
+        return rc;
     if ((rc = csr(H.L, &m->L)) || (rc = m->L_val.upload(H.L_val))) return rc;
     m->Ls.n_rows = m->n_int_nodes;
     m->Ls.n_slices = (int)H.lsell_w.size();

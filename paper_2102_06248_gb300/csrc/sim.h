@@ -195,6 +195,7 @@ struct Sim {
     DevBuf<double> cg_r, cg_z, cg_p0, cg_p1, cg_q, cg_part;
     DevBuf<double> hb;              // face vector H (b + b_prev)
     DevBuf<double> w_edge;          // gradient completion: M t - d2 Gbar on interior edges
+    DevBuf<double> ev;              // interior-edge scratch: 2e + e' (RHS), t (completion)
     DevBuf<double> me;              // M x on interior edges
     // Laplacian solver (interior nodes)
     DevBuf<double> L_Dinv, l_x, l_b, l_r, l_z, l_p0, l_p1, l_q, l_part;

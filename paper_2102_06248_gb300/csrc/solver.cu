@@ -108,26 +108,6 @@ __device__ __forceinline__ double row_reduce(double s) {
 }
 
 
-// face vector hb = H (b + b')
-__global__ void __launch_bounds__(kThreads) k_face_hb(int n, const int *__restrict__ rp, const int *__restrict__ col,
-                                                      const double *__restrict__ Hv, const double *__restrict__ b,
-                                                      const double *__restrict__ bp, double *__restrict__ hb) {
-    const int lane = threadIdx.x % kLanes;
-    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < n; r0_ += gridDim.x * kRowsPerBlock) {
-        const int r = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
-        const bool rv = r < n;
-        const int kb = rv ? rp[r] : 0, kend = rv ? rp[r + 1] : 0;
-        double s = 0.0;
-        _Pragma("unroll 4") for (int k = kb + lane; k < kend; k += kLanes) {
-            const int j = col[k];
-            s += Hv[k] * (b[j] + bp[j]);
-        }
-        s = row_reduce(s);
-        if (rv && lane == 0) hb[r] = s;
-    }
-}
-
-
 // ---------------------------------------------------------------------------
 // SELL-32 kernels on the Newmark pattern (thread per row, warp per slice):
 // the 32 rows of a slice read their j-th entries as one coalesced 128-byte
@@ -143,63 +123,94 @@ constexpr int kSlicesPerBlock = kThreads / 32;
         const bool rv = r < (n);                                                                       \
         const int kb = sp[sl] + lane, kw = sw[sl];
 
+// face vector hb = H (b + b')
+__global__ void __launch_bounds__(kThreads) k_face_hb(int n, int n_slices, const int *__restrict__ sp,
+                                                      const int *__restrict__ sw, const int *__restrict__ col,
+                                                      const double *__restrict__ Hv, const double *__restrict__ b,
+                                                      const double *__restrict__ bp, double *__restrict__ hb) {
+    SELL_LOOP(n_slices, n)
+        double acc = 0.0;
+#pragma unroll 4
+        for (int j = 0; j < kw; j++) {
+            const int k = kb + 32 * j, c = col[k];
+            acc = fma(Hv[k], b[c] + bp[c], acc);
+        }
+        if (rv) hb[r] = acc;
+    }
+}
+
+// Per-row combinations the SELL kernels below gather, formed once per row
+// instead of once per stored entry (FP64 instructions are the scarce ones):
+// x = 2e - e' (the predictor) and y = 2e + e'.
+__global__ void k_rhs_pre(int n, const double *__restrict__ e, const double *__restrict__ ep, double *__restrict__ x,
+                          double *__restrict__ y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const double ei = e[i], epi = ep[i];
+        x[i] = fma(2.0, ei, -epi);
+        y[i] = fma(2.0, ei, epi);
+    }
+}
+
+// wave form: rhs = M (2e - e') - dt^2/4 K (2e + e') - (g^{n+1} - 2g^n + g^{n-1})
 __global__ void __launch_bounds__(kThreads) k_rhs_we_sell(int n, int n_slices, const int *__restrict__ sp,
                                                           const int *__restrict__ sw, const int *__restrict__ col,
                                                           const double *__restrict__ Mv, const double *__restrict__ Kv,
-                                                          double c4, const double *__restrict__ e,
-                                                          const double *__restrict__ ep, const double *__restrict__ gn,
+                                                          double c4, const double *__restrict__ x,
+                                                          const double *__restrict__ y, const double *__restrict__ gn,
                                                           const double *__restrict__ g, const double *__restrict__ gp,
-                                                          double *__restrict__ rhs, double *__restrict__ x) {
+                                                          double *__restrict__ rhs) {
     SELL_LOOP(n_slices, n)
         double sm = 0.0, sk = 0.0;
 #pragma unroll 4
         for (int j = 0; j < kw; j++) {
             const int k = kb + 32 * j;
             const int c = col[k];
-            const double ej = e[c], epj = ep[c];
-            sm += Mv[k] * (2.0 * ej - epj);
-            sk += Kv[k] * (2.0 * ej + epj);
+            sm = fma(Mv[k], x[c], sm);
+            sk = fma(Kv[k], y[c], sk);
         }
-        if (rv) {
-            rhs[r] = sm - c4 * sk - (gn[r] - 2.0 * g[r] + gp[r]);
-            x[r] = 2.0 * e[r] - ep[r];
-        }
+        if (rv) rhs[r] = sm - c4 * sk - (gn[r] - 2.0 * g[r] + gp[r]);
     }
 }
 
+// Maxwell form: rhs = M e' - dt^2/4 K (2e + e') + dt C^T H (b + b') - (G^{n+1} - G^{n-1})
 __global__ void __launch_bounds__(kThreads) k_rhs_mfem_sell(int n, int n_slices, const int *__restrict__ sp,
                                                             const int *__restrict__ sw, const int *__restrict__ col,
                                                             const double *__restrict__ Mv, const double *__restrict__ Kv,
-                                                            double c4, double dt, const double *__restrict__ e,
-                                                            const double *__restrict__ ep, const double *__restrict__ gn,
+                                                            double c4, double dt, const double *__restrict__ ep,
+                                                            const double *__restrict__ y, const double *__restrict__ gn,
                                                             const double *__restrict__ gp, const int *__restrict__ efp,
                                                             const int *__restrict__ efc,
                                                             const signed char *__restrict__ efs,
-                                                            const double *__restrict__ hb, double *__restrict__ rhs,
-                                                            double *__restrict__ x) {
+                                                            const double *__restrict__ hb, double *__restrict__ rhs) {
     SELL_LOOP(n_slices, n)
         double sm = 0.0, sk = 0.0, sc = 0.0;
 #pragma unroll 4
         for (int j = 0; j < kw; j++) {
             const int k = kb + 32 * j;
             const int c = col[k];
-            const double ej = e[c], epj = ep[c];
-            sm += Mv[k] * epj;
-            sk += Kv[k] * (2.0 * ej + epj);
+            sm = fma(Mv[k], ep[c], sm);
+            sk = fma(Kv[k], y[c], sk);
         }
         if (rv) {
             for (int k = efp[r]; k < efp[r + 1]; k++) sc += (double)efs[k] * hb[efc[k]];
             rhs[r] = sm - c4 * sk + dt * sc - (gn[r] - gp[r]);
-            x[r] = 2.0 * e[r] - ep[r];
         }
     }
 }
 
+// t = 2e - e' - x (wave form) or e' - x (Maxwell form), formed once per row
+__global__ void k_gc_t(int n, int form, const double *__restrict__ e, const double *__restrict__ ep,
+                       const double *__restrict__ x, double *__restrict__ t) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) t[i] = form == PIC_FORM_WE ? fma(2.0, e[i], -ep[i]) - x[i] : ep[i] - x[i];
+}
+
+// w = M t - (second difference of Gbar), t from k_gc_t
 __global__ void __launch_bounds__(kThreads) k_gc_w_sell(int n, int n_slices, const int *__restrict__ sp,
                                                         const int *__restrict__ sw, const int *__restrict__ col,
                                                         const double *__restrict__ Mv, int form,
-                                                        const double *__restrict__ e, const double *__restrict__ ep,
-                                                        const double *__restrict__ x, const double *__restrict__ gn,
+                                                        const double *__restrict__ t, const double *__restrict__ gn,
                                                         const double *__restrict__ g, const double *__restrict__ gp,
                                                         double *__restrict__ w) {
     SELL_LOOP(n_slices, n)
@@ -207,9 +218,7 @@ __global__ void __launch_bounds__(kThreads) k_gc_w_sell(int n, int n_slices, con
 #pragma unroll 4
         for (int j = 0; j < kw; j++) {
             const int k = kb + 32 * j;
-            const int c = col[k];
-            const double t = form == PIC_FORM_WE ? 2.0 * e[c] - ep[c] - x[c] : ep[c] - x[c];
-            s += Mv[k] * t;
+            s = fma(Mv[k], t[col[k]], s);
         }
         if (rv) w[r] = s - (form == PIC_FORM_WE ? gn[r] - 2.0 * g[r] + gp[r] : gn[r] - gp[r]);
     }
@@ -545,20 +554,20 @@ __global__ void __launch_bounds__(kThreads) k_diag_divb(int nt, const int4 *__re
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_diag_energy_b(int nf, const int *__restrict__ rp, const int *__restrict__ col,
+__global__ void __launch_bounds__(kThreads) k_diag_energy_b(int nf, int n_slices, const int *__restrict__ sp,
+                                                            const int *__restrict__ sw, const int *__restrict__ col,
                                                             const double *__restrict__ Hv, const double *__restrict__ b,
                                                             double *part, DiagDev *dg) {
     __shared__ double sh[kThreads / 32];
-    const int lane = threadIdx.x % kLanes;
     double acc[1] = {0.0};
-    for (int r0_ = (blockIdx.x * kRowsPerBlock + threadIdx.x / kLanes) & ~(kRowsPerWarp - 1); r0_ < nf; r0_ += gridDim.x * kRowsPerBlock) {
-        const int r = r0_ + ((threadIdx.x / kLanes) & (kRowsPerWarp - 1));
-        const bool rv = r < nf;
-        const int kb = rv ? rp[r] : 0, kend = rv ? rp[r + 1] : 0;
+    SELL_LOOP(n_slices, nf)
         double s = 0.0;
-        _Pragma("unroll 4") for (int k = kb + lane; k < kend; k += kLanes) s += Hv[k] * b[col[k]];
-        s = row_reduce(s);
-        if (rv && lane == 0) acc[0] += b[r] * s;
+#pragma unroll 4
+        for (int j = 0; j < kw; j++) {
+            const int k = kb + 32 * j;
+            s = fma(Hv[k], b[col[k]], s);
+        }
+        if (rv) acc[0] = fma(b[r], s, acc[0]);
     }
     block_sum<1>(acc, sh);
     if (arrive<1>(acc, part, &dg->count)) {
@@ -571,13 +580,22 @@ __global__ void __launch_bounds__(kThreads) k_diag_energy_b(int nf, const int *_
     }
 }
 
-// kinetic energy from the push kernel's per-block partials (fixed order)
-__global__ void __launch_bounds__(kThreads) k_sum_ke(int nb, const double *__restrict__ kp, DiagDev *dg) {
+// kinetic energy from the push kernel's per-block partials (fixed order:
+// block b of this grid adds partials b*kThreads + t, b*kThreads + t +
+// grid*kThreads, ...; the last block adds the blocks' sums in block order)
+__global__ void __launch_bounds__(kThreads) k_sum_ke(int nb, const double *__restrict__ kp, double *part, DiagDev *dg) {
     __shared__ double sh[kThreads / 32];
     double acc[1] = {0.0};
-    for (int b = threadIdx.x; b < nb; b += kThreads) acc[0] += kp[b];
+    for (int b = blockIdx.x * kThreads + threadIdx.x; b < nb; b += gridDim.x * kThreads) acc[0] += kp[b];
     block_sum<1>(acc, sh);
-    if (threadIdx.x == 0) dg->energy_k = acc[0];
+    if (arrive<1>(acc, part, &dg->count)) {
+        double tot[1];
+        grid_combine<1, false>(tot, part, sh);
+        if (threadIdx.x == 0) {
+            dg->energy_k = tot[0];
+            dg->count = 0;
+        }
+    }
 }
 
 // max_n |a_n + b_n| (deterministic; max is order-free)
@@ -797,10 +815,13 @@ struct SolveCtx {
             wid = a->sw[sl];
         }
     }
-    // SpMV over the warp's slices with values Av: f(i, sum_j A_ij v_j, v_i)
-    // (the row's own v_i is read with the row's entries, not after them)
+    // SpMV one slice at a time (unrolled by 8), f(i, sum_j A_ij v_j, v_i):
+    // the form of the FP64 PCG.  (The SpMV forms below were chosen by
+    // measurement, each kernel with the form it ran fastest in: the code the
+    // compiler makes of these loops at 64 registers is sensitive to their
+    // shape, by up to 40% in time.)
     template <typename T, typename F>
-    __device__ __forceinline__ void spmv(const T *__restrict__ Av, const T *v, F f) const {
+    __device__ __forceinline__ void spmv1(const T *__restrict__ Av, const T *v, F f) const {
         const int *__restrict__ col = a->col;
         const int n = a->n, ns = a->n_slices;
         int off = 0, wid = 0;
@@ -817,6 +838,40 @@ struct SolveCtx {
             if (i < n) f(i, acc, vi);
             off = noff;
             wid = nwid;
+        }
+    }
+    // SpMV over the warp's slices with values Av: f(i, sum_j A_ij v_j, v_i):
+    // the form of the MIXED refinement (FP32 corrections, FP64 residuals).
+    // Two of the warp's slices at a time (two independent chains of loads in
+    // flight); the row's own v_i is read with the row's entries.
+    template <typename T, typename F>
+    __device__ __forceinline__ void spmv(const T *__restrict__ Av, const T *v, F f) const {
+        const int *__restrict__ col = a->col;
+        const int n = a->n, ns = a->n_slices;
+        for (int k = 0, sl = sl0; sl < ns; k += 2, sl += 2 * sls) {
+            const bool hb = sl + sls < ns;
+            int offa, wida, offb = 0, widb = 0;
+            slice(k, sl, offa, wida);
+            if (hb) slice(k + 1, sl + sls, offb, widb);
+            const int ia = sl * 32 + lane, ib = (sl + sls) * 32 + lane;
+            const T va = ia < n ? v[ia] : (T)0;
+            const T vb = hb && ib < n ? v[ib] : (T)0;
+            T acca = 0, accb = 0;
+            const int ka = offa + lane, kb = offb + lane, wmin = min(wida, widb);
+            // joint unroll: 4 for FP32 values, 8 for FP64 (measured best of 2, 4, 8)
+            constexpr int kU = std::is_same<T, float>::value ? 4 : 8;
+            int j = 0;
+#pragma unroll kU
+            for (; j < wmin; j++) {
+                acca = fma(Av[ka + 32 * j], __ldcg(v + col[ka + 32 * j]), acca);
+                accb = fma(Av[kb + 32 * j], __ldcg(v + col[kb + 32 * j]), accb);
+            }
+#pragma unroll 4
+            for (int ja = j; ja < wida; ja++) acca = fma(Av[ka + 32 * ja], __ldcg(v + col[ka + 32 * ja]), acca);
+#pragma unroll 4
+            for (int jb = j; jb < widb; jb++) accb = fma(Av[kb + 32 * jb], __ldcg(v + col[kb + 32 * jb]), accb);
+            if (ia < n) f(ia, acca, va);
+            if (hb && ib < n) f(ib, accb, vb);
         }
     }
 };
@@ -857,13 +912,16 @@ __device__ __forceinline__ bool cg_core(SolveCtx &c, const T *__restrict__ Av, c
             for (int sl = c.sl0; sl < a.n_slices; sl += c.sls)
                 if (sl * 32 + lane < n) init_row(sl * 32 + lane, (T)0, (T)0);
         } else {
-            c.spmv(Av, x, init_row);
+            if constexpr (std::is_same<T, double>::value) c.spmv1(Av, x, init_row);
+            else c.spmv(Av, x, init_row);
         }
         if (!grid_barrier(a.gb, ++c.epoch, c.nb)) return false;
-        c.spmv(Av, u, [&](int i, T au, T ui) {
+        auto wrow = [&](int i, T au, T ui) {
             w[i] = au;
             v[2] = fma(au, ui, v[2]);
-        });
+        };
+        if constexpr (std::is_same<T, double>::value) c.spmv1(Av, u, wrow);
+        else c.spmv(Av, u, wrow);
         const double vd[4] = {(double)v[0], (double)v[1], (double)v[2], (double)v[3]};
         if (!grid_reduce<4>(a.gb, a.part, vd, mx, c.shv, c.shm, ++c.epoch, t, c.nb, c.bid)) return false;
     }
@@ -928,10 +986,12 @@ __device__ __forceinline__ bool cg_core(SolveCtx &c, const T *__restrict__ Av, c
         }
         if (!grid_barrier(a.gb, ++c.epoch, c.nb)) return false;
         // ---- w = A u ----
-        c.spmv(Av, u, [&](int i, T au, T ui) {
+        auto wrow = [&](int i, T au, T ui) {
             w[i] = au;
             v[2] = fma(au, ui, v[2]);
-        });
+        };
+        if constexpr (std::is_same<T, double>::value) c.spmv1(Av, u, wrow);
+        else c.spmv(Av, u, wrow);
         const double vd[3] = {(double)v[0], (double)v[1], (double)v[2]};
         if (!grid_reduce<3>(a.gb, a.part, vd, mx, c.shv, c.shm, ++c.epoch, t, c.nb, c.bid)) return false;
         iters++;
@@ -950,7 +1010,11 @@ __device__ __forceinline__ bool cg_core(SolveCtx &c, const T *__restrict__ Av, c
     return true;
 }
 
-// the whole solve, run by block `bid` of the nb blocks that own it
+// the whole solve, run by block `bid` of the nb blocks that own it: FP64
+// PCG (REFINE false) or the MIXED refinement (REFINE true, a.refine set).
+// The two are separate kernels so that each gets the register allocation of
+// its own loops.
+template <bool REFINE>
 __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int nb, const int bid) {
     __shared__ double shv[4 * kThreads];
     __shared__ unsigned long long shm[kThreads];
@@ -986,7 +1050,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int nb, const i
     }
     CgOut o{0, false, 0.0, 0.0, 0.0};
     int outer = 0;
-    if (!a.refine) {
+    if constexpr (!REFINE) {
         if (!cg_core<double>(c, a.Av, a.Dinv, a.b, a.x, a.r, a.u, a.w, a.p, a.s, a.x_zero != 0, tol2, abs_inf,
                              a.max_iters, o))
             goto timeout;
@@ -1067,9 +1131,13 @@ timeout:
 }
 
 // one solve per launch (its arguments passed by value)
-__global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(const PcgArgs a) { pcg_body(a, gridDim.x, blockIdx.x); }
+template <bool REFINE>
+__global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(const PcgArgs a) {
+    pcg_body<REFINE>(a, gridDim.x, blockIdx.x);
+}
 
-// several solves per launch: run r owns blocks [block0, block0 + blocks)
+// several solves of one kind per launch: run r owns blocks [block0, block0 + blocks)
+template <bool REFINE>
 __global__ void __launch_bounds__(kThreads, 4) k_pcg_batched(const __grid_constant__ PcgBatch<kMaxBatchRuns> B) {
     // the block's run, copied to shared memory: read through a dynamic index
     // in parameter space, the arguments made the solve half as fast again
@@ -1080,7 +1148,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_pcg_batched(const __grid_consta
         sa = B.run[ri];
     }
     __syncthreads();
-    pcg_body(sa, sa.blocks, (int)blockIdx.x - sa.block0);
+    pcg_body<REFINE>(sa, sa.blocks, (int)blockIdx.x - sa.block0);
 }
 
 int grid_for_rows(int n) { return std::max(1, std::min(kMaxBlocks, (n + kRowsPerBlock - 1) / kRowsPerBlock)); }
@@ -1128,7 +1196,7 @@ int solver_alloc(Sim *s) {
         if ((rc = v->alloc(nn))) return rc;
         FP_CUDA(cudaMemset(v->p, 0, sizeof(double) * nn));
     }
-    DevBuf<double> *int_vecs[] = {&s->Dinv, &s->cg_r, &s->cg_z, &s->cg_p0, &s->cg_p1, &s->cg_q, &s->w_edge, &s->me};
+    DevBuf<double> *int_vecs[] = {&s->Dinv, &s->cg_r, &s->cg_z, &s->cg_p0, &s->cg_p1, &s->cg_q, &s->w_edge, &s->me, &s->ev};
     for (auto *v : int_vecs) {
         if ((rc = v->alloc(std::max(ni, 1)))) return rc;
         FP_CUDA(cudaMemset(v->p, 0, sizeof(double) * std::max(ni, 1)));
@@ -1168,12 +1236,12 @@ int newmark_rhs(Sim *s) {
     const double dt = s->cfg.dt, c4 = 0.25 * dt * dt;
     const DevSell &A = m->As;
     const int gs = grid_for_slices(A.n_slices);
+    { k_rhs_pre<<<(ni + 255) / 256, 256, 0, s->stream>>>(ni, s->e.p, s->e_prev.p, s->x.p, s->ev.p); note_launch(); }
     if (s->cfg.form == PIC_FORM_WE) {
-        { k_rhs_we_sell<<<gs, kThreads, 0, s->stream>>>(ni, A.n_slices, A.ptr.p, A.width.p, A.col.p, m->M_val.p, m->K_val.p, c4, s->e.p, s->e_prev.p, s->g_new.p, s->g.p, s->g_prev.p, s->rhs.p, s->x.p); note_launch(); }
+        { k_rhs_we_sell<<<gs, kThreads, 0, s->stream>>>(ni, A.n_slices, A.ptr.p, A.width.p, A.col.p, m->M_val.p, m->K_val.p, c4, s->x.p, s->ev.p, s->g_new.p, s->g.p, s->g_prev.p, s->rhs.p); note_launch(); }
     } else {
-        { k_face_hb<<<grid_for_rows(m->n_faces), kThreads, 0, s->stream>>>(m->n_faces, m->H.rowptr.p, m->H.col.p,
-                                                                         m->H_val.p, s->b.p, s->b_prev.p, s->hb.p); note_launch(); }
-        { k_rhs_mfem_sell<<<gs, kThreads, 0, s->stream>>>(ni, A.n_slices, A.ptr.p, A.width.p, A.col.p, m->M_val.p, m->K_val.p, c4, dt, s->e.p, s->e_prev.p, s->g_new.p, s->g_prev.p, m->e2f.rowptr.p, m->e2f.col.p, m->e2f_sgn.p, s->hb.p, s->rhs.p, s->x.p); note_launch(); }
+        { k_face_hb<<<grid_for_slices(m->Hs.n_slices), kThreads, 0, s->stream>>>(m->n_faces, m->Hs.n_slices, m->Hs.ptr.p, m->Hs.width.p, m->Hs.col.p, m->Hs_val.p, s->b.p, s->b_prev.p, s->hb.p); note_launch(); }
+        { k_rhs_mfem_sell<<<gs, kThreads, 0, s->stream>>>(ni, A.n_slices, A.ptr.p, A.width.p, A.col.p, m->M_val.p, m->K_val.p, c4, dt, s->e_prev.p, s->ev.p, s->g_new.p, s->g_prev.p, m->e2f.rowptr.p, m->e2f.col.p, m->e2f_sgn.p, s->hb.p, s->rhs.p); note_launch(); }
     }
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
@@ -1184,7 +1252,7 @@ int newmark_rhs(Sim *s) {
 // (queried once per device and kept: no runtime queries while a stream is
 // being captured)
 constexpr int kMaxDevices = 64;
-template <bool BATCHED>
+template <bool BATCHED, bool REFINE>
 static int coop_per_sm() {
     static int cache[kMaxDevices];   // 0: not queried, -1: unavailable
     int dev = 0, coop = 0, per_sm = 0;
@@ -1192,8 +1260,8 @@ static int coop_per_sm() {
     if (cache[dev]) return std::max(cache[dev], 0);
     cache[dev] = -1;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
-    cudaError_t e = BATCHED ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_batched, kThreads, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent, kThreads, 0);
+    cudaError_t e = BATCHED ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_batched<REFINE>, kThreads, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<REFINE>, kThreads, 0);
     if (e != cudaSuccess) return 0;
     cache[dev] = per_sm > 0 ? per_sm : -1;
     return std::max(per_sm, 0);
@@ -1266,8 +1334,14 @@ int launch_pcg_runs(PcgArgs *runs, int n_runs, int blocks_per_sm, cudaStream_t s
         set_error("at most " + std::to_string(kMaxBatchRuns) + " solves per persistent launch");
         return PIC_ERR_INVALID_ARG;
     }
-    const bool one = n_runs == 1;
-    int per_sm = one ? coop_per_sm<false>() : coop_per_sm<true>();
+    const bool one = n_runs == 1, refine = runs[0].refine != 0;
+    for (int r = 1; r < n_runs; r++)
+        if ((runs[r].refine != 0) != refine) {
+            set_error("the solves of one persistent launch must all be FP64 or all be refinements");
+            return PIC_ERR_INVALID_ARG;
+        }
+    int per_sm = one ? (refine ? coop_per_sm<false, true>() : coop_per_sm<false, false>())
+                     : (refine ? coop_per_sm<true, true>() : coop_per_sm<true, false>());
     if (per_sm <= 0) {
         set_error("the persistent PCG needs a device with cooperative launch");
         return PIC_ERR_CUDA;
@@ -1283,10 +1357,12 @@ int launch_pcg_runs(PcgArgs *runs, int n_runs, int blocks_per_sm, cudaStream_t s
     if (one) {
         PcgArgs a1 = all.run[0];
         void *args[] = {&a1};
-        FP_CUDA(cudaLaunchCooperativeKernel((const void *)k_pcg_persistent, G, kThreads, args, 0, st));
+        const void *k = refine ? (const void *)k_pcg_persistent<true> : (const void *)k_pcg_persistent<false>;
+        FP_CUDA(cudaLaunchCooperativeKernel(k, G, kThreads, args, 0, st));
     } else {
         void *args[] = {&all};
-        FP_CUDA(cudaLaunchCooperativeKernel((const void *)k_pcg_batched, G, kThreads, args, 0, st));
+        const void *k = refine ? (const void *)k_pcg_batched<true> : (const void *)k_pcg_batched<false>;
+        FP_CUDA(cudaLaunchCooperativeKernel(k, G, kThreads, args, 0, st));
     }
     note_launch();
     return PIC_OK;
@@ -1427,7 +1503,8 @@ int gc_prepare(Sim *s) {
     const Mesh *m = s->mesh;
     const int ni = m->n_int_edges, nin = m->n_int_nodes;
     if (ni == 0 || nin == 0) return PIC_OK;
-    { k_gc_w_sell<<<grid_for_slices(m->As.n_slices), kThreads, 0, s->stream>>>(ni, m->As.n_slices, m->As.ptr.p, m->As.width.p, m->As.col.p, m->M_val.p, s->cfg.form, s->e.p, s->e_prev.p, s->x.p, s->g_new.p, s->g.p, s->g_prev.p, s->w_edge.p); note_launch(); }
+    { k_gc_t<<<(ni + 255) / 256, 256, 0, s->stream>>>(ni, s->cfg.form, s->e.p, s->e_prev.p, s->x.p, s->ev.p); note_launch(); }
+    { k_gc_w_sell<<<grid_for_slices(m->As.n_slices), kThreads, 0, s->stream>>>(ni, m->As.n_slices, m->As.ptr.p, m->As.width.p, m->As.col.p, m->M_val.p, s->cfg.form, s->ev.p, s->g_new.p, s->g.p, s->g_prev.p, s->w_edge.p); note_launch(); }
     { k_gc_d<<<(nin + 255) / 256, 256, 0, s->stream>>>(nin, m->int_node.p, m->n2e.rowptr.p, m->n2e.col.p, m->n2e_sgn.p,
                                                      ni, s->w_edge.p, s->l_b.p); note_launch(); }
     // stopping threshold: completion_tol * max_n |rho_n + wall_n| (charge at t^{n+1})
@@ -1475,9 +1552,8 @@ int compute_diagnostics(Sim *s) {
         s->wall.p, s->wall_prev.p, s->rho_bg.p, m->node_bnd.p, s->diag_part.p, dg); note_launch(); }
     { k_diag_divb<<<grid_for_elems(m->n_tets), kThreads, 0, s->stream>>>(m->n_tets, m->tet_face.p, m->tet_sign.p, s->b.p,
                                                                        s->diag_part.p, dg); note_launch(); }
-    { k_diag_energy_b<<<grid_for_rows(m->n_faces), kThreads, 0, s->stream>>>(m->n_faces, m->H.rowptr.p, m->H.col.p,
-                                                                           m->H_val.p, s->b.p, s->diag_part.p, dg); note_launch(); }
-    { k_sum_ke<<<1, kThreads, 0, s->stream>>>(s->last_push_blocks, s->ke_part.p, dg); note_launch(); }
+    { k_diag_energy_b<<<grid_for_slices(m->Hs.n_slices), kThreads, 0, s->stream>>>(m->n_faces, m->Hs.n_slices, m->Hs.ptr.p, m->Hs.width.p, m->Hs.col.p, m->Hs_val.p, s->b.p, s->diag_part.p, dg); note_launch(); }
+    { k_sum_ke<<<grid_for_elems(s->last_push_blocks), kThreads, 0, s->stream>>>(s->last_push_blocks, s->ke_part.p, s->diag_part.p, dg); note_launch(); }
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
 }
