@@ -39,12 +39,13 @@ from paper_2102_06248_gb300 import workloads as W  # noqa: E402
 METRIC = "particle-steps/s (gather+push+deposit) and step time vs plain FP64 GPU path"
 FALLBACK_HBM_GBS = 6800.0
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (non-tensor) nominal rate
-# DRAM bytes over algorithmic bytes of the Newmark k_pcg_persistent launch, from
-# the ncu capture summarised in profiles/pcg_persistent_plasma_ball_64.md
-# (MIXED refinement: 21.350 GB measured for 60 FP32 + 2 FP64 iterations whose
-# algorithmic bytes are 21.233 GB; PLAIN: 28.588 GB for 50 iterations, 27.525 GB)
-TRAFFIC_RATIO_MIXED = 21.350 / 21.233
-TRAFFIC_RATIO_PLAIN = 28.588 / 27.525
+# DRAM bytes over algorithmic bytes of the MIXED Newmark launch
+# (k_pcg_persistent<1>), from the ncu capture summarised in
+# profiles/pcg_persistent_plasma_ball_64.md: 21.207 GB measured for 60 FP32 +
+# 2 FP64 iterations whose algorithmic bytes are 21.233 GB.  The FP64 Newmark
+# form has no capture of its current code: its traffic is reported as null.
+TRAFFIC_RATIO_MIXED = 21.206904 / 21.232650
+TRAFFIC_RATIO_PLAIN = None
 
 
 def dt_table():
@@ -52,22 +53,27 @@ def dt_table():
         return json.load(f)
 
 
+def workload_desc(name: str, cells: int, per_species: int) -> str:
+    if name == "plasma_ball":
+        return (f"plasma_ball {cells}^3 Kuhn cells ({6 * cells ** 3} tets, 20% jitter), "
+                f"{per_species} e- + {per_species} p+ Gaussian sphere, Te=10 eV, Ti=0.1 eV, "
+                f"WE Newmark, Boris, dt=4xCFL, Jacobi-PCG 1e-10, PEC walls")
+    if name == "thermal_cube":
+        return (f"thermal_cube {cells}^3 Kuhn cells, {per_species} e- Maxwellian 0.01c, "
+                f"B0=0.1 T, WE Newmark, Boris, dt=2xCFL, Jacobi-PCG 1e-10")
+    raise SystemExit(f"unknown workload {name}")
+
+
 def make_workload(name: str, cells: int, per_species: int):
     tab = dt_table()
+    desc = workload_desc(name, cells, per_species)
     if name == "plasma_ball":
         wl = W.plasma_ball(n_cells=cells, n_per_species=per_species)
         kappa = tab["kuhn_lattice_16^3_jitter0.2"]["kappa"]
         dt = wl.dt_cfl_multiple * kappa * wl.mesh.h / W.C0
-        desc = (f"plasma_ball {cells}^3 Kuhn cells ({6 * cells ** 3} tets, 20% jitter), "
-                f"{per_species} e- + {per_species} p+ Gaussian sphere, Te=10 eV, Ti=0.1 eV, "
-                f"WE Newmark, Boris, dt=4xCFL, Jacobi-PCG 1e-10, PEC walls")
-    elif name == "thermal_cube":
+    else:
         wl = W.thermal_plasma_cube(n_cells=cells, n_particles=per_species)
         dt = 2.0 * tab["thermal_plasma_cube_6^3"]["dt_cfl_s"] * (6.0 / cells)
-        desc = (f"thermal_cube {cells}^3 Kuhn cells, {per_species} e- Maxwellian 0.01c, "
-                f"B0=0.1 T, WE Newmark, Boris, dt=2xCFL, Jacobi-PCG 1e-10")
-    else:
-        raise SystemExit(f"unknown workload {name}")
     return wl, dt, desc
 
 
@@ -461,7 +467,7 @@ def gpu_arm(args):
         else:
             kernel = "k_pcg_persistent (Newmark PCG, Chronopoulos-Gear, SELL-32)"
             alg = iters_per_launch * pcg_iter_bytes(mesh.n_int_edges, nnz_A)
-            traffic = alg * TRAFFIC_RATIO_PLAIN
+            traffic = alg * TRAFFIC_RATIO_PLAIN if TRAFFIC_RATIO_PLAIN else None
             flops = iters_per_launch * pcg_iter_flops(mesh.n_int_edges, nnz_A)
             fp64_tf = flops / (avg_ms / 1e3) / 1e12
             fp64 = {"achieved_tflops": round(fp64_tf, 4), "peak_tflops": FP64_NOMINAL_TFLOPS,
@@ -574,11 +580,12 @@ def reference_arm(args):
     el = time.perf_counter() - t0
     n = wl.n_particles
     value = n * args.steps / el
-    sample = f"{desc}; scaled copy of the GPU workload ({cells}^3 cells, {n} particles), single thread"
+    sample = (f"{desc}: each step one step of this scaled copy of the workload (same density and dt recipe, "
+              f"{cells}^3 cells, {n} particles), single thread")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": sample},
+            "data": "synthetic", "config": {"workload": workload_desc(args.workload, args.cells, args.particles)},
             "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
