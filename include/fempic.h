@@ -155,7 +155,8 @@ typedef struct {
     double completion_tol;   /* the gradient-subspace completion of each Newmark solve stops
                                 when its defect is <= completion_tol * max|rho + wall| (1e-16) */
     int32_t walk_cap;        /* max tets one particle visits in one step (64) */
-    int32_t solver_blocks_per_sm; /* blocks per SM of the persistent PCG (0: as many as fit) */
+    int32_t solver_blocks_per_sm; /* blocks per SM of the persistent PCG (0: as many as fit for the
+                                     Newmark solve, two for the latency-bound completion) */
     int32_t max_species;     /* species slots (4) */
     int32_t profile;         /* 1: time the phases of every step with CUDA events (0) */
     void *stream;            /* cudaStream_t to run on; NULL = default stream */

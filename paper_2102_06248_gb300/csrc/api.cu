@@ -166,8 +166,12 @@ int one_step(Sim *s, bool fields) {
     prof_begin(s, PH_COMPLETION);
     if ((rc = gc_prepare(s))) return rc;
     {
+        // the completion is latency-bound: two blocks per SM, unless the
+        // configuration fixes the count (1, 2, 3, 4 per SM measured 4.25,
+        // 3.40, 3.49, 3.52 ms on the 64^3 plasma-ball mesh)
         PcgArgs a = pcg_args_completion(s);
-        if ((rc = launch_pcg_runs(&a, 1, s->cfg.solver_blocks_per_sm, s->stream))) return rc;
+        const int per_sm = s->cfg.solver_blocks_per_sm ? s->cfg.solver_blocks_per_sm : 2;
+        if ((rc = launch_pcg_runs(&a, 1, per_sm, s->stream))) return rc;
     }
     if ((rc = step_fields_end(s))) return rc;
     rc = read_control(s);

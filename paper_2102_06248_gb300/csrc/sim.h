@@ -235,7 +235,6 @@ int validate_particles(Sim *s, int n_new, int start);
 int solver_alloc(Sim *s);
 int newmark_rhs(Sim *s);
 int pcg_newmark(Sim *s);
-int gradient_completion(Sim *s);
 int laplacian_solve(Sim *s, const double *rhs_nodes, double *x_nodes, double tol, const double *abs_src,
                     double abs_factor);
 int faraday_update(Sim *s);

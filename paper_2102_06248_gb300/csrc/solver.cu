@@ -1522,16 +1522,6 @@ int gc_finish(Sim *s) {
     return PIC_OK;
 }
 
-int gradient_completion(Sim *s) {
-    const Mesh *m = s->mesh;
-    if (m->n_int_edges == 0 || m->n_int_nodes == 0) return PIC_OK;
-    int rc;
-    if ((rc = gc_prepare(s))) return rc;
-    PcgArgs a = pcg_args_completion(s);
-    if ((rc = launch_pcg_runs(&a, 1, s->cfg.solver_blocks_per_sm, s->stream))) return rc;
-    return gc_finish(s);
-}
-
 int faraday_update(Sim *s) {
     const Mesh *m = s->mesh;
     { k_faraday<<<(m->n_faces + 255) / 256, 256, 0, s->stream>>>(m->n_faces, m->f2e.p, s->cfg.form, s->cfg.dt, s->x.p,
