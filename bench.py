@@ -92,26 +92,75 @@ def measured_peak():
 
 
 class ClockSampler:
+    """SM clock, power and clock-event reasons of one GPU while the timed region
+    runs: NVML (the driver's libnvidia-ml, public API through ctypes) polled
+    every 2 ms from a thread, else nvidia-smi every 50 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # nvmlClocksEventReason bits (nvml.h)
+    REASON_BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+                   "hw_thermal_slowdown": 0x40, "hw_power_brake_slowdown": 0x80}
 
     def __init__(self, gpu: int):
         self.gpu = gpu
         self.proc = None
+        self.thread = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu}.csv")
+        self.nvml = None
+        try:
+            import ctypes
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() == 0:
+                h = ctypes.c_void_p()
+                if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(gpu), ctypes.byref(h)) == 0:
+                    self.nvml, self.handle, self.ct = lib, h, ctypes
+        except Exception:
+            self.nvml = None
+
+    def _poll(self):
+        ct, lib, h = self.ct, self.nvml, self.handle
+        clk, mx, mw, rs = ct.c_uint(), ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        lib.nvmlDeviceGetMaxClockInfo(h, 1, ct.byref(mx))
+        while not self.stop_flag:
+            if lib.nvmlDeviceGetClockInfo(h, 1, ct.byref(clk)) == 0:      # NVML_CLOCK_SM
+                lib.nvmlDeviceGetPowerUsage(h, ct.byref(mw))
+                get_reasons(h, ct.byref(rs))
+                self.samples.append((clk.value, mx.value, mw.value / 1000.0, rs.value))
+            time.sleep(0.002)
 
     def start(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        if self.nvml is not None:
+            import threading
+            self.samples, self.stop_flag = [], False
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
     def stop(self):
+        if self.thread is not None:
+            self.stop_flag = True
+            self.thread.join(timeout=5)
+            sm = [c for c, _, _, _ in self.samples]
+            smax = [m for _, m, _, _ in self.samples]
+            reasons = {n for _, _, _, r in self.samples for n, bit in self.REASON_BITS.items() if r & bit}
+            with open(self.path, "w") as fh:
+                fh.write("sm_mhz,max_sm_mhz,power_w,reasons_mask\n")
+                for c, m, w, r in self.samples:
+                    fh.write(f"{c},{m},{w:.1f},{r:#x}\n")
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                    "sm_mhz_min": min(sm) if sm else None, "reasons": sorted(reasons), "samples": len(sm),
+                    "source": "nvml, 2 ms"}
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -135,7 +184,7 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi, 50 ms"}
 
 
 def dist_setup(n_gpus: int):

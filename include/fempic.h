@@ -176,7 +176,11 @@ void pic_sim_destroy(pic_sim *sim);
  * in FP64.  For Boris, v is taken as v^{n-1/2}; for Adams-Bashforth as v^n.
  * tet_hint [n] gives each particle's tet (NULL: located by a walk from tet 0).
  * Particles outside their tet (any barycentric below -1e-10) give
- * PIC_ERR_PARTICLE_OUTSIDE.  Must be called before pic_sim_init.
+ * PIC_ERR_PARTICLE_OUTSIDE, non-finite x or v PIC_ERR_INVALID_ARG; a failed
+ * call loads nothing and leaves earlier loads in place.  x, v and tet_hint
+ * are host pointers (on_device 0) or device pointers (on_device 1); they are
+ * copied once, to device staging arrays that pic_sim_init consumes and frees,
+ * and checked there.  Must be called before pic_sim_init.
  * Particle ids are assigned in load order, starting at 0. */
 int pic_particles_load(pic_sim *sim, int32_t species, double q, double m, double w, int64_t n,
                        const double *x, const double *v, const int32_t *tet_hint, int32_t on_device);

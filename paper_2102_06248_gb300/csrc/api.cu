@@ -351,7 +351,7 @@ int pic_particles_load(pic_sim *sim, int32_t species, double q, double mass, dou
         set_error("pic_particles_load: species must be 0..3 with m > 0 and finite q, w");
         return PIC_ERR_INVALID_ARG;
     }
-    if ((int64_t)s->h_tet.size() + n >= (1LL << 30)) {
+    if ((int64_t)s->n_loaded + n >= (1LL << 30)) {
         set_error("pic_particles_load: more than 2^30 particles");
         return PIC_ERR_INVALID_ARG;
     }
@@ -370,37 +370,15 @@ int pic_particles_load(pic_sim *sim, int32_t species, double q, double mass, dou
         s->sp_w[species] = w;
         s->n_species++;
     }
-    const size_t start = s->h_tet.size();
-    s->h_x.resize(3 * (start + n));
-    s->h_v.resize(3 * (start + n));
-    s->h_tet.resize(start + n);
-    s->h_species.resize(start + n, species);
     if (n == 0) return PIC_OK;
-    cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
-    FP_CUDA(cudaMemcpy(s->h_x.data() + 3 * start, x, sizeof(double) * 3 * n, kind));
-    FP_CUDA(cudaMemcpy(s->h_v.data() + 3 * start, v, sizeof(double) * 3 * n, kind));
-    if (tet_hint) {
-        FP_CUDA(cudaMemcpy(s->h_tet.data() + start, tet_hint, sizeof(int) * n, kind));
-    } else {
-        s->h_tet[start] = -2;   // marks "locate" for validate_particles
-    }
-    for (int64_t i = 0; i < 3 * n; i++)
-        if (!std::isfinite(s->h_x[3 * start + i]) || !std::isfinite(s->h_v[3 * start + i])) {
-            set_error("pic_particles_load: non-finite position or velocity");
-            s->h_x.resize(3 * start);
-            s->h_v.resize(3 * start);
-            s->h_tet.resize(start);
-            s->h_species.resize(start);
-            return PIC_ERR_INVALID_ARG;
-        }
-    int rc = validate_particles(s, (int)n, (int)start);
-    if (rc) {
-        s->h_x.resize(3 * start);
-        s->h_v.resize(3 * start);
-        s->h_tet.resize(start);
-        s->h_species.resize(start);
-    }
-    return rc;
+    // straight to the device staging arrays (one copy of the caller's data,
+    // checked there); a failed load leaves the earlier loads as they were
+    const int start = s->n_loaded;
+    int rc = stage_particles(s, (int)n, x, v, tet_hint, on_device != 0);
+    if (rc) return rc;
+    s->load_runs.push_back({start, (int)n, species});
+    s->n_loaded = start + (int)n;
+    return PIC_OK;
 }
 
 int pic_sim_init(pic_sim *sim) {
@@ -479,7 +457,7 @@ int pic_set_ab_history(pic_sim *sim, int32_t levels, const double *a_hist, const
         set_error("pic_set_ab_history: call after init with 0 <= levels <= order - 1");
         return PIC_ERR_INVALID_ARG;
     }
-    const int np = (int)s->h_tet.size();
+    const int np = s->n_loaded;
     DevBuf<double> da, dv;
     int rc;
     std::vector<double> ha(a_hist, a_hist + (size_t)levels * np * 3), hv(v_hist, v_hist + (size_t)levels * np * 3);

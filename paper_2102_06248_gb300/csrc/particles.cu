@@ -233,16 +233,19 @@ int bitlen(unsigned long long x) {
 // and beta = (D b)_t / (3V) (zero up to rounding).  The uniform external field
 // b0 is added to B0 here; the face DOFs hold the self-consistent part only.
 // ---------------------------------------------------------------------------
+// Arithmetic in R: FP64 for the PLAIN path, FP32 (from the FP32 barycentric
+// maps) for the MIXED one, whose push consumes FP32 coefficients anyway; in
+// FP64 on GB300 this kernel was bound by its FP64 instructions.
 template <typename R>
-__global__ void __launch_bounds__(256) k_coefficients(int nt, const double *__restrict__ geo, const int *__restrict__ tet_edge,
+__global__ void __launch_bounds__(256) k_coefficients(int nt, const R *__restrict__ geo, const int *__restrict__ tet_edge,
                                                       const int4 *__restrict__ tet_face, const int4 *__restrict__ tet_nodes,
                                                       const signed char *__restrict__ tet_sign, const double *__restrict__ vol,
                                                       const double *__restrict__ xyz, const double *__restrict__ e,
                                                       const double *__restrict__ b, double3 b_ext, R *__restrict__ coef) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
-    const double *gp = geo + 12 * (size_t)t;
-    double g[4][3];
+    const R *gp = geo + 12 * (size_t)t;
+    R g[4][3];
     for (int i = 0; i < 3; i++) {
         g[1][i] = gp[3 + i];
         g[2][i] = gp[6 + i];
@@ -250,37 +253,39 @@ __global__ void __launch_bounds__(256) k_coefficients(int nt, const double *__re
         g[0][i] = -(g[1][i] + g[2][i] + g[3][i]);
     }
     const int *te = tet_edge + 6 * (size_t)t;
-    double ev[6];
-    for (int k = 0; k < 6; k++) ev[k] = e[te[k]];
+    R ev[6];
+    for (int k = 0; k < 6; k++) ev[k] = (R)e[te[k]];
     const int LI[6] = {0, 0, 0, 1, 1, 2}, LJ[6] = {1, 2, 3, 2, 3, 3};
-    double E0[3], Om[3] = {0, 0, 0};
+    R E0[3], Om[3] = {0, 0, 0};
     for (int i = 0; i < 3; i++) E0[i] = ev[0] * g[1][i] + ev[1] * g[2][i] + ev[2] * g[3][i];
     for (int k = 0; k < 6; k++) {
-        const double *a = g[LI[k]], *c = g[LJ[k]];
+        const R *a = g[LI[k]], *c = g[LJ[k]];
         Om[0] += ev[k] * (a[1] * c[2] - a[2] * c[1]);
         Om[1] += ev[k] * (a[2] * c[0] - a[0] * c[2]);
         Om[2] += ev[k] * (a[0] * c[1] - a[1] * c[0]);
     }
     const int4 tf = tet_face[t], tn = tet_nodes[t];
-    const double bv[4] = {b[tf.x], b[tf.y], b[tf.z], b[tf.w]};
+    const R bv[4] = {(R)b[tf.x], (R)b[tf.y], (R)b[tf.z], (R)b[tf.w]};
     const int nid[4] = {tn.x, tn.y, tn.z, tn.w};
-    const double s = tet_sign[t];
-    const double inv3v = 1.0 / (3.0 * vol[t]);
-    double B0[3] = {0, 0, 0}, divb = 0.0;
+    const R s = tet_sign[t];
+    const R inv3v = (R)1 / ((R)3 * (R)vol[t]);
+    // x0 - x_k from the FP64 node coordinates, then rounded to R
+    const double *x0 = xyz + 3 * (size_t)nid[0];
+    R B0[3] = {0, 0, 0}, divb = 0;
     for (int k = 0; k < 4; k++) {
-        const double Dk = (k & 1) ? -s : s;
+        const R Dk = (k & 1) ? -s : s;
         divb += Dk * bv[k];
         if (k == 0) continue;
-        for (int i = 0; i < 3; i++) B0[i] += Dk * bv[k] * (gp[i] - xyz[3 * (size_t)nid[k] + i]);
+        for (int i = 0; i < 3; i++) B0[i] += Dk * bv[k] * (R)(x0[i] - xyz[3 * (size_t)nid[k] + i]);
     }
     R *c = coef + 10 * (size_t)t;
-    const double bx[3] = {b_ext.x, b_ext.y, b_ext.z};
+    const R bx[3] = {(R)b_ext.x, (R)b_ext.y, (R)b_ext.z};
     for (int i = 0; i < 3; i++) {
-        c[i] = (R)E0[i];
-        c[3 + i] = (R)Om[i];
-        c[6 + i] = (R)(B0[i] * inv3v + bx[i]);
+        c[i] = E0[i];
+        c[3 + i] = Om[i];
+        c[6 + i] = B0[i] * inv3v + bx[i];
     }
-    c[9] = (R)(divb * inv3v);
+    c[9] = divb * inv3v;
 }
 
 // ---------------------------------------------------------------------------
@@ -1045,13 +1050,24 @@ __global__ void __launch_bounds__(256) k_gather_nodes(int nn, const int *__restr
 // load-time check (and location): every particle inside its tet.  Without a
 // hint the particle is located by a straight walk in physical space from the
 // centroid of tet 0 (exits through a wall mean the point is outside the mesh).
-__global__ void k_validate(int n, int start, const double *__restrict__ x, const int *__restrict__ tet, int nt,
-                           const double *__restrict__ geo, const int4 *__restrict__ tnbr, const int4 *__restrict__ tnodes,
-                           const double *__restrict__ xyz, int *__restrict__ tet_out, int *bad) {
+// x, v: the load's [n][3] values; tet: the staged tets, hint in and located
+// tet out at [start + p] (-1 when bad); bad[0] counts particles outside their
+// tet or the mesh, bad[1] non-finite positions or velocities.
+__global__ void k_validate(int n, int start, const double *__restrict__ x, const double *__restrict__ v,
+                           bool hint, int nt, const double *__restrict__ geo, const int4 *__restrict__ tnbr,
+                           const int4 *__restrict__ tnodes, const double *__restrict__ xyz, int *tet, int *bad) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
+    int *tet_out = tet;
     const double Q[3] = {x[3 * (size_t)p], x[3 * (size_t)p + 1], x[3 * (size_t)p + 2]};
-    int t = tet ? tet[p] : 0;
+    bool finite = true;
+    for (int d = 0; d < 3; d++) finite = finite && isfinite(Q[d]) && isfinite(v[3 * (size_t)p + d]);
+    if (!finite) {
+        atomicAdd(bad + 1, 1);
+        tet_out[start + p] = -1;
+        return;
+    }
+    int t = hint ? tet[start + p] : 0;
     if (t < 0 || t >= nt) {
         atomicAdd(bad, 1);
         tet_out[start + p] = -1;
@@ -1059,7 +1075,7 @@ __global__ void k_validate(int n, int start, const double *__restrict__ x, const
     }
     double gp[12], lq[4];
     load_geo(geo, t, gp);
-    if (!tet) {
+    if (!hint) {
         const int4 tn = tnodes[t];
         const int ids[4] = {tn.x, tn.y, tn.z, tn.w};
         double S[3] = {0, 0, 0};
@@ -1284,32 +1300,45 @@ int particles_alloc(Sim *s, size_t cap) {
     return PIC_OK;
 }
 
-int validate_particles(Sim *s, int n, int start) {
-    // positions / hints are staged on the host (s->h_x, s->h_tet) -- upload, check on the device
-    DevBuf<double> dx;
-    DevBuf<int> dt_in, dt_out, dbad;
+// Appends a load to the device staging arrays (grown by a device copy when
+// needed), copying the caller's arrays once, then checks and locates the new
+// particles on the device.
+int stage_particles(Sim *s, int n, const double *x, const double *v, const int *tet_hint, bool on_device) {
+    const size_t start = (size_t)s->n_loaded, need = start + (size_t)n;
     int rc;
-    std::vector<double> xs(s->h_x.begin() + 3 * (size_t)start, s->h_x.begin() + 3 * (size_t)(start + n));
-    if ((rc = dx.upload(xs))) return rc;
-    const bool have_hint = s->h_tet[start] != -2;
-    if (have_hint) {
-        std::vector<int> ts(s->h_tet.begin() + start, s->h_tet.begin() + start + n);
-        if ((rc = dt_in.upload(ts))) return rc;
+    if (s->st_tet.n < need) {
+        DevBuf<double> nx, nv;
+        DevBuf<int> nt;
+        if ((rc = nx.alloc(3 * need)) || (rc = nv.alloc(3 * need)) || (rc = nt.alloc(need))) return rc;
+        if (start > 0) {
+            FP_CUDA(cudaMemcpy(nx.p, s->st_x.p, sizeof(double) * 3 * start, cudaMemcpyDeviceToDevice));
+            FP_CUDA(cudaMemcpy(nv.p, s->st_v.p, sizeof(double) * 3 * start, cudaMemcpyDeviceToDevice));
+            FP_CUDA(cudaMemcpy(nt.p, s->st_tet.p, sizeof(int) * start, cudaMemcpyDeviceToDevice));
+        }
+        s->st_x = std::move(nx);
+        s->st_v = std::move(nv);
+        s->st_tet = std::move(nt);
     }
-    if ((rc = dt_out.alloc((size_t)start + n)) || (rc = dbad.alloc(1))) return rc;
-    FP_CUDA(cudaMemset(dbad.p, 0, sizeof(int)));
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    FP_CUDA(cudaMemcpy(s->st_x.p + 3 * start, x, sizeof(double) * 3 * n, kind));
+    FP_CUDA(cudaMemcpy(s->st_v.p + 3 * start, v, sizeof(double) * 3 * n, kind));
+    if (tet_hint) FP_CUDA(cudaMemcpy(s->st_tet.p + start, tet_hint, sizeof(int) * n, kind));
+    DevBuf<int> dbad;
+    if ((rc = dbad.alloc(2))) return rc;
+    FP_CUDA(cudaMemset(dbad.p, 0, 2 * sizeof(int)));
     const Mesh *m = s->mesh;
-    if (n > 0)
-        { k_validate<<<(n + 127) / 128, 128>>>(n, start, dx.p, have_hint ? dt_in.p : nullptr, m->n_tets, m->geo.p,
-                                             m->tet_nbr.p, m->tet_nodes.p, m->xyz.p, dt_out.p, dbad.p); note_launch(); }
+    { k_validate<<<(n + 127) / 128, 128>>>(n, (int)start, s->st_x.p + 3 * start, s->st_v.p + 3 * start,
+                                         tet_hint != nullptr, m->n_tets, m->geo.p, m->tet_nbr.p, m->tet_nodes.p,
+                                         m->xyz.p, s->st_tet.p, dbad.p); note_launch(); }
     FP_CUDA(cudaGetLastError());
-    int bad = 0;
-    FP_CUDA(cudaMemcpy(&bad, dbad.p, sizeof(int), cudaMemcpyDeviceToHost));
-    std::vector<int> out((size_t)start + n);
-    FP_CUDA(cudaMemcpy(out.data(), dt_out.p, sizeof(int) * ((size_t)start + n), cudaMemcpyDeviceToHost));
-    for (int p = 0; p < n; p++) s->h_tet[start + p] = out[start + p];
-    if (bad) {
-        set_error("pic_particles_load: " + std::to_string(bad) + " particle(s) outside their tet or the mesh");
+    int bad[2] = {0, 0};
+    FP_CUDA(cudaMemcpy(bad, dbad.p, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+    if (bad[1]) {
+        set_error("pic_particles_load: non-finite position or velocity");
+        return PIC_ERR_INVALID_ARG;
+    }
+    if (bad[0]) {
+        set_error("pic_particles_load: " + std::to_string(bad[0]) + " particle(s) outside their tet or the mesh");
         return PIC_ERR_PARTICLE_OUTSIDE;
     }
     return PIC_OK;
@@ -1317,7 +1346,7 @@ int validate_particles(Sim *s, int n, int start) {
 
 // uploads the staged particles into bank 0 (called by init)
 int upload_particles(Sim *s) {
-    const int n = (int)s->h_tet.size();
+    const int n = s->n_loaded;
     int rc = particles_alloc(s, std::max<size_t>((size_t)n, 1));
     if (rc) return rc;
     // per-tet accumulators: one set per species in MIXED (fixed point is per unit charge)
@@ -1325,31 +1354,25 @@ int upload_particles(Sim *s) {
     if ((rc = s->tacc.alloc((size_t)kNV * s->mesh->n_tets * s->nsp)) ||
         (rc = s->wacc.alloc((size_t)4 * s->mesh->n_tets * s->nsp)))
         return rc;
-    DevBuf<double> dx, dv;
-    DevBuf<int> dt;
-    if ((rc = dx.upload(s->h_x)) || (rc = dv.upload(s->h_v)) || (rc = dt.upload(s->h_tet))) return rc;
     PartBank &k = s->bank[0];
-    int start = 0;
-    while (start < n) {
-        int sp = s->h_species[start];
-        int end = start;
-        while (end < n && s->h_species[end] == sp) end++;
-        const int cnt = end - start;
-        const int blocks = (cnt + 255) / 256;
+    for (const Sim::LoadRun &r : s->load_runs) {
+        const int blocks = (r.n + 255) / 256;
+        const double *dx = s->st_x.p + 3 * (size_t)r.start, *dv = s->st_v.p + 3 * (size_t)r.start;
         if (s->mixed)
             { k_load_particles<float><<<blocks, 256, 0, s->stream>>>(
-                cnt, start, dx.p + 3 * (size_t)start, dv.p + 3 * (size_t)start, dt.p, sp, start, (float *)k.x[0].p,
-                (float *)k.x[1].p, (float *)k.x[2].p, (float *)k.v[0].p, (float *)k.v[1].p, (float *)k.v[2].p, k.key.p,
-                k.id.p); note_launch(); }
+                r.n, r.start, dx, dv, s->st_tet.p, r.species, r.start, (float *)k.x[0].p, (float *)k.x[1].p,
+                (float *)k.x[2].p, (float *)k.v[0].p, (float *)k.v[1].p, (float *)k.v[2].p, k.key.p, k.id.p); note_launch(); }
         else
             { k_load_particles<double><<<blocks, 256, 0, s->stream>>>(
-                cnt, start, dx.p + 3 * (size_t)start, dv.p + 3 * (size_t)start, dt.p, sp, start, (double *)k.x[0].p,
-                (double *)k.x[1].p, (double *)k.x[2].p, (double *)k.v[0].p, (double *)k.v[1].p, (double *)k.v[2].p,
-                k.key.p, k.id.p); note_launch(); }
-        start = end;
+                r.n, r.start, dx, dv, s->st_tet.p, r.species, r.start, (double *)k.x[0].p, (double *)k.x[1].p,
+                (double *)k.x[2].p, (double *)k.v[0].p, (double *)k.v[1].p, (double *)k.v[2].p, k.key.p, k.id.p); note_launch(); }
     }
     FP_CUDA(cudaGetLastError());
     FP_CUDA(cudaStreamSynchronize(s->stream));
+    // the staging arrays are not needed after init
+    s->st_x.free();
+    s->st_v.free();
+    s->st_tet.free();
     s->n_total = n;
     s->next_id = n;
     s->cur = 0;
@@ -1383,7 +1406,7 @@ int stage_coefficients(Sim *s, const double *e, const double *b) {
     const int nt = m->n_tets;
     if (s->mixed)
         { k_coefficients<float><<<(nt + 255) / 256, 256, 0, s->stream>>>(
-            nt, m->geo.p, m->tet_edge.p, m->tet_face.p, m->tet_nodes.p, m->tet_sign.p, m->tet_vol.p, m->xyz.p, e, b,
+            nt, m->geo32.p, m->tet_edge.p, m->tet_face.p, m->tet_nodes.p, m->tet_sign.p, m->tet_vol.p, m->xyz.p, e, b,
             make_double3(s->cfg.b0[0], s->cfg.b0[1], s->cfg.b0[2]), (float *)s->coef.p); note_launch(); }
     else
         { k_coefficients<double><<<(nt + 255) / 256, 256, 0, s->stream>>>(
@@ -1617,22 +1640,26 @@ int particles_inject(Sim *s, int species, int n, const double *hx, const double 
     const Mesh *m = s->mesh;
     // where the particles are: the hint checked, or a walk from tet 0
     DevBuf<double> dx, dv;
-    DevBuf<int> dt_in, dt, dbad;
-    std::vector<double> xs(hx, hx + 3 * (size_t)n), vs(hv, hv + 3 * (size_t)n);
-    if ((rc = dx.upload(xs)) || (rc = dv.upload(vs)) || (rc = dt.alloc(n)) || (rc = dbad.alloc(1))) return rc;
-    if (htet) {
-        std::vector<int> ts(htet, htet + n);
-        if ((rc = dt_in.upload(ts))) return rc;
-    }
-    FP_CUDA(cudaMemsetAsync(dbad.p, 0, sizeof(int), s->stream));
-    { k_validate<<<(n + 127) / 128, 128, 0, s->stream>>>(n, 0, dx.p, htet ? dt_in.p : nullptr, m->n_tets, m->geo.p,
+    DevBuf<int> dt, dbad;
+    if ((rc = dx.alloc(3 * (size_t)n)) || (rc = dv.alloc(3 * (size_t)n)) || (rc = dt.alloc(n)) ||
+        (rc = dbad.alloc(2)))
+        return rc;
+    FP_CUDA(cudaMemcpyAsync(dx.p, hx, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s->stream));
+    FP_CUDA(cudaMemcpyAsync(dv.p, hv, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s->stream));
+    if (htet) FP_CUDA(cudaMemcpyAsync(dt.p, htet, sizeof(int) * n, cudaMemcpyHostToDevice, s->stream));
+    FP_CUDA(cudaMemsetAsync(dbad.p, 0, 2 * sizeof(int), s->stream));
+    { k_validate<<<(n + 127) / 128, 128, 0, s->stream>>>(n, 0, dx.p, dv.p, htet != nullptr, m->n_tets, m->geo.p,
                                                        m->tet_nbr.p, m->tet_nodes.p, m->xyz.p, dt.p, dbad.p); note_launch(); }
     FP_CUDA(cudaGetLastError());
-    int bad = 0;
-    FP_CUDA(cudaMemcpyAsync(&bad, dbad.p, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    int bad[2] = {0, 0};
+    FP_CUDA(cudaMemcpyAsync(bad, dbad.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     FP_CUDA(cudaStreamSynchronize(s->stream));
-    if (bad) {
-        set_error("pic_particles_inject: " + std::to_string(bad) + " particle(s) outside their tet or the mesh");
+    if (bad[1]) {
+        set_error("pic_particles_inject: non-finite position or velocity");
+        return PIC_ERR_INVALID_ARG;
+    }
+    if (bad[0]) {
+        set_error("pic_particles_inject: " + std::to_string(bad[0]) + " particle(s) outside their tet or the mesh");
         return PIC_ERR_PARTICLE_OUTSIDE;
     }
     // the entries the last push wrote stay where they are; the new ones follow

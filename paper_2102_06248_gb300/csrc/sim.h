@@ -159,9 +159,15 @@ struct Sim {
     int cur = 0;              // current bank
     PartBank bank[2];
     int next_id = 0;
-    // host staging of loads before init
-    std::vector<double> h_x, h_v;
-    std::vector<int> h_tet, h_species;
+    // loads before init, staged on the device as the caller gave them (x, v
+    // as [n][3] FP64, located tets), one run per load call
+    struct LoadRun {
+        int start, n, species;
+    };
+    DevBuf<double> st_x, st_v;
+    DevBuf<int> st_tet;
+    std::vector<LoadRun> load_runs;
+    int n_loaded = 0;
 
     // sort
     DevBuf<uint32_t> skey, sval, tkey, tval;
@@ -229,7 +235,7 @@ int sort_particles(Sim *s);
 int stage_coefficients(Sim *s, const double *e, const double *b);
 int particle_push(Sim *s, int charge_only);
 int reduce_to_entities(Sim *s);          // per-tet accumulators -> dG, rho, wall
-int validate_particles(Sim *s, int n_new, int start);
+int stage_particles(Sim *s, int n, const double *x, const double *v, const int *tet_hint, bool on_device);
 
 // ---- launchers (solver.cu) ----
 int solver_alloc(Sim *s);
