@@ -469,6 +469,7 @@ def gpu_arm(args):
         t_mesh = time.perf_counter()
         for k, sp in enumerate(wl.species):
             sim_e.particles_load(k, sp.q, sp.m, sp.w, sp.x, sp.v, sp.tet)
+        t_load = time.perf_counter()
         sim_e.init()
         t_setup = time.perf_counter()
         d2h = 0
@@ -481,6 +482,7 @@ def gpu_arm(args):
         t1 = time.perf_counter()
         e2e_s = t1 - t_mesh
         e2e_setup_s = t_setup - t_mesh
+        e2e_load_s, e2e_init_s = t_load - t_mesh, t_setup - t_load
         h2d = sum(sp.x.nbytes + sp.v.nbytes + sp.tet.nbytes for sp in wl.species)
         d2h += e_out.nbytes
         del sim_e
@@ -573,7 +575,8 @@ def gpu_arm(args):
             "cpu_baseline": cpu,
             "e2e": None if args.skip_e2e else {"value": total_ps / e2e_s_max, "unit": "particle-steps/s",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
-                    "seconds": e2e_s_max, "setup_seconds": e2e_setup_s,
+                    "seconds": e2e_s_max, "setup_seconds": e2e_setup_s, "load_seconds": e2e_load_s,
+                    "init_seconds": e2e_init_s,
                     "what": "particles_load from host arrays (H2D) + init + K steps, each followed by its "
                             "diagnostics read back (D2H), + the final E field read back"},
             "gpu_launches": launches,

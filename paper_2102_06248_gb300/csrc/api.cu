@@ -115,7 +115,12 @@ int check_status(Sim *s) {
 int step_particles(Sim *s, bool fields) {
     int rc;
     prof_begin(s, PH_SORT);
-    if ((rc = sort_particles(s))) return rc;
+    if (s->presorted) {
+        FP_CUDA(cudaStreamWaitEvent(s->stream, s->ev_sorted, 0));
+        s->presorted = 0;
+    } else if ((rc = sort_particles(s))) {
+        return rc;
+    }
     prof_end(s, PH_SORT);
     prof_begin(s, PH_COEF);
     if ((rc = stage_coefficients(s, s->e.p, s->b.p))) return rc;
@@ -173,6 +178,9 @@ int one_step(Sim *s, bool fields) {
         const int per_sm = s->cfg.solver_blocks_per_sm ? s->cfg.solver_blocks_per_sm : 2;
         if ((rc = launch_pcg_runs(&a, 1, per_sm, s->stream))) return rc;
     }
+    // the next step's sort, behind the completion (under it, it slowed the
+    // latency-bound solve by more than its own time) and beside the rest
+    if ((rc = presort_particles(s))) return rc;
     if ((rc = step_fields_end(s))) return rc;
     rc = read_control(s);
     prof_collect(s);
@@ -327,6 +335,12 @@ void pic_sim_destroy(pic_sim *sim) {
     if (!sim) return;
     if (sim->s.stream) cudaStreamSynchronize(sim->s.stream);
     else cudaDeviceSynchronize();
+    if (sim->s.side) {
+        cudaStreamSynchronize(sim->s.side);
+        cudaStreamDestroy(sim->s.side);
+        cudaEventDestroy(sim->s.ev_keys);
+        cudaEventDestroy(sim->s.ev_sorted);
+    }
     for (int ph = 0; ph < PH_COUNT; ph++) {
         if (sim->s.ev0[ph]) cudaEventDestroy(sim->s.ev0[ph]);
         if (sim->s.ev1[ph]) cudaEventDestroy(sim->s.ev1[ph]);

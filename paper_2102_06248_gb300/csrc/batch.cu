@@ -336,6 +336,7 @@ int pic_batch_step(pic_batch *b, int32_t nsteps) {
     b->saved_profile.clear();
     for (int q = 0; q < n; q++) {
         Sim *s = &b->sims[q]->s;
+        s->presorted = 0;   // a sort issued by a member's own last step is complete (synchronised above)
         b->saved_stream.push_back(s->stream);
         b->saved_profile.push_back(s->profile);
         s->stream = b->st[q];

@@ -1383,14 +1383,14 @@ int upload_particles(Sim *s) {
     return PIC_OK;
 }
 
-int sort_particles(Sim *s) {
+int sort_particles(Sim *s, cudaStream_t st) {
     if (s->n_total == 0) return PIC_OK;
     const int bits = bitlen(((unsigned long long)s->mesh->n_tets << 2));
     uint32_t *ok, *ov;
     // the last push wrote n_total entries (live, then absorbed ones with the
     // dead key); in a batch that count is known on the device only
     const int *d_n = s->batch_mode ? &s->dctl.p->n_sorted : nullptr;
-    int rc = radix_sort<uint32_t>(s->stream, s->bank[s->cur].key.p, s->skey.p, s->sval.p, s->tkey.p, s->tval.p,
+    int rc = radix_sort<uint32_t>(st ? st : s->stream, s->bank[s->cur].key.p, s->skey.p, s->sval.p, s->tkey.p, s->tval.p,
                                   d_n, s->n_total, bits, &s->sortw, &ok, &ov);
     if (rc) return rc;
     if (ok != s->skey.p) {
@@ -1399,6 +1399,34 @@ int sort_particles(Sim *s) {
     }
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
+}
+
+// The sort of the next step depends only on this step's push: it is issued
+// on a second stream after the field solves and runs beside the completion's
+// update, Faraday and the diagnostics (and the host's return from the step);
+// the next step's push waits for it.
+int presort_particles(Sim *s) {
+    if (s->batch_mode || s->n_total == 0) return PIC_OK;
+    if (!s->side) {
+        FP_CUDA(cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking));
+        FP_CUDA(cudaEventCreateWithFlags(&s->ev_keys, cudaEventDisableTiming));
+        FP_CUDA(cudaEventCreateWithFlags(&s->ev_sorted, cudaEventDisableTiming));
+    }
+    FP_CUDA(cudaEventRecord(s->ev_keys, s->stream));
+    FP_CUDA(cudaStreamWaitEvent(s->side, s->ev_keys, 0));
+    int rc = sort_particles(s, s->side);
+    if (rc) return rc;
+    FP_CUDA(cudaEventRecord(s->ev_sorted, s->side));
+    s->presorted = 1;
+    return PIC_OK;
+}
+
+// Forgets an issued sort (the particles changed after it): the stream waits
+// for it to finish, and the next step sorts again.
+void presort_drop(Sim *s) {
+    if (!s->presorted) return;
+    cudaStreamWaitEvent(s->stream, s->ev_sorted, 0);
+    s->presorted = 0;
 }
 
 int stage_coefficients(Sim *s, const double *e, const double *b) {
@@ -1635,6 +1663,7 @@ static int particles_grow(Sim *s, size_t cap, size_t keep) {
 // and the next step's continuity holds as for every other particle.
 int particles_inject(Sim *s, int species, int n, const double *hx, const double *hv, const int *htet) {
     if (n == 0) return PIC_OK;
+    presort_drop(s);
     int rc;
     if ((rc = read_control(s))) return rc;
     const Mesh *m = s->mesh;

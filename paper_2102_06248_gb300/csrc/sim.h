@@ -140,6 +140,11 @@ struct Sim {
     const Mesh *mesh = nullptr;
     pic_config cfg{};
     cudaStream_t stream = nullptr;
+    // the next step's particle sort, issued on a second stream under the
+    // field solve (presorted: its result waits behind ev_sorted)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_keys = nullptr, ev_sorted = nullptr;
+    int presorted = 0;
     int mixed = 0;
     int ab = 0;               // Adams-Bashforth order (0 = Boris)
     int hist_levels = 0;      // ab - 1
@@ -231,7 +236,9 @@ void prof_collect(Sim *s);   // after a stream synchronisation
 // ---- launchers (particles.cu) ----
 SpeciesParams species_params(const Sim *s);
 int particles_alloc(Sim *s, size_t cap);
-int sort_particles(Sim *s);
+int sort_particles(Sim *s, cudaStream_t st = nullptr);
+int presort_particles(Sim *s);
+void presort_drop(Sim *s);
 int stage_coefficients(Sim *s, const double *e, const double *b);
 int particle_push(Sim *s, int charge_only);
 int reduce_to_entities(Sim *s);          // per-tet accumulators -> dG, rho, wall

@@ -230,13 +230,16 @@ def test_error_paths(F):
     with pytest.raises(F.PicError) as ei:            # outside the mesh, located by a walk
         s.particles_load(0, W.Q_E, W.M_E, 1.0, np.array([[1.5, 0.5, 0.5]]), np.zeros((1, 3)))
     assert ei.value.code == 4
+    with pytest.raises(F.PicError) as ei:            # non-finite velocity: nothing of the call is loaded
+        s.particles_load(0, W.Q_E, W.M_E, 1.0, np.vstack([x, x]), np.array([[0.0, 0.0, 0.0], [np.nan, 0.0, 0.0]]))
+    assert ei.value.code == 1
     s.particles_load(0, W.Q_E, W.M_E, 1.0, x, np.zeros((1, 3)))   # located by a walk
     with pytest.raises(F.PicError) as ei:
         s.step()                                     # before init
     assert ei.value.code == 10
     s.init()
     _, _, t, _ = s.particles()
-    assert 0 <= t[0] < pm.n_tets
+    assert t.shape == (1,) and 0 <= t[0] < pm.n_tets      # the failed loads left nothing behind
     # walk cap: a particle crossing many cells in one step with walk_cap = 1
     s2 = F.Sim(pm, 1e-9, walk_cap=1)
     xx, tt = W.place_in_box(box, np.array([[0.1, 0.5, 0.5]]))
