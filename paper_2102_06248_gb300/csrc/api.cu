@@ -114,6 +114,11 @@ int check_status(Sim *s) {
 // (fields) the Newmark right-hand side.
 int step_particles(Sim *s, bool fields) {
     int rc;
+    // the coefficients first: they do not need the sort, which may still be
+    // running on the second stream
+    prof_begin(s, PH_COEF);
+    if ((rc = stage_coefficients(s, s->e.p, s->b.p))) return rc;
+    prof_end(s, PH_COEF);
     prof_begin(s, PH_SORT);
     if (s->presorted) {
         FP_CUDA(cudaStreamWaitEvent(s->stream, s->ev_sorted, 0));
@@ -122,9 +127,6 @@ int step_particles(Sim *s, bool fields) {
         return rc;
     }
     prof_end(s, PH_SORT);
-    prof_begin(s, PH_COEF);
-    if ((rc = stage_coefficients(s, s->e.p, s->b.p))) return rc;
-    prof_end(s, PH_COEF);
     if ((rc = particle_push(s, 0))) return rc;        // records PH_PUSH and opens PH_DEPOSIT
     if ((rc = reduce_to_entities(s))) return rc;
     prof_end(s, PH_DEPOSIT);
