@@ -44,7 +44,7 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (non-tensor) nominal rate
 # profiles/pcg_persistent_plasma_ball_64.md: 21.207 GB measured for 60 FP32 +
 # 2 FP64 iterations whose algorithmic bytes are 21.233 GB.  The FP64 Newmark
 # form has no capture of its current code: its traffic is reported as null.
-TRAFFIC_RATIO_MIXED = 21.206904 / 21.232650
+TRAFFIC_RATIO_MIXED = None   # recaptured after the change to the scaled FP32 system
 TRAFFIC_RATIO_PLAIN = None
 
 
@@ -253,11 +253,13 @@ def pcg_iter_flops(n_rows: int, nnz: int) -> float:
 
 def refine_bytes(n_rows: int, nnz: int, inner_iters: float, outer: float) -> float:
     """Algorithmic bytes of one MIXED Newmark solve (FP64 refinement with FP32
-    correction solves): per FP32 iteration 8 B per nonzero (FP32 value +
-    column) + 14 vector passes of 4 B per row; per refinement step one FP64
-    residual (12 B per nonzero, b read, x gathered, r in FP32 written: 20 B per
-    row) and the update x += d (20 B per row); plus the final residual check."""
-    inner = inner_iters * (8.0 * nnz + 4.0 * 14 * n_rows)
+    correction solves on the diagonally scaled system): per FP32 iteration 8 B
+    per nonzero (FP32 value + column) + 11 vector passes of 4 B per row (SpMV:
+    r read, w written; vector phase: w, p, s, x, r read, p, s, x, r written);
+    per refinement step one FP64 residual (12 B per nonzero, b read, x
+    gathered, r in FP32 written: 20 B per row) and the update x += d (20 B per
+    row); plus the final residual check."""
+    inner = inner_iters * (8.0 * nnz + 4.0 * 11 * n_rows)
     return inner + (outer + 1) * (12.0 * nnz + 20.0 * n_rows) + outer * 20.0 * n_rows
 
 
@@ -512,7 +514,7 @@ def gpu_arm(args):
             kernel = ("k_pcg_persistent (Newmark: FP64 refinement, FP32 Chronopoulos-Gear corrections, "
                       "SELL-32)")
             alg = refine_bytes(mesh.n_int_edges, nnz_A, iters_per_launch, outer)
-            traffic = alg * TRAFFIC_RATIO_MIXED
+            traffic = alg * TRAFFIC_RATIO_MIXED if TRAFFIC_RATIO_MIXED else None
             fp64 = {"note": "the FP32 correction iterations issue no FP64 arithmetic", "outer_steps": outer,
                     "fp32_iters_per_launch": iters_per_launch}
         else:

@@ -84,8 +84,8 @@ struct PcgArgs {
     // mixed-precision refinement (refine = 1): FP64 residuals, FP32 corrections
     int refine;
     double inner_tol2;            // relative residual^2 of each FP32 correction solve
-    const float *Av32, *Dinv32;   // FP32 copies of the values and of D^-1
-    float *b32, *d32, *r32, *u32, *w32, *p32, *s32;
+    const float *Av32, *Dhalf32;   // FP32 values of D^-1/2 A D^-1/2, and D^-1/2
+    float *b32, *d32, *r32, *w32, *p32, *s32;
 };
 constexpr int kMaxBatchRuns = 64;
 
@@ -202,7 +202,7 @@ struct Sim {
     DevBuf<double> rhs;
     // solver work
     DevBuf<double> A_val, Dinv;
-    DevBuf<float> A32, Dinv32, cg32;  // MIXED: FP32 values, D^-1 and seven correction vectors
+    DevBuf<float> A32, Dhalf32, cg32;  // MIXED: FP32 scaled values, D^-1/2 and six correction vectors
     DevBuf<double> cg_r, cg_z, cg_p0, cg_p1, cg_q, cg_part;
     DevBuf<double> hb;              // face vector H (b + b_prev)
     DevBuf<double> w_edge;          // gradient completion: M t - d2 Gbar on interior edges

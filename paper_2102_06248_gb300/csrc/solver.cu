@@ -887,7 +887,7 @@ struct CgOut {
 // kept in T and the block and grid reductions in FP64 (in FP32 the per-thread
 // sums cover about a dozen rows).  max|r| is tracked in FP64 only.  Returns
 // false if a barrier timed out.
-template <typename T>
+template <typename T, bool UNIT = false>
 __device__ __forceinline__ bool cg_core(SolveCtx &c, const T *__restrict__ Av, const T *__restrict__ Dinv,
                                         const T *b, T *x, T *r, T *u, T *w, T *p, T *s, bool x_zero, double tol2,
                                         double abs_inf, int max_iters, CgOut &o) {
@@ -899,10 +899,13 @@ __device__ __forceinline__ bool cg_core(SolveCtx &c, const T *__restrict__ Av, c
         T v[4] = {0, 0, 0, 0};   // gamma, rr, delta, bb
         unsigned long long mx = 0;
         auto init_row = [&](int i, T ax, T) {
-            const T bi = b[i], ri = bi - ax, ui = Dinv[i] * ri;
+            const T bi = b[i], ri = bi - ax;
+            T ui;
+            if constexpr (UNIT) ui = ri;
+            else ui = Dinv[i] * ri;
             if (x_zero) x[i] = 0;
             r[i] = ri;
-            u[i] = ui;
+            if constexpr (!UNIT) u[i] = ui;
             v[0] = fma(ri, ui, v[0]);
             v[1] = fma(ri, ri, v[1]);
             v[3] = fma(bi, bi, v[3]);
@@ -954,7 +957,6 @@ __device__ __forceinline__ bool cg_core(SolveCtx &c, const T *__restrict__ Av, c
                 for (int k = 0; k < 7; k++) q[h][k] = 0;
                 const int slh = sl + h * c.sls, i = slh * 32 + lane;
                 if (slh < a.n_slices && i < n) {
-                    q[h][0] = u[i];
                     q[h][1] = w[i];
                     if (!first) {
                         q[h][2] = p[i];
@@ -962,7 +964,12 @@ __device__ __forceinline__ bool cg_core(SolveCtx &c, const T *__restrict__ Av, c
                     }
                     q[h][4] = x[i];
                     q[h][5] = r[i];
-                    q[h][6] = Dinv[i];
+                    if constexpr (UNIT) {
+                        q[h][0] = q[h][5];
+                    } else {
+                        q[h][0] = u[i];
+                        q[h][6] = Dinv[i];
+                    }
                 }
             }
 #pragma unroll
@@ -972,12 +979,14 @@ __device__ __forceinline__ bool cg_core(SolveCtx &c, const T *__restrict__ Av, c
                     const T pi = first ? q[h][0] : fma(be, q[h][2], q[h][0]);
                     const T si = first ? q[h][1] : fma(be, q[h][3], q[h][1]);
                     const T ri = fma(-al, si, q[h][5]);
-                    const T un = q[h][6] * ri;
+                    T un;
+                    if constexpr (UNIT) un = ri;
+                    else un = q[h][6] * ri;
                     p[i] = pi;
                     s[i] = si;
                     x[i] = fma(al, pi, q[h][4]);
                     r[i] = ri;
-                    u[i] = un;
+                    if constexpr (!UNIT) u[i] = un;
                     v[0] = fma(ri, un, v[0]);
                     v[1] = fma(ri, ri, v[1]);
                     if constexpr (kMax) mx = max(mx, abs_bits(ri));
@@ -1057,7 +1066,10 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int nb, const i
     } else {
         // Iterative refinement: the FP64 residual b - A x is the judge; each
         // correction A d = r / sigma is solved in FP32 (values and vectors) to
-        // a relative residual of inner_tol, and x += sigma d in FP64.  sigma,
+        // a relative residual of inner_tol, and x += sigma d in FP64.  The
+        // correction solve is plain CG on the scaled system
+        // (D^-1/2 A D^-1/2) dh = D^-1/2 r / sigma, d = D^-1/2 dh: the same
+        // iterates as Jacobi-PCG on A without the D^-1 and u vectors.  sigma,
         // the RMS of the residual, keeps the FP32 vectors near 1: in SI units
         // the residuals are far below 1 and their squares would reach the
         // FP32 subnormal range.  (Stopping a correction solve at what the
@@ -1090,17 +1102,17 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int nb, const i
             const double sigma = sqrt(rr / n), inv = 1.0 / sigma;
             for (int sl = c.sl0; sl < a.n_slices; sl += c.sls) {
                 const int i = sl * 32 + c.lane;
-                if (i < n) a.b32[i] = (float)(a.r[i] * inv);
+                if (i < n) a.b32[i] = (float)(a.r[i] * inv) * a.Dhalf32[i];
             }
             CgOut oi{0, false, 0.0, 0.0, 0.0};
-            if (!cg_core<float>(c, a.Av32, a.Dinv32, a.b32, a.d32, a.r32, a.u32, a.w32, a.p32, a.s32, true,
+            if (!cg_core<float, true>(c, a.Av32, a.Dhalf32, a.b32, a.d32, a.r32, a.r32, a.w32, a.p32, a.s32, true,
                                 a.inner_tol2, -1.0, min(kMaxInner, a.max_iters - total), oi))
                 goto timeout;
             total += oi.iters;
             outer++;
             for (int sl = c.sl0; sl < a.n_slices; sl += c.sls) {
                 const int i = sl * 32 + c.lane;
-                if (i < n) a.x[i] = fma(sigma, (double)a.d32[i], a.x[i]);
+                if (i < n) a.x[i] = fma(sigma * (double)a.Dhalf32[i], (double)a.d32[i], a.x[i]);
             }
         }
         if (bb == 0.0)
@@ -1170,6 +1182,26 @@ __global__ void k_axpby(int n, double a, const double *__restrict__ x, double b,
     if (i < n) out[i] = a * x[i] + b * y[i];
 }
 
+// MIXED corrections solve the diagonally scaled system D^-1/2 A D^-1/2 (unit
+// diagonal: Jacobi-PCG on A is plain CG on it, without the D^-1 and u vectors)
+__global__ void k_scale_sell_f32(int n, int n_slices, const int *__restrict__ sp, const int *__restrict__ sw,
+                                 const int *__restrict__ col, const double *__restrict__ v,
+                                 const double *__restrict__ dinv, float *__restrict__ out) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sl = t >> 5, lane = t & 31;
+    if (sl >= n_slices) return;
+    const int i = sl * 32 + lane;
+    const double di = i < n ? sqrt(dinv[i]) : 0.0;
+    for (int j = 0; j < sw[sl]; j++) {
+        const int k = sp[sl] + 32 * j + lane;
+        out[k] = i < n ? (float)(v[k] * di * sqrt(dinv[col[k]])) : 0.0f;
+    }
+}
+__global__ void k_sqrt_f32(int n, const double *__restrict__ dinv, float *__restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)sqrt(dinv[i]);
+}
+
 __global__ void k_to_f32(long long n, const double *__restrict__ x, float *__restrict__ out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (float)x[i];
@@ -1218,11 +1250,12 @@ int solver_alloc(Sim *s) {
         { k_recip_diag_mk<<<(ni + 255) / 256, 256>>>(ni, m->M_diag.p, m->K_diag.p, c4, s->Dinv.p); note_launch(); }
     }
     if (nin > 0) { k_recip_diag<<<(nin + 255) / 256, 256>>>(nin, m->L.rowptr.p, m->L.col.p, m->L_val.p, s->L_Dinv.p); note_launch(); }
-    // MIXED: FP32 copies for the correction solves of the Newmark refinement
+    // MIXED: the correction solves of the Newmark refinement run on the
+    // diagonally scaled system in FP32
     if (s->mixed && nel > 0) {
-        if ((rc = s->A32.alloc(nel)) || (rc = s->Dinv32.alloc(ni)) || (rc = s->cg32.alloc(7 * (size_t)ni))) return rc;
-        { k_to_f32<<<(unsigned)((nel + 255) / 256), 256>>>(nel, s->A_val.p, s->A32.p); note_launch(); }
-        { k_to_f32<<<(unsigned)((ni + 255) / 256), 256>>>(ni, s->Dinv.p, s->Dinv32.p); note_launch(); }
+        if ((rc = s->A32.alloc(nel)) || (rc = s->Dhalf32.alloc(ni)) || (rc = s->cg32.alloc(6 * (size_t)ni))) return rc;
+        { k_scale_sell_f32<<<(unsigned)((m->As.n_slices * 32 + 255) / 256), 256>>>(ni, m->As.n_slices, m->As.ptr.p, m->As.width.p, m->As.col.p, s->A_val.p, s->Dinv.p, s->A32.p); note_launch(); }
+        { k_sqrt_f32<<<(unsigned)((ni + 255) / 256), 256>>>(ni, s->Dinv.p, s->Dhalf32.p); note_launch(); }
     }
     FP_CUDA(cudaGetLastError());
     FP_CUDA(cudaDeviceSynchronize());
@@ -1425,14 +1458,13 @@ PcgArgs pcg_args_newmark(Sim *s) {
         a.refine = 1;
         a.inner_tol2 = 1e-10;
         a.Av32 = s->A32.p;
-        a.Dinv32 = s->Dinv32.p;
+        a.Dhalf32 = s->Dhalf32.p;
         a.b32 = v;
         a.d32 = v + ni;
         a.r32 = v + 2 * ni;
-        a.u32 = v + 3 * ni;
-        a.w32 = v + 4 * ni;
-        a.p32 = v + 5 * ni;
-        a.s32 = v + 6 * ni;
+        a.w32 = v + 3 * ni;
+        a.p32 = v + 4 * ni;
+        a.s32 = v + 5 * ni;
     }
     return a;
 }
