@@ -41,10 +41,10 @@ FALLBACK_HBM_GBS = 6800.0
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (non-tensor) nominal rate
 # DRAM bytes over algorithmic bytes of the MIXED Newmark launch
 # (k_pcg_persistent<1>), from the ncu capture summarised in
-# profiles/pcg_persistent_plasma_ball_64.md: 21.207 GB measured for 60 FP32 +
-# 2 FP64 iterations whose algorithmic bytes are 21.233 GB.  The FP64 Newmark
+# profiles/pcg_persistent_plasma_ball_64.md: 19.864 GB measured for 60 FP32 +
+# 2 FP64 iterations whose algorithmic bytes are 19.938 GB.  The FP64 Newmark
 # form has no capture of its current code: its traffic is reported as null.
-TRAFFIC_RATIO_MIXED = None   # recaptured after the change to the scaled FP32 system
+TRAFFIC_RATIO_MIXED = 19.863886 / 19.937848
 TRAFFIC_RATIO_PLAIN = None
 
 

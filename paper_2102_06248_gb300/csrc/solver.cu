@@ -1202,10 +1202,6 @@ __global__ void k_sqrt_f32(int n, const double *__restrict__ dinv, float *__rest
     if (i < n) out[i] = (float)sqrt(dinv[i]);
 }
 
-__global__ void k_to_f32(long long n, const double *__restrict__ x, float *__restrict__ out) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (float)x[i];
-}
 
 }  // namespace
 
