@@ -986,6 +986,29 @@ __global__ void __launch_bounds__(256) k_overflow_reduce(const int *d_count, int
     }
 }
 
+// MIXED crossing records hold integers (fixed point): they are added with
+// 64-bit atomics in whatever order, since integer sums do not depend on it
+// (modulo 2^64, so a partial sum that wraps still ends exact) -- no sort of
+// the records is needed, unlike the FP64 records of the PLAIN path.
+__global__ void __launch_bounds__(256) k_overflow_scatter(const int *d_count, int cap,
+                                                          const unsigned long long *__restrict__ okey,
+                                                          const long long *__restrict__ oval, int oshift,
+                                                          unsigned long long *tacc, unsigned long long *wacc) {
+    const int n = min(*d_count, cap);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const unsigned long long tw = okey[j] >> oshift;
+    const size_t idx = (size_t)(tw >> 1);
+    const long long *v = oval + (size_t)j * kNV;
+    if (tw & 1ull) {
+        for (int c = 0; c < 4; c++)
+            if (v[6 + c]) atomicAdd(wacc + idx * 4 + c, (unsigned long long)v[6 + c]);
+    } else {
+        for (int c = 0; c < kNV; c++)
+            if (v[c]) atomicAdd(tacc + idx * kNV + c, (unsigned long long)v[c]);
+    }
+}
+
 // per-tet accumulators -> edges and nodes, in the fixed order of the maps.
 // PLAIN accumulators hold charge already; MIXED ones hold fixed-point sums per
 // species, converted here with the species' q w.
@@ -1575,20 +1598,23 @@ int particle_push(Sim *s, int charge_only) {
     }
     if (s->n_total > 0) {
         int rc;
-        // crossing records: sort by (accumulator, wall, particle, piece) and add in that order
+        // crossing records: PLAIN sorts them by (accumulator, wall, particle,
+        // piece) and adds them in that order; MIXED adds its integers with atomics
         const int oshift = 6 + std::max(1, bitlen((unsigned long long)s->n_total));
         const int bits = oshift + bitlen(((unsigned long long)m->n_tets * s->nsp << 1) | 1ull);
         // known on the host since the push, or (batch) a device count bounded by the buffer
         const int nover = s->batch_mode ? s->ocap : s->hctl->n_over;
-        if (nover > 0) {
+        if (nover > 0 && s->mixed) {
+            { k_overflow_scatter<<<(nover + 255) / 256, 256, 0, s->stream>>>(&s->dctl.p->n_over, nover, s->okey.p, (const long long *)s->oval.p, oshift, (unsigned long long *)s->tacc.p, (unsigned long long *)s->wacc.p); note_launch(); }
+            FP_CUDA(cudaGetLastError());
+        } else if (nover > 0) {
             unsigned long long *ok;
             uint32_t *ov;
             rc = radix_sort<unsigned long long>(s->stream, s->okey.p, s->okey2.p, s->oidx.p, s->okey.p, s->oidx2.p,
                                                 s->batch_mode ? &s->dctl.p->n_over : nullptr, nover, bits,
                                                 &s->osortw, &ok, &ov);
             if (rc) return rc;
-            if (s->mixed) { k_overflow_reduce<long long><<<(nover + 255) / 256, 256, 0, s->stream>>>(&s->dctl.p->n_over, nover, ok, ov, (const long long *)s->oval.p, oshift, (long long *)s->tacc.p, (long long *)s->wacc.p); note_launch(); }
-            else { k_overflow_reduce<double><<<(nover + 255) / 256, 256, 0, s->stream>>>(&s->dctl.p->n_over, nover, ok, ov, (const double *)s->oval.p, oshift, (double *)s->tacc.p, (double *)s->wacc.p); note_launch(); }
+            { k_overflow_reduce<double><<<(nover + 255) / 256, 256, 0, s->stream>>>(&s->dctl.p->n_over, nover, ok, ov, (const double *)s->oval.p, oshift, (double *)s->tacc.p, (double *)s->wacc.p); note_launch(); }
             FP_CUDA(cudaGetLastError());
         }
         // the next step's live count; the new bank holds the first `live` entries
