@@ -60,3 +60,18 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
         cells, particles, workload, steps, warmup = 16, 1000, "plasma_ball", 1, 3
     assert bench.reference_arm(Args()) is None
     assert not called
+
+
+def test_clock_record_rejection_rule():
+    """A timing whose clock record shows a hardware or thermal slowdown, or SM
+    clocks well below their maximum with no reason, is measured again; a power
+    cap alone is kept."""
+    sys.path.insert(0, ROOT)
+    import bench
+    ok = {"sm_mhz": 2070, "sm_max_mhz": 2070, "reasons": []}
+    assert not bench.clock_rejected(ok)
+    assert not bench.clock_rejected(dict(ok, sm_mhz=1500, reasons=["sw_power_cap"]))
+    assert bench.clock_rejected(dict(ok, sm_mhz=1500))                       # a leftover clock lock
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.clock_rejected(dict(ok, reasons=[r]))
+    assert not bench.clock_rejected({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]})
