@@ -69,7 +69,9 @@ extern "C" {
 #define PIC_PUSH_BORIS 0     /* 1..5: Adams-Bashforth of that order */
 
 #define PIC_PRECISION_PLAIN 0 /* everything FP64 */
-#define PIC_PRECISION_MIXED 1 /* FP32 particle state, gather and push; FP64 barycentrics, deposit, solve */
+#define PIC_PRECISION_MIXED 1 /* FP32 particle state, field coefficients, gather and push; barycentrics in
+                                 24-bit fixed point and an integer deposit (continuity exact in integers);
+                                 Newmark solve judged by its FP64 residual, with FP32 correction solves */
 
 #define PIC_PRECOND_JACOBI 0
 #define PIC_PRECOND_GNN 1      /* learned edge preconditioner in a flexible PCG once it has weights

@@ -883,10 +883,12 @@ struct CgOut {
 };
 
 // Chronopoulos-Gear Jacobi-PCG on the context's matrix with values Av in
-// precision T: x, r, u = D^-1 r, w = A u, p, s = A p.  Per-thread sums are
-// kept in T and the block and grid reductions in FP64 (in FP32 the per-thread
-// sums cover about a dozen rows).  max|r| is tracked in FP64 only.  Returns
-// false if a barrier timed out.
+// precision T: x, r, u = D^-1 r, w = A u, p, s = A p.  With UNIT the matrix
+// has a unit diagonal (a diagonally scaled system): u is r itself (the caller
+// passes r for u), and neither D^-1 nor u is read or written.  Per-thread
+// sums are kept in T and the block and grid reductions in FP64 (in FP32 the
+// per-thread sums cover about a dozen rows).  max|r| is tracked in FP64 only.
+// Returns false if a barrier timed out.
 template <typename T, bool UNIT = false>
 __device__ __forceinline__ bool cg_core(SolveCtx &c, const T *__restrict__ Av, const T *__restrict__ Dinv,
                                         const T *b, T *x, T *r, T *u, T *w, T *p, T *s, bool x_zero, double tol2,
