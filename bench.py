@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -38,6 +39,7 @@ from paper_2102_06248_gb300 import workloads as W  # noqa: E402
 
 METRIC = "particle-steps/s (gather+push+deposit) and step time vs plain FP64 GPU path"
 FALLBACK_HBM_GBS = 6800.0
+CLOCK_LOG = None   # --clock-log: where the clock samples of the timed region go ({gpu}: the GPU index)
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (non-tensor) nominal rate
 # DRAM bytes over algorithmic bytes of the MIXED Newmark launch
 # (k_pcg_persistent<1>), from the ncu capture summarised in
@@ -106,7 +108,8 @@ class ClockSampler:
         self.gpu = gpu
         self.proc = None
         self.thread = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu}.csv")
+        self.path = (CLOCK_LOG.replace("{gpu}", str(gpu)) if CLOCK_LOG
+                     else os.path.join(tempfile.gettempdir(), f"fempic_clocks_gpu{gpu}.csv"))
         self.nvml = None
         try:
             import ctypes
@@ -132,7 +135,8 @@ class ClockSampler:
             time.sleep(0.002)
 
     def start(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        if os.path.dirname(self.path):
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
         if self.nvml is not None:
             import threading
             self.samples, self.stop_flag = [], False
@@ -686,6 +690,7 @@ def main():
     ap.add_argument("--particles", type=int, default=16 * 1024 * 1024, help="particles per species")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clock-log", default=None, help="CSV of the clock samples of the timed region ({gpu}: index)")
     ap.add_argument("--skip-plain", action="store_true", help="do not time the plain-FP64 path (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true", help="do not run the end-to-end leg (profiling runs)")
     ap.add_argument("--skip-batched", action="store_true", help="do not run the batched-runs leg")
@@ -698,6 +703,8 @@ def main():
     ap.add_argument("--batch-runs", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=60)
     args = ap.parse_args()
+    global CLOCK_LOG
+    CLOCK_LOG = args.clock_log
     if args.warmup < 3 and args.impl == "gb300":
         args.warmup = 3
     if args.impl == "reference":

@@ -1066,7 +1066,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int nb, const i
                              a.max_iters, o))
             goto timeout;
     } else {
-        // Iterative refinement: the FP64 residual b - A x is the judge; each
+        // Iterative refinement: the FP64 residual b - A x decides; each
         // correction A d = r / sigma is solved in FP32 (values and vectors) to
         // a relative residual of inner_tol, and x += sigma d in FP64.  The
         // correction solve is plain CG on the scaled system
