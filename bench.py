@@ -42,10 +42,11 @@ FALLBACK_HBM_GBS = 6800.0
 CLOCK_LOG = None   # --clock-log: where the clock samples of the timed region go ({gpu}: the GPU index)
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (non-tensor) nominal rate
 # DRAM bytes over algorithmic bytes of the MIXED Newmark launch
-# (k_pcg_persistent<1>), from the ncu capture summarised in
-# profiles/pcg_persistent_plasma_ball_64.md: 19.864 GB measured for 60 FP32 +
-# 2 FP64 iterations whose algorithmic bytes are 19.938 GB.  The FP64 Newmark
-# form has no capture of its current code: its traffic is reported as null.
+# (k_pcg_persistent<1>), from one ncu capture of that kernel on the 64^3
+# plasma ball: 19.864 GB (dram__bytes_read.sum + dram__bytes_write.sum) for 60
+# FP32 + 2 FP64 iterations whose algorithmic bytes are 19.938 GB.  The FP64
+# Newmark form has no capture of its current code: its traffic is reported as
+# null.
 TRAFFIC_RATIO_MIXED = 19.863886 / 19.937848
 TRAFFIC_RATIO_PLAIN = None
 
@@ -591,7 +592,7 @@ def gpu_arm(args):
             "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 push + f64 deposit/solve", "data": "synthetic",
+            "dtype": "f32 push + int64 fixed-point deposit + f32 CG corrections in f64 refinement", "data": "synthetic",
             "config": {"workload": desc, "particles_per_gpu": n_part, "tets": mesh.n_tets,
                        "edges": mesh.n_edges, "interior_edges": mesh.n_int_edges, "dt_s": dt,
                        "precision": "mixed", "parallelism": f"replicas x{world}",
@@ -672,7 +673,9 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_desc(args.workload, args.cells, args.particles)},
+            "data": "synthetic",
+            "config": {"workload": workload_desc(args.workload, cells, per),
+                       "sample_of": workload_desc(args.workload, args.cells, args.particles)},
             "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

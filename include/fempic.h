@@ -292,7 +292,15 @@ int pic_profile_reset(pic_sim *sim);
  * The solve still stops at the same relative residual, and the gradient-
  * subspace completion follows it, so conservation is unchanged.
  * ------------------------------------------------------------------------- */
-#define PIC_GNN_PARAMS 6369    /* float32 parameters (layout in the design notes) */
+/* float32 parameters, in this order: the input weights U[32], V[32] and bias
+ * c[32]; for each of the three layers l the self weights W_l[32][32] (row =
+ * output feature), the neighbour weights Q_l[32][32] and the bias b_l[32]; the
+ * output weights o[32]; the output bias d0.  The network, with A_hat =
+ * D^-1/2 A D^-1/2, a_i = log d_i - mean(log d), rho = sqrt(mean r_i^2 / d_i),
+ * x_i = r_i / (sqrt(d_i) rho):  h0_i = relu(U x_i + V a_i + c),
+ * h_l,i = relu(W_l h_{l-1,i} + Q_l (A_hat h_{l-1})_i + b_l),
+ * y_i = o . h_3,i + d0,  z_i = rho (x_i + y_i) / sqrt(d_i). */
+#define PIC_GNN_PARAMS 6369
 
 typedef struct {
     int32_t steps;          /* Adam steps (e.g. 300) */
@@ -358,9 +366,9 @@ int64_t pic_launch_count(void);
 
 /* Allocation-free electrostatic solve (the paper has no counterpart; it is a
  * service of this library).  For callers that cannot allocate device memory
- * when they need the solve: work recorded under CUDA stream capture, where
- * cudaMalloc is not allowed, or runtimes that hand out all device memory
- * from their own pool.  Solves (G^T M G) phi = rho on the interior nodes
+ * when they need the solve: runtimes that hand out all device memory from
+ * their own pool and forbid libraries to allocate, or services whose memory
+ * budget is fixed at start-up.  Solves (G^T M G) phi = rho on the interior nodes
  * (phi = 0 on wall nodes) with the Jacobi-PCG of pic_sim_init, to the relative
  * residual tol, on `stream`.
  *   rho_nodes [n_nodes], phi_nodes [n_nodes]: device arrays of the current
@@ -369,12 +377,13 @@ int64_t pic_launch_count(void);
  * the library (33.7 MB on every GPU that loads the solver, held until exit),
  * which limits the mesh to 524,288 interior nodes (PIC_ERR_INVALID_ARG above
  * that).  The mesh must already have its device copy, made by a
- * pic_sim_create on it (PIC_ERR_STATE otherwise).  The first call on each
- * device looks up the array's device address and should come before any
- * stream capture.  All calls share the array and it keeps the last call's
- * contents (the call sets everything it reads); calls that overlap on the
- * GPU, from two streams or two threads, race on it.  Synchronises `stream`
- * for its convergence checks. */
+ * pic_sim_create on it (PIC_ERR_STATE otherwise), and the current device
+ * must be the one that holds that copy (PIC_ERR_INVALID_ARG otherwise).  The
+ * first call on each device looks up the array's device address.  All calls
+ * share the array and it keeps the last call's contents (the call sets
+ * everything it reads); calls that overlap on the GPU, from two streams or
+ * two threads, race on it.  Synchronises `stream` for its convergence checks
+ * (PIC_ERR_STATE when `stream` is being captured). */
 int pic_electrostatic_solve_noalloc(const pic_mesh *mesh, const double *rho_nodes, double *phi_nodes, double tol,
                                     void *stream);
 

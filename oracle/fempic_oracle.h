@@ -9,8 +9,8 @@
  * no source.  Everything is FP64, one particle at a time in load order, with
  * sequential sums, no sorting of particles, no staging and no fusion.
  *
- * Conventions (the paper leaves them open; see the readings in the design
- * notes):
+ * Conventions (the paper leaves them open; these are the readings both the
+ * oracle and the GPU library follow):
  *   - edge e = (tail, head) with tail < head (global node ids); edges are
  *     numbered in lexicographic order of (tail, head);
  *   - face f = (a, b, c) with a < b < c, numbered lexicographically; its

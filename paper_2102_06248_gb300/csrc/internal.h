@@ -179,6 +179,7 @@ struct Mesh {
     // host build -> device upload (pic_sim_create uploads on first use)
     std::unique_ptr<HostStage> stage;
     int uploaded = 0;
+    int device = -1;           // CUDA device that holds the device copy
 };
 
 int build_mesh(const pic_mesh_desc *d, Mesh *m);   // host only

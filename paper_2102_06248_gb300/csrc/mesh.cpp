@@ -578,6 +578,9 @@ int mesh_upload(Mesh *m) {
     if ((rc = csr(H.n2e, &m->n2e)) || (rc = m->n2e_sgn.upload(H.n2e_sgn))) return rc;
     if ((rc = m->f2e.upload(H.f2e)) || (rc = m->edge_nodes.upload(H.edge_nodes))) return rc;
     if ((rc = m->edge_canon.upload(m->h_edge_canonical)) || (rc = m->node_bnd.upload(m->h_node_bnd))) return rc;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+    m->device = dev;
     m->uploaded = 1;
     m->stage.reset();
     return PIC_OK;

@@ -1607,10 +1607,10 @@ int read_control(Sim *s) {
 // Allocation-free electrostatic solve.
 //
 // Some callers cannot allocate device memory at the point where they need a
-// solve: code that runs while a CUDA stream is being captured into a graph
-// (cudaMalloc is not a capturable operation), or a host runtime that owns all
-// device memory through its own pool and forbids allocations from libraries.
-// For them pic_electrostatic_solve_noalloc runs the Jacobi-PCG of the node
+// solve: a host runtime that hands out all device memory from its own pool and
+// forbids libraries to allocate, or a service whose memory budget was fixed
+// when it started.  For them pic_electrostatic_solve_noalloc runs the
+// Jacobi-PCG of the node
 // Laplacian (the same kernels as the start-up solve of pic_sim_init) with its
 // working vectors in the fixed array below instead of buffers it allocates.
 //
@@ -1631,7 +1631,7 @@ constexpr int kNoAllocMaxDevices = 64;
 double *g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
 // device address of the scratch array on the current device (looked up once
-// per device; the first call on a device must not run under stream capture)
+// per device)
 int noalloc_scratch(double **out) {
     int dev = 0;
     FP_CUDA(cudaGetDevice(&dev));
@@ -1666,6 +1666,22 @@ int electrostatic_solve_noalloc(const Mesh *m, const double *rho_nodes, double *
     if (!(tol > 0) || !rho_nodes || !phi_nodes) {
         set_error("pic_electrostatic_solve_noalloc: needs tol > 0 and device arrays for rho and phi");
         return PIC_ERR_INVALID_ARG;
+    }
+    int dev = -1;
+    FP_CUDA(cudaGetDevice(&dev));
+    if (dev != m->device) {
+        set_error("pic_electrostatic_solve_noalloc: the current device (" + std::to_string(dev) +
+                  ") is not the device that holds the mesh (" + std::to_string(m->device) + ")");
+        return PIC_ERR_INVALID_ARG;
+    }
+    // the convergence checks below read the CG state back and wait for the
+    // stream, which a stream under capture does not allow
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FP_CUDA(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone) {
+        set_error("pic_electrostatic_solve_noalloc: the stream is being captured; the call waits on the stream "
+                  "for its convergence checks");
+        return PIC_ERR_STATE;
     }
     double *base = nullptr;
     int rc = noalloc_scratch(&base);

@@ -414,8 +414,20 @@ class Batch:
 def electrostatic_solve_noalloc(mesh: Mesh, rho, phi, tol: float = 1e-14, stream=None):
     """pic_electrostatic_solve_noalloc on CUDA tensors rho, phi [n_nodes] (float64).
 
-    The library allocates nothing during this call (see include/fempic.h)."""
+    The library allocates nothing during this call.  The C entry point takes
+    no lengths, so both tensors are checked here before any launch: float64,
+    contiguous, n_nodes elements, on the current CUDA device."""
     load()
+    import torch
+    for name, t in (("rho", rho), ("phi", phi)):
+        if not isinstance(t, torch.Tensor):
+            raise PicError(1, "electrostatic_solve_noalloc", f"{name} must be a torch tensor")
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous() or t.numel() != mesh.n_nodes:
+            raise PicError(1, "electrostatic_solve_noalloc",
+                           f"{name} must be a contiguous float64 CUDA tensor of {mesh.n_nodes} elements "
+                           f"(got {t.dtype}, {t.device}, {t.numel()} elements)")
+        if t.device.index != torch.cuda.current_device():
+            raise PicError(1, "electrostatic_solve_noalloc", f"{name} is not on the current CUDA device")
     st = None if stream is None else C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check(_lib.pic_electrostatic_solve_noalloc(mesh._h, C.c_void_p(rho.data_ptr()), C.c_void_p(phi.data_ptr()),
                                                 tol, st), "pic_electrostatic_solve_noalloc")

@@ -1,7 +1,7 @@
 """Batched stepping: several independent runs of uneven size stepped together
 (one stream per run, one persistent launch per solve over all runs, six-step
-CUDA graphs) give exactly what stepping each run alone gives, and each run
-still conserves charge.
+CUDA graphs) give exactly what stepping each run alone gives, each run still
+conserves charge, and each member agrees with the FP64 oracle.
 """
 import numpy as np
 import pytest
@@ -62,6 +62,35 @@ def test_batch_equals_individual_steps(F, precision):
     np.testing.assert_array_equal(solo[1].field("E"), memb[1].field("E"))
     batch.step(7)         # graph dropped (a member moved), recaptured
     assert batch.info()["graph"] == 1
+
+
+def test_batch_members_match_oracle(F, oracle_lib):
+    """Each member of a batch (eager first step, then a six-step graph
+    launch) against the FP64 oracle stepped alone: fields and particles
+    within 1e-10 relative, as for a single simulation (solves at 1e-13)."""
+    cases = runs(F, "plain")
+    memb = [F.sim_from_workload(wl, dt, cg_tol=1e-13) for wl, dt in cases]
+    orcs = [oracle_lib.from_workload(wl, dt, cg_tol=1e-13) for wl, dt in cases]
+    batch = F.Batch(memb)
+    steps = 7
+    batch.step(steps)
+    assert batch.info()["graph_launches"] == 1
+    for o in orcs:
+        o.step(steps)
+    for (wl, _), g, o in zip(cases, memb, orcs):
+        for f in ("E", "E_PREV", "G", "RHO", "WALL"):
+            a, b = g.field(f), o.field(f)
+            assert np.abs(a - b).max() <= 1e-10 * max(np.abs(b).max(), 1e-300), (wl.name, f)
+        b_ref = o.field("B")
+        sc = max(np.abs(b_ref).max(), np.abs(o.field("E")).max() * wl.mesh.h / W.C0)
+        assert np.abs(g.field("B") - b_ref).max() <= 1e-10 * sc, wl.name
+        gx, gv, gt, gid = g.particles()
+        ox, ov, ot, alive = o.particles()
+        ids = np.where(alive)[0]
+        assert np.array_equal(gid, ids) and np.array_equal(gt, ot[ids]), wl.name
+        assert np.abs(gx - ox[ids]).max() <= 1e-10
+        assert np.abs(gv - ov[ids]).max() <= 1e-10 * np.abs(ov).max()
+        assert g.diag()["n_alive"] == o.diag()["n_alive"]
 
 
 def test_batch_rejects_bad_members(F):

@@ -162,6 +162,37 @@ def test_larmor_mfem_parity(F, oracle_lib):
     assert d["continuity_abs"] <= 1e-12 * d["rho_max"] and d["gauss_abs"] <= 1e-12 * d["rho_max"]
 
 
+def test_larmor_mfem_mixed(F, oracle_lib):
+    """The single-electron orbit in MIXED precision against the FP64 oracle.
+    The electron moves v dt = 2 pi r_L / 64 per step in a box of 10 r_L, so an
+    FP32 position ulp is ~ 2 eps32 * 10 r_L / (v dt) ~ 2.4e-5 of a step's
+    current and of the fields it drives; after 40 steps the orbit still
+    agrees to FP32 round-off accumulated over the steps, and conservation
+    holds every step."""
+    wl = W.larmor_orbit_box(n_cells=8, steps=40)
+    from oracle.oracle import from_workload
+    osim = from_workload(wl, wl.dt, cg_tol=1e-13)
+    gsim = F.sim_from_workload(wl, wl.dt, precision="mixed", cg_tol=1e-13)
+    side = wl.mesh.size[0]
+    vperp = 0.05 * W.C0
+    tol = 2.0 * np.finfo(np.float32).eps * side / (vperp * wl.dt)
+    for step in range(40):
+        osim.step()
+        gsim.step()
+        if step < 10:
+            for name in ("E", "G", "RHO"):
+                assert rel_err(gsim.field(name), osim.field(name)) <= tol, (step, name)
+        d = gsim.diag()
+        assert d["continuity_abs"] <= 1e-12 * d["rho_max"], d
+        assert d["gauss_abs"] <= 1e-12 * d["rho_max"], d
+    gx, gv, gt, gid = gsim.particles()
+    ox, ov, ot, alive = osim.particles()
+    assert np.array_equal(gid, np.where(alive)[0]) and np.array_equal(gt, ot[alive])
+    # 40 steps, each adding at most a few ulps of the box to the position
+    assert np.abs(gx - ox[alive]).max() <= 40 * 4 * np.finfo(np.float32).eps * side
+    assert np.abs(gv - ov[alive]).max() <= 40 * 4 * np.finfo(np.float32).eps * vperp
+
+
 def test_conservation_100_steps(F):
     """Sec. III.A on the GPU: continuity and Gauss at round-off for 100 steps
     of the thermal cube at the production tolerance (cg_tol 1e-10)."""

@@ -45,19 +45,23 @@ def test_newmark_single_mode(oracle_lib, small, form):
     sim = empty_sim(oracle_lib, m, dt, form)
     sim.set_field("E", u)
     sim.set_field("E_PREV", math.cos(phi) * u)
-    if form == "mfem":
-        # Faraday/Ampere pair: b^n = beta_n C u with beta_n = -sin(n phi)/w
-        Cm = m.incidence_dense("C").astype(float)
-        cu = Cm @ u
-        sim.set_field("B", np.zeros(m.n_faces))
-        sim.set_field("B_PREV", (math.sin(phi) / omega) * cu)
+    # b^n = -sin(n phi)/w C u in both forms.  Maxwell-solver form: the
+    # Faraday/Ampere pair of the recurrence keeps it.  Wave-equation form: the
+    # trapezoid update b^{n+1} = b^n - dt/2 C (e^{n+1} + e^n) sums to it
+    # because tan(phi/2) = w dt/2 (the Newmark phase), so this pins the
+    # wave-equation Faraday step against a closed form as well.
+    Cm = m.incidence_dense("C").astype(float)
+    cu = Cm @ u
+    sim.set_field("B", np.zeros(m.n_faces))
+    sim.set_field("B_PREV", (math.sin(phi) / omega) * cu)
     n = 25
-    sim.step(n)
+    for k in range(1, n + 1):
+        sim.step()
+        if k in (1, 2, 7, n):
+            b = sim.field("B")
+            assert np.allclose(b, -(math.sin(k * phi) / omega) * cu, atol=1e-9 * np.abs(cu).max() / omega), k
     e = sim.field("E")
     assert np.allclose(e, math.cos(n * phi) * u, atol=1e-9)
-    if form == "mfem":
-        b = sim.field("B")
-        assert np.allclose(b, -(math.sin(n * phi) / omega) * cu, atol=1e-9 * np.abs(cu).max() / omega)
 
 
 def test_newmark_solve_matches_dense(oracle_lib):
