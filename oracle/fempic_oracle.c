@@ -99,9 +99,11 @@ struct orc_mesh {
     int *tet_nbr;             /* 4 per tet: tet across local face k, -1 on the wall */
     int *face_tets;           /* 2 per face */
     int *edge_bnd, *node_bnd, *face_bnd;
+    int *face_abs;            /* 1 for a wall face with the first-order absorbing condition */
     double *grad;             /* 12 per tet: grad lam_k */
     double *vol;
     csr M, K, H, L;           /* edge mass, curl-curl, face mass, node Laplacian G^T M G */
+    csr I;                    /* surface impedance matrix of the absorbing faces (all edges) */
 };
 
 static int cmp_i64(const void *x, const void *y) {
@@ -135,6 +137,7 @@ void orc_lambda(const orc_mesh *m, int t, const double *r, double *lam) {
 }
 
 static void assemble_matrices(orc_mesh *m, double eps0, double mu0);
+static int edge_of(const orc_mesh *m, int a, int b);
 
 orc_mesh *orc_mesh_new(int n_nodes, const double *xyz, int n_tets, const int *tets, char *err, int errlen) {
     if (n_nodes <= 0 || n_tets <= 0 || !xyz || !tets) { snprintf(err, errlen, "empty mesh"); return NULL; }
@@ -255,16 +258,89 @@ orc_mesh *orc_mesh_new(int n_nodes, const double *xyz, int n_tets, const int *te
     for (int e = 0; e < ne; e++) m->n_int_edges += !m->edge_bnd[e];
     for (int n = 0; n < n_nodes; n++) m->n_int_nodes += !m->node_bnd[n];
     free(ek); free(fk); free(fs);
+    m->face_abs = (int *)calloc((size_t)nf, sizeof(int));
     assemble_matrices(m, 8.8541878128e-12, 1.0 / (8.8541878128e-12 * 299792458.0 * 299792458.0));
+    m->I.n_rows = ne;
+    m->I.rowptr = (int *)calloc((size_t)ne + 1, sizeof(int));
+    m->I.col = (int *)malloc(sizeof(int));
+    m->I.val = (double *)malloc(sizeof(double));
     return m;
+}
+
+/* ------------------------------------------------------------------ */
+/* First-order absorbing walls (Sec. II.A, Eq. impedanceBC with the    */
+/* vacuum admittance, in its time-differentiated form).  The weak form  */
+/* of the wave equation gains the boundary term                         */
+/*   (1/c) [*I] de/dt,  [*I]_ij = <n x W1_i, mu0^-1 n x W1_j>_{absorbing} */
+/* (the paper's c [*I] of Eq. wave_cont is written for its scaled        */
+/* equation; in SI the factor is 1/(mu0 c) = eps0 c).  On a wall face    */
+/* only the three face edges have a tangential trace (the W1 of an edge  */
+/* to the opposite vertex is lam_a grad lam_d there, normal to the face), */
+/* and n x W1_ab = n x (lam_a grad_s lam_b - lam_b grad_s lam_a) with the */
+/* surface gradients of the face's own barycentrics:                    */
+/*   grad_s lam_A = n x (x_C - x_B) / (2 S)  for (A, B, C) cyclic in the */
+/* face orientation, S the face area.  Products of barycentrics on a     */
+/* triangle integrate to S (1 + delta_ab) / 12.                         */
+/* ------------------------------------------------------------------ */
+int orc_mesh_set_absorbing(orc_mesh *m, const int *tet_face_bc) {
+    int nf = m->n_faces, ne = m->n_edges;
+    memset(m->face_abs, 0, sizeof(int) * nf);
+    for (int t = 0; t < m->n_tets; t++)
+        for (int k = 0; k < 4; k++) {
+            int f = m->tet_face[4 * t + k];
+            if (m->face_bnd[f] && tet_face_bc[4 * t + k]) m->face_abs[f] = 1;
+        }
+    /* an edge is held at zero when it lies on a perfectly conducting wall face */
+    memset(m->edge_bnd, 0, sizeof(int) * ne);
+    for (int f = 0; f < nf; f++) {
+        if (!m->face_bnd[f] || m->face_abs[f]) continue;
+        int a = m->face[3 * f], b = m->face[3 * f + 1], c = m->face[3 * f + 2];
+        m->edge_bnd[edge_of(m, a, b)] = m->edge_bnd[edge_of(m, b, c)] = m->edge_bnd[edge_of(m, a, c)] = 1;
+    }
+    m->n_int_edges = 0;
+    for (int e = 0; e < ne; e++) m->n_int_edges += !m->edge_bnd[e];
+    const double mu0 = 1.0 / (8.8541878128e-12 * 299792458.0 * 299792458.0);
+    coo ci = {0};
+    for (int f = 0; f < nf; f++) {
+        if (!m->face_abs[f]) continue;
+        int v[3] = {m->face[3 * f], m->face[3 * f + 1], m->face[3 * f + 2]};
+        const double *x[3] = {m->xyz + 3 * v[0], m->xyz + 3 * v[1], m->xyz + 3 * v[2]};
+        double u[3], w[3], nrm[3];
+        sub3(x[1], x[0], u); sub3(x[2], x[0], w); cross3(u, w, nrm);
+        double twoS = sqrt(dot3(nrm, nrm));
+        for (int d = 0; d < 3; d++) nrm[d] /= twoS;
+        double S = 0.5 * twoS;
+        double gs[3][3];
+        for (int A = 0; A < 3; A++) {
+            int B = (A + 1) % 3, C = (A + 2) % 3;
+            double cb[3];
+            sub3(x[C], x[B], cb);
+            cross3(nrm, cb, gs[A]);
+            for (int d = 0; d < 3; d++) gs[A][d] /= twoS;
+        }
+        /* face edges in global orientation (tail < head): (0,1), (1,2), (0,2) */
+        const int fe[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+        for (int p = 0; p < 3; p++)
+            for (int q = 0; q < 3; q++) {
+                int i1 = fe[p][0], j1 = fe[p][1], i2 = fe[q][0], j2 = fe[q][1];
+#define LL(a, b) (S * ((a) == (b) ? 2.0 : 1.0) / 12.0)
+                double val = LL(i1, i2) * dot3(gs[j1], gs[j2]) - LL(i1, j2) * dot3(gs[j1], gs[i2])
+                           - LL(j1, i2) * dot3(gs[i1], gs[j2]) + LL(j1, j2) * dot3(gs[i1], gs[i2]);
+#undef LL
+                coo_add(&ci, edge_of(m, v[fe[p][0]], v[fe[p][1]]), edge_of(m, v[fe[q][0]], v[fe[q][1]]), val / mu0);
+            }
+    }
+    csr_free(&m->I);
+    m->I = coo_to_csr(&ci, ne);
+    return ORC_OK;
 }
 
 void orc_mesh_free(orc_mesh *m) {
     if (!m) return;
     free(m->xyz); free(m->tet); free(m->edge); free(m->face); free(m->tet_edge); free(m->tet_face);
     free(m->tet_face_sign); free(m->tet_nbr); free(m->face_tets); free(m->edge_bnd); free(m->node_bnd);
-    free(m->face_bnd); free(m->grad); free(m->vol);
-    csr_free(&m->M); csr_free(&m->K); csr_free(&m->H); csr_free(&m->L);
+    free(m->face_bnd); free(m->face_abs); free(m->grad); free(m->vol);
+    csr_free(&m->M); csr_free(&m->K); csr_free(&m->H); csr_free(&m->L); csr_free(&m->I);
     free(m);
 }
 
@@ -474,6 +550,7 @@ static const csr *mat_of(const orc_mesh *m, int which) {
     case ORC_MAT_M: return &m->M;
     case ORC_MAT_K: return &m->K;
     case ORC_MAT_H: return &m->H;
+    case ORC_MAT_I: return &m->I;
     default: return &m->L;
     }
 }
@@ -614,12 +691,17 @@ orc_sim *orc_sim_new(orc_mesh *m, const orc_config *cfg) {
     s->b = calloc(nf, 8); s->b_prev = calloc(nf, 8);
     s->rho = calloc(nn, 8); s->rho_prev = calloc(nn, 8); s->wall = calloc(nn, 8); s->wall_prev = calloc(nn, 8);
     s->rho_bg = calloc(nn, 8); s->phi = calloc(nn, 8);
-    /* A = M + dt^2/4 K (Sec. II.B, wave-equation and Maxwell-solver forms alike) */
-    double c4 = 0.25 * cfg->dt * cfg->dt;
+    /* System matrix of the field update.  Newmark (Sec. II.B), wave-equation
+     * and Maxwell-solver forms alike: A = M + dt^2/4 K + dt/2 (1/c) [*I].
+     * Backward difference: A = M + dt^2 K + dt (1/c) [*I].  [*I] is zero
+     * without absorbing walls. */
+    double c4 = (cfg->form == ORC_FORM_BD ? 1.0 : 0.25) * cfg->dt * cfg->dt;
+    double ci = (cfg->form == ORC_FORM_BD ? 1.0 : 0.5) * cfg->dt / 299792458.0;
     coo ca = {0};
     for (int r = 0; r < ne; r++) {
         for (int k = m->M.rowptr[r]; k < m->M.rowptr[r + 1]; k++) coo_add(&ca, r, m->M.col[k], m->M.val[k]);
         for (int k = m->K.rowptr[r]; k < m->K.rowptr[r + 1]; k++) coo_add(&ca, r, m->K.col[k], c4 * m->K.val[k]);
+        for (int k = m->I.rowptr[r]; k < m->I.rowptr[r + 1]; k++) coo_add(&ca, r, m->I.col[k], ci * m->I.val[k]);
     }
     s->A = coo_to_csr(&ca, ne);
     for (int r = 0; r < ne; r++)
@@ -754,12 +836,15 @@ static int pcg(const csr *A, const double *dA, const int *bnd, const double *b, 
 }
 
 static void compute_diag(orc_sim *s, int cg_iters, double cg_relres);
-/* Completion of the Newmark solve on the gradient subspace.  The part of the
+/* Completion of the field solve on the gradient subspace.  The part of the
  * residual that the divergence sees is d = G_int^T (b - A x).  Because
- * G^T K = 0 and G^T C^T = 0 it equals, for the wave-equation form,
- *   d = G_int^T [ M (2 e^n - e^{n-1} - x) - (Gbar^{n+1} - 2 Gbar^n + Gbar^{n-1}) ]
- * and for the Maxwell-solver form
+ * G^T K = 0, G^T C^T = 0 and G_int^T [*I] = 0 (an interior node touches no
+ * wall-face edge) it equals, for the wave-equation form,
+ *   d = G_int^T [ M (2 e^n - e^{n-1} - x) - (Gbar^{n+1} - 2 Gbar^n + Gbar^{n-1}) ],
+ * for the Newmark Maxwell-solver form
  *   d = G_int^T [ M (e^{n-1} - x) - (Gbar^{n+1} - Gbar^{n-1}) ],
+ * and for the backward-difference form
+ *   d = G_int^T [ M (e^n - x) - (Gbar^{n+1} - Gbar^n) ],
  * which is how it is evaluated here (the K terms would only add rounding).
  * A CG stopped at a relative residual leaves d at the tolerance, and the
  * Gauss residual then drifts by d every step (Sec. III.A: errors of the
@@ -773,12 +858,14 @@ static int gradient_completion(orc_sim *s, const double *b, const double *gn1, d
     double *r = calloc(ne, 8), *tmp = calloc(ne, 8), *d = calloc(nn, 8), *psi = calloc(nn, 8), *dL = calloc(nn, 8);
     for (int e = 0; e < ne; e++) {
         if (s->cfg.form == ORC_FORM_WE) tmp[e] = 2.0 * s->e[e] - s->e_prev[e] - x[e];
-        else tmp[e] = s->e_prev[e] - x[e];
+        else if (s->cfg.form == ORC_FORM_MFEM) tmp[e] = s->e_prev[e] - x[e];
+        else tmp[e] = s->e[e] - x[e];
     }
     csr_matvec(&m->M, tmp, r);
     for (int e = 0; e < ne; e++) {
         if (s->cfg.form == ORC_FORM_WE) r[e] -= gn1[e] - 2.0 * s->g[e] + s->g_prev[e];
-        else r[e] -= gn1[e] - s->g_prev[e];
+        else if (s->cfg.form == ORC_FORM_MFEM) r[e] -= gn1[e] - s->g_prev[e];
+        else r[e] -= gn1[e] - s->g[e];
     }
     for (int e = 0; e < ne; e++) {
         d[m->edge[2 * e + 1]] += r[e];
@@ -916,11 +1003,36 @@ static int move_particle(orc_sim *s, int p) {
     if (rc) { free(tl); free(pts); snprintf(s->err, sizeof s->err, "particle %d exceeded the walk cap", p); return rc; }
     double qw = s->q[p] * s->w[p];
     double S[3] = {r[0], r[1], r[2]};
-    for (int k = 0; k < nseg; k++) {
-        double g6[6];
-        orc_segment_w1(m, tl[k], S, pts + 3 * k, g6);
-        for (int l = 0; l < 6; l++) s->dg[m->tet_edge[6 * tl[k] + l]] += qw * g6[l];
-        memcpy(S, pts + 3 * k, 24);
+    if (s->cfg.current_form == ORC_CURRENT_POINT) {
+        /* Negative control (Sec. II.B, Eqs. badNmB / badwave): the field update
+         * is driven by the point current q w v W1(r) sampled once per step, at
+         * the midpoint of the path, instead of the path integral: the increment
+         * is q w W1(r_mid) . (r_end - r^n), W1 taken in the tet that holds
+         * r_mid.  It equals the path integral while the path stays in one tet
+         * (W1 is linear along it) and differs when the path crosses faces. */
+        const double *end = pts + 3 * (nseg - 1);
+        double mid[3], dr[3], len2 = 0.0;
+        for (int d = 0; d < 3; d++) { mid[d] = 0.5 * (r[d] + end[d]); dr[d] = end[d] - r[d]; len2 += dr[d] * dr[d]; }
+        int tm = tl[nseg - 1];
+        for (int k = 0; k < nseg; k++) {
+            double ek[3], l2 = 0.0;
+            for (int d = 0; d < 3; d++) { ek[d] = pts[3 * k + d] - r[d]; l2 += ek[d] * ek[d]; }
+            if (4.0 * l2 >= len2) { tm = tl[k]; break; }   /* the piece that ends past the midpoint */
+        }
+        double lam[4], w[3];
+        orc_lambda(m, tm, mid, lam);
+        for (int l = 0; l < 6; l++) {
+            whitney1(m, tm, l, lam, w);
+            s->dg[m->tet_edge[6 * tm + l]] += qw * dot3(w, dr);
+        }
+        memcpy(S, end, 24);
+    } else {
+        for (int k = 0; k < nseg; k++) {
+            double g6[6];
+            orc_segment_w1(m, tl[k], S, pts + 3 * k, g6);
+            for (int l = 0; l < 6; l++) s->dg[m->tet_edge[6 * tl[k] + l]] += qw * g6[l];
+            memcpy(S, pts + 3 * k, 24);
+        }
     }
     int tend = tl[nseg - 1];
     if (absorbed) {
@@ -962,14 +1074,35 @@ int orc_step(orc_sim *s) {
     double *gn1 = malloc(sizeof(double) * ne);
     for (int e = 0; e < ne; e++) gn1[e] = s->g[e] + s->dg[e];
     double *rhs = calloc(ne, 8), *t1 = calloc(ne, 8), *t2 = calloc(ne, 8), *x = calloc(ne, 8);
+    const double yi = dt / 299792458.0;   /* dt/c: the absorbing term's scale */
     if (s->cfg.form == ORC_FORM_WE) {
-        /* (M + dt^2/4 K) e^{n+1} = (2M - dt^2/2 K) e^n - (M + dt^2/4 K) e^{n-1}
-         *                          - (Gbar^{n+1} - 2 Gbar^n + Gbar^{n-1})        */
+        /* Newmark (gamma = 1/2, beta = 1/4) of M e'' + (1/c)[*I] e' + K e = -d/dt j
+         * with the Gbar substitution:
+         * (M + dt/2c I + dt^2/4 K) e^{n+1} = (2M - dt^2/2 K) e^n
+         *     - (M - dt/2c I + dt^2/4 K) e^{n-1} - (Gbar^{n+1} - 2 Gbar^n + Gbar^{n-1}),
+         * written with A = M + dt/2c I + dt^2/4 K as -A e^{n-1} + dt/c I e^{n-1} */
         csr_matvec(&m->M, s->e, t1);
         csr_matvec(&m->K, s->e, t2);
         for (int i = 0; i < ne; i++) rhs[i] = 2.0 * t1[i] - 0.5 * dt * dt * t2[i];
         csr_matvec(&s->A, s->e_prev, t1);
         for (int i = 0; i < ne; i++) rhs[i] -= t1[i] + (gn1[i] - 2.0 * s->g[i] + s->g_prev[i]);
+        csr_matvec(&m->I, s->e_prev, t1);
+        for (int i = 0; i < ne; i++) rhs[i] += yi * t1[i];
+    } else if (s->cfg.form == ORC_FORM_BD) {
+        /* First-order backward difference of the Maxwell-solver system, with
+         * dGbar/dt in place of the current:
+         *   (b^{n+1} - b^n) + dt C e^{n+1} = 0
+         *   M (e^{n+1} - e^n) - dt C^T H b^{n+1} + dt/c I e^{n+1} = -(Gbar^{n+1} - Gbar^n);
+         * eliminating b^{n+1}:
+         *   (M + dt^2 K + dt/c I) e^{n+1} = M e^n + dt C^T H b^n - (Gbar^{n+1} - Gbar^n) */
+        csr_matvec(&m->M, s->e, t1);
+        for (int i = 0; i < ne; i++) rhs[i] = t1[i] - (gn1[i] - s->g[i]);
+        double *hb = calloc(nf, 8);
+        csr_matvec(&m->H, s->b, hb);
+        int *cr = malloc(sizeof(int) * 3 * nf), *cc = malloc(sizeof(int) * 3 * nf), *cv = malloc(sizeof(int) * 3 * nf);
+        orc_mesh_C(m, cr, cc, cv);
+        for (int k = 0; k < 3 * nf; k++) rhs[cc[k]] += dt * cv[k] * hb[cr[k]];
+        free(cr); free(cc); free(cv); free(hb);
     } else {
         /* Maxwell-solver form: the Faraday row
          *   1/2 (b^{n+1} - b^{n-1}) + dt C (e^{n+1}/4 + e^n/2 + e^{n-1}/4) = 0
@@ -992,6 +1125,11 @@ int orc_step(orc_sim *s) {
         for (int k = 0; k < 3 * nf; k++) rhs[cc[k]] += dt * cv[k] * hb[cr[k]];
         free(cr); free(cc); free(cv); free(bs); free(hb);
         for (int i = 0; i < ne; i++) rhs[i] -= gn1[i] - s->g_prev[i];
+        /* absorbing walls: the Ampere row's 2 dt/c I (e^{n+1}/4 + e^n/2 + e^{n-1}/4)
+         * keeps its e^{n+1} part in A and moves - dt/c I (e^n + e^{n-1}/2) here */
+        for (int i = 0; i < ne; i++) t2[i] = s->e[i] + 0.5 * s->e_prev[i];
+        csr_matvec(&m->I, t2, t1);
+        for (int i = 0; i < ne; i++) rhs[i] -= yi * t1[i];
     }
     /* initial guess 2 e^n - e^{n-1} */
     for (int i = 0; i < ne; i++) x[i] = 2.0 * s->e[i] - s->e_prev[i];
@@ -1019,11 +1157,15 @@ int orc_step(orc_sim *s) {
         /* Faraday by the trapezoid rule: b^{n+1} = b^n - dt/2 C (e^{n+1} + e^n) */
         for (int f = 0; f < nf; f++) bn1[f] = s->b[f];
         for (int k = 0; k < 3 * nf; k++) bn1[cr[k]] -= 0.5 * dt * cv[k] * (x[cc[k]] + s->e[cc[k]]);
-    } else {
+    } else if (s->cfg.form == ORC_FORM_MFEM) {
         /* Faraday row of the Maxwell-solver recurrence */
         for (int f = 0; f < nf; f++) bn1[f] = s->b_prev[f];
         for (int k = 0; k < 3 * nf; k++)
             bn1[cr[k]] -= 2.0 * dt * cv[k] * (0.25 * x[cc[k]] + 0.5 * s->e[cc[k]] + 0.25 * s->e_prev[cc[k]]);
+    } else {
+        /* Faraday row of the backward difference: b^{n+1} = b^n - dt C e^{n+1} */
+        for (int f = 0; f < nf; f++) bn1[f] = s->b[f];
+        for (int k = 0; k < 3 * nf; k++) bn1[cr[k]] -= dt * cv[k] * x[cc[k]];
     }
     free(cr); free(cc); free(cv);
     memcpy(s->b_prev, s->b, sizeof(double) * nf);

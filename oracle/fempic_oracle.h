@@ -36,11 +36,16 @@ typedef struct orc_sim orc_sim;
 enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_MESH = 2, ORC_ERR_OUTSIDE = 3,
        ORC_ERR_WALK_CAP = 4, ORC_ERR_CG = 5, ORC_ERR_NAN = 6 };
 
-enum { ORC_FORM_WE = 0, ORC_FORM_MFEM = 1 };
+/* WE: Newmark wave equation; MFEM: Newmark Maxwell-solver (mixed) form;
+ * BD: Maxwell-solver form with the first-order backward difference */
+enum { ORC_FORM_WE = 0, ORC_FORM_MFEM = 1, ORC_FORM_BD = 2 };
+/* current_form: how the particles drive the field update */
+enum { ORC_CURRENT_GBAR = 0,    /* the path-integrated current Gbar (Sec. III.A) */
+       ORC_CURRENT_POINT = 1 }; /* negative control: point currents at the step midpoint */
 /* pusher: 0 = Boris, k = 1..5 = Adams-Bashforth of order k */
 enum { ORC_PUSH_BORIS = 0 };
 
-enum { ORC_MAT_M = 0, ORC_MAT_K = 1, ORC_MAT_H = 2, ORC_MAT_L = 3 };
+enum { ORC_MAT_M = 0, ORC_MAT_K = 1, ORC_MAT_H = 2, ORC_MAT_L = 3, ORC_MAT_I = 4 };
 
 enum { ORC_FIELD_E = 0, ORC_FIELD_E_PREV = 1, ORC_FIELD_B = 2, ORC_FIELD_G = 3,
        ORC_FIELD_RHO = 4, ORC_FIELD_WALL = 5, ORC_FIELD_PHI = 6, ORC_FIELD_DG = 7,
@@ -58,6 +63,7 @@ typedef struct {
     int walk_cap;        /* max tets visited by one particle in one step */
     int gradient_completion; /* 1: complete the solve on the gradient subspace */
     double completion_tol;   /* completion stops when max|defect| <= this * max|rho+wall| (0: relative init_tol) */
+    int current_form;        /* ORC_CURRENT_GBAR, or ORC_CURRENT_POINT (the negative control) */
 } orc_config;
 
 /* diagnostics record, all FP64 */
@@ -91,6 +97,13 @@ void orc_mesh_D(const orc_mesh *m, int *row, int *col, int *val);
 void orc_mesh_tet_data(const orc_mesh *m, int *tet_edge, int *tet_face, int *tet_nbr);
 void orc_mesh_flags(const orc_mesh *m, int *edge_bnd, int *node_bnd, int *face_bnd);
 void orc_mesh_geom(const orc_mesh *m, double *grad /* 12*n_tets */, double *vol);
+/* wall boundary conditions: tet_face_bc[4*t+k] for the face of tet t opposite
+ * its k-th vertex (vertex order as given), 1 = first-order absorbing, 0 =
+ * perfectly conducting; ignored for interior faces.  Edges on conducting wall
+ * faces are held at zero, every other edge is a degree of freedom; the
+ * surface impedance matrix ORC_MAT_I is assembled over the absorbing faces.
+ * Call before orc_sim_new. */
+int orc_mesh_set_absorbing(orc_mesh *m, const int *tet_face_bc);
 /* assembled sparse matrices (global numbering, all edges / faces / nodes) */
 int orc_matrix_nnz(const orc_mesh *m, int which);
 void orc_matrix_csr(const orc_mesh *m, int which, int *rowptr, int *col, double *val);

@@ -51,7 +51,8 @@ class _Config(C.Structure):
     _fields_ = [("form", C.c_int), ("pusher", C.c_int), ("dt", C.c_double), ("b0", C.c_double * 3),
                 ("cg_tol", C.c_double), ("cg_max_iters", C.c_int), ("init_tol", C.c_double),
                 ("rho_background", C.c_double), ("walk_cap", C.c_int),
-                ("gradient_completion", C.c_int), ("completion_tol", C.c_double)]
+                ("gradient_completion", C.c_int), ("completion_tol", C.c_double),
+                ("current_form", C.c_int)]
 
 
 def _load():
@@ -73,6 +74,8 @@ def _load():
     lib.orc_mesh_tet_data.argtypes = [P, ip, ip, ip]
     lib.orc_mesh_flags.argtypes = [P, ip, ip, ip]
     lib.orc_mesh_geom.argtypes = [P, dp, dp]
+    lib.orc_mesh_set_absorbing.argtypes = [P, ip]
+    lib.orc_mesh_set_absorbing.restype = C.c_int
     lib.orc_matrix_nnz.argtypes = [P, C.c_int]
     lib.orc_matrix_nnz.restype = C.c_int
     lib.orc_matrix_csr.argtypes = [P, C.c_int, ip, ip, dp]
@@ -117,7 +120,7 @@ def _ip(a: np.ndarray):
 
 FIELDS = {"E": 0, "E_PREV": 1, "B": 2, "G": 3, "RHO": 4, "WALL": 5, "PHI": 6, "DG": 7, "RHO_BG": 8,
           "B_PREV": 9, "G_PREV": 10}
-MATS = {"M": 0, "K": 1, "H": 2, "L": 3}
+MATS = {"M": 0, "K": 1, "H": 2, "L": 3, "I": 4}
 
 
 class OracleMesh:
@@ -193,7 +196,7 @@ class OracleMesh:
         """(rowptr, col, val) CSR of M, K, H or L (= G^T M G)."""
         w = MATS[which]
         nnz = _lib.orc_matrix_nnz(self._h, w)
-        n = {"M": self.n_edges, "K": self.n_edges, "H": self.n_faces, "L": self.n_nodes}[which]
+        n = {"M": self.n_edges, "K": self.n_edges, "I": self.n_edges, "H": self.n_faces, "L": self.n_nodes}[which]
         rp = np.zeros(n + 1, dtype=np.int32)
         col = np.zeros(nnz, dtype=np.int32)
         val = np.zeros(nnz)
@@ -207,6 +210,18 @@ class OracleMesh:
         for r in range(n):
             out[r, col[rp[r]:rp[r + 1]]] += val[rp[r]:rp[r + 1]]
         return out
+
+    def set_absorbing(self, tet_face_bc: np.ndarray):
+        """Wall conditions per tet face (1 absorbing, 0 conducting), [n_tets, 4]
+        with entry k the face opposite the tet's k-th vertex; call before
+        creating simulations."""
+        bc = np.ascontiguousarray(tet_face_bc, dtype=np.int32).reshape(-1)
+        if bc.size != 4 * self.n_tets:
+            raise ValueError("tet_face_bc needs 4 entries per tet")
+        _lib.orc_mesh_set_absorbing(self._h, _ip(bc))
+        c = np.zeros(6, dtype=np.int32)
+        _lib.orc_mesh_counts(self._h, _ip(c))
+        self.n_int_edges = int(c[4])
 
     def lam(self, tet: int, r: Sequence[float]) -> np.ndarray:
         out = np.zeros(4)
@@ -254,7 +269,7 @@ def boris(qm: float, dt: float, E, B, v) -> np.ndarray:
 @dataclasses.dataclass
 class OracleConfig:
     dt: float
-    form: str = "we"             # "we" | "mfem"
+    form: str = "we"             # "we" | "mfem" | "bd"
     pusher: str = "boris"        # "boris" | "ab1".."ab5"
     b0: Sequence[float] = (0.0, 0.0, 0.0)
     cg_tol: float = 1e-10
@@ -264,10 +279,12 @@ class OracleConfig:
     walk_cap: int = 64
     gradient_completion: bool = True
     completion_tol: float = 1e-16
+    current: str = "gbar"        # "gbar" (the paper's method) | "point" (negative control)
 
     def to_c(self) -> _Config:
         c = _Config()
-        c.form = {"we": 0, "mfem": 1}[self.form]
+        c.form = {"we": 0, "mfem": 1, "bd": 2}[self.form]
+        c.current_form = {"gbar": 0, "point": 1}[self.current]
         c.pusher = 0 if self.pusher == "boris" else int(self.pusher[2:])
         c.dt = self.dt
         for i in range(3):
@@ -354,12 +371,17 @@ class OracleSim:
 
 def from_workload(wl, dt: float, cg_tol: float = 1e-10, init_tol: float = 1e-14,
                   mesh: Optional[OracleMesh] = None, gradient_completion: bool = True,
-                  completion_tol: float = 1e-16) -> OracleSim:
-    """Oracle simulation of a ``workloads.Workload`` with the given dt."""
-    mesh = mesh or OracleMesh(wl.mesh.xyz, wl.mesh.tets)
+                  completion_tol: float = 1e-16, current: str = "gbar") -> OracleSim:
+    """Oracle simulation of a ``workloads.Workload`` with the given dt (its
+    walls absorbing where ``wl.wall_bc`` says so)."""
+    if mesh is None:
+        mesh = OracleMesh(wl.mesh.xyz, wl.mesh.tets)
+        if getattr(wl, "wall_bc", None) is not None:
+            mesh.set_absorbing(wl.wall_bc)
     cfg = OracleConfig(dt=dt, form=wl.form, pusher=wl.pusher, b0=wl.b0, cg_tol=cg_tol,
                        init_tol=init_tol, rho_background=wl.rho_background,
-                       gradient_completion=gradient_completion, completion_tol=completion_tol)
+                       gradient_completion=gradient_completion, completion_tol=completion_tol,
+                       current=current)
     sim = OracleSim(mesh, cfg)
     for sp in wl.species:
         sim.add_species(sp.q, sp.m, sp.w, sp.x, sp.v, sp.tet)

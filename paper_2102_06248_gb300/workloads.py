@@ -138,6 +138,28 @@ def kuhn_box(cells: Tuple[int, int, int], size: Tuple[float, float, float],
                    tets=tets.reshape(-1, 4).astype(np.int32), ref_xyz=ref)
 
 
+BOX_WALLS = ("x0", "x1", "y0", "y1", "z0", "z1")
+
+
+def box_wall_bc(mesh: "BoxMesh", absorbing=BOX_WALLS) -> np.ndarray:
+    """Per tet face (entry [t, k]: the face opposite the tet's k-th vertex) a
+    1 when the face lies on one of the named box walls ("x0" is x = 0, "x1"
+    is x = size_x, ...), else 0.  Boundary vertices are never jittered, so a
+    wall face is one whose three vertices share the wall coordinate."""
+    tets = mesh.tets
+    out = np.zeros((tets.shape[0], 4), dtype=np.int32)
+    tol = 1e-9 * max(mesh.size)
+    for name in absorbing:
+        ax = "xyz".index(name[0])
+        val = 0.0 if name[1] == "0" else mesh.size[ax]
+        on = np.abs(mesh.xyz[:, ax] - val) <= tol            # nodes on that wall
+        on_t = on[tets]                                       # [n_tets, 4]
+        for k in range(4):
+            others = [j for j in range(4) if j != k]
+            out[:, k] |= np.all(on_t[:, others], axis=1).astype(np.int32)
+    return out
+
+
 def place_in_box(mesh: BoxMesh, pos_ref: np.ndarray) -> Tuple[np.ndarray, np.ndarray]:
     """Map points given in unjittered box coordinates to (physical point, tet).
 
@@ -194,6 +216,7 @@ class Workload:
     steps: int
     rho_background: float    # uniform static background charge density (C/m^3)
     notes: str = ""
+    wall_bc: Optional[np.ndarray] = None   # [n_tets, 4] 1 = absorbing wall face, 0 = conducting (None: all conducting)
 
     @property
     def n_particles(self) -> int:
