@@ -28,7 +28,7 @@
  *     discrete laws the library maintains are continuity
  *       (rho + wall)^{n+1} - (rho + wall)^n = G^T dGbar   (every node)
  *     and Gauss  G^T M e + rho + wall + rho_background = 0 (interior nodes),
- *     where "wall" is the charge absorbed by the perfectly conducting walls.
+ *     where "wall" is the charge of the particles absorbed by the walls.
  *
  * Ownership: every handle owns its host and device memory.  Pointers passed
  * in are read (or written) only during the call.  A pointer flagged
@@ -63,8 +63,15 @@ extern "C" {
 #define PIC_ERR_OVERFLOW 9
 #define PIC_ERR_STATE 10
 
-#define PIC_FORM_WE 0        /* wave-equation form, Eq. wave_cont */
-#define PIC_FORM_MFEM 1      /* Maxwell-solver (mixed) form, Eq. maxwell_semi */
+#define PIC_FORM_WE 0        /* Newmark wave-equation form, Eq. wave_cont */
+#define PIC_FORM_MFEM 1      /* Newmark Maxwell-solver (mixed) form, Eq. maxwell_semi */
+#define PIC_FORM_BD 2        /* Maxwell-solver form with the first-order backward difference
+                                (the BD-MFEM integrator of Sec. IV.B):
+                                  (b^{n+1} - b^n) + dt C e^{n+1} = 0,
+                                  M (e^{n+1} - e^n) - dt C^T H b^{n+1} + (dt/c) I e^{n+1}
+                                    = -(Gbar^{n+1} - Gbar^n),
+                                solved as (M + dt^2 K + (dt/c) I) e^{n+1}
+                                  = M e^n + dt C^T H b^n - (Gbar^{n+1} - Gbar^n) */
 
 #define PIC_PUSH_BORIS 0     /* 1..5: Adams-Bashforth of that order */
 
@@ -111,6 +118,17 @@ typedef struct {
     const int32_t *G_coo;     /* [3 * 2*n_edges]  rows, cols, vals */
     const int32_t *C_coo;     /* [3 * 3*n_faces] */
     const int32_t *D_coo;     /* [3 * 4*n_tets] */
+    /* Optional wall conditions (NULL: every wall perfectly conducting).
+     * [4*n_tets]: entry 4t+k is for the face of tet t opposite its k-th
+     * vertex as given in `tets`: 1 = first-order absorbing (Sec. II.A,
+     * Eq. impedanceBC with the vacuum admittance), 0 = perfectly conducting;
+     * entries of interior faces are ignored.  Edges on conducting wall faces
+     * are held at zero; edges on absorbing faces are unknowns, and the
+     * surface impedance matrix [*I]_ij = <n x W1_i, mu0^-1 n x W1_j> over the
+     * absorbing faces enters every field update as the damping term
+     * (1/c) [*I] de/dt (the paper's c [*I] of Eq. wave_cont, written in SI).
+     * Particles reaching any wall face are absorbed. */
+    const int32_t *wall_bc;
 } pic_mesh_desc;
 
 /* Builds the mesh (Sec. II.A): validates the tets (distinct nodes, non-zero
@@ -144,7 +162,7 @@ int pic_mesh_incidence(const pic_mesh *mesh, int32_t which, int32_t *rows, int32
 typedef struct pic_sim pic_sim;
 
 typedef struct {
-    int32_t form;            /* PIC_FORM_WE or PIC_FORM_MFEM */
+    int32_t form;            /* PIC_FORM_WE, PIC_FORM_MFEM or PIC_FORM_BD */
     int32_t pusher;          /* PIC_PUSH_BORIS or 1..5 (Adams-Bashforth order) */
     int32_t precision;       /* PIC_PRECISION_PLAIN or PIC_PRECISION_MIXED */
     int32_t preconditioner;  /* PIC_PRECOND_JACOBI or PIC_PRECOND_GNN */
@@ -168,7 +186,9 @@ typedef struct {
 void pic_config_default(pic_config *cfg);
 
 /* Creates a simulation on the mesh (which must outlive it).  Assembles the
- * Newmark matrix A = [*eps] + dt^2/4 [*S] (Sec. II.B).  Errors:
+ * system matrix of the field update: A = [*eps] + dt^2/4 [*S] + dt/(2c) [*I]
+ * for the Newmark forms (Sec. II.B), A = [*eps] + dt^2 [*S] + (dt/c) [*I] for
+ * the backward difference ([*I] = 0 without absorbing walls).  Errors:
  * PIC_ERR_INVALID_ARG (bad config), PIC_ERR_OOM, PIC_ERR_CUDA. */
 int pic_sim_create(const pic_mesh *mesh, const pic_config *cfg, pic_sim **out);
 void pic_sim_destroy(pic_sim *sim);

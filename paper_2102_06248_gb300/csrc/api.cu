@@ -283,7 +283,7 @@ int pic_sim_create(const pic_mesh *mesh, const pic_config *cfg, pic_sim **out) {
         return PIC_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    if (!(cfg->dt > 0) || (cfg->form != PIC_FORM_WE && cfg->form != PIC_FORM_MFEM) || cfg->pusher < 0 ||
+    if (!(cfg->dt > 0) || (cfg->form != PIC_FORM_WE && cfg->form != PIC_FORM_MFEM && cfg->form != PIC_FORM_BD) || cfg->pusher < 0 ||
         cfg->pusher > 5 || (cfg->precision != PIC_PRECISION_PLAIN && cfg->precision != PIC_PRECISION_MIXED) ||
         !(cfg->cg_tol > 0) || cfg->cg_max_iters <= 0 || !(cfg->init_tol > 0) || !(cfg->completion_tol > 0) ||
         cfg->walk_cap <= 0 || cfg->walk_cap > kMaxWalk || cfg->solver_blocks_per_sm < 0 ||

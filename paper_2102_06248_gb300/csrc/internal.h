@@ -115,6 +115,10 @@ struct HostStage {
     std::vector<double> L_val;
     std::vector<int> sell_ptr, sell_w, sell_col, lsell_ptr, lsell_w, lsell_col, hsell_ptr, hsell_w, hsell_col;
     std::vector<double> sell_M, sell_K, M_diag, K_diag, lsell_L, L_diag, hsell_H;
+    std::vector<double> sell_I, I_diag;          // surface impedance of absorbing walls, A's layout
+    std::vector<int> irow;                       // DOF rows with surface-impedance entries
+    HostCsrStage Ir;                             // those rows' entries (CSR)
+    std::vector<double> Ir_val;
     std::vector<signed char> e2f_sgn, n2e_sgn;
 };
 
@@ -156,6 +160,14 @@ struct Mesh {
     DevSell As;
     DevBuf<double> M_val, K_val;     // in the SELL layout
     DevBuf<double> M_diag, K_diag;   // diagonals (interior rows)
+    // surface impedance [*I] of the absorbing wall faces (Sec. II.A): values
+    // in A's SELL layout (folded into the system matrix) and, for the
+    // right-hand sides, the few rows that have entries as a small CSR
+    int n_abs_faces = 0;
+    DevBuf<double> I_val, I_diag;
+    DevBuf<int> I_row;
+    DevCsr Ir;
+    DevBuf<double> Ir_val;
     // face mass [*mu^-1] on all faces (SELL-32, natural face order)
     DevSell Hs;
     DevBuf<double> Hs_val;

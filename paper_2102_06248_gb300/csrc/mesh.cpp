@@ -254,12 +254,33 @@ int build_mesh(const pic_mesh_desc *d, Mesh *m) {
         if (nbr[i] >= 0) face_bnd[m->h_tet_face[i]] = 0;
 
     // ---- wall entities ----
+    // A wall face is perfectly conducting unless the caller marks it
+    // absorbing (wall_bc, indexed by the caller's vertex order: entry k is
+    // the face opposite the tet's k-th given vertex).  Edges on conducting
+    // wall faces are held at zero; every other edge is an unknown.  Every
+    // wall node stays out of the node Laplacian (phi = 0 on the walls).
+    std::vector<unsigned char> face_abs(nf, 0);
+    if (d->wall_bc) {
+        for (int t = 0; t < nt; t++)
+            for (int k = 0; k < 4; k++) {
+                const int v = d->tets[4 * (size_t)t + k];
+                int pos = 0;
+                while (TS[4 * t + pos] != v) pos++;
+                const int f = m->h_tet_face[4 * (size_t)t + pos];
+                if (face_bnd[f] && d->wall_bc[4 * (size_t)t + k]) face_abs[f] = 1;
+            }
+    }
     std::vector<unsigned char> edge_bnd(ne, 0);
     m->h_node_bnd.assign(nn, 0);
+    m->n_abs_faces = 0;
     for (int f = 0; f < nf; f++) {
         if (!face_bnd[f]) continue;
         int a = m->h_faces[3 * f], b = m->h_faces[3 * f + 1], c = m->h_faces[3 * f + 2];
         m->h_node_bnd[a] = m->h_node_bnd[b] = m->h_node_bnd[c] = 1;
+        if (face_abs[f]) {
+            m->n_abs_faces++;
+            continue;
+        }
         edge_bnd[edge_id((uint64_t)a * nn + b)] = 1;
         edge_bnd[edge_id((uint64_t)b * nn + c)] = 1;
         edge_bnd[edge_id((uint64_t)a * nn + c)] = 1;
@@ -438,6 +459,69 @@ int build_mesh(const pic_mesh_desc *d, Mesh *m) {
         }
     }
 
+    // ---- surface impedance of the absorbing wall faces ----
+    // [*I]_kl = mu0^-1 int_face (n x W1_k).(n x W1_l) dS.  On a wall face
+    // (opposite local vertex k) the unit normal is grad lam_k / |grad lam_k|,
+    // the face area is 3 V |grad lam_k|, only the face's three edges have a
+    // tangential trace, and n x W1_(a,b) has the magnitude of the tangential
+    // part of lam_a g_b - lam_b g_a with g_a projected on the face plane;
+    // products of barycentrics integrate to S (1 + delta_ab) / 12 on it.
+    std::vector<double> Iv(pa.col.size(), 0.0);
+    if (m->n_abs_faces > 0) {
+        for (int t = 0; t < nt; t++) {
+            const double *gp = geo.data() + 12 * (size_t)t;
+            double g[4][3];
+            for (int i = 0; i < 3; i++) {
+                g[1][i] = gp[3 + i];
+                g[2][i] = gp[6 + i];
+                g[3][i] = gp[9 + i];
+                g[0][i] = -(g[1][i] + g[2][i] + g[3][i]);
+            }
+            for (int k = 0; k < 4; k++) {
+                const int f = m->h_tet_face[4 * (size_t)t + k];
+                if (!face_abs[f]) continue;
+                const double gn = std::sqrt(dot3(g[k], g[k]));
+                const double S = 3.0 * m->h_vol[t] * gn;
+                double nrm[3] = {g[k][0] / gn, g[k][1] / gn, g[k][2] / gn};
+                double gs[4][3];
+                for (int a = 0; a < 4; a++) {
+                    const double pn = dot3(g[a], nrm);
+                    for (int i = 0; i < 3; i++) gs[a][i] = g[a][i] - pn * nrm[i];
+                }
+                for (int p = 0; p < 6; p++) {
+                    const int i = kLE[p][0], j = kLE[p][1];
+                    if (i == k || j == k) continue;          // not a face edge
+                    const int row = tet_edge[6 * (size_t)t + p];
+                    if (row >= nie) continue;                 // also on a conducting face
+                    for (int q = 0; q < 6; q++) {
+                        const int a = kLE[q][0], b = kLE[q][1];
+                        if (a == k || b == k) continue;
+                        const int col = tet_edge[6 * (size_t)t + q];
+                        if (col >= nie) continue;
+                        const double v = (1.0 + (i == a)) * dot3(gs[j], gs[b]) - (1.0 + (i == b)) * dot3(gs[j], gs[a]) -
+                                         (1.0 + (j == a)) * dot3(gs[i], gs[b]) + (1.0 + (j == b)) * dot3(gs[i], gs[a]);
+                        Iv[find_col(pa, row, col)] += S / 12.0 * v / kMu0;
+                    }
+                }
+            }
+        }
+        // rows with surface entries, as a small CSR for the right-hand sides
+        H.Ir.rowptr.assign(1, 0);
+        for (int r = 0; r < nie; r++) {
+            int cnt = 0;
+            for (int k = pa.rowptr[r]; k < pa.rowptr[r + 1]; k++)
+                if (Iv[k] != 0.0) {
+                    H.Ir.col.push_back(pa.col[k]);
+                    H.Ir_val.push_back(Iv[k]);
+                    cnt++;
+                }
+            if (cnt) {
+                H.irow.push_back(r);
+                H.Ir.rowptr.push_back(H.Ir.rowptr.back() + cnt);
+            }
+        }
+    }
+
     // ---- incidence gathers ----
     // face -> (ab, bc, ac) internal edge ids
     std::vector<int4> f2e(nf);
@@ -512,11 +596,18 @@ int build_mesh(const pic_mesh_desc *d, Mesh *m) {
     // SELL-32 layout of the Newmark pattern (M and K values) and of the node Laplacian
     {
         std::vector<std::vector<double>> out, dg;
-        build_sell(pa, {&Mv, &Kv}, H.sell_ptr, H.sell_w, H.sell_col, out, dg);
+        if (m->n_abs_faces > 0)
+            build_sell(pa, {&Mv, &Kv, &Iv}, H.sell_ptr, H.sell_w, H.sell_col, out, dg);
+        else
+            build_sell(pa, {&Mv, &Kv}, H.sell_ptr, H.sell_w, H.sell_col, out, dg);
         H.sell_M = std::move(out[0]);
         H.sell_K = std::move(out[1]);
         H.M_diag = std::move(dg[0]);
         H.K_diag = std::move(dg[1]);
+        if (m->n_abs_faces > 0) {
+            H.sell_I = std::move(out[2]);
+            H.I_diag = std::move(dg[2]);
+        }
         m->nnz_A = (long long)pa.col.size();
         build_sell(pl, {&Lv}, H.lsell_ptr, H.lsell_w, H.lsell_col, out, dg);
         H.lsell_L = std::move(out[0]);
@@ -578,6 +669,11 @@ int mesh_upload(Mesh *m) {
     if ((rc = csr(H.n2e, &m->n2e)) || (rc = m->n2e_sgn.upload(H.n2e_sgn))) return rc;
     if ((rc = m->f2e.upload(H.f2e)) || (rc = m->edge_nodes.upload(H.edge_nodes))) return rc;
     if ((rc = m->edge_canon.upload(m->h_edge_canonical)) || (rc = m->node_bnd.upload(m->h_node_bnd))) return rc;
+    if (m->n_abs_faces > 0) {
+        if ((rc = m->I_val.upload(H.sell_I)) || (rc = m->I_diag.upload(H.I_diag)) || (rc = m->I_row.upload(H.irow)) ||
+            (rc = csr(H.Ir, &m->Ir)) || (rc = m->Ir_val.upload(H.Ir_val)))
+            return rc;
+    }
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
     m->device = dev;

@@ -246,6 +246,7 @@ int stage_particles(Sim *s, int n, const double *x, const double *v, const int *
 
 // ---- launchers (solver.cu) ----
 int solver_alloc(Sim *s);
+void system_coefficients(const Sim *s, double *c4, double *ci);
 int newmark_rhs(Sim *s);
 int pcg_newmark(Sim *s);
 int laplacian_solve(Sim *s, const double *rhs_nodes, double *x_nodes, double tol, const double *abs_src,

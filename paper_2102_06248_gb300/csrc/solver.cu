@@ -123,7 +123,9 @@ constexpr int kSlicesPerBlock = kThreads / 32;
         const bool rv = r < (n);                                                                       \
         const int kb = sp[sl] + lane, kw = sw[sl];
 
-// face vector hb = H (b + b')
+// face vector hb = H (b + b') (Newmark Maxwell form) or H b (backward
+// difference, ONE_LEVEL)
+template <bool ONE_LEVEL>
 __global__ void __launch_bounds__(kThreads) k_face_hb(int n, int n_slices, const int *__restrict__ sp,
                                                       const int *__restrict__ sw, const int *__restrict__ col,
                                                       const double *__restrict__ Hv, const double *__restrict__ b,
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(kThreads) k_face_hb(int n, int n_slices, const
 #pragma unroll 4
         for (int j = 0; j < kw; j++) {
             const int k = kb + 32 * j, c = col[k];
-            acc = fma(Hv[k], b[c] + bp[c], acc);
+            acc = fma(Hv[k], ONE_LEVEL ? b[c] : b[c] + bp[c], acc);
         }
         if (rv) hb[r] = acc;
     }
@@ -199,11 +201,53 @@ __global__ void __launch_bounds__(kThreads) k_rhs_mfem_sell(int n, int n_slices,
     }
 }
 
-// t = 2e - e' - x (wave form) or e' - x (Maxwell form), formed once per row
+// backward difference: rhs = M e + dt C^T H b - (G^{n+1} - G^n)
+__global__ void __launch_bounds__(kThreads) k_rhs_bd_sell(int n, int n_slices, const int *__restrict__ sp,
+                                                          const int *__restrict__ sw, const int *__restrict__ col,
+                                                          const double *__restrict__ Mv, double dt,
+                                                          const double *__restrict__ e, const double *__restrict__ gn,
+                                                          const double *__restrict__ g, const int *__restrict__ efp,
+                                                          const int *__restrict__ efc,
+                                                          const signed char *__restrict__ efs,
+                                                          const double *__restrict__ hb, double *__restrict__ rhs) {
+    SELL_LOOP(n_slices, n)
+        double sm = 0.0, sc = 0.0;
+#pragma unroll 4
+        for (int j = 0; j < kw; j++) {
+            const int k = kb + 32 * j;
+            sm = fma(Mv[k], e[col[k]], sm);
+        }
+        if (rv) {
+            for (int k = efp[r]; k < efp[r + 1]; k++) sc += (double)efs[k] * hb[efc[k]];
+            rhs[r] = sm + dt * sc - (gn[r] - g[r]);
+        }
+    }
+}
+
+// absorbing walls: rhs += I (a u + c v) on the few rows with surface entries
+// (wave form: a = dt/c, u = e', c = 0; Newmark Maxwell form: a = -dt/c,
+// u = e, c = -dt/(2c), v = e')
+__global__ void k_rhs_impedance(int nr, const int *__restrict__ row, const int *__restrict__ ptr,
+                                const int *__restrict__ col, const double *__restrict__ val, double a,
+                                const double *__restrict__ u, double c, const double *__restrict__ v,
+                                double *__restrict__ rhs) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nr) return;
+    double su = 0.0, sv = 0.0;
+    for (int k = ptr[i]; k < ptr[i + 1]; k++) {
+        su = fma(val[k], u[col[k]], su);
+        if (v) sv = fma(val[k], v[col[k]], sv);
+    }
+    rhs[row[i]] += a * su + c * sv;
+}
+
+// t = 2e - e' - x (wave form), e' - x (Newmark Maxwell form) or e - x
+// (backward difference), formed once per row
 __global__ void k_gc_t(int n, int form, const double *__restrict__ e, const double *__restrict__ ep,
                        const double *__restrict__ x, double *__restrict__ t) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) t[i] = form == PIC_FORM_WE ? fma(2.0, e[i], -ep[i]) - x[i] : ep[i] - x[i];
+    if (i < n)
+        t[i] = form == PIC_FORM_WE ? fma(2.0, e[i], -ep[i]) - x[i] : form == PIC_FORM_MFEM ? ep[i] - x[i] : e[i] - x[i];
 }
 
 // w = M t - (second difference of Gbar), t from k_gc_t
@@ -220,7 +264,8 @@ __global__ void __launch_bounds__(kThreads) k_gc_w_sell(int n, int n_slices, con
             const int k = kb + 32 * j;
             s = fma(Mv[k], t[col[k]], s);
         }
-        if (rv) w[r] = s - (form == PIC_FORM_WE ? gn[r] - 2.0 * g[r] + gp[r] : gn[r] - gp[r]);
+        if (rv)
+            w[r] = s - (form == PIC_FORM_WE ? gn[r] - 2.0 * g[r] + gp[r] : form == PIC_FORM_MFEM ? gn[r] - gp[r] : gn[r] - g[r]);
     }
 }
 
@@ -228,26 +273,29 @@ __global__ void __launch_bounds__(kThreads) k_gc_w_sell(int n, int n_slices, con
 // p = z + beta p_old (on the fly for the neighbours), q = A p, pq: the SpMV
 // of the Newmark PCG
 // true residual and M x on the Newmark pattern: relres, energy_e
+template <bool IMPEDANCE>
 __global__ void __launch_bounds__(kThreads) k_resid_sell(int n, int n_slices, const int *__restrict__ sp,
                                                          const int *__restrict__ sw, const int *__restrict__ col,
                                                          const double *__restrict__ Mv, const double *__restrict__ Kv,
-                                                         double c4, const double *__restrict__ x,
+                                                         const double *__restrict__ Iv, double c4, double ci,
+                                                         const double *__restrict__ x,
                                                          const double *__restrict__ rhs, double *__restrict__ me,
                                                          double *part, DiagDev *dg) {
     __shared__ double sh[3 * kThreads / 32];
     double acc[3] = {0.0, 0.0, 0.0};
     SELL_LOOP(n_slices, n)
-        double sm = 0.0, sk = 0.0;
+        double sm = 0.0, sk = 0.0, si = 0.0;
 #pragma unroll 4
         for (int j = 0; j < kw; j++) {
             const int k = kb + 32 * j;
             const double xj = x[col[k]];
             sm += Mv[k] * xj;
             sk += Kv[k] * xj;
+            if (IMPEDANCE) si += Iv[k] * xj;
         }
         if (rv) {
             me[r] = sm;
-            const double res = rhs[r] - (sm + c4 * sk);
+            const double res = rhs[r] - (sm + c4 * sk + ci * si);
             acc[0] += res * res;
             acc[1] += rhs[r] * rhs[r];
             acc[2] += x[r] * sm;
@@ -266,9 +314,9 @@ __global__ void __launch_bounds__(kThreads) k_resid_sell(int n, int n_slices, co
 }
 
 __global__ void k_recip_diag_mk(int n, const double *__restrict__ md, const double *__restrict__ kd, double c4,
-                                double *__restrict__ dinv) {
+                                const double *__restrict__ id, double ci, double *__restrict__ dinv) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dinv[i] = 1.0 / (md[i] + c4 * kd[i]);
+    if (i < n) dinv[i] = 1.0 / (md[i] + c4 * kd[i] + (id ? ci * id[i] : 0.0));
 }
 
 int grid_for_slices(int n_slices) {
@@ -477,7 +525,8 @@ __global__ void k_int_to_node(int nin, const int *__restrict__ int_node, const d
 
 
 // Faraday: wave equation b^{n+1} = b^n - dt/2 C (e^{n+1} + e^n);
-// Maxwell-solver row b^{n+1} = b^{n-1} - 2 dt C (e^{n+1}/4 + e^n/2 + e^{n-1}/4)
+// Maxwell-solver row b^{n+1} = b^{n-1} - 2 dt C (e^{n+1}/4 + e^n/2 + e^{n-1}/4);
+// backward difference b^{n+1} = b^n - dt C e^{n+1}
 __global__ void k_faraday(int nf, const int4 *__restrict__ f2e, int form, double dt, const double *__restrict__ x,
                           const double *__restrict__ e, const double *__restrict__ ep, const double *__restrict__ b,
                           const double *__restrict__ bp, double *__restrict__ bn) {
@@ -485,6 +534,10 @@ __global__ void k_faraday(int nf, const int4 *__restrict__ f2e, int form, double
     if (f >= nf) return;
     const int4 t = f2e[f];
     const double cx = x[t.x] + x[t.y] - x[t.z];
+    if (form == PIC_FORM_BD) {
+        bn[f] = b[f] - dt * cx;
+        return;
+    }
     const double ce = e[t.x] + e[t.y] - e[t.z];
     if (form == PIC_FORM_WE) {
         bn[f] = b[f] - 0.5 * dt * (cx + ce);
@@ -1239,13 +1292,17 @@ int solver_alloc(Sim *s) {
     if ((rc = s->cg_part.alloc(8 * kMaxBlocks)) || (rc = s->l_part.alloc(8 * kMaxBlocks)) ||
         (rc = s->diag_part.alloc(8 * kMaxBlocks)))
         return rc;
-    // A = M + dt^2/4 K and the Jacobi preconditioners
-    const double c4 = 0.25 * s->cfg.dt * s->cfg.dt;
+    // A = M + c4 K + ci I and the Jacobi preconditioners
+    double c4, ci;
+    system_coefficients(s, &c4, &ci);
     const long long nel = m->As.n_elems;
     if ((rc = s->A_val.alloc(std::max(nel, 1LL)))) return rc;
     if (nel > 0) {
         { k_axpby<<<(unsigned)((nel + 255) / 256), 256>>>((int)nel, 1.0, m->M_val.p, c4, m->K_val.p, s->A_val.p); note_launch(); }
-        { k_recip_diag_mk<<<(ni + 255) / 256, 256>>>(ni, m->M_diag.p, m->K_diag.p, c4, s->Dinv.p); note_launch(); }
+        if (m->n_abs_faces > 0)
+            { k_axpby<<<(unsigned)((nel + 255) / 256), 256>>>((int)nel, 1.0, s->A_val.p, ci, m->I_val.p, s->A_val.p); note_launch(); }
+        { k_recip_diag_mk<<<(ni + 255) / 256, 256>>>(ni, m->M_diag.p, m->K_diag.p, c4,
+                                                     m->n_abs_faces > 0 ? m->I_diag.p : nullptr, ci, s->Dinv.p); note_launch(); }
     }
     if (nin > 0) { k_recip_diag<<<(nin + 255) / 256, 256>>>(nin, m->L.rowptr.p, m->L.col.p, m->L_val.p, s->L_Dinv.p); note_launch(); }
     // MIXED: the correction solves of the Newmark refinement run on the
@@ -1260,6 +1317,16 @@ int solver_alloc(Sim *s) {
     return PIC_OK;
 }
 
+// Coefficients of the system matrix A = M + c4 K + ci I of the field update:
+// Newmark (gamma = 1/2, beta = 1/4), both forms: c4 = dt^2/4, ci = dt/(2c);
+// backward difference: c4 = dt^2, ci = dt/c.
+void system_coefficients(const Sim *s, double *c4, double *ci) {
+    const double dt = s->cfg.dt;
+    const bool bd = s->cfg.form == PIC_FORM_BD;
+    *c4 = (bd ? 1.0 : 0.25) * dt * dt;
+    *ci = (bd ? 1.0 : 0.5) * dt / kC0;
+}
+
 int newmark_rhs(Sim *s) {
     const Mesh *m = s->mesh;
     const int ni = m->n_int_edges;
@@ -1267,12 +1334,25 @@ int newmark_rhs(Sim *s) {
     const double dt = s->cfg.dt, c4 = 0.25 * dt * dt;
     const DevSell &A = m->As;
     const int gs = grid_for_slices(A.n_slices);
+    // the Newmark forms' predictor x = 2e - e' (also the initial guess of the
+    // backward difference, whose right-hand side does not use it)
     { k_rhs_pre<<<(ni + 255) / 256, 256, 0, s->stream>>>(ni, s->e.p, s->e_prev.p, s->x.p, s->ev.p); note_launch(); }
+    const int nr = m->I_row.n;
     if (s->cfg.form == PIC_FORM_WE) {
         { k_rhs_we_sell<<<gs, kThreads, 0, s->stream>>>(ni, A.n_slices, A.ptr.p, A.width.p, A.col.p, m->M_val.p, m->K_val.p, c4, s->x.p, s->ev.p, s->g_new.p, s->g.p, s->g_prev.p, s->rhs.p); note_launch(); }
-    } else {
-        { k_face_hb<<<grid_for_slices(m->Hs.n_slices), kThreads, 0, s->stream>>>(m->n_faces, m->Hs.n_slices, m->Hs.ptr.p, m->Hs.width.p, m->Hs.col.p, m->Hs_val.p, s->b.p, s->b_prev.p, s->hb.p); note_launch(); }
+        // -(M - dt/(2c) I + dt^2/4 K) e' = -A e' + (dt/c) I e'
+        if (nr > 0)
+            { k_rhs_impedance<<<(nr + 255) / 256, 256, 0, s->stream>>>(nr, m->I_row.p, m->Ir.rowptr.p, m->Ir.col.p, m->Ir_val.p, dt / kC0, s->e_prev.p, 0.0, nullptr, s->rhs.p); note_launch(); }
+    } else if (s->cfg.form == PIC_FORM_MFEM) {
+        { k_face_hb<false><<<grid_for_slices(m->Hs.n_slices), kThreads, 0, s->stream>>>(m->n_faces, m->Hs.n_slices, m->Hs.ptr.p, m->Hs.width.p, m->Hs.col.p, m->Hs_val.p, s->b.p, s->b_prev.p, s->hb.p); note_launch(); }
         { k_rhs_mfem_sell<<<gs, kThreads, 0, s->stream>>>(ni, A.n_slices, A.ptr.p, A.width.p, A.col.p, m->M_val.p, m->K_val.p, c4, dt, s->e_prev.p, s->ev.p, s->g_new.p, s->g_prev.p, m->e2f.rowptr.p, m->e2f.col.p, m->e2f_sgn.p, s->hb.p, s->rhs.p); note_launch(); }
+        // the Ampere row's 2 dt/c I (e^{n+1}/4 + e^n/2 + e^{n-1}/4): the e^{n+1}
+        // part is in A, - dt/c I (e^n + e^{n-1}/2) comes here
+        if (nr > 0)
+            { k_rhs_impedance<<<(nr + 255) / 256, 256, 0, s->stream>>>(nr, m->I_row.p, m->Ir.rowptr.p, m->Ir.col.p, m->Ir_val.p, -dt / kC0, s->e.p, -0.5 * dt / kC0, s->e_prev.p, s->rhs.p); note_launch(); }
+    } else {
+        { k_face_hb<true><<<grid_for_slices(m->Hs.n_slices), kThreads, 0, s->stream>>>(m->n_faces, m->Hs.n_slices, m->Hs.ptr.p, m->Hs.width.p, m->Hs.col.p, m->Hs_val.p, s->b.p, nullptr, s->hb.p); note_launch(); }
+        { k_rhs_bd_sell<<<gs, kThreads, 0, s->stream>>>(ni, A.n_slices, A.ptr.p, A.width.p, A.col.p, m->M_val.p, dt, s->e.p, s->g_new.p, s->g.p, m->e2f.rowptr.p, m->e2f.col.p, m->e2f_sgn.p, s->hb.p, s->rhs.p); note_launch(); }
     }
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
@@ -1522,11 +1602,13 @@ int laplacian_solve(Sim *s, const double *rhs_int, double *x_int, double tol, co
     return launch_pcg_runs(&a, 1, s->cfg.solver_blocks_per_sm, s->stream);
 }
 
-// Completion of the Newmark solve on the gradient subspace: the part of the
+// Completion of the field solve on the gradient subspace: the part of the
 // residual the discrete divergence sees, d = G_int^T (b - A x), equals (with
-// G^T K = 0 and G^T C^T = 0) G_int^T [M (2e - e' - x) - d2 Gbar] for the wave
-// form and G_int^T [M (e' - x) - (Gbar^{n+1} - Gbar^{n-1})] for the Maxwell
-// form.  Solving (G^T M G) psi = d and adding G psi removes it (A G = M G), so
+// G^T K = 0, G^T C^T = 0 and G_int^T I = 0, since no interior node touches a
+// wall-face edge) G_int^T [M (2e - e' - x) - d2 Gbar] for the wave form,
+// G_int^T [M (e' - x) - (Gbar^{n+1} - Gbar^{n-1})] for the Newmark Maxwell
+// form and G_int^T [M (e - x) - (Gbar^{n+1} - Gbar^n)] for the backward
+// difference.  Solving (G^T M G) psi = d and adding G psi removes it (A G = M G), so
 // the Gauss residual does not drift with the CG tolerance (Sec. III.A notes
 // that the linear solve is the only source of error).  The charge is not used.
 int gc_prepare(Sim *s) {
@@ -1565,8 +1647,14 @@ int compute_diagnostics(Sim *s) {
     const Mesh *m = s->mesh;
     DiagDev *dg = &s->dctl.p->diag;
     const int ni = m->n_int_edges;
-    if (ni > 0)
-        { k_resid_sell<<<grid_for_slices(m->As.n_slices), kThreads, 0, s->stream>>>(ni, m->As.n_slices, m->As.ptr.p, m->As.width.p, m->As.col.p, m->M_val.p, m->K_val.p, 0.25 * s->cfg.dt * s->cfg.dt, s->e.p, s->rhs.p, s->me.p, s->diag_part.p, dg); note_launch(); }
+    if (ni > 0) {
+        double c4, ci;
+        system_coefficients(s, &c4, &ci);
+        if (m->n_abs_faces > 0)
+            { k_resid_sell<true><<<grid_for_slices(m->As.n_slices), kThreads, 0, s->stream>>>(ni, m->As.n_slices, m->As.ptr.p, m->As.width.p, m->As.col.p, m->M_val.p, m->K_val.p, m->I_val.p, c4, ci, s->e.p, s->rhs.p, s->me.p, s->diag_part.p, dg); note_launch(); }
+        else
+            { k_resid_sell<false><<<grid_for_slices(m->As.n_slices), kThreads, 0, s->stream>>>(ni, m->As.n_slices, m->As.ptr.p, m->As.width.p, m->As.col.p, m->M_val.p, m->K_val.p, nullptr, c4, 0.0, s->e.p, s->rhs.p, s->me.p, s->diag_part.p, dg); note_launch(); }
+    }
     { k_diag_nodes<<<grid_for_elems(m->n_nodes), kThreads, 0, s->stream>>>(
         m->n_nodes, m->n2e.rowptr.p, m->n2e.col.p, m->n2e_sgn.p, ni, s->dg.p, s->me.p, s->rho.p, s->rho_prev.p,
         s->wall.p, s->wall_prev.p, s->rho_bg.p, m->node_bnd.p, s->diag_part.p, dg); note_launch(); }

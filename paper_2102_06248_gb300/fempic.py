@@ -19,7 +19,7 @@ from . import build as _build
 PIC_OK = 0
 ERRORS = {1: "INVALID_ARG", 2: "MESH", 3: "OOM", 4: "PARTICLE_OUTSIDE", 5: "WALK_CAP",
           6: "CG_NO_CONVERGENCE", 7: "NAN", 8: "CUDA", 9: "OVERFLOW", 10: "STATE"}
-FORMS = {"we": 0, "mfem": 1}
+FORMS = {"we": 0, "mfem": 1, "bd": 2}
 PRECISIONS = {"plain": 0, "mixed": 1}
 FIELDS = {"E": 0, "E_PREV": 1, "B": 2, "B_PREV": 3, "G": 4, "G_PREV": 5, "DG": 6, "RHO": 7,
           "WALL": 8, "RHO_BG": 9, "PHI": 10}
@@ -35,7 +35,8 @@ class pic_mesh_desc(C.Structure):
     _fields_ = [("n_nodes", C.c_int32), ("xyz", C.POINTER(C.c_double)), ("n_tets", C.c_int32),
                 ("tets", C.POINTER(C.c_int32)), ("n_edges", C.c_int32), ("edges", C.POINTER(C.c_int32)),
                 ("n_faces", C.c_int32), ("faces", C.POINTER(C.c_int32)), ("G_coo", C.POINTER(C.c_int32)),
-                ("C_coo", C.POINTER(C.c_int32)), ("D_coo", C.POINTER(C.c_int32))]
+                ("C_coo", C.POINTER(C.c_int32)), ("D_coo", C.POINTER(C.c_int32)),
+                ("wall_bc", C.POINTER(C.c_int32))]
 
 
 class pic_config(C.Structure):
@@ -144,7 +145,10 @@ class Mesh:
     """pic_mesh_create on node coordinates and tets (host arrays)."""
 
     def __init__(self, xyz: np.ndarray, tets: np.ndarray, edges: Optional[np.ndarray] = None,
-                 faces: Optional[np.ndarray] = None, incidence: Optional[Dict[str, np.ndarray]] = None):
+                 faces: Optional[np.ndarray] = None, incidence: Optional[Dict[str, np.ndarray]] = None,
+                 wall_bc: Optional[np.ndarray] = None):
+        """wall_bc: optional [n_tets, 4] per tet face (entry k: the face opposite
+        the tet's k-th vertex), 1 = first-order absorbing wall, 0 = conducting."""
         lib = load()
         self._xyz = np.ascontiguousarray(xyz, dtype=np.float64)
         self._tets = np.ascontiguousarray(tets, dtype=np.int32)
@@ -164,6 +168,12 @@ class Mesh:
             keep.append(f)
             d.n_faces = f.shape[0]
             d.faces = _ptr(f, C.c_int32)
+        if wall_bc is not None:
+            wb = np.ascontiguousarray(wall_bc, dtype=np.int32).reshape(-1)
+            if wb.size != 4 * d.n_tets:
+                raise PicError(1, "pic_mesh_create", "wall_bc needs 4 entries per tet")
+            keep.append(wb)
+            d.wall_bc = _ptr(wb, C.c_int32)
         for key, field in (("G", "G_coo"), ("C", "C_coo"), ("D", "D_coo")):
             if incidence and key in incidence:
                 a = np.ascontiguousarray(incidence[key], dtype=np.int32)
@@ -442,8 +452,9 @@ def sim_from_workload(wl, dt: float, precision: str = "plain", cg_tol: float = 1
                       init_tol: float = 1e-14, mesh: Optional[Mesh] = None, stream=None,
                       profile: bool = False, cg_max_iters: int = 10000, solver_blocks_per_sm: int = 0,
                       preconditioner: str = "jacobi") -> Sim:
-    """Builds and initialises a simulation of a ``workloads.Workload``."""
-    mesh = mesh or Mesh(wl.mesh.xyz, wl.mesh.tets)
+    """Builds and initialises a simulation of a ``workloads.Workload`` (its
+    walls absorbing where ``wl.wall_bc`` says so)."""
+    mesh = mesh or Mesh(wl.mesh.xyz, wl.mesh.tets, wall_bc=getattr(wl, "wall_bc", None))
     sim = Sim(mesh, dt, form=wl.form, pusher=wl.pusher, precision=precision, b0=wl.b0,
               rho_background=wl.rho_background, cg_tol=cg_tol, init_tol=init_tol, stream=stream,
               profile=profile, cg_max_iters=cg_max_iters, solver_blocks_per_sm=solver_blocks_per_sm,

@@ -90,3 +90,20 @@ def test_malformed_meshes_are_rejected():
     tets = np.array([[0, 1, 2, 3], [0, 1, 2, 4], [0, 1, 2, 5]], dtype=np.int32)
     with pytest.raises(F.PicError):
         F.Mesh(xyz, tets)
+
+
+@pytest.mark.parametrize("walls", [W.BOX_WALLS, ("z0", "z1"), ("x1",)])
+def test_absorbing_walls_unknowns_match_oracle(oracle_lib, walls):
+    """With absorbing wall faces (Sec. II.A, Eq. impedanceBC) the edges held at
+    zero are exactly those on conducting faces: the host-side mesh build and
+    the oracle agree on how many unknowns the field update has."""
+    box = W.kuhn_box((3, 4, 3), (0.3, 0.4, 0.3), jitter=0.1, seed=8)
+    bc = W.box_wall_bc(box, walls)
+    om = oracle_lib.OracleMesh(box.xyz, box.tets)
+    om.set_absorbing(bc)
+    pm = F.Mesh(box.xyz, box.tets, wall_bc=bc)
+    plain = F.Mesh(box.xyz, box.tets)
+    assert pm.n_int_edges == om.n_int_edges > plain.n_int_edges
+    assert pm.n_int_nodes == om.n_int_nodes == plain.n_int_nodes
+    with pytest.raises(F.PicError):
+        F.Mesh(box.xyz, box.tets, wall_bc=bc[:-1])
