@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(kThreads) k_rhs_bd_sell(int n, int n_slices, c
 }
 
 // absorbing walls: rhs += I (a u + c v) on the few rows with surface entries
-// (wave form: a = dt/c, u = e', c = 0; Newmark Maxwell form: a = -dt/c,
+// (wave form: a = dt/(2c), u = e', c = 0; Newmark Maxwell form: a = -dt/c,
 // u = e, c = -dt/(2c), v = e')
 __global__ void k_rhs_impedance(int nr, const int *__restrict__ row, const int *__restrict__ ptr,
                                 const int *__restrict__ col, const double *__restrict__ val, double a,
@@ -1340,9 +1340,10 @@ int newmark_rhs(Sim *s) {
     const int nr = m->I_row.n;
     if (s->cfg.form == PIC_FORM_WE) {
         { k_rhs_we_sell<<<gs, kThreads, 0, s->stream>>>(ni, A.n_slices, A.ptr.p, A.width.p, A.col.p, m->M_val.p, m->K_val.p, c4, s->x.p, s->ev.p, s->g_new.p, s->g.p, s->g_prev.p, s->rhs.p); note_launch(); }
-        // -(M - dt/(2c) I + dt^2/4 K) e' = -A e' + (dt/c) I e'
+        // the kernel above forms -(M + dt^2/4 K) e'; the absorbing walls add
+        // the rest of -(M - dt/(2c) I + dt^2/4 K) e', i.e. + dt/(2c) I e'
         if (nr > 0)
-            { k_rhs_impedance<<<(nr + 255) / 256, 256, 0, s->stream>>>(nr, m->I_row.p, m->Ir.rowptr.p, m->Ir.col.p, m->Ir_val.p, dt / kC0, s->e_prev.p, 0.0, nullptr, s->rhs.p); note_launch(); }
+            { k_rhs_impedance<<<(nr + 255) / 256, 256, 0, s->stream>>>(nr, m->I_row.p, m->Ir.rowptr.p, m->Ir.col.p, m->Ir_val.p, 0.5 * dt / kC0, s->e_prev.p, 0.0, nullptr, s->rhs.p); note_launch(); }
     } else if (s->cfg.form == PIC_FORM_MFEM) {
         { k_face_hb<false><<<grid_for_slices(m->Hs.n_slices), kThreads, 0, s->stream>>>(m->n_faces, m->Hs.n_slices, m->Hs.ptr.p, m->Hs.width.p, m->Hs.col.p, m->Hs_val.p, s->b.p, s->b_prev.p, s->hb.p); note_launch(); }
         { k_rhs_mfem_sell<<<gs, kThreads, 0, s->stream>>>(ni, A.n_slices, A.ptr.p, A.width.p, A.col.p, m->M_val.p, m->K_val.p, c4, dt, s->e_prev.p, s->ev.p, s->g_new.p, s->g_prev.p, m->e2f.rowptr.p, m->e2f.col.p, m->e2f_sgn.p, s->hb.p, s->rhs.p); note_launch(); }
