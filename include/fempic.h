@@ -180,6 +180,9 @@ typedef struct {
     int32_t max_species;     /* species slots (4) */
     int32_t profile;         /* 1: time the phases of every step with CUDA events (0) */
     void *stream;            /* cudaStream_t to run on; NULL = default stream */
+    int32_t barrier_spin_limit; /* polls a persistent solver block makes at one grid barrier before it
+                                   gives up, records PIC_ERR_CUDA ("timed out at a grid barrier") and
+                                   returns (0: about a second's worth, 2^22) */
 } pic_config;
 
 /* Fills a config with the defaults above (form WE, Boris, PLAIN, dt = 0). */
@@ -213,6 +216,15 @@ int pic_particles_load(pic_sim *sim, int32_t species, double q, double m, double
  * rho^0 from the particles; (G^T M G) phi = rho^0 + rho_bg on interior
  * nodes, e^0 = e^{-1} = -G phi; Gbar^0 = Gbar^{-1} = 0. */
 int pic_sim_init(pic_sim *sim);
+
+/* Static background node charges (C), e.g. an immobile ion species: host
+ * array [n_nodes] in the caller's node numbering, added to the node charges
+ * of the uniform rho_background of the config.  They enter the initial
+ * electrostatic solve and Gauss's law (G^T M e + rho + wall + rho_bg = 0 at
+ * interior nodes) and never move.  Call before pic_sim_init (PIC_ERR_STATE
+ * afterwards); a later call replaces the earlier array.  Errors:
+ * PIC_ERR_INVALID_ARG (NULL or non-finite values), PIC_ERR_STATE. */
+int pic_set_background_charge(pic_sim *sim, const double *rho_nodes);
 
 /* Particles entering between steps, e.g. from a beam source (the injected beam
  * of Sec. IV.B): n particles of an already loaded species (its q, m, w) at host

@@ -671,6 +671,7 @@ struct orc_sim {
     int nhist;                      /* number of history levels filled */
     double *e, *e_prev, *b, *b_prev, *g, *g_prev, *dg, *rho, *rho_prev, *wall, *wall_prev, *rho_bg, *phi;
     double *diagA;                  /* diag of A = M + dt^2/4 K */
+    double *bg_nodes;               /* static node charges added to the uniform background (or NULL) */
     csr A;
     int step;
     int last_completion_iters;
@@ -716,7 +717,7 @@ void orc_sim_free(orc_sim *s) {
     free(s->ahist); free(s->vhist);
     free(s->e); free(s->e_prev); free(s->b); free(s->b_prev); free(s->g); free(s->g_prev); free(s->dg);
     free(s->rho); free(s->rho_prev); free(s->wall); free(s->wall_prev); free(s->rho_bg); free(s->phi);
-    free(s->diagA);
+    free(s->diagA); free(s->bg_nodes);
     csr_free(&s->A);
     free(s);
 }
@@ -919,6 +920,8 @@ int orc_init(orc_sim *s) {
     memset(s->rho_bg, 0, sizeof(double) * nn);
     for (int t = 0; t < m->n_tets; t++)
         for (int k = 0; k < 4; k++) s->rho_bg[m->tet[4 * t + k]] += s->cfg.rho_background * m->vol[t] / 4.0;
+    if (s->bg_nodes)
+        for (int n = 0; n < nn; n++) s->rho_bg[n] += s->bg_nodes[n];
     deposit_charge(s, s->rho);
     memcpy(s->rho_prev, s->rho, sizeof(double) * nn);
     memset(s->wall, 0, sizeof(double) * nn);
@@ -943,6 +946,13 @@ int orc_init(orc_sim *s) {
     s->step = 0;
     compute_diag(s, it, rr);
     s->diag.continuity_abs = 0.0;
+    return ORC_OK;
+}
+
+/* static node charges (an immobile species), added to the background at orc_init */
+int orc_set_background_charge(orc_sim *s, const double *rho_nodes) {
+    if (!s->bg_nodes) s->bg_nodes = malloc(sizeof(double) * s->m->n_nodes);
+    memcpy(s->bg_nodes, rho_nodes, sizeof(double) * s->m->n_nodes);
     return ORC_OK;
 }
 

@@ -126,6 +126,8 @@ orc_sim *orc_sim_new(orc_mesh *m, const orc_config *cfg);
 void orc_sim_free(orc_sim *s);
 int orc_add_species(orc_sim *s, double q, double mass, double w, int n,
                     const double *x, const double *v, const int *tet);
+/* static node charges [n_nodes] added to the uniform background; before orc_init */
+int orc_set_background_charge(orc_sim *s, const double *rho_nodes);
 int orc_init(orc_sim *s);
 /* particles entering between steps (a beam source, Sec. IV.B), after orc_init:
  * appended like orc_add_species; their charge q w lambda(x) is added to rho^n

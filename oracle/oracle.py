@@ -94,6 +94,8 @@ def _load():
     for name in ("orc_init", "orc_step", "orc_particle_phase", "orc_add_species"):
         getattr(lib, name).restype = C.c_int
     lib.orc_init.argtypes = [P]
+    lib.orc_set_background_charge.argtypes = [P, dp]
+    lib.orc_set_background_charge.restype = C.c_int
     lib.orc_set_ab_history.argtypes = [P, C.c_int, dp, dp]
     lib.orc_set_ab_history.restype = C.c_int
     lib.orc_step.argtypes = [P]
@@ -326,6 +328,10 @@ class OracleSim:
         v = np.ascontiguousarray(v, dtype=np.float64)
         tet = np.ascontiguousarray(tet, dtype=np.int32)
         self._check(_lib.orc_inject(self._h, q, m, w, x.shape[0], _dp(x), _dp(v), _ip(tet)), "inject")
+
+    def set_background_charge(self, rho_nodes: np.ndarray):
+        a = np.ascontiguousarray(rho_nodes, dtype=np.float64)
+        self._check(_lib.orc_set_background_charge(self._h, _dp(a)), "set_background_charge")
 
     def init(self):
         self._check(_lib.orc_init(self._h), "init")

@@ -415,6 +415,8 @@ int pic_sim_init(pic_sim *sim) {
     std::vector<double> bg(m->n_nodes, 0.0);
     for (int t = 0; t < m->n_tets; t++)
         for (int k = 0; k < 4; k++) bg[m->h_tet_sorted[4 * (size_t)t + k]] += s->cfg.rho_background * m->h_vol[t] / 4.0;
+    if (!s->bg_nodes.empty())
+        for (int n = 0; n < m->n_nodes; n++) bg[n] += s->bg_nodes[n];
     FP_CUDA(cudaMemset(s->b.p, 0, sizeof(double) * m->n_faces));
     FP_CUDA(cudaMemset(s->b_prev.p, 0, sizeof(double) * m->n_faces));
     FP_CUDA(cudaMemcpy(s->rho_bg.p, bg.data(), sizeof(double) * m->n_nodes, cudaMemcpyHostToDevice));
@@ -437,6 +439,26 @@ int pic_sim_init(pic_sim *sim) {
     s->initialised = 1;
     s->nhist = 0;
     return check_status(s);
+}
+
+int pic_set_background_charge(pic_sim *sim, const double *rho_nodes) {
+    if (!sim || !rho_nodes) {
+        set_error("pic_set_background_charge: NULL argument");
+        return PIC_ERR_INVALID_ARG;
+    }
+    Sim *s = &sim->s;
+    if (s->initialised) {
+        set_error("pic_set_background_charge: call before pic_sim_init");
+        return PIC_ERR_STATE;
+    }
+    const int nn = s->mesh->n_nodes;
+    for (int n = 0; n < nn; n++)
+        if (!std::isfinite(rho_nodes[n])) {
+            set_error("pic_set_background_charge: node " + std::to_string(n) + " has a non-finite charge");
+            return PIC_ERR_INVALID_ARG;
+        }
+    s->bg_nodes.assign(rho_nodes, rho_nodes + nn);
+    return PIC_OK;
 }
 
 int pic_particles_inject(pic_sim *sim, int32_t species, int64_t n, const double *x, const double *v,

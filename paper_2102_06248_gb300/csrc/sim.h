@@ -42,7 +42,7 @@ struct GridBarrier {
     unsigned int count;   // arrivals since the launch (epoch k completes at k * blocks)
     unsigned int flag;    // last epoch whose reduction results are published
     int timeout;
-    int pad;
+    int spin_limit;       // polls before a wait gives up (set with the reset before each launch)
     double val[6];        // results the last arriving block publishes
 };
 
@@ -81,6 +81,7 @@ struct PcgArgs {
     int x_zero;                   // the initial guess is 0 (x is written, not read)
     int quiet;                    // reaching max_iters ends the solve without an error
     int block0, blocks;           // blocks of the launch that run this solve
+    int spin_limit;               // polls per grid-barrier wait before a timeout (> 0)
     // mixed-precision refinement (refine = 1): FP64 residuals, FP32 corrections
     int refine;
     double inner_tol2;            // relative residual^2 of each FP32 correction solve
@@ -151,6 +152,7 @@ struct Sim {
     int nhist = 0;            // history levels filled (order ramp)
     int initialised = 0;
     long step = 0;
+    std::vector<double> bg_nodes;   // static node charges set by the caller (added to the uniform background)
     size_t rsize = 8;         // bytes of one particle real
 
     // species

@@ -728,9 +728,10 @@ __device__ __forceinline__ void st_release(unsigned int *p, unsigned int v) {
 // block's timeout ends the wait.
 __device__ __forceinline__ bool spin_until(GridBarrier *gb, const unsigned int *p, unsigned int target) {
     volatile int *vto = &gb->timeout;
+    const long limit = gb->spin_limit;
     long spins = 0;
     while (ld_acquire(p) < target) {
-        if (++spins > kSpinLimit || ((spins & 255) == 0 && *vto != 0)) {
+        if (++spins > limit || ((spins & 255) == 0 && *vto != 0)) {
             atomicExch(&gb->timeout, 1);
             return false;
         }
@@ -1396,6 +1397,7 @@ __global__ void k_reset_barriers(PcgBatch<kMaxBatchRuns> B) {
         gb->count = 0;
         gb->flag = 0;
         gb->timeout = 0;
+        gb->spin_limit = B.run[r].spin_limit > 0 ? B.run[r].spin_limit : (int)kSpinLimit;
     }
 }
 
@@ -1512,6 +1514,7 @@ static PcgArgs make_args(Sim *s, const DevSell &A, const double *Av, const doubl
     a.max_iters = max_iters;
     a.x_zero = x_zero ? 1 : 0;
     a.quiet = quiet ? 1 : 0;
+    a.spin_limit = s->cfg.barrier_spin_limit > 0 ? s->cfg.barrier_spin_limit : (int)kSpinLimit;
     return a;
 }
 

@@ -45,7 +45,8 @@ class pic_config(C.Structure):
                 ("rho_background", C.c_double), ("cg_tol", C.c_double), ("cg_max_iters", C.c_int32),
                 ("init_tol", C.c_double), ("completion_tol", C.c_double), ("walk_cap", C.c_int32),
                 ("solver_blocks_per_sm", C.c_int32),
-                ("max_species", C.c_int32), ("profile", C.c_int32), ("stream", C.c_void_p)]
+                ("max_species", C.c_int32), ("profile", C.c_int32), ("stream", C.c_void_p),
+                ("barrier_spin_limit", C.c_int32)]
 
 
 class pic_gnn_train_cfg(C.Structure):
@@ -220,7 +221,7 @@ class Sim:
                  precision: str = "plain", b0: Sequence[float] = (0.0, 0.0, 0.0), rho_background: float = 0.0,
                  cg_tol: float = 1e-10, init_tol: float = 1e-14, cg_max_iters: int = 10000,
                  walk_cap: int = 63, stream=None, profile: bool = False, solver_blocks_per_sm: int = 0,
-                 preconditioner: str = "jacobi"):
+                 preconditioner: str = "jacobi", barrier_spin_limit: int = 0):
         lib = load()
         self.mesh = mesh
         c = default_config()
@@ -238,6 +239,7 @@ class Sim:
         c.solver_blocks_per_sm = solver_blocks_per_sm
         c.preconditioner = PRECONDITIONERS[preconditioner]
         c.profile = int(profile)
+        c.barrier_spin_limit = int(barrier_spin_limit)
         if stream is not None:
             c.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
         self.config = c
@@ -271,6 +273,13 @@ class Sim:
         _check(_lib.pic_particles_load(self._h, species, q, m, w, n, xp, vp, tp, int(on_dev)),
                "pic_particles_load")
         self.n_loaded += n
+
+    def set_background_charge(self, rho_nodes: np.ndarray):
+        """pic_set_background_charge: static node charges [n_nodes] (before init)."""
+        a = np.ascontiguousarray(rho_nodes, dtype=np.float64).reshape(-1)
+        if a.size != self.mesh.n_nodes:
+            raise PicError(1, "pic_set_background_charge", f"needs {self.mesh.n_nodes} node charges")
+        _check(_lib.pic_set_background_charge(self._h, _ptr(a, C.c_double)), "pic_set_background_charge")
 
     def init(self):
         _check(_lib.pic_sim_init(self._h), "pic_sim_init")

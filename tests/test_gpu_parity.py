@@ -193,6 +193,48 @@ def test_larmor_mfem_mixed(F, oracle_lib):
     assert np.abs(gv - ov[alive]).max() <= 40 * 4 * np.finfo(np.float32).eps * vperp
 
 
+def test_background_charge_parity(F, oracle_lib):
+    """pic_set_background_charge: a smooth static node background (an
+    immobile species) against the oracle, fields and particles within 1e-10
+    for 10 steps, Gauss's law with the background at round-off; the call is
+    refused after init and for non-finite charges."""
+    wl = W.thermal_plasma_cube(n_cells=5, n_particles=6000, seed=23)
+    wl.rho_background = 0.0
+    xyz = wl.mesh.xyz
+    bump = np.exp(-np.sum((xyz - 0.6) ** 2, axis=1) / 0.08)
+    sp = wl.species[0]
+    bg = -(sp.q * sp.w * sp.x.shape[0]) * bump / bump.sum()
+    dt = 2 * DT_CFL_6 * 6 / 5
+    om = oracle_lib.OracleMesh(xyz, wl.mesh.tets)
+    osim = oracle_lib.OracleSim(om, oracle_lib.OracleConfig(dt=dt, b0=wl.b0, cg_tol=1e-13))
+    osim.add_species(sp.q, sp.m, sp.w, sp.x, sp.v, sp.tet)
+    osim.set_background_charge(bg)
+    osim.init()
+    pm = F.Mesh(xyz, wl.mesh.tets)
+    gsim = F.Sim(pm, dt, b0=wl.b0, cg_tol=1e-13)
+    gsim.particles_load(0, sp.q, sp.m, sp.w, sp.x, sp.v, sp.tet)
+    bad = bg.copy()
+    bad[3] = np.nan
+    with pytest.raises(F.PicError) as ei:
+        gsim.set_background_charge(bad)
+    assert ei.value.code == 1
+    gsim.set_background_charge(bg)
+    gsim.init()
+    assert rel_err(gsim.field("RHO_BG"), osim.field("RHO_BG")) <= 1e-14
+    assert rel_err(gsim.field("PHI"), osim.field("PHI")) <= 1e-12
+    for step in range(10):
+        osim.step()
+        gsim.step()
+        for name in ("E", "G", "RHO"):
+            assert rel_err(gsim.field(name), osim.field(name)) <= 1e-10, (step, name)
+        compare_particles(gsim.particles(), osim.particles(), 1.0)
+        d = gsim.diag()
+        assert d["gauss_abs"] <= 1e-12 * d["rho_max"], d
+    with pytest.raises(F.PicError) as ei:
+        gsim.set_background_charge(bg)
+    assert ei.value.code == 10
+
+
 def test_conservation_100_steps(F):
     """Sec. III.A on the GPU: continuity and Gauss at round-off for 100 steps
     of the thermal cube at the production tolerance (cg_tol 1e-10)."""
@@ -290,6 +332,28 @@ def test_error_paths(F):
     s4 = F.sim_from_workload(wl, DT_CFL_6, mesh=m3)
     s4.step()
     assert s4.diag()["cg_iters"] > 1
+
+
+def test_grid_barrier_timeout_is_reported(F):
+    """A persistent solver whose grid-barrier waits give up after one poll
+    (barrier_spin_limit = 1, so blocks that arrive early stop waiting) ends
+    with the timeout status: every block leaves through the bounded path and
+    the call returns PIC_ERR_CUDA with the barrier message.  Nothing faults:
+    the next simulation on the same device solves and steps normally."""
+    wl = W.thermal_plasma_cube(n_cells=16, n_particles=20000, seed=6)
+    m = F.Mesh(wl.mesh.xyz, wl.mesh.tets)
+    sp = wl.species[0]
+    dt = 2 * DT_CFL_6 * 6 / 16
+    s = F.Sim(m, dt, b0=wl.b0, rho_background=wl.rho_background, barrier_spin_limit=1)
+    s.particles_load(0, sp.q, sp.m, sp.w, sp.x, sp.v, sp.tet)
+    with pytest.raises(F.PicError) as ei:
+        s.init()                   # the initial electrostatic solve is a persistent launch
+    assert ei.value.code == 8 and "grid barrier" in str(ei.value)
+    del s
+    ok = F.sim_from_workload(wl, dt, mesh=m)
+    ok.step(3)
+    d = ok.diag()
+    assert d["cg_iters"] > 1 and d["gauss_abs"] <= 1e-12 * d["rho_max"]
 
 
 # ---------------------------------------------------------------------------

@@ -121,3 +121,36 @@ def test_conservation_thermal_cube(oracle_lib, form):
     assert worst_c <= 1e-12 and worst_g <= 1e-12, (worst_c, worst_g)
     assert d["n_alive"] < 10_000       # some electrons reached the walls
     assert d["divb_abs"] <= 1e-12 * np.abs(sim.field("B")).max()
+
+
+def test_background_charge_neutralises(oracle_lib):
+    """A static node background equal to minus the particles' initial node
+    charge leaves nothing for the initial electrostatic solve: phi = 0 and
+    e^0 = 0 exactly; a smooth non-uniform background then keeps Gauss's law
+    (G^T M e + rho + wall + rho_bg = 0) at round-off while the plasma moves."""
+    wl = W.thermal_plasma_cube(n_cells=4, n_particles=3000, seed=19)
+    wl.rho_background = 0.0
+    from oracle.oracle import from_workload
+    probe = from_workload(wl, 3e-10)
+    rho0 = probe.field("RHO")
+    m = probe.mesh
+    sp = wl.species[0]
+    cfg = oracle_lib.OracleConfig(dt=3e-10, b0=wl.b0)
+    sim = oracle_lib.OracleSim(m, cfg)
+    sim.add_species(sp.q, sp.m, sp.w, sp.x, sp.v, sp.tet)
+    sim.set_background_charge(-rho0)
+    sim.init()
+    assert np.abs(sim.field("PHI")).max() == 0.0
+    assert np.abs(sim.field("E")).max() == 0.0
+    assert np.allclose(sim.field("RHO_BG"), -rho0, rtol=0, atol=0)
+    xyz = wl.mesh.xyz
+    bump = np.exp(-np.sum((xyz - 0.4) ** 2, axis=1) / 0.05)
+    bg = -rho0.sum() * bump / bump.sum()
+    sim2 = oracle_lib.OracleSim(m, cfg)
+    sim2.add_species(sp.q, sp.m, sp.w, sp.x, sp.v, sp.tet)
+    sim2.set_background_charge(bg)
+    sim2.init()
+    for _ in range(20):
+        sim2.step()
+        d = sim2.diag()
+        assert d["gauss_abs"] <= 1e-12 * d["rho_max"], d
