@@ -278,7 +278,10 @@ __global__ void __launch_bounds__(256) k_coefficients(int nt, const R *__restric
         if (k == 0) continue;
         for (int i = 0; i < 3; i++) B0[i] += Dk * bv[k] * (R)(x0[i] - xyz[3 * (size_t)nid[k] + i]);
     }
-    R *c = coef + 10 * (size_t)t;
+    // FP64: 10 values per tet; FP32: 12 (two zero pads), so that a tet's
+    // record is three aligned 16-byte vectors for the push
+    constexpr int kStride = std::is_same<R, float>::value ? 12 : 10;
+    R *c = coef + kStride * (size_t)t;
     const R bx[3] = {(R)b_ext.x, (R)b_ext.y, (R)b_ext.z};
     for (int i = 0; i < 3; i++) {
         c[i] = E0[i];
@@ -286,6 +289,10 @@ __global__ void __launch_bounds__(256) k_coefficients(int nt, const R *__restric
         c[6 + i] = B0[i] * inv3v + bx[i];
     }
     c[9] = divb * inv3v;
+    if (kStride == 12) {
+        c[10] = 0;
+        c[11] = 0;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -613,7 +620,11 @@ __device__ __forceinline__ void gather_push(const PushArgs<R, typename std::cond
             tv[k] = h * B[k];
         }
         const R t2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
-        const R f = (R)2 / ((R)1 + t2);
+        R f;
+        if constexpr (std::is_same<R, float>::value)
+            f = __fdividef(2.0f, 1.0f + t2);   // FP32 state: the fast quotient (2 ulp) is enough
+        else
+            f = (R)2 / ((R)1 + t2);
         const R vp[3] = {vm[0] + (vm[1] * tv[2] - vm[2] * tv[1]), vm[1] + (vm[2] * tv[0] - vm[0] * tv[2]),
                          vm[2] + (vm[0] * tv[1] - vm[1] * tv[0])};
         const R sv[3] = {f * tv[0], f * tv[1], f * tv[2]};
@@ -803,8 +814,128 @@ __global__ void __launch_bounds__(kPushBlock) k_push_plain(const PushArgs<double
 // MIXED: FP32 state, gather, push and walk; fixed-point barycentrics and an
 // integer deposit (exact), accumulators per (tet, species)
 // ---------------------------------------------------------------------------
+// Integer sums do not depend on their order (two's complement addition is
+// exact modulo 2^64), so every MIXED deposit that leaves a warp goes to the
+// per-(tet, species) accumulators with 64-bit atomic adds: the run sums of the
+// warp-segmented scan and every piece of a path after the first.  No block
+// merge, no carries between blocks and no crossing records are needed.
+__device__ __forceinline__ void red_add(long long *p, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(v));
+}
+
+// fixed-point barycentrics, rounded, non-negative and summing to 2^24
+// exactly: the largest component (lowest index on ties; `skip` excluded and
+// set to 0) takes what the other three leave
+__device__ __forceinline__ void quantize_fix(const float lam[4], int skip, int L[4]) {
+    int big = skip == 0 ? 1 : 0;
+    float lb = lam[big];
+#pragma unroll
+    for (int k = 1; k < 4; k++)
+        if (k != skip && lam[k] > lb) {
+            big = k;
+            lb = lam[k];
+        }
+    int sum = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        int v = __float2int_rn(lam[k] * 16777216.0f);
+        v = (v < 0 || k == skip || k == big) ? 0 : v;
+        L[k] = v;
+        sum += v;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        if (k == big) L[k] = kFixOne - sum;   // unrolled select: no local-memory indexing
+}
+
+// The path P -> Q leaves its start tet T through local face kmin at fixed-
+// point barycentrics LX (Algorithm 1 with the exact crossing of a straight
+// path).  Walks the rest: each further piece and, at a wall, the charge left
+// there go to the accumulators with integer atomics.  Returns the end tet, or
+// -1 when the particle is absorbed (or runs past the walk cap, flagged).
+__device__ __forceinline__ int walk_rest_mixed(const PushArgs<float, long long> &a, int T, int kmin, const int LX0[4],
+                                               const float Q[3], int spc) {
+    int LX[4] = {LX0[0], LX0[1], LX0[2], LX0[3]};
+    int LS[4];
+    int4 tn = a.tnodes[T];
+    for (int seg = 1; seg < a.walk_cap; seg++) {
+        const int nb = (&a.tnbr[T].x)[kmin];
+        if (nb < 0) {
+            long long *w = a.wacc + ((size_t)T * a.nsp + spc) * 4;
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (LX[k]) red_add(w + k, LX[k]);
+            return -1;
+        }
+        // carry the three shared barycentrics into the neighbour exactly
+        const int4 nn = a.tnodes[nb];
+        const int tv[4] = {tn.x, tn.y, tn.z, tn.w};
+        const int nv[4] = {nn.x, nn.y, nn.z, nn.w};
+        int entry = -1;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            int l = 0;
+            bool shared = false;
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (nv[j] == tv[k]) {
+                    l = LX[k];
+                    shared = true;
+                }
+            LS[j] = l;
+            if (!shared) entry = j;
+        }
+        T = nb;
+        tn = nn;
+        float gp[12];
+        load_geo32(a.geo32, T, gp);
+        float le[4];
+        bary32(gp, Q[0], Q[1], Q[2], le);
+        kmin = -1;
+        float smin = 2.0f;
+        float ls[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) ls[k] = (float)LS[k] * (1.0f / 16777216.0f);
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (k == entry || !(le[k] < 0.0f)) continue;
+            float sk = ls[k] / (ls[k] - le[k]);
+            sk = sk < 0.0f ? 0.0f : sk;
+            if (sk < smin) {
+                smin = sk;
+                kmin = k;
+            }
+        }
+        long long rec[6];
+        long long *acc = a.tacc + ((size_t)T * a.nsp + spc) * kNV;
+        if (kmin < 0) {
+            int LE[4];
+            quantize_fix(le, -1, LE);
+            segment_current_fix(LS, LE, rec);
+#pragma unroll
+            for (int c = 0; c < 6; c++)
+                if (rec[c]) red_add(acc + c, rec[c]);
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (LE[k]) red_add(acc + 6 + k, LE[k]);
+            return T;
+        }
+        float lx[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) lx[k] = ls[k] + smin * (le[k] - ls[k]);
+        quantize_fix(lx, kmin, LX);
+        segment_current_fix(LS, LX, rec);
+#pragma unroll
+        for (int c = 0; c < 6; c++)
+            if (rec[c]) red_add(acc + c, rec[c]);
+    }
+    atomicOr(a.status, (uint32_t)ST_WALK_CAP);
+    return -1;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kPushBlock, 4) k_push_mixed(const PushArgs<float, long long> a) {
+    const int lane = threadIdx.x & 31;
     const long i = (long)blockIdx.x * kPushBlock + threadIdx.x;
     const int n_alive = *a.d_n_alive;
     const bool active = i < n_alive;
@@ -820,103 +951,65 @@ __global__ void __launch_bounds__(kPushBlock, 4) k_push_mixed(const PushArgs<flo
         const long src = a.perm[i];
         const float P[3] = {a.sx0[src], a.sx1[src], a.sx2[src]};
         const float V[3] = {a.sv0[src], a.sv1[src], a.sv2[src]};
-        float gp[12];
+        // the tet's FP32 barycentric map and field coefficients: six aligned
+        // 16-byte loads
+        float gp[12], cf[12];
         load_geo32(a.geo32, tet, gp);
+        {
+            const float4 *c4 = reinterpret_cast<const float4 *>(a.coef + 12 * (size_t)tet);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const float4 v = __ldg(c4 + k);
+                cf[4 * k] = v.x;
+                cf[4 * k + 1] = v.y;
+                cf[4 * k + 2] = v.z;
+                cf[4 * k + 3] = v.w;
+            }
+        }
         float Q[3], Vn[3];
-        gather_push<float, MODE>(a, a.coef + 10 * (size_t)tet, P, V, P[0] - gp[0], P[1] - gp[1], P[2] - gp[2], spc,
-                                 src, i, Q, Vn);
-        float lf[4];
-        int LS[4], LE[4];
+        gather_push<float, MODE>(a, cf, P, V, P[0] - gp[0], P[1] - gp[1], P[2] - gp[2], spc, src, i, Q, Vn);
+        float lf[4], le[4];
+        int LS[4];
         bary32(gp, P[0], P[1], P[2], lf);
-        quantize(lf, -1, LS);
-        int T = tet;
-        int4 tn = a.tnodes[T];
-        int entry = -1;
-        bool done = false, absorbed = false;
+        quantize_fix(lf, -1, LS);
+        bary32(gp, Q[0], Q[1], Q[2], le);
         int endT = tet;
-        for (int seg = 0; seg < a.walk_cap; seg++) {
-            if (seg > 0) load_geo32(a.geo32, T, gp);
-            float le[4];
-            bary32(gp, Q[0], Q[1], Q[2], le);
-            int kmin = -1;
-            float smin = 2.0f;
+        // (written as !(le < 0) so that the crossing branch below always finds
+        // an exit face: a NaN end point counts as inside and is flagged later)
+        const bool stays = !(le[0] < 0.0f) && !(le[1] < 0.0f) && !(le[2] < 0.0f) && !(le[3] < 0.0f);
+        if (stays) {
+            // the common case: the whole path lies in the start tet
+            int LE[4];
+            quantize_fix(le, -1, LE);
+            segment_current_fix(LS, LE, vals);
+#pragma unroll
+            for (int k = 0; k < 4; k++) vals[6 + k] = LE[k];
+        } else {
+            // the first piece, to the face the path leaves through (the
+            // smallest crossing parameter among faces with lam(Q) < 0; ties
+            // to the lowest local index), then the rest of the walk
             float ls[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) ls[k] = (float)LS[k] * (1.0f / 16777216.0f);
+            int kmin = -1;
+            float smin = 2.0f;
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                if (k == entry || !(le[k] < 0.0f)) continue;
-                float s = ls[k] / (ls[k] - le[k]);
-                s = s < 0.0f ? 0.0f : s;
-                if (s < smin) {
-                    smin = s;
+                if (!(le[k] < 0.0f)) continue;
+                float sk = ls[k] / (ls[k] - le[k]);
+                sk = sk < 0.0f ? 0.0f : sk;
+                if (sk < smin) {
+                    smin = sk;
                     kmin = k;
                 }
-            }
-            long long rec[kNV];
-            if (kmin < 0) {
-                quantize(le, -1, LE);
-                segment_current_fix(LS, LE, rec);
-#pragma unroll
-                for (int k = 0; k < 4; k++) rec[6 + k] = LE[k];
-                if (seg == 0) {
-#pragma unroll
-                    for (int c = 0; c < kNV; c++) vals[c] = rec[c];
-                } else {
-                    push_record(a, (uint32_t)(T * a.nsp + spc), 0, i, seg, rec);
-                }
-                endT = T;
-                done = true;
-                break;
             }
             float lx[4];
             int LX[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) lx[k] = ls[k] + smin * (le[k] - ls[k]);
-            quantize(lx, kmin, LX);
-            segment_current_fix(LS, LX, rec);
-#pragma unroll
-            for (int k = 0; k < 4; k++) rec[6 + k] = 0;
-            if (seg == 0) {
-#pragma unroll
-                for (int c = 0; c < kNV; c++) vals[c] = rec[c];
-            } else {
-                push_record(a, (uint32_t)(T * a.nsp + spc), 0, i, seg, rec);
-            }
-            const int nb = (&a.tnbr[T].x)[kmin];
-            if (nb < 0) {
-                long long wrec[kNV];
-#pragma unroll
-                for (int k = 0; k < 6; k++) wrec[k] = 0;
-#pragma unroll
-                for (int k = 0; k < 4; k++) wrec[6 + k] = LX[k];
-                push_record(a, (uint32_t)(T * a.nsp + spc), 1, i, kMaxWalk, wrec);
-                absorbed = true;
-                done = true;
-                break;
-            }
-            const int4 nn = a.tnodes[nb];
-            const int tv[4] = {tn.x, tn.y, tn.z, tn.w};
-            const int nv[4] = {nn.x, nn.y, nn.z, nn.w};
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                int l = 0;
-                bool shared = false;
-#pragma unroll
-                for (int k = 0; k < 4; k++)
-                    if (nv[j] == tv[k]) {
-                        l = LX[k];
-                        shared = true;
-                    }
-                LS[j] = l;
-                if (!shared) entry = j;
-            }
-            T = nb;
-            tn = nn;
-        }
-        if (!done) {
-            atomicOr(a.status, (uint32_t)ST_WALK_CAP);
-            absorbed = true;
+            quantize_fix(lx, kmin, LX);
+            segment_current_fix(LS, LX, vals);
+            endT = walk_rest_mixed(a, tet, kmin, LX, Q, spc);
         }
         a.dx0[i] = Q[0];
         a.dx1[i] = Q[1];
@@ -925,15 +1018,58 @@ __global__ void __launch_bounds__(kPushBlock, 4) k_push_mixed(const PushArgs<flo
         a.dv1[i] = Vn[1];
         a.dv2[i] = Vn[2];
         a.did[i] = a.sid[src];
-        a.dkey[i] = absorbed ? a.dead_key : (((uint32_t)endT << 2) | (uint32_t)spc);
-        if (!absorbed) {
+        a.dkey[i] = endT < 0 ? a.dead_key : (((uint32_t)endT << 2) | (uint32_t)spc);
+        if (endT >= 0) {
             alive_out = 1;
             ke = 0.5f * a.mw32[spc] * (Vn[0] * Vn[0] + Vn[1] * Vn[1] + Vn[2] * Vn[2]);
             if (!(ke == ke) || !(Q[0] == Q[0])) atomicOr(a.status, (uint32_t)ST_NAN);
         }
         rkey = (uint32_t)(tet * a.nsp + spc);
     }
-    reduce_block<float, long long, float>(a, rkey, vals, ke, alive_out, n_alive);
+    // live count and kinetic energy: one value per warp (the energy partials
+    // are summed later in warp order, so the total does not depend on timing)
+    {
+        const unsigned ball = __ballot_sync(0xFFFFFFFFu, alive_out);
+        float k2 = ke;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) k2 += __shfl_down_sync(0xFFFFFFFFu, k2, o);
+        if (lane == 0) {
+            if (ball) atomicAdd(a.n_alive_next, __popc(ball));
+            a.ke_part[i >> 5] = (double)k2;
+        }
+    }
+    // first pieces: warp-segmented inclusive scan by key (the four node
+    // charges are integers in [0, 2^24]; a run of at most 32 sums below 2^29,
+    // so two share one 64-bit lane without carries: 8 scanned channels)
+    long long w[8];
+#pragma unroll
+    for (int c = 0; c < 6; c++) w[c] = vals[c];
+    w[6] = vals[6] | (vals[7] << 32);
+    w[7] = vals[8] | (vals[9] << 32);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t ko = __shfl_up_sync(0xFFFFFFFFu, rkey, off);
+        const bool take = lane >= off && ko == rkey;
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            const long long vo = shfl_up_v(w[c], off);
+            if (take) w[c] += vo;
+        }
+    }
+    // the last lane of every run adds the run's sums
+    const uint32_t knext = __shfl_down_sync(0xFFFFFFFFu, rkey, 1);
+    if ((lane == 31 || knext != rkey) && rkey != kInvalid) {
+        long long *dst = a.tacc + (size_t)rkey * kNV;
+#pragma unroll
+        for (int c = 0; c < 6; c++)
+            if (w[c]) red_add(dst + c, w[c]);
+        const long long n0 = w[6] & 0xFFFFFFFFll, n1 = (long long)((unsigned long long)w[6] >> 32);
+        const long long n2 = w[7] & 0xFFFFFFFFll, n3 = (long long)((unsigned long long)w[7] >> 32);
+        if (n0) red_add(dst + 6, n0);
+        if (n1) red_add(dst + 7, n1);
+        if (n2) red_add(dst + 8, n2);
+        if (n3) red_add(dst + 9, n3);
+    }
 }
 
 // spanning runs: a head piece (the last run of a block, or a block's first run
@@ -983,29 +1119,6 @@ __global__ void __launch_bounds__(256) k_overflow_reduce(const int *d_count, int
         for (int c = 0; c < 4; c++) wacc[idx * 4 + c] += sum[6 + c];
     } else {
         for (int c = 0; c < kNV; c++) tacc[idx * kNV + c] += sum[c];
-    }
-}
-
-// MIXED crossing records hold integers (fixed point): they are added with
-// 64-bit atomics in whatever order, since integer sums do not depend on it
-// (modulo 2^64, so a partial sum that wraps still ends exact) -- no sort of
-// the records is needed, unlike the FP64 records of the PLAIN path.
-__global__ void __launch_bounds__(256) k_overflow_scatter(const int *d_count, int cap,
-                                                          const unsigned long long *__restrict__ okey,
-                                                          const long long *__restrict__ oval, int oshift,
-                                                          unsigned long long *tacc, unsigned long long *wacc) {
-    const int n = min(*d_count, cap);
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const unsigned long long tw = okey[j] >> oshift;
-    const size_t idx = (size_t)(tw >> 1);
-    const long long *v = oval + (size_t)j * kNV;
-    if (tw & 1ull) {
-        for (int c = 0; c < 4; c++)
-            if (v[6 + c]) atomicAdd(wacc + idx * 4 + c, (unsigned long long)v[6 + c]);
-    } else {
-        for (int c = 0; c < kNV; c++)
-            if (v[c]) atomicAdd(tacc + idx * kNV + c, (unsigned long long)v[c]);
     }
 }
 
@@ -1312,11 +1425,12 @@ int particles_alloc(Sim *s, size_t cap) {
     if ((rc = s->skey.alloc(cap)) || (rc = s->sval.alloc(cap)) || (rc = s->tkey.alloc(cap)) ||
         (rc = s->tval.alloc(cap)))
         return rc;
-    if ((rc = overflow_alloc(s, (int)std::min<size_t>(std::max<size_t>(cap / 8, 65536), (size_t)1 << 30))))
+    // crossing records: PLAIN only (MIXED adds later pieces with integer atomics)
+    if (!s->mixed && (rc = overflow_alloc(s, (int)std::min<size_t>(std::max<size_t>(cap / 8, 65536), (size_t)1 << 30))))
         return rc;
     const size_t blocks = std::max<size_t>(1, (cap + kPushBlock - 1) / kPushBlock);
     if ((rc = s->bcar.alloc(2 * blocks * kNV)) || (rc = s->bcar_key.alloc(2 * blocks)) ||
-        (rc = s->ke_part.alloc(blocks)))
+        (rc = s->ke_part.alloc(blocks * (kPushBlock / 32))))
         return rc;
     s->push_blocks_cap = blocks;
     s->cap = cap;
@@ -1544,7 +1658,6 @@ static int launch_push(Sim *s, int mode) {
     // (in a batch the grid covers all n_total and the kernel reads n_alive)
     const int live = s->batch_mode ? s->n_total : s->hctl->n_alive;
     const int blocks = std::max(1, (live + kPushBlock - 1) / kPushBlock);
-    s->last_push_blocks = blocks;
     FP_CUDA(cudaMemsetAsync(&dc->pad, 0, sizeof(int), s->stream));
     prof_begin(s, PH_PUSH);
     if (std::is_same<R, float>::value) {
@@ -1561,7 +1674,13 @@ static int launch_push(Sim *s, int mode) {
     prof_end(s, PH_PUSH);
     prof_begin(s, PH_DEPOSIT);
     FP_CUDA(cudaGetLastError());
-    { k_fixup<V><<<(2 * blocks + 255) / 256, 256, 0, s->stream>>>(blocks, s->nsp, s->skey.p, &dc->n_alive, s->bcar_key.p, (const V *)s->bcar.p, (V *)s->tacc.p); note_launch(); }
+    if (std::is_same<R, double>::value) {
+        // PLAIN: runs that span blocks are added in block order
+        { k_fixup<V><<<(2 * blocks + 255) / 256, 256, 0, s->stream>>>(blocks, s->nsp, s->skey.p, &dc->n_alive, s->bcar_key.p, (const V *)s->bcar.p, (V *)s->tacc.p); note_launch(); }
+        s->n_ke_parts = blocks;
+    } else {
+        s->n_ke_parts = blocks * (kPushBlock / 32);   // one energy partial per warp
+    }
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
 }
@@ -1577,7 +1696,7 @@ int particle_push(Sim *s, int charge_only) {
         const int mode = charge_only ? 2 : (s->ab ? 1 : 0);
         int rc = s->mixed ? launch_push<float, long long>(s, mode) : launch_push<double, double>(s, mode);
         if (rc) return rc;
-        if (s->batch_mode) break;   // no retry: an overflow latches its status bit
+        if (s->batch_mode || s->mixed) break;   // MIXED writes no records; a batch latches an overflow
         // the push reads the current bank and writes the other one, so a push
         // whose record buffer overflowed is simply run again with more room
         FP_CUDA(cudaMemcpyAsync(&s->hctl->n_over, &s->dctl.p->n_over, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
@@ -1603,11 +1722,8 @@ int particle_push(Sim *s, int charge_only) {
         const int oshift = 6 + std::max(1, bitlen((unsigned long long)s->n_total));
         const int bits = oshift + bitlen(((unsigned long long)m->n_tets * s->nsp << 1) | 1ull);
         // known on the host since the push, or (batch) a device count bounded by the buffer
-        const int nover = s->batch_mode ? s->ocap : s->hctl->n_over;
-        if (nover > 0 && s->mixed) {
-            { k_overflow_scatter<<<(nover + 255) / 256, 256, 0, s->stream>>>(&s->dctl.p->n_over, nover, s->okey.p, (const long long *)s->oval.p, oshift, (unsigned long long *)s->tacc.p, (unsigned long long *)s->wacc.p); note_launch(); }
-            FP_CUDA(cudaGetLastError());
-        } else if (nover > 0) {
+        const int nover = s->mixed ? 0 : s->batch_mode ? s->ocap : s->hctl->n_over;
+        if (nover > 0) {
             unsigned long long *ok;
             uint32_t *ov;
             rc = radix_sort<unsigned long long>(s->stream, s->okey.p, s->okey2.p, s->oidx.p, s->okey.p, s->oidx2.p,
@@ -1633,7 +1749,7 @@ int particles_batch_prepare(Sim *s) {
     if (s->n_total == 0) return PIC_OK;
     const int want = std::min(std::max(s->n_total + 1024, s->ocap), (1 << 30) - 1);
     int rc;
-    if (want > s->ocap && (rc = overflow_alloc(s, want))) return rc;
+    if (!s->mixed && want > s->ocap && (rc = overflow_alloc(s, want))) return rc;
     return PIC_OK;
 }
 
@@ -1674,7 +1790,7 @@ static int particles_grow(Sim *s, size_t cap, size_t keep) {
         return rc;
     const size_t blocks = std::max<size_t>(1, (cap + kPushBlock - 1) / kPushBlock);
     if ((rc = s->bcar.alloc(2 * blocks * kNV)) || (rc = s->bcar_key.alloc(2 * blocks)) ||
-        (rc = s->ke_part.alloc(blocks)))
+        (rc = s->ke_part.alloc(blocks * (kPushBlock / 32))))
         return rc;
     s->push_blocks_cap = blocks;
     s->cap = cap;
@@ -1722,7 +1838,7 @@ int particles_inject(Sim *s, int species, int n, const double *hx, const double 
     if ((size_t)start + n > s->cap &&
         (rc = particles_grow(s, std::max<size_t>(2 * s->cap, (size_t)start + n), (size_t)start)))
         return rc;
-    if ((size_t)start + n > (size_t)s->ocap / 2 &&
+    if (!s->mixed && (size_t)start + n > (size_t)s->ocap / 2 &&
         (rc = overflow_alloc(s, (int)std::min<size_t>(2 * ((size_t)start + n), (size_t)1 << 30))))
         return rc;
     PartBank &k = s->bank[s->cur];

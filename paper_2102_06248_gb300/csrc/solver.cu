@@ -1665,7 +1665,7 @@ int compute_diagnostics(Sim *s) {
     { k_diag_divb<<<grid_for_elems(m->n_tets), kThreads, 0, s->stream>>>(m->n_tets, m->tet_face.p, m->tet_sign.p, s->b.p,
                                                                        s->diag_part.p, dg); note_launch(); }
     { k_diag_energy_b<<<grid_for_slices(m->Hs.n_slices), kThreads, 0, s->stream>>>(m->n_faces, m->Hs.n_slices, m->Hs.ptr.p, m->Hs.width.p, m->Hs.col.p, m->Hs_val.p, s->b.p, s->diag_part.p, dg); note_launch(); }
-    { k_sum_ke<<<grid_for_elems(s->last_push_blocks), kThreads, 0, s->stream>>>(s->last_push_blocks, s->ke_part.p, s->diag_part.p, dg); note_launch(); }
+    { k_sum_ke<<<grid_for_elems(s->n_ke_parts), kThreads, 0, s->stream>>>(s->n_ke_parts, s->ke_part.p, s->diag_part.p, dg); note_launch(); }
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
 }
