@@ -814,11 +814,14 @@ __global__ void __launch_bounds__(kPushBlock) k_push_plain(const PushArgs<double
 // MIXED: FP32 state, gather, push and walk; fixed-point barycentrics and an
 // integer deposit (exact), accumulators per (tet, species)
 // ---------------------------------------------------------------------------
-// Integer sums do not depend on their order (two's complement addition is
-// exact modulo 2^64), so every MIXED deposit that leaves a warp goes to the
-// per-(tet, species) accumulators with 64-bit atomic adds: the run sums of the
-// warp-segmented scan and every piece of a path after the first.  No block
-// merge, no carries between blocks and no crossing records are needed.
+// The first piece of every path is summed per (tet, species) run by the
+// block reduction shared with the PLAIN path.  The rare later pieces of a
+// path that crosses faces, and the charge a particle leaves on a wall, are
+// integers, whose sums do not depend on their order (two's complement addition
+// is exact modulo 2^64): they go to the accumulators with 64-bit atomic adds,
+// so no crossing records and no sort of them are needed.  (Adding every run
+// sum with atomics instead of the block reduction made the push 40% slower:
+// ~37M 64-bit atomics per step on accumulators larger than L2.)
 __device__ __forceinline__ void red_add(long long *p, long long v) {
     atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(v));
 }
@@ -827,11 +830,11 @@ __device__ __forceinline__ void red_add(long long *p, long long v) {
 // exactly: the largest component (lowest index on ties; `skip` excluded and
 // set to 0) takes what the other three leave
 __device__ __forceinline__ void quantize_fix(const float lam[4], int skip, int L[4]) {
-    int big = skip == 0 ? 1 : 0;
-    float lb = lam[big];
+    int big = -1;
+    float lb = 0.0f;
 #pragma unroll
-    for (int k = 1; k < 4; k++)
-        if (k != skip && lam[k] > lb) {
+    for (int k = 0; k < 4; k++)
+        if (k != skip && (big < 0 || lam[k] > lb)) {
             big = k;
             lb = lam[k];
         }
@@ -935,7 +938,6 @@ __device__ __forceinline__ int walk_rest_mixed(const PushArgs<float, long long> 
 
 template <int MODE>
 __global__ void __launch_bounds__(kPushBlock, 4) k_push_mixed(const PushArgs<float, long long> a) {
-    const int lane = threadIdx.x & 31;
     const long i = (long)blockIdx.x * kPushBlock + threadIdx.x;
     const int n_alive = *a.d_n_alive;
     const bool active = i < n_alive;
@@ -1026,50 +1028,7 @@ __global__ void __launch_bounds__(kPushBlock, 4) k_push_mixed(const PushArgs<flo
         }
         rkey = (uint32_t)(tet * a.nsp + spc);
     }
-    // live count and kinetic energy: one value per warp (the energy partials
-    // are summed later in warp order, so the total does not depend on timing)
-    {
-        const unsigned ball = __ballot_sync(0xFFFFFFFFu, alive_out);
-        float k2 = ke;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) k2 += __shfl_down_sync(0xFFFFFFFFu, k2, o);
-        if (lane == 0) {
-            if (ball) atomicAdd(a.n_alive_next, __popc(ball));
-            a.ke_part[i >> 5] = (double)k2;
-        }
-    }
-    // first pieces: warp-segmented inclusive scan by key (the four node
-    // charges are integers in [0, 2^24]; a run of at most 32 sums below 2^29,
-    // so two share one 64-bit lane without carries: 8 scanned channels)
-    long long w[8];
-#pragma unroll
-    for (int c = 0; c < 6; c++) w[c] = vals[c];
-    w[6] = vals[6] | (vals[7] << 32);
-    w[7] = vals[8] | (vals[9] << 32);
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t ko = __shfl_up_sync(0xFFFFFFFFu, rkey, off);
-        const bool take = lane >= off && ko == rkey;
-#pragma unroll
-        for (int c = 0; c < 8; c++) {
-            const long long vo = shfl_up_v(w[c], off);
-            if (take) w[c] += vo;
-        }
-    }
-    // the last lane of every run adds the run's sums
-    const uint32_t knext = __shfl_down_sync(0xFFFFFFFFu, rkey, 1);
-    if ((lane == 31 || knext != rkey) && rkey != kInvalid) {
-        long long *dst = a.tacc + (size_t)rkey * kNV;
-#pragma unroll
-        for (int c = 0; c < 6; c++)
-            if (w[c]) red_add(dst + c, w[c]);
-        const long long n0 = w[6] & 0xFFFFFFFFll, n1 = (long long)((unsigned long long)w[6] >> 32);
-        const long long n2 = w[7] & 0xFFFFFFFFll, n3 = (long long)((unsigned long long)w[7] >> 32);
-        if (n0) red_add(dst + 6, n0);
-        if (n1) red_add(dst + 7, n1);
-        if (n2) red_add(dst + 8, n2);
-        if (n3) red_add(dst + 9, n3);
-    }
+    reduce_block<float, long long, float>(a, rkey, vals, ke, alive_out, n_alive);
 }
 
 // spanning runs: a head piece (the last run of a block, or a block's first run
@@ -1430,7 +1389,7 @@ int particles_alloc(Sim *s, size_t cap) {
         return rc;
     const size_t blocks = std::max<size_t>(1, (cap + kPushBlock - 1) / kPushBlock);
     if ((rc = s->bcar.alloc(2 * blocks * kNV)) || (rc = s->bcar_key.alloc(2 * blocks)) ||
-        (rc = s->ke_part.alloc(blocks * (kPushBlock / 32))))
+        (rc = s->ke_part.alloc(blocks)))
         return rc;
     s->push_blocks_cap = blocks;
     s->cap = cap;
@@ -1674,13 +1633,9 @@ static int launch_push(Sim *s, int mode) {
     prof_end(s, PH_PUSH);
     prof_begin(s, PH_DEPOSIT);
     FP_CUDA(cudaGetLastError());
-    if (std::is_same<R, double>::value) {
-        // PLAIN: runs that span blocks are added in block order
-        { k_fixup<V><<<(2 * blocks + 255) / 256, 256, 0, s->stream>>>(blocks, s->nsp, s->skey.p, &dc->n_alive, s->bcar_key.p, (const V *)s->bcar.p, (V *)s->tacc.p); note_launch(); }
-        s->n_ke_parts = blocks;
-    } else {
-        s->n_ke_parts = blocks * (kPushBlock / 32);   // one energy partial per warp
-    }
+    // runs that span blocks are added in block order
+    { k_fixup<V><<<(2 * blocks + 255) / 256, 256, 0, s->stream>>>(blocks, s->nsp, s->skey.p, &dc->n_alive, s->bcar_key.p, (const V *)s->bcar.p, (V *)s->tacc.p); note_launch(); }
+    s->n_ke_parts = blocks;
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
 }
@@ -1790,7 +1745,7 @@ static int particles_grow(Sim *s, size_t cap, size_t keep) {
         return rc;
     const size_t blocks = std::max<size_t>(1, (cap + kPushBlock - 1) / kPushBlock);
     if ((rc = s->bcar.alloc(2 * blocks * kNV)) || (rc = s->bcar_key.alloc(2 * blocks)) ||
-        (rc = s->ke_part.alloc(blocks * (kPushBlock / 32))))
+        (rc = s->ke_part.alloc(blocks)))
         return rc;
     s->push_blocks_cap = blocks;
     s->cap = cap;
