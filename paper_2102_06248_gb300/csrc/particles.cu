@@ -815,16 +815,11 @@ __global__ void __launch_bounds__(kPushBlock) k_push_plain(const PushArgs<double
 // integer deposit (exact), accumulators per (tet, species)
 // ---------------------------------------------------------------------------
 // The first piece of every path is summed per (tet, species) run by the
-// block reduction shared with the PLAIN path.  The rare later pieces of a
-// path that crosses faces, and the charge a particle leaves on a wall, are
-// integers, whose sums do not depend on their order (two's complement addition
-// is exact modulo 2^64): they go to the accumulators with 64-bit atomic adds,
-// so no crossing records and no sort of them are needed.  (Adding every run
-// sum with atomics instead of the block reduction made the push 40% slower:
-// ~37M 64-bit atomics per step on accumulators larger than L2.)
-__device__ __forceinline__ void red_add(long long *p, long long v) {
-    atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(v));
-}
+// block reduction shared with the PLAIN path; the rare later pieces of a path
+// that crosses faces, and the charge a particle leaves on a wall, become
+// records that k_overflow_scatter adds after the kernel.  (Adding every run
+// sum with 64-bit atomics instead of the block reduction made the push 40%
+// slower: ~37M atomics per step on accumulators larger than L2.)
 
 // fixed-point barycentrics, rounded, non-negative and summing to 2^24
 // exactly: the largest component (lowest index on ties; `skip` excluded and
@@ -856,18 +851,20 @@ __device__ __forceinline__ void quantize_fix(const float lam[4], int skip, int L
 // path).  Walks the rest: each further piece and, at a wall, the charge left
 // there go to the accumulators with integer atomics.  Returns the end tet, or
 // -1 when the particle is absorbed (or runs past the walk cap, flagged).
-__device__ __forceinline__ int walk_rest_mixed(const PushArgs<float, long long> &a, int T, int kmin, const int LX0[4],
-                                               const float Q[3], int spc) {
+__device__ __forceinline__ int walk_rest_mixed(const PushArgs<float, long long> &a, long i, int T, int kmin,
+                                               const int LX0[4], const float Q[3], int spc) {
     int LX[4] = {LX0[0], LX0[1], LX0[2], LX0[3]};
     int LS[4];
     int4 tn = a.tnodes[T];
     for (int seg = 1; seg < a.walk_cap; seg++) {
         const int nb = (&a.tnbr[T].x)[kmin];
         if (nb < 0) {
-            long long *w = a.wacc + ((size_t)T * a.nsp + spc) * 4;
+            long long wrec[kNV];
 #pragma unroll
-            for (int k = 0; k < 4; k++)
-                if (LX[k]) red_add(w + k, LX[k]);
+            for (int k = 0; k < 6; k++) wrec[k] = 0;
+#pragma unroll
+            for (int k = 0; k < 4; k++) wrec[6 + k] = LX[k];
+            push_record(a, (uint32_t)(T * a.nsp + spc), 1, i, kMaxWalk, wrec);
             return -1;
         }
         // carry the three shared barycentrics into the neighbour exactly
@@ -909,18 +906,14 @@ __device__ __forceinline__ int walk_rest_mixed(const PushArgs<float, long long> 
                 kmin = k;
             }
         }
-        long long rec[6];
-        long long *acc = a.tacc + ((size_t)T * a.nsp + spc) * kNV;
+        long long rec[kNV];
         if (kmin < 0) {
             int LE[4];
             quantize_fix(le, -1, LE);
             segment_current_fix(LS, LE, rec);
 #pragma unroll
-            for (int c = 0; c < 6; c++)
-                if (rec[c]) red_add(acc + c, rec[c]);
-#pragma unroll
-            for (int k = 0; k < 4; k++)
-                if (LE[k]) red_add(acc + 6 + k, LE[k]);
+            for (int k = 0; k < 4; k++) rec[6 + k] = LE[k];
+            push_record(a, (uint32_t)(T * a.nsp + spc), 0, i, seg, rec);
             return T;
         }
         float lx[4];
@@ -929,8 +922,8 @@ __device__ __forceinline__ int walk_rest_mixed(const PushArgs<float, long long> 
         quantize_fix(lx, kmin, LX);
         segment_current_fix(LS, LX, rec);
 #pragma unroll
-        for (int c = 0; c < 6; c++)
-            if (rec[c]) red_add(acc + c, rec[c]);
+        for (int k = 0; k < 4; k++) rec[6 + k] = 0;
+        push_record(a, (uint32_t)(T * a.nsp + spc), 0, i, seg, rec);
     }
     atomicOr(a.status, (uint32_t)ST_WALK_CAP);
     return -1;
@@ -1011,7 +1004,7 @@ __global__ void __launch_bounds__(kPushBlock, 4) k_push_mixed(const PushArgs<flo
             for (int k = 0; k < 4; k++) lx[k] = ls[k] + smin * (le[k] - ls[k]);
             quantize_fix(lx, kmin, LX);
             segment_current_fix(LS, LX, vals);
-            endT = walk_rest_mixed(a, tet, kmin, LX, Q, spc);
+            endT = walk_rest_mixed(a, i, tet, kmin, LX, Q, spc);
         }
         a.dx0[i] = Q[0];
         a.dx1[i] = Q[1];
@@ -1078,6 +1071,29 @@ __global__ void __launch_bounds__(256) k_overflow_reduce(const int *d_count, int
         for (int c = 0; c < 4; c++) wacc[idx * 4 + c] += sum[6 + c];
     } else {
         for (int c = 0; c < kNV; c++) tacc[idx * kNV + c] += sum[c];
+    }
+}
+
+// MIXED crossing records hold integers (fixed point): they are added with
+// 64-bit atomics in whatever order, since integer sums do not depend on it
+// (modulo 2^64, so a partial sum that wraps still ends exact) -- no sort of
+// the records is needed, unlike the FP64 records of the PLAIN path.
+__global__ void __launch_bounds__(256) k_overflow_scatter(const int *d_count, int cap,
+                                                          const unsigned long long *__restrict__ okey,
+                                                          const long long *__restrict__ oval, int oshift,
+                                                          unsigned long long *tacc, unsigned long long *wacc) {
+    const int n = min(*d_count, cap);
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const unsigned long long tw = okey[j] >> oshift;
+    const size_t idx = (size_t)(tw >> 1);
+    const long long *v = oval + (size_t)j * kNV;
+    if (tw & 1ull) {
+        for (int c = 0; c < 4; c++)
+            if (v[6 + c]) atomicAdd(wacc + idx * 4 + c, (unsigned long long)v[6 + c]);
+    } else {
+        for (int c = 0; c < kNV; c++)
+            if (v[c]) atomicAdd(tacc + idx * kNV + c, (unsigned long long)v[c]);
     }
 }
 
@@ -1384,8 +1400,7 @@ int particles_alloc(Sim *s, size_t cap) {
     if ((rc = s->skey.alloc(cap)) || (rc = s->sval.alloc(cap)) || (rc = s->tkey.alloc(cap)) ||
         (rc = s->tval.alloc(cap)))
         return rc;
-    // crossing records: PLAIN only (MIXED adds later pieces with integer atomics)
-    if (!s->mixed && (rc = overflow_alloc(s, (int)std::min<size_t>(std::max<size_t>(cap / 8, 65536), (size_t)1 << 30))))
+    if ((rc = overflow_alloc(s, (int)std::min<size_t>(std::max<size_t>(cap / 8, 65536), (size_t)1 << 30))))
         return rc;
     const size_t blocks = std::max<size_t>(1, (cap + kPushBlock - 1) / kPushBlock);
     if ((rc = s->bcar.alloc(2 * blocks * kNV)) || (rc = s->bcar_key.alloc(2 * blocks)) ||
@@ -1651,7 +1666,7 @@ int particle_push(Sim *s, int charge_only) {
         const int mode = charge_only ? 2 : (s->ab ? 1 : 0);
         int rc = s->mixed ? launch_push<float, long long>(s, mode) : launch_push<double, double>(s, mode);
         if (rc) return rc;
-        if (s->batch_mode || s->mixed) break;   // MIXED writes no records; a batch latches an overflow
+        if (s->batch_mode) break;   // no retry: an overflow latches its status bit
         // the push reads the current bank and writes the other one, so a push
         // whose record buffer overflowed is simply run again with more room
         FP_CUDA(cudaMemcpyAsync(&s->hctl->n_over, &s->dctl.p->n_over, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
@@ -1677,8 +1692,11 @@ int particle_push(Sim *s, int charge_only) {
         const int oshift = 6 + std::max(1, bitlen((unsigned long long)s->n_total));
         const int bits = oshift + bitlen(((unsigned long long)m->n_tets * s->nsp << 1) | 1ull);
         // known on the host since the push, or (batch) a device count bounded by the buffer
-        const int nover = s->mixed ? 0 : s->batch_mode ? s->ocap : s->hctl->n_over;
-        if (nover > 0) {
+        const int nover = s->batch_mode ? s->ocap : s->hctl->n_over;
+        if (nover > 0 && s->mixed) {
+            { k_overflow_scatter<<<(nover + 255) / 256, 256, 0, s->stream>>>(&s->dctl.p->n_over, nover, s->okey.p, (const long long *)s->oval.p, oshift, (unsigned long long *)s->tacc.p, (unsigned long long *)s->wacc.p); note_launch(); }
+            FP_CUDA(cudaGetLastError());
+        } else if (nover > 0) {
             unsigned long long *ok;
             uint32_t *ov;
             rc = radix_sort<unsigned long long>(s->stream, s->okey.p, s->okey2.p, s->oidx.p, s->okey.p, s->oidx2.p,
@@ -1704,7 +1722,7 @@ int particles_batch_prepare(Sim *s) {
     if (s->n_total == 0) return PIC_OK;
     const int want = std::min(std::max(s->n_total + 1024, s->ocap), (1 << 30) - 1);
     int rc;
-    if (!s->mixed && want > s->ocap && (rc = overflow_alloc(s, want))) return rc;
+    if (want > s->ocap && (rc = overflow_alloc(s, want))) return rc;
     return PIC_OK;
 }
 
@@ -1793,7 +1811,7 @@ int particles_inject(Sim *s, int species, int n, const double *hx, const double 
     if ((size_t)start + n > s->cap &&
         (rc = particles_grow(s, std::max<size_t>(2 * s->cap, (size_t)start + n), (size_t)start)))
         return rc;
-    if (!s->mixed && (size_t)start + n > (size_t)s->ocap / 2 &&
+    if ((size_t)start + n > (size_t)s->ocap / 2 &&
         (rc = overflow_alloc(s, (int)std::min<size_t>(2 * ((size_t)start + n), (size_t)1 << 30))))
         return rc;
     PartBank &k = s->bank[s->cur];
