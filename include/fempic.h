@@ -183,6 +183,14 @@ typedef struct {
     int32_t barrier_spin_limit; /* polls a persistent solver block makes at one grid barrier before it
                                    gives up, records PIC_ERR_CUDA ("timed out at a grid barrier") and
                                    returns (0: about a second's worth, 2^22) */
+    int32_t curved_path;     /* 1: the path of a step is the Lagrange polynomial through r^{n+1}, r^n
+                                and the earlier positions at t_{n+1}, t_n, ... (Sec. III.B, Eq. path;
+                                degree = the Adams-Bashforth order in use, so it ramps up with the
+                                history), walked with Algorithm 1, exits found by Algorithm 2's
+                                bisection to 1e-15 of the step, Whitney-1 integrated over each in-cell
+                                piece by max(degree, 2)-point Gauss-Legendre (exact: the integrand has
+                                degree 2 deg - 1).  Adams-Bashforth pusher and PLAIN precision only
+                                (PIC_ERR_INVALID_ARG otherwise).  0: straight segments (default) */
 } pic_config;
 
 /* Fills a config with the defaults above (form WE, Boris, PLAIN, dt = 0). */

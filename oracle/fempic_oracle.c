@@ -669,6 +669,8 @@ struct orc_sim {
     int *tet, *alive;
     double *ahist, *vhist;          /* AB history: 5 x 3 per particle, newest first */
     int nhist;                      /* number of history levels filled */
+    double *rhist;                  /* earlier positions r^{n-1}, r^{n-2}, ...: 5 x 3 per particle */
+    int nrhist;                     /* number of position levels filled */
     double *e, *e_prev, *b, *b_prev, *g, *g_prev, *dg, *rho, *rho_prev, *wall, *wall_prev, *rho_bg, *phi;
     double *diagA;                  /* diag of A = M + dt^2/4 K */
     double *bg_nodes;               /* static node charges added to the uniform background (or NULL) */
@@ -714,7 +716,7 @@ orc_sim *orc_sim_new(orc_mesh *m, const orc_config *cfg) {
 void orc_sim_free(orc_sim *s) {
     if (!s) return;
     free(s->x); free(s->v); free(s->q); free(s->mass); free(s->w); free(s->tet); free(s->alive);
-    free(s->ahist); free(s->vhist);
+    free(s->ahist); free(s->vhist); free(s->rhist);
     free(s->e); free(s->e_prev); free(s->b); free(s->b_prev); free(s->g); free(s->g_prev); free(s->dg);
     free(s->rho); free(s->rho_prev); free(s->wall); free(s->wall_prev); free(s->rho_bg); free(s->phi);
     free(s->diagA); free(s->bg_nodes);
@@ -735,6 +737,7 @@ int orc_add_species(orc_sim *s, double q, double mass, double w, int n, const do
     s->alive = realloc(s->alive, sizeof(int) * (np ? np : 1));
     s->ahist = realloc(s->ahist, sizeof(double) * 15 * (np ? np : 1));
     s->vhist = realloc(s->vhist, sizeof(double) * 15 * (np ? np : 1));
+    s->rhist = realloc(s->rhist, sizeof(double) * 15 * (np ? np : 1));
     for (int i = 0; i < n; i++) {
         int p = s->np + i;
         int t = tet[i];
@@ -746,7 +749,7 @@ int orc_add_species(orc_sim *s, double q, double mass, double w, int n, const do
         memcpy(s->x + 3 * p, x + 3 * i, 24);
         memcpy(s->v + 3 * p, v + 3 * i, 24);
         s->q[p] = q; s->mass[p] = mass; s->w[p] = w; s->tet[p] = t; s->alive[p] = 1;
-        memset(s->ahist + 15 * p, 0, 120); memset(s->vhist + 15 * p, 0, 120);
+        memset(s->ahist + 15 * p, 0, 120); memset(s->vhist + 15 * p, 0, 120); memset(s->rhist + 15 * p, 0, 120);
     }
     s->np = np;
     return ORC_OK;
@@ -943,9 +946,22 @@ int orc_init(orc_sim *s) {
         s->g[e] = s->g_prev[e] = s->dg[e] = 0.0;
     }
     s->nhist = 0;
+    s->nrhist = 0;
     s->step = 0;
     compute_diag(s, it, rr);
     s->diag.continuity_abs = 0.0;
+    return ORC_OK;
+}
+
+/* earlier positions for the curved path, level j = r^{n-j} (j = 1..levels),
+ * array [levels][n_particles][3]; call after orc_init */
+int orc_set_position_history(orc_sim *s, int levels, const double *r_hist) {
+    if (levels < 0 || levels > 4) return ORC_ERR_ARG;
+    for (int p = 0; p < s->np; p++)
+        for (int j = 1; j <= levels; j++)
+            for (int d = 0; d < 3; d++)
+                s->rhist[15 * p + 3 * (j - 1) + d] = r_hist[((size_t)(j - 1) * s->np + p) * 3 + d];
+    s->nrhist = levels;
     return ORC_OK;
 }
 
@@ -967,6 +983,145 @@ int orc_set_ab_history(orc_sim *s, int levels, const double *a_hist, const doubl
             }
     s->nhist = levels;
     return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Curved path (Sec. III.B, Eq. path; Sec. III.C, Algorithms 1 and 2)    */
+/* ------------------------------------------------------------------ */
+/* With an Adams-Bashforth pusher the position over the step is the Lagrange
+ * polynomial through the newest positions.  Reading of the garbled indices of
+ * Eq. path: the interpolation nodes are t_{n+1}, t_n, ..., t_{n+1-d} and the
+ * values the positions at those times, r^{n+1}, r^n, ..., r^{n+1-d}; the
+ * degree d is the pusher's order (k = 4: five points), lower while the
+ * history fills up.  The step is parameterised by tau in [0, 1]
+ * (t = t_n + tau dt), so node j sits at tau_j = 1 - j. */
+typedef struct {
+    int d;              /* degree: d + 1 points */
+    double pt[6][3];    /* pt[j] = r^{n+1-j} */
+} lpath;
+
+static void lpath_eval(const lpath *L, double tau, double *r, double *dr) {
+    for (int c = 0; c < 3; c++) { r[c] = 0.0; if (dr) dr[c] = 0.0; }
+    for (int j = 0; j <= L->d; j++) {
+        /* l_j(tau) = prod_{m != j} (tau - tau_m) / (tau_j - tau_m) and its derivative */
+        double lj = 1.0, dl = 0.0;
+        for (int m = 0; m <= L->d; m++) {
+            if (m == j) continue;
+            double den = (double)(m - j);          /* tau_j - tau_m = (1-j) - (1-m) */
+            double fac = (tau - (1.0 - m)) / den;
+            dl = dl * fac + lj / den;
+            lj *= fac;
+        }
+        for (int c = 0; c < 3; c++) { r[c] += lj * L->pt[j][c]; if (dr) dr[c] += dl * L->pt[j][c]; }
+    }
+}
+
+static int inside_tet(const orc_mesh *m, int t, const double *r) {
+    double lam[4];
+    orc_lambda(m, t, r, lam);
+    return lam[0] >= 0.0 && lam[1] >= 0.0 && lam[2] >= 0.0 && lam[3] >= 0.0;
+}
+
+/* Gauss-Legendre nodes and weights on [-1, 1] for n = 2..5 (the path
+ * integrand W1(r(tau)) . r'(tau) has degree 2d - 1, so n = max(d, 2)
+ * points integrate it exactly, as Sec. III.C asks) */
+static void gauss_legendre(int n, double *x, double *w) {
+    /* roots of P_n by Newton from the Chebyshev guesses; weights 2/((1-x^2) P_n'(x)^2) */
+    for (int i = 0; i < n; i++) {
+        double z = cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5)), pp = 0.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; k++) { double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k; p0 = p1; p1 = p2; }
+            pp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / pp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    }
+}
+
+/* int_{a}^{b} W1_k(r(tau)) . r'(tau) dtau for the six edges of tet t */
+static void path_w1(const orc_mesh *m, int t, const lpath *L, double a, double b, double *out6) {
+    const int n = L->d > 2 ? L->d : 2;
+    double gx[5], gw[5];
+    gauss_legendre(n, gx, gw);
+    for (int k = 0; k < 6; k++) out6[k] = 0.0;
+    for (int q = 0; q < n; q++) {
+        double tau = 0.5 * (a + b) + 0.5 * (b - a) * gx[q];
+        double r[3], dr[3], lam[4], w[3];
+        lpath_eval(L, tau, r, dr);
+        orc_lambda(m, t, r, lam);
+        for (int k = 0; k < 6; k++) {
+            whitney1(m, t, k, lam, w);
+            out6[k] += 0.5 * (b - a) * gw[q] * dot3(w, dr);
+        }
+    }
+}
+
+/* Algorithm 1 for the curved path, with Algorithm 2's bisection (its loop
+ * condition read as "while |t_s - t_f| > tol", the printed one being
+ * inverted).  In the current cell the remaining path [tau_s, 1] is sampled
+ * at its quadrature points and its end; if all lie in the cell the rest is
+ * integrated there.  Otherwise the first sample outside brackets the exit with
+ * tau_s, bisection narrows the bracket to `tol` (47 halvings for 1e-15), the
+ * piece [tau_s, t_s] is integrated, and the path continues in the neighbour
+ * across the face whose barycentric is most negative at t_f (or ends on the
+ * wall there).  Returns the status; *tend the end cell, *absorbed and the
+ * absorption point when a wall was reached. */
+static int walk_curved(orc_sim *s, int p, int t, const lpath *L, double qw, int *tend, int *absorbed, double *rabs) {
+    orc_mesh *m = s->m;
+    const double tol = 1e-15;
+    const int n = L->d > 2 ? L->d : 2;
+    double gx[5], gw[5];
+    gauss_legendre(n, gx, gw);
+    double ts0 = 0.0;
+    *absorbed = 0;
+    for (int seg = 0; seg < s->cfg.walk_cap; seg++) {
+        /* samples of [ts0, 1] in increasing tau: the quadrature nodes, then the end */
+        double smp[6];
+        int ns = 0;
+        for (int q = n - 1; q >= 0; q--) smp[ns++] = 0.5 * (ts0 + 1.0) + 0.5 * (1.0 - ts0) * gx[q];
+        smp[ns++] = 1.0;
+        double tf = -1.0;
+        for (int q = 0; q < ns; q++) {
+            double r[3];
+            lpath_eval(L, smp[q], r, NULL);
+            if (!inside_tet(m, t, r)) { tf = smp[q]; break; }
+        }
+        double g6[6];
+        if (tf < 0.0) {
+            path_w1(m, t, L, ts0, 1.0, g6);
+            for (int l = 0; l < 6; l++) s->dg[m->tet_edge[6 * t + l]] += qw * g6[l];
+            *tend = t;
+            return ORC_OK;
+        }
+        double tsb = ts0;
+        while (tf - tsb > tol) {
+            double th = 0.5 * (tsb + tf), r[3];
+            lpath_eval(L, th, r, NULL);
+            if (inside_tet(m, t, r)) tsb = th; else tf = th;
+        }
+        path_w1(m, t, L, ts0, tsb, g6);
+        for (int l = 0; l < 6; l++) s->dg[m->tet_edge[6 * t + l]] += qw * g6[l];
+        double rf[3], lam[4];
+        lpath_eval(L, tf, rf, NULL);
+        orc_lambda(m, t, rf, lam);
+        int kmin = 0;
+        for (int k = 1; k < 4; k++) if (lam[k] < lam[kmin]) kmin = k;
+        int nb = m->tet_nbr[4 * t + kmin];
+        if (nb < 0) {
+            lpath_eval(L, tsb, rabs, NULL);
+            *tend = t;
+            *absorbed = 1;
+            return ORC_OK;
+        }
+        t = nb;
+        ts0 = tsb;
+    }
+    snprintf(s->err, sizeof s->err, "particle %d exceeded the walk cap", p);
+    return ORC_ERR_WALK_CAP;
 }
 
 /* One particle: gather at r^n, push, walk the straight path, deposit the W1
@@ -1004,6 +1159,36 @@ static int move_particle(orc_sim *s, int p) {
             Q[d] = r[d] + dt * sv;
         }
         for (int d = 0; d < 3; d++) v[d] = vn[d];
+    }
+    double qw0 = s->q[p] * s->w[p];
+    if (s->cfg.curved_path && s->cfg.pusher != ORC_PUSH_BORIS) {
+        /* the path through r^{n+1}, r^n and the stored earlier positions */
+        int k = s->cfg.pusher;
+        int order = s->nhist + 1 < k ? s->nhist + 1 : k;
+        int d = order < s->nrhist + 1 ? order : s->nrhist + 1;
+        lpath L;
+        L.d = d;
+        for (int c = 0; c < 3; c++) { L.pt[0][c] = Q[c]; L.pt[1][c] = r[c]; }
+        for (int j = 2; j <= d; j++)
+            for (int c = 0; c < 3; c++) L.pt[j][c] = s->rhist[15 * p + 3 * (j - 2) + c];
+        int tend, absorbed;
+        double rabs[3];
+        int rc = walk_curved(s, p, t, &L, qw0, &tend, &absorbed, rabs);
+        if (rc) return rc;
+        /* the earlier positions move one level back; r^n becomes level 0 */
+        memmove(s->rhist + 15 * p + 3, s->rhist + 15 * p, sizeof(double) * 12);
+        for (int c = 0; c < 3; c++) s->rhist[15 * p + c] = r[c];
+        if (absorbed) {
+            double lam[4];
+            orc_lambda(m, tend, rabs, lam);
+            for (int kk = 0; kk < 4; kk++) s->wall[m->tet[4 * tend + kk]] += qw0 * lam[kk];
+            s->alive[p] = 0;
+            memcpy(r, rabs, 24);
+        } else {
+            memcpy(r, Q, 24);
+        }
+        s->tet[p] = tend;
+        return ORC_OK;
     }
     int cap = s->cfg.walk_cap;
     int *tl = malloc(sizeof(int) * cap);
@@ -1068,6 +1253,7 @@ int orc_particle_phase(orc_sim *s) {
         if (rc) return rc;
     }
     if (s->cfg.pusher != ORC_PUSH_BORIS && s->nhist < 4) s->nhist++;
+    if (s->cfg.curved_path && s->nrhist < 4) s->nrhist++;
     deposit_charge(s, s->rho);
     return ORC_OK;
 }

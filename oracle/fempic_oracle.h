@@ -64,6 +64,9 @@ typedef struct {
     int gradient_completion; /* 1: complete the solve on the gradient subspace */
     double completion_tol;   /* completion stops when max|defect| <= this * max|rho+wall| (0: relative init_tol) */
     int current_form;        /* ORC_CURRENT_GBAR, or ORC_CURRENT_POINT (the negative control) */
+    int curved_path;         /* 1 (Adams-Bashforth only): the path over a step is the Lagrange polynomial
+                                through the newest positions (Sec. III.B), walked by Algorithms 1-2 and
+                                integrated by Gauss-Legendre quadrature; 0: the straight segment */
 } orc_config;
 
 /* diagnostics record, all FP64 */
@@ -137,6 +140,9 @@ int orc_inject(orc_sim *s, double q, double mass, double w, int n, const double 
 /* Adams-Bashforth history of the previous `levels` steps (level j = j steps
  * back, j = 1..levels), arrays [levels][n_particles][3]; call after orc_init */
 int orc_set_ab_history(orc_sim *s, int levels, const double *a_hist, const double *v_hist);
+/* earlier positions for the curved path, level j = r^{n-j} (j = 1..levels),
+ * array [levels][n_particles][3]; call after orc_init */
+int orc_set_position_history(orc_sim *s, int levels, const double *r_hist);
 int orc_step(orc_sim *s);
 /* run only the particle phase of one step (gather, push, walk, deposit) with
  * the fields frozen; fills dG and the node charge at the new positions */

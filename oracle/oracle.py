@@ -52,7 +52,7 @@ class _Config(C.Structure):
                 ("cg_tol", C.c_double), ("cg_max_iters", C.c_int), ("init_tol", C.c_double),
                 ("rho_background", C.c_double), ("walk_cap", C.c_int),
                 ("gradient_completion", C.c_int), ("completion_tol", C.c_double),
-                ("current_form", C.c_int)]
+                ("current_form", C.c_int), ("curved_path", C.c_int)]
 
 
 def _load():
@@ -98,6 +98,8 @@ def _load():
     lib.orc_set_background_charge.restype = C.c_int
     lib.orc_set_ab_history.argtypes = [P, C.c_int, dp, dp]
     lib.orc_set_ab_history.restype = C.c_int
+    lib.orc_set_position_history.argtypes = [P, C.c_int, dp]
+    lib.orc_set_position_history.restype = C.c_int
     lib.orc_step.argtypes = [P]
     lib.orc_particle_phase.argtypes = [P]
     lib.orc_n_particles.argtypes = [P]
@@ -282,11 +284,13 @@ class OracleConfig:
     gradient_completion: bool = True
     completion_tol: float = 1e-16
     current: str = "gbar"        # "gbar" (the paper's method) | "point" (negative control)
+    curved_path: bool = False    # Lagrange path through the newest positions (Adams-Bashforth only)
 
     def to_c(self) -> _Config:
         c = _Config()
         c.form = {"we": 0, "mfem": 1, "bd": 2}[self.form]
         c.current_form = {"gbar": 0, "point": 1}[self.current]
+        c.curved_path = int(self.curved_path)
         c.pusher = 0 if self.pusher == "boris" else int(self.pusher[2:])
         c.dt = self.dt
         for i in range(3):
@@ -340,6 +344,10 @@ class OracleSim:
         a = np.ascontiguousarray(a_hist, dtype=np.float64)
         v = np.ascontiguousarray(v_hist, dtype=np.float64)
         self._check(_lib.orc_set_ab_history(self._h, a.shape[0], _dp(a), _dp(v)), "set_ab_history")
+
+    def set_position_history(self, r_hist: np.ndarray):
+        r = np.ascontiguousarray(r_hist, dtype=np.float64)
+        self._check(_lib.orc_set_position_history(self._h, r.shape[0], _dp(r)), "set_position_history")
 
     def step(self, n: int = 1):
         for _ in range(n):

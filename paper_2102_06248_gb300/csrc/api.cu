@@ -287,9 +287,14 @@ int pic_sim_create(const pic_mesh *mesh, const pic_config *cfg, pic_sim **out) {
         cfg->pusher > 5 || (cfg->precision != PIC_PRECISION_PLAIN && cfg->precision != PIC_PRECISION_MIXED) ||
         !(cfg->cg_tol > 0) || cfg->cg_max_iters <= 0 || !(cfg->init_tol > 0) || !(cfg->completion_tol > 0) ||
         cfg->walk_cap <= 0 || cfg->walk_cap > kMaxWalk || cfg->solver_blocks_per_sm < 0 ||
-        (cfg->preconditioner != PIC_PRECOND_JACOBI && cfg->preconditioner != PIC_PRECOND_GNN)) {
-        set_error("pic_sim_create: invalid configuration (dt > 0, form WE/MFEM, pusher 0..5, precision, tolerances, "
-                  "walk_cap 1..63, Jacobi or GNN preconditioner)");
+        (cfg->preconditioner != PIC_PRECOND_JACOBI && cfg->preconditioner != PIC_PRECOND_GNN) ||
+        (cfg->curved_path != 0 && cfg->curved_path != 1)) {
+        set_error("pic_sim_create: invalid configuration (dt > 0, form WE/MFEM/BD, pusher 0..5, precision, tolerances, "
+                  "walk_cap 1..63, Jacobi or GNN preconditioner, curved_path 0/1)");
+        return PIC_ERR_INVALID_ARG;
+    }
+    if (cfg->curved_path && (cfg->pusher < 1 || cfg->precision != PIC_PRECISION_PLAIN)) {
+        set_error("pic_sim_create: the curved path needs an Adams-Bashforth pusher and PLAIN precision");
         return PIC_ERR_INVALID_ARG;
     }
     {
@@ -438,6 +443,7 @@ int pic_sim_init(pic_sim *sim) {
     if ((rc = compute_diagnostics(s)) || (rc = read_control(s))) return rc;
     s->initialised = 1;
     s->nhist = 0;
+    s->nrhist = 0;
     return check_status(s);
 }
 

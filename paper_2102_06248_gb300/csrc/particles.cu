@@ -10,6 +10,8 @@
 #include <cstdio>
 #include <type_traits>
 
+#include <cmath>
+
 #include "sim.h"
 
 namespace fp {
@@ -315,10 +317,12 @@ struct PushArgs {
     const R *sx0, *sx1, *sx2, *sv0, *sv1, *sv2;
     const int *sid;
     const R *sah, *svh;
+    const R *srh;           // earlier positions r^{n-1}, r^{n-2}, ... (curved path), levels*3 arrays of cap
     R *dx0, *dx1, *dx2, *dv0, *dv1, *dv2;
     uint32_t *dkey;
     int *did;
     R *dah, *dvh;
+    R *drh;
     long cap;
     const double *geo;      // FP64 barycentric maps (PLAIN)
     const float *geo32;     // FP32 barycentric maps (MIXED)
@@ -330,6 +334,10 @@ struct PushArgs {
     float qm32[kMaxSpecies], mw32[kMaxSpecies], dt32;   // FP32 copies (MIXED: no FP64 per particle)
     int ab_order, hist_levels;
     double abw[5];
+    // curved path (PLAIN Adams-Bashforth): degree of this step's Lagrange
+    // path (0: straight) and the Gauss-Legendre rule on [-1, 1] of its pieces
+    int path_deg, gl_n;
+    double glx[5], glw[5];
     int walk_cap;
     uint32_t dead_key;
     int nsp;                // species slots per tet in the accumulators (MIXED), 1 for PLAIN
@@ -680,6 +688,148 @@ __device__ __forceinline__ void gather_push(const PushArgs<R, typename std::cond
 }
 
 // ---------------------------------------------------------------------------
+// Curved path (PLAIN Adams-Bashforth, Sec. III.B Eq. path and Sec. III.C):
+// over the step, tau in [0, 1] (t = t_n + tau dt), the position is the
+// polynomial through r^{n+1}, r^n, ..., r^{n+1-d} at tau = 1, 0, ..., 1-d,
+// kept in Newton form on those nodes,
+//   r(tau) = c0 + (tau - 1) (c1 + tau (c2 + (tau + 1) (c3 + ...))),
+// with c the divided differences (node spacing 1), so r(1) = r^{n+1} exactly.
+// The walk follows Algorithms 1 and 2: sample the rest of the path at its
+// quadrature points and end; if one leaves the tet, bisect the bracket to
+// 1e-15, integrate W1 . r' over the piece with the Gauss-Legendre rule, and
+// continue in the neighbour across the most negative barycentric.
+// ---------------------------------------------------------------------------
+struct NewtonPath {
+    int d;
+    double c[6][3];
+};
+
+__device__ __forceinline__ void npath_eval(const NewtonPath &N, double tau, double r[3], double dr[3]) {
+    // nested form: node m is 1 - m
+    double v[3] = {N.c[N.d][0], N.c[N.d][1], N.c[N.d][2]}, dv[3] = {0.0, 0.0, 0.0};
+    for (int m = N.d - 1; m >= 0; m--) {
+        const double f = tau - (1.0 - m);
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            dv[k] = dv[k] * f + v[k];
+            v[k] = N.c[m][k] + f * v[k];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        r[k] = v[k];
+        dr[k] = dv[k];
+    }
+}
+
+__device__ __forceinline__ bool in_tet(const double gp[12], const double r[3]) {
+    double l[4];
+    bary(gp, r[0], r[1], r[2], l);
+    return l[0] >= 0.0 && l[1] >= 0.0 && l[2] >= 0.0 && l[3] >= 0.0;
+}
+
+// sum over the rule of W1 . r' on [ta, tb] in tet T (local edges (i, j), i < j)
+__device__ __forceinline__ void curved_piece(const PushArgs<double, double> &a, const double gp[12], const NewtonPath &N,
+                                             double ta, double tb, double qw, double out[6]) {
+    const double g[4][3] = {{-(gp[3] + gp[6] + gp[9]), -(gp[4] + gp[7] + gp[10]), -(gp[5] + gp[8] + gp[11])},
+                            {gp[3], gp[4], gp[5]}, {gp[6], gp[7], gp[8]}, {gp[9], gp[10], gp[11]}};
+#pragma unroll
+    for (int k = 0; k < 6; k++) out[k] = 0.0;
+    const double h = 0.5 * (tb - ta), mid = 0.5 * (ta + tb);
+    for (int q = 0; q < a.gl_n; q++) {
+        double r[3], dr[3], l[4];
+        npath_eval(N, mid + h * a.glx[q], r, dr);
+        bary(gp, r[0], r[1], r[2], l);
+        double gd[4];
+#pragma unroll
+        for (int v = 0; v < 4; v++) gd[v] = g[v][0] * dr[0] + g[v][1] * dr[1] + g[v][2] * dr[2];
+        const double wq = qw * h * a.glw[q];
+        out[0] += wq * (l[0] * gd[1] - l[1] * gd[0]);
+        out[1] += wq * (l[0] * gd[2] - l[2] * gd[0]);
+        out[2] += wq * (l[0] * gd[3] - l[3] * gd[0]);
+        out[3] += wq * (l[1] * gd[2] - l[2] * gd[1]);
+        out[4] += wq * (l[1] * gd[3] - l[3] * gd[1]);
+        out[5] += wq * (l[2] * gd[3] - l[3] * gd[2]);
+    }
+}
+
+// The walk of one curved path from tet `tet`; the first piece goes to vals
+// (with the end charge if the path ends there), later pieces and a wall charge
+// become records.  Returns the end tet, or -1 when absorbed / past the cap.
+__device__ int walk_curved_plain(const PushArgs<double, double> &a, long i, int tet, const NewtonPath &N, double qw,
+                                 double vals[kNV]) {
+    double gp[12];
+    int T = tet;
+    double ts0 = 0.0;
+    for (int seg = 0; seg < a.walk_cap; seg++) {
+        load_geo(a.geo, T, gp);
+        // samples of [ts0, 1] in increasing tau: the rule's nodes, then the end
+        double tf = -1.0;
+        for (int q = a.gl_n - 1; q >= -1 && tf < 0.0; q--) {
+            const double tq = q >= 0 ? 0.5 * (ts0 + 1.0) + 0.5 * (1.0 - ts0) * a.glx[q] : 1.0;
+            double r[3], dr[3];
+            npath_eval(N, tq, r, dr);
+            if (!in_tet(gp, r)) tf = tq;
+        }
+        double rec[kNV];
+        if (tf < 0.0) {
+            curved_piece(a, gp, N, ts0, 1.0, qw, rec);
+            double lE[4];
+            bary(gp, N.c[0][0], N.c[0][1], N.c[0][2], lE);   // r(1) = r^{n+1}
+#pragma unroll
+            for (int k = 0; k < 4; k++) rec[6 + k] = qw * lE[k];
+            if (seg == 0) {
+#pragma unroll
+                for (int c = 0; c < kNV; c++) vals[c] = rec[c];
+            } else {
+                push_record(a, (uint32_t)T, 0, i, seg, rec);
+            }
+            return T;
+        }
+        double tsb = ts0;
+        while (tf - tsb > 1e-15) {
+            const double th = 0.5 * (tsb + tf);
+            double r[3], dr[3];
+            npath_eval(N, th, r, dr);
+            if (in_tet(gp, r)) tsb = th;
+            else tf = th;
+        }
+        curved_piece(a, gp, N, ts0, tsb, qw, rec);
+#pragma unroll
+        for (int k = 0; k < 4; k++) rec[6 + k] = 0.0;
+        if (seg == 0) {
+#pragma unroll
+            for (int c = 0; c < kNV; c++) vals[c] = rec[c];
+        } else {
+            push_record(a, (uint32_t)T, 0, i, seg, rec);
+        }
+        double r[3], dr[3], l[4];
+        npath_eval(N, tf, r, dr);
+        bary(gp, r[0], r[1], r[2], l);
+        int kmin = 0;
+#pragma unroll
+        for (int k = 1; k < 4; k++)
+            if (l[k] < l[kmin]) kmin = k;
+        const int nb = (&a.tnbr[T].x)[kmin];
+        if (nb < 0) {
+            npath_eval(N, tsb, r, dr);
+            bary(gp, r[0], r[1], r[2], l);
+            double wrec[kNV];
+#pragma unroll
+            for (int k = 0; k < 6; k++) wrec[k] = 0.0;
+#pragma unroll
+            for (int k = 0; k < 4; k++) wrec[6 + k] = qw * l[k];
+            push_record(a, (uint32_t)T, 1, i, kMaxWalk, wrec);
+            return -1;
+        }
+        T = nb;
+        ts0 = tsb;
+    }
+    atomicOr(a.status, (uint32_t)ST_WALK_CAP);
+    return -1;
+}
+
+// ---------------------------------------------------------------------------
 // PLAIN: FP64 state, FP64 barycentrics, FP64 deposit
 // ---------------------------------------------------------------------------
 template <int MODE>   // 0: Boris, 1: Adams-Bashforth, 2: charge only
@@ -704,8 +854,55 @@ __global__ void __launch_bounds__(kPushBlock) k_push_plain(const PushArgs<double
         double Q[3], Vn[3];
         gather_push<double, MODE>(a, a.coef + 10 * (size_t)tet, P, V, P[0] - gp[0], P[1] - gp[1], P[2] - gp[2], spc,
                                   src, i, Q, Vn);
-        // walk the straight path P -> Q (Algorithm 1) with the exact deposit
         const double qw = a.sp.qw[spc];
+        if (MODE == 1 && a.path_deg > 1) {
+            // the Lagrange path through r^{n+1}, r^n and the earlier positions:
+            // divided differences on the nodes 1, 0, -1, ... (spacing 1)
+            NewtonPath N;
+            N.d = a.path_deg;
+            double pts[6][3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                pts[0][k] = Q[k];
+                pts[1][k] = P[k];
+            }
+            for (int j = 2; j <= N.d; j++)
+#pragma unroll
+                for (int k = 0; k < 3; k++) pts[j][k] = a.srh[((size_t)(j - 2) * 3 + k) * a.cap + src];
+            for (int j = 0; j <= N.d; j++)
+#pragma unroll
+                for (int k = 0; k < 3; k++) N.c[j][k] = pts[j][k];
+            // c_j = f[tau_0, ..., tau_j]; nodes decrease by 1, so each level
+            // divides the difference of neighbours by -(level)
+            for (int lev = 1; lev <= N.d; lev++)
+                for (int j = N.d; j >= lev; j--)
+#pragma unroll
+                    for (int k = 0; k < 3; k++) N.c[j][k] = (N.c[j][k] - N.c[j - 1][k]) / (double)(-lev);
+            // earlier positions move one level back; r^n becomes level 0
+            for (int j = a.hist_levels - 1; j >= 1; j--)
+#pragma unroll
+                for (int k = 0; k < 3; k++)
+                    a.drh[((size_t)j * 3 + k) * a.cap + i] = a.srh[((size_t)(j - 1) * 3 + k) * a.cap + src];
+#pragma unroll
+            for (int k = 0; k < 3; k++) a.drh[(size_t)k * a.cap + i] = P[k];
+            const int endT = walk_curved_plain(a, i, tet, N, qw, vals);
+            const bool absorbed = endT < 0;
+            a.dx0[i] = Q[0];
+            a.dx1[i] = Q[1];
+            a.dx2[i] = Q[2];
+            a.dv0[i] = Vn[0];
+            a.dv1[i] = Vn[1];
+            a.dv2[i] = Vn[2];
+            a.did[i] = a.sid[src];
+            a.dkey[i] = absorbed ? a.dead_key : (((uint32_t)endT << 2) | (uint32_t)spc);
+            if (!absorbed) {
+                alive_out = 1;
+                ke = 0.5 * a.sp.mw[spc] * (Vn[0] * Vn[0] + Vn[1] * Vn[1] + Vn[2] * Vn[2]);
+                if (!(ke == ke) || !(Q[0] == Q[0])) atomicOr(a.status, (uint32_t)ST_NAN);
+            }
+            rkey = (uint32_t)tet;
+        } else {
+        // walk the straight path P -> Q (Algorithm 1) with the exact deposit
         double lS[4], lE[4];
         bary(gp, P[0], P[1], P[2], lS);
         int T = tet;
@@ -806,6 +1003,7 @@ __global__ void __launch_bounds__(kPushBlock) k_push_plain(const PushArgs<double
             if (!(ke == ke) || !(Q[0] == Q[0])) atomicOr(a.status, (uint32_t)ST_NAN);
         }
         rkey = (uint32_t)tet;
+        }
     }
     reduce_block<double, double, double>(a, rkey, vals, ke, alive_out, n_alive);
 }
@@ -1395,6 +1593,7 @@ int particles_alloc(Sim *s, size_t cap) {
         if (s->hist_levels > 0) {
             if ((rc = k.ah.alloc(cap * rs * 3 * s->hist_levels)) || (rc = k.vh.alloc(cap * rs * 3 * s->hist_levels)))
                 return rc;
+            if (s->cfg.curved_path && (rc = k.rh.alloc(cap * rs * 3 * s->hist_levels))) return rc;
         }
     }
     if ((rc = s->skey.alloc(cap)) || (rc = s->sval.alloc(cap)) || (rc = s->tkey.alloc(cap)) ||
@@ -1572,6 +1771,8 @@ static void fill_push_args(Sim *s, PushArgs<R, V> &a) {
     a.sid = src.id.p;
     a.sah = (const R *)src.ah.p;
     a.svh = (const R *)src.vh.p;
+    a.srh = (const R *)src.rh.p;
+    a.drh = (R *)dst.rh.p;
     a.dx0 = (R *)dst.x[0].p;
     a.dx1 = (R *)dst.x[1].p;
     a.dx2 = (R *)dst.x[2].p;
@@ -1604,6 +1805,34 @@ static void fill_push_args(Sim *s, PushArgs<R, V> &a) {
     a.ab_order = s->ab ? std::min(s->nhist + 1, s->ab) : 1;
     a.hist_levels = s->hist_levels;
     for (int k = 0; k < 5; k++) a.abw[k] = W[a.ab_order - 1][k];
+    // curved path: degree = the order in use, limited by the stored positions;
+    // Gauss-Legendre on [-1, 1] in closed form, nodes in decreasing order
+    a.path_deg = (s->cfg.curved_path && s->ab) ? std::min(a.ab_order, s->nrhist + 1) : 0;
+    a.gl_n = std::max(a.path_deg, 2);
+    {
+        double x[5] = {0, 0, 0, 0, 0}, w[5] = {0, 0, 0, 0, 0};
+        if (a.gl_n == 2) {
+            x[0] = 1.0 / std::sqrt(3.0); x[1] = -x[0];
+            w[0] = w[1] = 1.0;
+        } else if (a.gl_n == 3) {
+            x[0] = std::sqrt(0.6); x[1] = 0.0; x[2] = -x[0];
+            w[0] = w[2] = 5.0 / 9.0; w[1] = 8.0 / 9.0;
+        } else if (a.gl_n == 4) {
+            const double u = 2.0 / 7.0 * std::sqrt(1.2);
+            x[0] = std::sqrt(3.0 / 7.0 + u); x[1] = std::sqrt(3.0 / 7.0 - u); x[2] = -x[1]; x[3] = -x[0];
+            w[0] = w[3] = (18.0 - std::sqrt(30.0)) / 36.0; w[1] = w[2] = (18.0 + std::sqrt(30.0)) / 36.0;
+        } else {
+            const double u = 2.0 * std::sqrt(10.0 / 7.0);
+            x[0] = std::sqrt(5.0 + u) / 3.0; x[1] = std::sqrt(5.0 - u) / 3.0; x[2] = 0.0; x[3] = -x[1]; x[4] = -x[0];
+            w[0] = w[4] = (322.0 - 13.0 * std::sqrt(70.0)) / 900.0;
+            w[1] = w[3] = (322.0 + 13.0 * std::sqrt(70.0)) / 900.0;
+            w[2] = 128.0 / 225.0;
+        }
+        for (int k = 0; k < 5; k++) {
+            a.glx[k] = x[k];
+            a.glw[k] = w[k];
+        }
+    }
     a.walk_cap = std::min(s->cfg.walk_cap, kMaxWalk);
     a.dead_key = (uint32_t)m->n_tets << 2;
     a.nsp = s->nsp;
@@ -1712,6 +1941,7 @@ int particle_push(Sim *s, int charge_only) {
         s->cur = 1 - s->cur;
         if (!s->batch_mode) s->n_total = s->hctl->n_alive;
         if (!charge_only && s->ab && s->nhist < s->hist_levels) s->nhist++;
+        if (!charge_only && s->cfg.curved_path && s->nrhist < s->hist_levels) s->nrhist++;
     }
     return PIC_OK;
 }

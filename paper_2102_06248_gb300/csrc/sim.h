@@ -125,6 +125,7 @@ struct PartBank {
     DevBuf<uint32_t> key;
     DevBuf<int> id;
     DevBuf<unsigned char> ah, vh;   // AB history, levels*3 component arrays of cap entries
+    DevBuf<unsigned char> rh;       // earlier positions for the curved path, levels*3 arrays of cap entries
 };
 
 // Reusable radix-sort workspace
@@ -150,6 +151,7 @@ struct Sim {
     int ab = 0;               // Adams-Bashforth order (0 = Boris)
     int hist_levels = 0;      // ab - 1
     int nhist = 0;            // history levels filled (order ramp)
+    int nrhist = 0;           // position levels filled (curved path)
     int initialised = 0;
     long step = 0;
     std::vector<double> bg_nodes;   // static node charges set by the caller (added to the uniform background)

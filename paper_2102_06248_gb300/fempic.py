@@ -46,7 +46,7 @@ class pic_config(C.Structure):
                 ("init_tol", C.c_double), ("completion_tol", C.c_double), ("walk_cap", C.c_int32),
                 ("solver_blocks_per_sm", C.c_int32),
                 ("max_species", C.c_int32), ("profile", C.c_int32), ("stream", C.c_void_p),
-                ("barrier_spin_limit", C.c_int32)]
+                ("barrier_spin_limit", C.c_int32), ("curved_path", C.c_int32)]
 
 
 class pic_gnn_train_cfg(C.Structure):
@@ -221,7 +221,7 @@ class Sim:
                  precision: str = "plain", b0: Sequence[float] = (0.0, 0.0, 0.0), rho_background: float = 0.0,
                  cg_tol: float = 1e-10, init_tol: float = 1e-14, cg_max_iters: int = 10000,
                  walk_cap: int = 63, stream=None, profile: bool = False, solver_blocks_per_sm: int = 0,
-                 preconditioner: str = "jacobi", barrier_spin_limit: int = 0):
+                 preconditioner: str = "jacobi", barrier_spin_limit: int = 0, curved_path: bool = False):
         lib = load()
         self.mesh = mesh
         c = default_config()
@@ -240,6 +240,7 @@ class Sim:
         c.preconditioner = PRECONDITIONERS[preconditioner]
         c.profile = int(profile)
         c.barrier_spin_limit = int(barrier_spin_limit)
+        c.curved_path = int(curved_path)
         if stream is not None:
             c.stream = C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
         self.config = c
