@@ -335,7 +335,8 @@ struct PushArgs {
     int ab_order, hist_levels;
     double abw[5];
     // curved path (PLAIN Adams-Bashforth): degree of this step's Lagrange
-    // path (0: straight) and the Gauss-Legendre rule on [-1, 1] of its pieces
+    // path (0: straight segments, no curved walk) and the Gauss-Legendre rule
+    // on [-1, 1] of its pieces
     int path_deg, gl_n;
     double glx[5], glw[5];
     int walk_cap;
@@ -599,6 +600,80 @@ __device__ __forceinline__ void reduce_block(const PushArgs<R, V> &a, uint32_t r
     }
 }
 
+// MIXED deposit reduction of the first pieces, per warp: a warp-segmented
+// inclusive scan by key; a run that lies inside the warp is stored directly
+// (its sole writer), and the warp's first and last runs, when they continue
+// into the neighbouring warps, go to the warp's two carry slots, which
+// k_fixup adds in warp order.  No block barrier: the barrier of the block
+// reduction and its serial merge were a fifth of the push's instructions and
+// stalls.  Live count and kinetic energy are one value per warp.
+__device__ __forceinline__ void reduce_warp_mixed(const PushArgs<float, long long> &a, long i, uint32_t rkey,
+                                                  const long long vals[kNV], float ke, int alive_out, int n_alive) {
+    const int lane = threadIdx.x & 31;
+    const long wid = i >> 5;
+    {
+        const unsigned ball = __ballot_sync(0xFFFFFFFFu, alive_out);
+        float k2 = ke;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) k2 += __shfl_down_sync(0xFFFFFFFFu, k2, o);
+        if (lane == 0) {
+            if (ball) atomicAdd(a.n_alive_next, __popc(ball));
+            a.ke_part[wid] = (double)k2;
+        }
+    }
+    // the four node charges are integers in [0, 2^24]; a run of at most 32
+    // sums below 2^29, so two share one 64-bit lane: 8 scanned channels
+    long long w[8];
+#pragma unroll
+    for (int c = 0; c < 6; c++) w[c] = vals[c];
+    w[6] = vals[6] | (vals[7] << 32);
+    w[7] = vals[8] | (vals[9] << 32);
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t ko = __shfl_up_sync(0xFFFFFFFFu, rkey, off);
+        const bool take = lane >= off && ko == rkey;
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            const long long vo = shfl_up_v(w[c], off);
+            if (take) w[c] += vo;
+        }
+    }
+    const uint32_t knext = __shfl_down_sync(0xFFFFFFFFu, rkey, 1);
+    const uint32_t kfirst = __shfl_sync(0xFFFFFFFFu, rkey, 0);
+    // keys of the particles just before and just after this warp
+    const long w0 = wid << 5;
+    uint32_t kedge = kInvalid;
+    if (lane == 0 && w0 > 0 && w0 - 1 < n_alive) kedge = acc_index<long long>(a.skey[w0 - 1], a.nsp);
+    if (lane == 31 && w0 + 32 < n_alive) kedge = acc_index<long long>(a.skey[w0 + 32], a.nsp);
+    const uint32_t prevk = __shfl_sync(0xFFFFFFFFu, kedge, 0), nextk = __shfl_sync(0xFFFFFFFFu, kedge, 31);
+    if (lane == 0) {
+        a.bcar_key[2 * wid] = kInvalid;
+        a.bcar_key[2 * wid + 1] = kInvalid;
+    }
+    __syncwarp();
+    if ((lane == 31 || knext != rkey) && rkey != kInvalid) {
+        const bool first = rkey == kfirst;
+        const bool touches = (first && prevk == rkey) || (lane == 31 && nextk == rkey);
+        long long out[kNV];
+#pragma unroll
+        for (int c = 0; c < 6; c++) out[c] = w[c];
+        out[6] = w[6] & 0xFFFFFFFFll;
+        out[7] = (long long)((unsigned long long)w[6] >> 32);
+        out[8] = w[7] & 0xFFFFFFFFll;
+        out[9] = (long long)((unsigned long long)w[7] >> 32);
+        long long *dst;
+        if (touches) {
+            const int slot = first ? 0 : 1;
+            a.bcar_key[2 * wid + slot] = rkey;
+            dst = a.bcar + (2 * (size_t)wid + slot) * kNV;
+        } else {
+            dst = a.tacc + (size_t)rkey * kNV;
+        }
+#pragma unroll
+        for (int c = 0; c < kNV; c++) dst[c] = out[c];
+    }
+}
+
 // gather + push shared by both precisions; returns the new position and velocity
 template <typename R, int MODE>
 __device__ __forceinline__ void gather_push(const PushArgs<R, typename std::conditional<std::is_same<R, double>::value, double, long long>::type> &a,
@@ -855,7 +930,7 @@ __global__ void __launch_bounds__(kPushBlock) k_push_plain(const PushArgs<double
         gather_push<double, MODE>(a, a.coef + 10 * (size_t)tet, P, V, P[0] - gp[0], P[1] - gp[1], P[2] - gp[2], spc,
                                   src, i, Q, Vn);
         const double qw = a.sp.qw[spc];
-        if (MODE == 1 && a.path_deg > 1) {
+        if (MODE == 1 && a.path_deg > 0) {
             // the Lagrange path through r^{n+1}, r^n and the earlier positions:
             // divided differences on the nodes 1, 0, -1, ... (spacing 1)
             NewtonPath N;
@@ -1128,7 +1203,7 @@ __device__ __forceinline__ int walk_rest_mixed(const PushArgs<float, long long> 
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kPushBlock, 4) k_push_mixed(const PushArgs<float, long long> a) {
+__global__ void __launch_bounds__(kPushBlock, 5) k_push_mixed(const PushArgs<float, long long> a) {
     const long i = (long)blockIdx.x * kPushBlock + threadIdx.x;
     const int n_alive = *a.d_n_alive;
     const bool active = i < n_alive;
@@ -1219,16 +1294,17 @@ __global__ void __launch_bounds__(kPushBlock, 4) k_push_mixed(const PushArgs<flo
         }
         rkey = (uint32_t)(tet * a.nsp + spc);
     }
-    reduce_block<float, long long, float>(a, rkey, vals, ke, alive_out, n_alive);
+    reduce_warp_mixed(a, i, rkey, vals, ke, alive_out, n_alive);
 }
 
 // spanning runs: a head piece (the last run of a block, or a block's first run
 // that does not continue from the previous block) adds the following blocks'
 // first-run pieces of the same key in block order
 template <typename V>
-__global__ void __launch_bounds__(256) k_fixup(int n_blocks, int nsp, const uint32_t *__restrict__ skey,
+__global__ void __launch_bounds__(256) k_fixup(int n_blocks, int unit, int nsp, const uint32_t *__restrict__ skey,
                                                const int *d_n_alive, const uint32_t *__restrict__ bkey,
                                                const V *__restrict__ bval, V *__restrict__ tacc) {
+    // units of `unit` particles (a block in PLAIN, a warp in MIXED), two carry slots each
     const long j = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= 2L * n_blocks) return;
     const uint32_t k = bkey[j];
@@ -1236,7 +1312,7 @@ __global__ void __launch_bounds__(256) k_fixup(int n_blocks, int nsp, const uint
     const long blk = j >> 1;
     const int slot = (int)(j & 1);
     if (slot == 0) {
-        const long p = blk * kPushBlock - 1;
+        const long p = blk * unit - 1;
         const int n_alive = *d_n_alive;
         if (blk > 0 && p < n_alive && acc_index<V>(skey[p], nsp) == k) return;
     }
@@ -1602,8 +1678,10 @@ int particles_alloc(Sim *s, size_t cap) {
     if ((rc = overflow_alloc(s, (int)std::min<size_t>(std::max<size_t>(cap / 8, 65536), (size_t)1 << 30))))
         return rc;
     const size_t blocks = std::max<size_t>(1, (cap + kPushBlock - 1) / kPushBlock);
-    if ((rc = s->bcar.alloc(2 * blocks * kNV)) || (rc = s->bcar_key.alloc(2 * blocks)) ||
-        (rc = s->ke_part.alloc(blocks)))
+    // carries and energy partials: per warp (MIXED), which also covers per block
+    const size_t units = blocks * (kPushBlock / 32);
+    if ((rc = s->bcar.alloc(2 * units * kNV)) || (rc = s->bcar_key.alloc(2 * units)) ||
+        (rc = s->ke_part.alloc(units)))
         return rc;
     s->push_blocks_cap = blocks;
     s->cap = cap;
@@ -1877,9 +1955,12 @@ static int launch_push(Sim *s, int mode) {
     prof_end(s, PH_PUSH);
     prof_begin(s, PH_DEPOSIT);
     FP_CUDA(cudaGetLastError());
-    // runs that span blocks are added in block order
-    { k_fixup<V><<<(2 * blocks + 255) / 256, 256, 0, s->stream>>>(blocks, s->nsp, s->skey.p, &dc->n_alive, s->bcar_key.p, (const V *)s->bcar.p, (V *)s->tacc.p); note_launch(); }
-    s->n_ke_parts = blocks;
+    // runs that span reduction units (blocks in PLAIN, warps in MIXED) are
+    // added in unit order
+    const int unit = std::is_same<R, double>::value ? kPushBlock : 32;
+    const int units = std::is_same<R, double>::value ? blocks : blocks * (kPushBlock / 32);
+    { k_fixup<V><<<(2 * units + 255) / 256, 256, 0, s->stream>>>(units, unit, s->nsp, s->skey.p, &dc->n_alive, s->bcar_key.p, (const V *)s->bcar.p, (V *)s->tacc.p); note_launch(); }
+    s->n_ke_parts = units;
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
 }
@@ -1992,8 +2073,10 @@ static int particles_grow(Sim *s, size_t cap, size_t keep) {
         (rc = s->tval.alloc(cap)))
         return rc;
     const size_t blocks = std::max<size_t>(1, (cap + kPushBlock - 1) / kPushBlock);
-    if ((rc = s->bcar.alloc(2 * blocks * kNV)) || (rc = s->bcar_key.alloc(2 * blocks)) ||
-        (rc = s->ke_part.alloc(blocks)))
+    // carries and energy partials: per warp (MIXED), which also covers per block
+    const size_t units = blocks * (kPushBlock / 32);
+    if ((rc = s->bcar.alloc(2 * units * kNV)) || (rc = s->bcar_key.alloc(2 * units)) ||
+        (rc = s->ke_part.alloc(units)))
         return rc;
     s->push_blocks_cap = blocks;
     s->cap = cap;

@@ -218,7 +218,7 @@ struct Sim {
     DevBuf<Control> dctl;
     Control *hctl = nullptr;
     DevBuf<double> diag_part;       // per-block partials of the diagnostic reductions
-    int n_ke_parts = 0;             // kinetic-energy partials of the last push (one per block)
+    int n_ke_parts = 0;             // kinetic-energy partials of the last push (per block PLAIN, per warp MIXED)
     long long cg_iters_sum = 0;     // PCG iterations over all steps (Newmark, completion)
     long long lap_iters_sum = 0;
     GnnState gnn;
