@@ -401,6 +401,164 @@ def batched_leg(F, torch, args):
             "solver_blocks_per_sm": info["solver_blocks_per_sm"], "tune_ms_2_3_4": info["tune_ms"]}
 
 
+def larmor_leg(F, torch, args):
+    """Single electron gyrating in uniform B0 (0.05 T, v_perp = 0.05c), 20^3
+    Kuhn-cell box of side 10 r_L, Maxwell-solver Newmark form, dt = T_c/64
+    (Sec. IV.A analogue): FP64 and MIXED precision on the GPU, orbit radius
+    about the fixed guiding centre and accumulated phase against the closed
+    forms of the continuous orbit (r_L, w_c t) and of the Boris map (radius
+    r_L sqrt(1 + (w_c dt/2)^2), phase 2 atan(w_c dt/2) per step)."""
+    wl = W.larmor_orbit_box(n_cells=args.larmor_cells, steps=args.larmor_steps)
+    wc = abs(W.Q_E) * wl.b0[2] / W.M_E
+    vperp = 0.05 * W.C0
+    r_l = vperp / wc
+    h = wl.mesh.h
+    centre = np.array([0.5 * wl.mesh.size[0], 0.5 * wl.mesh.size[1] + 0.137 * h])
+    th_b = 2.0 * math.atan(0.5 * wc * wl.dt)
+    r_boris = r_l * math.sqrt(1.0 + (0.5 * wc * wl.dt) ** 2)
+    out = {"workload": f"larmor_orbit {args.larmor_cells}^3 Kuhn cells, side 10 r_L, 1 e-, B0=0.05 T, "
+                       f"v_perp=0.05c, MFEM Newmark, Boris, dt=T_c/64", "steps": args.larmor_steps,
+           "r_L_m": r_l, "boris_radius_closed_form_m": r_boris, "boris_phase_per_step": th_b}
+    for prec in ("plain", "mixed"):
+        sim = F.sim_from_workload(wl, wl.dt, precision=prec)
+        x0, _, _, _ = sim.particles()
+        ph0 = math.atan2(x0[0, 1] - centre[1], x0[0, 0] - centre[0])
+        rads, phase, prev = [], 0.0, ph0
+        t0 = time.perf_counter()
+        for k in range(args.larmor_steps):
+            sim.step()
+            x, _, _, _ = sim.particles()
+            dx, dy = x[0, 0] - centre[0], x[0, 1] - centre[1]
+            rads.append(math.hypot(dx, dy))
+            ph = math.atan2(dy, dx)
+            d = ph - prev
+            d -= 2.0 * math.pi * round(d / (2.0 * math.pi))
+            phase += d
+            prev = ph
+        el = time.perf_counter() - t0
+        n = args.larmor_steps
+        # an electron (q < 0) in B0 z turns counter-clockwise: the phase grows
+        r_mean = float(np.mean(rads))
+        out[prec] = {"radius_mean_m": r_mean,
+                     "radius_rel_err_vs_r_L": r_mean / r_l - 1.0,
+                     "radius_rel_err_vs_boris": r_mean / r_boris - 1.0,
+                     "radius_rel_spread": float((np.max(rads) - np.min(rads)) / r_l),
+                     "phase_err_rad_vs_wc_t": phase - wc * wl.dt * n,
+                     "phase_err_rad_vs_boris": phase - th_b * n,
+                     "seconds": el}
+        del sim
+    out["mixed_minus_plain_radius_rel"] = out["mixed"]["radius_mean_m"] / out["plain"]["radius_mean_m"] - 1.0
+    out["mixed_minus_plain_phase_rad"] = out["mixed"]["phase_err_rad_vs_wc_t"] - out["plain"]["phase_err_rad_vs_wc_t"]
+    return out
+
+
+def pusher_sweep_leg(F, args):
+    """Sec. IV.A, Table I: the cyclotron orbit (B = 6.822756e-5 T, v0 = 3e6 m/s)
+    in frozen fields on the GPU for Boris and Adams-Bashforth orders 1-5 at
+    dt = T_c/N, with the exact start-up history; the paper's error
+    ||r - r_a||_2 / ||r_a||_2 over one period, and its log-log slope."""
+    with open(os.path.join(ROOT, "tests", "golden", "table1_cyclotron.json")) as f:
+        tab = json.load(f)
+    q, mass, bz = tab["q_C"], tab["m_kg"], tab["B_z_T"]
+    v0 = np.array(tab["v0_m_per_s"])
+    r0 = np.array(tab["r0_m"])
+    wc = abs(q) * bz / mass
+    t_c = 2.0 * math.pi / wc
+    r_l = np.linalg.norm(v0) / wc
+    cx, cy = r0[0] - r_l, r0[1]
+
+    def exact(t):
+        ph = wc * t
+        return (np.array([cx + r_l * math.cos(ph), cy + r_l * math.sin(ph), 0.0]),
+                np.array([-r_l * wc * math.sin(ph), r_l * wc * math.cos(ph), 0.0]))
+    box = W.kuhn_box((4, 4, 4), (1.0, 1.0, 1.0))
+    xyz = box.xyz.copy()
+    xyz[:, 2] -= 0.5
+    mesh = F.Mesh(xyz, box.tets)
+    xs, tet = W.place_in_box(box, (r0 + np.array([0, 0, 0.5]))[None, :])
+    xs = xs - np.array([0, 0, 0.5])
+    out = {"workload": "Table I cyclotron (Sec. IV.A), frozen uniform B, one period", "errors": {}, "slopes": {}}
+    ns = (128, 256, 512)
+    for pusher in ("boris", "ab1", "ab2", "ab3", "ab4", "ab5"):
+        errs = []
+        for nsteps in ns:
+            dt = t_c / nsteps
+            sim = F.Sim(mesh, dt, pusher=pusher, b0=(0, 0, bz))
+            if pusher == "boris":
+                # Boris takes v^{-1/2}: the exact velocity half a step back
+                _, vh = exact(-0.5 * dt)
+                sim.particles_load(0, q, mass, 1.0, xs, vh[None, :], tet)
+            else:
+                sim.particles_load(0, q, mass, 1.0, xs, v0[None, :], tet)
+            sim.init()
+            sim.set_field("E", np.zeros(mesh.n_edges))
+            sim.set_field("E_PREV", np.zeros(mesh.n_edges))
+            order = 0 if pusher == "boris" else int(pusher[2:])
+            if order > 1:
+                ah, vh_ = [], []
+                for j in range(1, order):
+                    _, vj = exact(-j * dt)
+                    ah.append((q / mass) * np.cross(vj, [0, 0, bz])[None, :])
+                    vh_.append(vj[None, :])
+                sim.set_ab_history(np.array(ah), np.array(vh_))
+            num = den = 0.0
+            for k in range(1, nsteps + 1):
+                sim.particle_phase()
+                x, _, _, _ = sim.particles()
+                ra, _ = exact(k * dt)
+                num += float(np.sum((x[0] - ra) ** 2))
+                den += float(np.sum(ra ** 2))
+            errs.append(math.sqrt(num / den))
+            del sim
+        out["errors"][pusher] = {f"T_c/{n}": e for n, e in zip(ns, errs)}
+        out["slopes"][pusher] = math.log(errs[0] / errs[-1]) / math.log(ns[-1] / ns[0])
+    return out
+
+
+def mixed_error_leg(F, args):
+    """MIXED precision against the FP64 oracle, per result, on reduced copies
+    of the benchmark workloads (10 steps, Newmark solves at 1e-13 on both
+    sides): the plasma ball at 16^3 cells with 2 x 65,536 particles and the
+    electron beam at 8 x 8 x 32 cells with 20,000 electrons in flight.
+    Errors are max |gpu - oracle| / max |oracle| per field; positions against
+    the box side, velocities against the species' largest speed."""
+    from oracle.oracle import from_workload
+    tab = dt_table()
+    cases = []
+    wl = W.plasma_ball(n_cells=16, n_per_species=65536, seed=41)
+    cases.append(("plasma_ball 16^3, 2 x 65536 e-/p+", wl,
+                   4.0 * tab["kuhn_lattice_16^3_jitter0.2"]["kappa"] * wl.mesh.h / W.C0))
+    wb = W.electron_beam(cells=(8, 8, 32), h=1.25e-3, n_inflight=20000, seed=1003)
+    cases.append(("electron_beam 8x8x32, 20000 e-", wb, 4.0 * tab["kuhn_lattice_16^3"]["kappa"] * wb.mesh.h / W.C0))
+    out = {}
+    for name, w, dt in cases:
+        o = from_workload(w, dt, cg_tol=1e-13)
+        g = F.sim_from_workload(w, dt, precision="mixed", cg_tol=1e-13)
+        worst = {}
+        for _ in range(10):
+            o.step()
+            g.step()
+            for f in ("E", "B", "G", "RHO", "WALL"):
+                b = o.field(f)
+                sc = max(np.abs(b).max(), 1e-300)
+                worst[f] = max(worst.get(f, 0.0), float(np.abs(g.field(f) - b).max() / sc))
+        gx, gv, gt, gid = g.particles()
+        ox, ov, ot, alive = o.particles()
+        ids = np.where(alive)[0]
+        common = np.intersect1d(gid, ids)
+        gi = np.searchsorted(gid, common)
+        worst["x_rel_box"] = float(np.abs(gx[gi] - ox[common]).max() / max(w.mesh.size))
+        worst["v_rel"] = float(np.abs(gv[gi] - ov[common]).max() / np.abs(ov).max())
+        worst["tet_agree_frac"] = float(np.mean(gt[gi] == ot[common]))
+        worst["alive_gpu_oracle"] = [int(len(gid)), int(len(ids))]
+        d = g.diag()
+        worst["continuity_rel"] = d["continuity_abs"] / d["rho_max"]
+        worst["gauss_rel"] = d["gauss_abs"] / d["rho_max"]
+        out[name] = worst
+        del o, g
+    return out
+
+
 def time_gpu(F, wl, dt, precision, steps, warmup, stream, dist, device, torch, profile=True):
     sim = F.sim_from_workload(wl, dt, precision=precision, stream=stream, profile=profile)
     for _ in range(warmup):
@@ -582,6 +740,15 @@ def gpu_arm(args):
     if not args.skip_batched:
         batched = batched_leg(F, torch, args)
 
+    # ---- single electron (config 2), pusher sweep (Table I), MIXED vs oracle ----
+    larmor = sweep = mixed_err = None
+    if rank == 0 and not args.skip_larmor:
+        larmor = larmor_leg(F, torch, args)
+    if rank == 0 and not args.skip_sweep:
+        sweep = pusher_sweep_leg(F, args)
+    if rank == 0 and not args.skip_mixed_error:
+        mixed_err = mixed_error_leg(F, args)
+
     # ---- CPU baseline: the oracle on a bounded, proportionally scaled sample ----
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -620,6 +787,9 @@ def gpu_arm(args):
             "gnn": gnn,
             "beam": beam,
             "batched": batched,
+            "larmor": larmor,
+            "pusher_sweep": sweep,
+            "mixed_vs_oracle": mixed_err,
         }
         print(json.dumps(line))
     if dist is not None:
@@ -705,6 +875,11 @@ def main():
     ap.add_argument("--gnn-steps", type=int, default=3)
     ap.add_argument("--batch-runs", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=60)
+    ap.add_argument("--skip-larmor", action="store_true", help="do not run the single-electron leg")
+    ap.add_argument("--larmor-cells", type=int, default=20)
+    ap.add_argument("--larmor-steps", type=int, default=2000)
+    ap.add_argument("--skip-sweep", action="store_true", help="do not run the Table I pusher sweep")
+    ap.add_argument("--skip-mixed-error", action="store_true", help="do not compare MIXED with the oracle")
     args = ap.parse_args()
     global CLOCK_LOG
     CLOCK_LOG = args.clock_log

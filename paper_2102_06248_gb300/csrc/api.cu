@@ -325,7 +325,7 @@ int pic_sim_create(const pic_mesh *mesh, const pic_config *cfg, pic_sim **out) {
     }
     std::memset(hc, 0, sizeof(Control));
     s->hctl = hc;
-    if ((rc = s->dctl.alloc(1)) || (rc = solver_alloc(s)) || (rc = s->coef.alloc((s->mixed ? 12 : 10) * (size_t)m->n_tets * s->rsize)) ||
+    if ((rc = s->dctl.alloc(1)) || (rc = solver_alloc(s)) || (rc = s->coef.alloc(10 * (size_t)m->n_tets * s->rsize)) ||
         (rc = s->tacc.alloc((size_t)kNV * m->n_tets)) || (rc = s->wacc.alloc(4 * (size_t)m->n_tets))) {
         pic_sim_destroy(h);
         return rc;

@@ -280,10 +280,7 @@ __global__ void __launch_bounds__(256) k_coefficients(int nt, const R *__restric
         if (k == 0) continue;
         for (int i = 0; i < 3; i++) B0[i] += Dk * bv[k] * (R)(x0[i] - xyz[3 * (size_t)nid[k] + i]);
     }
-    // FP64: 10 values per tet; FP32: 12 (two zero pads), so that a tet's
-    // record is three aligned 16-byte vectors for the push
-    constexpr int kStride = std::is_same<R, float>::value ? 12 : 10;
-    R *c = coef + kStride * (size_t)t;
+    R *c = coef + 10 * (size_t)t;
     const R bx[3] = {(R)b_ext.x, (R)b_ext.y, (R)b_ext.z};
     for (int i = 0; i < 3; i++) {
         c[i] = E0[i];
@@ -291,10 +288,6 @@ __global__ void __launch_bounds__(256) k_coefficients(int nt, const R *__restric
         c[6 + i] = B0[i] * inv3v + bx[i];
     }
     c[9] = divb * inv3v;
-    if (kStride == 12) {
-        c[10] = 0;
-        c[11] = 0;
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -600,80 +593,6 @@ __device__ __forceinline__ void reduce_block(const PushArgs<R, V> &a, uint32_t r
     }
 }
 
-// MIXED deposit reduction of the first pieces, per warp: a warp-segmented
-// inclusive scan by key; a run that lies inside the warp is stored directly
-// (its sole writer), and the warp's first and last runs, when they continue
-// into the neighbouring warps, go to the warp's two carry slots, which
-// k_fixup adds in warp order.  No block barrier: the barrier of the block
-// reduction and its serial merge were a fifth of the push's instructions and
-// stalls.  Live count and kinetic energy are one value per warp.
-__device__ __forceinline__ void reduce_warp_mixed(const PushArgs<float, long long> &a, long i, uint32_t rkey,
-                                                  const long long vals[kNV], float ke, int alive_out, int n_alive) {
-    const int lane = threadIdx.x & 31;
-    const long wid = i >> 5;
-    {
-        const unsigned ball = __ballot_sync(0xFFFFFFFFu, alive_out);
-        float k2 = ke;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) k2 += __shfl_down_sync(0xFFFFFFFFu, k2, o);
-        if (lane == 0) {
-            if (ball) atomicAdd(a.n_alive_next, __popc(ball));
-            a.ke_part[wid] = (double)k2;
-        }
-    }
-    // the four node charges are integers in [0, 2^24]; a run of at most 32
-    // sums below 2^29, so two share one 64-bit lane: 8 scanned channels
-    long long w[8];
-#pragma unroll
-    for (int c = 0; c < 6; c++) w[c] = vals[c];
-    w[6] = vals[6] | (vals[7] << 32);
-    w[7] = vals[8] | (vals[9] << 32);
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t ko = __shfl_up_sync(0xFFFFFFFFu, rkey, off);
-        const bool take = lane >= off && ko == rkey;
-#pragma unroll
-        for (int c = 0; c < 8; c++) {
-            const long long vo = shfl_up_v(w[c], off);
-            if (take) w[c] += vo;
-        }
-    }
-    const uint32_t knext = __shfl_down_sync(0xFFFFFFFFu, rkey, 1);
-    const uint32_t kfirst = __shfl_sync(0xFFFFFFFFu, rkey, 0);
-    // keys of the particles just before and just after this warp
-    const long w0 = wid << 5;
-    uint32_t kedge = kInvalid;
-    if (lane == 0 && w0 > 0 && w0 - 1 < n_alive) kedge = acc_index<long long>(a.skey[w0 - 1], a.nsp);
-    if (lane == 31 && w0 + 32 < n_alive) kedge = acc_index<long long>(a.skey[w0 + 32], a.nsp);
-    const uint32_t prevk = __shfl_sync(0xFFFFFFFFu, kedge, 0), nextk = __shfl_sync(0xFFFFFFFFu, kedge, 31);
-    if (lane == 0) {
-        a.bcar_key[2 * wid] = kInvalid;
-        a.bcar_key[2 * wid + 1] = kInvalid;
-    }
-    __syncwarp();
-    if ((lane == 31 || knext != rkey) && rkey != kInvalid) {
-        const bool first = rkey == kfirst;
-        const bool touches = (first && prevk == rkey) || (lane == 31 && nextk == rkey);
-        long long out[kNV];
-#pragma unroll
-        for (int c = 0; c < 6; c++) out[c] = w[c];
-        out[6] = w[6] & 0xFFFFFFFFll;
-        out[7] = (long long)((unsigned long long)w[6] >> 32);
-        out[8] = w[7] & 0xFFFFFFFFll;
-        out[9] = (long long)((unsigned long long)w[7] >> 32);
-        long long *dst;
-        if (touches) {
-            const int slot = first ? 0 : 1;
-            a.bcar_key[2 * wid + slot] = rkey;
-            dst = a.bcar + (2 * (size_t)wid + slot) * kNV;
-        } else {
-            dst = a.tacc + (size_t)rkey * kNV;
-        }
-#pragma unroll
-        for (int c = 0; c < kNV; c++) dst[c] = out[c];
-    }
-}
-
 // gather + push shared by both precisions; returns the new position and velocity
 template <typename R, int MODE>
 __device__ __forceinline__ void gather_push(const PushArgs<R, typename std::conditional<std::is_same<R, double>::value, double, long long>::type> &a,
@@ -703,11 +622,7 @@ __device__ __forceinline__ void gather_push(const PushArgs<R, typename std::cond
             tv[k] = h * B[k];
         }
         const R t2 = tv[0] * tv[0] + tv[1] * tv[1] + tv[2] * tv[2];
-        R f;
-        if constexpr (std::is_same<R, float>::value)
-            f = __fdividef(2.0f, 1.0f + t2);   // FP32 state: the fast quotient (2 ulp) is enough
-        else
-            f = (R)2 / ((R)1 + t2);
+        const R f = (R)2 / ((R)1 + t2);
         const R vp[3] = {vm[0] + (vm[1] * tv[2] - vm[2] * tv[1]), vm[1] + (vm[2] * tv[0] - vm[0] * tv[2]),
                          vm[2] + (vm[0] * tv[1] - vm[1] * tv[0])};
         const R sv[3] = {f * tv[0], f * tv[1], f * tv[2]};
@@ -1087,123 +1002,8 @@ __global__ void __launch_bounds__(kPushBlock) k_push_plain(const PushArgs<double
 // MIXED: FP32 state, gather, push and walk; fixed-point barycentrics and an
 // integer deposit (exact), accumulators per (tet, species)
 // ---------------------------------------------------------------------------
-// The first piece of every path is summed per (tet, species) run by the
-// block reduction shared with the PLAIN path; the rare later pieces of a path
-// that crosses faces, and the charge a particle leaves on a wall, become
-// records that k_overflow_scatter adds after the kernel.  (Adding every run
-// sum with 64-bit atomics instead of the block reduction made the push 40%
-// slower: ~37M atomics per step on accumulators larger than L2.)
-
-// fixed-point barycentrics, rounded, non-negative and summing to 2^24
-// exactly: the largest component (lowest index on ties; `skip` excluded and
-// set to 0) takes what the other three leave
-__device__ __forceinline__ void quantize_fix(const float lam[4], int skip, int L[4]) {
-    int big = -1;
-    float lb = 0.0f;
-#pragma unroll
-    for (int k = 0; k < 4; k++)
-        if (k != skip && (big < 0 || lam[k] > lb)) {
-            big = k;
-            lb = lam[k];
-        }
-    int sum = 0;
-#pragma unroll
-    for (int k = 0; k < 4; k++) {
-        int v = __float2int_rn(lam[k] * 16777216.0f);
-        v = (v < 0 || k == skip || k == big) ? 0 : v;
-        L[k] = v;
-        sum += v;
-    }
-#pragma unroll
-    for (int k = 0; k < 4; k++)
-        if (k == big) L[k] = kFixOne - sum;   // unrolled select: no local-memory indexing
-}
-
-// The path P -> Q leaves its start tet T through local face kmin at fixed-
-// point barycentrics LX (Algorithm 1 with the exact crossing of a straight
-// path).  Walks the rest: each further piece and, at a wall, the charge left
-// there go to the accumulators with integer atomics.  Returns the end tet, or
-// -1 when the particle is absorbed (or runs past the walk cap, flagged).
-__device__ __forceinline__ int walk_rest_mixed(const PushArgs<float, long long> &a, long i, int T, int kmin,
-                                               const int LX0[4], const float Q[3], int spc) {
-    int LX[4] = {LX0[0], LX0[1], LX0[2], LX0[3]};
-    int LS[4];
-    int4 tn = a.tnodes[T];
-    for (int seg = 1; seg < a.walk_cap; seg++) {
-        const int nb = (&a.tnbr[T].x)[kmin];
-        if (nb < 0) {
-            long long wrec[kNV];
-#pragma unroll
-            for (int k = 0; k < 6; k++) wrec[k] = 0;
-#pragma unroll
-            for (int k = 0; k < 4; k++) wrec[6 + k] = LX[k];
-            push_record(a, (uint32_t)(T * a.nsp + spc), 1, i, kMaxWalk, wrec);
-            return -1;
-        }
-        // carry the three shared barycentrics into the neighbour exactly
-        const int4 nn = a.tnodes[nb];
-        const int tv[4] = {tn.x, tn.y, tn.z, tn.w};
-        const int nv[4] = {nn.x, nn.y, nn.z, nn.w};
-        int entry = -1;
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            int l = 0;
-            bool shared = false;
-#pragma unroll
-            for (int k = 0; k < 4; k++)
-                if (nv[j] == tv[k]) {
-                    l = LX[k];
-                    shared = true;
-                }
-            LS[j] = l;
-            if (!shared) entry = j;
-        }
-        T = nb;
-        tn = nn;
-        float gp[12];
-        load_geo32(a.geo32, T, gp);
-        float le[4];
-        bary32(gp, Q[0], Q[1], Q[2], le);
-        kmin = -1;
-        float smin = 2.0f;
-        float ls[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) ls[k] = (float)LS[k] * (1.0f / 16777216.0f);
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            if (k == entry || !(le[k] < 0.0f)) continue;
-            float sk = ls[k] / (ls[k] - le[k]);
-            sk = sk < 0.0f ? 0.0f : sk;
-            if (sk < smin) {
-                smin = sk;
-                kmin = k;
-            }
-        }
-        long long rec[kNV];
-        if (kmin < 0) {
-            int LE[4];
-            quantize_fix(le, -1, LE);
-            segment_current_fix(LS, LE, rec);
-#pragma unroll
-            for (int k = 0; k < 4; k++) rec[6 + k] = LE[k];
-            push_record(a, (uint32_t)(T * a.nsp + spc), 0, i, seg, rec);
-            return T;
-        }
-        float lx[4];
-#pragma unroll
-        for (int k = 0; k < 4; k++) lx[k] = ls[k] + smin * (le[k] - ls[k]);
-        quantize_fix(lx, kmin, LX);
-        segment_current_fix(LS, LX, rec);
-#pragma unroll
-        for (int k = 0; k < 4; k++) rec[6 + k] = 0;
-        push_record(a, (uint32_t)(T * a.nsp + spc), 0, i, seg, rec);
-    }
-    atomicOr(a.status, (uint32_t)ST_WALK_CAP);
-    return -1;
-}
-
 template <int MODE>
-__global__ void __launch_bounds__(kPushBlock, 5) k_push_mixed(const PushArgs<float, long long> a) {
+__global__ void __launch_bounds__(kPushBlock, 4) k_push_mixed(const PushArgs<float, long long> a) {
     const long i = (long)blockIdx.x * kPushBlock + threadIdx.x;
     const int n_alive = *a.d_n_alive;
     const bool active = i < n_alive;
@@ -1219,65 +1019,103 @@ __global__ void __launch_bounds__(kPushBlock, 5) k_push_mixed(const PushArgs<flo
         const long src = a.perm[i];
         const float P[3] = {a.sx0[src], a.sx1[src], a.sx2[src]};
         const float V[3] = {a.sv0[src], a.sv1[src], a.sv2[src]};
-        // the tet's FP32 barycentric map and field coefficients: six aligned
-        // 16-byte loads
-        float gp[12], cf[12];
+        float gp[12];
         load_geo32(a.geo32, tet, gp);
-        {
-            const float4 *c4 = reinterpret_cast<const float4 *>(a.coef + 12 * (size_t)tet);
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                const float4 v = __ldg(c4 + k);
-                cf[4 * k] = v.x;
-                cf[4 * k + 1] = v.y;
-                cf[4 * k + 2] = v.z;
-                cf[4 * k + 3] = v.w;
-            }
-        }
         float Q[3], Vn[3];
-        gather_push<float, MODE>(a, cf, P, V, P[0] - gp[0], P[1] - gp[1], P[2] - gp[2], spc, src, i, Q, Vn);
-        float lf[4], le[4];
-        int LS[4];
+        gather_push<float, MODE>(a, a.coef + 10 * (size_t)tet, P, V, P[0] - gp[0], P[1] - gp[1], P[2] - gp[2], spc,
+                                 src, i, Q, Vn);
+        float lf[4];
+        int LS[4], LE[4];
         bary32(gp, P[0], P[1], P[2], lf);
-        quantize_fix(lf, -1, LS);
-        bary32(gp, Q[0], Q[1], Q[2], le);
+        quantize(lf, -1, LS);
+        int T = tet;
+        int4 tn = a.tnodes[T];
+        int entry = -1;
+        bool done = false, absorbed = false;
         int endT = tet;
-        // (written as !(le < 0) so that the crossing branch below always finds
-        // an exit face: a NaN end point counts as inside and is flagged later)
-        const bool stays = !(le[0] < 0.0f) && !(le[1] < 0.0f) && !(le[2] < 0.0f) && !(le[3] < 0.0f);
-        if (stays) {
-            // the common case: the whole path lies in the start tet
-            int LE[4];
-            quantize_fix(le, -1, LE);
-            segment_current_fix(LS, LE, vals);
-#pragma unroll
-            for (int k = 0; k < 4; k++) vals[6 + k] = LE[k];
-        } else {
-            // the first piece, to the face the path leaves through (the
-            // smallest crossing parameter among faces with lam(Q) < 0; ties
-            // to the lowest local index), then the rest of the walk
+        for (int seg = 0; seg < a.walk_cap; seg++) {
+            if (seg > 0) load_geo32(a.geo32, T, gp);
+            float le[4];
+            bary32(gp, Q[0], Q[1], Q[2], le);
+            int kmin = -1;
+            float smin = 2.0f;
             float ls[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) ls[k] = (float)LS[k] * (1.0f / 16777216.0f);
-            int kmin = -1;
-            float smin = 2.0f;
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                if (!(le[k] < 0.0f)) continue;
-                float sk = ls[k] / (ls[k] - le[k]);
-                sk = sk < 0.0f ? 0.0f : sk;
-                if (sk < smin) {
-                    smin = sk;
+                if (k == entry || !(le[k] < 0.0f)) continue;
+                float s = ls[k] / (ls[k] - le[k]);
+                s = s < 0.0f ? 0.0f : s;
+                if (s < smin) {
+                    smin = s;
                     kmin = k;
                 }
+            }
+            long long rec[kNV];
+            if (kmin < 0) {
+                quantize(le, -1, LE);
+                segment_current_fix(LS, LE, rec);
+#pragma unroll
+                for (int k = 0; k < 4; k++) rec[6 + k] = LE[k];
+                if (seg == 0) {
+#pragma unroll
+                    for (int c = 0; c < kNV; c++) vals[c] = rec[c];
+                } else {
+                    push_record(a, (uint32_t)(T * a.nsp + spc), 0, i, seg, rec);
+                }
+                endT = T;
+                done = true;
+                break;
             }
             float lx[4];
             int LX[4];
 #pragma unroll
             for (int k = 0; k < 4; k++) lx[k] = ls[k] + smin * (le[k] - ls[k]);
-            quantize_fix(lx, kmin, LX);
-            segment_current_fix(LS, LX, vals);
-            endT = walk_rest_mixed(a, i, tet, kmin, LX, Q, spc);
+            quantize(lx, kmin, LX);
+            segment_current_fix(LS, LX, rec);
+#pragma unroll
+            for (int k = 0; k < 4; k++) rec[6 + k] = 0;
+            if (seg == 0) {
+#pragma unroll
+                for (int c = 0; c < kNV; c++) vals[c] = rec[c];
+            } else {
+                push_record(a, (uint32_t)(T * a.nsp + spc), 0, i, seg, rec);
+            }
+            const int nb = (&a.tnbr[T].x)[kmin];
+            if (nb < 0) {
+                long long wrec[kNV];
+#pragma unroll
+                for (int k = 0; k < 6; k++) wrec[k] = 0;
+#pragma unroll
+                for (int k = 0; k < 4; k++) wrec[6 + k] = LX[k];
+                push_record(a, (uint32_t)(T * a.nsp + spc), 1, i, kMaxWalk, wrec);
+                absorbed = true;
+                done = true;
+                break;
+            }
+            const int4 nn = a.tnodes[nb];
+            const int tv[4] = {tn.x, tn.y, tn.z, tn.w};
+            const int nv[4] = {nn.x, nn.y, nn.z, nn.w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                int l = 0;
+                bool shared = false;
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if (nv[j] == tv[k]) {
+                        l = LX[k];
+                        shared = true;
+                    }
+                LS[j] = l;
+                if (!shared) entry = j;
+            }
+            T = nb;
+            tn = nn;
+        }
+        if (!done) {
+            atomicOr(a.status, (uint32_t)ST_WALK_CAP);
+            absorbed = true;
         }
         a.dx0[i] = Q[0];
         a.dx1[i] = Q[1];
@@ -1286,25 +1124,24 @@ __global__ void __launch_bounds__(kPushBlock, 5) k_push_mixed(const PushArgs<flo
         a.dv1[i] = Vn[1];
         a.dv2[i] = Vn[2];
         a.did[i] = a.sid[src];
-        a.dkey[i] = endT < 0 ? a.dead_key : (((uint32_t)endT << 2) | (uint32_t)spc);
-        if (endT >= 0) {
+        a.dkey[i] = absorbed ? a.dead_key : (((uint32_t)endT << 2) | (uint32_t)spc);
+        if (!absorbed) {
             alive_out = 1;
             ke = 0.5f * a.mw32[spc] * (Vn[0] * Vn[0] + Vn[1] * Vn[1] + Vn[2] * Vn[2]);
             if (!(ke == ke) || !(Q[0] == Q[0])) atomicOr(a.status, (uint32_t)ST_NAN);
         }
         rkey = (uint32_t)(tet * a.nsp + spc);
     }
-    reduce_warp_mixed(a, i, rkey, vals, ke, alive_out, n_alive);
+    reduce_block<float, long long, float>(a, rkey, vals, ke, alive_out, n_alive);
 }
 
 // spanning runs: a head piece (the last run of a block, or a block's first run
 // that does not continue from the previous block) adds the following blocks'
 // first-run pieces of the same key in block order
 template <typename V>
-__global__ void __launch_bounds__(256) k_fixup(int n_blocks, int unit, int nsp, const uint32_t *__restrict__ skey,
+__global__ void __launch_bounds__(256) k_fixup(int n_blocks, int nsp, const uint32_t *__restrict__ skey,
                                                const int *d_n_alive, const uint32_t *__restrict__ bkey,
                                                const V *__restrict__ bval, V *__restrict__ tacc) {
-    // units of `unit` particles (a block in PLAIN, a warp in MIXED), two carry slots each
     const long j = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= 2L * n_blocks) return;
     const uint32_t k = bkey[j];
@@ -1312,7 +1149,7 @@ __global__ void __launch_bounds__(256) k_fixup(int n_blocks, int unit, int nsp, 
     const long blk = j >> 1;
     const int slot = (int)(j & 1);
     if (slot == 0) {
-        const long p = blk * unit - 1;
+        const long p = blk * kPushBlock - 1;
         const int n_alive = *d_n_alive;
         if (blk > 0 && p < n_alive && acc_index<V>(skey[p], nsp) == k) return;
     }
@@ -1678,10 +1515,8 @@ int particles_alloc(Sim *s, size_t cap) {
     if ((rc = overflow_alloc(s, (int)std::min<size_t>(std::max<size_t>(cap / 8, 65536), (size_t)1 << 30))))
         return rc;
     const size_t blocks = std::max<size_t>(1, (cap + kPushBlock - 1) / kPushBlock);
-    // carries and energy partials: per warp (MIXED), which also covers per block
-    const size_t units = blocks * (kPushBlock / 32);
-    if ((rc = s->bcar.alloc(2 * units * kNV)) || (rc = s->bcar_key.alloc(2 * units)) ||
-        (rc = s->ke_part.alloc(units)))
+    if ((rc = s->bcar.alloc(2 * blocks * kNV)) || (rc = s->bcar_key.alloc(2 * blocks)) ||
+        (rc = s->ke_part.alloc(blocks)))
         return rc;
     s->push_blocks_cap = blocks;
     s->cap = cap;
@@ -1955,12 +1790,9 @@ static int launch_push(Sim *s, int mode) {
     prof_end(s, PH_PUSH);
     prof_begin(s, PH_DEPOSIT);
     FP_CUDA(cudaGetLastError());
-    // runs that span reduction units (blocks in PLAIN, warps in MIXED) are
-    // added in unit order
-    const int unit = std::is_same<R, double>::value ? kPushBlock : 32;
-    const int units = std::is_same<R, double>::value ? blocks : blocks * (kPushBlock / 32);
-    { k_fixup<V><<<(2 * units + 255) / 256, 256, 0, s->stream>>>(units, unit, s->nsp, s->skey.p, &dc->n_alive, s->bcar_key.p, (const V *)s->bcar.p, (V *)s->tacc.p); note_launch(); }
-    s->n_ke_parts = units;
+    // runs that span blocks are added in block order
+    { k_fixup<V><<<(2 * blocks + 255) / 256, 256, 0, s->stream>>>(blocks, s->nsp, s->skey.p, &dc->n_alive, s->bcar_key.p, (const V *)s->bcar.p, (V *)s->tacc.p); note_launch(); }
+    s->n_ke_parts = blocks;
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
 }
@@ -2073,10 +1905,8 @@ static int particles_grow(Sim *s, size_t cap, size_t keep) {
         (rc = s->tval.alloc(cap)))
         return rc;
     const size_t blocks = std::max<size_t>(1, (cap + kPushBlock - 1) / kPushBlock);
-    // carries and energy partials: per warp (MIXED), which also covers per block
-    const size_t units = blocks * (kPushBlock / 32);
-    if ((rc = s->bcar.alloc(2 * units * kNV)) || (rc = s->bcar_key.alloc(2 * units)) ||
-        (rc = s->ke_part.alloc(units)))
+    if ((rc = s->bcar.alloc(2 * blocks * kNV)) || (rc = s->bcar_key.alloc(2 * blocks)) ||
+        (rc = s->ke_part.alloc(blocks)))
         return rc;
     s->push_blocks_cap = blocks;
     s->cap = cap;

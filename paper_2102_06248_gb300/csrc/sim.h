@@ -42,7 +42,7 @@ struct GridBarrier {
     unsigned int count;   // arrivals since the launch (epoch k completes at k * blocks)
     unsigned int flag;    // last epoch whose reduction results are published
     int timeout;
-    int spin_limit;       // polls before a wait gives up (set with the reset before each launch)
+    int pad;
     double val[6];        // results the last arriving block publishes
 };
 
@@ -81,7 +81,8 @@ struct PcgArgs {
     int x_zero;                   // the initial guess is 0 (x is written, not read)
     int quiet;                    // reaching max_iters ends the solve without an error
     int block0, blocks;           // blocks of the launch that run this solve
-    int spin_limit;               // polls per grid-barrier wait before a timeout (> 0)
+    int spin_limit;               // polls per grid-barrier wait before a timeout (> 0; kernel argument, so
+                                  // that a wait reads no shared cache line for it)
     // mixed-precision refinement (refine = 1): FP64 residuals, FP32 corrections
     int refine;
     double inner_tol2;            // relative residual^2 of each FP32 correction solve
@@ -218,7 +219,7 @@ struct Sim {
     DevBuf<Control> dctl;
     Control *hctl = nullptr;
     DevBuf<double> diag_part;       // per-block partials of the diagnostic reductions
-    int n_ke_parts = 0;             // kinetic-energy partials of the last push (per block PLAIN, per warp MIXED)
+    int n_ke_parts = 0;             // kinetic-energy partials of the last push (one per block)
     long long cg_iters_sum = 0;     // PCG iterations over all steps (Newmark, completion)
     long long lap_iters_sum = 0;
     GnnState gnn;

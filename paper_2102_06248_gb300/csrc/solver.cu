@@ -726,9 +726,8 @@ __device__ __forceinline__ void st_release(unsigned int *p, unsigned int v) {
 
 // Spins (thread 0) until *p >= target; false when the bound or another
 // block's timeout ends the wait.
-__device__ __forceinline__ bool spin_until(GridBarrier *gb, const unsigned int *p, unsigned int target) {
+__device__ __forceinline__ bool spin_until(GridBarrier *gb, const unsigned int *p, unsigned int target, long limit) {
     volatile int *vto = &gb->timeout;
-    const long limit = gb->spin_limit;
     long spins = 0;
     while (ld_acquire(p) < target) {
         if (++spins > limit || ((spins & 255) == 0 && *vto != 0)) {
@@ -741,12 +740,12 @@ __device__ __forceinline__ bool spin_until(GridBarrier *gb, const unsigned int *
 
 // Barrier number `epoch` (1, 2, ... in every block) among the nb blocks of
 // one solve: the counter reaches epoch * nb once every block has arrived.
-__device__ __forceinline__ bool grid_barrier(GridBarrier *gb, unsigned int epoch, int nb) {
+__device__ __forceinline__ bool grid_barrier(GridBarrier *gb, unsigned int epoch, int nb, long limit) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         red_release_add(&gb->count, 1u);
-        ok = spin_until(gb, &gb->count, epoch * (unsigned)nb);
+        ok = spin_until(gb, &gb->count, epoch * (unsigned)nb, limit);
     }
     __syncthreads();
     return ok != 0;
@@ -795,7 +794,7 @@ __device__ __forceinline__ void block_reduce(const double v[NS], unsigned long l
 template <int NS>
 __device__ __forceinline__ bool grid_reduce(GridBarrier *gb, double *part, const double v[NS],
                                             unsigned long long mx, double *shv, unsigned long long *shm,
-                                            unsigned int epoch, double out[NS + 1], int nb, int bid) {
+                                            unsigned int epoch, double out[NS + 1], int nb, int bid, long limit) {
     __shared__ int role;   // 1: last block, 0: waits, -1: timed out
     __shared__ double res[NS + 1];
     const int G = nb;
@@ -828,7 +827,7 @@ __device__ __forceinline__ bool grid_reduce(GridBarrier *gb, double *part, const
         __syncthreads();
         if (threadIdx.x == 0) st_release(&gb->flag, epoch);
     } else if (role == 0 && threadIdx.x == 0) {
-        if (spin_until(gb, &gb->flag, epoch)) {
+        if (spin_until(gb, &gb->flag, epoch, limit)) {
 #pragma unroll
             for (int c = 0; c <= NS; c++) res[c] = __ldcg(&gb->val[c]);
         } else {
@@ -974,7 +973,7 @@ __device__ __forceinline__ bool cg_core(SolveCtx &c, const T *__restrict__ Av, c
             if constexpr (std::is_same<T, double>::value) c.spmv1(Av, x, init_row);
             else c.spmv(Av, x, init_row);
         }
-        if (!grid_barrier(a.gb, ++c.epoch, c.nb)) return false;
+        if (!grid_barrier(a.gb, ++c.epoch, c.nb, a.spin_limit)) return false;
         auto wrow = [&](int i, T au, T ui) {
             w[i] = au;
             v[2] = fma(au, ui, v[2]);
@@ -982,7 +981,7 @@ __device__ __forceinline__ bool cg_core(SolveCtx &c, const T *__restrict__ Av, c
         if constexpr (std::is_same<T, double>::value) c.spmv1(Av, u, wrow);
         else c.spmv(Av, u, wrow);
         const double vd[4] = {(double)v[0], (double)v[1], (double)v[2], (double)v[3]};
-        if (!grid_reduce<4>(a.gb, a.part, vd, mx, c.shv, c.shm, ++c.epoch, t, c.nb, c.bid)) return false;
+        if (!grid_reduce<4>(a.gb, a.part, vd, mx, c.shv, c.shm, ++c.epoch, t, c.nb, c.bid, a.spin_limit)) return false;
     }
     double gamma = t[0], rr = t[1];
     const double bb = t[3];
@@ -1049,7 +1048,7 @@ __device__ __forceinline__ bool cg_core(SolveCtx &c, const T *__restrict__ Av, c
                 }
             }
         }
-        if (!grid_barrier(a.gb, ++c.epoch, c.nb)) return false;
+        if (!grid_barrier(a.gb, ++c.epoch, c.nb, a.spin_limit)) return false;
         // ---- w = A u ----
         auto wrow = [&](int i, T au, T ui) {
             w[i] = au;
@@ -1058,7 +1057,7 @@ __device__ __forceinline__ bool cg_core(SolveCtx &c, const T *__restrict__ Av, c
         if constexpr (std::is_same<T, double>::value) c.spmv1(Av, u, wrow);
         else c.spmv(Av, u, wrow);
         const double vd[3] = {(double)v[0], (double)v[1], (double)v[2]};
-        if (!grid_reduce<3>(a.gb, a.part, vd, mx, c.shv, c.shm, ++c.epoch, t, c.nb, c.bid)) return false;
+        if (!grid_reduce<3>(a.gb, a.part, vd, mx, c.shv, c.shm, ++c.epoch, t, c.nb, c.bid, a.spin_limit)) return false;
         iters++;
         rr = t[1];
         done = (rr <= tol2 * bb) || (t[3] <= abs_inf);
@@ -1136,7 +1135,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int nb, const i
         bool failed = false;
         double rr = 0.0, bb = 0.0;
         while (true) {
-            if (outer > 0 && !grid_barrier(a.gb, ++c.epoch, nb)) goto timeout;   // x complete
+            if (outer > 0 && !grid_barrier(a.gb, ++c.epoch, nb, a.spin_limit)) goto timeout;   // x complete
             double t[3];
             {
                 double v2[2] = {0.0, 0.0};
@@ -1146,7 +1145,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int nb, const i
                     v2[0] = fma(ri, ri, v2[0]);
                     v2[1] = fma(bi, bi, v2[1]);
                 });
-                if (!grid_reduce<2>(a.gb, a.part, v2, 0ull, shv, shm, ++c.epoch, t, nb, bid)) goto timeout;
+                if (!grid_reduce<2>(a.gb, a.part, v2, 0ull, shv, shm, ++c.epoch, t, nb, bid, a.spin_limit)) goto timeout;
             }
             rr = t[0];
             bb = t[1];
@@ -1397,7 +1396,6 @@ __global__ void k_reset_barriers(PcgBatch<kMaxBatchRuns> B) {
         gb->count = 0;
         gb->flag = 0;
         gb->timeout = 0;
-        gb->spin_limit = B.run[r].spin_limit > 0 ? B.run[r].spin_limit : (int)kSpinLimit;
     }
 }
 
