@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfempic_gb300.so")
 
-SOURCES = ["mesh.cpp", "api.cu", "particles.cu", "solver.cu", "gnn.cu", "batch.cu"]
+SOURCES = ["mesh.cpp", "multigrid.cpp", "api.cu", "particles.cu", "solver.cu", "gnn.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

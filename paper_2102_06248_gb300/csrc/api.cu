@@ -172,7 +172,10 @@ int one_step(Sim *s, bool fields) {
     prof_end(s, PH_CG);
     prof_begin(s, PH_COMPLETION);
     if ((rc = gc_prepare(s))) return rc;
-    {
+    if (s->mesh->mg_levels > 0) {
+        // multigrid-preconditioned completion (large meshes)
+        if ((rc = mg_completion(s))) return rc;
+    } else {
         // the completion is latency-bound: two blocks per SM, unless the
         // configuration fixes the count (1, 2, 3, 4 per SM measured 4.25,
         // 3.40, 3.49, 3.52 ms on the 64^3 plasma-ball mesh)

@@ -120,6 +120,10 @@ struct HostStage {
     HostCsrStage Ir;                             // those rows' entries (CSR)
     std::vector<double> Ir_val;
     std::vector<signed char> e2f_sgn, n2e_sgn;
+    // multigrid hierarchy of the node Laplacian (multigrid.cpp), FP32 values
+    std::vector<float> mg_l0_32, mg_w0, mg_p0v, mg_r0v, mg_l1v, mg_w1, mg_l2inv;
+    HostCsrStage mg_p0, mg_r0, mg_l1, mg_r1;
+    std::vector<int> mg_agg1;
 };
 
 // Mesh on the device.  Internal edge numbering puts interior edges first
@@ -177,6 +181,15 @@ struct Mesh {
     DevBuf<double> L_val;
     DevSell Ls;
     DevBuf<double> Ls_val, L_diag;
+    // smoothed-aggregation hierarchy preconditioning the completion (3 levels;
+    // mg_levels = 0 when the mesh is small or the set-up declined)
+    int mg_levels = 0, mg_n1 = 0, mg_n2 = 0;
+    double mg_scale = 1.0;     // the FP32 operators are mg_scale * L
+    DevBuf<float> mg_l0_32;    // scaled L in the SELL layout of Ls
+    DevBuf<float> mg_w0, mg_w1;   // Jacobi weights 1 / (rho d_i) per level
+    DevCsr mg_p0, mg_r0, mg_l1, mg_r1;   // P0 (fine rows), P0^T, L1, aggregate members of level 1
+    DevBuf<float> mg_p0v, mg_r0v, mg_l1v, mg_l2inv;
+    DevBuf<int> mg_agg1;
     DevBuf<int> node_int;      // node -> interior index or -1
     DevBuf<int> int_node;      // interior index -> node
     // incidence gathers
@@ -195,6 +208,9 @@ struct Mesh {
 };
 
 int build_mesh(const pic_mesh_desc *d, Mesh *m);   // host only
+constexpr int kMgMinNodes = 8192;    // smaller node Laplacians keep Jacobi-PCG
+constexpr int kMgMaxCoarse = 4096;   // largest dense coarsest level
+int build_node_multigrid(Mesh *m, HostStage &H);   // host only (multigrid.cpp)
 int mesh_upload(Mesh *m);                           // to the current device, once
 // canonical G (0), C (1), D (2) triplets
 int mesh_incidence_triplets(const Mesh *m, int which, int *rows, int *cols, int *vals);

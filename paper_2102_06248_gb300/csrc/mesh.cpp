@@ -618,6 +618,7 @@ int build_mesh(const pic_mesh_desc *d, Mesh *m) {
     }
     H.L = {std::move(pl.rowptr), std::move(pl.col)};
     H.L_val = std::move(Lv);
+    if (int rc = build_node_multigrid(m, H)) return rc;
     H.node_int = std::move(node_int);
     H.int_node = std::move(int_node);
     H.f2e = std::move(f2e);
@@ -669,6 +670,14 @@ int mesh_upload(Mesh *m) {
     if ((rc = csr(H.n2e, &m->n2e)) || (rc = m->n2e_sgn.upload(H.n2e_sgn))) return rc;
     if ((rc = m->f2e.upload(H.f2e)) || (rc = m->edge_nodes.upload(H.edge_nodes))) return rc;
     if ((rc = m->edge_canon.upload(m->h_edge_canonical)) || (rc = m->node_bnd.upload(m->h_node_bnd))) return rc;
+    if (m->mg_levels > 0) {
+        if ((rc = m->mg_l0_32.upload(H.mg_l0_32)) || (rc = m->mg_w0.upload(H.mg_w0)) || (rc = m->mg_w1.upload(H.mg_w1)) ||
+            (rc = csr(H.mg_p0, &m->mg_p0)) || (rc = csr(H.mg_r0, &m->mg_r0)) || (rc = csr(H.mg_l1, &m->mg_l1)) ||
+            (rc = csr(H.mg_r1, &m->mg_r1)) || (rc = m->mg_p0v.upload(H.mg_p0v)) || (rc = m->mg_r0v.upload(H.mg_r0v)) ||
+            (rc = m->mg_l1v.upload(H.mg_l1v)) || (rc = m->mg_l2inv.upload(H.mg_l2inv)) ||
+            (rc = m->mg_agg1.upload(H.mg_agg1)))
+            return rc;
+    }
     if (m->n_abs_faces > 0) {
         if ((rc = m->I_val.upload(H.sell_I)) || (rc = m->I_diag.upload(H.I_diag)) || (rc = m->I_row.upload(H.irow)) ||
             (rc = csr(H.Ir, &m->Ir)) || (rc = m->Ir_val.upload(H.Ir_val)))

@@ -215,6 +215,7 @@ struct Sim {
     DevBuf<double> me;              // M x on interior edges
     // Laplacian solver (interior nodes)
     DevBuf<double> L_Dinv, l_x, l_b, l_r, l_z, l_p0, l_p1, l_q, l_part;
+    DevBuf<float> mg32;             // FP32 vectors of the multigrid V-cycle (allocated on first use)
     // device control and pinned host mirror
     DevBuf<Control> dctl;
     Control *hctl = nullptr;
@@ -268,6 +269,7 @@ PcgArgs pcg_args_truncated(Sim *s, int iters);
 PcgArgs pcg_args_completion(Sim *s);
 int launch_pcg_runs(PcgArgs *runs, int n_runs, int blocks_per_sm, cudaStream_t st);
 int gc_prepare(Sim *s);
+int mg_completion(Sim *s);   // the completion with the multigrid preconditioner (mesh->mg_levels > 0)
 int gc_finish(Sim *s);
 // the step in parts (api.cu) and the batch-mode particle set-up (particles.cu)
 int step_particles(Sim *s, bool fields);

@@ -1197,6 +1197,240 @@ timeout:
     }
 }
 
+// ---------------------------------------------------------------------------
+// Completion preconditioned by multigrid.  Flexible PCG (Polak-Ribiere beta,
+// since the preconditioner is applied in FP32) in FP64 on the node Laplacian
+// L, with one V-cycle of the smoothed-aggregation hierarchy of multigrid.cpp
+// as preconditioner: damped Jacobi before and after the coarse correction on
+// levels 0 and 1, the dense inverse on level 2.  The V-cycle runs on the
+// scaled operators s0 L in FP32 with the residual divided by its maximum
+// (sigma), so z = sigma s0 V(r / sigma).  One persistent cooperative launch:
+// every phase that reads other rows' values starts after a grid barrier, and
+// the reductions combine in the last block to arrive (fixed order).  Waits are
+// bounded like those of the Jacobi-PCG (timeout status, no hang).
+// ---------------------------------------------------------------------------
+struct MgArgs {
+    int n0, n1, n2, n_slices;
+    const int *sp, *sw, *col;                 // SELL-32 of L on interior nodes
+    const double *Lv;                         // FP64 values of L
+    const float *L32;                         // FP32 values of s0 L
+    const float *w0, *w1;                     // Jacobi weights 1 / (rho d_i)
+    const int *p0p, *p0c;                     // P0 (fine rows)
+    const float *p0v;
+    const int *r0p, *r0c;                     // P0^T (coarse rows)
+    const float *r0v;
+    const int *l1p, *l1c;                     // L1
+    const float *l1v;
+    const int *agg1, *r1p, *r1c;              // level-1 aggregates and their members
+    const float *l2inv;                       // n2 x n2
+    double s0;
+    const double *b;
+    double *x, *r, *p, *q, *z, *zo;
+    float *r32, *z0, *t0, *r1, *z1, *z1b, *t1, *r2, *z2;
+    double *part;
+    CgState *st;
+    GridBarrier *gb;
+    const double *abs_src;
+    double abs_factor, fallback_tol2;
+    uint32_t *status;
+    int max_iters, spin_limit;
+};
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(kThreads) k_mg_pcg(const MgArgs a) {
+    __shared__ double shv[4 * kThreads];
+    __shared__ unsigned long long shm[kThreads];
+    const int nb = gridDim.x, bid = blockIdx.x;
+    const int G = nb * kThreads, gt = bid * kThreads + threadIdx.x;
+    const int lane = threadIdx.x & 31, nw = G >> 5, gw = gt >> 5;
+    const long lim = a.spin_limit;
+    unsigned int epoch = 0;
+    double thr = -1.0, tol2 = a.fallback_tol2;
+    if (a.abs_src) {
+        const double qv = *a.abs_src;
+        if (qv > 0.0) thr = a.abs_factor * qv;
+    }
+    double t[4];
+    // x = 0, r = b; |b|^2 and max|r|
+    {
+        double v[1] = {0.0};
+        unsigned long long mx = 0;
+        for (int i = gt; i < a.n0; i += G) {
+            const double bi = a.b[i];
+            a.x[i] = 0.0;
+            a.r[i] = bi;
+            v[0] += bi * bi;
+            mx = max(mx, abs_bits(bi));
+        }
+        if (!grid_reduce<1>(a.gb, a.part, v, mx, shv, shm, ++epoch, t, nb, bid, lim)) goto timeout;
+    }
+    {
+        const double bb = t[0];
+        double rmax = t[1], rr = bb, rz_old = 0.0;
+        int it = 0;
+        bool failed = false;
+        auto converged = [&]() { return bb == 0.0 || (thr >= 0.0 ? rmax <= thr : rr <= tol2 * bb); };
+        while (!converged()) {
+            if (it >= a.max_iters) {
+                failed = true;
+                break;
+            }
+            const double sigma = rmax > 0.0 ? rmax : 1.0;
+            const float inv = (float)(1.0 / sigma);
+            // V1: scaled residual and the first Jacobi sweep from zero
+            for (int i = gt; i < a.n0; i += G) {
+                const float ri = (float)a.r[i] * inv;
+                a.r32[i] = ri;
+                a.z0[i] = a.w0[i] * ri;
+            }
+            if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
+            // V2: t0 = r - L z0 (warp per SELL slice)
+            for (int sl = gw; sl < a.n_slices; sl += nw) {
+                const int row = sl * 32 + lane, kb = a.sp[sl] + lane, kw = a.sw[sl];
+                float s = 0.0f;
+#pragma unroll 4
+                for (int j = 0; j < kw; j++) s = fmaf(a.L32[kb + 32 * j], a.z0[a.col[kb + 32 * j]], s);
+                if (row < a.n0) a.t0[row] = a.r32[row] - s;
+            }
+            if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
+            // V3: r1 = P0^T t0, z1 = w1 r1 (warp per coarse row)
+            for (int c = gw; c < a.n1; c += nw) {
+                float s = 0.0f;
+                for (int k = a.r0p[c] + lane; k < a.r0p[c + 1]; k += 32) s = fmaf(a.r0v[k], a.t0[a.r0c[k]], s);
+                s = warp_sum_f(s);
+                if (lane == 0) {
+                    a.r1[c] = s;
+                    a.z1[c] = a.w1[c] * s;
+                }
+            }
+            if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
+            // V4: t1 = r1 - L1 z1
+            for (int c = gw; c < a.n1; c += nw) {
+                float s = 0.0f;
+                for (int k = a.l1p[c] + lane; k < a.l1p[c + 1]; k += 32) s = fmaf(a.l1v[k], a.z1[a.l1c[k]], s);
+                s = warp_sum_f(s);
+                if (lane == 0) a.t1[c] = a.r1[c] - s;
+            }
+            if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
+            // V5: r2 = sum of t1 over each level-2 aggregate
+            for (int g = gw; g < a.n2; g += nw) {
+                float s = 0.0f;
+                for (int k = a.r1p[g] + lane; k < a.r1p[g + 1]; k += 32) s += a.t1[a.r1c[k]];
+                s = warp_sum_f(s);
+                if (lane == 0) a.r2[g] = s;
+            }
+            if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
+            // V6: z2 = L2^-1 r2 (dense)
+            for (int g = gw; g < a.n2; g += nw) {
+                const float *row = a.l2inv + (size_t)g * a.n2;
+                float s = 0.0f;
+                for (int k = lane; k < a.n2; k += 32) s = fmaf(row[k], a.r2[k], s);
+                s = warp_sum_f(s);
+                if (lane == 0) a.z2[g] = s;
+            }
+            if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
+            // V7: coarse correction of level 1
+            for (int c = gt; c < a.n1; c += G) a.z1b[c] = a.z1[c] + a.z2[a.agg1[c]];
+            if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
+            // V8: post-smoothing on level 1
+            for (int c = gw; c < a.n1; c += nw) {
+                float s = 0.0f;
+                for (int k = a.l1p[c] + lane; k < a.l1p[c + 1]; k += 32) s = fmaf(a.l1v[k], a.z1b[a.l1c[k]], s);
+                s = warp_sum_f(s);
+                if (lane == 0) a.z1[c] = a.z1b[c] + a.w1[c] * (a.r1[c] - s);
+            }
+            if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
+            // V9: coarse correction of level 0 (into t0, free now)
+            for (int i = gt; i < a.n0; i += G) {
+                float s = a.z0[i];
+                for (int k = a.p0p[i]; k < a.p0p[i + 1]; k++) s = fmaf(a.p0v[k], a.z1[a.p0c[k]], s);
+                a.t0[i] = s;
+            }
+            if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
+            // V10: post-smoothing on level 0, z = sigma s0 z0 in FP64; (r, z), (r, z_old)
+            {
+                double v[2] = {0.0, 0.0};
+                const double zs = sigma * a.s0;
+                for (int sl = gw; sl < a.n_slices; sl += nw) {
+                    const int row = sl * 32 + lane, kb = a.sp[sl] + lane, kw = a.sw[sl];
+                    float s = 0.0f;
+#pragma unroll 4
+                    for (int j = 0; j < kw; j++) s = fmaf(a.L32[kb + 32 * j], a.t0[a.col[kb + 32 * j]], s);
+                    if (row < a.n0) {
+                        const double zi = zs * (double)(a.t0[row] + a.w0[row] * (a.r32[row] - s));
+                        const double ri = a.r[row];
+                        v[0] += ri * zi;
+                        v[1] += ri * a.zo[row];
+                        a.z[row] = zi;
+                    }
+                }
+                if (!grid_reduce<2>(a.gb, a.part, v, 0ull, shv, shm, ++epoch, t, nb, bid, lim)) goto timeout;
+            }
+            const double rz = t[0];
+            const double beta = it == 0 ? 0.0 : (rz - t[1]) / rz_old;
+            rz_old = rz;
+            for (int i = gt; i < a.n0; i += G) {
+                const double zi = a.z[i];
+                a.p[i] = it == 0 ? zi : zi + beta * a.p[i];   // p is not read before it is set
+                a.zo[i] = zi;
+            }
+            if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
+            // q = L p (FP64, warp per slice) and (p, q)
+            {
+                double v[1] = {0.0};
+                for (int sl = gw; sl < a.n_slices; sl += nw) {
+                    const int row = sl * 32 + lane, kb = a.sp[sl] + lane, kw = a.sw[sl];
+                    double s = 0.0;
+#pragma unroll 4
+                    for (int j = 0; j < kw; j++) s = fma(a.Lv[kb + 32 * j], a.p[a.col[kb + 32 * j]], s);
+                    if (row < a.n0) {
+                        a.q[row] = s;
+                        v[0] += a.p[row] * s;
+                    }
+                }
+                if (!grid_reduce<1>(a.gb, a.part, v, 0ull, shv, shm, ++epoch, t, nb, bid, lim)) goto timeout;
+            }
+            const double alpha = rz_old / t[0];
+            // x += alpha p, r -= alpha q; |r|^2 and max|r|
+            {
+                double v[1] = {0.0};
+                unsigned long long mx = 0;
+                for (int i = gt; i < a.n0; i += G) {
+                    a.x[i] = fma(alpha, a.p[i], a.x[i]);
+                    const double ri = fma(-alpha, a.q[i], a.r[i]);
+                    a.r[i] = ri;
+                    v[0] += ri * ri;
+                    mx = max(mx, abs_bits(ri));
+                }
+                if (!grid_reduce<1>(a.gb, a.part, v, mx, shv, shm, ++epoch, t, nb, bid, lim)) goto timeout;
+            }
+            rr = t[0];
+            rmax = t[1];
+            it++;
+        }
+        if (bid == 0 && threadIdx.x == 0) {
+            a.st->iters = it;
+            a.st->rr = rr;
+            a.st->bb = bb;
+            a.st->done = 1;
+            a.st->failed = failed ? 1 : 0;
+            if (failed) atomicOr(a.status, (uint32_t)ST_CG_NO_CONV);
+        }
+        return;
+    }
+timeout:
+    if (bid == 0 && threadIdx.x == 0) {
+        a.st->done = 1;
+        a.st->failed = 1;
+        atomicOr(a.status, (uint32_t)ST_BARRIER);
+    }
+}
+
 // one solve per launch (its arguments passed by value)
 template <bool REFINE>
 __global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(const PcgArgs a) {
@@ -1387,6 +1621,12 @@ static int sm_count() {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     cache[dev] = sms;
     return sms;
+}
+
+__global__ void k_reset_gbar(GridBarrier *gb) {
+    gb->count = 0;
+    gb->flag = 0;
+    gb->timeout = 0;
 }
 
 __global__ void k_reset_barriers(PcgBatch<kMaxBatchRuns> B) {
@@ -1602,6 +1842,97 @@ int laplacian_solve(Sim *s, const double *rhs_int, double *x_int, double tol, co
                           s->l_p0.p, s->l_p1.p, s->l_part.p, &s->dctl.p->lap, tol, s->cfg.init_tol, 20000, abs_src,
                           abs_factor, true, false);
     return launch_pcg_runs(&a, 1, s->cfg.solver_blocks_per_sm, s->stream);
+}
+
+// The completion with the multigrid preconditioner (mesh with a hierarchy):
+// defect in l_b, solution in l_x, the same stopping rule as the Jacobi-PCG.
+int mg_completion(Sim *s) {
+    const Mesh *m = s->mesh;
+    const int n0 = m->n_int_nodes, n1 = m->mg_n1, n2 = m->mg_n2;
+    if (n0 == 0) return PIC_OK;
+    if (!s->mg32.p) {
+        int rc = s->mg32.alloc(3 * (size_t)n0 + 4 * (size_t)n1 + 2 * (size_t)n2);
+        if (rc) return rc;
+    }
+    Control *dc = s->dctl.p;
+    MgArgs a{};
+    a.n0 = n0;
+    a.n1 = n1;
+    a.n2 = n2;
+    a.n_slices = m->Ls.n_slices;
+    a.sp = m->Ls.ptr.p;
+    a.sw = m->Ls.width.p;
+    a.col = m->Ls.col.p;
+    a.Lv = m->Ls_val.p;
+    a.L32 = m->mg_l0_32.p;
+    a.w0 = m->mg_w0.p;
+    a.w1 = m->mg_w1.p;
+    a.p0p = m->mg_p0.rowptr.p;
+    a.p0c = m->mg_p0.col.p;
+    a.p0v = m->mg_p0v.p;
+    a.r0p = m->mg_r0.rowptr.p;
+    a.r0c = m->mg_r0.col.p;
+    a.r0v = m->mg_r0v.p;
+    a.l1p = m->mg_l1.rowptr.p;
+    a.l1c = m->mg_l1.col.p;
+    a.l1v = m->mg_l1v.p;
+    a.agg1 = m->mg_agg1.p;
+    a.r1p = m->mg_r1.rowptr.p;
+    a.r1c = m->mg_r1.col.p;
+    a.l2inv = m->mg_l2inv.p;
+    a.s0 = m->mg_scale;
+    a.b = s->l_b.p;
+    a.x = s->l_x.p;
+    a.r = s->l_r.p;
+    a.p = s->l_p0.p;
+    a.q = s->l_q.p;
+    a.z = s->l_z.p;
+    a.zo = s->l_p1.p;
+    float *f = s->mg32.p;
+    a.r32 = f;
+    a.z0 = f + n0;
+    a.t0 = f + 2 * (size_t)n0;
+    a.r1 = f + 3 * (size_t)n0;
+    a.z1 = a.r1 + n1;
+    a.z1b = a.z1 + n1;
+    a.t1 = a.z1b + n1;
+    a.r2 = a.t1 + n1;
+    a.z2 = a.r2 + n2;
+    a.part = s->l_part.p;
+    a.st = &dc->lap;
+    a.gb = &dc->gbar2;
+    a.abs_src = &dc->qmax;
+    a.abs_factor = s->cfg.completion_tol;
+    a.fallback_tol2 = s->cfg.init_tol * s->cfg.init_tol;
+    a.status = &dc->status;
+    a.max_iters = 2000;
+    a.spin_limit = s->cfg.barrier_spin_limit > 0 ? s->cfg.barrier_spin_limit : (int)kSpinLimit;
+    // z_old starts at zero (the first beta is 0 and ignores it, but it is read)
+    FP_CUDA(cudaMemsetAsync(s->l_p1.p, 0, sizeof(double) * n0, s->stream));
+    static int per_sm_cache[kMaxDevices];
+    int dev = 0;
+    FP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("mg_completion: device index out of range");
+        return PIC_ERR_CUDA;
+    }
+    if (!per_sm_cache[dev]) {
+        int per_sm = 0, coop = 0;
+        FP_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mg_pcg, kThreads, 0));
+        per_sm_cache[dev] = (coop && per_sm > 0) ? per_sm : -1;
+    }
+    if (per_sm_cache[dev] < 0) {
+        set_error("the multigrid completion needs a device with cooperative launch");
+        return PIC_ERR_CUDA;
+    }
+    const int want = s->cfg.solver_blocks_per_sm ? s->cfg.solver_blocks_per_sm : 2;
+    const int blocks = std::max(1, std::min(per_sm_cache[dev], want)) * sm_count();
+    { k_reset_gbar<<<1, 1, 0, s->stream>>>(a.gb); note_launch(); }
+    void *args[] = {&a};
+    FP_CUDA(cudaLaunchCooperativeKernel((const void *)k_mg_pcg, blocks, kThreads, args, 0, s->stream));
+    note_launch();
+    return PIC_OK;
 }
 
 // Completion of the field solve on the gradient subspace: the part of the
