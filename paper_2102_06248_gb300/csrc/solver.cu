@@ -1242,7 +1242,36 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     return v;
 }
 
-__global__ void __launch_bounds__(kThreads) k_mg_pcg(const MgArgs a) {
+// Sum over one CSR row by a half warp (16 lanes; the two halves of a warp take
+// two rows at once), with every index and value of up to 64 entries loaded
+// before the first gather: the phases are bound by the latency of these
+// dependent loads, not by bandwidth.  val == nullptr means unit weights.
+__device__ __forceinline__ float half_row_dot(const int *__restrict__ ptr, const int *__restrict__ col,
+                                              const float *__restrict__ val, const float *__restrict__ x, int row,
+                                              bool ok, int hl) {
+    float s = 0.0f;
+    if (ok) {
+        const int kb = ptr[row], ke = ptr[row + 1];
+        for (int k0 = kb; k0 < ke; k0 += 64) {
+            int c[4];
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int k = k0 + hl + 16 * u;
+                const bool in = k < ke;
+                c[u] = in ? col[k] : 0;
+                v[u] = in ? (val ? val[k] : 1.0f) : 0.0f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) s = fmaf(v[u], x[c[u]], s);
+        }
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    return s;
+}
+
+__global__ void __launch_bounds__(kThreads, 4) k_mg_pcg(const MgArgs a) {
     __shared__ double shv[4 * kThreads];
     __shared__ unsigned long long shm[kThreads];
     const int nb = gridDim.x, bid = blockIdx.x;
@@ -1298,37 +1327,37 @@ __global__ void __launch_bounds__(kThreads) k_mg_pcg(const MgArgs a) {
                 if (row < a.n0) a.t0[row] = a.r32[row] - s;
             }
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
-            // V3: r1 = P0^T t0, z1 = w1 r1 (warp per coarse row)
-            for (int c = gw; c < a.n1; c += nw) {
-                float s = 0.0f;
-                for (int k = a.r0p[c] + lane; k < a.r0p[c + 1]; k += 32) s = fmaf(a.r0v[k], a.t0[a.r0c[k]], s);
-                s = warp_sum_f(s);
-                if (lane == 0) {
-                    a.r1[c] = s;
-                    a.z1[c] = a.w1[c] * s;
+            // (coarse rows: half a warp per row, two rows per warp at a time)
+            const int hw = gt >> 4, nhw = G >> 4, hl = lane & 15;
+            // V3: r1 = P0^T t0, z1 = w1 r1
+            for (int c0 = hw - (hw & 1); c0 < a.n1; c0 += nhw) {
+                const int c = c0 + (hw & 1);
+                const float sum = half_row_dot(a.r0p, a.r0c, a.r0v, a.t0, c, c < a.n1, hl);
+                if (hl == 0 && c < a.n1) {
+                    a.r1[c] = sum;
+                    a.z1[c] = a.w1[c] * sum;
                 }
             }
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
             // V4: t1 = r1 - L1 z1
-            for (int c = gw; c < a.n1; c += nw) {
-                float s = 0.0f;
-                for (int k = a.l1p[c] + lane; k < a.l1p[c + 1]; k += 32) s = fmaf(a.l1v[k], a.z1[a.l1c[k]], s);
-                s = warp_sum_f(s);
-                if (lane == 0) a.t1[c] = a.r1[c] - s;
+            for (int c0 = hw - (hw & 1); c0 < a.n1; c0 += nhw) {
+                const int c = c0 + (hw & 1);
+                const float sum = half_row_dot(a.l1p, a.l1c, a.l1v, a.z1, c, c < a.n1, hl);
+                if (hl == 0 && c < a.n1) a.t1[c] = a.r1[c] - sum;
             }
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
             // V5: r2 = sum of t1 over each level-2 aggregate
-            for (int g = gw; g < a.n2; g += nw) {
-                float s = 0.0f;
-                for (int k = a.r1p[g] + lane; k < a.r1p[g + 1]; k += 32) s += a.t1[a.r1c[k]];
-                s = warp_sum_f(s);
-                if (lane == 0) a.r2[g] = s;
+            for (int g0 = hw - (hw & 1); g0 < a.n2; g0 += nhw) {
+                const int g = g0 + (hw & 1);
+                const float sum = half_row_dot(a.r1p, a.r1c, nullptr, a.t1, g, g < a.n2, hl);
+                if (hl == 0 && g < a.n2) a.r2[g] = sum;
             }
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
             // V6: z2 = L2^-1 r2 (dense)
             for (int g = gw; g < a.n2; g += nw) {
                 const float *row = a.l2inv + (size_t)g * a.n2;
                 float s = 0.0f;
+#pragma unroll 4
                 for (int k = lane; k < a.n2; k += 32) s = fmaf(row[k], a.r2[k], s);
                 s = warp_sum_f(s);
                 if (lane == 0) a.z2[g] = s;
@@ -1338,17 +1367,29 @@ __global__ void __launch_bounds__(kThreads) k_mg_pcg(const MgArgs a) {
             for (int c = gt; c < a.n1; c += G) a.z1b[c] = a.z1[c] + a.z2[a.agg1[c]];
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
             // V8: post-smoothing on level 1
-            for (int c = gw; c < a.n1; c += nw) {
-                float s = 0.0f;
-                for (int k = a.l1p[c] + lane; k < a.l1p[c + 1]; k += 32) s = fmaf(a.l1v[k], a.z1b[a.l1c[k]], s);
-                s = warp_sum_f(s);
-                if (lane == 0) a.z1[c] = a.z1b[c] + a.w1[c] * (a.r1[c] - s);
+            for (int c0 = hw - (hw & 1); c0 < a.n1; c0 += nhw) {
+                const int c = c0 + (hw & 1);
+                const float sum = half_row_dot(a.l1p, a.l1c, a.l1v, a.z1b, c, c < a.n1, hl);
+                if (hl == 0 && c < a.n1) a.z1[c] = a.z1b[c] + a.w1[c] * (a.r1[c] - sum);
             }
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
-            // V9: coarse correction of level 0 (into t0, free now)
+            // V9: coarse correction of level 0 (into t0, free now); the row's
+            // indices and values (up to 8) are loaded before the gathers
             for (int i = gt; i < a.n0; i += G) {
                 float s = a.z0[i];
-                for (int k = a.p0p[i]; k < a.p0p[i + 1]; k++) s = fmaf(a.p0v[k], a.z1[a.p0c[k]], s);
+                const int kb = a.p0p[i], ke = a.p0p[i + 1];
+                for (int k0 = kb; k0 < ke; k0 += 8) {
+                    int c[8];
+                    float v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; u++) {
+                        const bool in = k0 + u < ke;
+                        c[u] = in ? a.p0c[k0 + u] : 0;
+                        v[u] = in ? a.p0v[k0 + u] : 0.0f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; u++) s = fmaf(v[u], a.z1[c[u]], s);
+                }
                 a.t0[i] = s;
             }
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
@@ -1926,7 +1967,9 @@ int mg_completion(Sim *s) {
         set_error("the multigrid completion needs a device with cooperative launch");
         return PIC_ERR_CUDA;
     }
-    const int want = s->cfg.solver_blocks_per_sm ? s->cfg.solver_blocks_per_sm : 2;
+    // four blocks per SM (2, 3, 4 measured 2.87, 2.41, 2.17 ms per completion
+    // on the 64^3 plasma-ball mesh: the phases are latency-bound)
+    const int want = s->cfg.solver_blocks_per_sm ? s->cfg.solver_blocks_per_sm : 4;
     const int blocks = std::max(1, std::min(per_sm_cache[dev], want)) * sm_count();
     { k_reset_gbar<<<1, 1, 0, s->stream>>>(a.gb); note_launch(); }
     void *args[] = {&a};
