@@ -1206,8 +1206,12 @@ timeout:
 // scaled operators s0 L in FP32 with the residual divided by its maximum
 // (sigma), so z = sigma s0 V(r / sigma).  One persistent cooperative launch:
 // every phase that reads other rows' values starts after a grid barrier, and
-// the reductions combine in the last block to arrive (fixed order).  Waits are
-// bounded like those of the Jacobi-PCG (timeout status, no hang).
+// the reductions combine in the last block to arrive (fixed order).  An
+// iteration has ten such phases: the phases are bound by the latency of
+// dependent loads, so a sweep and the residual that follows it share a pass
+// where the neighbours' values can be formed on the fly, and q = L p comes as
+// L z + beta q right after the preconditioner.  Waits are bounded like those
+// of the Jacobi-PCG (timeout status, no hang).
 // ---------------------------------------------------------------------------
 struct MgArgs {
     int n0, n1, n2, n_slices;
@@ -1311,25 +1315,28 @@ __global__ void __launch_bounds__(kThreads, 4) k_mg_pcg(const MgArgs a) {
             }
             const double sigma = rmax > 0.0 ? rmax : 1.0;
             const float inv = (float)(1.0 / sigma);
-            // V1: scaled residual and the first Jacobi sweep from zero
-            for (int i = gt; i < a.n0; i += G) {
-                const float ri = (float)a.r[i] * inv;
-                a.r32[i] = ri;
-                a.z0[i] = a.w0[i] * ri;
-            }
-            if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
-            // V2: t0 = r - L z0 (warp per SELL slice)
+            // V1: scaled residual r32, the first Jacobi sweep z0 = w0 r32 and
+            // t0 = r32 - L z0, with the neighbours' z0 formed from r on the fly
+            // (no barrier between the sweep and the residual)
             for (int sl = gw; sl < a.n_slices; sl += nw) {
                 const int row = sl * 32 + lane, kb = a.sp[sl] + lane, kw = a.sw[sl];
                 float s = 0.0f;
 #pragma unroll 4
-                for (int j = 0; j < kw; j++) s = fmaf(a.L32[kb + 32 * j], a.z0[a.col[kb + 32 * j]], s);
-                if (row < a.n0) a.t0[row] = a.r32[row] - s;
+                for (int j = 0; j < kw; j++) {
+                    const int cj = a.col[kb + 32 * j];
+                    s = fmaf(a.L32[kb + 32 * j], a.w0[cj] * ((float)a.r[cj] * inv), s);
+                }
+                if (row < a.n0) {
+                    const float ri = (float)a.r[row] * inv;
+                    a.r32[row] = ri;
+                    a.z0[row] = a.w0[row] * ri;
+                    a.t0[row] = ri - s;
+                }
             }
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
             // (coarse rows: half a warp per row, two rows per warp at a time)
             const int hw = gt >> 4, nhw = G >> 4, hl = lane & 15;
-            // V3: r1 = P0^T t0, z1 = w1 r1
+            // V2: r1 = P0^T t0, z1 = w1 r1
             for (int c0 = hw - (hw & 1); c0 < a.n1; c0 += nhw) {
                 const int c = c0 + (hw & 1);
                 const float sum = half_row_dot(a.r0p, a.r0c, a.r0v, a.t0, c, c < a.n1, hl);
@@ -1339,21 +1346,21 @@ __global__ void __launch_bounds__(kThreads, 4) k_mg_pcg(const MgArgs a) {
                 }
             }
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
-            // V4: t1 = r1 - L1 z1
+            // V3: t1 = r1 - L1 z1
             for (int c0 = hw - (hw & 1); c0 < a.n1; c0 += nhw) {
                 const int c = c0 + (hw & 1);
                 const float sum = half_row_dot(a.l1p, a.l1c, a.l1v, a.z1, c, c < a.n1, hl);
                 if (hl == 0 && c < a.n1) a.t1[c] = a.r1[c] - sum;
             }
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
-            // V5: r2 = sum of t1 over each level-2 aggregate
+            // V4: r2 = sum of t1 over each level-2 aggregate
             for (int g0 = hw - (hw & 1); g0 < a.n2; g0 += nhw) {
                 const int g = g0 + (hw & 1);
                 const float sum = half_row_dot(a.r1p, a.r1c, nullptr, a.t1, g, g < a.n2, hl);
                 if (hl == 0 && g < a.n2) a.r2[g] = sum;
             }
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
-            // V6: z2 = L2^-1 r2 (dense)
+            // V5: z2 = L2^-1 r2 (dense)
             for (int g = gw; g < a.n2; g += nw) {
                 const float *row = a.l2inv + (size_t)g * a.n2;
                 float s = 0.0f;
@@ -1363,17 +1370,38 @@ __global__ void __launch_bounds__(kThreads, 4) k_mg_pcg(const MgArgs a) {
                 if (lane == 0) a.z2[g] = s;
             }
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
-            // V7: coarse correction of level 1
-            for (int c = gt; c < a.n1; c += G) a.z1b[c] = a.z1[c] + a.z2[a.agg1[c]];
-            if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
-            // V8: post-smoothing on level 1
+            // V6: coarse correction and post-smoothing of level 1 in one pass:
+            // z1b = (z1 + z2[agg]) + w1 (r1 - L1 (z1 + z2[agg])), the corrected
+            // neighbours formed on the fly
             for (int c0 = hw - (hw & 1); c0 < a.n1; c0 += nhw) {
                 const int c = c0 + (hw & 1);
-                const float sum = half_row_dot(a.l1p, a.l1c, a.l1v, a.z1b, c, c < a.n1, hl);
-                if (hl == 0 && c < a.n1) a.z1[c] = a.z1b[c] + a.w1[c] * (a.r1[c] - sum);
+                const bool ok = c < a.n1;
+                float s = 0.0f;
+                if (ok) {
+                    const int kb = a.l1p[c], ke = a.l1p[c + 1];
+                    for (int k0 = kb; k0 < ke; k0 += 64) {
+                        int cc[4];
+                        float v[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const int k = k0 + hl + 16 * u;
+                            const bool in = k < ke;
+                            cc[u] = in ? a.l1c[k] : 0;
+                            v[u] = in ? a.l1v[k] : 0.0f;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; u++) s = fmaf(v[u], a.z1[cc[u]] + a.z2[a.agg1[cc[u]]], s);
+                    }
+                }
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+                if (hl == 0 && ok) {
+                    const float zc = a.z1[c] + a.z2[a.agg1[c]];
+                    a.z1b[c] = zc + a.w1[c] * (a.r1[c] - s);
+                }
             }
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
-            // V9: coarse correction of level 0 (into t0, free now); the row's
+            // V7: coarse correction of level 0 (into t0, free now); the row's
             // indices and values (up to 8) are loaded before the gathers
             for (int i = gt; i < a.n0; i += G) {
                 float s = a.z0[i];
@@ -1388,12 +1416,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_mg_pcg(const MgArgs a) {
                         v[u] = in ? a.p0v[k0 + u] : 0.0f;
                     }
 #pragma unroll
-                    for (int u = 0; u < 8; u++) s = fmaf(v[u], a.z1[c[u]], s);
+                    for (int u = 0; u < 8; u++) s = fmaf(v[u], a.z1b[c[u]], s);
                 }
                 a.t0[i] = s;
             }
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
-            // V10: post-smoothing on level 0, z = sigma s0 z0 in FP64; (r, z), (r, z_old)
+            // V8: post-smoothing on level 0, z = sigma s0 z0 in FP64; (r, z), (r, z_old)
             {
                 double v[2] = {0.0, 0.0};
                 const double zs = sigma * a.s0;
@@ -1415,23 +1443,23 @@ __global__ void __launch_bounds__(kThreads, 4) k_mg_pcg(const MgArgs a) {
             const double rz = t[0];
             const double beta = it == 0 ? 0.0 : (rz - t[1]) / rz_old;
             rz_old = rz;
-            for (int i = gt; i < a.n0; i += G) {
-                const double zi = a.z[i];
-                a.p[i] = it == 0 ? zi : zi + beta * a.p[i];   // p is not read before it is set
-                a.zo[i] = zi;
-            }
-            if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
-            // q = L p (FP64, warp per slice) and (p, q)
+            // w = L z (z is complete: the reduction above was a grid barrier),
+            // p = z + beta p, q = w + beta q (= L p), and (p, q)
             {
                 double v[1] = {0.0};
                 for (int sl = gw; sl < a.n_slices; sl += nw) {
                     const int row = sl * 32 + lane, kb = a.sp[sl] + lane, kw = a.sw[sl];
                     double s = 0.0;
 #pragma unroll 4
-                    for (int j = 0; j < kw; j++) s = fma(a.Lv[kb + 32 * j], a.p[a.col[kb + 32 * j]], s);
+                    for (int j = 0; j < kw; j++) s = fma(a.Lv[kb + 32 * j], a.z[a.col[kb + 32 * j]], s);
                     if (row < a.n0) {
-                        a.q[row] = s;
-                        v[0] += a.p[row] * s;
+                        const double zi = a.z[row];
+                        const double pi = it == 0 ? zi : zi + beta * a.p[row];   // p, q not read before set
+                        const double qi = it == 0 ? s : s + beta * a.q[row];
+                        a.p[row] = pi;
+                        a.q[row] = qi;
+                        a.zo[row] = zi;
+                        v[0] += pi * qi;
                     }
                 }
                 if (!grid_reduce<1>(a.gb, a.part, v, 0ull, shv, shm, ++epoch, t, nb, bid, lim)) goto timeout;
