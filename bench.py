@@ -796,6 +796,30 @@ def gpu_arm(args):
         dist.destroy_process_group()
 
 
+def host_cpu() -> dict:
+    """The host's logical core count and CPU model (from /proc/cpuinfo or lscpu)."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"logical_cores": os.cpu_count(), "model": model or "unknown"}
+
+
 def cpu_baseline(args, seconds: float = 20.0):
     """The FP64 oracle, as it stands, on the host cores: a proportionally
     scaled copy of the workload (cells / 4 per axis, particles / 64, same
@@ -815,8 +839,10 @@ def cpu_baseline(args, seconds: float = 20.0):
             break
     el = time.perf_counter() - t0
     return {"value": n * steps / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "host": host_cpu(),
             "sample": f"{args.workload} scaled to {cells}^3 cells and {n} particles (same density and dt recipe), "
-                      f"{steps} full steps in {el:.1f} s, single thread"}
+                      f"{steps} full steps in {el:.1f} s, single thread (the oracle is timed as it stands: "
+                      f"one particle at a time in load order, sequential sums)"}
 
 
 def reference_arm(args):
@@ -847,7 +873,7 @@ def reference_arm(args):
             "config": {"workload": workload_desc(args.workload, cells, per),
                        "sample_of": workload_desc(args.workload, args.cells, args.particles)},
             "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "host": host_cpu(), "sample": sample},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
