@@ -820,59 +820,97 @@ def host_cpu() -> dict:
     return {"logical_cores": os.cpu_count(), "model": model or "unknown"}
 
 
+def _oracle_replica(spec):
+    """One process of the all-core oracle runs: builds the scaled sample, runs
+    `warmup` steps, waits for the other replicas, then steps it for `steps`
+    steps or until `seconds` have passed (whichever comes first)."""
+    workload, cells, per, warmup, steps, seconds, barrier = spec
+    from oracle.oracle import from_workload
+    wl, dt, _ = make_workload(workload, cells, per)
+    sim = from_workload(wl, dt)
+    for _ in range(warmup):
+        sim.step()
+    if barrier is not None:
+        barrier.wait()
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps:
+        sim.step()
+        done += 1
+        if seconds is not None and time.perf_counter() - t0 > seconds:
+            break
+    return wl.n_particles, done, time.perf_counter() - t0
+
+
+def oracle_runs(workload: str, cells: int, per: int, warmup: int, steps: int, seconds, procs: int):
+    """The oracle as it stands (one particle at a time, sequential sums: a
+    single-threaded program) on `procs` host cores: that many independent
+    replicas of the sample in spawned processes, started together after their
+    warm-up.  Returns (particle-steps/s summed over the replicas, per-replica
+    (particles, steps, seconds))."""
+    if procs <= 1:
+        r = _oracle_replica((workload, cells, per, warmup, steps, seconds, None))
+        return r[0] * r[1] / r[2], [r]
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        barrier = mgr.Barrier(procs)
+        with ctx.Pool(procs) as pool:
+            res = pool.map(_oracle_replica, [(workload, cells, per, warmup, steps, seconds, barrier)] * procs)
+    # every replica ran the same sample from a common start: the job's rate is
+    # all particle-steps over the slowest replica's time
+    return sum(n * k for n, k, _ in res) / max(el for _, _, el in res), res
+
+
+def default_cpu_procs() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
 def cpu_baseline(args, seconds: float = 20.0):
     """The FP64 oracle, as it stands, on the host cores: a proportionally
     scaled copy of the workload (cells / 4 per axis, particles / 64, same
-    density and dt recipe), stepped until about `seconds` of CPU work."""
-    from oracle.oracle import from_workload
+    density and dt recipe), stepped for about `seconds`: one replica per core
+    (the headline value) and, before that, a single thread."""
     cells = max(4, args.cells // 4)
     per = max(1000, args.particles // 64)
-    wl, dt, _ = make_workload(args.workload, cells, per)
-    sim = from_workload(wl, dt)
-    n = wl.n_particles
-    t0 = time.perf_counter()
-    steps = 0
-    while True:
-        sim.step()
-        steps += 1
-        if time.perf_counter() - t0 > seconds or steps >= 200:
-            break
-    el = time.perf_counter() - t0
-    return {"value": n * steps / el, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+    v1, r1 = oracle_runs(args.workload, cells, per, 0, 200, seconds, 1)
+    procs = args.cpu_procs or default_cpu_procs()
+    vall, rall = oracle_runs(args.workload, cells, per, 0, 200, seconds, procs) if procs > 1 else (v1, r1)
+    n = r1[0][0]
+    steps = min(k for _, k, _ in rall)
+    return {"value": vall, "unit": "particle-steps/s", "cores": procs, "kind": "oracle",
             "host": host_cpu(),
-            "sample": f"{args.workload} scaled to {cells}^3 cells and {n} particles (same density and dt recipe), "
-                      f"{steps} full steps in {el:.1f} s, single thread (the oracle is timed as it stands: "
-                      f"one particle at a time in load order, sequential sums)"}
+            "single_thread": {"value": v1, "steps": r1[0][1], "seconds": round(r1[0][2], 2)},
+            "sample": f"{args.workload} scaled to {cells}^3 cells and {n} particles (same density and dt recipe): "
+                      f"{procs} independent replicas, one per host core, each for about {seconds:.0f} s "
+                      f"(at least {steps} full steps each); the oracle is timed as it stands, a single-threaded "
+                      f"program (one particle at a time in load order, sequential sums)"}
 
 
 def reference_arm(args):
     """The oracle as the reference arm: K timed steps (after W warm-up steps)
-    of the bounded scaled sample of the same workload, on the host cores."""
+    of the bounded scaled sample of the same workload, one replica per host
+    core (the oracle is single-threaded)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle.oracle import from_workload
     cells = max(4, args.cells // 4)
     per = max(1000, args.particles // 64)
-    wl, dt, desc = make_workload(args.workload, cells, per)
-    sim = from_workload(wl, dt)
-    for _ in range(args.warmup):
-        sim.step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        sim.step()
-    el = time.perf_counter() - t0
-    n = wl.n_particles
-    value = n * args.steps / el
+    desc = workload_desc(args.workload, cells, per)
+    procs = args.cpu_procs or default_cpu_procs()
+    value, res = oracle_runs(args.workload, cells, per, args.warmup, args.steps, None, procs)
+    n = res[0][0]
+    el = max(r[2] for r in res)
     sample = (f"{desc}: each step one step of this scaled copy of the workload (same density and dt recipe, "
-              f"{cells}^3 cells, {n} particles), single thread")
+              f"{cells}^3 cells, {n} particles) in each of {procs} independent replicas, one per host core")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": workload_desc(args.workload, cells, per),
-                       "sample_of": workload_desc(args.workload, args.cells, args.particles)},
-            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                       "sample_of": workload_desc(args.workload, args.cells, args.particles),
+                       "replicas": procs},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": procs, "kind": "oracle",
                              "host": host_cpu(), "sample": sample},
             "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -889,6 +927,8 @@ def main():
     ap.add_argument("--particles", type=int, default=16 * 1024 * 1024, help="particles per species")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-procs", type=int, default=0,
+                    help="oracle replicas for the CPU baseline and the reference arm (0: one per host core)")
     ap.add_argument("--clock-log", default=None, help="CSV of the clock samples of the timed region ({gpu}: index)")
     ap.add_argument("--skip-plain", action="store_true", help="do not time the plain-FP64 path (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true", help="do not run the end-to-end leg (profiling runs)")

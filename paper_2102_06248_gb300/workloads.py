@@ -372,13 +372,14 @@ def larmor_orbit_box(n_cells: int = 20, b0z: float = 0.05, vperp_over_c: float =
 def plasma_ball(n_cells: int = 64, n_per_species: int = 16 * 1024 * 1024, seed: int = 1004,
                 steps: int = 1000, h: float = 1.0e-4, jitter: float = 0.2,
                 te_ev: float = 10.0, ti_ev: float = 0.1, sigma_frac: float = 0.15,
-                debye_over_h: float = 2.0) -> Workload:
+                debye_over_h: float = 2.0, mass_ratio: float = MASS_RATIO_P) -> Workload:
     """Neutral e-/p+ Gaussian plasma ball in a jittered PEC box (Sec. IV.C analogue).
 
     Defaults: 64^3 cells (1,572,864 tets) of side h = 0.1 mm with interior
     vertices jittered up to 20% of h; 16M electrons + 16M protons (mass ratio
     1836) in a Gaussian sphere of sigma = 0.15 L; Te = 10 eV, Ti = 0.1 eV;
     the weight puts the peak-density Debye length at 2h; dt = 4 x CFL.
+    `mass_ratio` sets the ion mass in electron masses.
     """
     side = n_cells * h
     mesh = kuhn_box((n_cells,) * 3, (side,) * 3, jitter=jitter, seed=seed)
@@ -387,7 +388,7 @@ def plasma_ball(n_cells: int = 64, n_per_species: int = 16 * 1024 * 1024, seed: 
     n_peak = EPS0 * te / ((debye_over_h * h) ** 2 * Q_E ** 2)
     weight = n_peak * (2.0 * math.pi) ** 1.5 * sigma ** 3 / n_per_species
     out = []
-    for s_idx, (q, m, temp) in enumerate(((Q_E, M_E, te), (-Q_E, MASS_RATIO_P * M_E, ti_ev * EV))):
+    for s_idx, (q, m, temp) in enumerate(((Q_E, M_E, te), (-Q_E, mass_ratio * M_E, ti_ev * EV))):
         base = 1000 * (s_idx + 1)
         ref = 0.5 * side + sigma * np.stack([normal(seed, base + a, n_per_species) for a in range(3)], axis=1)
         ref = np.clip(ref, 0.01 * side, 0.99 * side)

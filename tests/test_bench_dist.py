@@ -75,3 +75,16 @@ def test_clock_record_rejection_rule():
     for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
         assert bench.clock_rejected(dict(ok, reasons=[r]))
     assert not bench.clock_rejected({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]})
+
+
+def test_oracle_replicas_on_two_cores():
+    """The CPU baseline and the reference arm run the single-threaded oracle
+    as one replica per core: two spawned replicas of a small sample both step
+    it, and the reported rate is all their particle-steps over the slower
+    replica's time."""
+    sys.path.insert(0, ROOT)
+    import bench
+    rate, res = bench.oracle_runs("thermal_cube", 4, 1000, 1, 2, None, 2)
+    assert len(res) == 2
+    assert all(k == 2 and n == res[0][0] and el > 0 for n, k, el in res)
+    assert rate == pytest.approx(sum(n * k for n, k, _ in res) / max(el for _, _, el in res))
