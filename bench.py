@@ -398,7 +398,12 @@ def batched_leg(F, torch, args):
             "one_by_one": {"steps": seq_steps, "ms_per_step": 1e3 * (t3 - t2) / seq_steps, "value": ps_s},
             "speedup_batched": ps_b / ps_s, "continuity_ok": ok, "timing": "host clock around synchronising calls",
             "graph": info["graph"], "graph_steps": info["graph_steps"], "graph_launches": info["graph_launches"],
-            "solver_blocks_per_sm": info["solver_blocks_per_sm"], "tune_ms_2_3_4": info["tune_ms"]}
+            "tuned": {"newmark": {"blocks_per_sm": info["solver_blocks_per_sm"], "build": info["solver_build"]},
+                      "completion": {"blocks_per_sm": info["completion_blocks_per_sm"],
+                                     "build": info["completion_build"]},
+                      "candidates": "blocks/SM 2, 3, 4 (64-register build), 2, 3 (80-register), 5, 6 (40-register), 7, 8 (32-register)",
+                      "tune_newmark_ms": [round(v, 3) for v in info["tune_newmark_ms"]],
+                      "tune_completion_ms": [round(v, 3) for v in info["tune_completion_ms"]]}}
 
 
 def larmor_leg(F, torch, args):

@@ -373,8 +373,11 @@ int pic_gnn_loss_grad(pic_sim *sim, const double *r_edges, double *loss, double 
  * each of the step's two solves (Newmark PCG, gradient-subspace completion)
  * for all members in ONE persistent launch; six consecutive steps (the
  * period of the buffer rotations) are captured once as a CUDA graph and
- * replayed.  The solver's blocks per SM are picked by timing candidates on
- * the batch's own systems (kept per batch shape).  Results are those of
+ * replayed.  For each of the two solves a tuner picks the blocks per SM
+ * and the build of the batched solver kernel (64 registers, up to four
+ * blocks per SM; 80 registers, up to three; 40, up to six; 32, up to eight)
+ * by timing each candidate on the batch's own systems (kept per batch shape).
+ * Results are those of
  * pic_step on each member: bitwise when every member's solve gets the
  * blocks it would get alone (then the kernels and reduction orders are the
  * same), otherwise equal to the solve tolerance.
@@ -387,10 +390,20 @@ typedef struct {
     int32_t n_sims;
     int32_t graph;                /* 1: steps replay a captured graph, 0: not yet, -1: unavailable */
     int32_t graph_steps;          /* steps per graph launch (6) */
-    int32_t solver_blocks_per_sm; /* chosen by the tuner (0: not tuned yet) */
+    int32_t solver_blocks_per_sm; /* Newmark solve, chosen by the tuner (0: not tuned yet) */
     int64_t graph_launches;
     int64_t eager_steps;          /* steps issued one by one (warm-up, remainders) */
-    double tune_ms[3];            /* tuning solve time at 2, 3, 4 blocks per SM */
+    double tune_ms[3];            /* Newmark tuning solve at 2, 3, 4 blocks per SM, 64-register build */
+    int32_t solver_build;         /* Newmark solve's kernel build: 0 = 64 registers, 1 = 80, 2 = 40, 3 = 32 */
+    int32_t completion_blocks_per_sm; /* completion solve, chosen by the tuner (0: not tuned yet) */
+    int32_t completion_build;     /* completion solve's kernel build, as solver_build */
+    int32_t pad_;
+    /* tuning times (ms) per candidate: blocks per SM 2, 3, 4 with build 0;
+     * 2, 3 with build 1; 5, 6 with build 2; 7, 8 with build 3.  -1: not
+     * timed (the choice came from an earlier batch of the same shape in this
+     * process) */
+    double tune_newmark_ms[9];
+    double tune_completion_ms[9];
 } pic_batch_info_t;
 
 /* Creates a batch over sims[0..n) (the simulations must outlive it). */

@@ -15,14 +15,23 @@
 //     device), so six consecutive steps -- the period of the buffer rotations
 //     (three time levels, two particle banks) -- are captured once as a CUDA
 //     graph and replayed;
-//   * the solver's blocks per SM are picked by timing the candidates on the
-//     batch's own systems, and the choice is kept per batch shape.
+//   * for each of the two solves the tuner picks the blocks per SM and the
+//     build of the batched kernel (64 registers for up to four blocks per
+//     SM, 80 for up to three, 40 for up to six, 32 for up to eight) by
+//     timing every candidate on the batch's own systems; the choice is kept
+//     per batch shape.
 #include <map>
 #include <mutex>
 #include <utility>
 #include <vector>
 
 #include "sim.h"
+
+// tuner candidates: blocks per SM and kernel build (0: 64 registers, 1: 80,
+// 2: 40, 3: 32)
+constexpr int kTuneCands = 9;
+constexpr int kTuneBps[kTuneCands] = {2, 3, 4, 2, 3, 5, 6, 7, 8};
+constexpr int kTuneBuild[kTuneCands] = {0, 0, 0, 1, 1, 2, 2, 3, 3};
 
 struct pic_batch {
     std::vector<pic_sim *> sims;
@@ -38,8 +47,13 @@ struct pic_batch {
     int phase = 0;                             // steps since the captured pointer state, mod 6
     std::vector<long long> step_at;            // each sim's step counter the batch expects
     std::vector<int> n_total_at;               // particle counts the graph was captured with
-    int blocks_per_sm = 0;
-    double tune_ms[5] = {0, 0, 0, 0, 0};       // time of the tuning solve per blocks/SM (index 2..4)
+    int blocks_per_sm = 0;                     // Newmark solve (0: not tuned yet)
+    int build = 0;                             // Newmark solve: kernel build (launch_pcg_runs)
+    int gc_blocks_per_sm = 0, gc_build = 0;    // the same for the completion
+    // tuning times (ms) per candidate (kTuneBps, kTuneBuild; -1: not timed,
+    // e.g. the choice came from an earlier batch of the same shape)
+    double tune_ms[kTuneCands] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
+    double tune_gc_ms[kTuneCands] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
     long long graph_launches = 0, eager_steps = 0;
 };
 
@@ -49,7 +63,11 @@ namespace {
 constexpr int kGraphSteps = 6;   // lcm of the rotation periods (3 field levels, 2 banks)
 
 std::mutex g_tune_mutex;
-std::map<std::pair<int, long long>, int> g_tuned;   // (runs, total rows) -> blocks per SM
+struct Tuned {
+    int bps, build, gc_bps, gc_build;
+};
+// (runs, total rows, refinement) -> choices
+std::map<std::pair<std::pair<int, long long>, int>, Tuned> g_tuned;
 
 int fork_all(pic_batch *b) {
     FP_CUDA(cudaEventRecord(b->fork, b->ms));
@@ -77,7 +95,7 @@ int batch_step_once(pic_batch *b) {
     runs.clear();
     for (auto *ps : b->sims)
         if (ps->s.mesh->n_int_edges > 0) runs.push_back(pcg_args_newmark(&ps->s));
-    if ((rc = launch_pcg_runs(runs.data(), (int)runs.size(), b->blocks_per_sm, b->ms))) return rc;
+    if ((rc = launch_pcg_runs(runs.data(), (int)runs.size(), b->blocks_per_sm, b->ms, b->build))) return rc;
     if ((rc = fork_all(b))) return rc;
     for (auto *ps : b->sims)
         if ((rc = gc_prepare(&ps->s))) return rc;
@@ -85,7 +103,7 @@ int batch_step_once(pic_batch *b) {
     runs.clear();
     for (auto *ps : b->sims)
         if (ps->s.mesh->n_int_edges > 0 && ps->s.mesh->n_int_nodes > 0) runs.push_back(pcg_args_completion(&ps->s));
-    if ((rc = launch_pcg_runs(runs.data(), (int)runs.size(), b->blocks_per_sm, b->ms))) return rc;
+    if ((rc = launch_pcg_runs(runs.data(), (int)runs.size(), b->gc_blocks_per_sm, b->ms, b->gc_build))) return rc;
     if ((rc = fork_all(b))) return rc;
     for (auto *ps : b->sims)
         if ((rc = step_fields_end(&ps->s))) return rc;
@@ -94,49 +112,85 @@ int batch_step_once(pic_batch *b) {
     return PIC_OK;
 }
 
-// The solver's blocks per SM for this batch: a fixed-length solve of every
-// run's last Newmark system in one launch, timed for 2, 3 and 4 blocks per
-// SM; the fastest is kept for batches of the same shape.
+// The solvers' launch shape for this batch.  Each candidate (blocks per SM
+// 2, 3, 4 with the 64-register build, 2 and 3 with the 80-register one, 5 and
+// 6 with the 40-register one, 7 and 8 with the 32-register one) is timed on
+// every member's own last systems,
+// once to warm up and once timed:
+// the Newmark solve stopped after 40 iterations from x = 0 (x is rewritten
+// before the next solve), and the completion's solve of its last defect to
+// its tolerance.  The fastest of each is kept for batches of the same shape
+// (number of members, total rows, refinement or FP64 Newmark solve).
 int autotune(pic_batch *b) {
     long long rows = 0;
-    for (auto *ps : b->sims) rows += ps->s.mesh->n_int_edges;
-    const std::pair<int, long long> key((int)b->sims.size(), rows);
+    int refine = 0;
+    for (auto *ps : b->sims) {
+        rows += ps->s.mesh->n_int_edges;
+        if (ps->s.mixed) refine = 1;
+    }
+    const std::pair<std::pair<int, long long>, int> key({(int)b->sims.size(), rows}, refine);
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tuned.find(key);
         if (it != g_tuned.end()) {
-            b->blocks_per_sm = it->second;
+            b->blocks_per_sm = it->second.bps;
+            b->build = it->second.build;
+            b->gc_blocks_per_sm = it->second.gc_bps;
+            b->gc_build = it->second.gc_build;
             return PIC_OK;
         }
     }
     cudaEvent_t e0, e1;
     FP_CUDA(cudaEventCreate(&e0));
     FP_CUDA(cudaEventCreate(&e1));
-    int best = 4;
-    float best_ms = 1e30f;
-    for (int bps = 4; bps >= 2; bps--) {
-        std::vector<PcgArgs> runs;
-        for (auto *ps : b->sims)
-            if (ps->s.mesh->n_int_edges > 0) runs.push_back(pcg_args_truncated(&ps->s, 40));
-        int rc = launch_pcg_runs(runs.data(), (int)runs.size(), bps, b->ms);   // warm-up
-        if (rc) return rc;
-        FP_CUDA(cudaEventRecord(e0, b->ms));
-        if ((rc = launch_pcg_runs(runs.data(), (int)runs.size(), bps, b->ms))) return rc;
-        FP_CUDA(cudaEventRecord(e1, b->ms));
-        FP_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        FP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        b->tune_ms[bps] = ms;
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = bps;
+    int rc = PIC_OK;
+    for (int solve = 0; solve < 2 && rc == PIC_OK; solve++) {
+        int best = 2;
+        float best_ms = 1e30f;
+        for (int c = 0; c < kTuneCands && rc == PIC_OK; c++) {
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && rc == PIC_OK; rep++) {
+                std::vector<PcgArgs> runs;
+                for (auto *ps : b->sims) {
+                    Sim *s = &ps->s;
+                    if (s->mesh->n_int_edges == 0) continue;
+                    if (solve == 0) {
+                        if (cudaMemsetAsync(s->x.p, 0, sizeof(double) * s->mesh->n_int_edges, b->ms) != cudaSuccess) rc = PIC_ERR_CUDA;
+                        runs.push_back(pcg_args_newmark_truncated(s, 40));
+                    } else if (s->mesh->n_int_nodes > 0) {
+                        runs.push_back(pcg_args_completion(s));
+                    }
+                }
+                if (rc) break;
+                if (cudaEventRecord(e0, b->ms) != cudaSuccess) rc = PIC_ERR_CUDA;
+                if (!rc) rc = launch_pcg_runs(runs.data(), (int)runs.size(), kTuneBps[c], b->ms, kTuneBuild[c]);
+                if (!rc && cudaEventRecord(e1, b->ms) != cudaSuccess) rc = PIC_ERR_CUDA;
+                if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = PIC_ERR_CUDA;
+                if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = PIC_ERR_CUDA;
+            }
+            if (rc) break;
+            (solve == 0 ? b->tune_ms : b->tune_gc_ms)[c] = ms;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+            }
+        }
+        if (solve == 0) {
+            b->blocks_per_sm = kTuneBps[best];
+            b->build = kTuneBuild[best];
+        } else {
+            b->gc_blocks_per_sm = kTuneBps[best];
+            b->gc_build = kTuneBuild[best];
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    b->blocks_per_sm = best;
+    if (rc) {
+        set_error("batch tuning: a CUDA call failed");
+        return rc;
+    }
     std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tuned[key] = best;
+    g_tuned[key] = Tuned{b->blocks_per_sm, b->build, b->gc_blocks_per_sm, b->gc_build};
     return PIC_OK;
 }
 
@@ -397,7 +451,14 @@ int pic_batch_info(const pic_batch *b, pic_batch_info_t *out) {
     out->solver_blocks_per_sm = b->blocks_per_sm;
     out->graph_launches = b->graph_launches;
     out->eager_steps = b->eager_steps;
-    for (int i = 0; i < 3; i++) out->tune_ms[i] = b->tune_ms[i + 2];
+    for (int i = 0; i < 3; i++) out->tune_ms[i] = b->tune_ms[i];
+    out->solver_build = b->build;
+    out->completion_blocks_per_sm = b->gc_blocks_per_sm;
+    out->completion_build = b->gc_build;
+    for (int i = 0; i < kTuneCands; i++) {
+        out->tune_newmark_ms[i] = b->tune_ms[i];
+        out->tune_completion_ms[i] = b->tune_gc_ms[i];
+    }
     return PIC_OK;
 }
 

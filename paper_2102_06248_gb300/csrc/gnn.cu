@@ -151,6 +151,7 @@ __global__ void __launch_bounds__(kT) k_rnorm(int n, const double *__restrict__ 
 __device__ __forceinline__ double rho_of(const double *nrm, int n) { return sqrt(nrm[0] / n); }
 
 // ---- forward ----
+template <bool KEEP>
 __global__ void __launch_bounds__(kT) k_embed(int n, const double *__restrict__ r, const double *__restrict__ isd,
                                              const double *__restrict__ nrm, const float *__restrict__ feat_a,
                                              const unsigned short *__restrict__ th, float *__restrict__ xin,
@@ -161,8 +162,10 @@ __global__ void __launch_bounds__(kT) k_embed(int n, const double *__restrict__ 
     for (int i = blockIdx.x * kW + (threadIdx.x >> 5); i < n; i += gridDim.x * kW) {
         const float x = rho > 0.0 ? (float)(r[i] * isd[i] / rho) : 0.0f;
         const float p = fmaf(U, x, fmaf(V, feat_a[i], c));
-        if (lane == 0) xin[i] = x;
-        pre0[(size_t)i * kH + lane] = p;
+        if (KEEP) {
+            if (lane == 0) xin[i] = x;
+            pre0[(size_t)i * kH + lane] = p;
+        }
         h0[(size_t)i * kH + lane] = fmaxf(p, 0.0f);
     }
 }
@@ -194,8 +197,10 @@ __device__ __forceinline__ float aggregate(int i, const int *__restrict__ sp, co
     return acc;
 }
 
-// one message-passing layer; the last one also forms z
-template <bool LAST>
+// one message-passing layer; the last one also forms z.  KEEP: store the
+// aggregates and pre-activations the backward pass reads (a preconditioner
+// application inside the flexible PCG stores only h)
+template <bool LAST, bool KEEP>
 __global__ void __launch_bounds__(kT) k_layer(int n, const int *__restrict__ sp, const int *__restrict__ sw,
                                              const int *__restrict__ col, const float *__restrict__ ahat,
                                              const float *__restrict__ hp, const unsigned short *__restrict__ th,
@@ -227,9 +232,11 @@ __global__ void __launch_bounds__(kT) k_layer(int n, const int *__restrict__ sp,
             p = fmaf(Qt[k * kH + lane], __shfl_sync(0xFFFFFFFFu, gi, k), p);
         }
         const float hn = fmaxf(p, 0.0f);
-        g[(size_t)i * kH + lane] = gi;
-        pre[(size_t)i * kH + lane] = p;
-        h[(size_t)i * kH + lane] = hn;
+        if (KEEP) {
+            g[(size_t)i * kH + lane] = gi;
+            pre[(size_t)i * kH + lane] = p;
+        }
+        if (!LAST || KEEP) h[(size_t)i * kH + lane] = hn;
         if (LAST) {
             float y = osh[lane] * hn;
 #pragma unroll
@@ -533,9 +540,9 @@ int gnn_get_weights(Sim *s, float *w, long long np) {
     return PIC_OK;
 }
 
-// z = P(r) on interior edges (internal order, device arrays); keeps the
-// activations for a backward pass.  G.sc[0] receives n rho^2.
-int gnn_forward(Sim *s, const double *r, double *z) {
+// z = P(r) on interior edges (internal order, device arrays); with `keep`
+// the activations a backward pass needs are stored.  G.sc[0] receives n rho^2.
+int gnn_forward(Sim *s, const double *r, double *z, bool keep) {
     GnnState &G = s->gnn;
     const Mesh *m = s->mesh;
     const int n = m->n_int_edges;
@@ -545,12 +552,18 @@ int gnn_forward(Sim *s, const double *r, double *z) {
     int rc;
     { k_rnorm<<<kGB, kT, 0, st>>>(n, r, s->Dinv.p, G.part.p); note_launch(); }
     if ((rc = gnn_reduce_launch(s, 1, G.sc.p))) return rc;
-    { k_embed<<<kGB, kT, 0, st>>>(n, r, G.isd.p, G.sc.p, G.feat_a.p, G.theta_bf.p, G.xin.p, G.pre[0].p, G.h[0].p); note_launch(); }
+    if (keep) { k_embed<true><<<kGB, kT, 0, st>>>(n, r, G.isd.p, G.sc.p, G.feat_a.p, G.theta_bf.p, G.xin.p, G.pre[0].p, G.h[0].p); note_launch(); }
+    else { k_embed<false><<<kGB, kT, 0, st>>>(n, r, G.isd.p, G.sc.p, G.feat_a.p, G.theta_bf.p, G.xin.p, G.pre[0].p, G.h[0].p); note_launch(); }
     const int gr = rows_grid(n);
     for (int l = 1; l <= 3; l++) {
         const int off = kOffL + (l - 1) * kLayer;
-        if (l < 3) { k_layer<false><<<gr, kT, 0, st>>>(n, A.ptr.p, A.width.p, A.col.p, G.ahat.p, G.h[l - 1].p, G.theta_bf.p, off, G.g[l].p, G.pre[l].p, G.h[l].p, r, s->Dinv.p, G.isd.p, G.sc.p, z); note_launch(); }
-        else { k_layer<true><<<gr, kT, 0, st>>>(n, A.ptr.p, A.width.p, A.col.p, G.ahat.p, G.h[l - 1].p, G.theta_bf.p, off, G.g[l].p, G.pre[l].p, G.h[l].p, r, s->Dinv.p, G.isd.p, G.sc.p, z); note_launch(); }
+        // without keep, layers 1 and 2 ping-pong between h[0] and h[1]
+        const float *hin = keep ? G.h[l - 1].p : G.h[(l - 1) & 1].p;
+        float *hout = keep ? G.h[l].p : G.h[l & 1].p;
+        if (l < 3 && keep) { k_layer<false, true><<<gr, kT, 0, st>>>(n, A.ptr.p, A.width.p, A.col.p, G.ahat.p, hin, G.theta_bf.p, off, G.g[l].p, G.pre[l].p, hout, r, s->Dinv.p, G.isd.p, G.sc.p, z); note_launch(); }
+        else if (l < 3) { k_layer<false, false><<<gr, kT, 0, st>>>(n, A.ptr.p, A.width.p, A.col.p, G.ahat.p, hin, G.theta_bf.p, off, G.g[l].p, G.pre[l].p, hout, r, s->Dinv.p, G.isd.p, G.sc.p, z); note_launch(); }
+        else if (keep) { k_layer<true, true><<<gr, kT, 0, st>>>(n, A.ptr.p, A.width.p, A.col.p, G.ahat.p, hin, G.theta_bf.p, off, G.g[l].p, G.pre[l].p, hout, r, s->Dinv.p, G.isd.p, G.sc.p, z); note_launch(); }
+        else { k_layer<true, false><<<gr, kT, 0, st>>>(n, A.ptr.p, A.width.p, A.col.p, G.ahat.p, hin, G.theta_bf.p, off, G.g[l].p, G.pre[l].p, hout, r, s->Dinv.p, G.isd.p, G.sc.p, z); note_launch(); }
     }
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
@@ -590,7 +603,7 @@ int gnn_backward(Sim *s, const double *r, const double *z) {
 
 int gnn_loss_grad(Sim *s, const double *r, double *loss, double *grad_host) {
     int rc;
-    if ((rc = gnn_forward(s, r, s->gnn.z.p)) || (rc = gnn_backward(s, r, s->gnn.z.p))) return rc;
+    if ((rc = gnn_forward(s, r, s->gnn.z.p, true)) || (rc = gnn_backward(s, r, s->gnn.z.p))) return rc;
     double sc[2];
     FP_CUDA(cudaMemcpyAsync(sc, s->gnn.sc.p, sizeof(double) * 2, cudaMemcpyDeviceToHost, s->stream));
     if (grad_host)
@@ -622,7 +635,7 @@ int gnn_train(Sim *s, const pic_gnn_train_cfg *cfg, double *loss_out) {
     double last = 0.0;
     for (int t = 0; t < cfg->steps; t++) {
         const double *r = G.samples.p + (size_t)(t % ns) * n;
-        if ((rc = gnn_forward(s, r, G.z.p)) || (rc = gnn_backward(s, r, G.z.p))) return rc;
+        if ((rc = gnn_forward(s, r, G.z.p, true)) || (rc = gnn_backward(s, r, G.z.p))) return rc;
         G.adam_t++;
         const float c1 = 1.0f - std::pow(b1, (float)G.adam_t), c2 = 1.0f - std::pow(b2, (float)G.adam_t);
         { k_adam<<<(kGnnParams + 255) / 256, 256, 0, s->stream>>>(kGnnParams, G.theta.p, G.adam_m.p, G.adam_v.p, G.grad.p, (float)cfg->lr, b1, b2, eps, c1, c2, G.theta_bf.p); note_launch(); }
@@ -666,7 +679,7 @@ int fpcg_newmark(Sim *s, int *iters_out) {
             FP_CUDA(cudaGetLastError());
             return PIC_OK;
         }
-        return gnn_forward(s, rr, zz);
+        return gnn_forward(s, rr, zz, false);
     };
     { k_resid<<<kGB, kT, 0, st>>>(n, A.n_slices, A.ptr.p, A.width.p, A.col.p, s->A_val.p, b, x, r); note_launch(); }
     double bb_rr[2];

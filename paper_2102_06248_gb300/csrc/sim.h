@@ -266,8 +266,12 @@ int newmark_truncated_residual(Sim *s, int iters, double *r_out);
 // persistent launch over many of them (blocks_per_sm 0: as many as fit)
 PcgArgs pcg_args_newmark(Sim *s);
 PcgArgs pcg_args_truncated(Sim *s, int iters);
+PcgArgs pcg_args_newmark_truncated(Sim *s, int iters);
 PcgArgs pcg_args_completion(Sim *s);
-int launch_pcg_runs(PcgArgs *runs, int n_runs, int blocks_per_sm, cudaStream_t st);
+// build: the batched kernel's build (0: 64 registers, up to four blocks per
+// SM; 1: 80 registers, up to three; 2: 40 registers, up to six; 3: 32
+// registers, up to eight)
+int launch_pcg_runs(PcgArgs *runs, int n_runs, int blocks_per_sm, cudaStream_t st, int build = 0);
 int gc_prepare(Sim *s);
 int mg_completion(Sim *s);   // the completion with the multigrid preconditioner (mesh->mg_levels > 0)
 int gc_finish(Sim *s);
@@ -281,7 +285,7 @@ int particles_inject(Sim *s, int species, int n, const double *hx, const double 
 int gnn_prepare(Sim *s);
 int gnn_set_weights(Sim *s, const float *w, long long np);
 int gnn_get_weights(Sim *s, float *w, long long np);
-int gnn_forward(Sim *s, const double *r, double *z);
+int gnn_forward(Sim *s, const double *r, double *z, bool keep);
 int gnn_loss_grad(Sim *s, const double *r, double *loss, double *grad_host);
 int gnn_train(Sim *s, const pic_gnn_train_cfg *cfg, double *loss_out);
 int fpcg_newmark(Sim *s, int *iters_out);

@@ -1506,9 +1506,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_pcg_persistent(const PcgArgs a)
     pcg_body<REFINE>(a, gridDim.x, blockIdx.x);
 }
 
-// several solves of one kind per launch: run r owns blocks [block0, block0 + blocks)
-template <bool REFINE>
-__global__ void __launch_bounds__(kThreads, 4) k_pcg_batched(const __grid_constant__ PcgBatch<kMaxBatchRuns> B) {
+// several solves of one kind per launch: run r owns blocks [block0, block0 + blocks).
+// Built for MINB = 4 blocks per SM (64 registers), MINB = 3 (80: the
+// refinement form then keeps its state in registers), MINB = 6 (40) and
+// MINB = 8 (32: more warps to hide the latency of many small systems, at the
+// price of spills); a batch's tuner picks.
+template <bool REFINE, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_pcg_batched(const __grid_constant__ PcgBatch<kMaxBatchRuns> B) {
     // the block's run, copied to shared memory: read through a dynamic index
     // in parameter space, the arguments made the solve half as fast again
     __shared__ PcgArgs sa;
@@ -1667,7 +1671,7 @@ int newmark_rhs(Sim *s) {
 // (queried once per device and kept: no runtime queries while a stream is
 // being captured)
 constexpr int kMaxDevices = 64;
-template <bool BATCHED, bool REFINE>
+template <bool BATCHED, bool REFINE, int MINB = 4>
 static int coop_per_sm() {
     static int cache[kMaxDevices];   // 0: not queried, -1: unavailable
     int dev = 0, coop = 0, per_sm = 0;
@@ -1675,7 +1679,7 @@ static int coop_per_sm() {
     if (cache[dev]) return std::max(cache[dev], 0);
     cache[dev] = -1;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
-    cudaError_t e = BATCHED ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_batched<REFINE>, kThreads, 0)
+    cudaError_t e = BATCHED ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_batched<REFINE, MINB>, kThreads, 0)
                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_persistent<REFINE>, kThreads, 0);
     if (e != cudaSuccess) return 0;
     cache[dev] = per_sm > 0 ? per_sm : -1;
@@ -1749,7 +1753,7 @@ static int assign_blocks(PcgArgs *runs, int n_runs, int budget) {
 // One cooperative launch of the persistent PCG over n_runs solves on stream
 // st.  Results and failures reach the host through each run's CgState and
 // status word at the next synchronisation.
-int launch_pcg_runs(PcgArgs *runs, int n_runs, int blocks_per_sm, cudaStream_t st) {
+int launch_pcg_runs(PcgArgs *runs, int n_runs, int blocks_per_sm, cudaStream_t st, int build) {
     if (n_runs <= 0) return PIC_OK;
     if (n_runs > kMaxBatchRuns) {
         set_error("at most " + std::to_string(kMaxBatchRuns) + " solves per persistent launch");
@@ -1762,7 +1766,10 @@ int launch_pcg_runs(PcgArgs *runs, int n_runs, int blocks_per_sm, cudaStream_t s
             return PIC_ERR_INVALID_ARG;
         }
     int per_sm = one ? (refine ? coop_per_sm<false, true>() : coop_per_sm<false, false>())
-                     : (refine ? coop_per_sm<true, true>() : coop_per_sm<true, false>());
+                 : build == 1 ? (refine ? coop_per_sm<true, true, 3>() : coop_per_sm<true, false, 3>())
+                 : build == 2 ? (refine ? coop_per_sm<true, true, 6>() : coop_per_sm<true, false, 6>())
+                 : build == 3 ? (refine ? coop_per_sm<true, true, 8>() : coop_per_sm<true, false, 8>())
+                              : (refine ? coop_per_sm<true, true>() : coop_per_sm<true, false>());
     if (per_sm <= 0) {
         set_error("the persistent PCG needs a device with cooperative launch");
         return PIC_ERR_CUDA;
@@ -1782,7 +1789,10 @@ int launch_pcg_runs(PcgArgs *runs, int n_runs, int blocks_per_sm, cudaStream_t s
         FP_CUDA(cudaLaunchCooperativeKernel(k, G, kThreads, args, 0, st));
     } else {
         void *args[] = {&all};
-        const void *k = refine ? (const void *)k_pcg_batched<true> : (const void *)k_pcg_batched<false>;
+        const void *k = build == 1 ? (refine ? (const void *)k_pcg_batched<true, 3> : (const void *)k_pcg_batched<false, 3>)
+                      : build == 2 ? (refine ? (const void *)k_pcg_batched<true, 6> : (const void *)k_pcg_batched<false, 6>)
+                      : build == 3 ? (refine ? (const void *)k_pcg_batched<true, 8> : (const void *)k_pcg_batched<false, 8>)
+                                   : (refine ? (const void *)k_pcg_batched<true, 4> : (const void *)k_pcg_batched<false, 4>);
         FP_CUDA(cudaLaunchCooperativeKernel(k, G, kThreads, args, 0, st));
     }
     note_launch();
@@ -1831,6 +1841,17 @@ PcgArgs pcg_args_truncated(Sim *s, int iters) {
     const Mesh *m = s->mesh;
     return make_args(s, m->As, s->A_val.p, s->Dinv.p, s->rhs.p, s->x.p, s->cg_r.p, s->cg_z.p, s->cg_q.p, s->cg_p0.p,
                      s->cg_p1.p, s->cg_part.p, &s->dctl.p->cg, 0.0, 0.0, iters, nullptr, 0.0, true, true);
+}
+
+// The Newmark solve stopped after `iters` iterations (in MIXED, FP32
+// correction iterations) without an error: a fixed amount of work for timing.
+// It starts from the x it finds, so the caller zeroes x first.
+PcgArgs pcg_args_newmark_truncated(Sim *s, int iters) {
+    PcgArgs a = pcg_args_newmark(s);
+    a.max_iters = iters;
+    a.quiet = 1;
+    a.x_zero = 1;
+    return a;
 }
 
 // The Newmark solve.  MIXED refines in FP64 with FP32 correction solves

@@ -60,7 +60,12 @@ PRECONDITIONERS = {"jacobi": 0, "gnn": 1}
 class pic_batch_info_t(C.Structure):
     _fields_ = [("n_sims", C.c_int32), ("graph", C.c_int32), ("graph_steps", C.c_int32),
                 ("solver_blocks_per_sm", C.c_int32), ("graph_launches", C.c_int64), ("eager_steps", C.c_int64),
-                ("tune_ms", C.c_double * 3)]
+                ("tune_ms", C.c_double * 3), ("solver_build", C.c_int32), ("completion_blocks_per_sm", C.c_int32),
+                ("completion_build", C.c_int32), ("pad_", C.c_int32), ("tune_newmark_ms", C.c_double * 9),
+                ("tune_completion_ms", C.c_double * 9)]
+
+BATCH_BUILDS = ("64-register", "80-register", "40-register", "32-register")
+BATCH_TUNE_CANDIDATES = ((2, 0), (3, 0), (4, 0), (2, 1), (3, 1), (5, 2), (6, 2), (7, 3), (8, 3))   # (blocks/SM, build)
 
 
 class pic_diag(C.Structure):
@@ -423,7 +428,11 @@ class Batch:
         _check(_lib.pic_batch_info(self._h, C.byref(d)), "pic_batch_info")
         return {"n_sims": d.n_sims, "graph": d.graph, "graph_steps": d.graph_steps,
                 "solver_blocks_per_sm": d.solver_blocks_per_sm, "graph_launches": d.graph_launches,
-                "eager_steps": d.eager_steps, "tune_ms": list(d.tune_ms)}
+                "eager_steps": d.eager_steps, "tune_ms": list(d.tune_ms),
+                "solver_build": BATCH_BUILDS[d.solver_build],
+                "completion_blocks_per_sm": d.completion_blocks_per_sm,
+                "completion_build": BATCH_BUILDS[d.completion_build],
+                "tune_newmark_ms": list(d.tune_newmark_ms), "tune_completion_ms": list(d.tune_completion_ms)}
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

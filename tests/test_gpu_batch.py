@@ -1,7 +1,8 @@
 """Batched stepping: several independent runs of uneven size stepped together
 (one stream per run, one persistent launch per solve over all runs, six-step
-CUDA graphs) give exactly what stepping each run alone gives, each run still
-conserves charge, and each member agrees with the FP64 oracle.
+CUDA graphs, tuned solver launch shapes) give exactly what stepping each run
+alone gives, each run still conserves charge, and each member agrees with the
+FP64 oracle.
 """
 import numpy as np
 import pytest
@@ -44,6 +45,13 @@ def test_batch_equals_individual_steps(F, precision):
         s.step(steps)
     info = batch.info()
     assert info["graph"] == 1 and info["graph_launches"] == 2, info
+    # the tuner timed every candidate of both solves (or took an earlier
+    # batch's choice for this shape) and kept one of each
+    times = info["tune_newmark_ms"] + info["tune_completion_ms"]
+    assert all(t > 0 for t in times) or all(t == -1 for t in times), info
+    cands = {(b, F.BATCH_BUILDS[k]) for b, k in F.BATCH_TUNE_CANDIDATES}
+    assert (info["solver_blocks_per_sm"], info["solver_build"]) in cands, info
+    assert (info["completion_blocks_per_sm"], info["completion_build"]) in cands, info
     for a, b in zip(solo, memb):
         for f in ("E", "B", "RHO", "G"):
             np.testing.assert_array_equal(a.field(f), b.field(f))
