@@ -103,6 +103,33 @@ def test_particle_phase_many_crossings(F, oracle_lib):
     assert rel_err(gsim.field("WALL"), osim.field("WALL")) <= 1e-12
 
 
+@pytest.mark.parametrize("precision", ["plain", "mixed"])
+def test_record_buffer_grows(F, oracle_lib, precision):
+    """200,000 particles crossing ~4 cells per step write ~10x more crossing
+    records than the initial buffer holds (capacity / 8, at least 65,536):
+    the first push overflows it, the buffer grows and the push runs again;
+    the result is the oracle's (PLAIN at 1e-12, MIXED at its tolerance)."""
+    box, om, osim, gsim = frozen_field_case(F, oracle_lib, precision=precision, n=200_000, cells=6, speed=4.0,
+                                            seed=12)
+    osim.particle_phase()
+    gsim.particle_phase()
+    gx, gv, gt, gid = gsim.particles()
+    ox, ov, ot, alive = osim.particles()
+    ids = np.where(alive)[0]
+    if precision == "plain":
+        compare_particles((gx, gv, gt, gid), (ox, ov, ot, alive), 1.0)
+        tol = 1e-12
+    else:
+        common = np.intersect1d(gid, ids)
+        assert len(common) >= 0.999 * len(ids)
+        gi = np.searchsorted(gid, common)
+        assert np.abs(gx[gi] - ox[common]).max() <= 1e-5
+        tol = 2e-5
+    for name in ("DG", "RHO", "WALL"):
+        assert rel_err(gsim.field(name), osim.field(name)) <= tol, name
+    assert gsim.diag()["status"] == 0
+
+
 @pytest.mark.parametrize("pusher", ["ab2", "ab4"])
 def test_particle_phase_adams_bashforth(F, oracle_lib, pusher):
     box, om, osim, gsim = frozen_field_case(F, oracle_lib, pusher=pusher, n=1500, seed=4)
