@@ -1201,13 +1201,14 @@ timeout:
 // Completion preconditioned by multigrid.  Flexible PCG (Polak-Ribiere beta,
 // since the preconditioner is applied in FP32) in FP64 on the node Laplacian
 // L, with one V-cycle of the smoothed-aggregation hierarchy of multigrid.cpp
-// as preconditioner: damped Jacobi before and after the coarse correction on
-// levels 0 and 1, the dense inverse on level 2.  The V-cycle runs on the
+// as preconditioner: one damped-Jacobi sweep before and after the coarse
+// correction on level 0, two Chebyshev steps before and after it on level 1,
+// the dense inverse on level 2.  The V-cycle runs on the
 // scaled operators s0 L in FP32 with the residual divided by its maximum
 // (sigma), so z = sigma s0 V(r / sigma).  One persistent cooperative launch:
 // every phase that reads other rows' values starts after a grid barrier, and
 // the reductions combine in the last block to arrive (fixed order).  An
-// iteration has ten such phases: the phases are bound by the latency of
+// iteration has twelve such phases: the phases are bound by the latency of
 // dependent loads, so a sweep and the residual that follows it share a pass
 // where the neighbours' values can be formed on the fly, and q = L p comes as
 // L z + beta q right after the preconditioner.  Waits are bounded like those
@@ -1230,7 +1231,7 @@ struct MgArgs {
     double s0;
     const double *b;
     double *x, *r, *p, *q, *z, *zo;
-    float *r32, *z0, *t0, *r1, *z1, *z1b, *t1, *r2, *z2;
+    float *r32, *z0, *t0, *r1, *z1, *z1b, *t1, *d1, *r2, *z2;
     double *part;
     CgState *st;
     GridBarrier *gb;
@@ -1239,6 +1240,18 @@ struct MgArgs {
     uint32_t *status;
     int max_iters, spin_limit;
 };
+
+// Level-1 smoother: two steps of the Chebyshev iteration for D1^-1 L1 on
+// [rho1 / 8, rho1], rho1 the (over)estimate behind w1 = 1 / (rho1 d1).  With
+// theta, delta the centre and half-width of that interval (in units of rho1),
+// sigma = theta / delta, c0 = 1 / sigma, c1 = 1 / (2 sigma - c0):
+//   d = D^-1 res / theta = kCh1 w1 res,  z += d,  res -= L1 d,
+//   d = c1 c0 d + (2 c1 / delta) D^-1 res = kCh2a d + kCh2b w1 res,  z += d.
+// (A CPU prototype on the 64^3 mesh's Laplacian: 29 -> 20 PCG iterations
+// against one damped-Jacobi sweep before and after.)
+constexpr double kChTheta = (1.0 + 0.125) / 2.0, kChDelta = (1.0 - 0.125) / 2.0;
+constexpr double kChSigma = kChTheta / kChDelta, kChC0 = 1.0 / kChSigma, kChC1 = 1.0 / (2.0 * kChSigma - kChC0);
+constexpr float kCh1 = (float)(1.0 / kChTheta), kCh2a = (float)(kChC1 * kChC0), kCh2b = (float)(2.0 * kChC1 / kChDelta);
 
 __device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
@@ -1336,21 +1349,35 @@ __global__ void __launch_bounds__(kThreads, 4) k_mg_pcg(const MgArgs a) {
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
             // (coarse rows: half a warp per row, two rows per warp at a time)
             const int hw = gt >> 4, nhw = G >> 4, hl = lane & 15;
-            // V2: r1 = P0^T t0, z1 = w1 r1
+            // V2: r1 = P0^T t0, the first Chebyshev step z1 = kCh1 w1 r1
             for (int c0 = hw - (hw & 1); c0 < a.n1; c0 += nhw) {
                 const int c = c0 + (hw & 1);
                 const float sum = half_row_dot(a.r0p, a.r0c, a.r0v, a.t0, c, c < a.n1, hl);
                 if (hl == 0 && c < a.n1) {
                     a.r1[c] = sum;
-                    a.z1[c] = a.w1[c] * sum;
+                    a.z1[c] = kCh1 * a.w1[c] * sum;
                 }
             }
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
-            // V3: t1 = r1 - L1 z1
+            // V3: res = r1 - L1 z1 (into t1), the second step d1 = kCh2a z1 +
+            // kCh2b w1 res, z1 + d1 (into z1b, since z1 is still read here)
             for (int c0 = hw - (hw & 1); c0 < a.n1; c0 += nhw) {
                 const int c = c0 + (hw & 1);
                 const float sum = half_row_dot(a.l1p, a.l1c, a.l1v, a.z1, c, c < a.n1, hl);
-                if (hl == 0 && c < a.n1) a.t1[c] = a.r1[c] - sum;
+                if (hl == 0 && c < a.n1) {
+                    const float res = a.r1[c] - sum, zc = a.z1[c];
+                    const float d = kCh2a * zc + kCh2b * a.w1[c] * res;
+                    a.t1[c] = res;
+                    a.d1[c] = d;
+                    a.z1b[c] = zc + d;
+                }
+            }
+            if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
+            // V3b: the residual after the pre-smoothing, t1 = res - L1 d1
+            for (int c0 = hw - (hw & 1); c0 < a.n1; c0 += nhw) {
+                const int c = c0 + (hw & 1);
+                const float sum = half_row_dot(a.l1p, a.l1c, a.l1v, a.d1, c, c < a.n1, hl);
+                if (hl == 0 && c < a.n1) a.t1[c] -= sum;
             }
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
             // V4: r2 = sum of t1 over each level-2 aggregate
@@ -1370,9 +1397,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_mg_pcg(const MgArgs a) {
                 if (lane == 0) a.z2[g] = s;
             }
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
-            // V6: coarse correction and post-smoothing of level 1 in one pass:
-            // z1b = (z1 + z2[agg]) + w1 (r1 - L1 (z1 + z2[agg])), the corrected
-            // neighbours formed on the fly
+            // V6: coarse correction and the first post-smoothing step in one
+            // pass: zc = z1b + z2[agg] (the corrected neighbours formed on the
+            // fly), res = r1 - L1 zc (into t1), d1 = kCh1 w1 res, zc + d1 (into z1)
             for (int c0 = hw - (hw & 1); c0 < a.n1; c0 += nhw) {
                 const int c = c0 + (hw & 1);
                 const bool ok = c < a.n1;
@@ -1390,14 +1417,28 @@ __global__ void __launch_bounds__(kThreads, 4) k_mg_pcg(const MgArgs a) {
                             v[u] = in ? a.l1v[k] : 0.0f;
                         }
 #pragma unroll
-                        for (int u = 0; u < 4; u++) s = fmaf(v[u], a.z1[cc[u]] + a.z2[a.agg1[cc[u]]], s);
+                        for (int u = 0; u < 4; u++) s = fmaf(v[u], a.z1b[cc[u]] + a.z2[a.agg1[cc[u]]], s);
                     }
                 }
 #pragma unroll
                 for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
                 if (hl == 0 && ok) {
-                    const float zc = a.z1[c] + a.z2[a.agg1[c]];
-                    a.z1b[c] = zc + a.w1[c] * (a.r1[c] - s);
+                    const float zc = a.z1b[c] + a.z2[a.agg1[c]];
+                    const float res = a.r1[c] - s, d = kCh1 * a.w1[c] * res;
+                    a.t1[c] = res;
+                    a.d1[c] = d;
+                    a.z1[c] = zc + d;
+                }
+            }
+            if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
+            // V6b: the second post-smoothing step, res -= L1 d1,
+            // z1b = z1 + kCh2a d1 + kCh2b w1 res
+            for (int c0 = hw - (hw & 1); c0 < a.n1; c0 += nhw) {
+                const int c = c0 + (hw & 1);
+                const float sum = half_row_dot(a.l1p, a.l1c, a.l1v, a.d1, c, c < a.n1, hl);
+                if (hl == 0 && c < a.n1) {
+                    const float res = a.t1[c] - sum;
+                    a.z1b[c] = a.z1[c] + (kCh2a * a.d1[c] + kCh2b * a.w1[c] * res);
                 }
             }
             if (!grid_barrier(a.gb, ++epoch, nb, lim)) goto timeout;
@@ -1941,7 +1982,7 @@ int mg_completion(Sim *s) {
     const int n0 = m->n_int_nodes, n1 = m->mg_n1, n2 = m->mg_n2;
     if (n0 == 0) return PIC_OK;
     if (!s->mg32.p) {
-        int rc = s->mg32.alloc(3 * (size_t)n0 + 4 * (size_t)n1 + 2 * (size_t)n2);
+        int rc = s->mg32.alloc(3 * (size_t)n0 + 5 * (size_t)n1 + 2 * (size_t)n2);
         if (rc) return rc;
     }
     Control *dc = s->dctl.p;
@@ -1986,7 +2027,8 @@ int mg_completion(Sim *s) {
     a.z1 = a.r1 + n1;
     a.z1b = a.z1 + n1;
     a.t1 = a.z1b + n1;
-    a.r2 = a.t1 + n1;
+    a.d1 = a.t1 + n1;
+    a.r2 = a.d1 + n1;
     a.z2 = a.r2 + n2;
     a.part = s->l_part.p;
     a.st = &dc->lap;
