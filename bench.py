@@ -948,7 +948,7 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=60)
     ap.add_argument("--skip-larmor", action="store_true", help="do not run the single-electron leg")
     ap.add_argument("--larmor-cells", type=int, default=20)
-    ap.add_argument("--larmor-steps", type=int, default=2000)
+    ap.add_argument("--larmor-steps", type=int, default=10000)
     ap.add_argument("--skip-sweep", action="store_true", help="do not run the Table I pusher sweep")
     ap.add_argument("--skip-mixed-error", action="store_true", help="do not compare MIXED with the oracle")
     args = ap.parse_args()
