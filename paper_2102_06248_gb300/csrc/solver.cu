@@ -691,7 +691,9 @@ __global__ void __launch_bounds__(kThreads) k_max_abs_sum(int n, const double *_
 //    integer order is its numeric order, so it costs no FP64 instruction.
 // Every thread owns the same rows (row 32*slice + lane of its warp's slices)
 // in the vector phase and in the SpMV, so a thread reads back only what it
-// wrote itself, except the gathered u, which is read through L2 (__ldcg).
+// wrote itself, except the gathered vector (u, or the correction iterate):
+// plain loads in the two-slice form below, reads through L2 (__ldcg) in the
+// one-slice FP64 form; both see the other blocks' writes after the barrier.
 // The rest is latency work: the slice headers of a block's slices sit in
 // shared memory for the whole solve (the next one is read while the current
 // slice is summed), and the grid barriers are one release-add on a counter
@@ -896,7 +898,13 @@ struct SolveCtx {
     // SpMV over the warp's slices with values Av: f(i, sum_j A_ij v_j, v_i):
     // the form of the MIXED refinement (FP32 corrections, FP64 residuals).
     // Two of the warp's slices at a time (two independent chains of loads in
-    // flight); the row's own v_i is read with the row's entries.
+    // flight); the row's own v_i is read with the row's entries.  The matrix
+    // streams through once per iteration and is loaded evict-first, while
+    // the vector's gathers are plain loads that L1 may keep (coherent: the
+    // grid barrier before each phase is a release/acquire pair, so they see
+    // the other blocks' writes; the read-only path would not be): 4.79 ->
+    // 4.55 ms per MIXED Newmark solve on the 64^3 plasma ball, against
+    // 4.62 ms with the gathers bypassing L1.
     template <typename T, typename F>
     __device__ __forceinline__ void spmv(const T *__restrict__ Av, const T *v, F f) const {
         const int *__restrict__ col = a->col;
@@ -916,13 +924,13 @@ struct SolveCtx {
             int j = 0;
 #pragma unroll kU
             for (; j < wmin; j++) {
-                acca = fma(Av[ka + 32 * j], __ldcg(v + col[ka + 32 * j]), acca);
-                accb = fma(Av[kb + 32 * j], __ldcg(v + col[kb + 32 * j]), accb);
+                acca = fma(__ldcs(Av + ka + 32 * j), v[__ldcs(col + ka + 32 * j)], acca);
+                accb = fma(__ldcs(Av + kb + 32 * j), v[__ldcs(col + kb + 32 * j)], accb);
             }
 #pragma unroll 4
-            for (int ja = j; ja < wida; ja++) acca = fma(Av[ka + 32 * ja], __ldcg(v + col[ka + 32 * ja]), acca);
+            for (int ja = j; ja < wida; ja++) acca = fma(__ldcs(Av + ka + 32 * ja), v[__ldcs(col + ka + 32 * ja)], acca);
 #pragma unroll 4
-            for (int jb = j; jb < widb; jb++) accb = fma(Av[kb + 32 * jb], __ldcg(v + col[kb + 32 * jb]), accb);
+            for (int jb = j; jb < widb; jb++) accb = fma(__ldcs(Av + kb + 32 * jb), v[__ldcs(col + kb + 32 * jb)], accb);
             if (ia < n) f(ia, acca, va);
             if (hb && ib < n) f(ib, accb, vb);
         }
