@@ -919,8 +919,8 @@ struct SolveCtx {
             const T vb = hb && ib < n ? v[ib] : (T)0;
             T acca = 0, accb = 0;
             const int ka = offa + lane, kb = offb + lane, wmin = min(wida, widb);
-            // joint unroll: 4 for FP32 values, 8 for FP64 (measured best of 2, 4, 8)
-            constexpr int kU = std::is_same<T, float>::value ? 4 : 8;
+            // joint unroll: 2 for FP32 values, 8 for FP64 (measured best of 2, 4, 8)
+            constexpr int kU = std::is_same<T, float>::value ? 2 : 8;
             int j = 0;
 #pragma unroll kU
             for (; j < wmin; j++) {
