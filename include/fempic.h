@@ -381,9 +381,10 @@ int pic_gnn_loss_grad(pic_sim *sim, const double *r_edges, double *loss, double 
  * pic_step on each member: bitwise when every member's solve gets the
  * blocks it would get alone (then the kernels and reduction orders are the
  * same), otherwise equal to the solve tolerance.  A member whose mesh has
- * 8,192 or more interior nodes, which pic_step completes with the multigrid-
- * preconditioned solve, is completed in the batch by the batched Jacobi-PCG:
- * equal to the completion tolerance.
+ * 8,192 or more interior nodes completes with the multigrid-preconditioned
+ * solve as under pic_step; the batch runs all completions in one launch (the
+ * multigrid members' beside the others' Jacobi-PCG), and the tuner then
+ * picks only that launch's blocks per SM (one build).
  * Members: 1..64 initialised simulations on the current device, Jacobi
  * preconditioner; the mesh and particle arrays stay owned by each member.
  * ------------------------------------------------------------------------- */

@@ -54,6 +54,11 @@ struct pic_batch {
     // e.g. the choice came from an earlier batch of the same shape)
     double tune_ms[kTuneCands] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
     double tune_gc_ms[kTuneCands] = {-1, -1, -1, -1, -1, -1, -1, -1, -1};
+    // members with a multigrid hierarchy: the completions run as one launch
+    // of k_completion_batched over a device table of run records
+    bool use_mg = false;
+    void *ctable = nullptr;
+    int ct_runs = 0, ct_blocks = 0, ct_bps = -1;   // the table's runs, blocks, and the blocks/SM it was built for
     long long graph_launches = 0, eager_steps = 0;
 };
 
@@ -83,6 +88,26 @@ int join_all(pic_batch *b) {
     return PIC_OK;
 }
 
+// a multigrid completion reads z_old in its first iteration: zero it
+int zero_mg_history(Sim *s) {
+    const Mesh *m = s->mesh;
+    if (m->mg_levels > 0 && m->n_int_nodes > 0 && m->n_int_edges > 0)
+        FP_CUDA(cudaMemsetAsync(s->l_p1.p, 0, sizeof(double) * m->n_int_nodes, s->stream));
+    return PIC_OK;
+}
+
+// (re)builds the completion table for the current completion blocks/SM
+int completion_table(pic_batch *b) {
+    if (!b->use_mg || b->ct_bps == b->gc_blocks_per_sm) return PIC_OK;
+    std::vector<Sim *> sims;
+    for (auto *ps : b->sims) sims.push_back(&ps->s);
+    int rc = prepare_completion_table(sims.data(), (int)sims.size(), b->gc_blocks_per_sm, b->ctable, &b->ct_runs,
+                                      &b->ct_blocks);
+    if (rc) return rc;
+    b->ct_bps = b->gc_blocks_per_sm;
+    return PIC_OK;
+}
+
 // one step of every simulation, nothing waiting on the host
 int batch_step_once(pic_batch *b) {
     const int n = (int)b->sims.size();
@@ -97,13 +122,19 @@ int batch_step_once(pic_batch *b) {
         if (ps->s.mesh->n_int_edges > 0) runs.push_back(pcg_args_newmark(&ps->s));
     if ((rc = launch_pcg_runs(runs.data(), (int)runs.size(), b->blocks_per_sm, b->ms, b->build))) return rc;
     if ((rc = fork_all(b))) return rc;
-    for (auto *ps : b->sims)
+    for (auto *ps : b->sims) {
         if ((rc = gc_prepare(&ps->s))) return rc;
+        if (b->use_mg && (rc = zero_mg_history(&ps->s))) return rc;
+    }
     if ((rc = join_all(b))) return rc;
-    runs.clear();
-    for (auto *ps : b->sims)
-        if (ps->s.mesh->n_int_edges > 0 && ps->s.mesh->n_int_nodes > 0) runs.push_back(pcg_args_completion(&ps->s));
-    if ((rc = launch_pcg_runs(runs.data(), (int)runs.size(), b->gc_blocks_per_sm, b->ms, b->gc_build))) return rc;
+    if (b->use_mg) {
+        if ((rc = launch_completion_table(b->ctable, b->ct_runs, b->ct_blocks, b->ms))) return rc;
+    } else {
+        runs.clear();
+        for (auto *ps : b->sims)
+            if (ps->s.mesh->n_int_edges > 0 && ps->s.mesh->n_int_nodes > 0) runs.push_back(pcg_args_completion(&ps->s));
+        if ((rc = launch_pcg_runs(runs.data(), (int)runs.size(), b->gc_blocks_per_sm, b->ms, b->gc_build))) return rc;
+    }
     if ((rc = fork_all(b))) return rc;
     for (auto *ps : b->sims)
         if ((rc = step_fields_end(&ps->s))) return rc;
@@ -119,8 +150,11 @@ int batch_step_once(pic_batch *b) {
 // once to warm up and once timed:
 // the Newmark solve stopped after 40 iterations from x = 0 (x is rewritten
 // before the next solve), and the completion's solve of its last defect to
-// its tolerance.  The fastest of each is kept for batches of the same shape
-// (number of members, total rows, refinement or FP64 Newmark solve).
+// its tolerance.  When members have a multigrid hierarchy, the completions
+// run as one launch of the combined kernel, which has one build: only its
+// blocks per SM (2, 3, 4) are timed.  The fastest of each is kept for
+// batches of the same shape (number of members, total rows, refinement or
+// FP64 Newmark solve, multigrid members or not).
 int autotune(pic_batch *b) {
     long long rows = 0;
     int refine = 0;
@@ -128,7 +162,7 @@ int autotune(pic_batch *b) {
         rows += ps->s.mesh->n_int_edges;
         if (ps->s.mixed) refine = 1;
     }
-    const std::pair<std::pair<int, long long>, int> key({(int)b->sims.size(), rows}, refine);
+    const std::pair<std::pair<int, long long>, int> key({(int)b->sims.size(), rows}, 2 * refine + (b->use_mg ? 1 : 0));
     {
         std::lock_guard<std::mutex> lock(g_tune_mutex);
         auto it = g_tuned.find(key);
@@ -137,7 +171,7 @@ int autotune(pic_batch *b) {
             b->build = it->second.build;
             b->gc_blocks_per_sm = it->second.gc_bps;
             b->gc_build = it->second.gc_build;
-            return PIC_OK;
+            return completion_table(b);
         }
     }
     cudaEvent_t e0, e1;
@@ -149,7 +183,26 @@ int autotune(pic_batch *b) {
         float best_ms = 1e30f;
         for (int c = 0; c < kTuneCands && rc == PIC_OK; c++) {
             float ms = 0.f;
+            // the combined completion launch has one build (64 registers)
+            const bool mg_launch = solve == 1 && b->use_mg;
+            if (mg_launch && kTuneBuild[c] != 0) continue;
             for (int rep = 0; rep < 2 && rc == PIC_OK; rep++) {
+                if (mg_launch) {
+                    b->gc_blocks_per_sm = kTuneBps[c];
+                    if ((rc = completion_table(b))) break;
+                    for (auto *ps : b->sims) {
+                        const Mesh *m = ps->s.mesh;
+                        if (m->mg_levels > 0 && m->n_int_nodes > 0 && m->n_int_edges > 0 &&
+                            cudaMemsetAsync(ps->s.l_p1.p, 0, sizeof(double) * m->n_int_nodes, b->ms) != cudaSuccess)
+                            rc = PIC_ERR_CUDA;
+                    }
+                    if (!rc && cudaEventRecord(e0, b->ms) != cudaSuccess) rc = PIC_ERR_CUDA;
+                    if (!rc) rc = launch_completion_table(b->ctable, b->ct_runs, b->ct_blocks, b->ms);
+                    if (!rc && cudaEventRecord(e1, b->ms) != cudaSuccess) rc = PIC_ERR_CUDA;
+                    if (!rc && cudaEventSynchronize(e1) != cudaSuccess) rc = PIC_ERR_CUDA;
+                    if (!rc && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = PIC_ERR_CUDA;
+                    continue;
+                }
                 std::vector<PcgArgs> runs;
                 for (auto *ps : b->sims) {
                     Sim *s = &ps->s;
@@ -189,9 +242,11 @@ int autotune(pic_batch *b) {
         set_error("batch tuning: a CUDA call failed");
         return rc;
     }
-    std::lock_guard<std::mutex> lock(g_tune_mutex);
-    g_tuned[key] = Tuned{b->blocks_per_sm, b->build, b->gc_blocks_per_sm, b->gc_build};
-    return PIC_OK;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mutex);
+        g_tuned[key] = Tuned{b->blocks_per_sm, b->build, b->gc_blocks_per_sm, b->gc_build};
+    }
+    return completion_table(b);   // the table for the chosen blocks/SM
 }
 
 // The buffers a step rotates, to undo a capture that failed part-way (the
@@ -332,7 +387,13 @@ int pic_batch_create(pic_sim *const *sims, int32_t n, pic_batch **out) {
         return PIC_ERR_OOM;
     }
     b->sims.assign(sims, sims + n);
+    {
+        std::vector<Sim *> ss;
+        for (auto *ps : b->sims) ss.push_back(&ps->s);
+        b->use_mg = completion_uses_multigrid(ss.data(), n);
+    }
     cudaError_t e = cudaStreamCreateWithFlags(&b->ms, cudaStreamNonBlocking);
+    if (e == cudaSuccess && b->use_mg) e = cudaMalloc(&b->ctable, completion_table_bytes());
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     for (int i = 0; i < n && e == cudaSuccess; i++) {
         cudaStream_t s = nullptr;
@@ -361,6 +422,7 @@ void pic_batch_destroy(pic_batch *b) {
         if (ev) cudaEventDestroy(ev);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->ms) cudaStreamDestroy(b->ms);
+    if (b->ctable) cudaFree(b->ctable);
     delete b;
 }
 
@@ -399,6 +461,7 @@ int pic_batch_step(pic_batch *b, int32_t nsteps) {
     }
     int rc = PIC_OK;
     for (int q = 0; q < n && rc == PIC_OK; q++) rc = particles_batch_prepare(&b->sims[q]->s);
+    if (rc == PIC_OK) rc = completion_table(b);   // nothing in flight reads it (synchronised above)
     bool ramp_done = true;
     for (auto *ps : b->sims)
         if (ps->s.ab && ps->s.nhist < ps->s.hist_levels) ramp_done = false;

@@ -267,6 +267,12 @@ int newmark_truncated_residual(Sim *s, int iters, double *r_out);
 PcgArgs pcg_args_newmark(Sim *s);
 PcgArgs pcg_args_truncated(Sim *s, int iters);
 PcgArgs pcg_args_newmark_truncated(Sim *s, int iters);
+// batched completion (solver.cu): multigrid or Jacobi-PCG per member, one launch
+size_t completion_table_bytes();
+bool completion_uses_multigrid(Sim *const *sims, int n);
+int prepare_completion_table(Sim *const *sims, int n, int blocks_per_sm, void *table_dev, int *n_runs,
+                             int *total_blocks);
+int launch_completion_table(const void *table_dev, int n_runs, int total_blocks, cudaStream_t st);
 PcgArgs pcg_args_completion(Sim *s);
 // build: the batched kernel's build (0: 64 registers, up to four blocks per
 // SM; 1: 80 registers, up to three; 2: 40 registers, up to six; 3: 32

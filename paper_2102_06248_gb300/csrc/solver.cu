@@ -1296,10 +1296,10 @@ __device__ __forceinline__ float half_row_dot(const int *__restrict__ ptr, const
     return s;
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_mg_pcg(const MgArgs a) {
+// the whole solve, run by block `bid` of the nb blocks that own it
+__device__ __forceinline__ void mg_body(const MgArgs &a, const int nb, const int bid) {
     __shared__ double shv[4 * kThreads];
     __shared__ unsigned long long shm[kThreads];
-    const int nb = gridDim.x, bid = blockIdx.x;
     const int G = nb * kThreads, gt = bid * kThreads + threadIdx.x;
     const int lane = threadIdx.x & 31, nw = G >> 5, gw = gt >> 5;
     const long lim = a.spin_limit;
@@ -1548,6 +1548,8 @@ timeout:
         atomicOr(a.status, (uint32_t)ST_BARRIER);
     }
 }
+
+__global__ void __launch_bounds__(kThreads, 4) k_mg_pcg(const MgArgs a) { mg_body(a, gridDim.x, blockIdx.x); }
 
 // one solve per launch (its arguments passed by value)
 template <bool REFINE>
@@ -1985,16 +1987,16 @@ int laplacian_solve(Sim *s, const double *rhs_int, double *x_int, double tol, co
 
 // The completion with the multigrid preconditioner (mesh with a hierarchy):
 // defect in l_b, solution in l_x, the same stopping rule as the Jacobi-PCG.
-int mg_completion(Sim *s) {
+// the multigrid completion's arguments (allocates its FP32 scratch on first use)
+static int mg_args(Sim *s, MgArgs &a) {
     const Mesh *m = s->mesh;
     const int n0 = m->n_int_nodes, n1 = m->mg_n1, n2 = m->mg_n2;
-    if (n0 == 0) return PIC_OK;
     if (!s->mg32.p) {
         int rc = s->mg32.alloc(3 * (size_t)n0 + 5 * (size_t)n1 + 2 * (size_t)n2);
         if (rc) return rc;
     }
     Control *dc = s->dctl.p;
-    MgArgs a{};
+    a = MgArgs{};
     a.n0 = n0;
     a.n1 = n1;
     a.n2 = n2;
@@ -2047,6 +2049,15 @@ int mg_completion(Sim *s) {
     a.status = &dc->status;
     a.max_iters = 2000;
     a.spin_limit = s->cfg.barrier_spin_limit > 0 ? s->cfg.barrier_spin_limit : (int)kSpinLimit;
+    return PIC_OK;
+}
+
+int mg_completion(Sim *s) {
+    const int n0 = s->mesh->n_int_nodes;
+    if (n0 == 0) return PIC_OK;
+    MgArgs a;
+    int rc = mg_args(s, a);
+    if (rc) return rc;
     // z_old starts at zero (the first beta is 0 and ignores it, but it is read)
     FP_CUDA(cudaMemsetAsync(s->l_p1.p, 0, sizeof(double) * n0, s->stream));
     static int per_sm_cache[kMaxDevices];
@@ -2073,6 +2084,158 @@ int mg_completion(Sim *s) {
     { k_reset_gbar<<<1, 1, 0, s->stream>>>(a.gb); note_launch(); }
     void *args[] = {&a};
     FP_CUDA(cudaLaunchCooperativeKernel((const void *)k_mg_pcg, blocks, kThreads, args, 0, s->stream));
+    note_launch();
+    return PIC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Completion solves of a batch in one cooperative launch: members whose mesh
+// has a multigrid hierarchy run the multigrid-preconditioned PCG (as
+// pic_step does), the others Jacobi-PCG; run r owns blocks [block0, block0 +
+// blocks), its own grid barrier and partials.  The run records do not change
+// from step to step (every pointer is a member's fixed buffer), so the table
+// is written to device memory once, outside any stream capture, and the
+// launches (also the captured ones) only read it.
+// ---------------------------------------------------------------------------
+struct CompletionRun {
+    int kind;            // 1: multigrid, 0: Jacobi-PCG
+    int block0, blocks, pad;
+    PcgArgs pcg;
+    MgArgs mg;
+};
+struct CompletionTable {
+    int n_runs, total_blocks;
+    CompletionRun run[kMaxBatchRuns];
+};
+
+__global__ void __launch_bounds__(kThreads, 4) k_completion_batched(const CompletionTable *__restrict__ T) {
+    // the block's run record in shared memory (read through a dynamic index
+    // from global memory, every use would be a load)
+    __shared__ __align__(16) CompletionRun sr;
+    __shared__ int s_ri;
+    if (threadIdx.x == 0) {
+        int ri = 0;
+        while (ri + 1 < T->n_runs && (int)blockIdx.x >= T->run[ri + 1].block0) ri++;
+        s_ri = ri;
+    }
+    __syncthreads();
+    {
+        const int *src = reinterpret_cast<const int *>(&T->run[s_ri]);
+        int *dst = reinterpret_cast<int *>(&sr);
+        for (int k = threadIdx.x; k < (int)(sizeof(CompletionRun) / sizeof(int)); k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    if (sr.kind) mg_body(sr.mg, sr.blocks, (int)blockIdx.x - sr.block0);
+    else pcg_body<false>(sr.pcg, sr.blocks, (int)blockIdx.x - sr.block0);
+}
+
+__global__ void k_reset_completion_barriers(const CompletionTable *__restrict__ T) {
+    const int r = threadIdx.x;
+    if (r < T->n_runs) {
+        GridBarrier *gb = T->run[r].kind ? T->run[r].mg.gb : T->run[r].pcg.gb;
+        gb->count = 0;
+        gb->flag = 0;
+        gb->timeout = 0;
+    }
+}
+
+size_t completion_table_bytes() { return sizeof(CompletionTable); }
+
+bool completion_uses_multigrid(Sim *const *sims, int n) {
+    for (int i = 0; i < n; i++)
+        if (sims[i]->mesh->mg_levels > 0 && sims[i]->mesh->n_int_nodes > 0 && sims[i]->mesh->n_int_edges > 0) return true;
+    return false;
+}
+
+// Fills and uploads the table for the members with a completion to solve
+// (synchronously: call with nothing in flight that reads the table).  Blocks
+// go to the runs in proportion to their interior nodes' slices, at most one
+// warp per slice, up to blocks_per_sm (0: as many as fit) on every SM.
+int prepare_completion_table(Sim *const *sims, int n, int blocks_per_sm, void *table_dev, int *n_runs,
+                             int *total_blocks) {
+    static int per_sm_cache[kMaxDevices];
+    int dev = 0;
+    FP_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("batched completion: device index out of range");
+        return PIC_ERR_CUDA;
+    }
+    if (!per_sm_cache[dev]) {
+        int per_sm = 0, coop = 0;
+        FP_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        FP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_completion_batched, kThreads, 0));
+        per_sm_cache[dev] = (coop && per_sm > 0) ? per_sm : -1;
+    }
+    if (per_sm_cache[dev] < 0) {
+        set_error("the batched completion needs a device with cooperative launch");
+        return PIC_ERR_CUDA;
+    }
+    const int per_sm = blocks_per_sm > 0 ? std::min(per_sm_cache[dev], blocks_per_sm) : per_sm_cache[dev];
+    const int budget = per_sm * sm_count();
+    std::vector<CompletionTable> host(1);
+    CompletionTable &T = host[0];
+    std::memset(&T, 0, sizeof(T));
+    std::vector<long> slices;
+    for (int i = 0; i < n; i++) {
+        Sim *s = sims[i];
+        const Mesh *m = s->mesh;
+        if (m->n_int_edges == 0 || m->n_int_nodes == 0) continue;
+        CompletionRun &r = T.run[T.n_runs++];
+        if (m->mg_levels > 0) {
+            r.kind = 1;
+            int rc = mg_args(s, r.mg);
+            if (rc) return rc;
+        } else {
+            r.kind = 0;
+            r.pcg = pcg_args_completion(s);
+        }
+        slices.push_back(std::max(1, (m->n_int_nodes + 31) / 32));
+    }
+    if (T.n_runs > budget) {
+        set_error("more batched solves than co-resident blocks");
+        return PIC_ERR_INVALID_ARG;
+    }
+    long want_total = 0, total_slices = 0;
+    std::vector<int> want(T.n_runs), got(T.n_runs);
+    for (int r = 0; r < T.n_runs; r++) {
+        want[r] = (int)std::max(1L, std::min((long)kMaxPcgBlocks, (slices[r] + kSlicesPerBlock - 1) / kSlicesPerBlock));
+        want_total += want[r];
+        total_slices += slices[r];
+    }
+    long total = 0;
+    for (int r = 0; r < T.n_runs; r++) {
+        got[r] = want_total <= budget ? want[r]
+                                      : std::max(1, std::min(want[r], (int)((double)budget * slices[r] / total_slices)));
+        total += got[r];
+    }
+    while (total > budget) {
+        int big = 0;
+        for (int r = 1; r < T.n_runs; r++)
+            if (got[r] > got[big]) big = r;
+        got[big]--;
+        total--;
+    }
+    int b0 = 0;
+    for (int r = 0; r < T.n_runs; r++) {
+        T.run[r].block0 = b0;
+        T.run[r].blocks = got[r];
+        b0 += got[r];
+    }
+    T.total_blocks = b0;
+    FP_CUDA(cudaMemcpy(table_dev, &T, sizeof(T), cudaMemcpyHostToDevice));
+    *n_runs = T.n_runs;
+    *total_blocks = T.total_blocks;
+    return PIC_OK;
+}
+
+// One launch of the table's solves on st (the members' l_p1 zeroed first by
+// the caller for the multigrid runs).  total_blocks: the table's block count.
+int launch_completion_table(const void *table_dev, int n_runs, int total_blocks, cudaStream_t st) {
+    if (n_runs <= 0) return PIC_OK;
+    const CompletionTable *T = static_cast<const CompletionTable *>(table_dev);
+    { k_reset_completion_barriers<<<1, kMaxBatchRuns, 0, st>>>(T); note_launch(); }
+    void *args[] = {&T};
+    FP_CUDA(cudaLaunchCooperativeKernel((const void *)k_completion_batched, total_blocks, kThreads, args, 0, st));
     note_launch();
     return PIC_OK;
 }

@@ -110,3 +110,41 @@ def test_batch_rejects_bad_members(F):
     g = F.sim_from_workload(wl, 2 * DT_CFL_6 * 1.5, preconditioner="gnn")
     with pytest.raises(F.PicError):
         F.Batch([g])
+
+
+@pytest.mark.parametrize("precision", ["mixed", "plain"])
+def test_batch_with_multigrid_member(F, precision):
+    """A member with 8,192 or more interior nodes completes with the
+    multigrid-preconditioned solve in the batch too (the batch's completions
+    run as one launch: that member's multigrid PCG beside the others'
+    Jacobi-PCG), and the batch follows stepping each run alone to the solve
+    tolerance (the batch gives the multigrid member fewer blocks, so the
+    reduction order differs)."""
+    cases = [(22, 20000, 50), (6, 8000, 51), (8, 20000, 52)]
+    wls = []
+    for cells, n, seed in cases:
+        wl = W.thermal_plasma_cube(n_cells=cells, n_particles=n, seed=seed)
+        wls.append((wl, 2 * DT_CFL_6 * 6 / cells))
+    solo = [F.sim_from_workload(wl, dt, precision=precision, cg_tol=1e-13) for wl, dt in wls]
+    memb = [F.sim_from_workload(wl, dt, precision=precision, cg_tol=1e-13) for wl, dt in wls]
+    assert solo[0].mesh.n_int_nodes >= 8192
+    batch = F.Batch(memb)
+    steps = 13
+    batch.step(steps)
+    for s in solo:
+        s.step(steps)
+    info = batch.info()
+    assert info["graph"] == 1 and info["graph_launches"] == 2, info
+    assert info["completion_blocks_per_sm"] in (2, 3, 4) and info["completion_build"] == "64-register", info
+    tol = 1e-9 if precision == "plain" else 1e-6
+    for a, b in zip(solo, memb):
+        for f in ("E", "RHO", "G"):
+            ref = a.field(f)
+            assert np.abs(b.field(f) - ref).max() <= tol * np.abs(ref).max(), f
+        d = b.diag()
+        assert d["continuity_abs"] <= 1e-12 * d["rho_max"]
+        assert d["gauss_abs"] <= 1e-12 * d["rho_max"]
+    # the multigrid member's completion takes the iterations it takes alone (a
+    # Jacobi-PCG completion of that mesh would take several times more)
+    it_b, it_s = memb[0].diag()["completion_iters"], solo[0].diag()["completion_iters"]
+    assert it_b <= 30 and abs(it_b - it_s) <= 3, (it_b, it_s)
