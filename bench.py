@@ -43,12 +43,12 @@ CLOCK_LOG = None   # --clock-log: where the clock samples of the timed region go
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (non-tensor) nominal rate
 # DRAM bytes over algorithmic bytes of the MIXED Newmark launch
 # (k_pcg_persistent<1>), from one ncu capture of that kernel (its current code)
-# on the 64^3 plasma ball: 15.665 GB (dram__bytes_read.sum +
+# on the 64^3 plasma ball: 15.664 GB (dram__bytes_read.sum +
 # dram__bytes_write.sum) for 60 FP32 + 2 FP64 iterations whose algorithmic
 # bytes are 19.938 GB (below 1: with the matrix loaded evict-first, the
 # vectors written each iteration stay in L2).  The FP64 Newmark form has no
 # capture of its current code: its traffic is reported as null.
-TRAFFIC_RATIO_MIXED = (15.561788 + 0.102893) / 19.937848
+TRAFFIC_RATIO_MIXED = (15.561853 + 0.102376) / 19.937848
 TRAFFIC_RATIO_PLAIN = None
 
 
