@@ -49,6 +49,11 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (non-tensor) nominal rate
 # vectors written each iteration stay in L2).  The FP64 Newmark form has no
 # capture of its current code: its traffic is reported as null.
 TRAFFIC_RATIO_MIXED = (15.561853 + 0.102376) / 19.937848
+# DRAM bytes of one MIXED push launch (k_push_mixed<0>) on the 64^3 plasma-ball
+# mesh with 4M + 4M particles, from one ncu capture of the current kernel:
+# 0.408 + 0.336 GB (93 B per particle, per-tet bytes included); scaled to a
+# launch by the particles it pushes
+PUSH_TRAFFIC_SMALL = (0.408e9 + 0.336e9, 8_000_000)
 TRAFFIC_RATIO_PLAIN = None
 
 
@@ -731,6 +736,18 @@ def gpu_arm(args):
                 "algorithmic_bytes_per_launch": alg, "avg_launch_ms": round(avg_ms, 5),
                 "fp64": fp64}
 
+    # the push, the other hot kernel (issue- and latency-bound: its fraction
+    # of HBM is reported, not claimed as the bound)
+    push_alg = push_bytes(int(alive_m), mesh.n_tets, "mixed", len(wl.species))
+    push_ach = push_alg / (push_avg / 1e3) / 1e9
+    roofline_push = {"kernel": "k_push_mixed (fused gather/push/walk/deposit)", "bound": "issue/latency",
+                     "achieved": round(push_ach, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(push_ach / peak, 4), "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": push_alg, "avg_launch_ms": round(push_avg, 5),
+                     "traffic": PUSH_TRAFFIC_SMALL[0] * alive_m / PUSH_TRAFFIC_SMALL[1] if args.cells == 64 else None,
+                     "traffic_source": "ncu DRAM bytes of the same kernel on the same mesh with 8M particles, "
+                                       "scaled by the particles pushed"}
+
     # ---- learned preconditioner on the same workload ----
     gnn = None
     if not args.skip_gnn:
@@ -780,7 +797,7 @@ def gpu_arm(args):
             "completion_iters_last": diag_m["completion_iters"],
             "conservation_last": {"continuity_rel": diag_m["continuity_abs"] / max(diag_m["rho_max"], 1e-300),
                                   "gauss_rel": diag_m["gauss_abs"] / max(diag_m["rho_max"], 1e-300)},
-            "roofline": roofline,
+            "roofline": roofline, "roofline_push": roofline_push,
             "cpu_baseline": cpu,
             "e2e": None if args.skip_e2e else {"value": total_ps / e2e_s_max, "unit": "particle-steps/s",
                     "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
