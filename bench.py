@@ -17,6 +17,8 @@ Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|refere
         [--workload plasma_ball|thermal_cube] [--cells C] [--particles P]
 Under torchrun (N > 1) each rank runs an independent replica (the method's
 field solve couples the whole mesh, so there is nothing to shard): weak scaling.
+The side legs (learned preconditioner, beam, batch, single electron, pusher
+sweep, MIXED against the oracle) and the CPU baseline run at N = 1 only.
 """
 from __future__ import annotations
 
@@ -598,6 +600,12 @@ def gpu_arm(args):
     from paper_2102_06248_gb300 import fempic as F
 
     rank, world, local, dist = dist_setup(args.gpus)
+    if world > 1:
+        # the side legs and the CPU baseline do not depend on N and are
+        # reported by the N = 1 run; here they would hold every GPU meanwhile
+        args.skip_gnn = args.skip_beam = args.skip_batched = True
+        args.skip_larmor = args.skip_sweep = args.skip_mixed_error = True
+        args.no_cpu_baseline = True
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
