@@ -21,10 +21,7 @@ of A^-1 r, up to the constant r^T A^-1 r, so it needs no solve):
   L(z) = (z^T A z - 2 z^T r) / (r^T D^-1 r)
 
 Parameters are one float32 vector theta (layout in ``OFFSETS``); the network
-computes with their bfloat16 roundings (``bf16``).  relu'(0) = 0.  Applied
-as the preconditioner inside the flexible CG (``act_bf16``), the network
-stores the activations h_0 .. h_{L-1} between layers in bfloat16 (rounded
-to nearest even) and still accumulates in FP32; training keeps them in FP32.
+computes with their bfloat16 roundings (``bf16``).  relu'(0) = 0.
 
 Only the tests may import this module.
 """
@@ -99,11 +96,9 @@ class EdgeNet:
         self.a = logd - logd.mean()
         self.n = self.A.shape[0]
 
-    def forward(self, r: np.ndarray, theta: np.ndarray, act_bf16: bool = False):
+    def forward(self, r: np.ndarray, theta: np.ndarray):
         """z and the activations the backward pass needs (theta: float64 values
-        the network computes with, i.e. already rounded to bfloat16).  With
-        act_bf16 the activations passed between layers are rounded to
-        bfloat16, as in a preconditioner application."""
+        the network computes with, i.e. already rounded to bfloat16)."""
         p = unpack(theta)
         r = np.asarray(r, dtype=np.float64)
         rho = np.sqrt(np.mean(r * r / self.d))
@@ -111,13 +106,12 @@ class EdgeNet:
             return np.zeros(self.n), None
         x = r / (np.sqrt(self.d) * rho)
         pre = [np.outer(x, p["U"]) + np.outer(self.a, p["V"]) + p["c"]]
-        stored = (lambda v: bf16(v.astype(np.float32))) if act_bf16 else (lambda v: v)
-        h = [stored(relu(pre[0]))]
+        h = [relu(pre[0])]
         g = [None]
         for l in range(1, LAYERS + 1):
             g.append(self.Ahat @ h[l - 1])
             pre.append(h[l - 1] @ p[f"W{l}"].T + g[l] @ p[f"Q{l}"].T + p[f"b{l}"])
-            h.append(stored(relu(pre[l])) if l < LAYERS else relu(pre[l]))
+            h.append(relu(pre[l]))
         y = h[LAYERS] @ p["o"] + p["d0"][0]
         z = rho * (x + y) / np.sqrt(self.d)
         return z, {"rho": rho, "x": x, "pre": pre, "h": h, "g": g, "y": y}
