@@ -405,7 +405,8 @@ typedef struct {
     /* tuning times (ms) per candidate: blocks per SM 2, 3, 4 with build 0;
      * 2, 3 with build 1; 5, 6 with build 2; 7, 8 with build 3.  -1: not
      * timed (the choice came from an earlier batch of the same shape in this
-     * process) */
+     * process, or, for the completion of a batch with multigrid members, the
+     * candidate's build does not exist for the combined launch) */
     double tune_newmark_ms[9];
     double tune_completion_ms[9];
 } pic_batch_info_t;
