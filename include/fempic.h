@@ -360,7 +360,10 @@ int pic_gnn_get_weights(pic_sim *sim, float *w, int64_t n);
 /* Sets the weights (host array of PIC_GNN_PARAMS floats); marks the network usable. */
 int pic_gnn_set_weights(pic_sim *sim, const float *w, int64_t n);
 /* Applies the network to a residual: r_edges, z_edges are host arrays of
- * n_edges doubles in canonical edge order (wall edges are ignored / set to 0). */
+ * n_edges doubles in canonical edge order (wall edges are ignored / set to 0).
+ * This is the application the flexible PCG makes (message-passing layers on
+ * the tensor cores, TF32 products of split activations, FP32 sums); training
+ * runs its own FP32 forward pass. */
 int pic_gnn_apply(pic_sim *sim, const double *r_edges, double *z_edges);
 /* Training loss and its gradient for one residual (host arrays; grad holds
  * PIC_GNN_PARAMS doubles, d loss / d weight at the bfloat16 weights). */

@@ -827,7 +827,8 @@ int pic_gnn_apply(pic_sim *sim, const double *r_edges, double *z_edges) {
     const int n = m->n_int_edges;
     DevBuf<double> dr, dz;
     if ((rc = gnn_in(s, r_edges, dr)) || (rc = dz.alloc((size_t)std::max(n, 1)))) return rc;
-    if ((rc = gnn_forward(s, dr.p, dz.p, true))) return rc;
+    // the inference path the flexible PCG applies (tensor-core layers)
+    if ((rc = gnn_forward(s, dr.p, dz.p, false))) return rc;
     std::vector<double> h((size_t)std::max(n, 1));
     FP_CUDA(cudaMemcpyAsync(h.data(), dz.p, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
     FP_CUDA(cudaStreamSynchronize(s->stream));

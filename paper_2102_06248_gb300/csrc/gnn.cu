@@ -19,11 +19,14 @@
 //   L = (z^T A z - 2 z^T r) / (r^T D^-1 r),
 // the A-norm error of z against A^-1 r up to a constant (no solve needed).
 //
-// Layout: one warp per row, lane f = feature f, activations row-major
-// (32 floats = 128 B per row), so a neighbour's features are one coalesced
-// load; the 32x32 products broadcast the row's features with shuffles and read
-// the weights from shared memory (transposed where that avoids bank
-// conflicts).  Every reduction (weight gradients, rho, the loss, the PCG dot
+// Layout: activations row-major (32 floats = 128 B per row).  Training: one
+// warp per row, lane f = feature f, so a neighbour's features are one
+// coalesced load; the 32x32 products broadcast the row's features with
+// shuffles and read the weights from shared memory (transposed where that
+// avoids bank conflicts).  A preconditioner application runs its layers on
+// the tensor cores instead (k_layer_tc: 16-row tiles, TF32 products of split
+// activations), since the training layout spends most of its issue slots on
+// shuffles and shared loads rather than on the data.  Every reduction (weight gradients, rho, the loss, the PCG dot
 // products) uses per-block partials combined in a fixed order: results do not
 // depend on scheduling.
 #include <cuda_bf16.h>
@@ -197,10 +200,10 @@ __device__ __forceinline__ float aggregate(int i, const int *__restrict__ sp, co
     return acc;
 }
 
-// one message-passing layer; the last one also forms z.  KEEP: store the
-// aggregates and pre-activations the backward pass reads (a preconditioner
-// application inside the flexible PCG stores only h)
-template <bool LAST, bool KEEP>
+// one message-passing layer of the training forward pass; the last one also
+// forms z.  It stores the aggregates and pre-activations the backward pass
+// reads (a preconditioner application uses k_layer_tc below instead)
+template <bool LAST>
 __global__ void __launch_bounds__(kT) k_layer(int n, const int *__restrict__ sp, const int *__restrict__ sw,
                                              const int *__restrict__ col, const float *__restrict__ ahat,
                                              const float *__restrict__ hp, const unsigned short *__restrict__ th,
@@ -232,16 +235,186 @@ __global__ void __launch_bounds__(kT) k_layer(int n, const int *__restrict__ sp,
             p = fmaf(Qt[k * kH + lane], __shfl_sync(0xFFFFFFFFu, gi, k), p);
         }
         const float hn = fmaxf(p, 0.0f);
-        if (KEEP) {
-            g[(size_t)i * kH + lane] = gi;
-            pre[(size_t)i * kH + lane] = p;
-        }
-        if (!LAST || KEEP) h[(size_t)i * kH + lane] = hn;
+        g[(size_t)i * kH + lane] = gi;
+        pre[(size_t)i * kH + lane] = p;
+        h[(size_t)i * kH + lane] = hn;
         if (LAST) {
             float y = osh[lane] * hn;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) y += __shfl_down_sync(0xFFFFFFFFu, y, o);
             if (lane == 0) z[i] = fma(r[i], Dinv[i], rho * (double)(y + d0) * isd[i]);
+        }
+    }
+}
+
+// ---- inference layer on the tensor cores ----
+// The preconditioner application inside the flexible PCG (no backward pass,
+// so nothing but h is stored).  A warp takes a tile of 16 consecutive rows,
+// half of one SELL slice, so every row of the tile has the slice's width.
+//  1. Aggregation: lane (row rr = lane & 15, half = lane >> 4) sums 16
+//     features of its row over the row's entries: the entry's column and
+//     weight are one load each (the two lanes of a row read the same word),
+//     the neighbour's 16 features four 16-byte loads.  The row's own h and
+//     its aggregate g go to the warp's tile S[16][64] in shared memory.
+//  2. The 16 x 64 by 64 x 32 product [h g] [W Q]^T on mma.sync m16n8k8 TF32
+//     with FP32 accumulation.  The weights are bfloat16 values, exact in TF32;
+//     each activation is split as hi + lo with hi = TF32(a), lo = TF32(a - hi)
+//     (two products per tile), so the products carry ~22 significant bits,
+//     as close to the FP32 layer as the FP32 sums themselves.
+// Fragment layouts (PTX ISA, m16n8k8 .tf32; g = lane >> 2, t = lane & 3):
+//   A: a0 (g, t), a1 (g + 8, t), a2 (g, t + 4), a3 (g + 8, t + 4)
+//   B: b0 (k = t, n = g), b1 (k = t + 4, n = g)
+//   C: c0 (g, 2t), c1 (g, 2t + 1), c2 (g + 8, 2t), c3 (g + 8, 2t + 1)
+constexpr int kTileRows = 16;
+constexpr int kSRow = 2 * kH + 4;       // padded row of S: conflict-free fragment loads
+constexpr int kTcBlocksPerSm = 4;
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float c[4], const uint32_t a[4], float2 b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(__float_as_uint(b.x)), "r"(__float_as_uint(b.y)));
+}
+
+__device__ __forceinline__ void fma4(float4 &acc, float a, float4 v) {
+    acc.x = fmaf(a, v.x, acc.x);
+    acc.y = fmaf(a, v.y, acc.y);
+    acc.z = fmaf(a, v.z, acc.z);
+    acc.w = fmaf(a, v.w, acc.w);
+}
+
+template <bool LAST>
+__global__ void __launch_bounds__(kT, kTcBlocksPerSm) k_layer_tc(int n, const int *__restrict__ sp,
+                                                                 const int *__restrict__ sw,
+                                                                 const int *__restrict__ col,
+                                                                 const float *__restrict__ ahat,
+                                                                 const float *__restrict__ hp,
+                                                                 const unsigned short *__restrict__ th, int off,
+                                                                 float *__restrict__ h, const double *__restrict__ r,
+                                                                 const double *__restrict__ Dinv,
+                                                                 const double *__restrict__ isd,
+                                                                 const double *__restrict__ nrm,
+                                                                 double *__restrict__ z) {
+    // B fragments of [W Q]^T for k-step ks and column tile nt at Bf[(ks * 4 + nt) * 32 + lane]
+    __shared__ __align__(16) float2 Bf[8 * 4 * 32];
+    __shared__ __align__(16) float S[kW][kTileRows * kSRow];
+    __shared__ float bsh[kH], osh[kH];
+    for (int q = threadIdx.x; q < 8 * 4 * 32; q += kT) {
+        const int ks = q >> 7, nt = (q >> 5) & 3, ln = q & 31;
+        const int f = nt * 8 + (ln >> 2), k0 = ks * 8 + (ln & 3), k1 = k0 + 4;
+        // column k of [W Q]^T row f: W[f][k] for k < 32, Q[f][k - 32] after
+        const float w0 = k0 < kH ? bf(th, off + f * kH + k0) : bf(th, off + kH * kH + f * kH + (k0 - kH));
+        const float w1 = k1 < kH ? bf(th, off + f * kH + k1) : bf(th, off + kH * kH + f * kH + (k1 - kH));
+        Bf[q] = make_float2(w0, w1);
+    }
+    if (threadIdx.x < kH) {
+        bsh[threadIdx.x] = bf(th, off + 2 * kH * kH + threadIdx.x);
+        osh[threadIdx.x] = LAST ? bf(th, kOffO + threadIdx.x) : 0.0f;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rr = lane & 15, half = lane >> 4;
+    const int g = lane >> 2, t4 = lane & 3;
+    float *Sw = S[warp];
+    const float d0 = LAST ? bf(th, kOffD0) : 0.0f;
+    const double rho = LAST ? rho_of(nrm, n) : 0.0;
+    const int ntiles = (n + kTileRows - 1) / kTileRows;
+    for (int tile = blockIdx.x * kW + warp; tile < ntiles; tile += gridDim.x * kW) {
+        const int sl = tile >> 1;
+        const int i = tile * kTileRows + rr;   // the row this lane aggregates
+        const int kb = sp[sl] + (tile & 1) * kTileRows + rr, kw = sw[sl];
+        float4 acc[4], hv[4];
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            acc[m] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            hv[m] = acc[m];
+        }
+        if (i < n) {
+            // SELL padding points at the row itself with weight 0
+#pragma unroll 2
+            for (int j = 0; j < kw; j++) {
+                const int c = col[kb + 32 * j];
+                const float a = ahat[kb + 32 * j];
+                const float4 *src = reinterpret_cast<const float4 *>(hp + (size_t)c * kH + half * 16);
+#pragma unroll
+                for (int m = 0; m < 4; m++) fma4(acc[m], a, __ldg(src + m));
+            }
+            const float4 *own = reinterpret_cast<const float4 *>(hp + (size_t)i * kH + half * 16);
+#pragma unroll
+            for (int m = 0; m < 4; m++) hv[m] = __ldg(own + m);
+        }
+        __syncwarp();   // the previous tile's fragment loads are done
+        float4 *srow = reinterpret_cast<float4 *>(Sw + rr * kSRow + half * 16);
+#pragma unroll
+        for (int m = 0; m < 4; m++) {
+            srow[m] = hv[m];        // columns 0..31: h
+            srow[8 + m] = acc[m];   // columns 32..63: g
+        }
+        __syncwarp();
+        float c[4][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; nt++) {
+            const float b0 = bsh[nt * 8 + 2 * t4], b1 = bsh[nt * 8 + 2 * t4 + 1];
+            c[nt][0] = b0;
+            c[nt][1] = b1;
+            c[nt][2] = b0;
+            c[nt][3] = b1;
+        }
+#pragma unroll
+        for (int ks = 0; ks < 8; ks++) {
+            const float *s0 = Sw + g * kSRow + ks * 8 + t4;
+            const float av[4] = {s0[0], s0[8 * kSRow], s0[4], s0[8 * kSRow + 4]};
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                hi[q] = to_tf32(av[q]);
+                lo[q] = to_tf32(av[q] - __uint_as_float(hi[q]));
+            }
+#pragma unroll
+            for (int nt = 0; nt < 4; nt++) {
+                const float2 b = Bf[(ks * 4 + nt) * 32 + lane];
+                mma_tf32(c[nt], lo, b);
+                mma_tf32(c[nt], hi, b);
+            }
+        }
+        const int i0 = tile * kTileRows + g, i1 = i0 + 8;
+        if (!LAST) {
+#pragma unroll
+            for (int nt = 0; nt < 4; nt++) {
+                const int f = nt * 8 + 2 * t4;
+                if (i0 < n)
+                    *reinterpret_cast<float2 *>(h + (size_t)i0 * kH + f) =
+                        make_float2(fmaxf(c[nt][0], 0.0f), fmaxf(c[nt][1], 0.0f));
+                if (i1 < n)
+                    *reinterpret_cast<float2 *>(h + (size_t)i1 * kH + f) =
+                        make_float2(fmaxf(c[nt][2], 0.0f), fmaxf(c[nt][3], 0.0f));
+            }
+        } else {
+            float y0 = 0.0f, y1 = 0.0f;
+#pragma unroll
+            for (int nt = 0; nt < 4; nt++) {
+                const int f = nt * 8 + 2 * t4;
+                y0 = fmaf(osh[f], fmaxf(c[nt][0], 0.0f), y0);
+                y0 = fmaf(osh[f + 1], fmaxf(c[nt][1], 0.0f), y0);
+                y1 = fmaf(osh[f], fmaxf(c[nt][2], 0.0f), y1);
+                y1 = fmaf(osh[f + 1], fmaxf(c[nt][3], 0.0f), y1);
+            }
+#pragma unroll
+            for (int o = 1; o < 4; o <<= 1) {
+                y0 += __shfl_xor_sync(0xFFFFFFFFu, y0, o);
+                y1 += __shfl_xor_sync(0xFFFFFFFFu, y1, o);
+            }
+            if (t4 == 0) {
+                if (i0 < n) z[i0] = fma(r[i0], Dinv[i0], rho * (double)(y0 + d0) * isd[i0]);
+                if (i1 < n) z[i1] = fma(r[i1], Dinv[i1], rho * (double)(y1 + d0) * isd[i1]);
+            }
         }
     }
 }
@@ -437,6 +610,19 @@ double hash01(unsigned long long seed, unsigned long long i) {
 // one warp per row for the kernels whose rows wait on neighbour loads
 int rows_grid(int n) { return std::max(1, std::min((n + kW - 1) / kW, 152 * 64)); }
 
+// the tensor-core layer: one 16-row tile per warp at a time, kTcBlocksPerSm blocks per SM
+int tc_grid(int n) {
+    static int sms = 0;
+    if (sms <= 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            sms <= 0)
+            sms = 1;
+    }
+    const int tiles = (n + kTileRows - 1) / kTileRows;
+    return std::max(1, std::min((tiles + kW - 1) / kW, sms * kTcBlocksPerSm));
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -554,16 +740,16 @@ int gnn_forward(Sim *s, const double *r, double *z, bool keep) {
     if ((rc = gnn_reduce_launch(s, 1, G.sc.p))) return rc;
     if (keep) { k_embed<true><<<kGB, kT, 0, st>>>(n, r, G.isd.p, G.sc.p, G.feat_a.p, G.theta_bf.p, G.xin.p, G.pre[0].p, G.h[0].p); note_launch(); }
     else { k_embed<false><<<kGB, kT, 0, st>>>(n, r, G.isd.p, G.sc.p, G.feat_a.p, G.theta_bf.p, G.xin.p, G.pre[0].p, G.h[0].p); note_launch(); }
-    const int gr = rows_grid(n);
+    const int gr = rows_grid(n), gt = tc_grid(n);
     for (int l = 1; l <= 3; l++) {
         const int off = kOffL + (l - 1) * kLayer;
         // without keep, layers 1 and 2 ping-pong between h[0] and h[1]
         const float *hin = keep ? G.h[l - 1].p : G.h[(l - 1) & 1].p;
         float *hout = keep ? G.h[l].p : G.h[l & 1].p;
-        if (l < 3 && keep) { k_layer<false, true><<<gr, kT, 0, st>>>(n, A.ptr.p, A.width.p, A.col.p, G.ahat.p, hin, G.theta_bf.p, off, G.g[l].p, G.pre[l].p, hout, r, s->Dinv.p, G.isd.p, G.sc.p, z); note_launch(); }
-        else if (l < 3) { k_layer<false, false><<<gr, kT, 0, st>>>(n, A.ptr.p, A.width.p, A.col.p, G.ahat.p, hin, G.theta_bf.p, off, G.g[l].p, G.pre[l].p, hout, r, s->Dinv.p, G.isd.p, G.sc.p, z); note_launch(); }
-        else if (keep) { k_layer<true, true><<<gr, kT, 0, st>>>(n, A.ptr.p, A.width.p, A.col.p, G.ahat.p, hin, G.theta_bf.p, off, G.g[l].p, G.pre[l].p, hout, r, s->Dinv.p, G.isd.p, G.sc.p, z); note_launch(); }
-        else { k_layer<true, false><<<gr, kT, 0, st>>>(n, A.ptr.p, A.width.p, A.col.p, G.ahat.p, hin, G.theta_bf.p, off, G.g[l].p, G.pre[l].p, hout, r, s->Dinv.p, G.isd.p, G.sc.p, z); note_launch(); }
+        if (l < 3 && keep) { k_layer<false><<<gr, kT, 0, st>>>(n, A.ptr.p, A.width.p, A.col.p, G.ahat.p, hin, G.theta_bf.p, off, G.g[l].p, G.pre[l].p, hout, r, s->Dinv.p, G.isd.p, G.sc.p, z); note_launch(); }
+        else if (l < 3) { k_layer_tc<false><<<gt, kT, 0, st>>>(n, A.ptr.p, A.width.p, A.col.p, G.ahat.p, hin, G.theta_bf.p, off, hout, r, s->Dinv.p, G.isd.p, G.sc.p, z); note_launch(); }
+        else if (keep) { k_layer<true><<<gr, kT, 0, st>>>(n, A.ptr.p, A.width.p, A.col.p, G.ahat.p, hin, G.theta_bf.p, off, G.g[l].p, G.pre[l].p, hout, r, s->Dinv.p, G.isd.p, G.sc.p, z); note_launch(); }
+        else { k_layer_tc<true><<<gt, kT, 0, st>>>(n, A.ptr.p, A.width.p, A.col.p, G.ahat.p, hin, G.theta_bf.p, off, hout, r, s->Dinv.p, G.isd.p, G.sc.p, z); note_launch(); }
     }
     FP_CUDA(cudaGetLastError());
     return PIC_OK;
