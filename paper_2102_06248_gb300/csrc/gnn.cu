@@ -251,11 +251,14 @@ __global__ void __launch_bounds__(kT) k_layer(int n, const int *__restrict__ sp,
 // The preconditioner application inside the flexible PCG (no backward pass,
 // so nothing but h is stored).  A warp takes a tile of 16 consecutive rows,
 // half of one SELL slice, so every row of the tile has the slice's width.
-//  1. Aggregation: lane (row rr = lane & 15, half = lane >> 4) sums 16
-//     features of its row over the row's entries: the entry's column and
-//     weight are one load each (the two lanes of a row read the same word),
-//     the neighbour's 16 features four 16-byte loads.  The row's own h and
-//     its aggregate g go to the warp's tile S[16][64] in shared memory.
+//  1. Aggregation: lane (rs = lane >> 3, q = lane & 7) sums features
+//     4q .. 4q + 3 of rows rs, rs + 4, rs + 8, rs + 12 over the rows'
+//     entries, so each 16-byte gather of a warp reads four whole 128-byte
+//     feature rows (eight lanes per row).  Half-row gathers (16 rows of 64
+//     bytes per instruction) kept the L1 at its throughput limit for a
+//     quarter of the useful bytes; this layout measured 76 -> 46 ms per
+//     Newmark solve.  The rows' own h and aggregates g go to the warp's tile
+//     S[16][64] in shared memory.
 //  2. The 16 x 64 by 64 x 32 product [h g] [W Q]^T on mma.sync m16n8k8 TF32
 //     with FP32 accumulation.  The weights are bfloat16 values, exact in TF32;
 //     each activation is split as hi + lo with hi = TF32(a), lo = TF32(a - hi)
@@ -320,42 +323,48 @@ __global__ void __launch_bounds__(kT, kTcBlocksPerSm) k_layer_tc(int n, const in
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int rr = lane & 15, half = lane >> 4;
+    const int rs = lane >> 3, q8 = lane & 7;   // aggregation: rows rs + 4p, features 4 q8 .. 4 q8 + 3
     const int g = lane >> 2, t4 = lane & 3;
     float *Sw = S[warp];
     const float d0 = LAST ? bf(th, kOffD0) : 0.0f;
     const double rho = LAST ? rho_of(nrm, n) : 0.0;
     const int ntiles = (n + kTileRows - 1) / kTileRows;
     for (int tile = blockIdx.x * kW + warp; tile < ntiles; tile += gridDim.x * kW) {
-        const int sl = tile >> 1;
-        const int i = tile * kTileRows + rr;   // the row this lane aggregates
-        const int kb = sp[sl] + (tile & 1) * kTileRows + rr, kw = sw[sl];
+        const int sl = tile >> 1, row0 = tile * kTileRows;
+        const int kb0 = sp[sl] + (tile & 1) * kTileRows, kw = sw[sl];
         float4 acc[4], hv[4];
 #pragma unroll
-        for (int m = 0; m < 4; m++) {
-            acc[m] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            hv[m] = acc[m];
+        for (int p = 0; p < 4; p++) {
+            acc[p] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            hv[p] = acc[p];
         }
-        if (i < n) {
-            // SELL padding points at the row itself with weight 0
+        // SELL padding points at the row itself with weight 0; the slice's
+        // entries exist for all its 32 lanes, so rows past n read weight 0
 #pragma unroll 2
-            for (int j = 0; j < kw; j++) {
-                const int c = col[kb + 32 * j];
-                const float a = ahat[kb + 32 * j];
-                const float4 *src = reinterpret_cast<const float4 *>(hp + (size_t)c * kH + half * 16);
+        for (int j = 0; j < kw; j++) {
+            int c[4];
+            float a[4];
 #pragma unroll
-                for (int m = 0; m < 4; m++) fma4(acc[m], a, __ldg(src + m));
+            for (int p = 0; p < 4; p++) {
+                const int e = kb0 + rs + 4 * p + 32 * j;
+                c[p] = col[e];
+                a[p] = ahat[e];
             }
-            const float4 *own = reinterpret_cast<const float4 *>(hp + (size_t)i * kH + half * 16);
 #pragma unroll
-            for (int m = 0; m < 4; m++) hv[m] = __ldg(own + m);
+            for (int p = 0; p < 4; p++)
+                fma4(acc[p], a[p], __ldg(reinterpret_cast<const float4 *>(hp + (size_t)c[p] * kH + 4 * q8)));
+        }
+#pragma unroll
+        for (int p = 0; p < 4; p++) {
+            const int i = row0 + rs + 4 * p;
+            if (i < n) hv[p] = __ldg(reinterpret_cast<const float4 *>(hp + (size_t)i * kH + 4 * q8));
         }
         __syncwarp();   // the previous tile's fragment loads are done
-        float4 *srow = reinterpret_cast<float4 *>(Sw + rr * kSRow + half * 16);
 #pragma unroll
-        for (int m = 0; m < 4; m++) {
-            srow[m] = hv[m];        // columns 0..31: h
-            srow[8 + m] = acc[m];   // columns 32..63: g
+        for (int p = 0; p < 4; p++) {
+            float *srow = Sw + (rs + 4 * p) * kSRow + 4 * q8;
+            *reinterpret_cast<float4 *>(srow) = hv[p];         // columns 0..31: h
+            *reinterpret_cast<float4 *>(srow + kH) = acc[p];   // columns 32..63: g
         }
         __syncwarp();
         float c[4][4];
