@@ -363,7 +363,8 @@ def gnn_leg(F, torch, wl, dt, stream, args):
            "cg_ms_per_step": pr["cg"][0] / args.gnn_steps, "cg_iters": iters, "jacobi_cg_iters_before": jac_iters,
            "continuity_rel": d["continuity_abs"] / max(d["rho_max"], 1e-300),
            "gauss_rel": d["gauss_abs"] / max(d["rho_max"], 1e-300),
-           "solve": "flexible PCG (Polak-Ribiere) with the network, 3 message-passing layers, hidden 32, bf16 weights"}
+           "solve": ("flexible PCG (Polak-Ribiere) with the network, 3 message-passing layers, hidden 32, bf16 weights; "
+                     "inference layers on the tensor cores (mma.sync TF32 on split FP32 activations, FP32 sums)")}
     del sim
     return out
 
