@@ -56,6 +56,10 @@ TRAFFIC_RATIO_MIXED = (15.561853 + 0.102376) / 19.937848
 # 0.408 + 0.336 GB (93 B per particle, per-tet bytes included); scaled to a
 # launch by the particles it pushes
 PUSH_TRAFFIC_SMALL = (0.408e9 + 0.336e9, 8_000_000)
+# Warp instructions of the same capture (smsp__inst_executed.sum): 245M for the
+# 8M particles, the push's binding resource being instruction issue
+PUSH_WARP_INST_SMALL = (245.0e6, 8_000_000)
+SCHEDULERS_PER_SM = 4   # warp schedulers per SM, one warp instruction issued per cycle each
 TRAFFIC_RATIO_PLAIN = None
 
 
@@ -260,6 +264,34 @@ def push_bytes(n_particles: int, n_tets: int, precision: str, n_species: int = 1
     acc = 80 * (n_species if precision == "mixed" else 1)
     per_tet = 12 * r + 10 * r + acc                 # barycentric map, coefficients, accumulator write
     return n_particles * per_particle + n_tets * per_tet
+
+
+def measured_sm_mhz() -> float:
+    """Maximum SM clock of the machine's GPUs from MEASURED_PEAKS.json (the
+    nominal 2070 MHz when the file or the key is missing)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f).get("sm_max_mhz", 2070.0))
+    except (OSError, ValueError, TypeError):
+        return 2070.0
+
+
+def issue_roofline(n_particles: float, avg_ms: float, sms: int, sm_mhz: float) -> dict:
+    """The push against its binding resource, instruction issue: the warp
+    instructions of one launch (the ncu count per particle of the captured
+    launch times the particles pushed) over its duration, against every
+    scheduler issuing one warp instruction per cycle at the given SM clock."""
+    per_particle = PUSH_WARP_INST_SMALL[0] / PUSH_WARP_INST_SMALL[1]
+    inst = per_particle * n_particles
+    achieved = inst / (avg_ms / 1e3)
+    peak = float(sms) * SCHEDULERS_PER_SM * sm_mhz * 1e6
+    return {"bound": "issue", "warp_instructions_per_particle": round(per_particle, 2),
+            "achieved_warp_inst_per_s": achieved, "peak_warp_inst_per_s": peak,
+            "frac": round(achieved / peak, 4),
+            "peak_source": f"{sms} SMs x {SCHEDULERS_PER_SM} schedulers x {sm_mhz:.0f} MHz",
+            "source": "ncu smsp__inst_executed.sum of the same kernel on the same mesh with 8M particles, "
+                      "scaled by the particles pushed"}
 
 
 def pcg_iter_bytes(n_rows: int, nnz: int) -> float:
@@ -755,7 +787,11 @@ def gpu_arm(args):
                      "algorithmic_bytes_per_launch": push_alg, "avg_launch_ms": round(push_avg, 5),
                      "traffic": PUSH_TRAFFIC_SMALL[0] * alive_m / PUSH_TRAFFIC_SMALL[1] if args.cells == 64 else None,
                      "traffic_source": "ncu DRAM bytes of the same kernel on the same mesh with 8M particles, "
-                                       "scaled by the particles pushed"}
+                                       "scaled by the particles pushed",
+                     "issue": issue_roofline(alive_m, push_avg,
+                                             torch.cuda.get_device_properties(device).multi_processor_count,
+                                             measured_sm_mhz())
+                     if args.cells == 64 and args.workload == "plasma_ball" else None}
 
     # ---- learned preconditioner on the same workload ----
     gnn = None

@@ -88,3 +88,20 @@ def test_oracle_replicas_on_two_cores():
     assert len(res) == 2
     assert all(k == 2 and n == res[0][0] and el > 0 for n, k, el in res)
     assert rate == pytest.approx(sum(n * k for n, k, _ in res) / max(el for _, _, el in res))
+
+
+def test_push_issue_roofline():
+    """The push's issue roofline: the captured launch (245M warp instructions
+    for 8M particles in 0.434 ms) on 152 SMs at 2070 MHz issues at 0.45 of the
+    four schedulers' one instruction per cycle, as ncu's issue-active share
+    (45.5%) says; the count scales with the particles pushed."""
+    sys.path.insert(0, ROOT)
+    import bench
+    r = bench.issue_roofline(8_000_000, 0.434, 152, 2070.0)
+    assert r["warp_instructions_per_particle"] == pytest.approx(30.62, abs=0.01)
+    assert r["peak_warp_inst_per_s"] == pytest.approx(152 * 4 * 2.07e9)
+    assert r["frac"] == pytest.approx(245e6 / 0.434e-3 / (152 * 4 * 2.07e9), abs=1e-4)
+    assert 0.44 < r["frac"] < 0.46
+    r2 = bench.issue_roofline(33_554_432, 1.88, 152, 2070.0)
+    assert r2["achieved_warp_inst_per_s"] == pytest.approx(245e6 / 8e6 * 33_554_432 / 1.88e-3)
+    assert bench.measured_sm_mhz() > 1000.0
