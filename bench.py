@@ -273,7 +273,7 @@ def measured_sm_mhz() -> float:
     try:
         with open(path) as f:
             return float(json.load(f).get("sm_max_mhz", 2070.0))
-    except (OSError, ValueError, TypeError):
+    except (OSError, ValueError, TypeError, AttributeError):
         return 2070.0
 
 
